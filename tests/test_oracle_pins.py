@@ -1,0 +1,471 @@
+"""Pins of the FP64 oracle to facts the paper and the mathematics fix.
+
+CPU only. Each test names the passage it checks. None of them re-types the
+oracle's formula: they compare against closed forms, library routines
+(numpy.linalg), brute force with exact rationals, or invariants.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from gen import synth
+from oracle import kmeans as km
+from oracle import krylov, mlp
+from oracle import sparse as osp
+from oracle import twolevel as tl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def csr_of(dense):
+    dense = np.asarray(dense)
+    rows, cols = np.nonzero(dense)
+    row_ptr = np.zeros(dense.shape[0] + 1, np.int64)
+    np.cumsum(np.bincount(rows, minlength=dense.shape[0]), out=row_ptr[1:])
+    return dense.shape[0], dense.shape[1], row_ptr, cols.astype(np.int32)
+
+
+def random_binary(n, f, p, seed):
+    rng = np.random.default_rng(seed)
+    return (rng.random((n, f)) < p).astype(np.int64)
+
+
+# ---------------------------------------------------------------- generator / RNG
+
+def test_splitmix64_published_output():
+    g = json.load(open(os.path.join(GOLDEN, "splitmix64.json")))
+    for t, hx in enumerate(g["outputs_hex"]):
+        assert km.splitmix64(g["seed"], t) == int(hx, 16)
+
+
+def test_generator_zipf_shape():
+    X = synth.zipf_binary(2000, 1000, 0.01, 1.1, seed=0)
+    assert X.row_ptr[0] == 0 and np.all(np.diff(X.row_ptr) >= 0)
+    assert X.col_idx.min() >= 0 and X.col_idx.max() < 1000
+    # expected nnz = density * N * F, within a few standard deviations
+    assert abs(X.nnz - 20000) < 1500
+    counts = np.sort(np.bincount(X.col_idx, minlength=1000))[::-1]
+    q = synth.zipf_column_probs(1000, 0.01, 1.1)
+    # the heaviest columns follow the power law of their rank
+    assert abs(counts[0] - q[0] * 2000) < 5 * math.sqrt(2000) + 1
+    assert counts[:10].sum() > counts[500:].sum() / 10
+
+
+# ---------------------------------------------------------------- operator / CSC
+
+def test_csc_is_stable_transpose():
+    D = random_binary(30, 17, 0.3, 1)
+    n, f, rp, ci = csr_of(D)
+    cp, ri = osp.csc_pattern(n, f, rp, ci)
+    for j in range(f):
+        rows = ri[cp[j]:cp[j + 1]]
+        assert np.array_equal(rows, np.nonzero(D[:, j])[0])
+
+
+def test_apply_A_matches_dense():
+    D = random_binary(40, 25, 0.2, 2)
+    M = osp.from_csr(*csr_of(D))
+    v = np.random.default_rng(0).standard_normal(25)
+    ref = (D.T @ D + 0.3 * np.eye(25)) @ v
+    assert np.allclose(osp.apply_A(M, 0.3, v), ref, rtol=1e-14, atol=1e-12)
+
+
+# ---------------------------------------------------------------- closed forms (Eq. 1, Eq. rr)
+
+def test_single_feature_closed_form():
+    """One feature: w = x^T y / (x^T x + lambda) (Eq. rr with F = 1)."""
+    x = np.array([1, 0, 1, 1, 0, 1])[:, None]
+    y = np.array([0.5, -1.0, 2.0, 0.25, 3.0, -0.75])
+    lam = 0.37
+    M = osp.from_csr(*csr_of(x))
+    b = osp.rhs(M, y)
+    w_exact = (x[:, 0] @ y) / (x[:, 0] @ x[:, 0] + lam)
+    A = lambda v: osp.apply_A(M, lam, v)
+    assert abs(krylov.cg(A, b, tol=1e-14).w[0] - w_exact) < 1e-14
+    two = tl.setup_binary(*csr_of(x), lam, 1)
+    assert abs(krylov.pcg(two.A, two.apply, b, tol=1e-14).w[0] - w_exact) < 1e-14
+
+
+def test_disjoint_supports_diagonal_system():
+    """Disjoint column supports make X^T X diagonal: DCG finishes in one step
+    and w_i = x_i^T y / (n_i + lambda)."""
+    D = np.zeros((9, 3), np.int64)
+    D[0:2, 0] = 1
+    D[2:7, 1] = 1
+    D[7:9, 2] = 1
+    y = np.arange(1.0, 10.0)
+    lam = 0.5
+    M = osp.from_csr(*csr_of(D))
+    A = lambda v: osp.apply_A(M, lam, v)
+    b = osp.rhs(M, y)
+    d = osp.col_sq_norms(M) + lam
+    res = krylov.dcg(A, d, b, tol=1e-14)
+    assert res.iters == 1
+    expect = np.array([y[0:2].sum() / 2.5, y[2:7].sum() / 5.5, y[7:9].sum() / 2.5])
+    assert np.allclose(res.w, expect, rtol=1e-15)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_solvers_agree_with_dense_solve(seed):
+    """CG, DCG and two-level PCG reach the solution of Eq. (1) given by a dense solve."""
+    D = random_binary(60, 40, 0.15, seed)
+    D[:, 5] = D[:, 3]                      # a duplicated feature
+    lam = 0.05
+    n, f, rp, ci = csr_of(D)
+    y = np.random.default_rng(seed).standard_normal(n)
+    two = tl.setup_binary(n, f, rp, ci, lam, 8, seed=seed)
+    b = osp.rhs(two.M, y)
+    w_ref = np.linalg.solve(D.T @ D + lam * np.eye(f), D.T @ y)
+    for res in (krylov.cg(two.A, b, tol=1e-13), krylov.dcg(two.A, two.d, b, tol=1e-13),
+                krylov.pcg(two.A, two.apply, b, tol=1e-13)):
+        assert np.linalg.norm(res.w - w_ref) / np.linalg.norm(w_ref) < 1e-10
+        assert res.true_rel_res <= 1e-13
+
+
+# ---------------------------------------------------------------- Cholesky (Section 4, LAPACK's role)
+
+def test_cholesky_against_library():
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((30, 30))
+    A = B @ B.T + 0.1 * np.eye(30)
+    L = tl.cholesky(A)
+    assert np.allclose(L, np.linalg.cholesky(A), rtol=1e-12, atol=1e-12)
+    assert np.allclose(np.triu(L, 1), 0.0)
+    b = rng.standard_normal(30)
+    assert np.allclose(tl.chol_solve(L, b), np.linalg.solve(A, b), rtol=1e-10)
+    with pytest.raises(tl.NotSPD):
+        tl.cholesky(np.array([[1.0, 2.0], [2.0, 1.0]]))
+
+
+# ---------------------------------------------------------------- P and the coarse operator (Section 3.2)
+
+def test_prolongation_orthonormal_and_averaging():
+    labels = np.array([0, 1, 0, 2, 1, 0, 2, 2, 2], np.int32)
+    n_S = np.bincount(labels).astype(np.int64)
+    P = tl.prolongation_dense(labels, tl.prolong_scale(n_S))
+    assert np.allclose(P.T @ P, np.eye(3), atol=1e-15)
+    Pa = tl.averaging_dense(labels, n_S)
+    # the averaging operator gives diag(1/n_S), not a projection
+    assert np.allclose(Pa.T @ Pa, np.diag(1.0 / n_S), atol=1e-15)
+    r = np.arange(9.0)
+    assert np.allclose(tl.restrict(labels, tl.prolong_scale(n_S), r), P.T @ r)
+    e = np.array([1.0, -2.0, 0.5])
+    assert np.allclose(tl.prolong(labels, tl.prolong_scale(n_S), e), P @ e)
+
+
+@pytest.mark.parametrize("seed", [0, 4])
+def test_galerkin_coarse_operator(seed):
+    """A_c built from the exact integer Gram equals P^T A P formed densely."""
+    D = random_binary(50, 30, 0.2, seed)
+    lam = 0.01
+    n, f, rp, ci = csr_of(D)
+    two = tl.setup_binary(n, f, rp, ci, lam, 6, seed=seed)
+    P = tl.prolongation_dense(two.labels, two.s)
+    ref = P.T @ (D.T @ D + lam * np.eye(f)) @ P
+    assert np.allclose(two.Ac, ref, rtol=1e-13, atol=1e-13)
+    # the coarse regularisation equals the fine one because P^T P = I
+    X = D.astype(float)
+    assert np.allclose(tl.coarse_operator_dense(X, two.labels, two.s, lam), ref, rtol=1e-13)
+
+
+def test_theorem1_worked_example():
+    g = json.load(open(os.path.join(GOLDEN, "theorem1_example.json")))
+    base = np.array(g["x"], np.int64)
+    X, groups = synth.duplicated_features(base, g["counts"])
+    lam = 1e-3
+    n, f, rp, ci = csr_of(X)
+    two = tl.setup_binary(n, f, rp, ci, lam, 2, centers=[0, 2])
+    assert np.array_equal(two.labels, groups)
+    ev = np.linalg.eigvalsh(two.Ac) - lam
+    assert np.allclose(ev, g["eigenvalues"], rtol=1e-14)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_theorem1_random_duplicates(seed):
+    """Theorem 1: on duplicated features the non-zero spectrum of X^T X equals
+    that of P^T X^T X P, and its eigenvectors are constant within clusters,
+    so P P^T leaves them unchanged."""
+    rng = np.random.default_rng(seed)
+    base = (rng.random((40, 6)) < 0.4).astype(np.int64)
+    base[0] = 1                              # no all-zero columns
+    counts = [3, 1, 4, 2, 5, 2]
+    X, groups = synth.duplicated_features(base, counts)
+    perm = rng.permutation(X.shape[1])
+    X, groups = X[:, perm], groups[perm]
+    centers = [int(np.nonzero(groups == g)[0][0]) for g in range(6)]
+    n, f, rp, ci = csr_of(X)
+    two = tl.setup_binary(n, f, rp, ci, 1e-6, 6, centers=centers)
+    ev_c = np.sort(np.linalg.eigvalsh(two.Ac) - 1e-6)
+    ev, V = np.linalg.eigh((X.T @ X).astype(float))
+    nz = ev > 1e-9 * ev.max()
+    assert nz.sum() == np.linalg.matrix_rank(base)
+    assert np.allclose(np.sort(ev[nz]), ev_c[ev_c > 1e-9 * ev.max()], rtol=1e-10)
+    P = tl.prolongation_dense(two.labels, two.s)
+    assert np.allclose(P @ (P.T @ V[:, nz]), V[:, nz], atol=1e-10)
+
+
+# ---------------------------------------------------------------- the cycle (Section 3.1)
+
+def _tiny_two_level(seed=0, lam=0.02, k=7):
+    D = random_binary(45, 28, 0.18, seed)
+    n, f, rp, ci = csr_of(D)
+    two = tl.setup_binary(n, f, rp, ci, lam, k, seed=seed)
+    A = D.T @ D + lam * np.eye(f)
+    return two, A
+
+
+def _dense_of(fn, f):
+    return np.stack([fn(e) for e in np.eye(f)], axis=1)
+
+
+def test_coarse_correction_exact_on_coarse_space():
+    """The coarse-grid correction reproduces any error in range(P) exactly."""
+    two, A = _tiny_two_level()
+    P = tl.prolongation_dense(two.labels, two.s)
+    e_c = np.random.default_rng(1).standard_normal(two.k_eff)
+    e = P @ e_c
+    back = P @ two.coarse_correction(A @ e)
+    assert np.linalg.norm(back - e) <= 1e-12 * np.linalg.norm(e)
+
+
+def test_cycle_error_propagation_is_T():
+    """I - M^{-1} A equals T = (I - S A)(I - P A_c^{-1} P^T A)(I - S A)."""
+    two, A = _tiny_two_level(seed=2)
+    f = A.shape[0]
+    P = tl.prolongation_dense(two.labels, two.s)
+    S = two.omega * np.diag(1.0 / two.d)
+    I = np.eye(f)
+    T = (I - S @ A) @ (I - P @ np.linalg.solve(P.T @ A @ P, P.T @ A)) @ (I - S @ A)
+    Minv = _dense_of(two.apply, f)
+    assert np.allclose(I - Minv @ A, T, atol=1e-10)
+
+
+@pytest.mark.parametrize("seed", [0, 3, 5])
+def test_preconditioner_spd(seed):
+    two, A = _tiny_two_level(seed=seed)
+    f = A.shape[0]
+    Minv = _dense_of(two.apply, f)
+    assert np.linalg.norm(Minv - Minv.T) <= 1e-12 * np.linalg.norm(Minv)
+    assert np.linalg.eigvalsh(0.5 * (Minv + Minv.T)).min() > 0.0
+    np.linalg.cholesky(0.5 * (Minv + Minv.T))
+
+
+def test_omega_below_spectral_bound():
+    """w lambda_max(D^{-1} A) <= 1, so 2 D/w - A is SPD (smoother convergent in the A-norm)."""
+    two, A = _tiny_two_level(seed=6)
+    Dm = np.diag(1.0 / np.sqrt(two.d))
+    lmax = np.linalg.eigvalsh(Dm @ A @ Dm).max()
+    assert two.omega * lmax <= 1.0 + 1e-12
+    assert np.linalg.eigvalsh(2.0 / two.omega * np.diag(two.d) - A).min() > 0.0
+
+
+def test_two_level_fewer_iterations_than_cg_and_dcg():
+    """Section 4: the two-level method needs fewer iterations than CG and DCG."""
+    X, y, _, p = synth.workload("zipf_2000x1000")
+    two = tl.setup_binary(X.n_rows, X.n_cols, X.row_ptr, X.col_idx, 1e-2, 50, seed=0)
+    b = osp.rhs(two.M, y)
+    it_two = krylov.pcg(two.A, two.apply, b, tol=1e-8).iters
+    assert it_two < krylov.dcg(two.A, two.d, b, tol=1e-8).iters
+    assert it_two < krylov.cg(two.A, b, tol=1e-8).iters
+
+
+# ---------------------------------------------------------------- FCG (Algorithm 3)
+
+def test_fcg_matches_pcg_for_fixed_spd_preconditioner():
+    """With a fixed SPD preconditioner, FCG(1) and PCG generate the same iterates."""
+    two, A = _tiny_two_level(seed=7, lam=0.1)
+    b = A @ np.random.default_rng(7).standard_normal(A.shape[0])
+    Aop = lambda v: A @ v
+    r1 = krylov.pcg(Aop, two.apply, b, tol=1e-10)
+    r2 = krylov.fcg(Aop, lambda r, i: two.apply(r), b, m=1, tol=1e-10)
+    n = min(len(r1.history), len(r2.history))
+    assert abs(r1.iters - r2.iters) <= 1
+    h1, h2 = np.array(r1.history[:n]), np.array(r2.history[:n])
+    early = h1 > 1e-3          # before rounding differences are amplified
+    assert early.sum() >= 4
+    assert np.allclose(h1[early], h2[early], rtol=1e-6)
+    w = np.linalg.solve(A, b)
+    assert np.linalg.norm(r2.w - w) < 1e-8 * np.linalg.norm(w)
+
+
+def test_fcg_truncation_rule():
+    """m_0 = 0 and m_i = max(1, i mod (m+1)): with m = 3, FCG on an SPD system
+    with the identity preconditioner is CG and converges in <= f steps."""
+    rng = np.random.default_rng(8)
+    B = rng.standard_normal((12, 12))
+    A = B @ B.T + np.eye(12)
+    b = rng.standard_normal(12)
+    res = krylov.fcg(lambda v: A @ v, lambda r, i: r.copy(), b, m=3, tol=1e-12)
+    assert res.iters <= 14
+    assert np.allclose(res.w, np.linalg.solve(A, b), rtol=1e-9)
+
+
+# ---------------------------------------------------------------- k-means (Section 3.4)
+
+def _brute_force_lloyd(X, centers, max_iter):
+    """Lloyd with exact rational centroids and distances computed directly."""
+    X = np.asarray(X, np.int64)
+    N, F = X.shape
+    cols = [[Fraction(int(v)) for v in X[:, i]] for i in range(F)]
+    cent = [cols[c][:] for c in centers]
+    size = [1] * len(centers)
+    labels = None
+    it = 0
+    while it < max_iter:
+        it += 1
+        new = []
+        for i in range(F):
+            best, bd = None, None
+            for S in range(len(cent)):
+                if size[S] == 0:
+                    continue
+                dist = sum((cols[i][r] - cent[S][r]) ** 2 for r in range(N))
+                if bd is None or dist < bd:
+                    best, bd = S, dist
+            new.append(best)
+        if new == labels:
+            break
+        labels = new
+        k = len(cent)
+        size = [labels.count(S) for S in range(k)]
+        cent = [[sum((cols[i][r] for i in range(F) if labels[i] == S), Fraction(0)) / size[S]
+                 if size[S] else Fraction(0) for r in range(N)] for S in range(k)]
+    return np.array(labels, np.int32), it
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_lloyd_matches_brute_force(seed):
+    D = random_binary(12, 18, 0.35, 10 + seed)
+    n, f, rp, ci = csr_of(D)
+    cp, ri = osp.csc_pattern(n, f, rp, ci)
+    centers = np.random.default_rng(seed).choice(f, size=4, replace=False)
+    lab, it = km.lloyd_binary(n, f, rp, ci, cp, ri, centers, 50)
+    ref, it_ref = _brute_force_lloyd(D, centers, 50)
+    assert np.array_equal(lab, ref)
+    assert it == it_ref
+
+
+def test_lloyd_fixed_point_at_exit():
+    """At convergence every label is the exact argmin for the exact means."""
+    D = random_binary(15, 25, 0.3, 42)
+    n, f, rp, ci = csr_of(D)
+    cp, ri = osp.csc_pattern(n, f, rp, ci)
+    lab, it = km.lloyd_binary(n, f, rp, ci, cp, ri, [0, 5, 9, 17, 21], 100)
+    assert it < 100
+    X = D.astype(object)
+    for i in range(f):
+        best = None
+        for S in sorted(set(lab.tolist())):
+            members = np.nonzero(lab == S)[0]
+            mu = [Fraction(int(X[r, members].sum()), len(members)) for r in range(n)]
+            dist = sum((Fraction(int(X[r, i])) - mu[r]) ** 2 for r in range(n))
+            if best is None or dist < best[1]:
+                best = (S, dist)
+        assert lab[i] == best[0]
+
+
+def test_lloyd_recovers_duplicate_groups():
+    """Definition 1's ideal data with one centre per group: one assignment
+    step gives the groups and the second changes nothing."""
+    rng = np.random.default_rng(5)
+    base = (rng.random((30, 5)) < 0.5).astype(np.int64)
+    base[0] = 1
+    X, groups = synth.duplicated_features(base, [2, 3, 1, 4, 2])
+    perm = rng.permutation(X.shape[1])
+    X, groups = X[:, perm], groups[perm]
+    centers = [int(np.nonzero(groups == g)[0][-1]) for g in range(5)]
+    n, f, rp, ci = csr_of(X)
+    cp, ri = osp.csc_pattern(n, f, rp, ci)
+    lab, it = km.lloyd_binary(n, f, rp, ci, cp, ri, centers, 10)
+    assert np.array_equal(lab, groups)
+    assert it == 2
+
+
+def test_kmeanspp_picks_other_group():
+    """Seeding: a second centre is never drawn where the squared distance to
+    the first is zero (duplicates of the first centre)."""
+    base = np.array([[1, 0], [1, 1], [0, 1], [1, 0]], np.int64)
+    X, groups = synth.duplicated_features(base, [5, 4])
+    n, f, rp, ci = csr_of(X)
+    cp, ri = osp.csc_pattern(n, f, rp, ci)
+    for seed in range(20):
+        c = km.kmeanspp_binary(n, f, rp, ci, cp, ri, 2, seed)
+        assert groups[c[0]] != groups[c[1]]
+    # more centres than distinct features: the rest are the lowest unchosen ids
+    c = km.kmeanspp_binary(n, f, rp, ci, cp, ri, 4, 0)
+    assert len(set(c.tolist())) == 4
+
+
+def test_kmeanspp_draw_follows_d2_weights():
+    """The second centre is drawn with probability proportional to D^2."""
+    X = np.zeros((8, 4), np.int64)
+    X[0:1, 0] = 1          # feature 0: 1 row
+    X[0:2, 1] = 1          # feature 1: overlaps 0 in one row
+    X[2:6, 2] = 1          # feature 2: 4 disjoint rows
+    X[6:8, 3] = 1          # feature 3: 2 disjoint rows
+    n, f, rp, ci = csr_of(X)
+    cp, ri = osp.csc_pattern(n, f, rp, ci)
+    counts = np.zeros(4)
+    firsts = 0
+    for seed in range(4000):
+        c = km.kmeanspp_binary(n, f, rp, ci, cp, ri, 2, seed)
+        if c[0] == 0:
+            firsts += 1
+            counts[c[1]] += 1
+    # D^2 from feature 0: [0, 1, 5, 3] -> probabilities [0, 1/9, 5/9, 3/9]
+    p = counts / counts.sum()
+    assert counts[0] == 0
+    assert np.allclose(p[1:], [1 / 9, 5 / 9, 3 / 9], atol=0.06)
+    assert abs(firsts / 4000 - 0.25) < 0.04
+
+
+def test_dense_kmeans_recovers_groups():
+    rng = np.random.default_rng(9)
+    base = rng.standard_normal((20, 3)).astype(np.float32)
+    X, groups = synth.duplicated_features(base, [3, 2, 4])
+    centers = [int(np.nonzero(groups == g)[0][0]) for g in range(3)]
+    lab, it = km.lloyd_dense(X, centers, 10)
+    assert np.array_equal(lab, groups) and it == 2
+
+
+# ---------------------------------------------------------------- MLP (learned coarse correction)
+
+def test_mlp_gradients_finite_differences():
+    rng = np.random.default_rng(11)
+    p = mlp.init_params(6, 5, lambda n: rng.random(n))
+    for name in ("b1", "b2", "b3"):
+        p[name] = 0.1 * rng.standard_normal(p[name].shape)
+    X = rng.standard_normal((4, 6))
+    T = rng.standard_normal((4, 6))
+    g = mlp.backward(p, X, T)
+    h = 1e-6
+    for name in p:
+        flat = p[name].reshape(-1)
+        for idx in range(0, flat.size, max(1, flat.size // 7)):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp = mlp.loss(p, X, T)
+            flat[idx] = old - h
+            lm = mlp.loss(p, X, T)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            an = g[name].reshape(-1)[idx]
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_adam_first_step_is_lr_times_sign():
+    p = {"W": np.array([1.0, -2.0, 3.0])}
+    g = {"W": np.array([0.5, -7.0, 1e-3])}
+    mlp.adam_step(p, g, {}, lr=0.01)
+    assert np.allclose(p["W"], [0.99, -1.99, 2.99], atol=1e-6)
+
+
+def test_learned_correction_positively_homogeneous():
+    rng = np.random.default_rng(12)
+    p = mlp.init_params(5, 4, lambda n: rng.random(n))
+    rc = rng.standard_normal(5)
+    assert np.allclose(mlp.coarse_correction(p, 3.5 * rc), 3.5 * mlp.coarse_correction(p, rc))
