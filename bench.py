@@ -1,0 +1,423 @@
+"""Benchmark: seconds to relative residual 1e-8 for two-level PCG on GB300.
+
+One step = one pass of the whole hot path over the workload: setup (k-means++
+clustering, coarse Gram, Cholesky factor, smoother) at the first lambda, then
+for every lambda of the workload the coarse factor at that lambda and a solve
+of (X^T X + lambda I) w = X^T y to ||r|| <= 1e-8 ||X^T y||.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun (N > 1) every rank runs an
+independent replica of the workload on its own GPU ("replicas only": one
+solve does not shard), value = the slowest rank's seconds per step.
+--impl reference times the FP64 CPU oracle on the host cores instead, each
+step a bounded sample of the same workload extrapolated to the full step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s to rel. residual 1e-8: batched/learned vs plain two-level PCG, same GB300"
+WORKLOAD = "zipf_200000x100000"
+TOL = 1e-8
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline inputs
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(kernel, workload):
+    """dram read+write bytes per launch recorded by an ncu capture in profiles/."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    try:
+        for line in open(path):
+            if line.startswith("traffic_bytes_per_launch:"):
+                v = line.split(":", 1)[1].strip()
+                return None if v in ("", "null") else float(v)
+    except OSError:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local):
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from gen import synth
+    from paper_1806_05826_gb300 import rr
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    X, y, _, p = synth.workload(args.workload)
+    N, F, nnz, k, lams = X.n_rows, X.n_cols, X.nnz, p["k"], p["lambdas"]
+    stream = torch.cuda.current_stream(dev)
+    row_ptr = torch.as_tensor(X.row_ptr, device=dev)
+    col_idx = torch.as_tensor(X.col_idx, device=dev)
+    y_dev = torch.as_tensor(y, device=dev)
+    W = [torch.empty(F, dtype=torch.float64, device=dev) for _ in lams]
+
+    def step(host=None):
+        if host is None:
+            h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], k, seed=p["seed"], stream=stream)
+            yd = y_dev
+        else:
+            h = rr.rr_setup(host["rp"], host["ci"], N, F, lams[0], k, seed=p["seed"], stream=stream)
+            yd = host["y"].to(dev, non_blocking=True)
+        infos = []
+        for j, lam in enumerate(lams):
+            if j:
+                rr.rr_set_lambda(h, lam)
+            infos.append(rr.rr_solve(h, yd, W[j], tol=TOL))
+            if host is not None:
+                host["w"][j].copy_(W[j], non_blocking=True)
+        if host is not None:
+            torch.cuda.current_stream(dev).synchronize()
+        rr.rr_free(h)
+        return infos
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(3, args.warmup)):
+        infos = step()
+    for inf in infos:
+        assert inf["status"] == "RR_OK" and inf["true_rel_res"] <= TOL, inf
+
+    # ---- timed region: device-resident inputs
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    l0 = rr.rr_launch_count()
+    all_infos = []
+    with ClockSampler(local) as clk:
+        ev[0].record(stream)
+        for s in range(args.steps):
+            all_infos.append(step())
+            ev[s + 1].record(stream)
+        torch.cuda.synchronize(dev)
+    launches = rr.rr_launch_count() - l0
+    barrier()
+    step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = total_ms / 1000.0 / args.steps
+
+    # ---- roofline: the two mat-vec kernels timed alone on the library's stream
+    h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], k, seed=p["seed"], stream=stream)
+    v = torch.randn(F, dtype=torch.float64, device=dev)
+    u = torch.empty(N, dtype=torch.float64, device=dev)
+    z = torch.empty(F, dtype=torch.float64, device=dev)
+    reps = 20
+    kern = {}
+    for name, fn in (("csr_spmv", lambda: rr.rr_matvec(h, v, u)),
+                     ("csc_spmv", lambda: rr.rr_rhs(h, u, z))):
+        for _ in range(3):
+            fn()
+        es = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+        for i in range(reps):
+            es[2 * i].record(stream)
+            fn()
+            es[2 * i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        kern[name] = statistics.mean(es[2 * i].elapsed_time(es[2 * i + 1]) for i in range(reps))
+    rr.rr_free(h)
+    algo = {  # algorithmic bytes per launch: index streams, pointers, each vector once
+        "csr_spmv": 4 * nnz + 8 * (N + 1) + 8 * F + 8 * N,
+        "csc_spmv": 4 * nnz + 8 * (F + 1) + 8 * N + 8 * F,
+    }
+    dom = max(kern, key=kern.get)
+    peak, peak_kind = peaks()
+    achieved = algo[dom] / (kern[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "peak_kind": f"{peak_kind} (burst copy)", "unit": "GB/s",
+                "frac": round(achieved / peak, 4),
+                "traffic": profiled_traffic(dom, args.workload),
+                "algorithmic_bytes": algo[dom], "launch_ms": round(kern[dom], 4),
+                "other": {n: {"launch_ms": round(t, 4),
+                              "achieved_gbs": round(algo[n] / (t * 1e-3) / 1e9, 1)}
+                          for n, t in kern.items() if n != dom}}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = {"rp": torch.as_tensor(X.row_ptr).pin_memory().numpy(),
+                "ci": torch.as_tensor(X.col_idx).pin_memory().numpy(),
+                "y": torch.as_tensor(y).pin_memory(),
+                "w": [torch.empty(F, dtype=torch.float64).pin_memory() for _ in lams]}
+        step(host)
+        barrier()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            step(host)
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        e_ms = t0.elapsed_time(t1) / args.steps
+        e2e = {"value": round(e_ms / 1000.0, 5), "unit": "s",
+               "h2d_bytes_per_step": 8 * (N + 1) + 4 * nnz + 8 * N,
+               "d2h_bytes_per_step": 8 * F * len(lams)}
+
+    last = all_infos[-1]
+    out = {
+        "metric": METRIC, "value": round(value, 5), "unit": "s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(total_ms / args.steps, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Zipf s=1.1 binary CSR, y = X w* + N(0, 0.1^2))",
+        "config": {"workload": args.workload, "n_rows": N, "n_cols": F, "nnz": nnz, "k": k,
+                   "lambdas": list(lams), "tol": TOL,
+                   "method": "two-level PCG: k-means++ clusters, SA prolongation, Cholesky "
+                             "coarse solve, symmetric damped-Jacobi V(1,1)",
+                   "l2": "inputs larger than L2 (CSR+CSC indices 8*nnz bytes)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "breakdown": {"setup_ms": round(last[0]["setup_ms"], 2),
+                      "solve_ms": [round(i["solve_ms"], 2) for i in last],
+                      "iters": [i["iters"] for i in last],
+                      "restarts": [i["restarts"] for i in last],
+                      "true_rel_res": [i["true_rel_res"] for i in last],
+                      "kmeans_iters": last[0]["kmeans_iters"], "k_eff": last[0]["k_eff"],
+                      "step_ms": [round(t, 3) for t in step_ms]},
+        "e2e": e2e, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        iters = [i["iters"] for i in last]
+        out["cpu_baseline"] = cpu_baseline(X, y, p, iters, last[0]["kmeans_iters"],
+                                           last[0]["k_eff"])
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out
+
+
+# ---------------------------------------------------------------- the oracle on host cores
+
+SAMPLE_NOTE = ("component sample of the FP64 oracle at full size, extrapolated to one step: CSC "
+               "build (full), k-means++ seeding (first 8 centres, x k/8), one Lloyd assignment "
+               "step (full, x the Lloyd steps taken), coarse counts (full) and 8 columns of the "
+               "Gram (x k_eff/8), one Cholesky (x lambdas), two two-level PCG iterations (x the "
+               "iterations taken)")
+
+
+def _oracle_sample(npz_path, k, lam, iters, kmeans_iters, k_eff, seed):
+    """Runs in a child process with one BLAS thread; returns the extrapolated seconds."""
+    import numpy as np
+    from oracle import kmeans as km
+    from oracle import krylov, twolevel
+    from oracle import sparse as osp
+
+    d = np.load(npz_path)
+    rp, ci, y = d["row_ptr"], d["col_idx"], d["y"]
+    N, F = len(rp) - 1, int(d["n_cols"])
+    T = {}
+    t = time.perf_counter()
+    cp, ri = osp.csc_pattern(N, F, rp, ci)
+    T["csc"] = time.perf_counter() - t
+    t = time.perf_counter()
+    seeds = km.kmeanspp_binary(N, F, rp, ci, cp, ri, 8, seed)
+    T["seed_per_centre"] = (time.perf_counter() - t) / 8
+    t = time.perf_counter()
+    labels, _ = km.lloyd_binary(N, F, rp, ci, cp, ri, seeds, 1)
+    T["lloyd_step"] = time.perf_counter() - t
+    # a clustering with k_eff clusters for the coarse-level timings (cost depends on sizes only)
+    lab = (np.arange(F) % k_eff).astype(np.int32)
+    t = time.perf_counter()
+    C = twolevel.coarse_counts(N, F, rp, ci, lab, k_eff)
+    Ct = C.T.tocsr()
+    T["counts"] = time.perf_counter() - t
+    t = time.perf_counter()
+    cols = C[:, :8].toarray()
+    _ = Ct @ cols
+    T["gram_per_col"] = (time.perf_counter() - t) / 8
+    rng = np.random.default_rng(0)
+    B = rng.standard_normal((k_eff, k_eff))
+    Ac = B @ B.T / k_eff + np.eye(k_eff)
+    t = time.perf_counter()
+    L = twolevel.cholesky(Ac)
+    T["cholesky"] = time.perf_counter() - t
+    M = osp.from_csr(N, F, rp, ci)
+    n_S = np.bincount(lab, minlength=k_eff).astype(np.int64)
+    s = twolevel.prolong_scale(n_S)
+    dd = osp.col_sq_norms(M) + lam
+    two = twolevel.TwoLevel(M, lam, lab, n_S, s, None, Ac, L, dd, 1.0 / 200.0,
+                            seeds, 1)
+    b = osp.rhs(M, y)
+    t = time.perf_counter()
+    krylov.pcg(two.A, two.apply, b, tol=1e-30, max_iter=2, max_restarts=0)
+    T["pcg_iter"] = (time.perf_counter() - t) / 2.0   # includes the final true-residual check
+    total = (T["csc"] + k * T["seed_per_centre"] + kmeans_iters * T["lloyd_step"] + T["counts"]
+             + k_eff * T["gram_per_col"] + len(iters) * T["cholesky"] + sum(iters) * T["pcg_iter"])
+    return total, T
+
+
+def cpu_baseline(X, y, p, iters, kmeans_iters, k_eff, quiet=False):
+    """Times the oracle sample in a child process pinned to one thread."""
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "x.npz")
+        np.savez(path, row_ptr=X.row_ptr, col_idx=X.col_idx, y=y, n_cols=X.n_cols)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
+                   MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+        code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+                "tot, T = bench._oracle_sample(%r, %d, %r, %r, %d, %d, %d); "
+                "print(json.dumps({'total': tot, 'parts': T}))" %
+                (ROOT, path, p["k"], float(p["lambdas"][0]), list(iters), kmeans_iters, k_eff,
+                 p["seed"]))
+        t0 = time.perf_counter()
+        res = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                             cwd=ROOT)
+        wall = time.perf_counter() - t0
+    if res.returncode != 0:
+        return {"value": None, "unit": "s", "cores": 1, "kind": "oracle",
+                "error": res.stderr.strip().splitlines()[-1:] if res.stderr else "failed"}
+    r = json.loads(res.stdout.strip().splitlines()[-1])
+    return {"value": round(r["total"], 3), "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": SAMPLE_NOTE, "sample_wall_s": round(wall, 1),
+            "parts_s": {k2: round(v, 4) for k2, v in r["parts"].items()}}
+
+
+def run_reference(args, rank, world):
+    """The oracle arm: each timed step re-measures the bounded sample."""
+    if rank != 0:
+        return None
+    from gen import synth
+    X, y, _, p = synth.workload(args.workload)
+    # iteration counts of the oracle's own two-level PCG are those of the
+    # method; the GPU run records them, and so does a previous oracle run.
+    iters = [int(v) for v in os.environ.get("RR_REF_ITERS", "60,40,12").split(",")]
+    km_iters = int(os.environ.get("RR_REF_KMEANS_ITERS", "50"))
+    vals, last = [], None
+    for _ in range(args.steps):
+        last = cpu_baseline(X, y, p, iters, km_iters, p["k"])
+        vals.append(last["value"])
+    v = statistics.mean(vals)
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(v * 1000, 1), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "k": p["k"], "lambdas": list(p["lambdas"]),
+                       "tol": TOL, "iters_assumed": iters, "kmeans_iters_assumed": km_iters},
+            "cpu_baseline": dict(last, value=round(v, 3)),
+            "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

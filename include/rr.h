@@ -1,0 +1,180 @@
+/*
+ * rr.h — C ABI of the GB300 two-level preconditioned CG solver for the
+ * regularised normal equations
+ *
+ *     (X^T X + lambda I) w = X^T y                       (paper Eq. (1))
+ *
+ * from Tavernier, Simm, Meerbergen & Moreau, "Two-level preconditioning for
+ * Ridge Regression" (arXiv 1806.05826). The paper calls lambda "beta".
+ *
+ * Conventions for every entry point:
+ *  - Return a status code; never abort and never trap on the device. On any
+ *    status other than RR_OK, rr_last_error() holds a one-line message
+ *    (thread-local, valid until the next call on the same thread).
+ *  - Vectors passed as `const double*` / `double*` are DEVICE pointers in FP64
+ *    unless the comment says "host". They are caller-owned; the library reads
+ *    and writes them only on the handle's stream (rr_options.stream), and the
+ *    call returns before that work is complete unless it says otherwise.
+ *  - Feature vectors (w, v, labels) are in the caller's feature order 0..F-1;
+ *    sample vectors (y) in row order 0..N-1.
+ *  - A handle is not thread-safe; different handles may be used from
+ *    different threads. The handle owns all of its device memory.
+ */
+#ifndef RR_H_
+#define RR_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rr_handle rr_handle;
+
+typedef enum {
+  RR_OK = 0,
+  RR_INVALID_ARG = 1,    /* bad sizes, CSR not monotone / out of range, lambda <= 0, k < 1 */
+  RR_CUDA_ERROR = 2,     /* a CUDA runtime call failed */
+  RR_OOM = 3,            /* device allocation failed */
+  RR_NOT_SPD = 4,        /* coarse Cholesky met a pivot <= 0 */
+  RR_NOT_CONVERGED = 5,  /* iteration cap reached; w and info still written */
+  RR_NONFINITE = 6,      /* NaN/Inf met in a norm or dot product */
+  RR_TIMEOUT = 7,        /* a bounded device wait gave up */
+  RR_UNSUPPORTED = 8     /* input outside the documented limits */
+} rr_status;
+
+/* rr_matrix.layout */
+enum { RR_CSR_BINARY = 0,       /* pattern only: every stored entry is 1 */
+       RR_DENSE_F32_ROWMAJOR = 1 };
+
+/* rr_options.solver — the preconditioner inside CG */
+enum { RR_SOLVER_TWOLEVEL = 0,  /* symmetric two-level cycle (Section 3.1) in PCG */
+       RR_SOLVER_CG = 1,        /* no preconditioner (Table 2, "CG") */
+       RR_SOLVER_DCG = 2 };     /* Jacobi preconditioner (Table 2, "DCG") */
+
+/* rr_options.precision */
+enum { RR_PREC_FP64 = 0 };
+
+/* The feature matrix X (N x F).
+ *  CSR_BINARY: row_ptr int64[N+1] (row_ptr[0] = 0, non-decreasing,
+ *    row_ptr[N] = nnz) and col_idx int32[nnz], strictly increasing within each
+ *    row, each in [0, F). values must be NULL.
+ *  DENSE_F32_ROWMAJOR: values float[N*F], row-major; row_ptr/col_idx NULL.
+ *  on_device = 1: the pointers are device pointers; 0: host pointers (copied
+ *  inside rr_setup). rr_setup copies X into the handle; the caller may free
+ *  its copy when rr_setup returns. */
+typedef struct {
+  int64_t n_rows, n_cols, nnz;
+  const int64_t *row_ptr;
+  const int32_t *col_idx;
+  const float *values;
+  int32_t layout;
+  int32_t on_device;
+} rr_matrix;
+
+typedef struct {
+  int32_t kmeans_max_iter;      /* Lloyd assignment steps at most (default 50) */
+  int32_t max_iter;             /* Krylov iterations at most, all restarts together (default 20000) */
+  uint64_t seed;                /* SplitMix64 seed of the k-means++ draws (default 0) */
+  const int32_t *init_centers;  /* host int32[k] distinct feature ids, or NULL for k-means++ */
+  int32_t solver;               /* RR_SOLVER_* (default RR_SOLVER_TWOLEVEL) */
+  int32_t precision;            /* RR_PREC_* (default RR_PREC_FP64) */
+  int32_t check_every;          /* iterations between convergence read-backs (default 8) */
+  int32_t max_restarts;         /* true-residual refinement restarts at most (default 5) */
+  void *stream;                 /* cudaStream_t for all work; NULL = legacy default stream */
+} rr_options;
+
+typedef struct {
+  int32_t iters;          /* Krylov iterations, all restarts together */
+  int32_t restarts;       /* refinement restarts taken */
+  int32_t k_eff;          /* non-empty clusters */
+  int32_t kmeans_iters;   /* Lloyd assignment steps taken in rr_setup */
+  double rel_res;         /* recurrence ||r|| / ||X^T y|| at exit */
+  double true_rel_res;    /* ||X^T y - A w|| / ||X^T y|| at exit */
+  double omega;           /* Jacobi damping used */
+  double setup_ms;        /* wall time of rr_setup (host clock, synchronised) */
+  double solve_ms;        /* wall time of this solve (host clock, synchronised) */
+  int64_t launches;       /* kernels this call launched */
+} rr_info;
+
+/* Fills *o with the defaults listed above. */
+void rr_default_options(rr_options *o);
+
+/* Builds the two-level preconditioner for X at regularisation lambda
+ * (Section 3): k-means++ clustering of the F feature columns into k clusters
+ * (Section 3.4, Euclidean distance), the prolongation P(i,S) = 1/sqrt(n_S)
+ * (Eq. (prolong)), the Galerkin coarse operator P^T A P = X_c^T X_c +
+ * lambda I (Section 3.2), its Cholesky factor (Section 4), and the damped
+ * Jacobi smoother. Empty clusters are dropped (info k_eff). Synchronises the
+ * stream before returning. o may be NULL (defaults). On success *out owns
+ * the handle; release it with rr_free.
+ * Errors: RR_INVALID_ARG (see rr_matrix; lambda <= 0 or not finite; k < 1 or
+ * k > F; repeated or out-of-range init_centers), RR_UNSUPPORTED (nnz >= 2^31,
+ * k > 16384, a row holding more than 2048 features of one cluster),
+ * RR_NOT_SPD, RR_OOM, RR_CUDA_ERROR. */
+rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_options *o,
+                   rr_handle **out);
+
+/* Re-targets the handle to another lambda, keeping the clustering: rebuilds
+ * the coarse operator, its factor and the smoother (Section 4: the Cholesky
+ * factor must be recomputed when beta changes). Synchronises the stream. */
+rr_status rr_set_lambda(rr_handle *h, double lambda);
+
+/* Solves Eq. (1) for one right-hand side by CG preconditioned as
+ * rr_options.solver says, from w_0 = 0 (Algorithm 3's initialisation), until
+ * the recurrence residual satisfies ||r|| <= tol ||X^T y||; then checks the
+ * true residual and restarts on the correction while it is above tol
+ * (at most max_restarts times).
+ * y: device double[N]. w: device double[F], overwritten with the solution.
+ * info may be NULL. Synchronises the stream before returning.
+ * Errors: RR_INVALID_ARG (tol not in (0, 1)), RR_NOT_CONVERGED (cap reached;
+ * w holds the last iterate), RR_NONFINITE, RR_CUDA_ERROR. */
+rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info *info);
+
+/* out = (X^T X + lambda I) v (Eq. (1)'s operator, applied matrix-free as
+ * u = X v then X^T u + lambda v). v, out: device double[F]; may not alias. */
+rr_status rr_apply(rr_handle *h, const double *v, double *out);
+
+/* z = M^{-1} r for the handle's preconditioner (the two-level cycle of
+ * Section 3.1 for RR_SOLVER_TWOLEVEL). r, z: device double[F]; may not alias. */
+rr_status rr_precondition(rr_handle *h, const double *r, double *z);
+
+/* b = X^T y (Eq. (1)'s right-hand side; also the transposed mat-vec alone).
+ * y: device double[N]; b: device double[F]. */
+rr_status rr_rhs(rr_handle *h, const double *y, double *b);
+
+/* u = X v (the first half of the operator, Section 1's mat-vec).
+ * v: device double[F]; u: device double[N]. */
+rr_status rr_matvec(rr_handle *h, const double *v, double *u);
+
+/* Copies the final cluster of every feature (compacted to 0..k_eff-1, empty
+ * clusters dropped in order) to host int32[F]. Synchronises. */
+rr_status rr_get_labels(const rr_handle *h, int32_t *labels_host);
+
+/* Copies the k initial centres (feature ids) used by Lloyd to host int32[k]. */
+rr_status rr_get_centers(const rr_handle *h, int32_t *centers_host);
+
+/* Copies the coarse operator A_c (k_eff x k_eff, row-major, FP64, lower
+ * triangle mirrored) and the exact coarse Gram G = C^T C (k_eff x k_eff,
+ * int64) to host buffers; either may be NULL. Synchronises. */
+rr_status rr_get_coarse(const rr_handle *h, double *Ac_host, int64_t *G_host);
+
+/* Number of non-empty clusters, Jacobi damping and sizes of the handle. */
+rr_status rr_query(const rr_handle *h, int64_t *n_rows, int64_t *n_cols, int32_t *k_eff,
+                   double *omega, double *lambda);
+
+/* Number of kernels the library has launched from the calling thread since it
+ * was loaded (counts every launch of every call, setup included). */
+int64_t rr_launch_count(void);
+
+/* Releases the handle and all of its device memory (synchronises its stream). */
+void rr_free(rr_handle *h);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *rr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RR_H_ */

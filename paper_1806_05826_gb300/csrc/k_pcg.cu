@@ -1,0 +1,269 @@
+// Preconditioner pieces and CG recurrences (FP64).
+//  restriction  r_c = P^T r1, r_c[S] = s_S * sum_{i in S} r1[i]   (Eq. (prolong))
+//  coarse solve e_c = A_c^{-1} r_c with the explicit inverse of the Cholesky factor
+//  prolongation z2 = z1 + P e_c
+//  smoother     z = omega D^{-1} r
+//  CG           Hestenes-Stiefel recurrences from x_0 = 0, r_0 = b (Algorithm 3's
+//               initialisation), stopping on ||r|| <= tol ||b|| (Section 4's residual).
+// Every scalar is a fixed-order sum of per-block partials; each consuming block
+// recomputes it, so no extra finishing kernel is needed and runs are bitwise
+// repeatable. The scalar state lives on the device (PcgScalars); once
+// `converged` is set every later kernel of the loop returns at once.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rr {
+
+namespace {
+
+__global__ void k_restrict(int32_t k, const int64_t *__restrict__ cl_ptr,
+                           const int32_t *__restrict__ members, const double *__restrict__ s,
+                           const double *__restrict__ r1, double *__restrict__ rc,
+                           const int32_t *__restrict__ stop) {
+  if (stop && *stop) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t S = warp; S < k; S += nwarps) {
+    double acc = 0.0;
+    for (int64_t p = cl_ptr[S] + lane; p < cl_ptr[S + 1]; p += 32) acc += r1[members[p]];
+    acc = warp_sum(acc);
+    if (lane == 0) rc[S] = s[S] * acc;
+  }
+}
+
+__global__ void k_coarse_matvec(int32_t k, const double *__restrict__ Ainv,
+                                const double *__restrict__ rc, double *__restrict__ ec,
+                                const int32_t *__restrict__ stop) {
+  if (stop && *stop) return;
+  extern __shared__ double rcs[];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) rcs[i] = rc[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t S = warp; S < k; S += nwarps) {
+    const double *row = Ainv + S * k;
+    double acc = 0.0;
+    for (int t = lane; t < k; t += 32) acc += row[t] * rcs[t];
+    acc = warp_sum(acc);
+    if (lane == 0) ec[S] = acc;
+  }
+}
+
+__global__ void k_prolong_add(int64_t F, const int32_t *__restrict__ labels,
+                              const double *__restrict__ s, const double *__restrict__ ec,
+                              const double *__restrict__ z1, double *__restrict__ z2,
+                              const int32_t *__restrict__ stop) {
+  if (stop && *stop) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t l = labels[i];
+    z2[i] = z1[i] + s[l] * ec[l];
+  }
+}
+
+__global__ void k_jacobi(int64_t F, double omega, const double *__restrict__ r,
+                         const double *__restrict__ d, double *__restrict__ z,
+                         double *__restrict__ rz_part, const int32_t *__restrict__ stop) {
+  if (stop && *stop) return;
+  __shared__ double sm[kWarps + 1];
+  double dot = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double zi = d ? omega * r[i] / d[i] : r[i];
+    z[i] = zi;
+    dot += r[i] * zi;
+  }
+  if (rz_part) {
+    const double tot = block_sum(dot, sm);
+    if (threadIdx.x == 0) rz_part[blockIdx.x] = tot;
+  }
+}
+
+__global__ void k_pcg_direction(int64_t F, const double *__restrict__ rz_part, int n_rz,
+                                const double *__restrict__ z, double *__restrict__ p,
+                                const PcgScalars *__restrict__ S) {
+  if (S->converged) return;
+  __shared__ double sm[kWarps + 1];
+  const double rho = sum_partials(rz_part, n_rz, sm);
+  const double beta = S->first ? 0.0 : rho / S->rho_old;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = S->first ? z[i] : z[i] + beta * p[i];
+}
+
+__global__ void k_pcg_update(int64_t F, const double *__restrict__ rz_part, int n_rz,
+                             const double *__restrict__ pq_part, int n_pq,
+                             const double *__restrict__ p, const double *__restrict__ q,
+                             double *__restrict__ w, double *__restrict__ r, double omega,
+                             const double *__restrict__ d, double *__restrict__ z1,
+                             double *__restrict__ rr_part, const PcgScalars *__restrict__ S) {
+  if (S->converged) return;
+  __shared__ double sm[kWarps + 1];
+  const double rho = sum_partials(rz_part, n_rz, sm);
+  const double pq = sum_partials(pq_part, n_pq, sm);
+  const double alpha = rho / pq;
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    w[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    acc += ri * ri;
+    if (z1) z1[i] = omega * ri / d[i];
+  }
+  const double tot = block_sum(acc, sm);
+  if (threadIdx.x == 0) rr_part[blockIdx.x] = tot;
+}
+
+__global__ void k_pcg_finish(const double *__restrict__ rz_part, int n_rz,
+                             const double *__restrict__ rr_part, int n_rr, PcgScalars *S,
+                             double *__restrict__ history, int32_t hist_cap) {
+  if (S->converged) return;
+  __shared__ double sm[kWarps + 1];
+  const double rho = sum_partials(rz_part, n_rz, sm);
+  const double rr = sum_partials(rr_part, n_rr, sm);
+  if (threadIdx.x == 0) {
+    S->rho_old = rho;
+    S->rr = rr;
+    S->first = 0;
+    const int32_t it = S->iter + 1;
+    S->iter = it;
+    const double rn = sqrt(rr);
+    if (history && it <= hist_cap) history[it - 1] = rn / S->bnorm;
+    if (!isfinite(rr) || !isfinite(rho)) {
+      S->nonfinite = 1;
+      S->converged = 1;
+    } else if (rn <= S->target) {
+      S->converged = 1;
+    }
+  }
+}
+
+__global__ void k_dot_parts(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
+                            double *__restrict__ part) {
+  __shared__ double sm[kWarps + 1];
+  double acc = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc += a[i] * b[i];
+  const double tot = block_sum(acc, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void k_pcg_start(const double *__restrict__ bb_part, int n_bb,
+                            const double *__restrict__ rr_part, int n_rr, double tol,
+                            int32_t set_bnorm, PcgScalars *S) {
+  __shared__ double sm[kWarps + 1];
+  const double bb = sum_partials(bb_part, n_bb, sm);
+  const double rr = sum_partials(rr_part, n_rr, sm);
+  if (threadIdx.x == 0) {
+    if (set_bnorm) {
+      S->bnorm = sqrt(bb);
+      S->target = tol * S->bnorm;
+      S->iter = 0;
+      S->nonfinite = isfinite(bb) ? 0 : 1;
+    }
+    S->rr = rr;
+    S->rho_old = 0.0;
+    S->first = 1;
+    S->converged = (S->nonfinite || sqrt(rr) <= S->target) ? 1 : 0;
+  }
+}
+
+__global__ void k_sum_parts(const double *__restrict__ part, int n, double *out) {
+  __shared__ double sm[kWarps + 1];
+  const double v = sum_partials(part, n, sm);
+  if (threadIdx.x == 0) *out = v;
+}
+
+__global__ void k_axpby(int64_t n, double a, const double *__restrict__ x, double b,
+                        double *__restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (x ? a * x[i] : 0.0) + (b != 0.0 ? b * y[i] : 0.0);
+}
+
+}  // namespace
+
+rr_status restrict_clusters(int32_t k, const int64_t *cl_ptr, const int32_t *members,
+                            const double *s, const double *r1, double *rc, const int32_t *stop,
+                            cudaStream_t st) {
+  RR_LAUNCH(k_restrict, grid_for(k, kWarps), kThreads, 0, st, k, cl_ptr, members, s, r1, rc, stop);
+  return RR_OK;
+}
+
+rr_status coarse_matvec(int32_t k, const double *Ainv, const double *rc, double *ec,
+                        const int32_t *stop, cudaStream_t st) {
+  const size_t smem = sizeof(double) * (size_t)k;
+  static int attr_for = -1;
+  if (smem > 48 * 1024 && attr_for < k) {
+    RR_CUDA(cudaFuncSetAttribute(k_coarse_matvec, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    attr_for = k;
+  }
+  RR_LAUNCH(k_coarse_matvec, grid_for(k, kWarps), kThreads, smem, st, k, Ainv, rc, ec, stop);
+  return RR_OK;
+}
+
+rr_status prolong_add(int64_t F, const int32_t *labels, const double *s, const double *ec,
+                      const double *z1, double *z2, const int32_t *stop, cudaStream_t st) {
+  RR_LAUNCH(k_prolong_add, kVecGrid, kThreads, 0, st, F, labels, s, ec, z1, z2, stop);
+  return RR_OK;
+}
+
+rr_status jacobi(int64_t F, double omega, const double *r, const double *d, double *z,
+                 double *rz_part, const int32_t *stop, cudaStream_t st) {
+  RR_LAUNCH(k_jacobi, kVecGrid, kThreads, 0, st, F, omega, r, d, z, rz_part, stop);
+  return RR_OK;
+}
+
+rr_status pcg_direction(int64_t F, const double *rz_part, int n_rz, const double *z, double *p,
+                        PcgScalars *S, cudaStream_t st) {
+  RR_LAUNCH(k_pcg_direction, kVecGrid, kThreads, 0, st, F, rz_part, n_rz, z, p, S);
+  return RR_OK;
+}
+
+rr_status pcg_update(int64_t F, const double *rz_part, int n_rz, const double *pq_part, int n_pq,
+                     const double *p, const double *q, double *w, double *r, double omega,
+                     const double *d, double *z1, double *rr_part, PcgScalars *S,
+                     cudaStream_t st) {
+  RR_LAUNCH(k_pcg_update, kVecGrid, kThreads, 0, st, F, rz_part, n_rz, pq_part, n_pq, p, q, w, r,
+            omega, d, z1, rr_part, S);
+  return RR_OK;
+}
+
+rr_status pcg_finish(const double *rz_part, int n_rz, const double *rr_part, int n_rr,
+                     PcgScalars *S, double *history, int32_t hist_cap, cudaStream_t st) {
+  RR_LAUNCH(k_pcg_finish, 1, kThreads, 0, st, rz_part, n_rz, rr_part, n_rr, S, history, hist_cap);
+  return RR_OK;
+}
+
+rr_status dot_parts(int64_t n, const double *a, const double *b, double *part, cudaStream_t st) {
+  RR_LAUNCH(k_dot_parts, kVecGrid, kThreads, 0, st, n, a, b, part);
+  return RR_OK;
+}
+
+rr_status pcg_start(const double *bb_part, int n_bb, const double *rr_part, int n_rr, double tol,
+                    int32_t set_bnorm, PcgScalars *S, cudaStream_t st) {
+  RR_LAUNCH(k_pcg_start, 1, kThreads, 0, st, bb_part, n_bb, rr_part, n_rr, tol, set_bnorm, S);
+  return RR_OK;
+}
+
+rr_status sum_parts(const double *part, int n, double *out, cudaStream_t st) {
+  RR_LAUNCH(k_sum_parts, 1, kThreads, 0, st, part, n, out);
+  return RR_OK;
+}
+
+rr_status copy_f64(double *dst, const double *src, int64_t n, cudaStream_t st) {
+  RR_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  return RR_OK;
+}
+
+rr_status axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t st) {
+  RR_LAUNCH(k_axpby, kVecGrid, kThreads, 0, st, n, a, x, b, y);
+  return RR_OK;
+}
+
+}  // namespace rr

@@ -1,0 +1,690 @@
+// C ABI of the two-level preconditioned CG solver (include/rr.h): handle
+// life cycle, setup orchestration and the solve loop. All arithmetic runs in
+// the kernels of this directory; this file only sequences them on the
+// handle's stream and moves status words to the host.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+static thread_local char g_err[1024] = "";
+thread_local int64_t rr_launch_counter = 0;
+
+void rr_set_error(const char *fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+}
+
+namespace {
+
+using rr::kThreads;
+
+struct DevArena {
+  std::vector<void *> ptrs;
+  template <class T>
+  rr_status alloc(T **p, size_t n) {
+    void *q = nullptr;
+    const size_t bytes = sizeof(T) * (n ? n : 1);
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      rr_set_error("cudaMalloc of %zu bytes failed", bytes);
+      return RR_OOM;
+    }
+    ptrs.push_back(q);
+    *p = static_cast<T *>(q);
+    return RR_OK;
+  }
+  void release(void *p) {
+    for (auto &q : ptrs)
+      if (q == p) {
+        cudaFree(q);
+        q = nullptr;
+      }
+  }
+  void free_all() {
+    for (void *q : ptrs)
+      if (q) cudaFree(q);
+    ptrs.clear();
+  }
+};
+
+// d_i = ||x_i||^2 + lambda (column nnz for binary X); ratio_i = (sum_j |A_ij|) / d_i
+// with sum_j |(X^T X)_ij| = sum_{r in col i} rownnz_r (exact integers). The
+// maximum ratio is kept through the order-preserving bit pattern of positive doubles.
+__global__ void k_jacobi_setup(int64_t F, double lambda, const int64_t *__restrict__ row_ptr,
+                               const int64_t *__restrict__ col_ptr,
+                               const int32_t *__restrict__ row_idx, double *__restrict__ d,
+                               unsigned long long *__restrict__ max_bits) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < F; i += nwarps) {
+    int64_t s = 0;
+    for (int64_t p = col_ptr[i] + lane; p < col_ptr[i + 1]; p += 32) {
+      const int64_t r = row_idx[p];
+      s += row_ptr[r + 1] - row_ptr[r];
+    }
+    s = rr::warp_sum_i64(s);
+    if (lane == 0) {
+      const double di = (double)(col_ptr[i + 1] - col_ptr[i]) + lambda;
+      d[i] = di;
+      const double ratio = ((double)s + lambda) / di;
+      unsigned long long bits = (unsigned long long)__double_as_longlong(ratio);
+      atomicMax(max_bits, bits);
+    }
+  }
+}
+
+__global__ void k_omega(const unsigned long long *max_bits, double *omega_out) {
+  if (threadIdx.x == 0) *omega_out = 1.0 / __longlong_as_double((long long)*max_bits);
+}
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+}  // namespace
+
+struct rr_handle {
+  cudaStream_t st = nullptr;
+  rr_options opt{};
+  int64_t N = 0, F = 0, nnz = 0;
+  int32_t k_req = 0, k_eff = 0, kmeans_iters = 0;
+  double lambda = 0.0, omega = 1.0, setup_ms = 0.0;
+  // X and its transposed copy
+  int64_t *row_ptr = nullptr;
+  int32_t *col_idx = nullptr;
+  int64_t *col_ptr = nullptr;
+  int32_t *row_idx = nullptr;
+  // clustering
+  int32_t *labels = nullptr;
+  int32_t *centers = nullptr;
+  int64_t *n_S = nullptr;
+  int64_t *cl_ptr = nullptr;
+  int32_t *members = nullptr;
+  double *s = nullptr;
+  // coarse level
+  double *G = nullptr, *Ac = nullptr, *Lw = nullptr, *Linv = nullptr, *Ainv = nullptr;
+  // smoother
+  double *d = nullptr;
+  double *omega_dev = nullptr;
+  unsigned long long *max_bits = nullptr;
+  rr::CscPlan plan;
+  // solve workspace
+  double *b = nullptr, *r = nullptr, *z1 = nullptr, *z2 = nullptr, *z = nullptr, *p = nullptr,
+         *q = nullptr, *r1 = nullptr, *u = nullptr, *rc = nullptr, *ec = nullptr, *rt = nullptr;
+  double *part_rz = nullptr, *part_pq = nullptr, *part_rr = nullptr, *part_bb = nullptr;
+  double *scal = nullptr;
+  rr::PcgScalars *S = nullptr;
+  rr::PcgScalars *S_host = nullptr;
+  double *scal_host = nullptr;
+  double *history = nullptr;
+  int32_t hist_cap = 0;
+  int32_t *err = nullptr;
+  int32_t *err_host = nullptr;
+  int n_parts = 0;
+  DevArena mem;
+};
+
+namespace {
+
+rr_status check_dev_error(rr_handle *h, const char *where) {
+  RR_CUDA(cudaMemcpyAsync(h->err_host, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st));
+  RR_CUDA(cudaStreamSynchronize(h->st));
+  const int32_t e = *h->err_host;
+  if (e == rr::DEV_OK) return RR_OK;
+  RR_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int32_t), h->st));
+  switch (e) {
+    case rr::DEV_BAD_INDEX:
+      rr_set_error("%s: CSR indices not strictly increasing or out of range", where);
+      return RR_INVALID_ARG;
+    case rr::DEV_NOT_SPD:
+      rr_set_error("%s: coarse Cholesky met a pivot <= 0", where);
+      return RR_NOT_SPD;
+    case rr::DEV_COUNT_OVERFLOW:
+      rr_set_error("%s: a row holds more than 2048 features of one cluster", where);
+      return RR_UNSUPPORTED;
+    default:
+      rr_set_error("%s: device error %d", where, e);
+      return RR_CUDA_ERROR;
+  }
+}
+
+// Coarse operator, its factor and inverse, Jacobi diagonal and damping at lambda.
+rr_status build_lambda(rr_handle *h, double lambda) {
+  cudaStream_t st = h->st;
+  const int32_t k = h->k_eff;
+  RR_TRY(rr::coarse_operator(k, h->G, h->s, lambda, h->Ac, st));
+  RR_CUDA(cudaMemcpyAsync(h->Lw, h->Ac, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, st));
+  RR_TRY(rr::cholesky(k, h->Lw, h->err, st));
+  RR_TRY(rr::chol_inverse(k, h->Lw, h->Linv, h->Ainv, st));
+  RR_CUDA(cudaMemsetAsync(h->max_bits, 0, sizeof(unsigned long long), st));
+  RR_LAUNCH(k_jacobi_setup, rr::grid_for(h->F, rr::kWarps), kThreads, 0, st, h->F, lambda,
+            h->row_ptr, h->col_ptr, h->row_idx, h->d, h->max_bits);
+  RR_LAUNCH(k_omega, 1, 32, 0, st, h->max_bits, h->omega_dev);
+  double om = 0.0;
+  RR_CUDA(cudaMemcpyAsync(&om, h->omega_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  RR_TRY(check_dev_error(h, "coarse factor"));
+  h->omega = om;
+  h->lambda = lambda;
+  return RR_OK;
+}
+
+rr_status validate_host_csr(const rr_matrix *X) {
+  if (X->row_ptr[0] != 0 || X->row_ptr[X->n_rows] != X->nnz) {
+    rr_set_error("row_ptr[0] must be 0 and row_ptr[N] must equal nnz");
+    return RR_INVALID_ARG;
+  }
+  for (int64_t r = 0; r < X->n_rows; ++r) {
+    const int64_t b = X->row_ptr[r], e = X->row_ptr[r + 1];
+    if (e < b) {
+      rr_set_error("row_ptr decreases at row %lld", (long long)r);
+      return RR_INVALID_ARG;
+    }
+    for (int64_t p = b; p < e; ++p) {
+      const int32_t c = X->col_idx[p];
+      if (c < 0 || c >= X->n_cols || (p > b && X->col_idx[p - 1] >= c)) {
+        rr_set_error("col_idx out of range or not strictly increasing in row %lld", (long long)r);
+        return RR_INVALID_ARG;
+      }
+    }
+  }
+  return RR_OK;
+}
+
+rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k) {
+  cudaStream_t st = h->st;
+  DevArena &m = h->mem;
+  const int64_t N = X->n_rows, F = X->n_cols, nnz = X->nnz;
+  h->N = N;
+  h->F = F;
+  h->nnz = nnz;
+  h->k_req = k;
+  RR_TRY(m.alloc(&h->err, 1));
+  RR_CUDA(cudaMallocHost(&h->err_host, sizeof(int32_t)));
+  RR_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int32_t), st));
+
+  // ---- X on the device
+  RR_TRY(m.alloc(&h->row_ptr, N + 1));
+  RR_TRY(m.alloc(&h->col_idx, nnz));
+  if (X->on_device) {
+    int64_t ends[2];
+    RR_CUDA(cudaMemcpyAsync(&ends[0], X->row_ptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaMemcpyAsync(&ends[1], X->row_ptr + N, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaStreamSynchronize(st));
+    if (ends[0] != 0 || ends[1] != nnz) {
+      rr_set_error("row_ptr[0] must be 0 and row_ptr[N] must equal nnz");
+      return RR_INVALID_ARG;
+    }
+    RR_CUDA(cudaMemcpyAsync(h->row_ptr, X->row_ptr, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToDevice, st));
+    RR_CUDA(cudaMemcpyAsync(h->col_idx, X->col_idx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, st));
+    RR_TRY(rr::validate_csr(N, F, h->row_ptr, h->col_idx, h->err, st));
+    RR_TRY(check_dev_error(h, "rr_setup"));
+  } else {
+    RR_TRY(validate_host_csr(X));
+    RR_CUDA(cudaMemcpyAsync(h->row_ptr, X->row_ptr, sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, st));
+    RR_CUDA(cudaMemcpyAsync(h->col_idx, X->col_idx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+  }
+
+  // ---- transposed copy (CSC), rows ascending within columns
+  const int64_t big = std::max(N, F) + 1;
+  int64_t *scratch64 = nullptr;
+  const int64_t scan_len = rr::scan_scratch_len(big) + 8;
+  RR_TRY(m.alloc(&scratch64, 2 * big + scan_len + 256));
+  int32_t *tmp32 = nullptr;
+  RR_TRY(m.alloc(&tmp32, std::max(nnz, F)));
+  RR_TRY(m.alloc(&h->col_ptr, F + 1));
+  RR_TRY(m.alloc(&h->row_idx, nnz));
+  RR_TRY(rr::transpose_pattern(N, F, nnz, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx,
+                               scratch64, scratch64 + big, tmp32, scratch64 + 2 * big, st));
+
+  // ---- k-means++ seeding and Lloyd steps (Section 3.4)
+  rr::KmeansBuffers kb{};
+  const int64_t ntiles = (F + 1023) / 1024;
+  RR_TRY(m.alloc(&kb.d2, F));
+  RR_TRY(m.alloc(&kb.ov, F));
+  RR_TRY(m.alloc(&kb.part_i, ntiles + 1));
+  RR_TRY(m.alloc(&h->centers, k));
+  kb.centers = h->centers;
+  RR_TRY(m.alloc(&h->labels, F));
+  kb.labels = h->labels;
+  RR_TRY(m.alloc(&kb.next, F));
+  RR_TRY(m.alloc(&h->n_S, 2 * (int64_t)k));
+  kb.n_S = h->n_S;
+  RR_TRY(m.alloc(&kb.Q, k));
+  RR_TRY(m.alloc(&kb.D, F * (int64_t)k));
+  RR_TRY(m.alloc(&kb.changes, 1));
+  RR_TRY(m.alloc(&kb.work_ctr, 1));
+  RR_TRY(m.alloc(&kb.order, F));
+  if (h->opt.init_centers) {
+    std::vector<char> seen(F, 0);
+    for (int32_t s = 0; s < k; ++s) {
+      const int32_t c = h->opt.init_centers[s];
+      if (c < 0 || c >= F || seen[c]) {
+        rr_set_error("init_centers[%d] = %d is out of range or repeated", s, c);
+        return RR_INVALID_ARG;
+      }
+      seen[c] = 1;
+    }
+    RR_CUDA(cudaMemcpyAsync(h->centers, h->opt.init_centers, sizeof(int32_t) * k,
+                            cudaMemcpyHostToDevice, st));
+  } else {
+    RR_TRY(rr::kmeanspp_seed(N, F, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx, k,
+                             h->opt.seed, kb, st));
+  }
+  RR_TRY(rr::kmeans_init_labels(F, k, kb, st));
+  RR_TRY(rr::kmeans_work_order(F, h->row_ptr, h->col_ptr, h->row_idx, kb, scratch64, st));
+  int64_t *changes_host = nullptr;
+  RR_CUDA(cudaMallocHost(&changes_host, sizeof(int64_t)));
+  int32_t it = 0;
+  rr_status ks = RR_OK;
+  while (it < h->opt.kmeans_max_iter) {
+    ++it;
+    ks = rr::kmeans_lloyd_step(N, F, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx, k, kb,
+                               changes_host, st);
+    if (ks != RR_OK || *changes_host == 0) break;
+  }
+  cudaFreeHost(changes_host);
+  RR_TRY(ks);
+  h->kmeans_iters = it;
+  m.release(kb.D);
+  m.release(kb.d2);
+  m.release(kb.ov);
+  m.release(kb.Q);
+
+  // ---- compaction, member lists, prolongation scale
+  int32_t *remap = nullptr;
+  RR_TRY(m.alloc(&remap, k + 1));
+  int32_t k_eff = 0;
+  RR_TRY(rr::compact_clusters(F, k, h->labels, h->n_S, remap, &k_eff, st));
+  h->k_eff = k_eff;
+  RR_TRY(m.alloc(&h->cl_ptr, k_eff + 1));
+  RR_TRY(m.alloc(&h->members, F));
+  int64_t *iota = nullptr;
+  RR_TRY(m.alloc(&iota, F + 1));
+  RR_TRY(rr::iota_i64(iota, F + 1, st));
+  RR_TRY(rr::transpose_pattern(F, k_eff, F, iota, h->labels, h->cl_ptr, h->members, scratch64,
+                               scratch64 + big, tmp32, scratch64 + 2 * big, st));
+  RR_TRY(m.alloc(&h->s, k_eff));
+  RR_TRY(rr::prolong_scale(k_eff, h->n_S, h->s, st));
+
+  // ---- exact coarse Gram G = C^T C
+  const int64_t n_pad = round_up(std::max<int64_t>(N, 1), 64);
+  const int32_t k_pad = (int32_t)round_up(k_eff, 128);
+  void *Ct = nullptr;
+  if (cudaMalloc(&Ct, 2 * (size_t)k_pad * n_pad) != cudaSuccess) {
+    cudaGetLastError();
+    rr_set_error("cudaMalloc of the coarse count matrix failed");
+    return RR_OOM;
+  }
+  rr_status gs = rr::coarse_counts(N, n_pad, k_pad, h->row_ptr, h->col_idx, h->labels, Ct, h->err, st);
+  if (gs == RR_OK) gs = check_dev_error(h, "coarse counts");
+  RR_TRY(m.alloc(&h->G, (int64_t)k_eff * k_eff));
+  if (gs == RR_OK) gs = rr::gram_exact_cuda_cores(k_eff, k_pad, n_pad, Ct, h->G, st);
+  if (gs == RR_OK && cudaStreamSynchronize(st) != cudaSuccess) {
+    rr_set_error("coarse Gram failed");
+    gs = RR_CUDA_ERROR;
+  }
+  cudaFree(Ct);
+  RR_TRY(gs);
+
+  // ---- per-lambda coarse factor and smoother
+  const int64_t kk = (int64_t)k_eff * k_eff;
+  RR_TRY(m.alloc(&h->Ac, kk));
+  RR_TRY(m.alloc(&h->Lw, kk));
+  RR_TRY(m.alloc(&h->Linv, kk));
+  RR_TRY(m.alloc(&h->Ainv, kk));
+  RR_TRY(m.alloc(&h->d, F));
+  RR_TRY(m.alloc(&h->omega_dev, 1));
+  RR_TRY(m.alloc(&h->max_bits, 1));
+  RR_TRY(build_lambda(h, lambda));
+
+  // ---- transposed mat-vec plan and solve workspace
+  RR_TRY(rr::csc_plan_build(F, h->col_ptr, h->plan, st));
+  h->n_parts = std::max(rr::csc_dot_parts(h->plan), rr::kVecGrid);
+  for (double **v : {&h->b, &h->r, &h->z1, &h->z2, &h->z, &h->p, &h->q, &h->r1, &h->rt})
+    RR_TRY(m.alloc(v, F));
+  RR_TRY(m.alloc(&h->u, std::max<int64_t>(N, 1)));
+  RR_TRY(m.alloc(&h->rc, k_eff));
+  RR_TRY(m.alloc(&h->ec, k_eff));
+  for (double **v : {&h->part_rz, &h->part_pq, &h->part_rr, &h->part_bb})
+    RR_TRY(m.alloc(v, h->n_parts));
+  RR_TRY(m.alloc(&h->scal, 4));
+  RR_TRY(m.alloc(&h->S, 1));
+  RR_CUDA(cudaMallocHost(&h->S_host, sizeof(rr::PcgScalars)));
+  RR_CUDA(cudaMallocHost(&h->scal_host, 4 * sizeof(double)));
+  h->hist_cap = h->opt.max_iter;
+  RR_TRY(m.alloc(&h->history, h->hist_cap));
+  m.release(tmp32);
+  m.release(scratch64);
+  m.release(iota);
+  m.release(remap);
+  m.release(kb.part_i);
+  m.release(kb.next);
+  m.release(kb.changes);
+  m.release(kb.work_ctr);
+  m.release(kb.order);
+  RR_CUDA(cudaStreamSynchronize(st));
+  return RR_OK;
+}
+
+// ---- the preconditioner: z = M^{-1} r, with <r, z> partials in part_rz.
+rr_status apply_precond(rr_handle *h, const double *r, double *z, const int32_t *stop, int *n_rz,
+                        bool z1_ready) {
+  cudaStream_t st = h->st;
+  const int64_t N = h->N, F = h->F;
+  switch (h->opt.solver) {
+    case RR_SOLVER_CG:
+      *n_rz = rr::kVecGrid;
+      return rr::jacobi(F, 1.0, r, nullptr, z, h->part_rz, stop, st);
+    case RR_SOLVER_DCG:
+      *n_rz = rr::kVecGrid;
+      return rr::jacobi(F, 1.0, r, h->d, z, h->part_rz, stop, st);
+    default: {
+      // symmetric two-level cycle: z1 = w D^-1 r; r1 = r - A z1; e_c = A_c^-1 P^T r1;
+      // z2 = z1 + P e_c; r2 = r - A z2; z = z2 + w D^-1 r2
+      if (!z1_ready) RR_TRY(rr::jacobi(F, h->omega, r, h->d, h->z1, nullptr, stop, st));
+      RR_TRY(rr::csr_spmv(N, h->row_ptr, h->col_idx, h->z1, h->u, stop, st));
+      rr::CscEpilogue pre{rr::CSC_PRE, h->lambda, h->omega, h->z1, r, h->d, h->r1, nullptr, stop};
+      RR_TRY(rr::csc_spmv(F, h->row_idx, h->u, h->plan, pre, st));
+      RR_TRY(rr::restrict_clusters(h->k_eff, h->cl_ptr, h->members, h->s, h->r1, h->rc, stop, st));
+      RR_TRY(rr::coarse_matvec(h->k_eff, h->Ainv, h->rc, h->ec, stop, st));
+      RR_TRY(rr::prolong_add(F, h->labels, h->s, h->ec, h->z1, h->z2, stop, st));
+      RR_TRY(rr::csr_spmv(N, h->row_ptr, h->col_idx, h->z2, h->u, stop, st));
+      rr::CscEpilogue post{rr::CSC_POST, h->lambda, h->omega, h->z2, r, h->d, z, h->part_rz, stop};
+      RR_TRY(rr::csc_spmv(F, h->row_idx, h->u, h->plan, post, st));
+      *n_rz = rr::csc_dot_parts(h->plan);
+      return RR_OK;
+    }
+  }
+}
+
+rr_status true_residual(rr_handle *h, const double *w, double *rr_out) {
+  cudaStream_t st = h->st;
+  RR_TRY(rr::csr_spmv(h->N, h->row_ptr, h->col_idx, w, h->u, nullptr, st));
+  rr::CscEpilogue ep{rr::CSC_RESID, h->lambda, h->omega, w, h->b, h->d, h->rt, h->part_bb, nullptr};
+  RR_TRY(rr::csc_spmv(h->F, h->row_idx, h->u, h->plan, ep, st));
+  RR_TRY(rr::sum_parts(h->part_bb, rr::csc_dot_parts(h->plan), h->scal, st));
+  RR_CUDA(cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  *rr_out = h->scal_host[0];
+  return RR_OK;
+}
+
+rr_status solve_impl(rr_handle *h, const double *y, double *w, double tol, rr_info *info) {
+  cudaStream_t st = h->st;
+  const int64_t F = h->F;
+  const bool twolevel = h->opt.solver == RR_SOLVER_TWOLEVEL;
+  const int32_t *stop = &h->S->converged;
+  // b = X^T y; w = 0; r = b
+  rr::CscEpilogue rhs{rr::CSC_RHS, 0.0, 0.0, nullptr, nullptr, nullptr, h->b, nullptr, nullptr};
+  RR_TRY(rr::csc_spmv(F, h->row_idx, y, h->plan, rhs, st));
+  RR_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * F, st));
+  RR_TRY(rr::copy_f64(h->r, h->b, F, st));
+  RR_TRY(rr::dot_parts(F, h->b, h->b, h->part_bb, st));
+  RR_CUDA(cudaMemsetAsync(h->S, 0, sizeof(rr::PcgScalars), st));
+  RR_TRY(rr::pcg_start(h->part_bb, rr::kVecGrid, h->part_bb, rr::kVecGrid, tol, 1, h->S, st));
+  if (twolevel) RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st));
+
+  const int32_t max_iter = h->opt.max_iter;
+  const int32_t every = std::max(1, h->opt.check_every);
+  int32_t launched = 0, restarts = 0;
+  double true_rr = 0.0;
+  rr_status result = RR_OK;
+  for (;;) {
+    const int32_t batch = std::min(every, max_iter - launched);
+    for (int32_t c = 0; c < batch; ++c) {
+      int n_rz = 0;
+      RR_TRY(apply_precond(h, h->r, h->z, stop, &n_rz, twolevel));
+      RR_TRY(rr::pcg_direction(F, h->part_rz, n_rz, h->z, h->p, h->S, st));
+      RR_TRY(rr::csr_spmv(h->N, h->row_ptr, h->col_idx, h->p, h->u, stop, st));
+      rr::CscEpilogue ap{rr::CSC_PCG, h->lambda, h->omega, h->p, nullptr, nullptr, h->q, h->part_pq, stop};
+      RR_TRY(rr::csc_spmv(F, h->row_idx, h->u, h->plan, ap, st));
+      RR_TRY(rr::pcg_update(F, h->part_rz, n_rz, h->part_pq, rr::csc_dot_parts(h->plan), h->p,
+                            h->q, w, h->r, h->omega, h->d, twolevel ? h->z1 : nullptr, h->part_rr,
+                            h->S, st));
+      RR_TRY(rr::pcg_finish(h->part_rz, n_rz, h->part_rr, rr::kVecGrid, h->S, h->history,
+                            h->hist_cap, st));
+    }
+    launched += batch;
+    RR_CUDA(cudaMemcpyAsync(h->S_host, h->S, sizeof(rr::PcgScalars), cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaStreamSynchronize(st));
+    const rr::PcgScalars Sh = *h->S_host;
+    if (Sh.nonfinite) {
+      rr_set_error("rr_solve: non-finite residual or dot product");
+      result = RR_NONFINITE;
+      break;
+    }
+    if (Sh.converged || launched >= max_iter) {
+      RR_TRY(true_residual(h, w, &true_rr));
+      if (!isfinite(true_rr)) {
+        rr_set_error("rr_solve: non-finite true residual");
+        result = RR_NONFINITE;
+        break;
+      }
+      if (sqrt(true_rr) <= Sh.target) break;
+      if (launched >= max_iter || restarts >= h->opt.max_restarts) {
+        rr_set_error("rr_solve: not converged after %d iterations (%d restarts)", Sh.iter, restarts);
+        result = RR_NOT_CONVERGED;
+        break;
+      }
+      // refinement: continue from w with the true residual and a fresh direction
+      ++restarts;
+      RR_TRY(rr::copy_f64(h->r, h->rt, F, st));
+      RR_TRY(rr::dot_parts(F, h->r, h->r, h->part_rr, st));
+      RR_TRY(rr::pcg_start(h->part_bb, 1, h->part_rr, rr::kVecGrid, tol, 0, h->S, st));
+      if (twolevel) RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st));
+    }
+  }
+  RR_CUDA(cudaMemcpyAsync(h->S_host, h->S, sizeof(rr::PcgScalars), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  if (info) {
+    const rr::PcgScalars Sh = *h->S_host;
+    info->iters = Sh.iter;
+    info->restarts = restarts;
+    info->rel_res = Sh.bnorm > 0 ? sqrt(Sh.rr) / Sh.bnorm : 0.0;
+    info->true_rel_res = Sh.bnorm > 0 ? sqrt(true_rr) / Sh.bnorm : 0.0;
+  }
+  return result;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rr_default_options(rr_options *o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->kmeans_max_iter = 50;
+  o->max_iter = 20000;
+  o->seed = 0;
+  o->init_centers = nullptr;
+  o->solver = RR_SOLVER_TWOLEVEL;
+  o->precision = RR_PREC_FP64;
+  o->check_every = 8;
+  o->max_restarts = 5;
+  o->stream = nullptr;
+}
+
+const char *rr_last_error(void) { return g_err; }
+
+int64_t rr_launch_count(void) { return rr_launch_counter; }
+
+rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_options *o,
+                   rr_handle **out) {
+  g_err[0] = 0;
+  if (!X || !out) {
+    rr_set_error("rr_setup: X and out must not be NULL");
+    return RR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (X->layout != RR_CSR_BINARY) {
+    rr_set_error("rr_setup: only the binary CSR layout is supported by this build");
+    return RR_UNSUPPORTED;
+  }
+  if (X->n_rows < 1 || X->n_cols < 1 || X->nnz < 0 || !X->row_ptr || (X->nnz > 0 && !X->col_idx) ||
+      X->values) {
+    rr_set_error("rr_setup: bad matrix description");
+    return RR_INVALID_ARG;
+  }
+  if (!(lambda > 0.0) || !isfinite(lambda)) {
+    rr_set_error("rr_setup: lambda must be positive and finite");
+    return RR_INVALID_ARG;
+  }
+  if (k < 1 || k > X->n_cols) {
+    rr_set_error("rr_setup: k must be in [1, F]");
+    return RR_INVALID_ARG;
+  }
+  if (X->nnz >= (1LL << 31) || X->n_rows >= (1LL << 31) || X->n_cols >= (1LL << 31)) {
+    rr_set_error("rr_setup: nnz, N and F must be below 2^31");
+    return RR_UNSUPPORTED;
+  }
+  if (k > 16384) {
+    rr_set_error("rr_setup: k above 16384 is not supported");
+    return RR_UNSUPPORTED;
+  }
+  rr_options opt;
+  if (o) opt = *o; else rr_default_options(&opt);
+  if (opt.kmeans_max_iter < 1 || opt.max_iter < 1) {
+    rr_set_error("rr_setup: kmeans_max_iter and max_iter must be positive");
+    return RR_INVALID_ARG;
+  }
+  rr_handle *h = new rr_handle();
+  h->opt = opt;
+  h->opt.init_centers = nullptr;
+  h->st = static_cast<cudaStream_t>(opt.stream);
+  const auto t0 = std::chrono::steady_clock::now();
+  h->opt.init_centers = opt.init_centers;
+  rr_status s = setup_impl(h, X, lambda, k);
+  h->opt.init_centers = nullptr;
+  if (s != RR_OK) {
+    rr_free(h);
+    return s;
+  }
+  h->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = h;
+  return RR_OK;
+}
+
+rr_status rr_set_lambda(rr_handle *h, double lambda) {
+  if (!h) return RR_INVALID_ARG;
+  if (!(lambda > 0.0) || !isfinite(lambda)) {
+    rr_set_error("rr_set_lambda: lambda must be positive and finite");
+    return RR_INVALID_ARG;
+  }
+  RR_TRY(build_lambda(h, lambda));
+  RR_CUDA(cudaStreamSynchronize(h->st));
+  return RR_OK;
+}
+
+rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info *info) {
+  if (!h || !y || !w) {
+    rr_set_error("rr_solve: handle, y and w must not be NULL");
+    return RR_INVALID_ARG;
+  }
+  if (!(tol > 0.0 && tol < 1.0)) {
+    rr_set_error("rr_solve: tol must be in (0, 1)");
+    return RR_INVALID_ARG;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t l0 = rr_launch_counter;
+  rr_status s = solve_impl(h, y, w, tol, info);
+  if (info) {
+    info->k_eff = h->k_eff;
+    info->kmeans_iters = h->kmeans_iters;
+    info->omega = h->omega;
+    info->setup_ms = h->setup_ms;
+    info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    info->launches = rr_launch_counter - l0;
+  }
+  return s;
+}
+
+rr_status rr_apply(rr_handle *h, const double *v, double *out) {
+  if (!h || !v || !out || v == out) return RR_INVALID_ARG;
+  RR_TRY(rr::csr_spmv(h->N, h->row_ptr, h->col_idx, v, h->u, nullptr, h->st));
+  rr::CscEpilogue ep{rr::CSC_APPLY, h->lambda, h->omega, v, nullptr, nullptr, out, nullptr, nullptr};
+  RR_TRY(rr::csc_spmv(h->F, h->row_idx, h->u, h->plan, ep, h->st));
+  return RR_OK;
+}
+
+rr_status rr_precondition(rr_handle *h, const double *r, double *z) {
+  if (!h || !r || !z || r == z) return RR_INVALID_ARG;
+  int n = 0;
+  RR_TRY(apply_precond(h, r, z, nullptr, &n, false));
+  return RR_OK;
+}
+
+rr_status rr_rhs(rr_handle *h, const double *y, double *b) {
+  if (!h || !y || !b) return RR_INVALID_ARG;
+  rr::CscEpilogue ep{rr::CSC_RHS, 0.0, 0.0, nullptr, nullptr, nullptr, b, nullptr, nullptr};
+  RR_TRY(rr::csc_spmv(h->F, h->row_idx, y, h->plan, ep, h->st));
+  return RR_OK;
+}
+
+rr_status rr_matvec(rr_handle *h, const double *v, double *u) {
+  if (!h || !v || !u) return RR_INVALID_ARG;
+  RR_TRY(rr::csr_spmv(h->N, h->row_ptr, h->col_idx, v, u, nullptr, h->st));
+  return RR_OK;
+}
+
+rr_status rr_get_labels(const rr_handle *h, int32_t *labels_host) {
+  if (!h || !labels_host) return RR_INVALID_ARG;
+  RR_CUDA(cudaMemcpyAsync(labels_host, h->labels, sizeof(int32_t) * h->F, cudaMemcpyDeviceToHost, h->st));
+  RR_CUDA(cudaStreamSynchronize(h->st));
+  return RR_OK;
+}
+
+rr_status rr_get_centers(const rr_handle *h, int32_t *centers_host) {
+  if (!h || !centers_host) return RR_INVALID_ARG;
+  RR_CUDA(cudaMemcpyAsync(centers_host, h->centers, sizeof(int32_t) * h->k_req, cudaMemcpyDeviceToHost, h->st));
+  RR_CUDA(cudaStreamSynchronize(h->st));
+  return RR_OK;
+}
+
+rr_status rr_get_coarse(const rr_handle *h, double *Ac_host, int64_t *G_host) {
+  if (!h) return RR_INVALID_ARG;
+  const size_t kk = (size_t)h->k_eff * h->k_eff;
+  if (Ac_host)
+    RR_CUDA(cudaMemcpyAsync(Ac_host, h->Ac, sizeof(double) * kk, cudaMemcpyDeviceToHost, h->st));
+  std::vector<double> g;
+  if (G_host) {
+    g.resize(kk);
+    RR_CUDA(cudaMemcpyAsync(g.data(), h->G, sizeof(double) * kk, cudaMemcpyDeviceToHost, h->st));
+  }
+  RR_CUDA(cudaStreamSynchronize(h->st));
+  if (G_host)
+    for (size_t i = 0; i < kk; ++i) G_host[i] = (int64_t)g[i];
+  return RR_OK;
+}
+
+rr_status rr_query(const rr_handle *h, int64_t *n_rows, int64_t *n_cols, int32_t *k_eff,
+                   double *omega, double *lambda) {
+  if (!h) return RR_INVALID_ARG;
+  if (n_rows) *n_rows = h->N;
+  if (n_cols) *n_cols = h->F;
+  if (k_eff) *k_eff = h->k_eff;
+  if (omega) *omega = h->omega;
+  if (lambda) *lambda = h->lambda;
+  return RR_OK;
+}
+
+void rr_free(rr_handle *h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  rr::csc_plan_free(h->plan);
+  h->mem.free_all();
+  if (h->err_host) cudaFreeHost(h->err_host);
+  if (h->S_host) cudaFreeHost(h->S_host);
+  if (h->scal_host) cudaFreeHost(h->scal_host);
+  delete h;
+}
+
+}  // extern "C"

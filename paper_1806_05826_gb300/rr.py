@@ -1,0 +1,240 @@
+"""Python binding of include/rr.h (ctypes): argument marshalling only.
+
+Every computation happens in librr.so's CUDA kernels. Device vectors are
+torch CUDA tensors (FP64) passed by pointer on the current torch stream.
+Importing this module without a built librr.so raises at once: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librr.so")
+
+RR_OK, RR_INVALID_ARG, RR_CUDA_ERROR, RR_OOM, RR_NOT_SPD = 0, 1, 2, 3, 4
+RR_NOT_CONVERGED, RR_NONFINITE, RR_TIMEOUT, RR_UNSUPPORTED = 5, 6, 7, 8
+RR_CSR_BINARY, RR_DENSE_F32_ROWMAJOR = 0, 1
+RR_SOLVER_TWOLEVEL, RR_SOLVER_CG, RR_SOLVER_DCG = 0, 1, 2
+RR_PREC_FP64 = 0
+
+_STATUS = {0: "RR_OK", 1: "RR_INVALID_ARG", 2: "RR_CUDA_ERROR", 3: "RR_OOM", 4: "RR_NOT_SPD",
+           5: "RR_NOT_CONVERGED", 6: "RR_NONFINITE", 7: "RR_TIMEOUT", 8: "RR_UNSUPPORTED"}
+
+
+class rr_matrix(ctypes.Structure):
+    _fields_ = [("n_rows", ctypes.c_int64), ("n_cols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p),
+                ("values", ctypes.c_void_p), ("layout", ctypes.c_int32),
+                ("on_device", ctypes.c_int32)]
+
+
+class rr_options(ctypes.Structure):
+    _fields_ = [("kmeans_max_iter", ctypes.c_int32), ("max_iter", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("init_centers", ctypes.c_void_p),
+                ("solver", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class rr_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("k_eff", ctypes.c_int32), ("kmeans_iters", ctypes.c_int32),
+                ("rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double),
+                ("omega", ctypes.c_double), ("setup_ms", ctypes.c_double),
+                ("solve_ms", ctypes.c_double), ("launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class RRError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+# the C ABI: name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_SIGS = {
+    "rr_default_options": (None, [ctypes.POINTER(rr_options)]),
+    "rr_setup": (ctypes.c_int, [ctypes.POINTER(rr_matrix), ctypes.c_double, ctypes.c_int32,
+                                ctypes.POINTER(rr_options), ctypes.POINTER(_P)]),
+    "rr_set_lambda": (ctypes.c_int, [_P, ctypes.c_double]),
+    "rr_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.POINTER(rr_info)]),
+    "rr_apply": (ctypes.c_int, [_P, _P, _P]),
+    "rr_precondition": (ctypes.c_int, [_P, _P, _P]),
+    "rr_rhs": (ctypes.c_int, [_P, _P, _P]),
+    "rr_matvec": (ctypes.c_int, [_P, _P, _P]),
+    "rr_get_labels": (ctypes.c_int, [_P, _P]),
+    "rr_get_centers": (ctypes.c_int, [_P, _P]),
+    "rr_get_coarse": (ctypes.c_int, [_P, _P, _P]),
+    "rr_query": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "rr_free": (None, [_P]),
+    "rr_last_error": (ctypes.c_char_p, []),
+    "rr_launch_count": (ctypes.c_int64, []),
+}
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads librr.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_1806_05826_gb300/build.py "
+                               "(or __graft_entry__.build()); there is no CPU fallback")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def rr_launch_count() -> int:
+    return int(load().rr_launch_count())
+
+
+def rr_last_error() -> str:
+    return load().rr_last_error().decode()
+
+
+def _check(status):
+    if status != RR_OK:
+        raise RRError(status, rr_last_error())
+
+
+def _ptr(t):
+    """Device or host pointer of a torch tensor or numpy array."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def rr_default_options(**kw) -> rr_options:
+    o = rr_options()
+    load().rr_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Handle:
+    """Owns an rr_handle; the functions below take it as their first argument."""
+
+    def __init__(self, ptr, F, N, keepalive):
+        self.ptr = ptr
+        self.F, self.N = F, N
+        self._keep = keepalive
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().rr_free(self.ptr)
+            self.ptr = None
+
+
+def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=None,
+             kmeans_max_iter=50, max_iter=20000, solver=RR_SOLVER_TWOLEVEL, check_every=8,
+             max_restarts=5, stream=None) -> Handle:
+    """rr_setup on a binary CSR pattern given as numpy arrays (host) or torch
+    CUDA tensors (device): row_ptr int64[N+1], col_idx int32[nnz]."""
+    lib = load()
+    on_device = 0 if isinstance(row_ptr, np.ndarray) else 1
+    if on_device == 0:
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    X = rr_matrix(n_rows, n_cols, int(row_ptr[-1]) if on_device == 0 else int(col_idx.numel()),
+                  _ptr(row_ptr), _ptr(col_idx), None, RR_CSR_BINARY, on_device)
+    ic = None
+    if init_centers is not None:
+        ic = np.ascontiguousarray(init_centers, dtype=np.int32)
+    o = rr_default_options(kmeans_max_iter=kmeans_max_iter, max_iter=max_iter, seed=seed,
+                           init_centers=_ptr(ic), solver=solver, check_every=check_every,
+                           max_restarts=max_restarts, stream=_stream_ptr(stream))
+    out = _P()
+    _check(lib.rr_setup(ctypes.byref(X), float(lam), int(k), ctypes.byref(o), ctypes.byref(out)))
+    return Handle(out, n_cols, n_rows, (ic,))
+
+
+def rr_set_lambda(h: Handle, lam: float):
+    _check(load().rr_set_lambda(h.ptr, float(lam)))
+
+
+def rr_solve(h: Handle, y, w, tol=1e-8) -> dict:
+    info = rr_info()
+    st = load().rr_solve(h.ptr, _ptr(y), _ptr(w), float(tol), ctypes.byref(info))
+    d = info.as_dict()
+    d["status"] = _STATUS[st]
+    if st not in (RR_OK, RR_NOT_CONVERGED):
+        raise RRError(st, rr_last_error())
+    return d
+
+
+def rr_apply(h: Handle, v, out):
+    _check(load().rr_apply(h.ptr, _ptr(v), _ptr(out)))
+
+
+def rr_precondition(h: Handle, r, z):
+    _check(load().rr_precondition(h.ptr, _ptr(r), _ptr(z)))
+
+
+def rr_rhs(h: Handle, y, b):
+    _check(load().rr_rhs(h.ptr, _ptr(y), _ptr(b)))
+
+
+def rr_matvec(h: Handle, v, u):
+    _check(load().rr_matvec(h.ptr, _ptr(v), _ptr(u)))
+
+
+def rr_get_labels(h: Handle) -> np.ndarray:
+    out = np.empty(h.F, dtype=np.int32)
+    _check(load().rr_get_labels(h.ptr, out.ctypes.data))
+    return out
+
+
+def rr_get_centers(h: Handle, k: int) -> np.ndarray:
+    out = np.empty(k, dtype=np.int32)
+    _check(load().rr_get_centers(h.ptr, out.ctypes.data))
+    return out
+
+
+def rr_query(h: Handle) -> dict:
+    n, f = ctypes.c_int64(), ctypes.c_int64()
+    k, om, lam = ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+    _check(load().rr_query(h.ptr, ctypes.byref(n), ctypes.byref(f), ctypes.byref(k),
+                           ctypes.byref(om), ctypes.byref(lam)))
+    return {"n_rows": n.value, "n_cols": f.value, "k_eff": k.value, "omega": om.value,
+            "lambda": lam.value}
+
+
+def rr_get_coarse(h: Handle):
+    k = rr_query(h)["k_eff"]
+    Ac = np.empty((k, k), dtype=np.float64)
+    G = np.empty((k, k), dtype=np.int64)
+    _check(load().rr_get_coarse(h.ptr, Ac.ctypes.data, G.ctypes.data))
+    return Ac, G
+
+
+def rr_free(h: Handle):
+    h.close()

@@ -1,0 +1,269 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bars: bit-exact for the integer work (k-means++ centres, Lloyd labels, the
+coarse Gram) and for the quantities both sides compute with the same IEEE
+operations (A_c, omega); for floating-point sums in another order, the
+tolerances below (derived in each test from the arithmetic); for the solve,
+||w - w_ref|| / ||w_ref|| <= 1e-6 at relative residual 1e-8.
+"""
+import numpy as np
+import pytest
+
+from gen import synth
+from oracle import kmeans as okm
+from oracle import krylov, twolevel
+from oracle import sparse as osp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_05826_gb300 import build
+    build.build_library()
+    from paper_1806_05826_gb300 import rr as rrmod
+    rrmod.load()
+    return rrmod
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def csr_of(D):
+    D = np.asarray(D)
+    rows, cols = np.nonzero(D)
+    rp = np.zeros(D.shape[0] + 1, np.int64)
+    np.cumsum(np.bincount(rows, minlength=D.shape[0]), out=rp[1:])
+    return rp, cols.astype(np.int32)
+
+
+CASES = {
+    # name: (N, F, density, k, lambda, seed) — small, ragged, several tiles
+    "zipf_2000x1000": (2000, 1000, 0.01, 50, 1e-2, 0),
+    "ragged_3001x1777": (3001, 1777, 0.006, 37, 1e-3, 5),
+    "tall_9000x2500": (9000, 2500, 0.004, 129, 0.1, 7),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request, rr):
+    N, F, dens, k, lam, seed = CASES[request.param]
+    X = synth.zipf_binary(N, F, dens, 1.1, seed)
+    y, _ = synth.ridge_targets(X, seed)
+    ref = twolevel.setup_binary(N, F, X.row_ptr, X.col_idx, lam, k, seed=seed)
+    h = rr.rr_setup(X.row_ptr, X.col_idx, N, F, lam, k, seed=seed)
+    return dict(X=X, y=y, ref=ref, h=h, lam=lam, k=k, seed=seed)
+
+
+def test_kmeanspp_centres_bit_exact(case, rr):
+    got = rr.rr_get_centers(case["h"], case["k"])
+    assert np.array_equal(got, case["ref"].centers)
+
+
+def test_lloyd_labels_bit_exact(case, rr):
+    got = rr.rr_get_labels(case["h"])
+    assert np.array_equal(got, case["ref"].labels)
+    assert rr.rr_query(case["h"])["k_eff"] == case["ref"].k_eff
+
+
+def test_coarse_gram_exact_and_operator(case, rr):
+    Ac, G = rr.rr_get_coarse(case["h"])
+    assert np.array_equal(G, case["ref"].G)
+    # same IEEE operations in the same order on both sides: identical bits
+    assert np.array_equal(Ac, case["ref"].Ac)
+    assert rr.rr_query(case["h"])["omega"] == case["ref"].omega
+
+
+def test_operator_and_rhs(case, rr):
+    X, ref = case["X"], case["ref"]
+    v = np.random.default_rng(1).standard_normal(X.n_cols)
+    out = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
+    rr.rr_apply(case["h"], dev(v), out)
+    want = ref.A(v)
+    # sums of O(nnz) terms of size O(1) in another order: rounding O(1e-16 * sqrt(terms))
+    scale = np.abs(want).max()
+    assert np.max(np.abs(out.cpu().numpy() - want)) <= 1e-13 * scale
+    b = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
+    rr.rr_rhs(case["h"], dev(case["y"]), b)
+    bw = osp.rhs(ref.M, case["y"])
+    assert np.max(np.abs(b.cpu().numpy() - bw)) <= 1e-13 * np.abs(bw).max()
+
+
+def test_preconditioner(case, rr):
+    X, ref = case["X"], case["ref"]
+    r = np.random.default_rng(2).standard_normal(X.n_cols)
+    z = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
+    rr.rr_precondition(case["h"], dev(r), z)
+    want = ref.apply(r)
+    # the coarse solve amplifies rounding by up to cond(A_c) ~ 1/lambda * ||A_c||
+    cond = np.linalg.cond(ref.Ac)
+    tol = max(1e-12, 1e-15 * cond)
+    rel = np.linalg.norm(z.cpu().numpy() - want) / np.linalg.norm(want)
+    assert rel <= tol, (rel, tol)
+
+
+def test_two_level_solve_matches_oracle(case, rr):
+    X, ref = case["X"], case["ref"]
+    b = osp.rhs(ref.M, case["y"])
+    want = krylov.pcg(ref.A, ref.apply, b, tol=1e-8)
+    w = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
+    info = rr.rr_solve(case["h"], dev(case["y"]), w, tol=1e-8)
+    assert info["status"] == "RR_OK"
+    wg = w.cpu().numpy()
+    assert np.linalg.norm(wg - want.w) / np.linalg.norm(want.w) <= 1e-6
+    # the true residual, recomputed by the oracle's operator
+    assert np.linalg.norm(b - ref.A(wg)) / np.linalg.norm(b) <= 1e-8
+    assert abs(info["iters"] - want.iters) <= 2
+    assert info["true_rel_res"] <= 1e-8
+
+
+@pytest.mark.parametrize("solver", ["cg", "dcg"])
+def test_baseline_solvers(case, rr, solver):
+    """CG and DCG (Table 2's baselines). They stall on the small eigenvalues,
+    so at residual 1e-8 two runs that differ only in rounding can still be
+    ~1e-5 apart (error <= cond(A) * residual); the solutions are therefore
+    compared at residual 1e-11, where both sit within 1e-8 of the exact one."""
+    X, ref = case["X"], case["ref"]
+    b = osp.rhs(ref.M, case["y"])
+    tol = 1e-11
+    if solver == "cg":
+        want = krylov.cg(ref.A, b, tol=tol, max_iter=100000)
+        code = rr.RR_SOLVER_CG
+    else:
+        want = krylov.dcg(ref.A, ref.d, b, tol=tol, max_iter=100000)
+        code = rr.RR_SOLVER_DCG
+    h = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, case["lam"], case["k"],
+                    seed=case["seed"], solver=code, max_iter=100000)
+    w = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
+    info = rr.rr_solve(h, dev(case["y"]), w, tol=tol)
+    wg = w.cpu().numpy()
+    assert info["status"] == "RR_OK"
+    assert np.linalg.norm(wg - want.w) / np.linalg.norm(want.w) <= 1e-6
+    assert np.linalg.norm(b - ref.A(wg)) / np.linalg.norm(b) <= tol
+
+
+def test_set_lambda_reuses_clustering(case, rr):
+    X, ref = case["X"], case["ref"]
+    lam2 = case["lam"] * 30.0
+    rr.rr_set_lambda(case["h"], lam2)
+    ref2 = ref.with_lambda(lam2)
+    Ac, _ = rr.rr_get_coarse(case["h"])
+    assert np.array_equal(Ac, ref2.Ac)
+    b = osp.rhs(ref2.M, case["y"])
+    want = krylov.pcg(ref2.A, ref2.apply, b, tol=1e-8)
+    w = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
+    info = rr.rr_solve(case["h"], dev(case["y"]), w, tol=1e-8)
+    assert np.linalg.norm(w.cpu().numpy() - want.w) / np.linalg.norm(want.w) <= 1e-6
+    rr.rr_set_lambda(case["h"], case["lam"])
+    assert info["status"] == "RR_OK"
+
+
+def test_repeatable_bits(case, rr):
+    X = case["X"]
+    w1 = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
+    w2 = torch.empty_like(w1)
+    i1 = rr.rr_solve(case["h"], dev(case["y"]), w1, tol=1e-8)
+    i2 = rr.rr_solve(case["h"], dev(case["y"]), w2, tol=1e-8)
+    assert i1["iters"] == i2["iters"]
+    assert torch.equal(w1, w2)
+
+
+# ---------------------------------------------------------------- edge cases
+
+def _setup_dense01(rr, D, lam, k, **kw):
+    rp, ci = csr_of(D)
+    return rr.rr_setup(rp, ci, D.shape[0], D.shape[1], lam, k, **kw), rp, ci
+
+
+@pytest.mark.parametrize("k", [1, 2, 13])
+def test_edge_empty_rows_cols_duplicates(rr, k):
+    rng = np.random.default_rng(k)
+    D = (rng.random((60, 13)) < 0.3).astype(np.int64)
+    D[5] = 0              # empty row
+    D[:, 4] = 0           # empty column
+    D[:, 7] = D[:, 2]     # duplicated feature
+    D[:, 9] = 1           # all-ones feature
+    lam = 0.05
+    h, rp, ci = _setup_dense01(rr, D, lam, k, seed=3)
+    ref = twolevel.setup_binary(60, 13, rp, ci, lam, k, seed=3)
+    assert np.array_equal(rr.rr_get_labels(h), ref.labels)
+    y = rng.standard_normal(60)
+    w = torch.empty(13, dtype=torch.float64, device="cuda")
+    info = rr.rr_solve(h, dev(y), w, tol=1e-10)
+    w_ref = np.linalg.solve(D.T @ D + lam * np.eye(13), D.T @ y)
+    assert info["status"] == "RR_OK"
+    assert np.linalg.norm(w.cpu().numpy() - w_ref) / np.linalg.norm(w_ref) <= 1e-8
+
+
+def test_edge_k_equals_F_and_given_centres(rr):
+    rng = np.random.default_rng(4)
+    D = (rng.random((40, 9)) < 0.4).astype(np.int64)
+    D[0] = 1
+    rp, ci = csr_of(D)
+    centers = np.array([8, 0, 3, 5, 1, 2, 7, 4, 6], np.int32)
+    h = rr.rr_setup(rp, ci, 40, 9, 0.01, 9, init_centers=centers)
+    cp, ri = osp.csc_pattern(40, 9, rp, ci)
+    lab, _ = okm.lloyd_binary(40, 9, rp, ci, cp, ri, centers, 50)
+    lab, _ = okm.compact(lab)
+    assert np.array_equal(rr.rr_get_labels(h), lab)
+    assert np.array_equal(rr.rr_get_centers(h, 9), centers)
+
+
+def test_edge_zero_rhs(rr):
+    D = np.eye(6, dtype=np.int64)
+    h, _, _ = _setup_dense01(rr, D, 1.0, 2)
+    w = torch.full((6,), 7.0, dtype=torch.float64, device="cuda")
+    info = rr.rr_solve(h, dev(np.zeros(6)), w, tol=1e-8)
+    assert info["iters"] == 0 and torch.count_nonzero(w) == 0
+
+
+def test_invalid_inputs_rejected_on_host(rr):
+    rp = np.array([0, 2, 3], np.int64)
+    ci = np.array([1, 1, 0], np.int32)       # repeated index in row 0
+    with pytest.raises(rr.RRError) as e:
+        rr.rr_setup(rp, ci, 2, 3, 1.0, 1)
+    assert e.value.status == rr.RR_INVALID_ARG
+    ci = np.array([0, 3, 0], np.int32)       # out of range
+    with pytest.raises(rr.RRError):
+        rr.rr_setup(rp, ci, 2, 3, 1.0, 1)
+    with pytest.raises(rr.RRError):
+        rr.rr_setup(np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32), 2, 3, 1.0, 1,
+                    init_centers=[1])
+    ok = rr.rr_setup(np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32), 2, 3, 1.0, 1)
+    w = torch.empty(3, dtype=torch.float64, device="cuda")
+    with pytest.raises(rr.RRError):
+        rr.rr_solve(ok, dev(np.ones(2)), w, tol=0.0)
+
+
+def test_invalid_device_csr_detected_by_kernel(rr):
+    rp = torch.tensor([0, 2, 3], dtype=torch.int64, device="cuda")
+    ci = torch.tensor([2, 1, 0], dtype=torch.int32, device="cuda")   # decreasing in row 0
+    with pytest.raises(rr.RRError) as e:
+        rr.rr_setup(rp, ci, 2, 3, 1.0, 1)
+    assert e.value.status == rr.RR_INVALID_ARG
+
+
+def test_iteration_cap_reports_not_converged(rr):
+    X = synth.zipf_binary(2000, 1000, 0.01, 1.1, 0)
+    y, _ = synth.ridge_targets(X, 0)
+    h = rr.rr_setup(X.row_ptr, X.col_idx, 2000, 1000, 1e-2, 50, max_iter=3, check_every=1,
+                    solver=rr.RR_SOLVER_CG)
+    w = torch.empty(1000, dtype=torch.float64, device="cuda")
+    info = rr.rr_solve(h, dev(y), w, tol=1e-8)
+    assert info["status"] == "RR_NOT_CONVERGED"
+    assert info["iters"] == 3 and np.isfinite(info["rel_res"])
+
+
+def test_nonfinite_rhs_reported(rr):
+    X = synth.zipf_binary(300, 100, 0.05, 1.1, 0)
+    y = np.ones(300)
+    y[3] = np.nan
+    h = rr.rr_setup(X.row_ptr, X.col_idx, 300, 100, 1e-2, 5)
+    w = torch.empty(100, dtype=torch.float64, device="cuda")
+    with pytest.raises(rr.RRError) as e:
+        rr.rr_solve(h, dev(y), w, tol=1e-8)
+    assert e.value.status == rr.RR_NONFINITE
