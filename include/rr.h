@@ -52,6 +52,11 @@ enum { RR_SOLVER_TWOLEVEL = 0,  /* symmetric two-level cycle (Section 3.1) in PC
        RR_SOLVER_CG = 1,        /* no preconditioner (Table 2, "CG") */
        RR_SOLVER_DCG = 2 };     /* Jacobi preconditioner (Table 2, "DCG") */
 
+/* rr_options.gram — how rr_setup forms the exact coarse Gram C^T C */
+enum { RR_GRAM_AUTO = 0,        /* tcgen05 tensor cores (FP16 counts, exact FP32 chunks) when
+                                   the counts allow exact chunks, else CUDA cores */
+       RR_GRAM_CUDA_CORES = 1 };/* int32 products summed in int64 on CUDA cores */
+
 /* rr_options.precision */
 enum { RR_PREC_FP64 = 0 };
 
@@ -79,8 +84,13 @@ typedef struct {
   const int32_t *init_centers;  /* host int32[k] distinct feature ids, or NULL for k-means++ */
   int32_t solver;               /* RR_SOLVER_* (default RR_SOLVER_TWOLEVEL) */
   int32_t precision;            /* RR_PREC_* (default RR_PREC_FP64) */
-  int32_t check_every;          /* iterations between convergence read-backs (default 8) */
+  int32_t check_every;          /* iterations between convergence read-backs when use_graphs = 0
+                                   (default 8) */
   int32_t max_restarts;         /* true-residual refinement restarts at most (default 5) */
+  int32_t use_graphs;           /* 1: the iteration loop runs on the device as one CUDA graph with a
+                                   conditional while node (default); 0: host-driven batches of
+                                   check_every iterations */
+  int32_t gram;                 /* RR_GRAM_* (default RR_GRAM_AUTO) */
   void *stream;                 /* cudaStream_t for all work; NULL = legacy default stream */
 } rr_options;
 
@@ -95,6 +105,7 @@ typedef struct {
   double setup_ms;        /* wall time of rr_setup (host clock, synchronised) */
   double solve_ms;        /* wall time of this solve (host clock, synchronised) */
   int64_t launches;       /* kernels this call launched */
+  int32_t gram_tensor_cores; /* 1 if rr_setup formed the coarse Gram on the tensor cores */
 } rr_info;
 
 /* Fills *o with the defaults listed above. */
@@ -110,7 +121,8 @@ void rr_default_options(rr_options *o);
  * the handle; release it with rr_free.
  * Errors: RR_INVALID_ARG (see rr_matrix; lambda <= 0 or not finite; k < 1 or
  * k > F; repeated or out-of-range init_centers), RR_UNSUPPORTED (nnz >= 2^31,
- * k > 16384, a row holding more than 2048 features of one cluster),
+ * k > 16384, a row holding more than 8191 features of one cluster), RR_TIMEOUT (a bounded
+ * device wait expired),
  * RR_NOT_SPD, RR_OOM, RR_CUDA_ERROR. */
 rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_options *o,
                    rr_handle **out);
@@ -159,7 +171,8 @@ rr_status rr_get_centers(const rr_handle *h, int32_t *centers_host);
  * int64) to host buffers; either may be NULL. Synchronises. */
 rr_status rr_get_coarse(const rr_handle *h, double *Ac_host, int64_t *G_host);
 
-/* Number of non-empty clusters, Jacobi damping and sizes of the handle. */
+/* Number of non-empty clusters, Jacobi damping and sizes of the handle. Any
+ * pointer may be NULL. */
 rr_status rr_query(const rr_handle *h, int64_t *n_rows, int64_t *n_cols, int32_t *k_eff,
                    double *omega, double *lambda);
 

@@ -61,6 +61,7 @@ enum DevError : int32_t {
   DEV_NOT_SPD = 2,        // Cholesky pivot <= 0
   DEV_COUNT_OVERFLOW = 3, // a per-row cluster count above the FP16-exact range
   DEV_NONFINITE = 4,
+  DEV_TIMEOUT = 5,        // a bounded wait on an mbarrier expired
 };
 
 }  // namespace rr

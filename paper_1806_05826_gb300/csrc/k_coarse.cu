@@ -71,31 +71,43 @@ __global__ void k_prolong_scale(int32_t k, const int64_t *__restrict__ n, double
     s[i] = 1.0 / sqrt((double)n[i]);
 }
 
-// Ct[S, r] += 1 for every entry (r, j) with label_j = S. FP16 holds integers
-// exactly up to 2048; a count reaching that is recorded as an error.
+// C32[S, r] += 1 for every entry (r, j) with label_j = S (exact int32 counts);
+// *max_count = the largest count (one atomic per warp).
 __global__ void k_coarse_counts(int64_t N, int64_t n_pad, const int64_t *__restrict__ row_ptr,
                                 const int32_t *__restrict__ col_idx,
-                                const int32_t *__restrict__ labels, __half *__restrict__ Ct,
-                                int32_t *err) {
+                                const int32_t *__restrict__ labels, int32_t *__restrict__ C32,
+                                int32_t *max_count) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int32_t mx = 0;
   for (int64_t r = warp; r < N; r += nwarps) {
     for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) {
       const int64_t S = labels[col_idx[e]];
-      const __half old = atomicAdd(&Ct[S * n_pad + r], __float2half(1.0f));
-      if (__half2float(old) >= 2048.0f) set_dev_error(err, DEV_COUNT_OVERFLOW);
+      const int32_t now = atomicAdd(&C32[S * n_pad + r], 1) + 1;
+      mx = max(mx, now);
     }
   }
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0 && mx > 0) atomicMax(max_count, mx);
 }
 
-// G = Ct Ct^T over the lower tile triangle, exact: int32 products of counts
-// summed over 32-row steps (each step's sum < 2^31), steps summed in int64,
-// result stored as FP64 (exact below 2^53).
+// FP16 copy of the counts for the tensor cores (exact: every count <= 2048).
+__global__ void k_counts_to_half(int64_t n, const int32_t *__restrict__ C32,
+                                 __half *__restrict__ C16) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    C16[i] = __int2half_rn(C32[i]);
+}
+
+// G = C32 C32^T over the lower tile triangle, exact: int32 products of counts
+// summed over 32-row steps, steps summed in int64, stored as FP64 (exact below
+// 2^53). A step's sum is below 2^31 while every count is below 8192; larger
+// counts are reported as unsupported by the caller.
 constexpr int kGT = 64;   // output tile
 constexpr int kGK = 32;   // rows per step
 __global__ void __launch_bounds__(kThreads) k_gram_cc(int32_t k, int64_t n_pad,
-                                                      const __half *__restrict__ Ct,
+                                                      const int32_t *__restrict__ Ct,
                                                       double *__restrict__ G) {
   // blockIdx.x enumerates lower-triangular tile pairs (ti >= tj)
   int64_t t = blockIdx.x;
@@ -116,8 +128,8 @@ __global__ void __launch_bounds__(kThreads) k_gram_cc(int32_t k, int64_t n_pad,
     for (int idx = threadIdx.x; idx < kGK * kGT; idx += kThreads) {
       const int row = idx / kGK, kk = idx % kGK;   // consecutive threads read consecutive rows r
       const int S = S0 + row, T = T0 + row;
-      a[kk][row] = (S < k) ? __half2int_rn(Ct[(int64_t)S * n_pad + r0 + kk]) : 0;
-      bsm[kk][row] = (T < k) ? __half2int_rn(Ct[(int64_t)T * n_pad + r0 + kk]) : 0;
+      a[kk][row] = (S < k) ? Ct[(int64_t)S * n_pad + r0 + kk] : 0;
+      bsm[kk][row] = (T < k) ? Ct[(int64_t)T * n_pad + r0 + kk] : 0;
     }
     __syncthreads();
     int32_t part[4][4];
@@ -352,19 +364,25 @@ rr_status prolong_scale(int32_t k, const int64_t *n_S, double *s, cudaStream_t s
 }
 
 rr_status coarse_counts(int64_t N, int64_t n_pad, int32_t k_pad, const int64_t *row_ptr,
-                        const int32_t *col_idx, const int32_t *labels, void *Ct, int32_t *err,
-                        cudaStream_t st) {
-  RR_CUDA(cudaMemsetAsync(Ct, 0, sizeof(__half) * (size_t)k_pad * n_pad, st));
+                        const int32_t *col_idx, const int32_t *labels, int32_t *C32,
+                        int32_t *max_count, cudaStream_t st) {
+  RR_CUDA(cudaMemsetAsync(C32, 0, sizeof(int32_t) * (size_t)k_pad * n_pad, st));
+  RR_CUDA(cudaMemsetAsync(max_count, 0, sizeof(int32_t), st));
   RR_LAUNCH(k_coarse_counts, grid_for(N, kWarps), kThreads, 0, st, N, n_pad, row_ptr, col_idx,
-            labels, (__half *)Ct, err);
+            labels, C32, max_count);
   return RR_OK;
 }
 
-rr_status gram_exact_cuda_cores(int32_t k, int32_t k_pad, int64_t n_pad, const void *Ct, double *G,
-                                cudaStream_t st) {
+rr_status counts_to_half(int64_t n, const int32_t *C32, void *C16, cudaStream_t st) {
+  RR_LAUNCH(k_counts_to_half, grid_for(n, kThreads), kThreads, 0, st, n, C32, (__half *)C16);
+  return RR_OK;
+}
+
+rr_status gram_exact_cuda_cores(int32_t k, int32_t k_pad, int64_t n_pad, const int32_t *C32,
+                                double *G, cudaStream_t st) {
   (void)k_pad;
   const int64_t nt = (k + kGT - 1) / kGT;
-  RR_LAUNCH(k_gram_cc, tri_tiles(nt), kThreads, 0, st, k, n_pad, (const __half *)Ct, G);
+  RR_LAUNCH(k_gram_cc, tri_tiles(nt), kThreads, 0, st, k, n_pad, C32, G);
   return RR_OK;
 }
 

@@ -1,0 +1,333 @@
+// Coarse Gram G = C^T C on the 5th-generation tensor cores (tcgen05), the one
+// dense contraction of the method (Section 3.2: X_c^T X_c with X_c = X P; the
+// integer counts C = X * onehot(labels) carry it, G = D_s^-1 X_c^T X_c D_s^-1).
+//
+// Operands: Ct (k_pad x n_pad, FP16, rows = clusters, K = samples contiguous)
+// serves as both A and B (K-major). TMA brings 128 x 64 tiles with the 128-byte
+// swizzle into a 4-stage shared-memory ring; one thread issues
+// tcgen05.mma.kind::f16 (M = N = 128, K = 16) into a 128-column FP32
+// accumulator in tensor memory; four warps read it back with tcgen05.ld.
+//
+// Exactness: counts are integers <= 2048 (exact in FP16), products <= 2^22;
+// the K range of one CTA is limited so that every FP32 partial sum stays
+// below 2^24 (exact), and the chunks are added into G in FP64 (exact below
+// 2^53, so the order of the atomic additions does not matter).
+//
+// Every wait on an mbarrier is bounded: on expiry the CTA records
+// DEV_TIMEOUT, waits (bounded) for its own copies still in flight, frees its
+// tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rr {
+
+namespace {
+
+constexpr int kTM = 128, kTN = 128, kTK = 64;   // tile: rows x cols x K per stage
+constexpr int kStages = 4;
+constexpr int kStageBytes = (kTM + kTN) * kTK * 2;   // A and B tiles, FP16
+constexpr int kTmemCols = 128;
+constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kGramThreads = 128;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false when the limit expired or another thread of the CTA
+// gave up (abort flag set).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          const int32_t *abort_flag) {
+  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 255u) == 255u && *(volatile const int32_t *)abort_flag) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int32_t x, int32_t y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// 8-row core groups 1024 bytes apart (SBO), leading offset unused (1).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);          // start address
+  d |= (uint64_t)1u << 16;                          // leading byte offset (unused)
+  d |= (uint64_t)(1024u >> 4) << 32;                // stride byte offset
+  d |= (uint64_t)1u << 46;                          // descriptor version (sm_100 family)
+  d |= (uint64_t)2u << 61;                          // swizzle: 128 bytes
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, FP16 A and B, both
+// K-major, N = 128, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTN >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+      "%30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// One CTA: the lower tile (ti >= tj) blockIdx.x % n_tiles over the K chunk
+// blockIdx.x / n_tiles.
+__global__ void __launch_bounds__(kGramThreads, 1)
+    k_gram_tc(const __grid_constant__ CUtensorMap tmap, int32_t k, int32_t n_tiles_lower,
+              int64_t n_pad, int64_t k_chunk, double *__restrict__ G, int32_t *err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 1024-byte alignment of the tile ring (the 128-byte swizzle repeats every 1024 bytes)
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *ring = smem;
+  uint64_t *full = (uint64_t *)(smem + kStages * kStageBytes);
+  uint64_t *empty = full + kStages;
+  uint64_t *done = empty + kStages;
+  uint32_t *tmem_slot = (uint32_t *)(done + 1);
+  int32_t *abort_flag = (int32_t *)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tile = blockIdx.x % n_tiles_lower;
+  const int64_t chunk = blockIdx.x / n_tiles_lower;
+  int ti = (int)((sqrt(8.0 * (double)tile + 1.0) - 1.0) * 0.5);
+  while ((int64_t)(ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+  while ((int64_t)ti * (ti + 1) / 2 > tile) --ti;
+  const int tj = (int)(tile - (int64_t)ti * (ti + 1) / 2);
+  const int S0 = ti * kTM, T0 = tj * kTN;
+  const int64_t kbeg = chunk * k_chunk;
+  const int64_t kend = min(n_pad, kbeg + k_chunk);
+  const int nk = (int)((kend - kbeg) / kTK);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer: TMA loads of the A (rows S0..) and B (rows T0..) tiles
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kStages;
+      if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) + 1) & 1, abort_flag)) {
+        set_dev_error(err, DEV_TIMEOUT);
+        atomicExch(abort_flag, 1);
+        break;
+      }
+      if (*(volatile int32_t *)abort_flag) break;
+      uint8_t *a = ring + s * kStageBytes;
+      uint8_t *b = a + kTM * kTK * 2;
+      mbar_expect_tx(&full[s], kStageBytes);
+      const int32_t x = (int32_t)(kbeg + (int64_t)kb * kTK);
+      tma_load_2d(a, &tmap, &full[s], x, S0);
+      tma_load_2d(b, &tmap, &full[s], x, T0);
+      issued = kb + 1;
+    }
+    // copies of the last stages may still be in flight if the consumer
+    // stopped: wait for them (bounded) before the CTA can exit
+    const int32_t never = 0;   // the copies themselves must land: ignore the abort flag
+    for (int kb = max(0, issued - kStages); kb < issued; ++kb)
+      (void)mbar_wait(&full[kb % kStages], (kb / kStages) & 1, &never);
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    bool ok = true;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kStages;
+      if (!mbar_wait(&full[s], (kb / kStages) & 1, abort_flag) || *(volatile int32_t *)abort_flag) {
+        set_dev_error(err, DEV_TIMEOUT);
+        atomicExch(abort_flag, 1);
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a = smem_u32(ring + s * kStageBytes);
+      const uint32_t b = a + kTM * kTK * 2;
+#pragma unroll
+      for (int kk = 0; kk < kTK / 16; ++kk) {
+        umma_f16(tmem, smem_desc_sw128(a + kk * 32), smem_desc_sw128(b + kk * 32),
+                 (kb > 0 || kk > 0) ? 1u : 0u);
+      }
+      umma_commit(&empty[s]);   // the stage is free once these MMAs have read it
+    }
+    if (ok) umma_commit(done);
+  }
+  __syncthreads();
+
+  // epilogue: all four warps; warp w owns accumulator rows 32w..32w+31
+  bool have = !*(volatile int32_t *)abort_flag && nk > 0;
+  if (have && !mbar_wait(done, 0, abort_flag)) {
+    set_dev_error(err, DEV_TIMEOUT);
+    have = false;
+  }
+  tc_fence_after();
+  if (have) {
+    const int row = S0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kTN; c0 += 32) {
+      float v[32];
+      tmem_ld_32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (row < k) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = T0 + c0 + j;
+          if (col < k && col <= row && v[j] != 0.0f) {
+            atomicAdd(&G[(int64_t)row * k + col], (double)v[j]);
+            if (col != row) atomicAdd(&G[(int64_t)col * k + row], (double)v[j]);
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+int64_t gram_tc_chunk(int32_t max_count) {
+  // largest multiple of the K tile with chunk * max_count^2 < 2^24
+  if (max_count <= 0) max_count = 1;
+  const int64_t c = ((int64_t)1 << 24) / ((int64_t)max_count * max_count);
+  return (c / kTK) * kTK;
+}
+
+rr_status gram_tensor_cores(int32_t k, int32_t k_pad, int64_t n_pad, const void *Ct,
+                            int32_t max_count, double *G, int32_t *err, cudaStream_t st) {
+  const int64_t chunk = gram_tc_chunk(max_count);
+  if (chunk < kTK || k_pad % kTM != 0 || n_pad % kTK != 0) {
+    rr_set_error("tensor-core Gram: counts too large for exact FP32 chunks");
+    return RR_UNSUPPORTED;
+  }
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) {
+    rr_set_error("cuTensorMapEncodeTiled is not available");
+    return RR_CUDA_ERROR;
+  }
+  CUtensorMap map;
+  const cuuint64_t dims[2] = {(cuuint64_t)n_pad, (cuuint64_t)k_pad};
+  const cuuint64_t strides[1] = {(cuuint64_t)n_pad * 2};
+  const cuuint32_t box[2] = {kTK, kTM};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(Ct), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (cr != CUDA_SUCCESS) {
+    rr_set_error("cuTensorMapEncodeTiled failed (%d)", (int)cr);
+    return RR_CUDA_ERROR;
+  }
+  const int32_t nt = k_pad / kTM;
+  const int32_t n_lower = nt * (nt + 1) / 2;
+  const int64_t n_chunks = (n_pad + chunk - 1) / chunk;
+  const size_t smem = (size_t)kStages * kStageBytes + 1024 + 256;
+  static bool attr = false;
+  if (!attr) {
+    RR_CUDA(cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  RR_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * (size_t)k * k, st));
+  RR_LAUNCH(k_gram_tc, (unsigned)(n_lower * n_chunks), kGramThreads, smem, st, map, k, n_lower,
+            n_pad, chunk, G, err);
+  return RR_OK;
+}
+
+}  // namespace rr

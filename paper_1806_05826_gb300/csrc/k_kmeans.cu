@@ -70,22 +70,24 @@ __device__ int64_t block_incl_scan_i64(int64_t v, int64_t *sm, int64_t *total) {
   return sm[warp] + inc;
 }
 
-__global__ void k_first_center(int64_t F, uint64_t seed, int32_t *centers, uint8_t *chosen) {
+__global__ void k_first_center(int64_t F, uint64_t seed, int32_t *centers, uint8_t *chosen,
+                               int32_t *round) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     int64_t c = (int64_t)floor(uniform53(seed, 0) * (double)F);
     if (c >= F) c = F - 1;
     centers[0] = (int32_t)c;
     chosen[c] = 1;
+    *round = 0;
   }
 }
 
 // ov[j] += 1 for every feature j sharing a row with centre centers[t].
-__global__ void k_seed_overlap(int32_t t, const int32_t *__restrict__ centers,
+__global__ void k_seed_overlap(const int32_t *__restrict__ round, const int32_t *__restrict__ centers,
                                const int64_t *__restrict__ row_ptr,
                                const int32_t *__restrict__ col_idx,
                                const int64_t *__restrict__ col_ptr,
                                const int32_t *__restrict__ row_idx, int32_t *__restrict__ ov) {
-  const int64_t c = centers[t];
+  const int64_t c = centers[*round];
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -97,10 +99,12 @@ __global__ void k_seed_overlap(int32_t t, const int32_t *__restrict__ centers,
 
 // d2[i] = min(d2[i], n_i + n_c - 2 ov[i]) (plain assignment for the first centre);
 // ov reset; per-tile sums of d2.
-__global__ void k_seed_update(int32_t t, int64_t F, const int32_t *__restrict__ centers,
+__global__ void k_seed_update(const int32_t *__restrict__ round, int64_t F,
+                              const int32_t *__restrict__ centers,
                               const int64_t *__restrict__ col_ptr, int32_t *__restrict__ ov,
                               int64_t *__restrict__ d2, int64_t *__restrict__ tile_sum) {
   __shared__ int64_t sm[kWarps + 1];
+  const int32_t t = *round;
   const int64_t c = centers[t];
   const int64_t nc = col_ptr[c + 1] - col_ptr[c];
   int64_t s = 0;
@@ -119,12 +123,18 @@ __global__ void k_seed_update(int32_t t, int64_t F, const int32_t *__restrict__ 
   if (threadIdx.x == 0) tile_sum[blockIdx.x] = s;
 }
 
-// Single block: draws centre t.
-__global__ void k_seed_pick(int32_t t, int64_t F, int64_t ntiles, uint64_t seed,
+// Single block: draws centre t = *round + 1 (if t < k), then advances the round.
+__global__ void k_seed_pick(int32_t *round, int32_t k, int64_t F, int64_t ntiles, uint64_t seed,
                             const int64_t *__restrict__ d2, const int64_t *__restrict__ tile_sum,
                             int32_t *centers, uint8_t *chosen) {
   __shared__ int64_t sm[kWarps + 1];
   __shared__ int64_t found;
+  const int32_t t = *round + 1;
+  __syncthreads();
+  if (t >= k) {
+    if (threadIdx.x == 0) *round = t;
+    return;
+  }
   int64_t s = 0;
   for (int64_t b = threadIdx.x; b < ntiles; b += kThreads) s += tile_sum[b];
   const int64_t total = block_sum_i64(s, sm);
@@ -186,7 +196,12 @@ __global__ void k_seed_pick(int32_t t, int64_t F, int64_t ntiles, uint64_t seed,
   if (threadIdx.x == 0) {
     centers[t] = (int32_t)found;
     if (found >= 0) chosen[found] = 1;
+    *round = t;
   }
+}
+
+__global__ void k_seed_condition(cudaGraphConditionalHandle hc, const int32_t *round, int32_t k) {
+  if (threadIdx.x == 0) cudaGraphSetConditional(hc, *round < k ? 1u : 0u);
 }
 
 __global__ void k_init_labels(int64_t F, int32_t k, const int32_t *__restrict__ centers,
@@ -200,15 +215,6 @@ __global__ void k_set_center_labels(int32_t k, const int32_t *__restrict__ cente
                                     int32_t *__restrict__ labels) {
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < k; s += gridDim.x * blockDim.x)
     labels[centers[s]] = s;
-}
-
-__global__ void k_cluster_sizes(int64_t F, const int32_t *__restrict__ labels,
-                                unsigned long long *__restrict__ n_S) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t l = labels[i];
-    if (l >= 0) atomicAdd(&n_S[l], 1ULL);
-  }
 }
 
 // work_i = sum of the row lengths over the rows of column i (the cost of D_i.)
@@ -251,40 +257,122 @@ __global__ void k_bucket_scatter(int64_t F, const int64_t *__restrict__ work,
     order[atomicAdd(&cursor[work_bucket(work[i])], 1ULL)] = (int32_t)i;
 }
 
-// D[i, S] = x_i . c_S for every feature i, and Q_S += D[i, label_i].
-// Persistent blocks take features heaviest-first from a shared counter; each
-// block counts, in a shared-memory histogram over clusters, the labels of all
-// entries of all rows of column i.
-__global__ void __launch_bounds__(kThreads) k_lloyd_scores(
-    int64_t F, int32_t k, const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
-    const int64_t *__restrict__ col_ptr, const int32_t *__restrict__ row_idx,
-    const int32_t *__restrict__ labels, const int32_t *__restrict__ order, int32_t *work_ctr,
-    int32_t *__restrict__ D, unsigned long long *__restrict__ Q) {
+// Lloyd steps keep D[i, S] = x_i . c_S (integer) resident and update it only
+// through the features whose label changed since the previous step:
+//   D[i, new_j] += |x_i AND x_j|,  D[i, old_j] -= |x_i AND x_j|  for each moved j.
+// The entries of X that belong to moved features are first compacted row by
+// row into (old+1, new) pairs; then every feature accumulates, in a shared
+// histogram over clusters, the pairs of all rows of its column. Exact integer
+// arithmetic: the result equals a full recomputation.
+
+// per row: number of entries whose feature moved
+__global__ void k_moved_count(int64_t N, const int64_t *__restrict__ row_ptr,
+                              const int32_t *__restrict__ col_idx, const int32_t *__restrict__ prev,
+                              const int32_t *__restrict__ cur, int64_t *__restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < N; r += nwarps) {
+    int c = 0;
+    for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) {
+      const int32_t j = col_idx[e];
+      c += prev[j] != cur[j];
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cnt[r] = c;
+  }
+}
+
+// per row: the moved entries as packed pairs ((old + 1) << 16) | new, in row order
+__global__ void k_moved_fill(int64_t N, const int64_t *__restrict__ row_ptr,
+                             const int32_t *__restrict__ col_idx, const int32_t *__restrict__ prev,
+                             const int32_t *__restrict__ cur, const int64_t *__restrict__ mptr,
+                             uint32_t *__restrict__ xm) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < N; r += nwarps) {
+    int64_t out = mptr[r];
+    for (int64_t e0 = row_ptr[r]; e0 < row_ptr[r + 1]; e0 += 32) {
+      const int64_t e = e0 + lane;
+      int32_t o = 0, n = 0;
+      bool moved = false;
+      if (e < row_ptr[r + 1]) {
+        const int32_t j = col_idx[e];
+        o = prev[j];
+        n = cur[j];
+        moved = o != n;
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, moved);
+      if (moved) xm[out + __popc(m & ((1u << lane) - 1u))] = ((uint32_t)(o + 1) << 16) | (uint32_t)n;
+      out += __popc(m);
+    }
+  }
+}
+
+// D[i, .] += delta from the moved pairs of the rows of column i.
+// Persistent blocks take features heaviest-first from a shared counter.
+__global__ void __launch_bounds__(kThreads) k_lloyd_delta(
+    int64_t F, int32_t k, const int64_t *__restrict__ col_ptr, const int32_t *__restrict__ row_idx,
+    const int64_t *__restrict__ mptr, const uint32_t *__restrict__ xm,
+    const int32_t *__restrict__ order, int32_t *work_ctr, int32_t *__restrict__ D) {
   extern __shared__ int32_t acc[];
   __shared__ int32_t cur;
+  __shared__ int32_t touched;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (;;) {
-    if (threadIdx.x == 0) cur = atomicAdd(work_ctr, 1);
+    if (threadIdx.x == 0) {
+      cur = atomicAdd(work_ctr, 1);
+      touched = 0;
+    }
     for (int s = threadIdx.x; s < k; s += kThreads) acc[s] = 0;
     __syncthreads();
     const int32_t it = cur;
     if (it >= F) break;
     const int64_t i = order[it];
+    int any = 0;
     for (int64_t p = col_ptr[i] + warp; p < col_ptr[i + 1]; p += kWarps) {
       const int64_t r = row_idx[p];
-      for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) {
-        const int32_t l = labels[col_idx[e]];
-        if (l >= 0) atomicAdd(&acc[l], 1);
+      const int64_t b = mptr[r], e1 = mptr[r + 1];
+      any |= (e1 > b);
+      // warp-uniform loop; lanes holding the same cluster combine their
+      // increments before one shared-memory atomic (hot clusters repeat in a row)
+      for (int64_t e0 = b; e0 < e1; e0 += 32) {
+        const int64_t e = e0 + lane;
+        const bool valid = e < e1;
+        const uint32_t pr = valid ? xm[e] : 0u;
+        const int32_t nl = valid ? (int32_t)(pr & 0xffffu) : -1;
+        const unsigned m1 = __match_any_sync(0xffffffffu, nl);
+        if (nl >= 0 && lane == __ffs(m1) - 1) atomicAdd(&acc[nl], __popc(m1));
+        const int32_t old = valid ? (int32_t)(pr >> 16) - 1 : -1;
+        const unsigned m2 = __match_any_sync(0xffffffffu, old);
+        if (old >= 0 && lane == __ffs(m2) - 1) atomicSub(&acc[old], __popc(m2));
+      }
+    }
+    if (any) touched = 1;   // benign race: every writer stores 1
+    __syncthreads();
+    if (touched) {
+      int32_t *Di = D + i * (int64_t)k;
+      for (int s = threadIdx.x; s < k; s += kThreads) {
+        const int32_t a = acc[s];
+        if (a) Di[s] += a;
       }
     }
     __syncthreads();
-    int32_t *Di = D + i * (int64_t)k;
-    for (int s = threadIdx.x; s < k; s += kThreads) Di[s] = acc[s];
-    if (threadIdx.x == 0) {
-      const int32_t l = labels[i];
-      if (l >= 0) atomicAdd(&Q[l], (unsigned long long)acc[l]);
+  }
+}
+
+// Q_S = ||c_S||^2 = sum over members i of S of D[i, S]; n_S = |S|.
+__global__ void k_q_sizes(int64_t F, int32_t k, const int32_t *__restrict__ labels,
+                          const int32_t *__restrict__ D, unsigned long long *__restrict__ Q,
+                          unsigned long long *__restrict__ n_S) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t l = labels[i];
+    if (l >= 0) {
+      atomicAdd(&Q[l], (unsigned long long)D[i * (int64_t)k + l]);
+      atomicAdd(&n_S[l], 1ULL);
     }
-    __syncthreads();
   }
 }
 
@@ -339,6 +427,8 @@ __global__ void k_lloyd_argmin(int64_t F, int32_t k, const int32_t *__restrict__
 
 }  // namespace
 
+// The k rounds run as one CUDA graph: a conditional while node whose body is
+// one round (overlaps with the newest centre, distance update, next draw).
 rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                         const int64_t *col_ptr, const int32_t *row_idx, int32_t k, uint64_t seed,
                         KmeansBuffers &b, cudaStream_t st) {
@@ -347,31 +437,72 @@ rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int3
   uint8_t *chosen = reinterpret_cast<uint8_t *>(b.next);   // F bytes of the (unused yet) next[]
   RR_CUDA(cudaMemsetAsync(chosen, 0, F, st));
   RR_CUDA(cudaMemsetAsync(b.ov, 0, sizeof(int32_t) * F, st));
-  RR_LAUNCH(k_first_center, 1, 32, 0, st, F, seed, b.centers, chosen);
-  for (int32_t t = 0; t < k; ++t) {
-    RR_LAUNCH(k_seed_overlap, kSMs * 2, kThreads, 0, st, t, b.centers, row_ptr, col_idx, col_ptr,
-              row_idx, b.ov);
-    RR_LAUNCH(k_seed_update, (unsigned)ntiles, kThreads, 0, st, t, F, b.centers, col_ptr, b.ov,
-              b.d2, b.part_i);
-    if (t + 1 < k)
-      RR_LAUNCH(k_seed_pick, 1, kThreads, 0, st, t + 1, F, ntiles, seed, b.d2, b.part_i,
+  RR_LAUNCH(k_first_center, 1, 32, 0, st, F, seed, b.centers, chosen, b.round);
+
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  rr_status s = RR_OK;
+  auto build = [&]() -> rr_status {
+    RR_CUDA(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle hc;
+    RR_CUDA(cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    RR_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+    RR_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    RR_CUDA(cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    auto body = [&]() -> rr_status {
+      RR_LAUNCH(k_seed_overlap, kSMs * 2, kThreads, 0, cs, b.round, b.centers, row_ptr, col_idx,
+                col_ptr, row_idx, b.ov);
+      RR_LAUNCH(k_seed_update, (unsigned)ntiles, kThreads, 0, cs, b.round, F, b.centers, col_ptr,
+                b.ov, b.d2, b.part_i);
+      RR_LAUNCH(k_seed_pick, 1, kThreads, 0, cs, b.round, k, F, ntiles, seed, b.d2, b.part_i,
                 b.centers, chosen);
-  }
-  return RR_OK;
+      RR_LAUNCH(k_seed_condition, 1, 32, 0, cs, hc, b.round, k);
+      return RR_OK;
+    };
+    const int64_t l0 = rr_launch_counter;
+    rr_status bs = body();
+    rr_launch_counter = l0;
+    cudaGraph_t cap = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &cap);
+    RR_TRY(bs);
+    if (ec != cudaSuccess) {
+      rr_set_error("seeding graph capture failed: %s", cudaGetErrorString(ec));
+      return RR_CUDA_ERROR;
+    }
+    RR_CUDA(cudaGraphInstantiate(&exec, g, 0));
+    RR_CUDA(cudaGraphLaunch(exec, st));
+    rr_launch_counter += 4LL * k;   // the body ran k times
+    RR_CUDA(cudaStreamSynchronize(st));
+    return RR_OK;
+  };
+  s = build();
+  if (exec) cudaGraphExecDestroy(exec);
+  if (g) cudaGraphDestroy(g);
+  if (cs) cudaStreamDestroy(cs);
+  return s;
 }
 
 rr_status kmeans_init_labels(int64_t F, int32_t k, KmeansBuffers &b, cudaStream_t st) {
+  RR_LAUNCH(k_init_labels, grid_for(F, kThreads), kThreads, 0, st, F, k, b.centers, b.prev);
   RR_LAUNCH(k_init_labels, grid_for(F, kThreads), kThreads, 0, st, F, k, b.centers, b.labels);
   RR_LAUNCH(k_set_center_labels, grid_for(k, kThreads), kThreads, 0, st, k, b.centers, b.labels);
+  RR_CUDA(cudaMemsetAsync(b.D, 0, sizeof(int32_t) * (size_t)F * k, st));
   return RR_OK;
 }
 
 rr_status kmeans_work_order(int64_t F, const int64_t *row_ptr, const int64_t *col_ptr,
-                            const int32_t *row_idx, KmeansBuffers &b, int64_t *scratch,
-                            cudaStream_t st) {
-  // scratch: >= F + 2 * kBuckets + scan scratch int64
-  int64_t *work = scratch;
-  int64_t *cnt = scratch + F;
+                            const int32_t *row_idx, KmeansBuffers &b, int64_t *work,
+                            int64_t *scratch, cudaStream_t st) {
+  // scratch: >= 2 * kBuckets + 1 + scan scratch int64
+  int64_t *cnt = scratch;
   int64_t *offs = cnt + kBuckets;              // kBuckets + 1
   int64_t *sscr = offs + kBuckets + 1;
   RR_LAUNCH(k_feature_work, grid_for(F, kWarps), kThreads, 0, st, F, row_ptr, col_ptr, row_idx,
@@ -388,24 +519,33 @@ rr_status kmeans_work_order(int64_t F, const int64_t *row_ptr, const int64_t *co
 rr_status kmeans_lloyd_step(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                             const int64_t *col_ptr, const int32_t *row_idx, int32_t k,
                             KmeansBuffers &b, int64_t *changes_host, cudaStream_t st) {
-  (void)N;
-  RR_CUDA(cudaMemsetAsync(b.n_S, 0, sizeof(int64_t) * k, st));
-  RR_CUDA(cudaMemsetAsync(b.Q, 0, sizeof(int64_t) * k, st));
-  RR_CUDA(cudaMemsetAsync(b.changes, 0, sizeof(int64_t), st));
+  // (1) moved entries (prev != labels), compacted per row
+  RR_LAUNCH(k_moved_count, grid_for(N, kWarps), kThreads, 0, st, N, row_ptr, col_idx, b.prev,
+            b.labels, b.mcount);
+  RR_TRY(scan_exclusive(b.mcount, b.mptr, N, b.scan_scratch, st));
+  RR_LAUNCH(k_moved_fill, grid_for(N, kWarps), kThreads, 0, st, N, row_ptr, col_idx, b.prev,
+            b.labels, b.mptr, b.xm);
+  // (2) D += delta
   RR_CUDA(cudaMemsetAsync(b.work_ctr, 0, sizeof(int32_t), st));
-  RR_LAUNCH(k_cluster_sizes, grid_for(F, kThreads), kThreads, 0, st, F, b.labels,
-            (unsigned long long *)b.n_S);
   const size_t smem = sizeof(int32_t) * (size_t)k;
-  RR_CUDA(cudaFuncSetAttribute(k_lloyd_scores, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  RR_CUDA(cudaFuncSetAttribute(k_lloyd_delta, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)std::max<size_t>(smem, 1)));
   int per_sm = 0;
-  RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lloyd_scores, kThreads, smem));
-  const int grid = kSMs * std::max(1, per_sm);
-  RR_LAUNCH(k_lloyd_scores, grid, kThreads, smem, st, F, k, row_ptr, col_idx, col_ptr, row_idx,
-            b.labels, b.order, b.work_ctr, b.D, (unsigned long long *)b.Q);
+  RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lloyd_delta, kThreads, smem));
+  RR_LAUNCH(k_lloyd_delta, kSMs * std::max(1, per_sm), kThreads, smem, st, F, k, col_ptr, row_idx,
+            b.mptr, b.xm, b.order, b.work_ctr, b.D);
+  // (3) sizes and Q from the updated D
+  RR_CUDA(cudaMemsetAsync(b.n_S, 0, sizeof(int64_t) * k, st));
+  RR_CUDA(cudaMemsetAsync(b.Q, 0, sizeof(int64_t) * k, st));
+  RR_LAUNCH(k_q_sizes, grid_for(F, kThreads), kThreads, 0, st, F, k, b.labels, b.D,
+            (unsigned long long *)b.Q, (unsigned long long *)b.n_S);
+  // (4) assignment
+  RR_CUDA(cudaMemsetAsync(b.changes, 0, sizeof(int64_t), st));
   RR_LAUNCH(k_lloyd_argmin, grid_for(F, kWarps), kThreads, 0, st, F, k, b.D,
             (const unsigned long long *)b.Q, (const unsigned long long *)b.n_S, b.labels, b.next,
             (unsigned long long *)b.changes);
+  // (5) prev <- labels <- next
+  RR_CUDA(cudaMemcpyAsync(b.prev, b.labels, sizeof(int32_t) * F, cudaMemcpyDeviceToDevice, st));
   RR_CUDA(cudaMemcpyAsync(b.labels, b.next, sizeof(int32_t) * F, cudaMemcpyDeviceToDevice, st));
   RR_CUDA(cudaMemcpyAsync(changes_host, b.changes, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   RR_CUDA(cudaStreamSynchronize(st));

@@ -16,28 +16,38 @@ namespace rr {
 
 namespace {
 
-__global__ void k_restrict(int32_t k, const int64_t *__restrict__ cl_ptr,
-                           const int32_t *__restrict__ members, const double *__restrict__ s,
-                           const double *__restrict__ r1, double *__restrict__ rc,
-                           const int32_t *__restrict__ stop) {
+// Restriction, pass 1: one block per work item, an item being a range of at
+// most kRestrictItem members of one cluster (large clusters have several).
+__global__ void k_restrict_items(const RestrictItem *__restrict__ items, int32_t n_items,
+                                 const int32_t *__restrict__ members, const double *__restrict__ r1,
+                                 double *__restrict__ item_sum, const int32_t *__restrict__ stop) {
   if (stop && *stop) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t S = warp; S < k; S += nwarps) {
+  __shared__ double sm[kWarps + 1];
+  for (int32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const RestrictItem w = items[it];
     double acc = 0.0;
-    for (int64_t p = cl_ptr[S] + lane; p < cl_ptr[S + 1]; p += 32) acc += r1[members[p]];
-    acc = warp_sum(acc);
-    if (lane == 0) rc[S] = s[S] * acc;
+    for (int32_t m = w.begin + threadIdx.x; m < w.end; m += blockDim.x) acc += r1[members[m]];
+    const double tot = block_sum(acc, sm);
+    if (threadIdx.x == 0) item_sum[it] = tot;
   }
 }
 
+// Restriction, pass 2 fused with the coarse solve: r_c[S] = s_S * (sum of the
+// item sums of S, in order) is staged in shared memory, then e_c = Ainv r_c.
 __global__ void k_coarse_matvec(int32_t k, const double *__restrict__ Ainv,
-                                const double *__restrict__ rc, double *__restrict__ ec,
+                                const int32_t *__restrict__ item_ptr,
+                                const double *__restrict__ item_sum, const double *__restrict__ s,
+                                double *__restrict__ rc_out, double *__restrict__ ec,
                                 const int32_t *__restrict__ stop) {
   if (stop && *stop) return;
   extern __shared__ double rcs[];
-  for (int i = threadIdx.x; i < k; i += blockDim.x) rcs[i] = rc[i];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    double acc = 0.0;
+    for (int32_t q = item_ptr[i]; q < item_ptr[i + 1]; ++q) acc += item_sum[q];
+    const double v = s[i] * acc;
+    rcs[i] = v;
+    if (blockIdx.x == 0 && rc_out) rc_out[i] = v;
+  }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -49,6 +59,28 @@ __global__ void k_coarse_matvec(int32_t k, const double *__restrict__ Ainv,
     acc = warp_sum(acc);
     if (lane == 0) ec[S] = acc;
   }
+}
+
+__global__ void k_restrict_plan(int32_t k, const int64_t *__restrict__ cl_ptr,
+                                const int32_t *__restrict__ item_ptr, RestrictItem *__restrict__ items) {
+  for (int32_t S = blockIdx.x * blockDim.x + threadIdx.x; S < k; S += gridDim.x * blockDim.x) {
+    const int64_t b = cl_ptr[S], e = cl_ptr[S + 1];
+    int32_t q = item_ptr[S];
+    for (int64_t m = b; m < e; m += kRestrictItem, ++q)
+      items[q] = RestrictItem{(int32_t)m, (int32_t)min(e, m + kRestrictItem)};
+  }
+}
+
+__global__ void k_restrict_counts(int32_t k, const int64_t *__restrict__ cl_ptr,
+                                  int64_t *__restrict__ cnt) {
+  for (int32_t S = blockIdx.x * blockDim.x + threadIdx.x; S < k; S += gridDim.x * blockDim.x)
+    cnt[S] = (cl_ptr[S + 1] - cl_ptr[S] + kRestrictItem - 1) / kRestrictItem;
+}
+
+__global__ void k_i64_to_i32(int64_t n, const int64_t *__restrict__ in, int32_t *__restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (int32_t)in[i];
 }
 
 __global__ void k_prolong_add(int64_t F, const int32_t *__restrict__ labels,
@@ -178,6 +210,11 @@ __global__ void k_sum_parts(const double *__restrict__ part, int n, double *out)
   if (threadIdx.x == 0) *out = v;
 }
 
+__global__ void k_loop_condition(cudaGraphConditionalHandle hc, const PcgScalars *__restrict__ S) {
+  if (threadIdx.x == 0)
+    cudaGraphSetConditional(hc, (!S->converged && S->iter < S->limit) ? 1u : 0u);
+}
+
 __global__ void k_axpby(int64_t n, double a, const double *__restrict__ x, double b,
                         double *__restrict__ y) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -187,15 +224,43 @@ __global__ void k_axpby(int64_t n, double a, const double *__restrict__ x, doubl
 
 }  // namespace
 
-rr_status restrict_clusters(int32_t k, const int64_t *cl_ptr, const int32_t *members,
-                            const double *s, const double *r1, double *rc, const int32_t *stop,
-                            cudaStream_t st) {
-  RR_LAUNCH(k_restrict, grid_for(k, kWarps), kThreads, 0, st, k, cl_ptr, members, s, r1, rc, stop);
+rr_status restrict_plan(int32_t k, const int64_t *cl_ptr, RestrictPlan &plan, int64_t *scratch,
+                        cudaStream_t st) {
+  // scratch: >= 2 (k + 1) + scan scratch int64
+  int64_t *cnt = scratch, *off = scratch + (k + 1), *scr = scratch + 2 * (k + 1);
+  RR_LAUNCH(k_restrict_counts, grid_for(k, kThreads), kThreads, 0, st, k, cl_ptr, cnt);
+  RR_TRY(scan_exclusive(cnt, off, k, scr, st));
+  int64_t n = 0;
+  RR_CUDA(cudaMemcpyAsync(&n, off + k, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  plan.n_items = (int32_t)n;
+  RR_CUDA(cudaMalloc(&plan.item_ptr, sizeof(int32_t) * (k + 1)));
+  RR_CUDA(cudaMalloc(&plan.items, sizeof(RestrictItem) * std::max<int64_t>(1, n)));
+  RR_CUDA(cudaMalloc(&plan.item_sum, sizeof(double) * std::max<int64_t>(1, n)));
+  RR_LAUNCH(k_i64_to_i32, grid_for(k + 1, kThreads), kThreads, 0, st, (int64_t)k + 1, off,
+            plan.item_ptr);
+  RR_LAUNCH(k_restrict_plan, grid_for(k, kThreads), kThreads, 0, st, k, cl_ptr, plan.item_ptr,
+            plan.items);
+  RR_CUDA(cudaStreamSynchronize(st));
   return RR_OK;
 }
 
-rr_status coarse_matvec(int32_t k, const double *Ainv, const double *rc, double *ec,
-                        const int32_t *stop, cudaStream_t st) {
+void restrict_free(RestrictPlan &plan) {
+  cudaFree(plan.item_ptr);
+  cudaFree(plan.items);
+  cudaFree(plan.item_sum);
+  plan = RestrictPlan{};
+}
+
+rr_status restrict_clusters(const RestrictPlan &plan, const int32_t *members, const double *r1,
+                            const int32_t *stop, cudaStream_t st) {
+  RR_LAUNCH(k_restrict_items, std::max(1, std::min(plan.n_items, kSMs * 4)), kThreads, 0, st,
+            plan.items, plan.n_items, members, r1, plan.item_sum, stop);
+  return RR_OK;
+}
+
+rr_status coarse_matvec(int32_t k, const double *Ainv, const RestrictPlan &plan, const double *s,
+                        double *rc, double *ec, const int32_t *stop, cudaStream_t st) {
   const size_t smem = sizeof(double) * (size_t)k;
   static int attr_for = -1;
   if (smem > 48 * 1024 && attr_for < k) {
@@ -203,7 +268,8 @@ rr_status coarse_matvec(int32_t k, const double *Ainv, const double *rc, double 
                                  (int)smem));
     attr_for = k;
   }
-  RR_LAUNCH(k_coarse_matvec, grid_for(k, kWarps), kThreads, smem, st, k, Ainv, rc, ec, stop);
+  RR_LAUNCH(k_coarse_matvec, grid_for(k, kWarps), kThreads, smem, st, k, Ainv, plan.item_ptr,
+            plan.item_sum, s, rc, ec, stop);
   return RR_OK;
 }
 
@@ -258,6 +324,11 @@ rr_status sum_parts(const double *part, int n, double *out, cudaStream_t st) {
 
 rr_status copy_f64(double *dst, const double *src, int64_t n, cudaStream_t st) {
   RR_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  return RR_OK;
+}
+
+rr_status loop_condition(cudaGraphConditionalHandle hc, const PcgScalars *S, cudaStream_t st) {
+  RR_LAUNCH(k_loop_condition, 1, 32, 0, st, hc, S);
   return RR_OK;
 }
 

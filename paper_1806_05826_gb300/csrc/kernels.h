@@ -38,28 +38,37 @@ struct KmeansBuffers {
   double *part;        // [kMaxGrid] per-block D^2 sums (exact integers in FP64 range)
   int64_t *part_i;     // [kMaxGrid]
   int32_t *centers;    // [k]
-  int32_t *labels;     // [F]
+  int32_t *labels;     // [F]   current labels (-1: not assigned yet)
+  int32_t *prev;       // [F]   labels of the previous step
   int32_t *next;       // [F]
+  int64_t *mcount;     // [N]   moved entries per row
+  int64_t *mptr;       // [N+1]
+  uint32_t *xm;        // [nnz] moved entries as ((old+1) << 16) | new
+  int64_t *scan_scratch;
   int64_t *n_S;        // [k]
   int64_t *Q;          // [k]
-  int32_t *D;          // [F*k]
+  int32_t *D;          // [F*k] D[i, S] = x_i . c_S for the current labels
   int64_t *changes;    // [1]
   int32_t *work_ctr;   // [1]
   int32_t *order;      // [F] features by descending work (heaviest first)
+  int32_t *round;      // [1] seeding round (device-side loop counter)
 };
 rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                         const int64_t *col_ptr, const int32_t *row_idx, int32_t k, uint64_t seed,
                         KmeansBuffers &b, cudaStream_t st);
-// labels <- -1 except labels[centers[S]] = S.
+// labels <- -1 except labels[centers[S]] = S; prev <- -1; D <- 0.
 rr_status kmeans_init_labels(int64_t F, int32_t k, KmeansBuffers &b, cudaStream_t st);
 // One Lloyd assignment step; on return (stream synchronised) *changes_host holds
 // the number of labels that changed.
 rr_status kmeans_lloyd_step(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                             const int64_t *col_ptr, const int32_t *row_idx, int32_t k,
                             KmeansBuffers &b, int64_t *changes_host, cudaStream_t st);
+// order[] = features by descending work_i = sum of the row lengths of column i
+// (heaviest first); work[] receives work_i, which is also the Gershgorin row
+// sum of X^T X for binary X.
 rr_status kmeans_work_order(int64_t F, const int64_t *row_ptr, const int64_t *col_ptr,
-                            const int32_t *row_idx, KmeansBuffers &b, int64_t *scratch,
-                            cudaStream_t st);
+                            const int32_t *row_idx, KmeansBuffers &b, int64_t *work,
+                            int64_t *scratch, cudaStream_t st);
 
 // ---- k_coarse.cu --------------------------------------------------------
 // Compacts labels in place to 0..k_eff-1 (order kept); n_S compacted too.
@@ -68,13 +77,23 @@ rr_status compact_clusters(int64_t F, int32_t k, int32_t *labels, int64_t *n_S, 
                            int32_t *k_eff_host, cudaStream_t st);
 // s_S = 1/sqrt(n_S)
 rr_status prolong_scale(int32_t k, const int64_t *n_S, double *s, cudaStream_t st);
-// Ct[S, r] (k_pad x n_pad, FP16, K-major) = number of features of cluster S in row r.
+// C32[S, r] (k_pad x n_pad, int32, K-major) = number of features of cluster S in
+// row r; *max_count receives the largest count.
 rr_status coarse_counts(int64_t N, int64_t n_pad, int32_t k_pad, const int64_t *row_ptr,
-                        const int32_t *col_idx, const int32_t *labels, void *Ct, int32_t *err,
-                        cudaStream_t st);
-// G = Ct Ct^T exact (CUDA cores, int32 chunks summed in int64) -> G as FP64 (k x k).
-rr_status gram_exact_cuda_cores(int32_t k, int32_t k_pad, int64_t n_pad, const void *Ct, double *G,
-                                cudaStream_t st);
+                        const int32_t *col_idx, const int32_t *labels, int32_t *C32,
+                        int32_t *max_count, cudaStream_t st);
+// FP16 copy of n counts (each <= 2048, so exact).
+rr_status counts_to_half(int64_t n, const int32_t *C32, void *C16, cudaStream_t st);
+// ---- k_gram_tc.cu -------------------------------------------------------
+// K rows per tensor-core chunk that keep every FP32 partial sum exact (< 2^24)
+// for counts up to max_count; < 64 means the tensor-core path cannot be exact.
+int64_t gram_tc_chunk(int32_t max_count);
+// G = Ct Ct^T (k x k, FP64, exact) with tcgen05 MMAs; k_pad % 128 == 0, n_pad % 64 == 0.
+rr_status gram_tensor_cores(int32_t k, int32_t k_pad, int64_t n_pad, const void *Ct,
+                            int32_t max_count, double *G, int32_t *err, cudaStream_t st);
+// G = C32 C32^T exact (CUDA cores, int32 steps summed in int64) -> G as FP64 (k x k).
+rr_status gram_exact_cuda_cores(int32_t k, int32_t k_pad, int64_t n_pad, const int32_t *C32,
+                                double *G, cudaStream_t st);
 // A_c lower triangle (G[S,T] s_S) s_T + lambda on the diagonal, mirrored.
 rr_status coarse_operator(int32_t k, const double *G, const double *s, double lambda, double *Ac,
                           cudaStream_t st);
@@ -83,30 +102,9 @@ rr_status cholesky(int32_t k, double *L, int32_t *err, cudaStream_t st);
 // Ainv = L^{-T} L^{-1} (full symmetric). Linv: k x k workspace.
 rr_status chol_inverse(int32_t k, const double *L, double *Linv, double *Ainv, cudaStream_t st);
 
-// ---- k_spmv.cu ----------------------------------------------------------
-// Work items of the transpose mat-vec: every column is cut into pieces of at
-// most kCscChunk nonzeros; columns of one piece finish in place, longer ones
-// in a second pass over their piece sums.
-struct CscItem {
-  int64_t begin, end;  // range in row_idx
-  int32_t col;         // column
-  int32_t slot;        // -1: whole column; else index into piece sums
-};
-struct CscPlan {
-  CscItem *items = nullptr;
-  int64_t n_items = 0;
-  int32_t *heavy_col = nullptr;   // columns cut into >1 pieces
-  int32_t *heavy_first = nullptr; // their first slot
-  int32_t *heavy_n = nullptr;     // their number of slots
-  int64_t n_heavy = 0;
-  int64_t n_slots = 0;
-  double *slot_sum = nullptr;     // [n_slots]
-};
-constexpr int kCscChunk = 2048;
-rr_status csc_plan_build(int64_t F, const int64_t *col_ptr, CscPlan &plan, cudaStream_t st);
-void csc_plan_free(CscPlan &plan);
-
-// Epilogues of t_i = (X^T u)_i + lambda v_i, fused into the transpose mat-vec.
+// ---- operator epilogues ------------------------------------------------
+// Epilogues of t_i = (X^T u)_i + lambda v_i, applied where the transposed
+// mat-vec's piece sums are combined (k_sliced.cu).
 enum CscMode : int32_t {
   CSC_RHS = 0,     // out = X^T u                    (b = X^T y; v unused)
   CSC_APPLY = 1,   // out = t
@@ -126,12 +124,47 @@ struct CscEpilogue {
   double *dot_part;   // per-block partial dots (POST/PCG/RESID), 2 * kMaxGrid entries
   const int32_t *stop;  // if non-null and *stop != 0 the kernels return at once
 };
-rr_status csr_spmv(int64_t N, const int64_t *row_ptr, const int32_t *col_idx, const double *v,
-                   double *u, const int32_t *stop, cudaStream_t st);
-rr_status csc_spmv(int64_t F, const int32_t *row_idx, const double *u, const CscPlan &plan,
-                   const CscEpilogue &ep, cudaStream_t st);
-// Number of partial dots csc_spmv writes into ep.dot_part.
-int csc_dot_parts(const CscPlan &plan);
+
+// ---- k_sliced.cu --------------------------------------------------------
+// Sliced binary pattern (see k_sliced.cu): the gathered dimension (n_inner)
+// cut into nb slices of W <= kSliceMax entries, 16-bit offsets in 16-byte
+// words, segments cut into pieces of <= kPieceWords words, one FP64 sum slot
+// per piece, slots of an outer index contiguous.
+constexpr int kSliceMax = 27648;   // FP64 slice + pad = 216 KiB of shared memory
+constexpr int kPieceWords = 32;
+struct SlicedView {
+  int32_t W;
+  int64_t n_inner;
+  const int32_t *pw;
+  const int32_t *slot;
+  const uint4 *idx;
+  const int32_t *task_slice;
+  const int32_t *task_p;
+};
+struct SlicedPattern {
+  int64_t n_outer = 0, n_inner = 0, nwords = 0, npieces = 0;
+  int32_t nb = 0, W = 0, ntasks = 0, tasks_per_slice = 0;
+  int32_t *pw = nullptr;         // [npieces+1] first word of each piece (slice-major)
+  int32_t *slot = nullptr;       // [npieces]   sum slot of each piece (outer-major)
+  int32_t *slot_ptr = nullptr;   // [n_outer+1] slots of each outer index
+  uint4 *idx = nullptr;          // [nwords]
+  double *psum = nullptr;        // [npieces]   piece sums
+  int32_t *task_slice = nullptr; // [ntasks]
+  int32_t *task_p = nullptr;     // [ntasks+1]
+  SlicedView view() const { return SlicedView{W, n_inner, pw, slot, idx, task_slice, task_p}; }
+};
+// outer_ptr/inner: a pattern with inner indices ascending within each outer index.
+rr_status sliced_build(int64_t n_outer, int64_t n_inner, const int64_t *outer_ptr,
+                       const int32_t *inner, SlicedPattern &P, cudaStream_t st);
+void sliced_free(SlicedPattern &P);
+// piece sums of P against x (or, when `in` is given, against the per-index
+// sums of in's slots: the output of a previous pass).
+rr_status sliced_gather(const SlicedPattern &P, const double *x, const SlicedPattern *in,
+                        const int32_t *stop, cudaStream_t st);
+// out[o] = sum of the slots of outer index o.
+rr_status sliced_slot_sum(const SlicedPattern &P, double *out, cudaStream_t st);
+// t_i = slot sums of feature i, then the epilogue; kVecGrid partial dots.
+rr_status sliced_epilogue(const SlicedPattern &P, const CscEpilogue &ep, cudaStream_t st);
 
 // ---- k_pcg.cu -----------------------------------------------------------
 struct PcgScalars {
@@ -143,16 +176,31 @@ struct PcgScalars {
   int32_t converged; // 1 once ||r|| <= target: later kernels of the loop return at once
   int32_t nonfinite; // 1 if a NaN/Inf was met
   int32_t first;     // 1 before the first direction of a (re)start
+  int32_t limit;     // iteration limit of the device-side loop
 };
 constexpr int kVecGrid = kSMs * 4;   // fixed grid of the vector kernels (deterministic partials)
 
-// r_c[S] = s_S * sum_{i in S} r1[i] (members ascending), one warp per cluster.
-rr_status restrict_clusters(int32_t k, const int64_t *cl_ptr, const int32_t *members,
-                            const double *s, const double *r1, double *rc, const int32_t *stop,
-                            cudaStream_t st);
-// e_c = Ainv r_c.
-rr_status coarse_matvec(int32_t k, const double *Ainv, const double *rc, double *ec,
-                        const int32_t *stop, cudaStream_t st);
+// Restriction r_c[S] = s_S * sum_{i in S} r1[i] over the member list (members of
+// S ascending). Large clusters are cut into items of <= kRestrictItem members;
+// item sums are combined per cluster, in order, inside coarse_matvec.
+constexpr int kRestrictItem = 4096;
+struct RestrictItem {
+  int32_t begin, end;   // range in the member list
+};
+struct RestrictPlan {
+  int32_t n_items = 0;
+  int32_t *item_ptr = nullptr;    // [k+1] items of each cluster
+  RestrictItem *items = nullptr;  // [n_items]
+  double *item_sum = nullptr;     // [n_items]
+};
+rr_status restrict_plan(int32_t k, const int64_t *cl_ptr, RestrictPlan &plan, int64_t *scratch,
+                        cudaStream_t st);
+void restrict_free(RestrictPlan &plan);
+rr_status restrict_clusters(const RestrictPlan &plan, const int32_t *members, const double *r1,
+                            const int32_t *stop, cudaStream_t st);
+// r_c from the item sums (also written to rc when non-null), then e_c = Ainv r_c.
+rr_status coarse_matvec(int32_t k, const double *Ainv, const RestrictPlan &plan, const double *s,
+                        double *rc, double *ec, const int32_t *stop, cudaStream_t st);
 // z2 = z1 + s[l(i)] e_c[l(i)].
 rr_status prolong_add(int64_t F, const int32_t *labels, const double *s, const double *ec,
                       const double *z1, double *z2, const int32_t *stop, cudaStream_t st);
@@ -181,6 +229,8 @@ rr_status pcg_start(const double *bb_part, int n_bb, const double *rr_part, int 
 // *out = fixed-order sum of n partials.
 rr_status sum_parts(const double *part, int n, double *out, cudaStream_t st);
 rr_status copy_f64(double *dst, const double *src, int64_t n, cudaStream_t st);
+// Sets the while-loop condition of a graph: !converged && iter < limit.
+rr_status loop_condition(cudaGraphConditionalHandle hc, const PcgScalars *S, cudaStream_t st);
 // dst = src (or zero when src == nullptr) for vectors of F entries; device helper kernels.
 rr_status axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t st);
 

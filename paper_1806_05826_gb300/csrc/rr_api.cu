@@ -58,30 +58,25 @@ struct DevArena {
 };
 
 // d_i = ||x_i||^2 + lambda (column nnz for binary X); ratio_i = (sum_j |A_ij|) / d_i
-// with sum_j |(X^T X)_ij| = sum_{r in col i} rownnz_r (exact integers). The
-// maximum ratio is kept through the order-preserving bit pattern of positive doubles.
-__global__ void k_jacobi_setup(int64_t F, double lambda, const int64_t *__restrict__ row_ptr,
-                               const int64_t *__restrict__ col_ptr,
-                               const int32_t *__restrict__ row_idx, double *__restrict__ d,
+// with sum_j |(X^T X)_ij| = gsum_i (an exact integer). The maximum ratio is
+// kept through the order-preserving bit pattern of positive doubles.
+__global__ void k_jacobi_setup(int64_t F, double lambda, const int64_t *__restrict__ col_ptr,
+                               const int64_t *__restrict__ gsum, double *__restrict__ d,
                                unsigned long long *__restrict__ max_bits) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = warp; i < F; i += nwarps) {
-    int64_t s = 0;
-    for (int64_t p = col_ptr[i] + lane; p < col_ptr[i + 1]; p += 32) {
-      const int64_t r = row_idx[p];
-      s += row_ptr[r + 1] - row_ptr[r];
-    }
-    s = rr::warp_sum_i64(s);
-    if (lane == 0) {
-      const double di = (double)(col_ptr[i + 1] - col_ptr[i]) + lambda;
-      d[i] = di;
-      const double ratio = ((double)s + lambda) / di;
-      unsigned long long bits = (unsigned long long)__double_as_longlong(ratio);
-      atomicMax(max_bits, bits);
-    }
+  unsigned long long best = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double di = (double)(col_ptr[i + 1] - col_ptr[i]) + lambda;
+    d[i] = di;
+    const double ratio = ((double)gsum[i] + lambda) / di;
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(ratio);
+    best = bits > best ? bits : best;
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t = __shfl_xor_sync(0xffffffffu, best, o);
+    best = t > best ? t : best;
+  }
+  if ((threadIdx.x & 31) == 0) atomicMax(max_bits, best);
 }
 
 __global__ void k_omega(const unsigned long long *max_bits, double *omega_out) {
@@ -114,14 +109,24 @@ struct rr_handle {
   double *G = nullptr, *Ac = nullptr, *Lw = nullptr, *Linv = nullptr, *Ainv = nullptr;
   // smoother
   double *d = nullptr;
+  int64_t *gsum = nullptr;   // sum_j |(X^T X)_ij| = sum of the row lengths over column i
   double *omega_dev = nullptr;
   unsigned long long *max_bits = nullptr;
-  rr::CscPlan plan;
+  rr::RestrictPlan rplan;
+  rr::SlicedPattern pcsr;   // X by row, vector v cut in feature slices
+  rr::SlicedPattern pcsc;   // X^T by column, vector u cut in row slices
   // solve workspace
   double *b = nullptr, *r = nullptr, *z1 = nullptr, *z2 = nullptr, *z = nullptr, *p = nullptr,
          *q = nullptr, *r1 = nullptr, *u = nullptr, *rc = nullptr, *ec = nullptr, *rt = nullptr;
   double *part_rz = nullptr, *part_pq = nullptr, *part_rr = nullptr, *part_bb = nullptr;
   double *scal = nullptr;
+  double *w_int = nullptr;         // the iterate (graphs capture fixed pointers)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t loop_graph = nullptr;
+  cudaGraphExec_t loop_exec = nullptr;
+  int32_t *limit_host = nullptr;
+  int64_t body_kernels = 0;
+  bool gram_on_tensor_cores = false;
   rr::PcgScalars *S = nullptr;
   rr::PcgScalars *S_host = nullptr;
   double *scal_host = nullptr;
@@ -151,6 +156,9 @@ rr_status check_dev_error(rr_handle *h, const char *where) {
     case rr::DEV_COUNT_OVERFLOW:
       rr_set_error("%s: a row holds more than 2048 features of one cluster", where);
       return RR_UNSUPPORTED;
+    case rr::DEV_TIMEOUT:
+      rr_set_error("%s: a bounded device wait expired", where);
+      return RR_TIMEOUT;
     default:
       rr_set_error("%s: device error %d", where, e);
       return RR_CUDA_ERROR;
@@ -166,8 +174,8 @@ rr_status build_lambda(rr_handle *h, double lambda) {
   RR_TRY(rr::cholesky(k, h->Lw, h->err, st));
   RR_TRY(rr::chol_inverse(k, h->Lw, h->Linv, h->Ainv, st));
   RR_CUDA(cudaMemsetAsync(h->max_bits, 0, sizeof(unsigned long long), st));
-  RR_LAUNCH(k_jacobi_setup, rr::grid_for(h->F, rr::kWarps), kThreads, 0, st, h->F, lambda,
-            h->row_ptr, h->col_ptr, h->row_idx, h->d, h->max_bits);
+  RR_LAUNCH(k_jacobi_setup, rr::grid_for(h->F, kThreads), kThreads, 0, st, h->F, lambda,
+            h->col_ptr, h->gsum, h->d, h->max_bits);
   RR_LAUNCH(k_omega, 1, 32, 0, st, h->max_bits, h->omega_dev);
   double om = 0.0;
   RR_CUDA(cudaMemcpyAsync(&om, h->omega_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -256,6 +264,11 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&h->labels, F));
   kb.labels = h->labels;
   RR_TRY(m.alloc(&kb.next, F));
+  RR_TRY(m.alloc(&kb.prev, F));
+  RR_TRY(m.alloc(&kb.mcount, N));
+  RR_TRY(m.alloc(&kb.mptr, N + 1));
+  RR_TRY(m.alloc(&kb.xm, nnz));
+  RR_TRY(m.alloc(&kb.scan_scratch, rr::scan_scratch_len(N) + 8));
   RR_TRY(m.alloc(&h->n_S, 2 * (int64_t)k));
   kb.n_S = h->n_S;
   RR_TRY(m.alloc(&kb.Q, k));
@@ -263,6 +276,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&kb.changes, 1));
   RR_TRY(m.alloc(&kb.work_ctr, 1));
   RR_TRY(m.alloc(&kb.order, F));
+  RR_TRY(m.alloc(&kb.round, 1));
   if (h->opt.init_centers) {
     std::vector<char> seen(F, 0);
     for (int32_t s = 0; s < k; ++s) {
@@ -280,7 +294,8 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
                              h->opt.seed, kb, st));
   }
   RR_TRY(rr::kmeans_init_labels(F, k, kb, st));
-  RR_TRY(rr::kmeans_work_order(F, h->row_ptr, h->col_ptr, h->row_idx, kb, scratch64, st));
+  RR_TRY(m.alloc(&h->gsum, F));
+  RR_TRY(rr::kmeans_work_order(F, h->row_ptr, h->col_ptr, h->row_idx, kb, h->gsum, scratch64, st));
   int64_t *changes_host = nullptr;
   RR_CUDA(cudaMallocHost(&changes_host, sizeof(int64_t)));
   int32_t it = 0;
@@ -295,6 +310,11 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(ks);
   h->kmeans_iters = it;
   m.release(kb.D);
+  m.release(kb.prev);
+  m.release(kb.mcount);
+  m.release(kb.mptr);
+  m.release(kb.xm);
+  m.release(kb.scan_scratch);
   m.release(kb.d2);
   m.release(kb.ov);
   m.release(kb.Q);
@@ -314,25 +334,44 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
                                scratch64 + big, tmp32, scratch64 + 2 * big, st));
   RR_TRY(m.alloc(&h->s, k_eff));
   RR_TRY(rr::prolong_scale(k_eff, h->n_S, h->s, st));
+  RR_TRY(rr::restrict_plan(k_eff, h->cl_ptr, h->rplan, scratch64, st));
 
-  // ---- exact coarse Gram G = C^T C
+  // ---- exact coarse Gram G = C^T C (C = X * onehot(labels), integer counts)
   const int64_t n_pad = round_up(std::max<int64_t>(N, 1), 64);
   const int32_t k_pad = (int32_t)round_up(k_eff, 128);
-  void *Ct = nullptr;
-  if (cudaMalloc(&Ct, 2 * (size_t)k_pad * n_pad) != cudaSuccess) {
-    cudaGetLastError();
-    rr_set_error("cudaMalloc of the coarse count matrix failed");
-    return RR_OOM;
-  }
-  rr_status gs = rr::coarse_counts(N, n_pad, k_pad, h->row_ptr, h->col_idx, h->labels, Ct, h->err, st);
-  if (gs == RR_OK) gs = check_dev_error(h, "coarse counts");
+  const size_t ncount = (size_t)k_pad * n_pad;
+  int32_t *C32 = nullptr;
+  void *C16 = nullptr;
+  int32_t *maxc_dev = nullptr;
+  RR_TRY(m.alloc(&maxc_dev, 1));
   RR_TRY(m.alloc(&h->G, (int64_t)k_eff * k_eff));
-  if (gs == RR_OK) gs = rr::gram_exact_cuda_cores(k_eff, k_pad, n_pad, Ct, h->G, st);
-  if (gs == RR_OK && cudaStreamSynchronize(st) != cudaSuccess) {
-    rr_set_error("coarse Gram failed");
+  rr_status gs = m.alloc(&C32, ncount);
+  int32_t max_count = 0;
+  if (gs == RR_OK)
+    gs = rr::coarse_counts(N, n_pad, k_pad, h->row_ptr, h->col_idx, h->labels, C32, maxc_dev, st);
+  if (gs == RR_OK &&
+      (cudaMemcpyAsync(&max_count, maxc_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess)) {
+    rr_set_error("coarse counts failed");
     gs = RR_CUDA_ERROR;
   }
-  cudaFree(Ct);
+  if (gs == RR_OK && max_count >= 8192) {
+    rr_set_error("rr_setup: a row holds %d features of one cluster (limit 8191)", max_count);
+    gs = RR_UNSUPPORTED;
+  }
+  h->gram_on_tensor_cores = h->opt.gram == RR_GRAM_AUTO && max_count <= 2048 &&
+                            rr::gram_tc_chunk(max_count) >= 64;
+  if (gs == RR_OK && h->gram_on_tensor_cores) {
+    gs = m.alloc(reinterpret_cast<uint16_t **>(&C16), ncount);
+    if (gs == RR_OK) gs = rr::counts_to_half((int64_t)ncount, C32, C16, st);
+    if (gs == RR_OK) m.release(C32), C32 = nullptr;
+    if (gs == RR_OK) gs = rr::gram_tensor_cores(k_eff, k_pad, n_pad, C16, max_count, h->G, h->err, st);
+  } else if (gs == RR_OK) {
+    gs = rr::gram_exact_cuda_cores(k_eff, k_pad, n_pad, C32, h->G, st);
+  }
+  if (gs == RR_OK) gs = check_dev_error(h, "coarse Gram");
+  if (C32) m.release(C32);
+  if (C16) m.release(C16);
   RR_TRY(gs);
 
   // ---- per-lambda coarse factor and smoother
@@ -346,10 +385,11 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&h->max_bits, 1));
   RR_TRY(build_lambda(h, lambda));
 
-  // ---- transposed mat-vec plan and solve workspace
-  RR_TRY(rr::csc_plan_build(F, h->col_ptr, h->plan, st));
-  h->n_parts = std::max(rr::csc_dot_parts(h->plan), rr::kVecGrid);
-  for (double **v : {&h->b, &h->r, &h->z1, &h->z2, &h->z, &h->p, &h->q, &h->r1, &h->rt})
+  // ---- sliced patterns of X and X^T and the solve workspace
+  RR_TRY(rr::sliced_build(N, F, h->row_ptr, h->col_idx, h->pcsr, st));
+  RR_TRY(rr::sliced_build(F, N, h->col_ptr, h->row_idx, h->pcsc, st));
+  h->n_parts = rr::kVecGrid;
+  for (double **v : {&h->b, &h->r, &h->z1, &h->z2, &h->z, &h->p, &h->q, &h->r1, &h->rt, &h->w_int})
     RR_TRY(m.alloc(v, F));
   RR_TRY(m.alloc(&h->u, std::max<int64_t>(N, 1)));
   RR_TRY(m.alloc(&h->rc, k_eff));
@@ -360,6 +400,8 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&h->S, 1));
   RR_CUDA(cudaMallocHost(&h->S_host, sizeof(rr::PcgScalars)));
   RR_CUDA(cudaMallocHost(&h->scal_host, 4 * sizeof(double)));
+  RR_CUDA(cudaMallocHost(&h->limit_host, sizeof(int32_t)));
+  RR_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   h->hist_cap = h->opt.max_iter;
   RR_TRY(m.alloc(&h->history, h->hist_cap));
   m.release(tmp32);
@@ -371,50 +413,142 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   m.release(kb.changes);
   m.release(kb.work_ctr);
   m.release(kb.order);
+  m.release(kb.round);
   RR_CUDA(cudaStreamSynchronize(st));
+  return RR_OK;
+}
+
+// ---- the operator: t = X^T (X v) + lambda v, finished by the epilogue ep.
+rr_status op_apply(rr_handle *h, const double *v, const rr::CscEpilogue &ep, const int32_t *stop,
+                   cudaStream_t st) {
+  RR_TRY(rr::sliced_gather(h->pcsr, v, nullptr, stop, st));
+  RR_TRY(rr::sliced_gather(h->pcsc, nullptr, &h->pcsr, stop, st));
+  RR_TRY(rr::sliced_epilogue(h->pcsc, ep, st));
   return RR_OK;
 }
 
 // ---- the preconditioner: z = M^{-1} r, with <r, z> partials in part_rz.
 rr_status apply_precond(rr_handle *h, const double *r, double *z, const int32_t *stop, int *n_rz,
-                        bool z1_ready) {
-  cudaStream_t st = h->st;
-  const int64_t N = h->N, F = h->F;
+                        bool z1_ready, cudaStream_t st) {
+  const int64_t F = h->F;
+  *n_rz = rr::kVecGrid;
   switch (h->opt.solver) {
     case RR_SOLVER_CG:
-      *n_rz = rr::kVecGrid;
       return rr::jacobi(F, 1.0, r, nullptr, z, h->part_rz, stop, st);
     case RR_SOLVER_DCG:
-      *n_rz = rr::kVecGrid;
       return rr::jacobi(F, 1.0, r, h->d, z, h->part_rz, stop, st);
     default: {
       // symmetric two-level cycle: z1 = w D^-1 r; r1 = r - A z1; e_c = A_c^-1 P^T r1;
       // z2 = z1 + P e_c; r2 = r - A z2; z = z2 + w D^-1 r2
       if (!z1_ready) RR_TRY(rr::jacobi(F, h->omega, r, h->d, h->z1, nullptr, stop, st));
-      RR_TRY(rr::csr_spmv(N, h->row_ptr, h->col_idx, h->z1, h->u, stop, st));
       rr::CscEpilogue pre{rr::CSC_PRE, h->lambda, h->omega, h->z1, r, h->d, h->r1, nullptr, stop};
-      RR_TRY(rr::csc_spmv(F, h->row_idx, h->u, h->plan, pre, st));
-      RR_TRY(rr::restrict_clusters(h->k_eff, h->cl_ptr, h->members, h->s, h->r1, h->rc, stop, st));
-      RR_TRY(rr::coarse_matvec(h->k_eff, h->Ainv, h->rc, h->ec, stop, st));
+      RR_TRY(op_apply(h, h->z1, pre, stop, st));
+      RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->r1, stop, st));
+      RR_TRY(rr::coarse_matvec(h->k_eff, h->Ainv, h->rplan, h->s, nullptr, h->ec, stop, st));
       RR_TRY(rr::prolong_add(F, h->labels, h->s, h->ec, h->z1, h->z2, stop, st));
-      RR_TRY(rr::csr_spmv(N, h->row_ptr, h->col_idx, h->z2, h->u, stop, st));
       rr::CscEpilogue post{rr::CSC_POST, h->lambda, h->omega, h->z2, r, h->d, z, h->part_rz, stop};
-      RR_TRY(rr::csc_spmv(F, h->row_idx, h->u, h->plan, post, st));
-      *n_rz = rr::csc_dot_parts(h->plan);
-      return RR_OK;
+      return op_apply(h, h->z2, post, stop, st);
     }
   }
 }
 
+// ---- one PCG iteration on the handle's vectors (w_int, r, z, p, q); every
+// kernel returns at once when S->converged is set.
+rr_status pcg_iteration(rr_handle *h, cudaStream_t st) {
+  const int64_t F = h->F;
+  const bool twolevel = h->opt.solver == RR_SOLVER_TWOLEVEL;
+  const int32_t *stop = &h->S->converged;
+  int n_rz = 0;
+  RR_TRY(apply_precond(h, h->r, h->z, stop, &n_rz, twolevel, st));
+  RR_TRY(rr::pcg_direction(F, h->part_rz, n_rz, h->z, h->p, h->S, st));
+  rr::CscEpilogue ap{rr::CSC_PCG, h->lambda, h->omega, h->p, nullptr, nullptr, h->q, h->part_pq, stop};
+  RR_TRY(op_apply(h, h->p, ap, stop, st));
+  RR_TRY(rr::pcg_update(F, h->part_rz, n_rz, h->part_pq, rr::kVecGrid, h->p, h->q, h->w_int,
+                        h->r, h->omega, h->d, twolevel ? h->z1 : nullptr, h->part_rr, h->S, st));
+  RR_TRY(rr::pcg_finish(h->part_rz, n_rz, h->part_rr, rr::kVecGrid, h->S, h->history,
+                        h->hist_cap, st));
+  return RR_OK;
+}
+
+void destroy_graph(rr_handle *h) {
+  if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
+  if (h->loop_graph) cudaGraphDestroy(h->loop_graph);
+  h->loop_exec = nullptr;
+  h->loop_graph = nullptr;
+}
+
+// The whole iteration loop as one graph: a conditional while node whose body
+// is one PCG iteration followed by a kernel that keeps the loop going while
+// the device-side state says "not converged and below the iteration limit".
+rr_status build_loop_graph(rr_handle *h) {
+  destroy_graph(h);
+  cudaGraph_t g = nullptr;
+  RR_CUDA(cudaGraphCreate(&g, 0));
+  h->loop_graph = g;
+  cudaGraphConditionalHandle hc;
+  RR_CUDA(cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  RR_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaStream_t cs = h->cap_stream;
+  RR_CUDA(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  const int64_t l0 = rr_launch_counter;
+  rr_status s = pcg_iteration(h, cs);
+  if (s == RR_OK) s = rr::loop_condition(hc, h->S, cs);
+  h->body_kernels = rr_launch_counter - l0;   // recorded, not launched
+  rr_launch_counter = l0;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(cs, &captured);
+  RR_TRY(s);
+  if (ec != cudaSuccess) {
+    rr_set_error("graph capture failed: %s", cudaGetErrorString(ec));
+    return RR_CUDA_ERROR;
+  }
+  RR_CUDA(cudaGraphInstantiate(&h->loop_exec, g, 0));
+  return RR_OK;
+}
+
 rr_status true_residual(rr_handle *h, const double *w, double *rr_out) {
   cudaStream_t st = h->st;
-  RR_TRY(rr::csr_spmv(h->N, h->row_ptr, h->col_idx, w, h->u, nullptr, st));
   rr::CscEpilogue ep{rr::CSC_RESID, h->lambda, h->omega, w, h->b, h->d, h->rt, h->part_bb, nullptr};
-  RR_TRY(rr::csc_spmv(h->F, h->row_idx, h->u, h->plan, ep, st));
-  RR_TRY(rr::sum_parts(h->part_bb, rr::csc_dot_parts(h->plan), h->scal, st));
+  RR_TRY(op_apply(h, w, ep, nullptr, st));
+  RR_TRY(rr::sum_parts(h->part_bb, rr::kVecGrid, h->scal, st));
   RR_CUDA(cudaMemcpyAsync(h->scal_host, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
   RR_CUDA(cudaStreamSynchronize(st));
   *rr_out = h->scal_host[0];
+  return RR_OK;
+}
+
+// Runs PCG iterations until convergence or the limit: one graph launch, or
+// (use_graphs = 0) batches of check_every iterations with a read-back each.
+rr_status run_iterations(rr_handle *h, int32_t limit) {
+  cudaStream_t st = h->st;
+  *h->limit_host = limit;
+  RR_CUDA(cudaMemcpyAsync(&h->S->limit, h->limit_host, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  if (h->opt.use_graphs) {
+    if (!h->loop_exec) RR_TRY(build_loop_graph(h));
+    const int32_t it0 = h->S_host->iter;
+    RR_CUDA(cudaGraphLaunch(h->loop_exec, st));
+    RR_CUDA(cudaMemcpyAsync(h->S_host, h->S, sizeof(rr::PcgScalars), cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaStreamSynchronize(st));
+    // every run of the loop body launches all of its kernels
+    rr_launch_counter += h->body_kernels * std::max<int64_t>(1, h->S_host->iter - it0);
+  } else {
+    const int32_t every = std::max(1, h->opt.check_every);
+    for (;;) {
+      for (int32_t c = 0; c < every; ++c) RR_TRY(pcg_iteration(h, st));
+      RR_CUDA(cudaMemcpyAsync(h->S_host, h->S, sizeof(rr::PcgScalars), cudaMemcpyDeviceToHost, st));
+      RR_CUDA(cudaStreamSynchronize(st));
+      if (h->S_host->converged || h->S_host->iter >= limit) break;
+    }
+  }
+  RR_CUDA(cudaMemcpyAsync(h->S_host, h->S, sizeof(rr::PcgScalars), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
   return RR_OK;
 }
 
@@ -422,67 +556,51 @@ rr_status solve_impl(rr_handle *h, const double *y, double *w, double tol, rr_in
   cudaStream_t st = h->st;
   const int64_t F = h->F;
   const bool twolevel = h->opt.solver == RR_SOLVER_TWOLEVEL;
-  const int32_t *stop = &h->S->converged;
   // b = X^T y; w = 0; r = b
   rr::CscEpilogue rhs{rr::CSC_RHS, 0.0, 0.0, nullptr, nullptr, nullptr, h->b, nullptr, nullptr};
-  RR_TRY(rr::csc_spmv(F, h->row_idx, y, h->plan, rhs, st));
-  RR_CUDA(cudaMemsetAsync(w, 0, sizeof(double) * F, st));
+  RR_TRY(rr::sliced_gather(h->pcsc, y, nullptr, nullptr, st));
+  RR_TRY(rr::sliced_epilogue(h->pcsc, rhs, st));
+  RR_CUDA(cudaMemsetAsync(h->w_int, 0, sizeof(double) * F, st));
   RR_TRY(rr::copy_f64(h->r, h->b, F, st));
   RR_TRY(rr::dot_parts(F, h->b, h->b, h->part_bb, st));
   RR_CUDA(cudaMemsetAsync(h->S, 0, sizeof(rr::PcgScalars), st));
   RR_TRY(rr::pcg_start(h->part_bb, rr::kVecGrid, h->part_bb, rr::kVecGrid, tol, 1, h->S, st));
   if (twolevel) RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st));
+  RR_CUDA(cudaMemcpyAsync(h->S_host, h->S, sizeof(rr::PcgScalars), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
 
   const int32_t max_iter = h->opt.max_iter;
-  const int32_t every = std::max(1, h->opt.check_every);
-  int32_t launched = 0, restarts = 0;
+  int32_t restarts = 0;
   double true_rr = 0.0;
   rr_status result = RR_OK;
   for (;;) {
-    const int32_t batch = std::min(every, max_iter - launched);
-    for (int32_t c = 0; c < batch; ++c) {
-      int n_rz = 0;
-      RR_TRY(apply_precond(h, h->r, h->z, stop, &n_rz, twolevel));
-      RR_TRY(rr::pcg_direction(F, h->part_rz, n_rz, h->z, h->p, h->S, st));
-      RR_TRY(rr::csr_spmv(h->N, h->row_ptr, h->col_idx, h->p, h->u, stop, st));
-      rr::CscEpilogue ap{rr::CSC_PCG, h->lambda, h->omega, h->p, nullptr, nullptr, h->q, h->part_pq, stop};
-      RR_TRY(rr::csc_spmv(F, h->row_idx, h->u, h->plan, ap, st));
-      RR_TRY(rr::pcg_update(F, h->part_rz, n_rz, h->part_pq, rr::csc_dot_parts(h->plan), h->p,
-                            h->q, w, h->r, h->omega, h->d, twolevel ? h->z1 : nullptr, h->part_rr,
-                            h->S, st));
-      RR_TRY(rr::pcg_finish(h->part_rz, n_rz, h->part_rr, rr::kVecGrid, h->S, h->history,
-                            h->hist_cap, st));
-    }
-    launched += batch;
-    RR_CUDA(cudaMemcpyAsync(h->S_host, h->S, sizeof(rr::PcgScalars), cudaMemcpyDeviceToHost, st));
-    RR_CUDA(cudaStreamSynchronize(st));
+    RR_TRY(run_iterations(h, max_iter));
     const rr::PcgScalars Sh = *h->S_host;
     if (Sh.nonfinite) {
       rr_set_error("rr_solve: non-finite residual or dot product");
       result = RR_NONFINITE;
       break;
     }
-    if (Sh.converged || launched >= max_iter) {
-      RR_TRY(true_residual(h, w, &true_rr));
-      if (!isfinite(true_rr)) {
-        rr_set_error("rr_solve: non-finite true residual");
-        result = RR_NONFINITE;
-        break;
-      }
-      if (sqrt(true_rr) <= Sh.target) break;
-      if (launched >= max_iter || restarts >= h->opt.max_restarts) {
-        rr_set_error("rr_solve: not converged after %d iterations (%d restarts)", Sh.iter, restarts);
-        result = RR_NOT_CONVERGED;
-        break;
-      }
-      // refinement: continue from w with the true residual and a fresh direction
-      ++restarts;
-      RR_TRY(rr::copy_f64(h->r, h->rt, F, st));
-      RR_TRY(rr::dot_parts(F, h->r, h->r, h->part_rr, st));
-      RR_TRY(rr::pcg_start(h->part_bb, 1, h->part_rr, rr::kVecGrid, tol, 0, h->S, st));
-      if (twolevel) RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st));
+    RR_TRY(true_residual(h, h->w_int, &true_rr));
+    if (!isfinite(true_rr)) {
+      rr_set_error("rr_solve: non-finite true residual");
+      result = RR_NONFINITE;
+      break;
     }
+    if (sqrt(true_rr) <= Sh.target) break;
+    if (Sh.iter >= max_iter || restarts >= h->opt.max_restarts) {
+      rr_set_error("rr_solve: not converged after %d iterations (%d restarts)", Sh.iter, restarts);
+      result = RR_NOT_CONVERGED;
+      break;
+    }
+    // refinement: continue from w with the true residual and a fresh direction
+    ++restarts;
+    RR_TRY(rr::copy_f64(h->r, h->rt, F, st));
+    RR_TRY(rr::dot_parts(F, h->r, h->r, h->part_rr, st));
+    RR_TRY(rr::pcg_start(h->part_bb, 1, h->part_rr, rr::kVecGrid, tol, 0, h->S, st));
+    if (twolevel) RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st));
   }
+  RR_TRY(rr::copy_f64(w, h->w_int, F, st));
   RR_CUDA(cudaMemcpyAsync(h->S_host, h->S, sizeof(rr::PcgScalars), cudaMemcpyDeviceToHost, st));
   RR_CUDA(cudaStreamSynchronize(st));
   if (info) {
@@ -510,6 +628,8 @@ void rr_default_options(rr_options *o) {
   o->precision = RR_PREC_FP64;
   o->check_every = 8;
   o->max_restarts = 5;
+  o->use_graphs = 1;
+  o->gram = RR_GRAM_AUTO;
   o->stream = nullptr;
 }
 
@@ -579,6 +699,7 @@ rr_status rr_set_lambda(rr_handle *h, double lambda) {
     rr_set_error("rr_set_lambda: lambda must be positive and finite");
     return RR_INVALID_ARG;
   }
+  destroy_graph(h);   // the captured kernels hold lambda and omega by value
   RR_TRY(build_lambda(h, lambda));
   RR_CUDA(cudaStreamSynchronize(h->st));
   return RR_OK;
@@ -603,35 +724,37 @@ rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info
     info->setup_ms = h->setup_ms;
     info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     info->launches = rr_launch_counter - l0;
+    info->gram_tensor_cores = h->gram_on_tensor_cores ? 1 : 0;
   }
   return s;
 }
 
 rr_status rr_apply(rr_handle *h, const double *v, double *out) {
   if (!h || !v || !out || v == out) return RR_INVALID_ARG;
-  RR_TRY(rr::csr_spmv(h->N, h->row_ptr, h->col_idx, v, h->u, nullptr, h->st));
   rr::CscEpilogue ep{rr::CSC_APPLY, h->lambda, h->omega, v, nullptr, nullptr, out, nullptr, nullptr};
-  RR_TRY(rr::csc_spmv(h->F, h->row_idx, h->u, h->plan, ep, h->st));
+  RR_TRY(op_apply(h, v, ep, nullptr, h->st));
   return RR_OK;
 }
 
 rr_status rr_precondition(rr_handle *h, const double *r, double *z) {
   if (!h || !r || !z || r == z) return RR_INVALID_ARG;
   int n = 0;
-  RR_TRY(apply_precond(h, r, z, nullptr, &n, false));
+  RR_TRY(apply_precond(h, r, z, nullptr, &n, false, h->st));
   return RR_OK;
 }
 
 rr_status rr_rhs(rr_handle *h, const double *y, double *b) {
   if (!h || !y || !b) return RR_INVALID_ARG;
   rr::CscEpilogue ep{rr::CSC_RHS, 0.0, 0.0, nullptr, nullptr, nullptr, b, nullptr, nullptr};
-  RR_TRY(rr::csc_spmv(h->F, h->row_idx, y, h->plan, ep, h->st));
+  RR_TRY(rr::sliced_gather(h->pcsc, y, nullptr, nullptr, h->st));
+  RR_TRY(rr::sliced_epilogue(h->pcsc, ep, h->st));
   return RR_OK;
 }
 
 rr_status rr_matvec(rr_handle *h, const double *v, double *u) {
   if (!h || !v || !u) return RR_INVALID_ARG;
-  RR_TRY(rr::csr_spmv(h->N, h->row_ptr, h->col_idx, v, u, nullptr, h->st));
+  RR_TRY(rr::sliced_gather(h->pcsr, v, nullptr, nullptr, h->st));
+  RR_TRY(rr::sliced_slot_sum(h->pcsr, u, h->st));
   return RR_OK;
 }
 
@@ -679,7 +802,12 @@ rr_status rr_query(const rr_handle *h, int64_t *n_rows, int64_t *n_cols, int32_t
 void rr_free(rr_handle *h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
-  rr::csc_plan_free(h->plan);
+  destroy_graph(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->limit_host) cudaFreeHost(h->limit_host);
+  rr::restrict_free(h->rplan);
+  rr::sliced_free(h->pcsr);
+  rr::sliced_free(h->pcsc);
   h->mem.free_all();
   if (h->err_host) cudaFreeHost(h->err_host);
   if (h->S_host) cudaFreeHost(h->S_host);

@@ -20,6 +20,7 @@ RR_NOT_CONVERGED, RR_NONFINITE, RR_TIMEOUT, RR_UNSUPPORTED = 5, 6, 7, 8
 RR_CSR_BINARY, RR_DENSE_F32_ROWMAJOR = 0, 1
 RR_SOLVER_TWOLEVEL, RR_SOLVER_CG, RR_SOLVER_DCG = 0, 1, 2
 RR_PREC_FP64 = 0
+RR_GRAM_AUTO, RR_GRAM_CUDA_CORES = 0, 1
 
 _STATUS = {0: "RR_OK", 1: "RR_INVALID_ARG", 2: "RR_CUDA_ERROR", 3: "RR_OOM", 4: "RR_NOT_SPD",
            5: "RR_NOT_CONVERGED", 6: "RR_NONFINITE", 7: "RR_TIMEOUT", 8: "RR_UNSUPPORTED"}
@@ -37,6 +38,7 @@ class rr_options(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("init_centers", ctypes.c_void_p),
                 ("solver", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
+                ("use_graphs", ctypes.c_int32), ("gram", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -45,7 +47,8 @@ class rr_info(ctypes.Structure):
                 ("k_eff", ctypes.c_int32), ("kmeans_iters", ctypes.c_int32),
                 ("rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double),
                 ("omega", ctypes.c_double), ("setup_ms", ctypes.c_double),
-                ("solve_ms", ctypes.c_double), ("launches", ctypes.c_int64)]
+                ("solve_ms", ctypes.c_double), ("launches", ctypes.c_int64),
+                ("gram_tensor_cores", ctypes.c_int32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -156,7 +159,7 @@ class Handle:
 
 def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=None,
              kmeans_max_iter=50, max_iter=20000, solver=RR_SOLVER_TWOLEVEL, check_every=8,
-             max_restarts=5, stream=None) -> Handle:
+             max_restarts=5, use_graphs=1, gram=RR_GRAM_AUTO, stream=None) -> Handle:
     """rr_setup on a binary CSR pattern given as numpy arrays (host) or torch
     CUDA tensors (device): row_ptr int64[N+1], col_idx int32[nnz]."""
     lib = load()
@@ -171,7 +174,8 @@ def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=N
         ic = np.ascontiguousarray(init_centers, dtype=np.int32)
     o = rr_default_options(kmeans_max_iter=kmeans_max_iter, max_iter=max_iter, seed=seed,
                            init_centers=_ptr(ic), solver=solver, check_every=check_every,
-                           max_restarts=max_restarts, stream=_stream_ptr(stream))
+                           max_restarts=max_restarts, use_graphs=use_graphs, gram=gram,
+                           stream=_stream_ptr(stream))
     out = _P()
     _check(lib.rr_setup(ctypes.byref(X), float(lam), int(k), ctypes.byref(o), ctypes.byref(out)))
     return Handle(out, n_cols, n_rows, (ic,))

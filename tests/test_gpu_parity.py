@@ -42,17 +42,38 @@ def csr_of(D):
 
 
 CASES = {
-    # name: (N, F, density, k, lambda, seed) — small, ragged, several tiles
-    "zipf_2000x1000": (2000, 1000, 0.01, 50, 1e-2, 0),
-    "ragged_3001x1777": (3001, 1777, 0.006, 37, 1e-3, 5),
-    "tall_9000x2500": (9000, 2500, 0.004, 129, 0.1, 7),
+    # name: (N, F, density, k, lambda, seed, dense rows) — small, ragged, several
+    # shared-memory slices in both directions with multi-piece rows and columns
+    "zipf_2000x1000": (2000, 1000, 0.01, 50, 1e-2, 0, 0),
+    "ragged_3001x1777": (3001, 1777, 0.006, 37, 1e-3, 5, 0),
+    "tall_9000x2500": (9000, 2500, 0.004, 129, 0.1, 7, 0),
+    "multislice_70001x60013": (70001, 60013, 0.0004, 200, 1e-2, 11, 3),
 }
+
+
+def with_dense_rows(X, n_dense, seed, width=2400):
+    """X with n_dense rows replaced by rows of `width` random features, far
+    longer than one piece in every slice."""
+    rng = np.random.default_rng(seed)
+    rows = set(rng.choice(X.n_rows, size=n_dense, replace=False).tolist())
+    parts = []
+    for r in range(X.n_rows):
+        if r in rows:
+            parts.append(np.sort(rng.choice(X.n_cols, size=width, replace=False)).astype(np.int32))
+        else:
+            parts.append(X.col_idx[X.row_ptr[r]:X.row_ptr[r + 1]])
+    lens = np.array([len(q) for q in parts], np.int64)
+    rp = np.zeros(X.n_rows + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    return synth.CSR(X.n_rows, X.n_cols, rp, np.concatenate(parts).astype(np.int32))
 
 
 @pytest.fixture(scope="module", params=list(CASES))
 def case(request, rr):
-    N, F, dens, k, lam, seed = CASES[request.param]
+    N, F, dens, k, lam, seed, n_dense = CASES[request.param]
     X = synth.zipf_binary(N, F, dens, 1.1, seed)
+    if n_dense:
+        X = with_dense_rows(X, n_dense, seed)
     y, _ = synth.ridge_targets(X, seed)
     ref = twolevel.setup_binary(N, F, X.row_ptr, X.col_idx, lam, k, seed=seed)
     h = rr.rr_setup(X.row_ptr, X.col_idx, N, F, lam, k, seed=seed)
@@ -76,6 +97,28 @@ def test_coarse_gram_exact_and_operator(case, rr):
     # same IEEE operations in the same order on both sides: identical bits
     assert np.array_equal(Ac, case["ref"].Ac)
     assert rr.rr_query(case["h"])["omega"] == case["ref"].omega
+
+
+def test_gram_tensor_cores_equals_cuda_cores(case, rr):
+    """The tcgen05 Gram (FP16 counts, exact FP32 chunks, FP64 sums) equals the
+    CUDA-core integer Gram and the oracle bit for bit. It is taken whenever every
+    count is exact in FP16 (<= 2048); the case with 2400-feature rows has larger
+    counts and must fall back to the CUDA-core Gram."""
+    X = case["X"]
+    w = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
+    info = rr.rr_solve(case["h"], dev(case["y"]), w, tol=1e-8)
+    C = np.zeros((X.n_rows, case["ref"].k_eff), np.int64)
+    rows = np.repeat(np.arange(X.n_rows), np.diff(X.row_ptr))
+    np.add.at(C, (rows, case["ref"].labels[X.col_idx]), 1)
+    assert info["gram_tensor_cores"] == (1 if C.max() <= 2048 else 0)
+    h2 = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, case["lam"], case["k"],
+                     seed=case["seed"], gram=rr.RR_GRAM_CUDA_CORES)
+    info2 = rr.rr_solve(h2, dev(case["y"]), w, tol=1e-8)
+    assert info2["gram_tensor_cores"] == 0
+    _, G1 = rr.rr_get_coarse(case["h"])
+    _, G2 = rr.rr_get_coarse(h2)
+    assert np.array_equal(G1, G2)
+    assert np.array_equal(G1, case["ref"].G)
 
 
 def test_operator_and_rhs(case, rr):
@@ -172,6 +215,20 @@ def test_repeatable_bits(case, rr):
     assert torch.equal(w1, w2)
 
 
+def test_graph_loop_equals_host_loop(case, rr):
+    """The device-side while-loop graph and host-driven batches run the same
+    kernels in the same order: identical bits and iteration counts."""
+    X = case["X"]
+    h2 = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, case["lam"], case["k"],
+                     seed=case["seed"], use_graphs=0, check_every=5)
+    w1 = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
+    w2 = torch.empty_like(w1)
+    i1 = rr.rr_solve(case["h"], dev(case["y"]), w1, tol=1e-8)
+    i2 = rr.rr_solve(h2, dev(case["y"]), w2, tol=1e-8)
+    assert i1["iters"] == i2["iters"] and i1["restarts"] == i2["restarts"]
+    assert torch.equal(w1, w2)
+
+
 # ---------------------------------------------------------------- edge cases
 
 def _setup_dense01(rr, D, lam, k, **kw):
@@ -232,7 +289,7 @@ def test_invalid_inputs_rejected_on_host(rr):
         rr.rr_setup(rp, ci, 2, 3, 1.0, 1)
     with pytest.raises(rr.RRError):
         rr.rr_setup(np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32), 2, 3, 1.0, 1,
-                    init_centers=[1])
+                    init_centers=[5])       # centre out of range
     ok = rr.rr_setup(np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32), 2, 3, 1.0, 1)
     w = torch.empty(3, dtype=torch.float64, device="cuda")
     with pytest.raises(rr.RRError):
