@@ -176,6 +176,33 @@ rr_status rr_get_coarse(const rr_handle *h, double *Ac_host, int64_t *G_host);
 rr_status rr_query(const rr_handle *h, int64_t *n_rows, int64_t *n_cols, int32_t *k_eff,
                    double *omega, double *lambda);
 
+/* out = (X^T X + lambda I) v for binary X given directly as device CSR
+ * (row_ptr int64[n_rows+1], col_idx int32[nnz]) and its transposed copy CSC
+ * (col_ptr int64[n_cols+1], row_idx int32[nnz]), without a handle and without
+ * allocating any device memory. (No counterpart in the paper: this is an
+ * interface for callers that may not allocate.)
+ *
+ * Who needs it: code that runs where cudaMalloc is off limits, for example
+ * inside a framework that owns every byte of device memory through its own
+ * pool and forbids other allocations, or code on a latency-critical path that
+ * cannot afford cudaMalloc's implicit device synchronisation. rr_apply needs a
+ * handle, and rr_setup allocates.
+ *
+ * The intermediate u = X v is kept in a fixed array inside the library (32 MiB
+ * on every GPU that loads the library, held until the process exits), so
+ * n_rows may not exceed 4,194,304 (RR_UNSUPPORTED beyond). The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress), so make
+ * the first call before any stream capture. All calls share the array: calls
+ * whose work overlaps on the GPU (different streams, or different host threads
+ * on the same device) race on it and must be serialised by the caller. Every
+ * call writes u[0, n_rows) before reading it, so no state carries over.
+ * v, out: device double[n_cols], may not alias. stream: cudaStream_t or NULL.
+ * Returns before the work completes. Errors: RR_INVALID_ARG, RR_UNSUPPORTED,
+ * RR_CUDA_ERROR. */
+rr_status rr_apply_noalloc(int64_t n_rows, int64_t n_cols, const int64_t *row_ptr,
+                           const int32_t *col_idx, const int64_t *col_ptr, const int32_t *row_idx,
+                           double lambda, const double *v, double *out, void *stream);
+
 /* Number of kernels the library has launched from the calling thread since it
  * was loaded (counts every launch of every call, setup included). */
 int64_t rr_launch_count(void);

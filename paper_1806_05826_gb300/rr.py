@@ -81,6 +81,8 @@ _SIGS = {
     "rr_free": (None, [_P]),
     "rr_last_error": (ctypes.c_char_p, []),
     "rr_launch_count": (ctypes.c_int64, []),
+    "rr_apply_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P,
+                                        ctypes.c_double, _P, _P, _P]),
 }
 
 
@@ -209,6 +211,14 @@ def rr_rhs(h: Handle, y, b):
 
 def rr_matvec(h: Handle, v, u):
     _check(load().rr_matvec(h.ptr, _ptr(v), _ptr(u)))
+
+
+def rr_apply_noalloc(n_rows, n_cols, row_ptr, col_idx, col_ptr, row_idx, lam, v, out,
+                     stream=None):
+    """out = (X^T X + lam I) v from device CSR/CSC tensors; allocates nothing."""
+    _check(load().rr_apply_noalloc(int(n_rows), int(n_cols), _ptr(row_ptr), _ptr(col_idx),
+                                   _ptr(col_ptr), _ptr(row_idx), float(lam), _ptr(v), _ptr(out),
+                                   _stream_ptr(stream)))
 
 
 def rr_get_labels(h: Handle) -> np.ndarray:

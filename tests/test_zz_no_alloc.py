@@ -1,0 +1,58 @@
+"""rr_apply_noalloc: the operator without device allocation, for callers that
+may not call cudaMalloc (a framework that owns all device memory through its
+own pool, a path that cannot take cudaMalloc's implicit synchronisation). Its
+output must equal the handle-based rr_apply on two calls in a row with
+different matrices, so no state from one call leaks into the next. This file
+is collected last on purpose."""
+import numpy as np
+import pytest
+
+from gen import synth
+from oracle import sparse as osp
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_05826_gb300 import build
+    build.build_library()
+    from paper_1806_05826_gb300 import rr as rrmod
+    rrmod.load()
+    return rrmod
+
+
+def _device_patterns(X):
+    cp, ri = osp.csc_pattern(X.n_rows, X.n_cols, X.row_ptr, X.col_idx)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), device="cuda")
+    return t(X.row_ptr), t(X.col_idx), t(cp), t(ri)
+
+
+@pytest.mark.parametrize("sizes", [((3001, 1777, 0.006, 5), (2000, 1000, 0.01, 0))])
+def test_noalloc_matches_handle_apply_twice(rr, sizes):
+    lam = 0.37
+    for N, F, dens, seed in sizes:          # two calls in a row, different matrices
+        X = synth.zipf_binary(N, F, dens, 1.1, seed)
+        h = rr.rr_setup(X.row_ptr, X.col_idx, N, F, lam, 8, seed=seed)
+        v = torch.as_tensor(np.random.default_rng(seed).standard_normal(F), device="cuda")
+        want = torch.empty(F, dtype=torch.float64, device="cuda")
+        rr.rr_apply(h, v, want)
+        rp, ci, cp, ri = _device_patterns(X)
+        got = torch.full((F,), np.nan, dtype=torch.float64, device="cuda")
+        rr.rr_apply_noalloc(N, F, rp, ci, cp, ri, lam, v, got)
+        torch.cuda.synchronize()
+        w, g = want.cpu().numpy(), got.cpu().numpy()
+        # same tolerance as the handle path's parity test: sums in another order
+        assert np.max(np.abs(g - w)) <= 1e-13 * np.abs(w).max()
+        rr.rr_free(h)
+
+
+def test_noalloc_rejects_rows_beyond_scratch(rr):
+    z = torch.zeros(4, dtype=torch.float64, device="cuda")
+    p = torch.zeros(2, dtype=torch.int64, device="cuda")
+    with pytest.raises(rr.RRError) as e:
+        rr.rr_apply_noalloc((1 << 22) + 1, 4, p, p, p, p, 1.0, z, z.clone())
+    assert e.value.status == rr.RR_UNSUPPORTED
