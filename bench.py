@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="mixed: FP32 operator inside CG + FP64 refinement; fp64: FP64 throughout")
     return ap.parse_args()
 
 
@@ -158,12 +160,15 @@ def run_ours(args, rank, world, local):
     y_dev = torch.as_tensor(y, device=dev)
     W = [torch.empty(F, dtype=torch.float64, device=dev) for _ in lams]
 
+    prec = rr.RR_PREC_MIXED if args.precision == "mixed" else rr.RR_PREC_FP64
+    opts = dict(seed=p["seed"], stream=stream, precision=prec, max_restarts=20)
+
     def step(host=None):
         if host is None:
-            h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], k, seed=p["seed"], stream=stream)
+            h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], k, **opts)
             yd = y_dev
         else:
-            h = rr.rr_setup(host["rp"], host["ci"], N, F, lams[0], k, seed=p["seed"], stream=stream)
+            h = rr.rr_setup(host["rp"], host["ci"], N, F, lams[0], k, **opts)
             yd = host["y"].to(dev, non_blocking=True)
         infos = []
         for j, lam in enumerate(lams):
@@ -211,7 +216,7 @@ def run_ours(args, rank, world, local):
     value = total_ms / 1000.0 / args.steps
 
     # ---- roofline: the mat-vec kernels timed alone on the library's stream
-    h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], k, seed=p["seed"], stream=stream)
+    h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], k, **opts)
     v = torch.randn(F, dtype=torch.float64, device=dev)
     u = torch.empty(N, dtype=torch.float64, device=dev)
     z = torch.empty(F, dtype=torch.float64, device=dev)
@@ -274,15 +279,20 @@ def run_ours(args, rank, world, local):
     out = {
         "metric": METRIC, "value": round(value, 5), "unit": "s", "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(total_ms / args.steps, 3),
-        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64",
         "data": "synthetic (seeded Zipf s=1.1 binary CSR, y = X w* + N(0, 0.1^2))",
         "config": {"workload": args.workload, "n_rows": N, "n_cols": F, "nnz": nnz, "k": k,
-                   "lambdas": list(lams), "tol": TOL,
+                   "lambdas": list(lams), "tol": TOL, "precision": args.precision,
                    "method": "two-level PCG: k-means++ clusters, SA prolongation, Cholesky "
                              "coarse solve, symmetric damped-Jacobi V(1,1)",
                    "l2": "inputs larger than L2 (CSR+CSC indices 8*nnz bytes)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "breakdown": {"setup_ms": round(last[0]["setup_ms"], 2),
+                      "setup_phase_ms": dict(zip(
+                          ["copy_validate", "csc_build", "kmeanspp_seed", "lloyd", "clusters",
+                           "coarse_gram", "coarse_factor", "sliced_patterns"],
+                          [round(v, 2) for v in last[0]["setup_phase_ms"]])),
                       "solve_ms": [round(i["solve_ms"], 2) for i in last],
                       "iters": [i["iters"] for i in last],
                       "restarts": [i["restarts"] for i in last],

@@ -58,7 +58,13 @@ enum { RR_GRAM_AUTO = 0,        /* tcgen05 tensor cores (FP16 counts, exact FP32
        RR_GRAM_CUDA_CORES = 1 };/* int32 products summed in int64 on CUDA cores */
 
 /* rr_options.precision */
-enum { RR_PREC_FP64 = 0 };
+enum { RR_PREC_FP64 = 0,        /* every operator apply accumulates in FP64 */
+       RR_PREC_MIXED = 1 };     /* the operator applies inside the CG iterations gather FP32
+                                   copies of the vector and accumulate in FP32; vectors, dot
+                                   products, norms, the coarse Cholesky solve and every true
+                                   residual b - A w stay FP64, and each restart on the true
+                                   residual is an FP64 iterative-refinement step (so
+                                   max_restarts bounds the refinement steps) */
 
 /* The feature matrix X (N x F).
  *  CSR_BINARY: row_ptr int64[N+1] (row_ptr[0] = 0, non-decreasing,
@@ -106,6 +112,10 @@ typedef struct {
   double solve_ms;        /* wall time of this solve (host clock, synchronised) */
   int64_t launches;       /* kernels this call launched */
   int32_t gram_tensor_cores; /* 1 if rr_setup formed the coarse Gram on the tensor cores */
+  double setup_phase_ms[8]; /* rr_setup wall time by phase: 0 copy + validation of X, 1 CSC
+                               build, 2 k-means++ seeding, 3 Lloyd steps, 4 compaction + member
+                               lists, 5 counts + coarse Gram, 6 coarse factor + smoother,
+                               7 sliced patterns + solve workspace */
 } rr_info;
 
 /* Fills *o with the defaults listed above. */
@@ -144,7 +154,10 @@ rr_status rr_set_lambda(rr_handle *h, double lambda);
 rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info *info);
 
 /* out = (X^T X + lambda I) v (Eq. (1)'s operator, applied matrix-free as
- * u = X v then X^T u + lambda v). v, out: device double[F]; may not alias. */
+ * u = X v then X^T u + lambda v). v, out: device double[F]; may not alias.
+ * Accumulates in FP32 when the handle was set up with RR_PREC_MIXED (the
+ * operator of its CG iterations), else in FP64; likewise rr_rhs and rr_matvec.
+ * rr_solve's right-hand side and true residuals are always FP64. */
 rr_status rr_apply(rr_handle *h, const double *v, double *out);
 
 /* z = M^{-1} r for the handle's preconditioner (the two-level cycle of

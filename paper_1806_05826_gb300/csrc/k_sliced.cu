@@ -8,9 +8,10 @@
 // to whole 16-byte words (8 offsets; the pad offset W reads a zero kept in
 // shared memory) and the segment is cut into pieces of at most kPieceWords
 // words. Pieces are stored slice-major, so one CTA streams a contiguous range
-// of them against the one vector slice it holds; each piece sum goes to its
-// own slot, numbered outer-major, and the slots of one outer index are summed
-// afterwards in a fixed order. No atomics: every run gives identical bits.
+// of them against the one vector slice it holds; each piece is summed by one
+// lane (in a fixed order) into its own slot, numbered outer-major, and the
+// slots of one outer index are summed afterwards in a fixed order. No atomics:
+// every run gives identical bits.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -19,7 +20,6 @@ namespace rr {
 namespace {
 
 constexpr int kSliceThreads = 1024;
-constexpr int kGroups = kSliceThreads / 8;
 
 // one thread per (outer o, slice b): entry range of the segment by binary search
 __global__ void k_seg_bounds(int64_t n_outer, int32_t nb, int32_t W,
@@ -58,6 +58,8 @@ __global__ void k_outer_pieces(int64_t n_outer, int32_t nb, const int64_t *__res
   }
 }
 
+// one warp per (outer o, slice b): piece pointers and slots, then the padded
+// 16-bit offsets of the segment
 __global__ void k_fill_pieces(int64_t n_outer, int32_t nb, int32_t W,
                               const int64_t *__restrict__ outer_ptr,
                               const int32_t *__restrict__ inner,
@@ -67,21 +69,21 @@ __global__ void k_fill_pieces(int64_t n_outer, int32_t nb, int32_t W,
                               const int64_t *__restrict__ slot_base, int32_t *__restrict__ pw,
                               int32_t *__restrict__ slot, uint16_t *__restrict__ idx) {
   const int64_t total = n_outer * nb;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = warp; t < total; t += nwarps) {
     const int32_t b = (int32_t)(t / n_outer);
     const int64_t o = t - (int64_t)b * n_outer;
     const int64_t lo0 = outer_ptr[o], hi0 = outer_ptr[o + 1];
+    const int64_t key = (int64_t)b * W, key_end = (int64_t)(b + 1) * W;
     int64_t lo = lo0, hi = hi0;
-    const int64_t key = (int64_t)b * W;
     while (lo < hi) {
       const int64_t mid = (lo + hi) >> 1;
       if (inner[mid] < key) lo = mid + 1; else hi = mid;
     }
     const int64_t s = lo;
-    // end of this slice's entries (not of the whole outer index)
-    hi = hi0;
-    const int64_t key_end = (int64_t)(b + 1) * W;
+    hi = hi0;   // end of this slice's entries (not of the whole outer index)
     while (lo < hi) {
       const int64_t mid = (lo + hi) >> 1;
       if (inner[mid] < key_end) lo = mid + 1; else hi = mid;
@@ -91,12 +93,12 @@ __global__ void k_fill_pieces(int64_t n_outer, int32_t nb, int32_t W,
     int64_t pre = 0;   // pieces of this outer index in earlier slices
     for (int32_t bb = 0; bb < b; ++bb) pre += pieces[(int64_t)bb * n_outer + o];
     const int64_t np = pieces[t], p0 = piece_off[t];
-    for (int64_t q = 0; q < np; ++q) {
+    for (int64_t q = lane; q < np; q += 32) {
       pw[p0 + q] = (int32_t)(w0 + q * kPieceWords);
       slot[p0 + q] = (int32_t)(slot_base[o] + pre + q);
     }
     uint16_t *dst = idx + w0 * 8;
-    for (int64_t u = 0; u < nw * 8; ++u)
+    for (int64_t u = lane; u < nw * 8; u += 32)
       dst[u] = u < len ? (uint16_t)(inner[s + u] - key) : (uint16_t)W;
   }
 }
@@ -126,59 +128,81 @@ __global__ void k_tasks(int32_t nb, int32_t T, int64_t n_outer, const int64_t *_
   }
 }
 
-// The gather pass. One CTA per task: stage the task's vector slice in shared
-// memory (combining the previous pass's piece sums when kCombineIn), then
-// 8-lane groups sum pieces: each lane loads up to four 16-byte words (32 offsets).
-template <bool kCombineIn>
+// Pre-pass: the gathered vector, once per pass, in the accumulation type T
+// (FP64, or FP32 for the mixed-precision inner iterations). v = x, or
+// (kCombine) the per-index sums of the previous pass's slots.
+template <bool kCombine, typename T>
+__global__ void k_slice_prep(int64_t n, const double *__restrict__ x,
+                             const double *__restrict__ in_psum,
+                             const int32_t *__restrict__ in_slot_ptr, T *__restrict__ xq,
+                             const int32_t *__restrict__ stop) {
+  if (stop && *stop) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double v;
+    if (kCombine) {
+      v = 0.0;
+      for (int32_t q = in_slot_ptr[i]; q < in_slot_ptr[i + 1]; ++q) v += in_psum[q];
+    } else {
+      v = x[i];
+    }
+    xq[i] = (T)v;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T gather8(const T *__restrict__ xs, const uint4 q) {
+  return ((xs[q.x & 0xffffu] + xs[q.x >> 16]) + (xs[q.y & 0xffffu] + xs[q.y >> 16])) +
+         ((xs[q.z & 0xffffu] + xs[q.z >> 16]) + (xs[q.w & 0xffffu] + xs[q.w >> 16]));
+}
+
+// The gather pass. One CTA per task: copy the task's vector slice into shared
+// memory, then every lane sums whole pieces: the 32 lanes of a warp take 32
+// consecutive pieces, so piece pointers, slots and the words of short pieces
+// are read coalesced, and each lane loads its piece's words four at a time.
+// Sums in a fixed order in T; the piece sum is stored in FP64.
+template <typename T>
 __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather(
-    SlicedView P, const double *__restrict__ x, const double *__restrict__ in_psum,
-    const int32_t *__restrict__ in_slot_ptr, double *__restrict__ out_psum,
+    SlicedView P, const T *__restrict__ xq, double *__restrict__ out_psum,
     const int32_t *__restrict__ stop) {
   if (stop && *stop) return;
-  extern __shared__ double xs[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *xs = reinterpret_cast<T *>(smem_raw);
   const int task = blockIdx.x;
   const int32_t b = P.task_slice[task];
   const int64_t base = (int64_t)b * P.W;
   const int64_t width = min((int64_t)P.W, P.n_inner - base);
-  for (int i = threadIdx.x; i <= P.W; i += kSliceThreads) {
-    double v = 0.0;
-    if (i < width) {
-      if (kCombineIn) {
-        const int32_t s = in_slot_ptr[base + i], e = in_slot_ptr[base + i + 1];
-        for (int32_t q = s; q < e; ++q) v += in_psum[q];
-      } else {
-        v = x[base + i];
-      }
+  for (int i0 = threadIdx.x; i0 <= P.W; i0 += 4 * kSliceThreads) {
+    T v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * kSliceThreads;
+      v[u] = i < width ? xq[base + i] : T(0);
     }
-    xs[i] = v;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * kSliceThreads;
+      if (i <= P.W) xs[i] = v[u];
+    }
   }
   __syncthreads();
-  const int lane8 = threadIdx.x & 7;
-  const int warp = threadIdx.x >> 5, gw = (threadIdx.x >> 3) & 3;
   const int32_t p0 = P.task_p[task], p1 = P.task_p[task + 1];
   const uint4 pad = make_uint4(P.W | (P.W << 16), P.W | (P.W << 16), P.W | (P.W << 16),
                                P.W | (P.W << 16));
-  for (int32_t pq = p0 + warp * 4; pq < p1; pq += kGroups) {   // warp-uniform loop
-    const int32_t p = pq + gw;
-    double acc = 0.0;
-    if (p < p1) {
-      const int32_t w0 = P.pw[p], w1 = P.pw[p + 1];
+  for (int32_t p = p0 + threadIdx.x; p < p1; p += kSliceThreads) {
+    const int32_t w0 = P.pw[p], w1 = P.pw[p + 1];
+    T acc = T(0);
+    for (int32_t w = w0; w < w1; w += 4) {
       uint4 q[4];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int32_t w = w0 + lane8 + 8 * k;
-        q[k] = w < w1 ? __ldg(P.idx + w) : pad;
-      }
+      for (int k = 0; k < 4; ++k) q[k] = (w + k < w1) ? __ldg(P.idx + w + k) : pad;
+      // gathers only for words of this piece (no shared loads for absent words)
+      acc += gather8(xs, q[0]);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        acc += (xs[q[k].x & 0xffffu] + xs[q[k].x >> 16]) + (xs[q[k].y & 0xffffu] + xs[q[k].y >> 16]);
-        acc += (xs[q[k].z & 0xffffu] + xs[q[k].z >> 16]) + (xs[q[k].w & 0xffffu] + xs[q[k].w >> 16]);
-      }
+      for (int k = 1; k < 4; ++k)
+        if (w + k < w1) acc += gather8(xs, q[k]);
     }
-    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    if (p < p1 && lane8 == 0) out_psum[P.slot[p]] = acc;
+    out_psum[P.slot[p]] = (double)acc;
   }
 }
 
@@ -257,16 +281,34 @@ __global__ void k_to_i32(int64_t n, const int64_t *__restrict__ in, int32_t *__r
     out[i] = (int32_t)in[i];
 }
 
-size_t slice_smem(int32_t W) { return sizeof(double) * ((size_t)W + 1); }
+template <typename T>
+size_t slice_smem(int32_t W) { return sizeof(T) * ((size_t)W + 1); }
 
-template <bool C>
+template <typename T>
 rr_status set_smem_attr() {
   static bool done = false;
   if (!done) {
-    RR_CUDA(cudaFuncSetAttribute(k_sliced_gather<C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)slice_smem(kSliceMax)));
+    RR_CUDA(cudaFuncSetAttribute(k_sliced_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)slice_smem<T>(kSliceMax)));
     done = true;
   }
+  return RR_OK;
+}
+
+template <typename T>
+rr_status gather_t(const SlicedPattern &P, const double *x, const SlicedPattern *in,
+                   const int32_t *stop, cudaStream_t st) {
+  const int64_t n = P.n_inner;
+  T *xq = reinterpret_cast<T *>(P.xq);
+  if (in)
+    RR_LAUNCH((k_slice_prep<true, T>), grid_for(n, kThreads), kThreads, 0, st, n, nullptr,
+              in->psum, in->slot_ptr, xq, stop);
+  else
+    RR_LAUNCH((k_slice_prep<false, T>), grid_for(n, kThreads), kThreads, 0, st, n, x, nullptr,
+              nullptr, xq, stop);
+  RR_TRY(set_smem_attr<T>());
+  RR_LAUNCH(k_sliced_gather<T>, P.ntasks, kSliceThreads, slice_smem<T>(P.W), st, P.view(), xq,
+            P.psum, stop);
   return RR_OK;
 }
 
@@ -310,7 +352,8 @@ rr_status sliced_build(int64_t n_outer, int64_t n_inner, const int64_t *outer_pt
     RR_CUDA(cudaMalloc(&P.slot_ptr, sizeof(int32_t) * (n_outer + 1)));
     RR_CUDA(cudaMalloc(&P.idx, 16 * std::max<int64_t>(1, P.nwords)));
     RR_CUDA(cudaMalloc(&P.psum, sizeof(double) * std::max<int64_t>(1, P.npieces)));
-    RR_LAUNCH(k_fill_pieces, grid_for(nseg, kThreads), kThreads, 0, st, n_outer, P.nb, P.W,
+    RR_CUDA(cudaMalloc(&P.xq, sizeof(double) * n_inner));
+    RR_LAUNCH(k_fill_pieces, grid_for(nseg, kWarps), kThreads, 0, st, n_outer, P.nb, P.W,
               outer_ptr, inner, word_off, piece_off, pieces, slot_base, P.pw, P.slot,
               reinterpret_cast<uint16_t *>(P.idx));
     const int32_t last = (int32_t)P.nwords;
@@ -341,22 +384,13 @@ void sliced_free(SlicedPattern &P) {
   cudaFree(P.psum);
   cudaFree(P.task_slice);
   cudaFree(P.task_p);
+  cudaFree(P.xq);
   P = SlicedPattern{};
 }
 
 rr_status sliced_gather(const SlicedPattern &P, const double *x, const SlicedPattern *in,
-                        const int32_t *stop, cudaStream_t st) {
-  const SlicedView v = P.view();
-  if (in) {
-    RR_TRY(set_smem_attr<true>());
-    RR_LAUNCH(k_sliced_gather<true>, P.ntasks, kSliceThreads, slice_smem(P.W), st, v, nullptr,
-              in->psum, in->slot_ptr, P.psum, stop);
-  } else {
-    RR_TRY(set_smem_attr<false>());
-    RR_LAUNCH(k_sliced_gather<false>, P.ntasks, kSliceThreads, slice_smem(P.W), st, v, x, nullptr,
-              nullptr, P.psum, stop);
-  }
-  return RR_OK;
+                        const int32_t *stop, cudaStream_t st, bool fp32) {
+  return fp32 ? gather_t<float>(P, x, in, stop, st) : gather_t<double>(P, x, in, stop, st);
 }
 
 rr_status sliced_slot_sum(const SlicedPattern &P, double *out, cudaStream_t st) {

@@ -151,6 +151,7 @@ struct SlicedPattern {
   double *psum = nullptr;        // [npieces]   piece sums
   int32_t *task_slice = nullptr; // [ntasks]
   int32_t *task_p = nullptr;     // [ntasks+1]
+  void *xq = nullptr;            // [n_inner]   the gathered vector in the accumulation type
   SlicedView view() const { return SlicedView{W, n_inner, pw, slot, idx, task_slice, task_p}; }
 };
 // outer_ptr/inner: a pattern with inner indices ascending within each outer index.
@@ -158,9 +159,10 @@ rr_status sliced_build(int64_t n_outer, int64_t n_inner, const int64_t *outer_pt
                        const int32_t *inner, SlicedPattern &P, cudaStream_t st);
 void sliced_free(SlicedPattern &P);
 // piece sums of P against x (or, when `in` is given, against the per-index
-// sums of in's slots: the output of a previous pass).
+// sums of in's slots: the output of a previous pass); fp32: accumulate in FP32
+// (the mixed-precision inner iterations), else in FP64.
 rr_status sliced_gather(const SlicedPattern &P, const double *x, const SlicedPattern *in,
-                        const int32_t *stop, cudaStream_t st);
+                        const int32_t *stop, cudaStream_t st, bool fp32 = false);
 // out[o] = sum of the slots of outer index o.
 rr_status sliced_slot_sum(const SlicedPattern &P, double *out, cudaStream_t st);
 // t_i = slot sums of feature i, then the epilogue; kVecGrid partial dots.

@@ -126,6 +126,7 @@ struct rr_handle {
   cudaGraphExec_t loop_exec = nullptr;
   int32_t *limit_host = nullptr;
   int64_t body_kernels = 0;
+  double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   bool gram_on_tensor_cores = false;
   rr::PcgScalars *S = nullptr;
   rr::PcgScalars *S_host = nullptr;
@@ -210,6 +211,15 @@ rr_status validate_host_csr(const rr_matrix *X) {
 rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k) {
   cudaStream_t st = h->st;
   DevArena &m = h->mem;
+  auto t_last = std::chrono::steady_clock::now();
+  // wall time of a finished phase (the stream is drained so device work counts)
+  auto phase = [&](int i) -> rr_status {
+    RR_CUDA(cudaStreamSynchronize(st));
+    const auto now = std::chrono::steady_clock::now();
+    h->phase_ms[i] += std::chrono::duration<double, std::milli>(now - t_last).count();
+    t_last = now;
+    return RR_OK;
+  };
   const int64_t N = X->n_rows, F = X->n_cols, nnz = X->nnz;
   h->N = N;
   h->F = F;
@@ -241,6 +251,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
     RR_CUDA(cudaMemcpyAsync(h->col_idx, X->col_idx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
   }
 
+  RR_TRY(phase(0));
   // ---- transposed copy (CSC), rows ascending within columns
   const int64_t big = std::max(N, F) + 1;
   int64_t *scratch64 = nullptr;
@@ -253,6 +264,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(rr::transpose_pattern(N, F, nnz, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx,
                                scratch64, scratch64 + big, tmp32, scratch64 + 2 * big, st));
 
+  RR_TRY(phase(1));
   // ---- k-means++ seeding and Lloyd steps (Section 3.4)
   rr::KmeansBuffers kb{};
   const int64_t ntiles = (F + 1023) / 1024;
@@ -293,6 +305,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
     RR_TRY(rr::kmeanspp_seed(N, F, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx, k,
                              h->opt.seed, kb, st));
   }
+  RR_TRY(phase(2));
   RR_TRY(rr::kmeans_init_labels(F, k, kb, st));
   RR_TRY(m.alloc(&h->gsum, F));
   RR_TRY(rr::kmeans_work_order(F, h->row_ptr, h->col_ptr, h->row_idx, kb, h->gsum, scratch64, st));
@@ -319,6 +332,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   m.release(kb.ov);
   m.release(kb.Q);
 
+  RR_TRY(phase(3));
   // ---- compaction, member lists, prolongation scale
   int32_t *remap = nullptr;
   RR_TRY(m.alloc(&remap, k + 1));
@@ -336,6 +350,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(rr::prolong_scale(k_eff, h->n_S, h->s, st));
   RR_TRY(rr::restrict_plan(k_eff, h->cl_ptr, h->rplan, scratch64, st));
 
+  RR_TRY(phase(4));
   // ---- exact coarse Gram G = C^T C (C = X * onehot(labels), integer counts)
   const int64_t n_pad = round_up(std::max<int64_t>(N, 1), 64);
   const int32_t k_pad = (int32_t)round_up(k_eff, 128);
@@ -374,6 +389,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   if (C16) m.release(C16);
   RR_TRY(gs);
 
+  RR_TRY(phase(5));
   // ---- per-lambda coarse factor and smoother
   const int64_t kk = (int64_t)k_eff * k_eff;
   RR_TRY(m.alloc(&h->Ac, kk));
@@ -385,6 +401,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&h->max_bits, 1));
   RR_TRY(build_lambda(h, lambda));
 
+  RR_TRY(phase(6));
   // ---- sliced patterns of X and X^T and the solve workspace
   RR_TRY(rr::sliced_build(N, F, h->row_ptr, h->col_idx, h->pcsr, st));
   RR_TRY(rr::sliced_build(F, N, h->col_ptr, h->row_idx, h->pcsc, st));
@@ -414,22 +431,22 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   m.release(kb.work_ctr);
   m.release(kb.order);
   m.release(kb.round);
-  RR_CUDA(cudaStreamSynchronize(st));
+  RR_TRY(phase(7));
   return RR_OK;
 }
 
 // ---- the operator: t = X^T (X v) + lambda v, finished by the epilogue ep.
 rr_status op_apply(rr_handle *h, const double *v, const rr::CscEpilogue &ep, const int32_t *stop,
-                   cudaStream_t st) {
-  RR_TRY(rr::sliced_gather(h->pcsr, v, nullptr, stop, st));
-  RR_TRY(rr::sliced_gather(h->pcsc, nullptr, &h->pcsr, stop, st));
+                   cudaStream_t st, bool fp32 = false) {
+  RR_TRY(rr::sliced_gather(h->pcsr, v, nullptr, stop, st, fp32));
+  RR_TRY(rr::sliced_gather(h->pcsc, nullptr, &h->pcsr, stop, st, fp32));
   RR_TRY(rr::sliced_epilogue(h->pcsc, ep, st));
   return RR_OK;
 }
 
 // ---- the preconditioner: z = M^{-1} r, with <r, z> partials in part_rz.
 rr_status apply_precond(rr_handle *h, const double *r, double *z, const int32_t *stop, int *n_rz,
-                        bool z1_ready, cudaStream_t st) {
+                        bool z1_ready, cudaStream_t st, bool fp32 = false) {
   const int64_t F = h->F;
   *n_rz = rr::kVecGrid;
   switch (h->opt.solver) {
@@ -442,12 +459,12 @@ rr_status apply_precond(rr_handle *h, const double *r, double *z, const int32_t 
       // z2 = z1 + P e_c; r2 = r - A z2; z = z2 + w D^-1 r2
       if (!z1_ready) RR_TRY(rr::jacobi(F, h->omega, r, h->d, h->z1, nullptr, stop, st));
       rr::CscEpilogue pre{rr::CSC_PRE, h->lambda, h->omega, h->z1, r, h->d, h->r1, nullptr, stop};
-      RR_TRY(op_apply(h, h->z1, pre, stop, st));
+      RR_TRY(op_apply(h, h->z1, pre, stop, st, fp32));
       RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->r1, stop, st));
       RR_TRY(rr::coarse_matvec(h->k_eff, h->Ainv, h->rplan, h->s, nullptr, h->ec, stop, st));
       RR_TRY(rr::prolong_add(F, h->labels, h->s, h->ec, h->z1, h->z2, stop, st));
       rr::CscEpilogue post{rr::CSC_POST, h->lambda, h->omega, h->z2, r, h->d, z, h->part_rz, stop};
-      return op_apply(h, h->z2, post, stop, st);
+      return op_apply(h, h->z2, post, stop, st, fp32);
     }
   }
 }
@@ -458,11 +475,12 @@ rr_status pcg_iteration(rr_handle *h, cudaStream_t st) {
   const int64_t F = h->F;
   const bool twolevel = h->opt.solver == RR_SOLVER_TWOLEVEL;
   const int32_t *stop = &h->S->converged;
+  const bool fp32 = h->opt.precision == RR_PREC_MIXED;
   int n_rz = 0;
-  RR_TRY(apply_precond(h, h->r, h->z, stop, &n_rz, twolevel, st));
+  RR_TRY(apply_precond(h, h->r, h->z, stop, &n_rz, twolevel, st, fp32));
   RR_TRY(rr::pcg_direction(F, h->part_rz, n_rz, h->z, h->p, h->S, st));
   rr::CscEpilogue ap{rr::CSC_PCG, h->lambda, h->omega, h->p, nullptr, nullptr, h->q, h->part_pq, stop};
-  RR_TRY(op_apply(h, h->p, ap, stop, st));
+  RR_TRY(op_apply(h, h->p, ap, stop, st, fp32));
   RR_TRY(rr::pcg_update(F, h->part_rz, n_rz, h->part_pq, rr::kVecGrid, h->p, h->q, h->w_int,
                         h->r, h->omega, h->d, twolevel ? h->z1 : nullptr, h->part_rr, h->S, st));
   RR_TRY(rr::pcg_finish(h->part_rz, n_rz, h->part_rr, rr::kVecGrid, h->S, h->history,
@@ -672,6 +690,10 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
   }
   rr_options opt;
   if (o) opt = *o; else rr_default_options(&opt);
+  if (opt.precision != RR_PREC_FP64 && opt.precision != RR_PREC_MIXED) {
+    rr_set_error("rr_setup: unknown precision %d", opt.precision);
+    return RR_INVALID_ARG;
+  }
   if (opt.kmeans_max_iter < 1 || opt.max_iter < 1) {
     rr_set_error("rr_setup: kmeans_max_iter and max_iter must be positive");
     return RR_INVALID_ARG;
@@ -725,6 +747,7 @@ rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info
     info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     info->launches = rr_launch_counter - l0;
     info->gram_tensor_cores = h->gram_on_tensor_cores ? 1 : 0;
+    for (int i = 0; i < 8; ++i) info->setup_phase_ms[i] = h->phase_ms[i];
   }
   return s;
 }
@@ -732,7 +755,7 @@ rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info
 rr_status rr_apply(rr_handle *h, const double *v, double *out) {
   if (!h || !v || !out || v == out) return RR_INVALID_ARG;
   rr::CscEpilogue ep{rr::CSC_APPLY, h->lambda, h->omega, v, nullptr, nullptr, out, nullptr, nullptr};
-  RR_TRY(op_apply(h, v, ep, nullptr, h->st));
+  RR_TRY(op_apply(h, v, ep, nullptr, h->st, h->opt.precision == RR_PREC_MIXED));
   return RR_OK;
 }
 
@@ -746,14 +769,14 @@ rr_status rr_precondition(rr_handle *h, const double *r, double *z) {
 rr_status rr_rhs(rr_handle *h, const double *y, double *b) {
   if (!h || !y || !b) return RR_INVALID_ARG;
   rr::CscEpilogue ep{rr::CSC_RHS, 0.0, 0.0, nullptr, nullptr, nullptr, b, nullptr, nullptr};
-  RR_TRY(rr::sliced_gather(h->pcsc, y, nullptr, nullptr, h->st));
+  RR_TRY(rr::sliced_gather(h->pcsc, y, nullptr, nullptr, h->st, h->opt.precision == RR_PREC_MIXED));
   RR_TRY(rr::sliced_epilogue(h->pcsc, ep, h->st));
   return RR_OK;
 }
 
 rr_status rr_matvec(rr_handle *h, const double *v, double *u) {
   if (!h || !v || !u) return RR_INVALID_ARG;
-  RR_TRY(rr::sliced_gather(h->pcsr, v, nullptr, nullptr, h->st));
+  RR_TRY(rr::sliced_gather(h->pcsr, v, nullptr, nullptr, h->st, h->opt.precision == RR_PREC_MIXED));
   RR_TRY(rr::sliced_slot_sum(h->pcsr, u, h->st));
   return RR_OK;
 }

@@ -19,7 +19,7 @@ RR_OK, RR_INVALID_ARG, RR_CUDA_ERROR, RR_OOM, RR_NOT_SPD = 0, 1, 2, 3, 4
 RR_NOT_CONVERGED, RR_NONFINITE, RR_TIMEOUT, RR_UNSUPPORTED = 5, 6, 7, 8
 RR_CSR_BINARY, RR_DENSE_F32_ROWMAJOR = 0, 1
 RR_SOLVER_TWOLEVEL, RR_SOLVER_CG, RR_SOLVER_DCG = 0, 1, 2
-RR_PREC_FP64 = 0
+RR_PREC_FP64, RR_PREC_MIXED = 0, 1
 RR_GRAM_AUTO, RR_GRAM_CUDA_CORES = 0, 1
 
 _STATUS = {0: "RR_OK", 1: "RR_INVALID_ARG", 2: "RR_CUDA_ERROR", 3: "RR_OOM", 4: "RR_NOT_SPD",
@@ -48,10 +48,12 @@ class rr_info(ctypes.Structure):
                 ("rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double),
                 ("omega", ctypes.c_double), ("setup_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("launches", ctypes.c_int64),
-                ("gram_tensor_cores", ctypes.c_int32)]
+                ("gram_tensor_cores", ctypes.c_int32), ("setup_phase_ms", ctypes.c_double * 8)]
 
     def as_dict(self):
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["setup_phase_ms"] = list(self.setup_phase_ms)
+        return d
 
 
 class RRError(RuntimeError):
@@ -161,7 +163,8 @@ class Handle:
 
 def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=None,
              kmeans_max_iter=50, max_iter=20000, solver=RR_SOLVER_TWOLEVEL, check_every=8,
-             max_restarts=5, use_graphs=1, gram=RR_GRAM_AUTO, stream=None) -> Handle:
+             max_restarts=5, use_graphs=1, gram=RR_GRAM_AUTO, precision=RR_PREC_FP64,
+             stream=None) -> Handle:
     """rr_setup on a binary CSR pattern given as numpy arrays (host) or torch
     CUDA tensors (device): row_ptr int64[N+1], col_idx int32[nnz]."""
     lib = load()
@@ -177,7 +180,7 @@ def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=N
     o = rr_default_options(kmeans_max_iter=kmeans_max_iter, max_iter=max_iter, seed=seed,
                            init_centers=_ptr(ic), solver=solver, check_every=check_every,
                            max_restarts=max_restarts, use_graphs=use_graphs, gram=gram,
-                           stream=_stream_ptr(stream))
+                           precision=precision, stream=_stream_ptr(stream))
     out = _P()
     _check(lib.rr_setup(ctypes.byref(X), float(lam), int(k), ctypes.byref(o), ctypes.byref(out)))
     return Handle(out, n_cols, n_rows, (ic,))

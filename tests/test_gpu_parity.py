@@ -150,18 +150,65 @@ def test_preconditioner(case, rr):
 
 
 def test_two_level_solve_matches_oracle(case, rr):
+    """Same recurrences, same solution.
+    (1) Same recurrences: after 20 iterations of Jacobi-preconditioned CG (the
+        same CG loop, without the coarse solve) the GPU iterate equals the
+        oracle's to 1e-10; only the summation order differs. The coarse level
+        is compared directly by test_preconditioner: the GPU applies
+        A_c^-1 = L^-T L^-1 formed once, the oracle substitutes with L, and the
+        two agree only to ~cond(A_c) * eps, which PCG turns into different,
+        equally valid, intermediate iterates.
+    (2) The full two-level solves stop within 5% of each other's iteration
+        count with true residuals <= 1e-8 (recomputed by the oracle's operator).
+    (3) The solutions agree to 1e-6, or, on systems so ill-conditioned that two
+        residual-1e-8 solutions need not be that close, to the bound that the
+        residuals themselves give: ||w1 - w2|| <= (||r1|| + ||r2||) / lambda."""
     X, ref = case["X"], case["ref"]
     b = osp.rhs(ref.M, case["y"])
+    bn = np.linalg.norm(b)
+    h20 = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, case["lam"], case["k"],
+                      seed=case["seed"], max_iter=20, max_restarts=0, solver=rr.RR_SOLVER_DCG)
+    w20 = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
+    info20 = rr.rr_solve(h20, dev(case["y"]), w20, tol=1e-12)
+    same = krylov.pcg(ref.A, lambda r: r / ref.d, b, tol=1e-30, max_iter=info20["iters"],
+                      max_restarts=0)
+    assert same.iters == info20["iters"]
+    assert np.linalg.norm(w20.cpu().numpy() - same.w) / np.linalg.norm(same.w) <= 1e-10
+
     want = krylov.pcg(ref.A, ref.apply, b, tol=1e-8)
     w = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
     info = rr.rr_solve(case["h"], dev(case["y"]), w, tol=1e-8)
     assert info["status"] == "RR_OK"
     wg = w.cpu().numpy()
-    assert np.linalg.norm(wg - want.w) / np.linalg.norm(want.w) <= 1e-6
-    # the true residual, recomputed by the oracle's operator
-    assert np.linalg.norm(b - ref.A(wg)) / np.linalg.norm(b) <= 1e-8
-    assert abs(info["iters"] - want.iters) <= 2
-    assert info["true_rel_res"] <= 1e-8
+    r_gpu = np.linalg.norm(b - ref.A(wg))
+    r_ref = np.linalg.norm(b - ref.A(want.w))
+    assert r_gpu / bn <= 1e-8 and info["true_rel_res"] <= 1e-8
+    assert abs(info["iters"] - want.iters) <= max(2, 0.05 * want.iters)
+    diff = np.linalg.norm(wg - want.w)
+    assert diff <= max(1e-6 * np.linalg.norm(want.w), (r_gpu + r_ref) / case["lam"])
+
+
+def test_mixed_precision_refinement(case, rr):
+    """FP32 operator inside the CG iterations, FP64 true residuals and
+    refinement restarts: the same stopping rule as the FP64 path (true residual
+    <= 1e-8, recomputed by the oracle) and the same solution, to 1e-6 or to the
+    bound the two residuals give (see test_two_level_solve_matches_oracle)."""
+    X, ref = case["X"], case["ref"]
+    b = osp.rhs(ref.M, case["y"])
+    h = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, case["lam"], case["k"],
+                    seed=case["seed"], precision=rr.RR_PREC_MIXED, max_restarts=20)
+    w = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
+    info = rr.rr_solve(h, dev(case["y"]), w, tol=1e-8)
+    assert info["status"] == "RR_OK"
+    wg = w.cpu().numpy()
+    r_gpu = np.linalg.norm(b - ref.A(wg))
+    assert r_gpu / np.linalg.norm(b) <= 1e-8
+    want = krylov.pcg(ref.A, ref.apply, b, tol=1e-8)
+    r_ref = np.linalg.norm(b - ref.A(want.w))
+    diff = np.linalg.norm(wg - want.w)
+    assert diff <= max(1e-6 * np.linalg.norm(want.w), (r_gpu + r_ref) / case["lam"])
+    # FP32 iterations cost some extra iterations, not a different method
+    assert info["iters"] <= 2 * want.iters + 20
 
 
 @pytest.mark.parametrize("solver", ["cg", "dcg"])
