@@ -18,6 +18,9 @@ namespace rr {
 namespace {
 
 constexpr int kTile = 1024;   // features per block in the seeding pass
+// below this many (row entry x delta pair) updates a Lloyd step pushes the
+// changes with global atomics instead of re-gathering every feature
+constexpr unsigned long long kPushWorkLimit = 200ull * 1000 * 1000;
 
 __device__ __forceinline__ uint64_t splitmix64_out(uint64_t seed, int64_t t) {
   uint64_t z = seed + (uint64_t)(t + 1) * 0x9E3779B97F4A7C15ULL;
@@ -279,43 +282,81 @@ __global__ void k_moved_count(int64_t N, const int64_t *__restrict__ row_ptr,
       c += prev[j] != cur[j];
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) cnt[r] = c;
+    if (lane == 0) cnt[r] = 2 * (int64_t)c;   // room for one (new) and one (old) pair each
   }
 }
 
-// per row: the moved entries as packed pairs ((old + 1) << 16) | new, in row order
-__global__ void k_moved_fill(int64_t N, const int64_t *__restrict__ row_ptr,
-                             const int32_t *__restrict__ col_idx, const int32_t *__restrict__ prev,
-                             const int32_t *__restrict__ cur, const int64_t *__restrict__ mptr,
-                             uint32_t *__restrict__ xm) {
-  const int lane = threadIdx.x & 31;
+// per row r: the net change of the row's cluster counts C[r, .] between the
+// previous and the current labels, as a list of distinct (cluster, delta)
+// pairs (delta != 0). A warp owns a row and a private shared histogram over
+// the clusters: moved entries add +1 at their new and -1 at their old
+// cluster; then each nonzero bin is claimed once (atomicExch back to zero,
+// which also leaves the histogram clean for the next row).
+// *work += sum over rows of rownnz_r * |list_r| (the cost of applying them).
+__global__ void k_row_delta(int64_t N, int32_t k, const int64_t *__restrict__ row_ptr,
+                            const int32_t *__restrict__ col_idx, const int32_t *__restrict__ prev,
+                            const int32_t *__restrict__ cur, const int64_t *__restrict__ dptr,
+                            int2 *__restrict__ dlist, int32_t *__restrict__ dcount,
+                            unsigned long long *__restrict__ work) {
+  extern __shared__ int32_t hist_all[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  int32_t *hist = hist_all + (int64_t)wib * k;
+  for (int s = lane; s < k; s += 32) hist[s] = 0;
+  __syncwarp();
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long my_work = 0;
   for (int64_t r = warp; r < N; r += nwarps) {
-    int64_t out = mptr[r];
-    for (int64_t e0 = row_ptr[r]; e0 < row_ptr[r + 1]; e0 += 32) {
+    const int64_t b = row_ptr[r], e1 = row_ptr[r + 1];
+    if (dptr[r + 1] == dptr[r]) {      // no moved entry in this row
+      if (lane == 0) dcount[r] = 0;
+      continue;
+    }
+    for (int64_t e = b + lane; e < e1; e += 32) {
+      const int32_t j = col_idx[e];
+      const int32_t o = prev[j], n = cur[j];
+      if (o != n) {
+        atomicAdd(&hist[n], 1);
+        if (o >= 0) atomicSub(&hist[o], 1);
+      }
+    }
+    __syncwarp();
+    int64_t out = dptr[r];
+    for (int64_t e0 = b; e0 < e1; e0 += 32) {
       const int64_t e = e0 + lane;
-      int32_t o = 0, n = 0;
-      bool moved = false;
-      if (e < row_ptr[r + 1]) {
+      int32_t o = -1, n = -1;
+      if (e < e1) {
         const int32_t j = col_idx[e];
         o = prev[j];
         n = cur[j];
-        moved = o != n;
+        if (o == n) o = n = -1;
       }
-      const unsigned m = __ballot_sync(0xffffffffu, moved);
-      if (moved) xm[out + __popc(m & ((1u << lane) - 1u))] = ((uint32_t)(o + 1) << 16) | (uint32_t)n;
-      out += __popc(m);
+      const int32_t vn = n >= 0 ? atomicExch(&hist[n], 0) : 0;
+      const unsigned mn = __ballot_sync(0xffffffffu, vn != 0);
+      if (vn != 0) dlist[out + __popc(mn & ((1u << lane) - 1u))] = make_int2(n, vn);
+      out += __popc(mn);
+      const int32_t vo = o >= 0 ? atomicExch(&hist[o], 0) : 0;
+      const unsigned mo = __ballot_sync(0xffffffffu, vo != 0);
+      if (vo != 0) dlist[out + __popc(mo & ((1u << lane) - 1u))] = make_int2(o, vo);
+      out += __popc(mo);
     }
+    __syncwarp();
+    const int32_t cnt = (int32_t)(out - dptr[r]);
+    if (lane == 0) dcount[r] = cnt;
+    my_work += (unsigned long long)(e1 - b) * (unsigned long long)cnt;
   }
+  if (lane == 0 && my_work) atomicAdd(work, my_work);
 }
 
-// D[i, .] += delta from the moved pairs of the rows of column i.
-// Persistent blocks take features heaviest-first from a shared counter.
-__global__ void __launch_bounds__(kThreads) k_lloyd_delta(
+// Pull: D[i, .] += sum over the rows of column i of their delta lists.
+// Persistent blocks take features heaviest-first from a shared counter; each
+// block gathers into a shared histogram (distinct clusters within a row, so no
+// two lanes of one instruction hit the same bin).
+__global__ void __launch_bounds__(kThreads) k_lloyd_pull(
     int64_t F, int32_t k, const int64_t *__restrict__ col_ptr, const int32_t *__restrict__ row_idx,
-    const int64_t *__restrict__ mptr, const uint32_t *__restrict__ xm,
-    const int32_t *__restrict__ order, int32_t *work_ctr, int32_t *__restrict__ D) {
+    const int64_t *__restrict__ dptr, const int32_t *__restrict__ dcount,
+    const int2 *__restrict__ dlist, const int32_t *__restrict__ order, int32_t *work_ctr,
+    int32_t *__restrict__ D) {
   extern __shared__ int32_t acc[];
   __shared__ int32_t cur;
   __shared__ int32_t touched;
@@ -333,20 +374,13 @@ __global__ void __launch_bounds__(kThreads) k_lloyd_delta(
     int any = 0;
     for (int64_t p = col_ptr[i] + warp; p < col_ptr[i + 1]; p += kWarps) {
       const int64_t r = row_idx[p];
-      const int64_t b = mptr[r], e1 = mptr[r + 1];
-      any |= (e1 > b);
-      // warp-uniform loop; lanes holding the same cluster combine their
-      // increments before one shared-memory atomic (hot clusters repeat in a row)
-      for (int64_t e0 = b; e0 < e1; e0 += 32) {
-        const int64_t e = e0 + lane;
-        const bool valid = e < e1;
-        const uint32_t pr = valid ? xm[e] : 0u;
-        const int32_t nl = valid ? (int32_t)(pr & 0xffffu) : -1;
-        const unsigned m1 = __match_any_sync(0xffffffffu, nl);
-        if (nl >= 0 && lane == __ffs(m1) - 1) atomicAdd(&acc[nl], __popc(m1));
-        const int32_t old = valid ? (int32_t)(pr >> 16) - 1 : -1;
-        const unsigned m2 = __match_any_sync(0xffffffffu, old);
-        if (old >= 0 && lane == __ffs(m2) - 1) atomicSub(&acc[old], __popc(m2));
+      const int32_t c = dcount[r];
+      if (c == 0) continue;
+      any = 1;
+      const int2 *lst = dlist + dptr[r];
+      for (int32_t q = lane; q < c; q += 32) {
+        const int2 pr = lst[q];
+        atomicAdd(&acc[pr.x], pr.y);
       }
     }
     if (any) touched = 1;   // benign race: every writer stores 1
@@ -359,6 +393,30 @@ __global__ void __launch_bounds__(kThreads) k_lloyd_delta(
       }
     }
     __syncthreads();
+  }
+}
+
+// Push: for every row with a delta list, D[i, S] += delta for each feature i of
+// the row and each (S, delta) of the list (global atomics; used when few
+// labels moved, so only a few rows carry work).
+__global__ void k_lloyd_push(int64_t N, int32_t k, const int64_t *__restrict__ row_ptr,
+                             const int32_t *__restrict__ col_idx, const int64_t *__restrict__ dptr,
+                             const int32_t *__restrict__ dcount, const int2 *__restrict__ dlist,
+                             int32_t *__restrict__ D) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = warp; r < N; r += nwarps) {
+    const int32_t c = dcount[r];
+    if (c == 0) continue;
+    const int2 *lst = dlist + dptr[r];
+    for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) {
+      int32_t *Di = D + (int64_t)col_idx[e] * k;
+      for (int32_t q = 0; q < c; ++q) {
+        const int2 pr = lst[q];
+        atomicAdd(&Di[pr.x], pr.y);
+      }
+    }
   }
 }
 
@@ -519,21 +577,34 @@ rr_status kmeans_work_order(int64_t F, const int64_t *row_ptr, const int64_t *co
 rr_status kmeans_lloyd_step(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                             const int64_t *col_ptr, const int32_t *row_idx, int32_t k,
                             KmeansBuffers &b, int64_t *changes_host, cudaStream_t st) {
-  // (1) moved entries (prev != labels), compacted per row
+  // (1) per-row delta lists of the cluster counts (prev -> labels)
   RR_LAUNCH(k_moved_count, grid_for(N, kWarps), kThreads, 0, st, N, row_ptr, col_idx, b.prev,
             b.labels, b.mcount);
   RR_TRY(scan_exclusive(b.mcount, b.mptr, N, b.scan_scratch, st));
-  RR_LAUNCH(k_moved_fill, grid_for(N, kWarps), kThreads, 0, st, N, row_ptr, col_idx, b.prev,
-            b.labels, b.mptr, b.xm);
-  // (2) D += delta
-  RR_CUDA(cudaMemsetAsync(b.work_ctr, 0, sizeof(int32_t), st));
-  const size_t smem = sizeof(int32_t) * (size_t)k;
-  RR_CUDA(cudaFuncSetAttribute(k_lloyd_delta, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)std::max<size_t>(smem, 1)));
-  int per_sm = 0;
-  RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lloyd_delta, kThreads, smem));
-  RR_LAUNCH(k_lloyd_delta, kSMs * std::max(1, per_sm), kThreads, smem, st, F, k, col_ptr, row_idx,
-            b.mptr, b.xm, b.order, b.work_ctr, b.D);
+  RR_CUDA(cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), st));
+  const int warps_per_cta = (int)std::max<int64_t>(1, std::min<int64_t>(kWarps, (96 * 1024) / (4 * (int64_t)k)));
+  const size_t hsmem = sizeof(int32_t) * (size_t)k * warps_per_cta;
+  RR_CUDA(cudaFuncSetAttribute(k_row_delta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
+  RR_LAUNCH(k_row_delta, std::min<int64_t>((N + warps_per_cta - 1) / warps_per_cta, kSMs * 16),
+            32 * warps_per_cta, hsmem, st, N, k, row_ptr, col_idx, b.prev, b.labels, b.mptr,
+            b.dlist, b.dcount, (unsigned long long *)b.work);
+  unsigned long long work = 0;
+  RR_CUDA(cudaMemcpyAsync(&work, b.work, sizeof(work), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  // (2) D += delta: pull per feature when much changed, push per row otherwise
+  if (work > kPushWorkLimit) {
+    RR_CUDA(cudaMemsetAsync(b.work_ctr, 0, sizeof(int32_t), st));
+    const size_t smem = sizeof(int32_t) * (size_t)k;
+    RR_CUDA(cudaFuncSetAttribute(k_lloyd_pull, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)std::max<size_t>(smem, 1)));
+    int per_sm = 0;
+    RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lloyd_pull, kThreads, smem));
+    RR_LAUNCH(k_lloyd_pull, kSMs * std::max(1, per_sm), kThreads, smem, st, F, k, col_ptr, row_idx,
+              b.mptr, b.dcount, b.dlist, b.order, b.work_ctr, b.D);
+  } else if (work > 0) {
+    RR_LAUNCH(k_lloyd_push, grid_for(N, kWarps), kThreads, 0, st, N, k, row_ptr, col_idx, b.mptr,
+              b.dcount, b.dlist, b.D);
+  }
   // (3) sizes and Q from the updated D
   RR_CUDA(cudaMemsetAsync(b.n_S, 0, sizeof(int64_t) * k, st));
   RR_CUDA(cudaMemsetAsync(b.Q, 0, sizeof(int64_t) * k, st));

@@ -189,20 +189,37 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather(
   const int32_t p0 = P.task_p[task], p1 = P.task_p[task + 1];
   const uint4 pad = make_uint4(P.W | (P.W << 16), P.W | (P.W << 16), P.W | (P.W << 16),
                                P.W | (P.W << 16));
-  for (int32_t p = p0 + threadIdx.x; p < p1; p += kSliceThreads) {
-    const int32_t w0 = P.pw[p], w1 = P.pw[p + 1];
-    T acc = T(0);
-    for (int32_t w = w0; w < w1; w += 4) {
-      uint4 q[4];
+  // four pieces per lane at a time: their pointers and first words are loaded
+  // together, so four independent 16-byte loads are in flight per lane
+  constexpr int kILP = 4;
+  for (int32_t pb = p0 + threadIdx.x; pb < p1; pb += kILP * kSliceThreads) {
+    int32_t w0[kILP], w1[kILP];
+    uint4 first[kILP];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) q[k] = (w + k < w1) ? __ldg(P.idx + w + k) : pad;
-      // gathers only for words of this piece (no shared loads for absent words)
-      acc += gather8(xs, q[0]);
-#pragma unroll
-      for (int k = 1; k < 4; ++k)
-        if (w + k < w1) acc += gather8(xs, q[k]);
+    for (int u = 0; u < kILP; ++u) {
+      const int32_t p = pb + u * kSliceThreads;
+      w0[u] = p < p1 ? __ldg(P.pw + p) : 0;
+      w1[u] = p < p1 ? __ldg(P.pw + p + 1) : 0;
     }
-    out_psum[P.slot[p]] = (double)acc;
+#pragma unroll
+    for (int u = 0; u < kILP; ++u) first[u] = w0[u] < w1[u] ? __ldg(P.idx + w0[u]) : pad;
+#pragma unroll
+    for (int u = 0; u < kILP; ++u) {
+      const int32_t p = pb + u * kSliceThreads;
+      if (p >= p1) break;
+      T acc = gather8(xs, first[u]);
+      for (int32_t w = w0[u] + 1; w < w1[u]; w += 4) {
+        uint4 q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = (w + k < w1[u]) ? __ldg(P.idx + w + k) : pad;
+        // gathers only for words of this piece (no shared loads for absent words)
+        acc += gather8(xs, q[0]);
+#pragma unroll
+        for (int k = 1; k < 4; ++k)
+          if (w + k < w1[u]) acc += gather8(xs, q[k]);
+      }
+      out_psum[__ldg(P.slot + p)] = (double)acc;
+    }
   }
 }
 

@@ -41,9 +41,11 @@ struct KmeansBuffers {
   int32_t *labels;     // [F]   current labels (-1: not assigned yet)
   int32_t *prev;       // [F]   labels of the previous step
   int32_t *next;       // [F]
-  int64_t *mcount;     // [N]   moved entries per row
-  int64_t *mptr;       // [N+1]
-  uint32_t *xm;        // [nnz] moved entries as ((old+1) << 16) | new
+  int64_t *mcount;     // [N]   room for each row's delta list (2 x moved entries)
+  int64_t *mptr;       // [N+1] start of each row's delta list
+  int2 *dlist;         // [2 nnz] (cluster, delta) pairs of the rows' count changes
+  int32_t *dcount;     // [N]   length of each row's delta list
+  int64_t *work;       // [1]   total cost of applying the delta lists
   int64_t *scan_scratch;
   int64_t *n_S;        // [k]
   int64_t *Q;          // [k]

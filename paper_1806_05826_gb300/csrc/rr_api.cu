@@ -279,7 +279,9 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&kb.prev, F));
   RR_TRY(m.alloc(&kb.mcount, N));
   RR_TRY(m.alloc(&kb.mptr, N + 1));
-  RR_TRY(m.alloc(&kb.xm, nnz));
+  RR_TRY(m.alloc(&kb.dlist, 2 * std::max<int64_t>(nnz, 1)));
+  RR_TRY(m.alloc(&kb.dcount, N));
+  RR_TRY(m.alloc(&kb.work, 1));
   RR_TRY(m.alloc(&kb.scan_scratch, rr::scan_scratch_len(N) + 8));
   RR_TRY(m.alloc(&h->n_S, 2 * (int64_t)k));
   kb.n_S = h->n_S;
@@ -326,7 +328,9 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   m.release(kb.prev);
   m.release(kb.mcount);
   m.release(kb.mptr);
-  m.release(kb.xm);
+  m.release(kb.dlist);
+  m.release(kb.dcount);
+  m.release(kb.work);
   m.release(kb.scan_scratch);
   m.release(kb.d2);
   m.release(kb.ov);
