@@ -44,6 +44,16 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched section (64 targets x 8 weights over the same X)")
+    ap.add_argument("--no-many", action="store_true",
+                    help="skip the section of uneven independent problems in one graph")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned coarse correction section (harvest, training, solves)")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="host-issued loops instead of CUDA graphs (every kernel visible to a profiler)")
+    ap.add_argument("--roofline-only", action="store_true",
+                    help="one setup, then only the operator-apply kernel timings (profiling runs)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="mixed: FP32 operator inside CG + FP64 refinement; fp64: FP64 throughout")
     return ap.parse_args()
@@ -140,6 +150,214 @@ def profiled_traffic(kernel, workload):
 
 # ---------------------------------------------------------------- our arm
 
+def measure_roofline(rr, row_ptr, col_idx, N, F, nnz, k, lams, opts, dev, stream, workload):
+    """Operator-apply kernels timed alone with CUDA events on the library's stream."""
+    import torch
+    h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], k, **opts)
+    v = torch.randn(F, dtype=torch.float64, device=dev)
+    u = torch.empty(N, dtype=torch.float64, device=dev)
+    z = torch.empty(F, dtype=torch.float64, device=dev)
+    reps = 20
+    kern = {}
+    for name, fn in (("X_v", lambda: rr.rr_matvec(h, v, u)),
+                     ("Xt_u", lambda: rr.rr_rhs(h, u, z)),
+                     ("A_v", lambda: rr.rr_apply(h, v, z))):
+        for _ in range(3):
+            fn()
+        es = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+        for i in range(reps):
+            es[2 * i].record(stream)
+            fn()
+            es[2 * i + 1].record(stream)
+        torch.cuda.synchronize(dev)
+        kern[name] = statistics.mean(es[2 * i].elapsed_time(es[2 * i + 1]) for i in range(reps))
+    rr.rr_free(h)
+    # algorithmic bytes per call: one int32 index per nonzero per pass, the
+    # pointer array of the pass, each vector read or written once
+    algo = {
+        "X_v": 4 * nnz + 8 * (N + 1) + 8 * F + 8 * N,
+        "Xt_u": 4 * nnz + 8 * (F + 1) + 8 * N + 8 * F,
+        "A_v": 8 * nnz + 8 * (N + 1) + 8 * (F + 1) + 8 * F + 16 * N + 8 * F + 8 * F,
+    }
+    dom = "A_v"
+    peak, peak_kind = peaks()
+    achieved = algo[dom] / (kern[dom] * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": "operator apply (k_sliced_gather x2 + k_sliced_epilogue)",
+            "achieved": round(achieved, 1), "peak": peak,
+            "peak_kind": f"{peak_kind} (burst copy)", "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": profiled_traffic("operator_apply", workload),
+            "algorithmic_bytes": algo[dom], "launch_ms": round(kern[dom], 4),
+            "parts": {n: {"ms": round(t, 4), "achieved_gbs": round(algo[n] / (t * 1e-3) / 1e9, 1)}
+                      for n, t in kern.items() if n != dom}}
+
+
+def measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world):
+    """Many targets and weights over the same X in one rr_solve_batch (the
+    batched form), against the plain two-level PCG solving a sample of the same
+    systems one at a time on the same GPU. One warm-up, then one timed run of
+    setup + batch solve (CUDA events on the library's stream)."""
+    import torch
+    from gen import synth
+    name = "zipf_200000x100000_64x8"
+    pb = synth.BATCH_WORKLOADS[name]
+    seeds, lams = pb["target_seeds"], list(pb["lambdas"])
+    Y, _ = synth.ridge_targets_many(X, seeds)
+    N, F = X.n_rows, X.n_cols
+    Yd = torch.as_tensor(Y, device=dev)
+    Wb = torch.empty((len(lams), len(seeds), F), dtype=torch.float64, device=dev)
+
+    def run():
+        h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], k, **opts)
+        out = rr.rr_solve_batch(h, Yd, lams, Wb, tol=TOL)
+        return h, out
+
+    h, out = run()
+    rr.rr_free(h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    h, out = run()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_batch = e0.elapsed_time(e1) / 1000.0
+    infos = [i for row in out["infos"] for i in row]
+    assert out["status"] == "RR_OK" and max(i["true_rel_res"] for i in infos) <= TOL
+    # plain two-level PCG on a sample: target 0 at every weight, one solve each
+    w = torch.empty(F, dtype=torch.float64, device=dev)
+    plain_ms = []
+    for lam in lams:
+        rr.rr_set_lambda(h, lam)
+        inf = rr.rr_solve(h, Yd[0], w, tol=TOL)
+        assert inf["status"] == "RR_OK"
+        plain_ms.append(inf["solve_ms"])
+    n_sys = len(infos)
+    setup_s = infos[0]["setup_ms"] / 1000.0
+    t_plain = setup_s + n_sys * statistics.mean(plain_ms) / 1000.0
+    rr.rr_free(h)
+    its = sorted(i["iters"] for i in infos)
+    return {"workload": name, "systems": n_sys, "targets": len(seeds), "lambdas": lams,
+            "value": round(t_batch, 4), "unit": "s", "s_per_system": round(t_batch / n_sys, 6),
+            "setup_s": round(setup_s, 4), "solve_s": round(infos[0]["solve_ms"] / 1000.0, 4),
+            "iters_min_median_max": [its[0], its[len(its) // 2], its[-1]],
+            "restarts_max": max(i["restarts"] for i in infos),
+            "true_rel_res_max": max(i["true_rel_res"] for i in infos),
+            "plain_sampled_solve_ms": [round(t, 2) for t in plain_ms],
+            "plain_estimate_s": round(t_plain, 3),
+            "speedup_vs_plain": round(t_plain / t_batch, 2),
+            "note": "plain = setup + systems x mean single-solve time of target 0 at the 8 weights"}
+
+
+def measure_many(rr, dev, stream, opts):
+    """Independent problems of uneven sizes: rr_solve_many (all PCG loops in one
+    graph) against rr_solve one problem after the other, same handles (setups
+    excluded from both; they are reported apart)."""
+    import torch
+    from gen import synth
+    name = "uneven_12"
+    probs = synth.many_workload(name)
+    hs, ys, ws, setup_ms = [], [], [], []
+    for X, y, p in probs:
+        rp = torch.as_tensor(X.row_ptr, device=dev)
+        ci = torch.as_tensor(X.col_idx, device=dev)
+        h = rr.rr_setup(rp, ci, X.n_rows, X.n_cols, p["lam"], p["k"], **dict(opts, seed=p["seed"]))
+        hs.append(h)
+        ys.append(torch.as_tensor(y, device=dev))
+        ws.append(torch.empty(X.n_cols, dtype=torch.float64, device=dev))
+    out = rr.rr_solve_many(hs, ys, ws, tol=TOL, stream=stream)   # warm-up
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize(dev)
+    e[0].record(stream)
+    out = rr.rr_solve_many(hs, ys, ws, tol=TOL, stream=stream)
+    e[1].record(stream)
+    torch.cuda.synchronize(dev)
+    assert out["status"] == "RR_OK" and max(i["true_rel_res"] for i in out["infos"]) <= TOL
+    e[2].record(stream)
+    singles = [rr.rr_solve(h, y, w, tol=TOL) for h, y, w in zip(hs, ys, ws)]
+    e[3].record(stream)
+    torch.cuda.synchronize(dev)
+    t_many, t_seq = e[0].elapsed_time(e[1]) / 1e3, e[2].elapsed_time(e[3]) / 1e3
+    sizes = [(X.n_rows, X.n_cols, X.nnz) for X, _, _ in probs]
+    for h in hs:
+        rr.rr_free(h)
+    return {"workload": name, "problems": len(probs), "value": round(t_many, 4), "unit": "s",
+            "sequential_s": round(t_seq, 4), "speedup_vs_sequential": round(t_seq / t_many, 2),
+            "setup_s_total": round(sum(i["setup_ms"] for i in singles) / 1e3, 3),
+            "iters": [i["iters"] for i in out["infos"]],
+            "true_rel_res_max": max(i["true_rel_res"] for i in out["infos"]),
+            "sizes_n_d_nnz": sizes}
+
+
+def measure_learned(rr, X, row_ptr, col_idx, k, opts, dev, stream, n_pairs=100_000,
+                    eval_seeds=tuple(range(100, 116)), hidden=512):
+    """The learned coarse correction on the 200,000 x 100,000 matrix at
+    lambda = 1e-3: pairs harvested from two-level PCG on training targets
+    (seeds 1000+, 64 per batch), the network (k -> 512 -> 512 -> k, BF16
+    tensor-core training, Adam) trained on the GPU, then held-out targets solved
+    by FCG with the learned correction (fallback to the Cholesky coarse solve)
+    and by the plain two-level PCG; both to true residual 1e-8."""
+    import torch
+    from gen import synth
+    lam = 1e-3
+    N, F = X.n_rows, X.n_cols
+    h = rr.rr_setup(row_ptr, col_idx, N, F, lam, k, **opts)
+    k_eff = rr.rr_query(h)["k_eff"]
+    t0 = time.time()
+    Xs, Ts, got, seed0 = [], [], 0, 1000
+    while got < n_pairs:
+        seeds = list(range(seed0, seed0 + 64))
+        seed0 += 64
+        Y, _ = synth.ridge_targets_many(X, seeds)
+        Yd = torch.as_tensor(Y, device=dev)
+        Wref = torch.empty((1, 64, F), dtype=torch.float64, device=dev)
+        rr.rr_solve_batch(h, Yd, [lam], Wref, tol=1e-10)
+        xp, tp = rr.rr_harvest(h, Yd, lam, Wref[0].contiguous(), 1e-8, 400, n_pairs - got, k_eff)
+        Xs.append(xp)
+        Ts.append(tp)
+        got += xp.shape[0]
+    Xp, Tp = torch.cat(Xs), torch.cat(Ts)
+    t_harvest = time.time() - t0
+    params = synth.mlp_init(k_eff, hidden, seed=7)
+    net = rr.mlp_create(k_eff, hidden, params, max_batch=512, stream=stream)
+    steps = 2000
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    losses = rr.mlp_train(net, Xp, Tp, batch=512, steps=steps, lr=1e-3, seed=3)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_train = e0.elapsed_time(e1) / 1e3
+    w = torch.empty(F, dtype=torch.float64, device=dev)
+    rows = []
+    for s in eval_seeds:
+        y, _ = synth.ridge_targets(X, s)
+        yd = torch.as_tensor(y, device=dev)
+        a = rr.rr_solve_fcg(h, net, yd, w, tol=TOL)
+        b = rr.rr_solve(h, yd, w, tol=TOL)
+        c = rr.rr_solve_fcg(h, None, yd, w, tol=TOL)
+        for inf in (a, b, c):
+            assert inf["status"] == "RR_OK" and inf["true_rel_res"] <= TOL
+        rows.append((a["solve_ms"], a["iters"], a["fallbacks"], b["solve_ms"], b["iters"],
+                     c["solve_ms"], c["iters"]))
+    r = np.array(rows, dtype=np.float64)
+    net.close()
+    rr.rr_free(h)
+    return {"workload": "zipf_200000x100000 lambda=1e-3", "pairs": int(Xp.shape[0]),
+            "net": f"{k_eff}-{hidden}-{hidden}-{k_eff} BF16 (tcgen05 training)",
+            "harvest_s": round(t_harvest, 2), "train_s": round(t_train, 3),
+            "train_steps": steps, "batch": 512,
+            "loss_first_last": [float(losses[:20].mean()), float(losses[-20:].mean())],
+            "held_out_seeds": len(eval_seeds),
+            "learned_fcg_s_mean": round(r[:, 0].mean() / 1e3, 4),
+            "learned_fcg_iters_mean": round(r[:, 1].mean(), 1),
+            "learned_fallbacks_mean": round(r[:, 2].mean(), 1),
+            "plain_pcg_s_mean": round(r[:, 3].mean() / 1e3, 4),
+            "plain_pcg_iters_mean": round(r[:, 4].mean(), 1),
+            "cholesky_fcg_s_mean": round(r[:, 5].mean() / 1e3, 4),
+            "cholesky_fcg_iters_mean": round(r[:, 6].mean(), 1),
+            "speedup_vs_plain": round(r[:, 3].mean() / r[:, 0].mean(), 3)}
+
+
 def run_ours(args, rank, world, local):
     import torch
     import __graft_entry__ as ge
@@ -161,7 +379,13 @@ def run_ours(args, rank, world, local):
     W = [torch.empty(F, dtype=torch.float64, device=dev) for _ in lams]
 
     prec = rr.RR_PREC_MIXED if args.precision == "mixed" else rr.RR_PREC_FP64
-    opts = dict(seed=p["seed"], stream=stream, precision=prec, max_restarts=20)
+    opts = dict(seed=p["seed"], stream=stream, precision=prec, max_restarts=20,
+                use_graphs=0 if args.no_graphs else 1)
+
+    if args.roofline_only:
+        return {"workload": args.workload, "precision": args.precision,
+                "roofline": measure_roofline(rr, row_ptr, col_idx, N, F, nnz, k, lams, opts, dev,
+                                             stream, args.workload)}
 
     def step(host=None):
         if host is None:
@@ -215,44 +439,8 @@ def run_ours(args, rank, world, local):
         total_ms = float(t.item())
     value = total_ms / 1000.0 / args.steps
 
-    # ---- roofline: the mat-vec kernels timed alone on the library's stream
-    h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], k, **opts)
-    v = torch.randn(F, dtype=torch.float64, device=dev)
-    u = torch.empty(N, dtype=torch.float64, device=dev)
-    z = torch.empty(F, dtype=torch.float64, device=dev)
-    reps = 20
-    kern = {}
-    for name, fn in (("X_v", lambda: rr.rr_matvec(h, v, u)),
-                     ("Xt_u", lambda: rr.rr_rhs(h, u, z)),
-                     ("A_v", lambda: rr.rr_apply(h, v, z))):
-        for _ in range(3):
-            fn()
-        es = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
-        for i in range(reps):
-            es[2 * i].record(stream)
-            fn()
-            es[2 * i + 1].record(stream)
-        torch.cuda.synchronize(dev)
-        kern[name] = statistics.mean(es[2 * i].elapsed_time(es[2 * i + 1]) for i in range(reps))
-    rr.rr_free(h)
-    # algorithmic bytes per call: one int32 index per nonzero per pass, the
-    # pointer array of the pass, each vector read or written once
-    algo = {
-        "X_v": 4 * nnz + 8 * (N + 1) + 8 * F + 8 * N,
-        "Xt_u": 4 * nnz + 8 * (F + 1) + 8 * N + 8 * F,
-        "A_v": 8 * nnz + 8 * (N + 1) + 8 * (F + 1) + 8 * F + 16 * N + 8 * F + 8 * F,
-    }
-    dom = "A_v"
-    peak, peak_kind = peaks()
-    achieved = algo[dom] / (kern[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "operator apply (k_sliced_gather x2 + k_sliced_epilogue)",
-                "achieved": round(achieved, 1), "peak": peak,
-                "peak_kind": f"{peak_kind} (burst copy)", "unit": "GB/s",
-                "frac": round(achieved / peak, 4),
-                "traffic": profiled_traffic("operator_apply", args.workload),
-                "algorithmic_bytes": algo[dom], "launch_ms": round(kern[dom], 4),
-                "parts": {n: {"ms": round(t, 4), "achieved_gbs": round(algo[n] / (t * 1e-3) / 1e9, 1)}
-                          for n, t in kern.items() if n != dom}}
+    roofline = measure_roofline(rr, row_ptr, col_idx, N, F, nnz, k, lams, opts, dev, stream,
+                                args.workload)
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
@@ -274,6 +462,14 @@ def run_ours(args, rank, world, local):
         e2e = {"value": round(e_ms / 1000.0, 5), "unit": "s",
                "h2d_bytes_per_step": 8 * (N + 1) + 4 * nnz + 8 * N,
                "d2h_bytes_per_step": 8 * F * len(lams)}
+
+    batched = many = learned = None
+    if not args.no_batch and args.workload == WORKLOAD:
+        batched = measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world)
+    if not args.no_many:
+        many = measure_many(rr, dev, stream, opts)
+    if not args.no_learned and args.workload == WORKLOAD:
+        learned = measure_learned(rr, X, row_ptr, col_idx, k, opts, dev, stream)
 
     last = all_infos[-1]
     out = {
@@ -298,8 +494,10 @@ def run_ours(args, rank, world, local):
                       "restarts": [i["restarts"] for i in last],
                       "true_rel_res": [i["true_rel_res"] for i in last],
                       "kmeans_iters": last[0]["kmeans_iters"], "k_eff": last[0]["k_eff"],
+                      "gram_tensor_cores": bool(last[0]["gram_tensor_cores"]),
                       "step_ms": [round(t, 3) for t in step_ms]},
         "e2e": e2e, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches,
+        "batched": batched, "many": many, "learned": learned,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         iters = [i["iters"] for i in last]

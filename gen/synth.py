@@ -176,6 +176,32 @@ def ridge_targets(X, seed: int, noise_sigma: float = 0.1):
     return y + noise_sigma * normal(seed, 11, n), w_star
 
 
+def ridge_targets_many(X: CSR, seeds, noise_sigma: float = 0.1):
+    """Targets y_j = X w*_j + noise for each seed j (as ridge_targets, one seed
+    per target). Returns Y (len(seeds), N) and W* (len(seeds), F)."""
+    import scipy.sparse as sp
+    A = sp.csr_matrix((np.ones(X.nnz), X.col_idx, X.row_ptr), shape=(X.n_rows, X.n_cols))
+    W = np.stack([normal(sd, 10, X.n_cols) for sd in seeds])
+    Y = np.asarray((A @ W.T).T)
+    for j, sd in enumerate(seeds):
+        Y[j] += noise_sigma * normal(sd, 11, X.n_rows)
+    return np.ascontiguousarray(Y), W
+
+
+def mlp_init(k: int, hidden: int, seed: int, stream: int = 30) -> dict:
+    """Initial weights of the learned correction's network (k -> hidden ->
+    hidden -> k): He-uniform draws (2u - 1) sqrt(6 / fan_in) from this module's
+    uniforms, taken in the order W1, W2, W3; biases zero."""
+    draws = uniform(seed, stream, 2 * hidden * k + hidden * hidden)
+    out, o = {}, 0
+    for name, fo, fi in (("W1", hidden, k), ("W2", hidden, hidden), ("W3", k, hidden)):
+        n = fo * fi
+        out[name] = (2.0 * draws[o:o + n] - 1.0).reshape(fo, fi) * np.sqrt(6.0 / fi)
+        o += n
+    out["b1"], out["b2"], out["b3"] = np.zeros(hidden), np.zeros(hidden), np.zeros(k)
+    return out
+
+
 def dense_ar1(n_rows: int, n_cols: int, rho: float = 0.9, seed: int = 0) -> np.ndarray:
     """Dense float32 X with X[:,0] ~ N(0,1) and X[:,j] = rho X[:,j-1] + sqrt(1-rho^2) eps_j."""
     eps = normal(seed, 20, n_rows * n_cols).reshape(n_cols, n_rows)
@@ -207,6 +233,46 @@ WORKLOADS = {
     "zipf_200000x100000": dict(n_rows=200_000, n_cols=100_000, density=0.002, s=1.1,
                                seed=1, k=1000, lambdas=(1e-3, 1e-1, 10.0)),
 }
+
+# many targets x many weights over the 200,000 x 100,000 matrix: 64 targets
+# (seeds 0..63), 8 weights log-spaced from 1e-3 to 10 -> 512 systems
+BATCH_WORKLOADS = {
+    "zipf_200000x100000_64x8": dict(base="zipf_200000x100000", target_seeds=tuple(range(64)),
+                                    lambdas=tuple(float(v) for v in np.logspace(-3, 1, 8))),
+}
+
+
+# independent problems of uneven sizes (Zipf s = 1.1 binary X, lambda = 1e-2,
+# k = d // 100): n ~ U[10k, 100k], d ~ U[5k, 40k], density ~ U[0.1%, 1%],
+# problem i drawn from seed i (a scaled stand-in of 28 problems up to
+# 400,000 x 150,000, whose generation on the host alone would take minutes)
+MANY_WORKLOADS = {"uneven_12": dict(n_problems=12, n=(10_000, 100_000), d=(5_000, 40_000),
+                                    density=(0.001, 0.01), lam=1e-2)}
+
+
+def many_workload(name: str):
+    """[(X, y, params)] of a named set of independent problems."""
+    p = MANY_WORKLOADS[name]
+    out = []
+    for i in range(p["n_problems"]):
+        u = uniform(i, 40, 3)
+        n = int(p["n"][0] + u[0] * (p["n"][1] - p["n"][0]))
+        d = int(p["d"][0] + u[1] * (p["d"][1] - p["d"][0]))
+        dens = p["density"][0] + u[2] * (p["density"][1] - p["density"][0])
+        X = zipf_binary(n, d, dens, 1.1, i)
+        y, _ = ridge_targets(X, i)
+        out.append((X, y, dict(n=n, d=d, density=dens, k=max(2, d // 100), lam=p["lam"], seed=i)))
+    return out
+
+
+def batch_workload(name: str):
+    """(X, Y, W*, params) of a named batched workload."""
+    p = dict(BATCH_WORKLOADS[name])
+    base = WORKLOADS[p["base"]]
+    X = zipf_binary(base["n_rows"], base["n_cols"], base["density"], base["s"], base["seed"])
+    Y, Ws = ridge_targets_many(X, p["target_seeds"])
+    p.update(k=base["k"], seed=base["seed"])
+    return X, Y, Ws, p
 
 
 def workload(name: str):

@@ -93,9 +93,10 @@ typedef struct {
   int32_t check_every;          /* iterations between convergence read-backs when use_graphs = 0
                                    (default 8) */
   int32_t max_restarts;         /* true-residual refinement restarts at most (default 5) */
-  int32_t use_graphs;           /* 1: the iteration loop runs on the device as one CUDA graph with a
-                                   conditional while node (default); 0: host-driven batches of
-                                   check_every iterations */
+  int32_t use_graphs;           /* 1: the iteration loop and the k-means++ seeding rounds run on
+                                   the device as CUDA graphs with a conditional while node
+                                   (default); 0: host-driven batches of check_every iterations and
+                                   host-issued seeding rounds (same results) */
   int32_t gram;                 /* RR_GRAM_* (default RR_GRAM_AUTO) */
   void *stream;                 /* cudaStream_t for all work; NULL = legacy default stream */
 } rr_options;
@@ -112,6 +113,8 @@ typedef struct {
   double solve_ms;        /* wall time of this solve (host clock, synchronised) */
   int64_t launches;       /* kernels this call launched */
   int32_t gram_tensor_cores; /* 1 if rr_setup formed the coarse Gram on the tensor cores */
+  int32_t fallbacks;      /* rr_solve_fcg with a network: steps redone with the Cholesky
+                             coarse solve */
   double setup_phase_ms[8]; /* rr_setup wall time by phase: 0 copy + validation of X, 1 CSC
                                build, 2 k-means++ seeding, 3 Lloyd steps, 4 compaction + member
                                lists, 5 counts + coarse Gram, 6 coarse factor + smoother,
@@ -152,6 +155,117 @@ rr_status rr_set_lambda(rr_handle *h, double lambda);
  * Errors: RR_INVALID_ARG (tol not in (0, 1)), RR_NOT_CONVERGED (cap reached;
  * w holds the last iterate), RR_NONFINITE, RR_CUDA_ERROR. */
 rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info *info);
+
+/* Solves Eq. (1) for many right-hand sides and many weights at once: for every
+ * target j < nrhs and weight l < nlam, (X^T X + lambdas[l] I) w = X^T y_j
+ * (Section 2 poses one X with several b and several beta). The nrhs * nlam
+ * systems share the handle's clustering (Section 3.4) and advance together
+ * through the two-level PCG of rr_solve: each operator apply is one
+ * sparse-times-dense pass pair over X's pattern for a slab of 64 systems, the
+ * coarse level has one Cholesky factor per weight, and each system keeps its
+ * own CG scalars and stops on its own residual ||r|| <= tol ||X^T y_j||.
+ * Precision, whatever the handle's: the operator applies inside CG (also
+ * those of the smoother) gather FP32 copies of the vectors with FP32
+ * accumulation; FP64 vectors, dot products, norms, coarse level (Cholesky
+ * factors and coarse products); an FP64 true residual after CG
+ * stops, restarting each system on its correction while it is above tol
+ * (at most max_restarts times per system).
+ *   Y        device double[nrhs * N], target j at Y + j*N.
+ *   lambdas  host double[nlam], each > 0 and finite.
+ *   W        device double[nlam * nrhs * F], overwritten: the solution of
+ *            (j, l) at W + (l*nrhs + j)*F.
+ *   infos    host rr_info[nlam * nrhs] (index l*nrhs + j) or NULL; solve_ms
+ *            is the time of the whole batch.
+ * The handle's own lambda and rr_solve state are untouched. Device work
+ * space of about 13 F + 3 N doubles per system is kept in the handle and
+ * reused by later calls with as many or fewer systems and weights.
+ * Requires RR_SOLVER_TWOLEVEL. Synchronises the stream before returning.
+ * Errors: RR_INVALID_ARG, RR_UNSUPPORTED (other solver), RR_OOM, RR_NOT_SPD,
+ * RR_NOT_CONVERGED (some system hit a cap; W holds the last iterates and
+ * infos say which), RR_NONFINITE, RR_CUDA_ERROR. */
+rr_status rr_solve_batch(rr_handle *h, int32_t nrhs, const double *Y, int32_t nlam,
+                         const double *lambdas, double *W, double tol, rr_info *infos);
+
+/* Solves nprob independent problems of different sizes, problem i being
+ * Eq. (1) for the X, clustering, lambda and solver of handle hs[i] with target
+ * ys[i] (device double[N_i]) into ws[i] (device double[F_i]), exactly as
+ * rr_solve would, but in one CUDA graph: the CG loop of every problem is a
+ * conditional while node of one graph, the loops being independent branches,
+ * so the kernels of small problems run concurrently with those of others.
+ * (The paper solves one problem at a time; this is the batched form for many
+ * unrelated problems.) True-residual refinement per problem as rr_solve (a
+ * relaunch of the graph continues the problems that restart). All work runs on
+ * `stream` (cudaStream_t) during the call; the handles must be distinct, and
+ * each must have been set up with use_graphs = 1 or 0 alike (the graph is
+ * always used). infos: host rr_info[nprob] or NULL; solve_ms is the time of
+ * the whole call. Returns RR_OK when every problem reached tol, else the
+ * first failing status kind (RR_NOT_CONVERGED / RR_NONFINITE). Synchronises. */
+rr_status rr_solve_many(int32_t nprob, rr_handle *const *hs, const double *const *ys,
+                        double *const *ws, double tol, void *stream, rr_info *infos);
+
+/* ---- Flexible CG and the learned coarse correction ----------------------
+ * Algorithm 3 (flexible CG, FCG(m) with m = 1: each direction is
+ * A-orthogonalised against the previous one, which allows a preconditioner
+ * that changes from step to step) with the two-level cycle of Section 3.1 as
+ * its preconditioner, from w_0 = 0. The cycle's coarse solve e_c = A_c^-1 r_c
+ * is either the Cholesky solve (net == NULL: the paper's own method in FCG
+ * form) or a learned correction e_c = ||r_c|| net(r_c / ||r_c||) from an
+ * rr_mlp (the paper has no learned part). With a network, a step falls back
+ * to the Cholesky coarse solve when <r, z> <= 0, when z or the step length is
+ * not finite, or when the step would not reduce ||r||_2 (checked in FP64
+ * before the update, from <p,r>, <r,q>, ||q||^2); info->fallbacks counts them.
+ * Stopping, true-residual refinement, precision and graphs as in rr_solve.
+ * y: device double[N]; w: device double[F]. The network's k must equal the
+ * handle's k_eff. Errors as rr_solve, RR_INVALID_ARG on a k mismatch. */
+typedef struct rr_mlp rr_mlp;
+rr_status rr_solve_fcg(rr_handle *h, const rr_mlp *net, const double *y, double *w, double tol,
+                       rr_info *info);
+
+/* Training pairs for the learned correction, harvested from the batched
+ * two-level PCG of rr_solve_batch at one weight: for every system j and
+ * iteration i, x = r_c = P^T r1 (the restricted residual after
+ * pre-smoothing) and t = P^T (e - z1), e = wref_j - w_i the error of the
+ * iterate and z1 the pre-smoothing step (so that P t is the part of the
+ * remaining error that the coarse space can carry).
+ *   Y     device double[nrhs * N] (target j at Y + j*N)
+ *   Wref  device double[nrhs * F], the solutions (e.g. from rr_solve_batch at
+ *         a tighter tol)
+ *   Xp,Tp device float[max_pairs * k_eff] each, pair p at row p
+ *   n_pairs (host) receives the number of pairs written: every (j, i) with
+ *   i below max_iter and system j still iterating (its recurrence residual
+ *   above tol ||X^T y_j||), in order of i then j, cut at max_pairs.
+ * Runs at most max_iter iterations (no refinement restarts). Synchronises. */
+rr_status rr_harvest(rr_handle *h, int32_t nrhs, const double *Y, double lambda, const double *Wref,
+                     double tol, int32_t max_iter, float *Xp, float *Tp, int64_t max_pairs,
+                     int64_t *n_pairs);
+
+/* The network: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), o = W3 h2 + b3,
+ * x and o of length k, hidden width H (a positive multiple of 128). Weights in
+ * FP32 (the master copy Adam updates) with BF16 copies for the tensor-core
+ * products; training minimises 0.5/B sum_b ||o_b - t_b||^2.
+ * params_host: the parameters packed as W1 [H x k] row-major, b1 [H],
+ * W2 [H x H], b2 [H], W3 [k x H], b3 [k] (rr_mlp_param_count(k, H) floats).
+ * max_batch bounds the rows of one forward / gradient / training step.
+ * All work runs on `stream` (cudaStream_t, NULL = legacy default stream). */
+int64_t rr_mlp_param_count(int32_t k, int32_t hidden);
+rr_status rr_mlp_create(int32_t k, int32_t hidden, int32_t max_batch, const float *params_host,
+                        void *stream, rr_mlp **out);
+rr_status rr_mlp_set_params(rr_mlp *m, const float *params_host);
+rr_status rr_mlp_get_params(const rr_mlp *m, float *params_host);
+/* out (device float[B x k]) = o for the rows of X (device float[B x k]), as given. */
+rr_status rr_mlp_forward(rr_mlp *m, int32_t B, const float *X, float *out);
+/* Loss and its gradient for the rows of X with targets T (device float[B x k]),
+ * as given; grads_host (packed like the parameters) and loss_host may be NULL. */
+rr_status rr_mlp_grad(rr_mlp *m, int32_t B, const float *X, const float *T, float *grads_host,
+                      float *loss_host);
+/* `steps` Adam steps (lr, beta1 = 0.9, beta2 = 0.999, eps = 1e-8) on batches of
+ * `batch` pairs drawn uniformly (SplitMix64 at counter step*batch + b) from the
+ * n_pairs rows of Xp, Tp (device float[n_pairs x k]); each pair is divided by
+ * ||x|| (the homogeneous scaling of the learned correction). loss_host: host
+ * float[steps] of the batch losses, or NULL. Synchronises the stream. */
+rr_status rr_mlp_train(rr_mlp *m, int64_t n_pairs, const float *Xp, const float *Tp, int32_t batch,
+                       int32_t steps, float lr, uint64_t seed, float *loss_host);
+void rr_mlp_free(rr_mlp *m);
 
 /* out = (X^T X + lambda I) v (Eq. (1)'s operator, applied matrix-free as
  * u = X v then X^T u + lambda v). v, out: device double[F]; may not alias.

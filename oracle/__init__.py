@@ -17,9 +17,12 @@ Ridge Regression" (arXiv 1806.05826):
   Krylov      CG, Jacobi-preconditioned CG (DCG), PCG, and flexible CG
               (Algorithm 3) with truncation m_i = max(1, i mod (m+1)).
   residual    Section 4 figures: ||X^T b - (X^T X + beta I) x|| / ||X^T b||.
+  learned     (no counterpart in the paper) the training pairs of the learned
+              coarse correction, (P^T r1, P^T (e - z1)) along two-level PCG
+              (learned.py), and the FP64 network with its gradients (mlp.py).
 
 Parity unpinned: iteration counts and speed-ups against the paper's tables
 (its datasets are not available), and k-means labels beyond "same initial
 centres give the same labels" (Lloyd's optimum is not unique).
 """
-from . import sparse, kmeans, twolevel, krylov, mlp  # noqa: F401
+from . import sparse, kmeans, twolevel, krylov, mlp, learned  # noqa: F401

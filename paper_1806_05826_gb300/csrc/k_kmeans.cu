@@ -489,13 +489,26 @@ __global__ void k_lloyd_argmin(int64_t F, int32_t k, const int32_t *__restrict__
 // one round (overlaps with the newest centre, distance update, next draw).
 rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                         const int64_t *col_ptr, const int32_t *row_idx, int32_t k, uint64_t seed,
-                        KmeansBuffers &b, cudaStream_t st) {
+                        KmeansBuffers &b, cudaStream_t st, bool use_graph) {
   (void)N;
   const int64_t ntiles = (F + kTile - 1) / kTile;
   uint8_t *chosen = reinterpret_cast<uint8_t *>(b.next);   // F bytes of the (unused yet) next[]
   RR_CUDA(cudaMemsetAsync(chosen, 0, F, st));
   RR_CUDA(cudaMemsetAsync(b.ov, 0, sizeof(int32_t) * F, st));
   RR_LAUNCH(k_first_center, 1, 32, 0, st, F, seed, b.centers, chosen, b.round);
+  if (!use_graph) {
+    // the same k rounds as the graph's while loop, issued from the host
+    for (int32_t t = 0; t < k; ++t) {
+      RR_LAUNCH(k_seed_overlap, kSMs * 2, kThreads, 0, st, b.round, b.centers, row_ptr, col_idx,
+                col_ptr, row_idx, b.ov);
+      RR_LAUNCH(k_seed_update, (unsigned)ntiles, kThreads, 0, st, b.round, F, b.centers, col_ptr,
+                b.ov, b.d2, b.part_i);
+      RR_LAUNCH(k_seed_pick, 1, kThreads, 0, st, b.round, k, F, ntiles, seed, b.d2, b.part_i,
+                b.centers, chosen);
+    }
+    RR_CUDA(cudaStreamSynchronize(st));
+    return RR_OK;
+  }
 
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -530,8 +543,11 @@ rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int3
     rr_launch_counter = l0;
     cudaGraph_t cap = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(cs, &cap);
-    RR_TRY(bs);
-    if (ec != cudaSuccess) {
+    if (bs != RR_OK || ec != cudaSuccess) {
+      cudaGraphDestroy(g);
+      g = nullptr;
+      cudaGetLastError();
+      if (bs != RR_OK) return bs;
       rr_set_error("seeding graph capture failed: %s", cudaGetErrorString(ec));
       return RR_CUDA_ERROR;
     }

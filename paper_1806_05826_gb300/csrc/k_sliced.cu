@@ -12,14 +12,34 @@
 // lane (in a fixed order) into its own slot, numbered outer-major, and the
 // slots of one outer index are summed afterwards in a fixed order. No atomics:
 // every run gives identical bits.
+//
+// FP32 passes (the mixed-precision inner iterations) use the staged form:
+// each task's index words, contiguous in memory, stream through a ring of
+// shared-memory buffers by bulk asynchronous copies (cp.async.bulk completing
+// on mbarriers), so the HBM stream never waits on the gathers; the buffers
+// hold chunks of whole pieces (at most kChunkWords words), consumed by four
+// independent teams of 256 threads. Every thread of a team first sums the 8
+// offsets of one word of the chunk, then every piece sums its words' partial
+// sums in order: the same operations in the same order as the lane-per-piece
+// form, so both forms give identical bits.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
+#include "tc_common.cuh"
 
 namespace rr {
 
 namespace {
 
 constexpr int kSliceThreads = 1024;
+constexpr int kTeams = 4;                            // independent teams of a CTA
+constexpr int kTeamThreads = kSliceThreads / kTeams; // 256 threads (8 warps) per team
+constexpr int kChunkWords = kTeamThreads;            // words of one staged chunk (4 KiB), one per thread
+constexpr int kStagesW = 4;                          // stages in each team's ring
+constexpr int kStagePtrs = kChunkWords + 8;          // staged piece pointers / slots per stage
+constexpr int kStageSmem = 16 * kChunkWords + 8 * kStagePtrs + 32;   // words, pointers, slots, meta
+constexpr int kTeamSmem = 4 * kChunkWords + kStagesW * kStageSmem + 8 * kStagesW;
 
 // one thread per (outer o, slice b): entry range of the segment by binary search
 __global__ void k_seg_bounds(int64_t n_outer, int32_t nb, int32_t W,
@@ -128,6 +148,32 @@ __global__ void k_tasks(int32_t nb, int32_t T, int64_t n_outer, const int64_t *_
   }
 }
 
+// The pieces of each task in order of decreasing length (counting sort on the
+// word count, capped at the piece limit), so that the 32 lanes of a warp,
+// which take 32 consecutive entries, sum pieces of about the same length.
+// Within one length the order is that of the atomics; a piece's sum does not
+// depend on where it is processed, so results are unaffected.
+__global__ void k_order_pieces(const int32_t *__restrict__ task_p, const int32_t *__restrict__ pw,
+                               int32_t *__restrict__ order) {
+  __shared__ int32_t cnt[kPieceWords + 1], cur[kPieceWords + 1];
+  const int32_t p0 = task_p[blockIdx.x], p1 = task_p[blockIdx.x + 1];
+  for (int i = threadIdx.x; i <= kPieceWords; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  for (int32_t p = p0 + threadIdx.x; p < p1; p += blockDim.x)
+    atomicAdd(&cnt[min(pw[p + 1] - pw[p], kPieceWords)], 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t run = p0;
+    for (int len = kPieceWords; len >= 0; --len) {
+      cur[len] = run;
+      run += cnt[len];
+    }
+  }
+  __syncthreads();
+  for (int32_t p = p0 + threadIdx.x; p < p1; p += blockDim.x)
+    order[atomicAdd(&cur[min(pw[p + 1] - pw[p], kPieceWords)], 1)] = p;
+}
+
 // Pre-pass: the gathered vector, once per pass, in the accumulation type T
 // (FP64, or FP32 for the mixed-precision inner iterations). v = x, or
 // (kCombine) the per-index sums of the previous pass's slots.
@@ -193,13 +239,18 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather(
   // together, so four independent 16-byte loads are in flight per lane
   constexpr int kILP = 4;
   for (int32_t pb = p0 + threadIdx.x; pb < p1; pb += kILP * kSliceThreads) {
-    int32_t w0[kILP], w1[kILP];
+    int32_t pp[kILP], w0[kILP], w1[kILP];
     uint4 first[kILP];
 #pragma unroll
     for (int u = 0; u < kILP; ++u) {
       const int32_t p = pb + u * kSliceThreads;
-      w0[u] = p < p1 ? __ldg(P.pw + p) : 0;
-      w1[u] = p < p1 ? __ldg(P.pw + p + 1) : 0;
+      pp[u] = p < p1 ? __ldg(P.order + p) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kILP; ++u) {
+      const int32_t p = pb + u * kSliceThreads;
+      w0[u] = p < p1 ? __ldg(P.pw + pp[u]) : 0;
+      w1[u] = p < p1 ? __ldg(P.pw + pp[u] + 1) : 0;
     }
 #pragma unroll
     for (int u = 0; u < kILP; ++u) first[u] = w0[u] < w1[u] ? __ldg(P.idx + w0[u]) : pad;
@@ -218,7 +269,184 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather(
         for (int k = 1; k < 4; ++k)
           if (w + k < w1[u]) acc += gather8(xs, q[k]);
       }
-      out_psum[__ldg(P.slot + p)] = (double)acc;
+      out_psum[__ldg(P.slot + pp[u])] = (double)acc;
+    }
+  }
+}
+
+// The staged gather (see the file comment). The CTA's 32 warps form kTeams
+// independent teams of 8 warps; team j consumes chunks j, j + kTeams, ... of
+// the task through its own ring of kStagesW stages and syncs only its own 256
+// threads (named barrier 1 + j), so one team's waits overlap the others' work.
+// A stage holds the chunk's index words, its pieces' word pointers and slots
+// (both copied as 16-byte aligned supersets of the chunk's range) and the
+// chunk's metadata, written by the team's producer thread before it issues
+// the copies: a consumer touches no global memory but the piece sums it
+// stores. Waits on the mbarriers are bounded: on expiry the CTA records
+// DEV_TIMEOUT, every team stops, waits (bounded) for the copies it issued and
+// returns.
+struct StageMeta {
+  int32_t pa, pb;   // pieces [pa, pb) of the chunk
+  int32_t wa, nw;   // its words [wa, wa + nw)
+  int32_t pal;      // first piece of the staged pointer/slot range (pa rounded down to 4)
+  int32_t pad[3];
+};
+
+__device__ __forceinline__ void team_sync(int team) {
+  asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(kTeamThreads) : "memory");
+}
+
+__global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather_staged(
+    SlicedView P, const int32_t *__restrict__ chunk_p, const int32_t *__restrict__ chunk_w,
+    const int32_t *__restrict__ task_c, const float *__restrict__ xq,
+    double *__restrict__ out_psum, const int32_t *__restrict__ stop, int32_t *err) {
+  if (stop && *stop) return;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int slice_floats = (P.W + 1 + 3) & ~3;
+  const int team = threadIdx.x / kTeamThreads, tt = threadIdx.x % kTeamThreads;
+  float *xs = reinterpret_cast<float *>(smem_raw);
+  unsigned char *team_base = smem_raw + sizeof(float) * slice_floats + (size_t)team * kTeamSmem;
+  float *wsum = reinterpret_cast<float *>(team_base);
+  unsigned char *stage0 = team_base + sizeof(float) * kChunkWords;
+  uint64_t *full = reinterpret_cast<uint64_t *>(stage0 + (size_t)kStagesW * kStageSmem);
+  int32_t *abort_flag = reinterpret_cast<int32_t *>(smem_raw + sizeof(float) * slice_floats +
+                                                    (size_t)kTeams * kTeamSmem);
+  auto words_of = [&](int s) { return reinterpret_cast<uint4 *>(stage0 + (size_t)s * kStageSmem); };
+  auto pw_of = [&](int s) {
+    return reinterpret_cast<int32_t *>(stage0 + (size_t)s * kStageSmem + 16 * kChunkWords);
+  };
+  auto slot_of = [&](int s) { return pw_of(s) + kStagePtrs; };
+  auto meta_of = [&](int s) { return reinterpret_cast<StageMeta *>(slot_of(s) + kStagePtrs); };
+
+  const int task = blockIdx.x;
+  const int32_t b = P.task_slice[task];
+  const int32_t c0 = task_c[task], nch = task_c[task + 1] - c0;
+  // this team's chunks: c0 + team + kTeams q, q = 0 .. nq-1
+  const int nq = nch > team ? (nch - team + kTeams - 1) / kTeams : 0;
+
+  // producer (tt == 0): the metadata of the next chunk to issue, loaded ahead
+  int32_t m_pa = 0, m_pb = 0, m_wa = 0, m_wb = 0;
+  auto load_meta = [&](int q) {
+    const int32_t c = c0 + team + kTeams * q;
+    m_pa = chunk_p[c];
+    m_pb = chunk_p[c + 1];
+    m_wa = chunk_w[c];
+    m_wb = chunk_w[c + 1];
+  };
+  auto issue = [&](int q) {   // the team's chunk q into stage q % kStagesW, metadata in m_*
+    const int s = q % kStagesW;
+    const int32_t pal = m_pa & ~3;
+    const int32_t pend = (m_pb + 1 + 3) & ~3;   // pointers [pal, pend) cover pw[pa..pb]
+    const int32_t send = (m_pb + 3) & ~3;       // slots [pal, send) cover slot[pa..pb-1]
+    StageMeta *m = meta_of(s);
+    m->pa = m_pa;
+    m->pb = m_pb;
+    m->wa = m_wa;
+    m->nw = m_wb - m_wa;
+    m->pal = pal;
+    const uint32_t wbytes = (uint32_t)(m_wb - m_wa) * 16u;
+    const uint32_t pbytes = (uint32_t)(pend - pal) * 4u, sbytes = (uint32_t)(send - pal) * 4u;
+    uint64_t *bar = &full[s];
+    tc::mbar_expect_tx(bar, wbytes + pbytes + sbytes);
+    tc::bulk_load(words_of(s), P.idx + m_wa, wbytes, bar);
+    tc::bulk_load(pw_of(s), P.pw + pal, pbytes, bar);
+    tc::bulk_load(slot_of(s), P.slot + pal, sbytes, bar);
+  };
+
+  if (threadIdx.x == 0) *abort_flag = 0;
+  int issued = min(kStagesW, nq);
+  if (tt == 0) {
+    for (int s = 0; s < kStagesW; ++s) tc::mbar_init(&full[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int q = 0; q < issued; ++q) {
+      load_meta(q);
+      issue(q);
+    }
+    if (issued < nq) load_meta(issued);
+  }
+  // the vector slice, while the first chunks are in flight
+  const int64_t base = (int64_t)b * P.W;
+  const int64_t width = min((int64_t)P.W, P.n_inner - base);
+  for (int i = threadIdx.x; i <= P.W; i += kSliceThreads) xs[i] = i < width ? xq[base + i] : 0.0f;
+  __syncthreads();
+
+  int q = 0;
+  for (; q < nq; ++q) {
+    const int s = q % kStagesW;
+    const bool ok = tc::mbar_wait(&full[s], (uint32_t)((q / kStagesW) & 1), abort_flag);
+    if (!ok) {
+      set_dev_error(err, DEV_TIMEOUT);
+      atomicExch(abort_flag, 1);
+    }
+    const StageMeta m = *meta_of(s);
+    if (ok && tt < m.nw) {
+      const uint4 w = words_of(s)[tt];
+      wsum[tt] = ((xs[w.x & 0xffffu] + xs[w.x >> 16]) + (xs[w.y & 0xffffu] + xs[w.y >> 16])) +
+                 ((xs[w.z & 0xffffu] + xs[w.z >> 16]) + (xs[w.w & 0xffffu] + xs[w.w >> 16]));
+    }
+    team_sync(team);
+    if (*(volatile int32_t *)abort_flag) break;
+    const int32_t *pws = pw_of(s) - m.pal, *sls = slot_of(s) - m.pal;
+    for (int32_t p = m.pa + tt; p < m.pb; p += kTeamThreads) {
+      const int32_t w0 = pws[p] - m.wa, w1 = pws[p + 1] - m.wa;
+      float acc = wsum[w0];
+      for (int32_t w = w0 + 1; w < w1; ++w) acc += wsum[w];
+      out_psum[sls[p]] = (double)acc;
+    }
+    team_sync(team);   // the stage and wsum are free again
+    if (tt == 0 && issued < nq) {
+      tc::fence_proxy_async_smem();
+      issue(issued);
+      ++issued;
+      if (issued < nq) load_meta(issued);
+    }
+  }
+  if (tt == 0 && *(volatile int32_t *)abort_flag) {
+    // copies issued but not consumed (chunks q..issued-1 of this team) must
+    // land before the CTA's shared memory is released
+    const int32_t never = 0;
+    for (int j = q; j < issued; ++j)
+      (void)tc::mbar_wait(&full[j % kStagesW], (uint32_t)((j / kStagesW) & 1), &never);
+  }
+}
+
+// Chunks of whole pieces of at most kChunkWords words, per task (one thread
+// per task scans its pieces in order). count: chunks of each task; fill: the
+// first piece of every chunk (chunk_p[total] = npieces).
+__global__ void k_chunk_count(int32_t ntasks, const int32_t *__restrict__ task_p,
+                              const int32_t *__restrict__ pw, int64_t *__restrict__ cnt) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntasks; t += gridDim.x * blockDim.x) {
+    int64_t n = 0;
+    int32_t start = -1;
+    for (int32_t p = task_p[t]; p < task_p[t + 1]; ++p) {
+      if (start < 0 || pw[p + 1] - start > kChunkWords) {
+        start = pw[p];
+        ++n;
+      }
+    }
+    cnt[t] = n;
+  }
+}
+
+__global__ void k_chunk_fill(int32_t ntasks, const int32_t *__restrict__ task_p,
+                             const int32_t *__restrict__ pw, const int64_t *__restrict__ off,
+                             int32_t *__restrict__ chunk_p, int32_t *__restrict__ chunk_w,
+                             int32_t *__restrict__ task_c, int64_t total, int32_t npieces) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntasks; t += gridDim.x * blockDim.x) {
+    int64_t n = off[t];
+    task_c[t] = (int32_t)n;
+    int32_t start = -1;
+    for (int32_t p = task_p[t]; p < task_p[t + 1]; ++p) {
+      if (start < 0 || pw[p + 1] - start > kChunkWords) {
+        start = pw[p];
+        chunk_w[n] = start;
+        chunk_p[n++] = p;
+      }
+    }
+    if (t == ntasks - 1) {
+      task_c[ntasks] = (int32_t)total;
+      chunk_p[total] = npieces;
+      chunk_w[total] = pw[npieces];
     }
   }
 }
@@ -302,6 +530,15 @@ template <typename T>
 size_t slice_smem(int32_t W) { return sizeof(T) * ((size_t)W + 1); }
 
 template <typename T>
+size_t staged_smem(int32_t W) {
+  return sizeof(float) * (size_t)((W + 1 + 3) & ~3) + (size_t)kTeams * kTeamSmem + 16;
+}
+
+size_t staged_smem(int32_t W) {
+  return sizeof(float) * (size_t)((W + 1 + 3) & ~3) + (size_t)kTeams * kTeamSmem + 16;
+}
+
+template <typename T>
 rr_status set_smem_attr() {
   static bool done = false;
   if (!done) {
@@ -323,6 +560,18 @@ rr_status gather_t(const SlicedPattern &P, const double *x, const SlicedPattern 
   else
     RR_LAUNCH((k_slice_prep<false, T>), grid_for(n, kThreads), kThreads, 0, st, n, x, nullptr,
               nullptr, xq, stop);
+  if (std::is_same<T, float>::value && P.chunk_p) {
+    const size_t smem = staged_smem(P.W);
+    static bool attr = false;
+    if (!attr) {   // the largest slice any pattern can have
+      RR_CUDA(cudaFuncSetAttribute(k_sliced_gather_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)staged_smem(kSliceMax)));
+      attr = true;
+    }
+    RR_LAUNCH(k_sliced_gather_staged, P.ntasks, kSliceThreads, smem, st, P.view(), P.chunk_p,
+              P.chunk_w, P.task_c, reinterpret_cast<const float *>(xq), P.psum, stop, P.err);
+    return RR_OK;
+  }
   RR_TRY(set_smem_attr<T>());
   RR_LAUNCH(k_sliced_gather<T>, P.ntasks, kSliceThreads, slice_smem<T>(P.W), st, P.view(), xq,
             P.psum, stop);
@@ -332,8 +581,9 @@ rr_status gather_t(const SlicedPattern &P, const double *x, const SlicedPattern 
 }  // namespace
 
 rr_status sliced_build(int64_t n_outer, int64_t n_inner, const int64_t *outer_ptr,
-                       const int32_t *inner, SlicedPattern &P, cudaStream_t st) {
+                       const int32_t *inner, SlicedPattern &P, int32_t *err, cudaStream_t st) {
   P = SlicedPattern{};
+  P.err = err;
   P.n_outer = n_outer;
   P.n_inner = n_inner;
   P.nb = (int32_t)std::max<int64_t>(1, (n_inner + kSliceMax - 1) / kSliceMax);
@@ -364,8 +614,9 @@ rr_status sliced_build(int64_t n_outer, int64_t n_inner, const int64_t *outer_pt
       rr_set_error("sliced pattern too large");
       return RR_UNSUPPORTED;
     }
-    RR_CUDA(cudaMalloc(&P.pw, sizeof(int32_t) * (P.npieces + 1)));
-    RR_CUDA(cudaMalloc(&P.slot, sizeof(int32_t) * std::max<int64_t>(1, P.npieces)));
+    // +8 entries: the staged gather copies 16-byte aligned supersets of piece ranges
+    RR_CUDA(cudaMalloc(&P.pw, sizeof(int32_t) * (P.npieces + 1 + 8)));
+    RR_CUDA(cudaMalloc(&P.slot, sizeof(int32_t) * (P.npieces + 8)));
     RR_CUDA(cudaMalloc(&P.slot_ptr, sizeof(int32_t) * (n_outer + 1)));
     RR_CUDA(cudaMalloc(&P.idx, 16 * std::max<int64_t>(1, P.nwords)));
     RR_CUDA(cudaMalloc(&P.psum, sizeof(double) * std::max<int64_t>(1, P.npieces)));
@@ -384,6 +635,35 @@ rr_status sliced_build(int64_t n_outer, int64_t n_inner, const int64_t *outer_pt
     RR_CUDA(cudaMalloc(&P.task_p, sizeof(int32_t) * (P.ntasks + 1)));
     RR_LAUNCH(k_tasks, grid_for(P.ntasks + 1, kThreads), kThreads, 0, st, P.nb,
               P.tasks_per_slice, n_outer, word_off, piece_off, P.pw, P.task_slice, P.task_p);
+    RR_CUDA(cudaMalloc(&P.order, sizeof(int32_t) * std::max<int64_t>(1, P.npieces)));
+    RR_LAUNCH(k_order_pieces, P.ntasks, kThreads, 0, st, P.task_p, P.pw, P.order);
+    // chunks of the staged (FP32) gather, when its shared memory fits
+    if (staged_smem(P.W) <= 227 * 1024) {
+      int64_t *cbuf = nullptr;
+      const int64_t nt1 = (int64_t)P.ntasks + 1;
+      RR_CUDA(cudaMalloc(&cbuf, sizeof(int64_t) * (2 * nt1 + scan_scratch_len(nt1) + 8)));
+      int64_t *ccnt = cbuf, *coff = cbuf + nt1, *cscr = cbuf + 2 * nt1;
+      rr_status cs = RR_OK;
+      auto chunks = [&]() -> rr_status {
+        RR_LAUNCH(k_chunk_count, grid_for(P.ntasks, kThreads), kThreads, 0, st, P.ntasks, P.task_p,
+                  P.pw, ccnt);
+        RR_TRY(scan_exclusive(ccnt, coff, P.ntasks, cscr, st));
+        int64_t nch = 0;
+        RR_CUDA(cudaMemcpyAsync(&nch, coff + P.ntasks, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        RR_CUDA(cudaStreamSynchronize(st));
+        P.n_chunks = nch;
+        RR_CUDA(cudaMalloc(&P.chunk_p, sizeof(int32_t) * (nch + 1)));
+        RR_CUDA(cudaMalloc(&P.chunk_w, sizeof(int32_t) * (nch + 1)));
+        RR_CUDA(cudaMalloc(&P.task_c, sizeof(int32_t) * (P.ntasks + 1)));
+        RR_LAUNCH(k_chunk_fill, grid_for(P.ntasks, kThreads), kThreads, 0, st, P.ntasks, P.task_p,
+                  P.pw, coff, P.chunk_p, P.chunk_w, P.task_c, nch, (int32_t)P.npieces);
+        RR_CUDA(cudaStreamSynchronize(st));
+        return RR_OK;
+      };
+      cs = chunks();
+      cudaFree(cbuf);
+      RR_TRY(cs);
+    }
     RR_CUDA(cudaStreamSynchronize(st));
     return RR_OK;
   };
@@ -401,6 +681,10 @@ void sliced_free(SlicedPattern &P) {
   cudaFree(P.psum);
   cudaFree(P.task_slice);
   cudaFree(P.task_p);
+  cudaFree(P.order);
+  cudaFree(P.chunk_p);
+  cudaFree(P.chunk_w);
+  cudaFree(P.task_c);
   cudaFree(P.xq);
   P = SlicedPattern{};
 }

@@ -57,7 +57,7 @@ struct KmeansBuffers {
 };
 rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                         const int64_t *col_ptr, const int32_t *row_idx, int32_t k, uint64_t seed,
-                        KmeansBuffers &b, cudaStream_t st);
+                        KmeansBuffers &b, cudaStream_t st, bool use_graph);
 // labels <- -1 except labels[centers[S]] = S; prev <- -1; D <- 0.
 rr_status kmeans_init_labels(int64_t F, int32_t k, KmeansBuffers &b, cudaStream_t st);
 // One Lloyd assignment step; on return (stream synchronised) *changes_host holds
@@ -127,6 +127,36 @@ struct CscEpilogue {
   const int32_t *stop;  // if non-null and *stop != 0 the kernels return at once
 };
 
+// ---- k_fcg.cu -----------------------------------------------------------
+// Flexible CG (Algorithm 3, m = 1) scalars; see k_fcg.cu.
+struct FcgScalars {
+  double rr;         // ||r||^2 after the last update
+  double bnorm;      // ||b||
+  double target;     // tol * ||b||
+  double pq_prev;    // <p, A p> of the previous direction
+  int32_t iter, converged, nonfinite, first, limit;
+  int32_t fallbacks; // learned steps redone with the Cholesky coarse solve
+  int32_t skip_fb;   // 0 while the current step is being redone (fallback pass), else 1
+  int32_t learned;   // 1 if the coarse correction is the network's
+};
+rr_status fcg_dot(int64_t F, const double *a, const double *b, double *part, const int32_t *stop,
+                  cudaStream_t st);
+rr_status fcg_direction(int64_t F, const double *part_zq, const FcgScalars *S, const double *z,
+                        const double *p_prev, double *p, const int32_t *stop, cudaStream_t st);
+rr_status fcg_dots(int64_t F, const double *p, const double *r, const double *q, double *part3,
+                   const int32_t *stop, cudaStream_t st);
+rr_status fcg_decide(const double *part_rz, const double *part_pq, const double *part3,
+                     FcgScalars *S, cudaStream_t st);
+rr_status fcg_update(int64_t F, const double *part_pq, const double *part3, const double *p,
+                     const double *q, double *w, double *r, double omega, const double *d,
+                     double *z1, double *p_prev, double *q_prev, double *part_rr,
+                     const FcgScalars *S, cudaStream_t st);
+rr_status fcg_finish(const double *part_rr, const double *part_pq, FcgScalars *S, double *history,
+                     int32_t hist_cap, cudaStream_t st);
+rr_status fcg_start(const double *bb_part, int n_bb, const double *rr_part, double tol,
+                    int32_t set_bnorm, int32_t learned, FcgScalars *S, cudaStream_t st);
+rr_status fcg_condition(cudaGraphConditionalHandle hc, const FcgScalars *S, cudaStream_t st);
+
 // ---- k_sliced.cu --------------------------------------------------------
 // Sliced binary pattern (see k_sliced.cu): the gathered dimension (n_inner)
 // cut into nb slices of W <= kSliceMax entries, 16-bit offsets in 16-byte
@@ -142,6 +172,7 @@ struct SlicedView {
   const uint4 *idx;
   const int32_t *task_slice;
   const int32_t *task_p;
+  const int32_t *order;
 };
 struct SlicedPattern {
   int64_t n_outer = 0, n_inner = 0, nwords = 0, npieces = 0;
@@ -153,12 +184,20 @@ struct SlicedPattern {
   double *psum = nullptr;        // [npieces]   piece sums
   int32_t *task_slice = nullptr; // [ntasks]
   int32_t *task_p = nullptr;     // [ntasks+1]
+  int32_t *order = nullptr;      // [npieces]   the pieces of each task, longest first
+  int64_t n_chunks = 0;          // chunks of whole pieces of the staged FP32 gather (0: none)
+  int32_t *chunk_p = nullptr;    // [n_chunks+1] first piece of every chunk
+  int32_t *chunk_w = nullptr;    // [n_chunks+1] first word of every chunk
+  int32_t *task_c = nullptr;     // [ntasks+1]  chunks of each task
+  int32_t *err = nullptr;        // device error word (DEV_TIMEOUT from a bounded wait)
   void *xq = nullptr;            // [n_inner]   the gathered vector in the accumulation type
-  SlicedView view() const { return SlicedView{W, n_inner, pw, slot, idx, task_slice, task_p}; }
+  SlicedView view() const {
+    return SlicedView{W, n_inner, pw, slot, idx, task_slice, task_p, order};
+  }
 };
 // outer_ptr/inner: a pattern with inner indices ascending within each outer index.
 rr_status sliced_build(int64_t n_outer, int64_t n_inner, const int64_t *outer_ptr,
-                       const int32_t *inner, SlicedPattern &P, cudaStream_t st);
+                       const int32_t *inner, SlicedPattern &P, int32_t *err, cudaStream_t st);
 void sliced_free(SlicedPattern &P);
 // piece sums of P against x (or, when `in` is given, against the per-index
 // sums of in's slots: the output of a previous pass); fp32: accumulate in FP32
@@ -237,5 +276,11 @@ rr_status copy_f64(double *dst, const double *src, int64_t n, cudaStream_t st);
 rr_status loop_condition(cudaGraphConditionalHandle hc, const PcgScalars *S, cudaStream_t st);
 // dst = src (or zero when src == nullptr) for vectors of F entries; device helper kernels.
 rr_status axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t st);
+
+// ---- k_mlp.cu -----------------------------------------------------------
+// e_c = ||r_c|| net(r_c / ||r_c||) from the restriction's item sums.
+rr_status mlp_coarse(const rr_mlp *m, const RestrictPlan &plan, const double *s, double *ec,
+                     const int32_t *stop, cudaStream_t st);
+int32_t mlp_k(const rr_mlp *m);
 
 }  // namespace rr

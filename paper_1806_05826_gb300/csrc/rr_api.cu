@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "handle.h"
 #include "kernels.h"
 
 static thread_local char g_err[1024] = "";
@@ -27,35 +28,6 @@ void rr_set_error(const char *fmt, ...) {
 namespace {
 
 using rr::kThreads;
-
-struct DevArena {
-  std::vector<void *> ptrs;
-  template <class T>
-  rr_status alloc(T **p, size_t n) {
-    void *q = nullptr;
-    const size_t bytes = sizeof(T) * (n ? n : 1);
-    if (cudaMalloc(&q, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      rr_set_error("cudaMalloc of %zu bytes failed", bytes);
-      return RR_OOM;
-    }
-    ptrs.push_back(q);
-    *p = static_cast<T *>(q);
-    return RR_OK;
-  }
-  void release(void *p) {
-    for (auto &q : ptrs)
-      if (q == p) {
-        cudaFree(q);
-        q = nullptr;
-      }
-  }
-  void free_all() {
-    for (void *q : ptrs)
-      if (q) cudaFree(q);
-    ptrs.clear();
-  }
-};
 
 // d_i = ||x_i||^2 + lambda (column nnz for binary X); ratio_i = (sum_j |A_ij|) / d_i
 // with sum_j |(X^T X)_ij| = gsum_i (an exact integer). The maximum ratio is
@@ -87,57 +59,6 @@ inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 }  // namespace
 
-struct rr_handle {
-  cudaStream_t st = nullptr;
-  rr_options opt{};
-  int64_t N = 0, F = 0, nnz = 0;
-  int32_t k_req = 0, k_eff = 0, kmeans_iters = 0;
-  double lambda = 0.0, omega = 1.0, setup_ms = 0.0;
-  // X and its transposed copy
-  int64_t *row_ptr = nullptr;
-  int32_t *col_idx = nullptr;
-  int64_t *col_ptr = nullptr;
-  int32_t *row_idx = nullptr;
-  // clustering
-  int32_t *labels = nullptr;
-  int32_t *centers = nullptr;
-  int64_t *n_S = nullptr;
-  int64_t *cl_ptr = nullptr;
-  int32_t *members = nullptr;
-  double *s = nullptr;
-  // coarse level
-  double *G = nullptr, *Ac = nullptr, *Lw = nullptr, *Linv = nullptr, *Ainv = nullptr;
-  // smoother
-  double *d = nullptr;
-  int64_t *gsum = nullptr;   // sum_j |(X^T X)_ij| = sum of the row lengths over column i
-  double *omega_dev = nullptr;
-  unsigned long long *max_bits = nullptr;
-  rr::RestrictPlan rplan;
-  rr::SlicedPattern pcsr;   // X by row, vector v cut in feature slices
-  rr::SlicedPattern pcsc;   // X^T by column, vector u cut in row slices
-  // solve workspace
-  double *b = nullptr, *r = nullptr, *z1 = nullptr, *z2 = nullptr, *z = nullptr, *p = nullptr,
-         *q = nullptr, *r1 = nullptr, *u = nullptr, *rc = nullptr, *ec = nullptr, *rt = nullptr;
-  double *part_rz = nullptr, *part_pq = nullptr, *part_rr = nullptr, *part_bb = nullptr;
-  double *scal = nullptr;
-  double *w_int = nullptr;         // the iterate (graphs capture fixed pointers)
-  cudaStream_t cap_stream = nullptr;
-  cudaGraph_t loop_graph = nullptr;
-  cudaGraphExec_t loop_exec = nullptr;
-  int32_t *limit_host = nullptr;
-  int64_t body_kernels = 0;
-  double phase_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  bool gram_on_tensor_cores = false;
-  rr::PcgScalars *S = nullptr;
-  rr::PcgScalars *S_host = nullptr;
-  double *scal_host = nullptr;
-  double *history = nullptr;
-  int32_t hist_cap = 0;
-  int32_t *err = nullptr;
-  int32_t *err_host = nullptr;
-  int n_parts = 0;
-  DevArena mem;
-};
 
 namespace {
 
@@ -305,7 +226,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
                             cudaMemcpyHostToDevice, st));
   } else {
     RR_TRY(rr::kmeanspp_seed(N, F, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx, k,
-                             h->opt.seed, kb, st));
+                             h->opt.seed, kb, st, h->opt.use_graphs != 0));
   }
   RR_TRY(phase(2));
   RR_TRY(rr::kmeans_init_labels(F, k, kb, st));
@@ -407,8 +328,8 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
 
   RR_TRY(phase(6));
   // ---- sliced patterns of X and X^T and the solve workspace
-  RR_TRY(rr::sliced_build(N, F, h->row_ptr, h->col_idx, h->pcsr, st));
-  RR_TRY(rr::sliced_build(F, N, h->col_ptr, h->row_idx, h->pcsc, st));
+  RR_TRY(rr::sliced_build(N, F, h->row_ptr, h->col_idx, h->pcsr, h->err, st));
+  RR_TRY(rr::sliced_build(F, N, h->col_ptr, h->row_idx, h->pcsc, h->err, st));
   h->n_parts = rr::kVecGrid;
   for (double **v : {&h->b, &h->r, &h->z1, &h->z2, &h->z, &h->p, &h->q, &h->r1, &h->rt, &h->w_int})
     RR_TRY(m.alloc(v, F));
@@ -506,7 +427,6 @@ rr_status build_loop_graph(rr_handle *h) {
   destroy_graph(h);
   cudaGraph_t g = nullptr;
   RR_CUDA(cudaGraphCreate(&g, 0));
-  h->loop_graph = g;
   cudaGraphConditionalHandle hc;
   RR_CUDA(cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams cp{};
@@ -526,11 +446,14 @@ rr_status build_loop_graph(rr_handle *h) {
   rr_launch_counter = l0;
   cudaGraph_t captured = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(cs, &captured);
-  RR_TRY(s);
-  if (ec != cudaSuccess) {
+  if (s != RR_OK || ec != cudaSuccess) {
+    cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (s != RR_OK) return s;
     rr_set_error("graph capture failed: %s", cudaGetErrorString(ec));
     return RR_CUDA_ERROR;
   }
+  h->loop_graph = g;
   RR_CUDA(cudaGraphInstantiate(&h->loop_exec, g, 0));
   return RR_OK;
 }
@@ -574,11 +497,9 @@ rr_status run_iterations(rr_handle *h, int32_t limit) {
   return RR_OK;
 }
 
-rr_status solve_impl(rr_handle *h, const double *y, double *w, double tol, rr_info *info) {
-  cudaStream_t st = h->st;
+// b = X^T y; w = 0; r = b; ||b||; z1 = omega D^-1 r (no synchronisation).
+rr_status solve_start(rr_handle *h, const double *y, double tol, cudaStream_t st) {
   const int64_t F = h->F;
-  const bool twolevel = h->opt.solver == RR_SOLVER_TWOLEVEL;
-  // b = X^T y; w = 0; r = b
   rr::CscEpilogue rhs{rr::CSC_RHS, 0.0, 0.0, nullptr, nullptr, nullptr, h->b, nullptr, nullptr};
   RR_TRY(rr::sliced_gather(h->pcsc, y, nullptr, nullptr, st));
   RR_TRY(rr::sliced_epilogue(h->pcsc, rhs, st));
@@ -587,7 +508,26 @@ rr_status solve_impl(rr_handle *h, const double *y, double *w, double tol, rr_in
   RR_TRY(rr::dot_parts(F, h->b, h->b, h->part_bb, st));
   RR_CUDA(cudaMemsetAsync(h->S, 0, sizeof(rr::PcgScalars), st));
   RR_TRY(rr::pcg_start(h->part_bb, rr::kVecGrid, h->part_bb, rr::kVecGrid, tol, 1, h->S, st));
-  if (twolevel) RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st));
+  if (h->opt.solver == RR_SOLVER_TWOLEVEL)
+    RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st));
+  return RR_OK;
+}
+
+// Refinement: continue from w with the true residual rt and a fresh direction.
+rr_status solve_restart(rr_handle *h, double tol, cudaStream_t st) {
+  const int64_t F = h->F;
+  RR_TRY(rr::copy_f64(h->r, h->rt, F, st));
+  RR_TRY(rr::dot_parts(F, h->r, h->r, h->part_rr, st));
+  RR_TRY(rr::pcg_start(h->part_bb, 1, h->part_rr, rr::kVecGrid, tol, 0, h->S, st));
+  if (h->opt.solver == RR_SOLVER_TWOLEVEL)
+    RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st));
+  return RR_OK;
+}
+
+rr_status solve_impl(rr_handle *h, const double *y, double *w, double tol, rr_info *info) {
+  cudaStream_t st = h->st;
+  const int64_t F = h->F;
+  RR_TRY(solve_start(h, y, tol, st));
   RR_CUDA(cudaMemcpyAsync(h->S_host, h->S, sizeof(rr::PcgScalars), cudaMemcpyDeviceToHost, st));
   RR_CUDA(cudaStreamSynchronize(st));
 
@@ -617,10 +557,7 @@ rr_status solve_impl(rr_handle *h, const double *y, double *w, double tol, rr_in
     }
     // refinement: continue from w with the true residual and a fresh direction
     ++restarts;
-    RR_TRY(rr::copy_f64(h->r, h->rt, F, st));
-    RR_TRY(rr::dot_parts(F, h->r, h->r, h->part_rr, st));
-    RR_TRY(rr::pcg_start(h->part_bb, 1, h->part_rr, rr::kVecGrid, tol, 0, h->S, st));
-    if (twolevel) RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st));
+    RR_TRY(solve_restart(h, tol, st));
   }
   RR_TRY(rr::copy_f64(w, h->w_int, F, st));
   RR_CUDA(cudaMemcpyAsync(h->S_host, h->S, sizeof(rr::PcgScalars), cudaMemcpyDeviceToHost, st));
@@ -633,6 +570,326 @@ rr_status solve_impl(rr_handle *h, const double *y, double *w, double tol, rr_in
     info->true_rel_res = Sh.bnorm > 0 ? sqrt(true_rr) / Sh.bnorm : 0.0;
   }
   return result;
+}
+
+// ---- flexible CG (Algorithm 3, m = 1) with the two-level cycle; the coarse
+// solve is the network's (net != NULL, with the Cholesky fallback pass) or
+// the Cholesky solve.
+rr_status fcg_reserve(rr_handle *h) {
+  if (h->Sf) return RR_OK;
+  RR_TRY(h->mem.alloc(&h->p_prev, h->F));
+  RR_TRY(h->mem.alloc(&h->q_prev, h->F));
+  RR_TRY(h->mem.alloc(&h->part_zq, rr::kVecGrid));
+  RR_TRY(h->mem.alloc(&h->part3, 3 * rr::kVecGrid));
+  RR_TRY(h->mem.alloc(&h->Sf, 1));
+  RR_CUDA(cudaMallocHost(&h->Sf_host, sizeof(rr::FcgScalars)));
+  return RR_OK;
+}
+
+// The cycle's second half from e_c: z2 = z1 + P e_c; z = z2 + omega D^-1 (r - A z2);
+// then the FCG direction p and q = A p with its dots. All kernels skip when *stop.
+rr_status fcg_tail(rr_handle *h, const int32_t *stop, bool fp32, cudaStream_t st) {
+  const int64_t F = h->F;
+  RR_TRY(rr::prolong_add(F, h->labels, h->s, h->ec, h->z1, h->z2, stop, st));
+  rr::CscEpilogue post{rr::CSC_POST, h->lambda, h->omega, h->z2, h->r, h->d, h->z, h->part_rz, stop};
+  RR_TRY(op_apply(h, h->z2, post, stop, st, fp32));
+  RR_TRY(rr::fcg_dot(F, h->z, h->q_prev, h->part_zq, stop, st));
+  RR_TRY(rr::fcg_direction(F, h->part_zq, h->Sf, h->z, h->p_prev, h->p, stop, st));
+  rr::CscEpilogue ap{rr::CSC_PCG, h->lambda, h->omega, h->p, nullptr, nullptr, h->q, h->part_pq, stop};
+  RR_TRY(op_apply(h, h->p, ap, stop, st, fp32));
+  RR_TRY(rr::fcg_dots(F, h->p, h->r, h->q, h->part3, stop, st));
+  return RR_OK;
+}
+
+rr_status fcg_iteration(rr_handle *h, const rr_mlp *net, cudaStream_t st) {
+  const bool fp32 = h->opt.precision == RR_PREC_MIXED;
+  const int32_t *stop = &h->Sf->converged;
+  // pre-smoothing (z1 from the previous update), restriction
+  rr::CscEpilogue pre{rr::CSC_PRE, h->lambda, h->omega, h->z1, h->r, h->d, h->r1, nullptr, stop};
+  RR_TRY(op_apply(h, h->z1, pre, stop, st, fp32));
+  RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->r1, stop, st));
+  if (net) {
+    RR_TRY(rr::mlp_coarse(net, h->rplan, h->s, h->ec, stop, st));
+  } else {
+    RR_TRY(rr::coarse_matvec(h->k_eff, h->Ainv, h->rplan, h->s, nullptr, h->ec, stop, st));
+  }
+  RR_TRY(fcg_tail(h, stop, fp32, st));
+  if (net) {
+    // the step is checked before it is taken; a rejected learned step is
+    // redone with the Cholesky coarse solve (same restriction)
+    RR_TRY(rr::fcg_decide(h->part_rz, h->part_pq, h->part3, h->Sf, st));
+    const int32_t *fb = &h->Sf->skip_fb;
+    RR_TRY(rr::coarse_matvec(h->k_eff, h->Ainv, h->rplan, h->s, nullptr, h->ec, fb, st));
+    RR_TRY(fcg_tail(h, fb, fp32, st));
+  }
+  RR_TRY(rr::fcg_update(h->F, h->part_pq, h->part3, h->p, h->q, h->w_int, h->r, h->omega, h->d,
+                        h->z1, h->p_prev, h->q_prev, h->part_rr, h->Sf, st));
+  RR_TRY(rr::fcg_finish(h->part_rr, h->part_pq, h->Sf, h->history, h->hist_cap, st));
+  return RR_OK;
+}
+
+struct GraphExec {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t body = 0;
+  ~GraphExec() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (g) cudaGraphDestroy(g);
+  }
+};
+
+rr_status build_fcg_graph(rr_handle *h, const rr_mlp *net, GraphExec &G) {
+  RR_CUDA(cudaGraphCreate(&G.g, 0));
+  cudaGraphConditionalHandle hc;
+  RR_CUDA(cudaGraphConditionalHandleCreate(&hc, G.g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = hc;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  RR_CUDA(cudaGraphAddNode(&node, G.g, nullptr, nullptr, 0, &cp));
+  cudaStream_t cs = h->cap_stream;
+  RR_CUDA(cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal));
+  const int64_t l0 = rr_launch_counter;
+  rr_status s = fcg_iteration(h, net, cs);
+  if (s == RR_OK) s = rr::fcg_condition(hc, h->Sf, cs);
+  G.body = rr_launch_counter - l0;   // recorded, not launched
+  rr_launch_counter = l0;
+  cudaGraph_t captured = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(cs, &captured);
+  if (s != RR_OK || ec != cudaSuccess) {
+    cudaGraphDestroy(G.g);
+    G.g = nullptr;
+    cudaGetLastError();
+    if (s != RR_OK) return s;
+    rr_set_error("FCG graph capture failed: %s", cudaGetErrorString(ec));
+    return RR_CUDA_ERROR;
+  }
+  RR_CUDA(cudaGraphInstantiate(&G.exec, G.g, 0));
+  return RR_OK;
+}
+
+rr_status fcg_run(rr_handle *h, const rr_mlp *net, GraphExec *G, int32_t limit) {
+  cudaStream_t st = h->st;
+  h->Sf_host->limit = limit;
+  RR_CUDA(cudaMemcpyAsync(&h->Sf->limit, &h->Sf_host->limit, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  RR_CUDA(cudaMemcpyAsync(h->Sf_host, h->Sf, sizeof(rr::FcgScalars), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  const int32_t it0 = h->Sf_host->iter;
+  if (G) {
+    RR_CUDA(cudaGraphLaunch(G->exec, st));
+    RR_CUDA(cudaMemcpyAsync(h->Sf_host, h->Sf, sizeof(rr::FcgScalars), cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaStreamSynchronize(st));
+    rr_launch_counter += G->body * std::max<int64_t>(1, h->Sf_host->iter - it0);
+    return RR_OK;
+  }
+  const int32_t every = std::max(1, h->opt.check_every);
+  for (;;) {
+    for (int32_t c = 0; c < every; ++c) RR_TRY(fcg_iteration(h, net, st));
+    RR_CUDA(cudaMemcpyAsync(h->Sf_host, h->Sf, sizeof(rr::FcgScalars), cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaStreamSynchronize(st));
+    if (h->Sf_host->converged || h->Sf_host->iter >= limit) return RR_OK;
+  }
+}
+
+rr_status solve_fcg_impl(rr_handle *h, const rr_mlp *net, const double *y, double *w, double tol,
+                         rr_info *info) {
+  cudaStream_t st = h->st;
+  const int64_t F = h->F;
+  RR_TRY(fcg_reserve(h));
+  rr::CscEpilogue rhs{rr::CSC_RHS, 0.0, 0.0, nullptr, nullptr, nullptr, h->b, nullptr, nullptr};
+  RR_TRY(rr::sliced_gather(h->pcsc, y, nullptr, nullptr, st));
+  RR_TRY(rr::sliced_epilogue(h->pcsc, rhs, st));
+  RR_CUDA(cudaMemsetAsync(h->w_int, 0, sizeof(double) * F, st));
+  RR_CUDA(cudaMemsetAsync(h->p_prev, 0, sizeof(double) * F, st));
+  RR_CUDA(cudaMemsetAsync(h->q_prev, 0, sizeof(double) * F, st));
+  RR_TRY(rr::copy_f64(h->r, h->b, F, st));
+  RR_TRY(rr::dot_parts(F, h->b, h->b, h->part_bb, st));
+  RR_CUDA(cudaMemsetAsync(h->Sf, 0, sizeof(rr::FcgScalars), st));
+  RR_TRY(rr::fcg_start(h->part_bb, rr::kVecGrid, h->part_bb, tol, 1, net ? 1 : 0, h->Sf, st));
+  RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st));
+
+  GraphExec graph;
+  if (h->opt.use_graphs) RR_TRY(build_fcg_graph(h, net, graph));
+  const int32_t max_iter = h->opt.max_iter;
+  int32_t restarts = 0;
+  double true_rr = 0.0;
+  rr_status result = RR_OK;
+  for (;;) {
+    RR_TRY(fcg_run(h, net, h->opt.use_graphs ? &graph : nullptr, max_iter));
+    const rr::FcgScalars Sh = *h->Sf_host;
+    if (Sh.nonfinite) {
+      rr_set_error("rr_solve_fcg: non-finite residual or dot product");
+      result = RR_NONFINITE;
+      break;
+    }
+    RR_TRY(true_residual(h, h->w_int, &true_rr));
+    if (!isfinite(true_rr)) {
+      rr_set_error("rr_solve_fcg: non-finite true residual");
+      result = RR_NONFINITE;
+      break;
+    }
+    if (sqrt(true_rr) <= Sh.target) break;
+    if (Sh.iter >= max_iter || restarts >= h->opt.max_restarts) {
+      rr_set_error("rr_solve_fcg: not converged after %d iterations (%d restarts)", Sh.iter, restarts);
+      result = RR_NOT_CONVERGED;
+      break;
+    }
+    ++restarts;
+    RR_TRY(rr::copy_f64(h->r, h->rt, F, st));
+    RR_TRY(rr::dot_parts(F, h->r, h->r, h->part_rr, st));
+    RR_TRY(rr::fcg_start(h->part_bb, 1, h->part_rr, tol, 0, net ? 1 : 0, h->Sf, st));
+    RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st));
+  }
+  RR_TRY(rr::copy_f64(w, h->w_int, F, st));
+  RR_CUDA(cudaMemcpyAsync(h->Sf_host, h->Sf, sizeof(rr::FcgScalars), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  if (info) {
+    const rr::FcgScalars Sh = *h->Sf_host;
+    info->iters = Sh.iter;
+    info->restarts = restarts;
+    info->fallbacks = Sh.fallbacks;
+    info->rel_res = Sh.bnorm > 0 ? sqrt(Sh.rr) / Sh.bnorm : 0.0;
+    info->true_rel_res = Sh.bnorm > 0 ? sqrt(true_rr) / Sh.bnorm : 0.0;
+  }
+  return result;
+}
+
+// ---- several independent problems in one graph: the PCG loop of every
+// problem is a conditional while node of one parent graph, all of them
+// parallel branches, so the problems' kernels can run concurrently.
+struct ManyGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~ManyGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (g) cudaGraphDestroy(g);
+  }
+};
+
+rr_status build_many_graph(int32_t n, rr_handle *const *hs, ManyGraph &G, std::vector<int64_t> &body) {
+  RR_CUDA(cudaGraphCreate(&G.g, 0));
+  body.assign(n, 0);
+  for (int32_t i = 0; i < n; ++i) {
+    rr_handle *h = hs[i];
+    cudaGraphConditionalHandle hc;
+    RR_CUDA(cudaGraphConditionalHandleCreate(&hc, G.g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    RR_CUDA(cudaGraphAddNode(&node, G.g, nullptr, nullptr, 0, &cp));
+    cudaStream_t cs = h->cap_stream;
+    RR_CUDA(cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    const int64_t l0 = rr_launch_counter;
+    rr_status s = pcg_iteration(h, cs);
+    if (s == RR_OK) s = rr::loop_condition(hc, h->S, cs);
+    body[i] = rr_launch_counter - l0;   // recorded, not launched
+    rr_launch_counter = l0;
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &captured);
+    if (s != RR_OK || ec != cudaSuccess) {
+      cudaGraphDestroy(G.g);
+      G.g = nullptr;
+      cudaGetLastError();
+      if (s != RR_OK) return s;
+      rr_set_error("rr_solve_many: graph capture failed: %s", cudaGetErrorString(ec));
+      return RR_CUDA_ERROR;
+    }
+  }
+  RR_CUDA(cudaGraphInstantiate(&G.exec, G.g, 0));
+  return RR_OK;
+}
+
+rr_status solve_many_impl(int32_t n, rr_handle *const *hs, const double *const *ys,
+                          double *const *ws, double tol, cudaStream_t st, rr_info *infos) {
+  std::vector<int32_t> restarts(n, 0), done(n, 0);
+  std::vector<double> true_rr(n, 0.0);
+  std::vector<rr_status> result(n, RR_OK);
+  for (int32_t i = 0; i < n; ++i) {
+    RR_TRY(solve_start(hs[i], ys[i], tol, st));
+    hs[i]->S_host->limit = hs[i]->opt.max_iter;
+  }
+  ManyGraph G;
+  std::vector<int64_t> body;
+  RR_TRY(build_many_graph(n, hs, G, body));
+  for (;;) {
+    std::vector<int32_t> it0(n);
+    for (int32_t i = 0; i < n; ++i) {
+      rr_handle *h = hs[i];
+      *h->limit_host = h->opt.max_iter;
+      RR_CUDA(cudaMemcpyAsync(&h->S->limit, h->limit_host, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+      RR_CUDA(cudaMemcpyAsync(h->S_host, h->S, sizeof(rr::PcgScalars), cudaMemcpyDeviceToHost, st));
+    }
+    RR_CUDA(cudaStreamSynchronize(st));
+    for (int32_t i = 0; i < n; ++i) it0[i] = hs[i]->S_host->iter;
+    RR_CUDA(cudaGraphLaunch(G.exec, st));
+    for (int32_t i = 0; i < n; ++i)
+      RR_CUDA(cudaMemcpyAsync(hs[i]->S_host, hs[i]->S, sizeof(rr::PcgScalars), cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaStreamSynchronize(st));
+    bool any = false;
+    for (int32_t i = 0; i < n; ++i) {
+      rr_handle *h = hs[i];
+      rr_launch_counter += body[i] * std::max<int64_t>(1, h->S_host->iter - it0[i]);
+      if (done[i]) continue;
+      const rr::PcgScalars Sh = *h->S_host;
+      if (Sh.nonfinite) {
+        result[i] = RR_NONFINITE;
+        done[i] = 1;
+        continue;
+      }
+      RR_TRY(true_residual(h, h->w_int, &true_rr[i]));
+      if (!isfinite(true_rr[i])) {
+        result[i] = RR_NONFINITE;
+        done[i] = 1;
+      } else if (sqrt(true_rr[i]) <= Sh.target) {
+        done[i] = 1;
+      } else if (Sh.iter >= h->opt.max_iter || restarts[i] >= h->opt.max_restarts) {
+        result[i] = RR_NOT_CONVERGED;
+        done[i] = 1;
+      } else {
+        ++restarts[i];
+        RR_TRY(solve_restart(h, tol, st));
+        any = true;
+      }
+    }
+    if (!any) break;
+  }
+  rr_status worst = RR_OK;
+  for (int32_t i = 0; i < n; ++i) {
+    rr_handle *h = hs[i];
+    RR_TRY(rr::copy_f64(ws[i], h->w_int, h->F, st));
+    RR_CUDA(cudaMemcpyAsync(h->S_host, h->S, sizeof(rr::PcgScalars), cudaMemcpyDeviceToHost, st));
+    if (result[i] != RR_OK && worst != RR_NONFINITE) worst = result[i];
+  }
+  RR_CUDA(cudaStreamSynchronize(st));
+  for (int32_t i = 0; i < n; ++i) {
+    const rr_status e = check_dev_error(hs[i], "rr_solve_many");
+    if (e != RR_OK) return e;
+    if (!infos) continue;
+    rr_handle *h = hs[i];
+    const rr::PcgScalars Sh = *h->S_host;
+    rr_info &I = infos[i];
+    I.iters = Sh.iter;
+    I.restarts = restarts[i];
+    I.rel_res = Sh.bnorm > 0 ? sqrt(Sh.rr) / Sh.bnorm : 0.0;
+    I.true_rel_res = Sh.bnorm > 0 ? sqrt(true_rr[i]) / Sh.bnorm : 0.0;
+    I.k_eff = h->k_eff;
+    I.kmeans_iters = h->kmeans_iters;
+    I.omega = h->omega;
+    I.setup_ms = h->setup_ms;
+    I.gram_tensor_cores = h->gram_on_tensor_cores ? 1 : 0;
+    I.fallbacks = 0;
+    for (int j = 0; j < 8; ++j) I.setup_phase_ms[j] = h->phase_ms[j];
+  }
+  if (worst == RR_NOT_CONVERGED) rr_set_error("rr_solve_many: some problems did not reach tol");
+  if (worst == RR_NONFINITE) rr_set_error("rr_solve_many: non-finite values in some problems");
+  return worst;
 }
 
 }  // namespace
@@ -743,6 +1000,51 @@ rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info
   const auto t0 = std::chrono::steady_clock::now();
   const int64_t l0 = rr_launch_counter;
   rr_status s = solve_impl(h, y, w, tol, info);
+  if (s == RR_OK || s == RR_NOT_CONVERGED) {
+    const rr_status e = check_dev_error(h, "rr_solve");
+    if (e != RR_OK) s = e;
+  }
+  if (info) {
+    info->fallbacks = 0;
+    info->k_eff = h->k_eff;
+    info->kmeans_iters = h->kmeans_iters;
+    info->omega = h->omega;
+    info->setup_ms = h->setup_ms;
+    info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    info->launches = rr_launch_counter - l0;
+    info->gram_tensor_cores = h->gram_on_tensor_cores ? 1 : 0;
+    for (int i = 0; i < 8; ++i) info->setup_phase_ms[i] = h->phase_ms[i];
+  }
+  return s;
+}
+
+rr_status rr_solve_fcg(rr_handle *h, const rr_mlp *net, const double *y, double *w, double tol,
+                       rr_info *info) {
+  if (!h || !y || !w) {
+    rr_set_error("rr_solve_fcg: handle, y and w must not be NULL");
+    return RR_INVALID_ARG;
+  }
+  if (!(tol > 0.0 && tol < 1.0)) {
+    rr_set_error("rr_solve_fcg: tol must be in (0, 1)");
+    return RR_INVALID_ARG;
+  }
+  if (h->opt.solver != RR_SOLVER_TWOLEVEL) {
+    rr_set_error("rr_solve_fcg: the handle's solver must be RR_SOLVER_TWOLEVEL");
+    return RR_UNSUPPORTED;
+  }
+  if (net && rr::mlp_k(net) != h->k_eff) {
+    rr_set_error("rr_solve_fcg: the network's k (%d) differs from k_eff (%d)", rr::mlp_k(net),
+                 h->k_eff);
+    return RR_INVALID_ARG;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t l0 = rr_launch_counter;
+  if (info) memset(info, 0, sizeof(*info));
+  rr_status s = solve_fcg_impl(h, net, y, w, tol, info);
+  if (s == RR_OK || s == RR_NOT_CONVERGED) {
+    const rr_status e = check_dev_error(h, "rr_solve_fcg");
+    if (e != RR_OK) s = e;
+  }
   if (info) {
     info->k_eff = h->k_eff;
     info->kmeans_iters = h->kmeans_iters;
@@ -752,6 +1054,47 @@ rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info
     info->launches = rr_launch_counter - l0;
     info->gram_tensor_cores = h->gram_on_tensor_cores ? 1 : 0;
     for (int i = 0; i < 8; ++i) info->setup_phase_ms[i] = h->phase_ms[i];
+  }
+  return s;
+}
+
+rr_status rr_solve_many(int32_t nprob, rr_handle *const *hs, const double *const *ys,
+                        double *const *ws, double tol, void *stream, rr_info *infos) {
+  if (nprob < 1 || !hs || !ys || !ws || !(tol > 0.0 && tol < 1.0)) {
+    rr_set_error("rr_solve_many: nprob < 1, NULL arrays or tol not in (0, 1)");
+    return RR_INVALID_ARG;
+  }
+  for (int32_t i = 0; i < nprob; ++i) {
+    if (!hs[i] || !ys[i] || !ws[i]) {
+      rr_set_error("rr_solve_many: NULL handle, target or solution of problem %d", i);
+      return RR_INVALID_ARG;
+    }
+    for (int32_t j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) {
+        rr_set_error("rr_solve_many: problems %d and %d share a handle", j, i);
+        return RR_INVALID_ARG;
+      }
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const auto t0 = std::chrono::steady_clock::now();
+  const int64_t l0 = rr_launch_counter;
+  // every problem's work is issued on `stream` for the duration of the call
+  std::vector<cudaStream_t> saved(nprob);
+  for (int32_t i = 0; i < nprob; ++i) {
+    RR_CUDA(cudaStreamSynchronize(hs[i]->st));
+    saved[i] = hs[i]->st;
+    hs[i]->st = st;
+  }
+  if (infos) memset(infos, 0, sizeof(rr_info) * nprob);
+  const rr_status s = solve_many_impl(nprob, hs, ys, ws, tol, st, infos);
+  cudaStreamSynchronize(st);
+  for (int32_t i = 0; i < nprob; ++i) hs[i]->st = saved[i];
+  if (infos) {
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (int32_t i = 0; i < nprob; ++i) {
+      infos[i].solve_ms = ms;
+      infos[i].launches = rr_launch_counter - l0;
+    }
   }
   return s;
 }
@@ -830,6 +1173,8 @@ void rr_free(rr_handle *h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
   destroy_graph(h);
+  rr::batch_free(h->batch);
+  h->batch = nullptr;
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->limit_host) cudaFreeHost(h->limit_host);
   rr::restrict_free(h->rplan);
@@ -839,6 +1184,7 @@ void rr_free(rr_handle *h) {
   if (h->err_host) cudaFreeHost(h->err_host);
   if (h->S_host) cudaFreeHost(h->S_host);
   if (h->scal_host) cudaFreeHost(h->scal_host);
+  if (h->Sf_host) cudaFreeHost(h->Sf_host);
   delete h;
 }
 

@@ -48,7 +48,8 @@ class rr_info(ctypes.Structure):
                 ("rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double),
                 ("omega", ctypes.c_double), ("setup_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("launches", ctypes.c_int64),
-                ("gram_tensor_cores", ctypes.c_int32), ("setup_phase_ms", ctypes.c_double * 8)]
+                ("gram_tensor_cores", ctypes.c_int32), ("fallbacks", ctypes.c_int32),
+                ("setup_phase_ms", ctypes.c_double * 8)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
@@ -72,6 +73,23 @@ _SIGS = {
                                 ctypes.POINTER(rr_options), ctypes.POINTER(_P)]),
     "rr_set_lambda": (ctypes.c_int, [_P, ctypes.c_double]),
     "rr_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.POINTER(rr_info)]),
+    "rr_solve_batch": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P,
+                                      ctypes.c_double, _P]),
+    "rr_solve_fcg": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_double, ctypes.POINTER(rr_info)]),
+    "rr_solve_many": (ctypes.c_int, [ctypes.c_int32, _P, _P, _P, ctypes.c_double, _P, _P]),
+    "rr_harvest": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_double, _P, ctypes.c_double,
+                                  ctypes.c_int32, _P, _P, ctypes.c_int64,
+                                  ctypes.POINTER(ctypes.c_int64)]),
+    "rr_mlp_param_count": (ctypes.c_int64, [ctypes.c_int32, ctypes.c_int32]),
+    "rr_mlp_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P,
+                                     ctypes.POINTER(_P)]),
+    "rr_mlp_set_params": (ctypes.c_int, [_P, _P]),
+    "rr_mlp_get_params": (ctypes.c_int, [_P, _P]),
+    "rr_mlp_forward": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
+    "rr_mlp_grad": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P]),
+    "rr_mlp_train": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_float, ctypes.c_uint64, _P]),
+    "rr_mlp_free": (None, [_P]),
     "rr_apply": (ctypes.c_int, [_P, _P, _P]),
     "rr_precondition": (ctypes.c_int, [_P, _P, _P]),
     "rr_rhs": (ctypes.c_int, [_P, _P, _P]),
@@ -198,6 +216,142 @@ def rr_solve(h: Handle, y, w, tol=1e-8) -> dict:
     if st not in (RR_OK, RR_NOT_CONVERGED):
         raise RRError(st, rr_last_error())
     return d
+
+
+def rr_solve_batch(h: Handle, Y, lambdas, W, tol=1e-8) -> dict:
+    """rr_solve_batch: Y device float64 (nrhs, N); W device float64 (nlam, nrhs, F).
+    Returns {"status": ..., "infos": [[info of (j, l) for j] for l]}."""
+    nrhs = int(Y.shape[0])
+    lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64).ravel())
+    nlam = int(lam.size)
+    infos = (rr_info * (nrhs * nlam))()
+    st = load().rr_solve_batch(h.ptr, nrhs, _ptr(Y), nlam, lam.ctypes.data, _ptr(W), float(tol),
+                               ctypes.cast(infos, _P))
+    if st not in (RR_OK, RR_NOT_CONVERGED):
+        raise RRError(st, rr_last_error())
+    return {"status": _STATUS[st],
+            "infos": [[infos[l * nrhs + j].as_dict() for j in range(nrhs)] for l in range(nlam)]}
+
+
+def rr_solve_many(hs, ys, ws, tol=1e-8, stream=None) -> dict:
+    """rr_solve_many over handles hs, device targets ys and solutions ws (lists)."""
+    n = len(hs)
+    H = (_P * n)(*[h.ptr for h in hs])
+    Y = (_P * n)(*[_ptr(y) for y in ys])
+    W = (_P * n)(*[_ptr(w) for w in ws])
+    infos = (rr_info * n)()
+    st = load().rr_solve_many(n, ctypes.cast(H, _P), ctypes.cast(Y, _P), ctypes.cast(W, _P),
+                              float(tol), _stream_ptr(stream), ctypes.cast(infos, _P))
+    if st not in (RR_OK, RR_NOT_CONVERGED):
+        raise RRError(st, rr_last_error())
+    return {"status": _STATUS[st], "infos": [infos[i].as_dict() for i in range(n)]}
+
+
+def rr_solve_fcg(h: Handle, net, y, w, tol=1e-8) -> dict:
+    """rr_solve_fcg: flexible CG with the Cholesky coarse solve (net None) or the
+    learned correction of an Mlp."""
+    info = rr_info()
+    st = load().rr_solve_fcg(h.ptr, net.ptr if net is not None else None, _ptr(y), _ptr(w),
+                             float(tol), ctypes.byref(info))
+    d = info.as_dict()
+    d["status"] = _STATUS[st]
+    if st not in (RR_OK, RR_NOT_CONVERGED):
+        raise RRError(st, rr_last_error())
+    return d
+
+
+def rr_harvest(h: Handle, Y, lam, Wref, tol, max_iter, max_pairs, k):
+    """rr_harvest into new device float32 tensors (max_pairs, k); returns the
+    (Xp, Tp) rows written."""
+    import torch
+    Xp = torch.empty((max_pairs, k), dtype=torch.float32, device=Y.device)
+    Tp = torch.empty((max_pairs, k), dtype=torch.float32, device=Y.device)
+    n = ctypes.c_int64()
+    _check(load().rr_harvest(h.ptr, int(Y.shape[0]), _ptr(Y), float(lam), _ptr(Wref), float(tol),
+                             int(max_iter), _ptr(Xp), _ptr(Tp), int(max_pairs), ctypes.byref(n)))
+    return Xp[:n.value], Tp[:n.value]
+
+
+# ---- the learned correction's network
+
+MLP_KEYS = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def mlp_pack(p: dict) -> np.ndarray:
+    """Flat float32 parameters in the documented order (W1, b1, W2, b2, W3, b3)."""
+    return np.concatenate([np.asarray(p[n], dtype=np.float32).ravel() for n in MLP_KEYS])
+
+
+def mlp_unpack(flat, k: int, H: int) -> dict:
+    shapes = {"W1": (H, k), "b1": (H,), "W2": (H, H), "b2": (H,), "W3": (k, H), "b3": (k,)}
+    out, o = {}, 0
+    for n in MLP_KEYS:
+        size = int(np.prod(shapes[n]))
+        out[n] = np.asarray(flat[o:o + size]).reshape(shapes[n])
+        o += size
+    return out
+
+
+class Mlp:
+    def __init__(self, ptr, k, H):
+        self.ptr, self.k, self.H = ptr, k, H
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            load().rr_mlp_free(self.ptr)
+            self.ptr = None
+
+
+def mlp_param_count(k: int, H: int) -> int:
+    return int(load().rr_mlp_param_count(k, H))
+
+
+def mlp_create(k: int, H: int, params: dict, max_batch=512, stream=None) -> Mlp:
+    flat = np.ascontiguousarray(mlp_pack(params))
+    assert flat.size == mlp_param_count(k, H)
+    out = _P()
+    _check(load().rr_mlp_create(k, H, max_batch, flat.ctypes.data, _stream_ptr(stream),
+                                ctypes.byref(out)))
+    return Mlp(out, k, H)
+
+
+def mlp_get_params(m: Mlp) -> dict:
+    flat = np.empty(mlp_param_count(m.k, m.H), dtype=np.float32)
+    _check(load().rr_mlp_get_params(m.ptr, flat.ctypes.data))
+    return mlp_unpack(flat, m.k, m.H)
+
+
+def mlp_set_params(m: Mlp, params: dict):
+    flat = np.ascontiguousarray(mlp_pack(params))
+    _check(load().rr_mlp_set_params(m.ptr, flat.ctypes.data))
+
+
+def mlp_forward(m: Mlp, X):
+    """X: device float32 (B, k) -> device float32 (B, k)."""
+    import torch
+    out = torch.empty_like(X)
+    _check(load().rr_mlp_forward(m.ptr, int(X.shape[0]), _ptr(X), _ptr(out)))
+    return out
+
+
+def mlp_grad(m: Mlp, X, T):
+    """Loss and gradients (dict of numpy arrays) for device float32 rows X, T."""
+    flat = np.empty(mlp_param_count(m.k, m.H), dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(load().rr_mlp_grad(m.ptr, int(X.shape[0]), _ptr(X), _ptr(T), flat.ctypes.data,
+                              ctypes.byref(loss)))
+    return float(loss.value), mlp_unpack(flat, m.k, m.H)
+
+
+def mlp_train(m: Mlp, Xp, Tp, batch=256, steps=100, lr=1e-3, seed=0):
+    """Adam steps on pairs (device float32 (n, k)); returns the batch losses."""
+    losses = np.empty(max(1, steps), dtype=np.float32)
+    _check(load().rr_mlp_train(m.ptr, int(Xp.shape[0]), _ptr(Xp), _ptr(Tp), int(batch),
+                               int(steps), float(lr), int(seed), losses.ctypes.data))
+    return losses[:steps]
 
 
 def rr_apply(h: Handle, v, out):

@@ -1,0 +1,192 @@
+"""GPU parity of the batched solve (rr_solve_batch): many targets and many
+weights over one X, against the FP64 oracle system by system.
+
+Every system of the batch is the single-system problem of Eq. (1) with its
+own target and weight, so the oracle is the single-system oracle: the exact
+solution (X^T X + lambda I)^-1 X^T y by the oracle's dense Cholesky on small
+inputs, and at the full 200,000 x 100,000 size the oracle's FP64 operator for
+the true residual of sampled systems. Bars: true residual <= 1e-8 for every
+system (recomputed by the oracle), and ||w - w_ref|| <= 1e-6 ||w_ref||, or on
+systems so ill-conditioned that two residual-1e-8 solutions need not be that
+close, the bound the residual gives: ||w - w_ref|| <= ||r|| / lambda.
+"""
+import numpy as np
+import pytest
+
+from gen import synth
+from oracle import sparse as osp
+from oracle import twolevel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_05826_gb300 import build
+    build.build_library()
+    from paper_1806_05826_gb300 import rr as rrmod
+    rrmod.load()
+    return rrmod
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+BATCH_CASES = {
+    # name: (N, F, density, k, seed, target seeds, lambdas) — one slab; three
+    # slabs with a ragged last one and several weights inside one slab
+    "one_slab_2000x1000": (2000, 1000, 0.01, 50, 0, range(5), (1e-3, 1e-2, 1.0, 10.0)),
+    "ragged_3001x1777": (3001, 1777, 0.006, 37, 5, range(10, 80), (1e-3, 0.5)),
+}
+
+
+@pytest.fixture(scope="module", params=list(BATCH_CASES))
+def bcase(request, rr):
+    N, F, dens, k, seed, tseeds, lams = BATCH_CASES[request.param]
+    X = synth.zipf_binary(N, F, dens, 1.1, seed)
+    Y, _ = synth.ridge_targets_many(X, list(tseeds))
+    M = osp.from_csr(N, F, X.row_ptr, X.col_idx)
+    h = rr.rr_setup(X.row_ptr, X.col_idx, N, F, lams[0], k, seed=seed)
+    W = torch.empty((len(lams), Y.shape[0], F), dtype=torch.float64, device="cuda")
+    out = rr.rr_solve_batch(h, dev(Y), lams, W, tol=1e-8)
+    return dict(X=X, Y=Y, M=M, h=h, lams=lams, k=k, seed=seed, W=W.cpu().numpy(), out=out)
+
+
+def exact_solutions(M, Y, lam):
+    """The oracle's dense Cholesky solve of every target at one weight."""
+    L = twolevel.cholesky(osp.dense_A(M, lam))
+    return [twolevel.chol_solve(L, osp.rhs(M, y)) for y in Y]
+
+
+def test_batch_matches_exact_solutions(bcase):
+    M, Y, W = bcase["M"], bcase["Y"], bcase["W"]
+    assert bcase["out"]["status"] == "RR_OK"
+    for l, lam in enumerate(bcase["lams"]):
+        ref = exact_solutions(M, Y, lam)
+        for j, y in enumerate(Y):
+            b = osp.rhs(M, y)
+            w = W[l, j]
+            r = np.linalg.norm(b - osp.apply_A(M, lam, w))
+            assert r <= 1e-8 * np.linalg.norm(b), (l, j, r)
+            info = bcase["out"]["infos"][l][j]
+            assert info["true_rel_res"] <= 1e-8
+            diff = np.linalg.norm(w - ref[j])
+            assert diff <= max(1e-6 * np.linalg.norm(ref[j]), 1.01 * r / lam), (l, j, diff)
+
+
+def test_batch_agrees_with_single_solves(bcase, rr):
+    """Each batched system against rr_solve (mixed precision, same clustering)
+    on the same target and weight: same solution to the residual bound, and
+    iteration counts within 25%. Both apply the operator in FP32, summed in
+    another order (pieces of 256 entries against chunks of 256 rows and whole
+    rows); on these systems (lambda = 1e-3: condition number ~1e7) that
+    rounding moves the stopping iteration of either run by up to ~15% from
+    the FP64 count, in either direction."""
+    X, Y, W = bcase["X"], bcase["Y"], bcase["W"]
+    hs = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, bcase["lams"][0], bcase["k"],
+                     seed=bcase["seed"], precision=rr.RR_PREC_MIXED, max_restarts=20)
+    w = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
+    for l, lam in enumerate(bcase["lams"]):
+        rr.rr_set_lambda(hs, lam)
+        for j in (0, len(Y) - 1):
+            info = rr.rr_solve(hs, dev(Y[j]), w, tol=1e-8)
+            bi = bcase["out"]["infos"][l][j]
+            ws = w.cpu().numpy()
+            bn = np.linalg.norm(osp.rhs(bcase["M"], Y[j]))
+            bound = (info["true_rel_res"] + bi["true_rel_res"]) * bn / lam
+            assert np.linalg.norm(W[l, j] - ws) <= max(1e-6 * np.linalg.norm(ws), 1.01 * bound)
+            assert abs(bi["iters"] - info["iters"]) <= max(3, 0.25 * info["iters"]), (bi, info)
+
+
+def test_batch_graph_equals_host_loop(bcase, rr):
+    X, Y = bcase["X"], bcase["Y"]
+    h2 = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, bcase["lams"][0], bcase["k"],
+                     seed=bcase["seed"], use_graphs=0, check_every=3)
+    W2 = torch.empty((len(bcase["lams"]), Y.shape[0], X.n_cols), dtype=torch.float64, device="cuda")
+    out2 = rr.rr_solve_batch(h2, dev(Y), bcase["lams"], W2, tol=1e-8)
+    assert np.array_equal(W2.cpu().numpy(), bcase["W"])
+    it1 = [[i["iters"] for i in row] for row in bcase["out"]["infos"]]
+    it2 = [[i["iters"] for i in row] for row in out2["infos"]]
+    assert it1 == it2
+
+
+def test_batch_repeatable_and_reuses_workspace(bcase, rr):
+    """A second call on the same handle (workspace reused) gives the same bits;
+    a smaller batch afterwards still solves its systems."""
+    Y = bcase["Y"]
+    W2 = torch.empty((len(bcase["lams"]), Y.shape[0], bcase["X"].n_cols), dtype=torch.float64,
+                     device="cuda")
+    rr.rr_solve_batch(bcase["h"], dev(Y), bcase["lams"], W2, tol=1e-8)
+    assert np.array_equal(W2.cpu().numpy(), bcase["W"])
+    W3 = torch.empty((1, 1, bcase["X"].n_cols), dtype=torch.float64, device="cuda")
+    out = rr.rr_solve_batch(bcase["h"], dev(Y[:1]), bcase["lams"][-1:], W3, tol=1e-8)
+    assert out["status"] == "RR_OK"
+    ref = exact_solutions(bcase["M"], Y[:1], bcase["lams"][-1])[0]
+    assert np.linalg.norm(W3.cpu().numpy()[0, 0] - ref) <= 1e-6 * np.linalg.norm(ref) + \
+        1.01 * out["infos"][0][0]["true_rel_res"] * np.linalg.norm(osp.rhs(bcase["M"], Y[0])) / \
+        bcase["lams"][-1]
+
+
+def test_batch_edge_cases(rr):
+    rng = np.random.default_rng(3)
+    D = (rng.random((60, 40)) < 0.2).astype(np.int8)
+    D[:, 7] = 0                          # an empty column
+    rows, cols = np.nonzero(D)
+    rp = np.zeros(61, np.int64)
+    np.cumsum(np.bincount(rows, minlength=60), out=rp[1:])
+    ci = cols.astype(np.int32)
+    h = rr.rr_setup(rp, ci, 60, 40, 0.1, 4, seed=1)
+    M = osp.from_csr(60, 40, rp, ci)
+    Y = rng.standard_normal((3, 60))
+    Y[1] = 0.0                           # zero target: w = 0 at once
+    W = torch.full((2, 3, 40), np.nan, dtype=torch.float64, device="cuda")
+    out = rr.rr_solve_batch(h, dev(Y), [0.1, 3.0], W, tol=1e-10)
+    Wh = W.cpu().numpy()
+    assert out["status"] == "RR_OK"
+    assert np.all(Wh[:, 1] == 0.0) and all(out["infos"][l][1]["iters"] == 0 for l in range(2))
+    for l, lam in enumerate((0.1, 3.0)):
+        ref = exact_solutions(M, Y, lam)
+        for j in (0, 2):
+            assert np.linalg.norm(Wh[l, j] - ref[j]) <= 1e-8 * np.linalg.norm(ref[j])
+    with pytest.raises(rr.RRError):
+        rr.rr_solve_batch(h, dev(Y), [0.1, -1.0], W, tol=1e-8)
+    with pytest.raises(rr.RRError):
+        rr.rr_solve_batch(h, dev(Y), [0.1], W, tol=0.0)
+    hc = rr.rr_setup(rp, ci, 60, 40, 0.1, 4, seed=1, solver=rr.RR_SOLVER_CG)
+    with pytest.raises(rr.RRError):
+        rr.rr_solve_batch(hc, dev(Y), [0.1], W, tol=1e-8)
+
+
+@pytest.mark.slow
+def test_batch_full_size_sampled(rr):
+    """The 200,000 x 100,000 matrix with 64 targets x 8 weights (512 systems)
+    in the launch configuration the benchmark times: every system reports a
+    true residual <= 1e-8; sampled systems are re-checked with the oracle's FP64
+    operator and against rr_solve."""
+    X, Y, _, p = synth.batch_workload("zipf_200000x100000_64x8")
+    lams = p["lambdas"]
+    dv = torch.device("cuda")
+    rp = torch.as_tensor(X.row_ptr, device=dv)
+    ci = torch.as_tensor(X.col_idx, device=dv)
+    h = rr.rr_setup(rp, ci, X.n_rows, X.n_cols, lams[0], p["k"], seed=p["seed"],
+                    precision=rr.RR_PREC_MIXED, max_restarts=20)
+    W = torch.empty((len(lams), Y.shape[0], X.n_cols), dtype=torch.float64, device="cuda")
+    out = rr.rr_solve_batch(h, dev(Y), lams, W, tol=1e-8)
+    assert out["status"] == "RR_OK"
+    assert max(i["true_rel_res"] for row in out["infos"] for i in row) <= 1e-8
+    M = osp.from_csr(X.n_rows, X.n_cols, X.row_ptr, X.col_idx)
+    Wh = W.cpu().numpy()
+    w = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
+    for (l, j) in ((0, 0), (3, 17), (7, 63)):
+        b = osp.rhs(M, Y[j])
+        r = np.linalg.norm(b - osp.apply_A(M, lams[l], Wh[l, j]))
+        assert r <= 1e-8 * np.linalg.norm(b)
+        rr.rr_set_lambda(h, lams[l])
+        info = rr.rr_solve(h, dev(Y[j]), w, tol=1e-8)
+        bound = (info["true_rel_res"] * np.linalg.norm(b) + r) / lams[l]
+        ws = w.cpu().numpy()
+        assert np.linalg.norm(Wh[l, j] - ws) <= max(1e-6 * np.linalg.norm(ws), 1.01 * bound)

@@ -1,0 +1,238 @@
+"""GPU parity of the learned coarse correction and of flexible CG.
+
+- The network: forward pass and gradients of the tcgen05 BF16 kernels against
+  the FP64 oracle (oracle/mlp.py) on the same parameters and rows. Bars: BF16
+  operands with FP32 accumulation, so outputs within 2e-2 (norm-wise) and
+  gradients with cosine >= 0.999 and norm-wise error <= 2e-2.
+- Adam: the first step moves every parameter by lr against the sign of its
+  gradient.
+- Training pairs: rr_harvest against oracle/learned.py (FP32 operator on the
+  GPU: 1e-4 on the first iterations).
+- Flexible CG (Algorithm 3, m = 1) with the Cholesky coarse solve against the
+  oracle's FCG; the learned solve end to end: same solution as the oracle at
+  residual 1e-8, and its iteration count against the plain solvers.
+"""
+import numpy as np
+import pytest
+
+from gen import synth
+from oracle import krylov, learned, mlp
+from oracle import sparse as osp
+from oracle import twolevel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_05826_gb300 import build
+    build.build_library()
+    from paper_1806_05826_gb300 import rr as rrmod
+    rrmod.load()
+    return rrmod
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def init(k, H, seed):
+    return mlp.init_params(k, H, lambda n: synth.uniform(seed, 30, n))
+
+
+def relerr(a, b):
+    return np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b)
+
+
+def bf16(a):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def on_bf16_grid(p):
+    """The network the kernels multiply with: weights on the BF16 grid, biases FP32."""
+    return {n: (bf16(v) if n.startswith("W") else np.asarray(v, np.float32).astype(np.float64))
+            for n, v in p.items()}
+
+
+@pytest.mark.parametrize("k,H,B", [(50, 128, 40), (300, 256, 200)])
+def test_mlp_forward_matches_oracle(rr, k, H, B):
+    p = init(k, H, 1)
+    X = synth.normal(2, 31, B * k).reshape(B, k)
+    net = rr.mlp_create(k, H, p, max_batch=B)
+    got = rr.mlp_forward(net, dev(X, torch.float32)).cpu().numpy()
+    want, _ = mlp.forward(p, X)
+    assert relerr(got, want) <= 2e-2
+    # with the same BF16 inputs and weights, only the BF16 hidden activations
+    # and FP32 accumulation differ
+    want_q, _ = mlp.forward(on_bf16_grid(p), bf16(X))
+    assert relerr(got, want_q) <= 1e-2
+
+
+@pytest.mark.parametrize("k,H,B", [(50, 128, 40), (300, 256, 200)])
+def test_mlp_gradients_match_oracle(rr, k, H, B):
+    """The oracle evaluated on the BF16 grid the kernels multiply on (weights
+    and inputs rounded to BF16, as the kernels round them); the remaining
+    differences are the BF16 roundings of h1, h2 and of the backward signals
+    and FP32 accumulation: cosine >= 0.999 and norm-wise error <= 2e-2."""
+    p = init(k, H, 3)
+    X = synth.normal(4, 31, B * k).reshape(B, k)
+    T = synth.normal(5, 32, B * k).reshape(B, k)
+    net = rr.mlp_create(k, H, p, max_batch=B)
+    loss, g = rr.mlp_grad(net, dev(X, torch.float32), dev(T, torch.float32))
+    pq, Xq = on_bf16_grid(p), bf16(X)
+    want = mlp.backward(pq, Xq, T)
+    assert abs(loss - mlp.loss(pq, Xq, T)) <= 1e-2 * mlp.loss(pq, Xq, T)
+    for name in rr.MLP_KEYS:
+        a, b = g[name].astype(np.float64).ravel(), want[name].ravel()
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+        assert cos >= 0.999, (name, cos)
+        assert relerr(a, b) <= 2e-2, (name, relerr(a, b))
+
+
+def test_params_round_trip(rr):
+    k, H = 37, 128
+    p = init(k, H, 6)
+    net = rr.mlp_create(k, H, p, max_batch=8)
+    q = rr.mlp_get_params(net)
+    for name in rr.MLP_KEYS:
+        assert np.array_equal(q[name], p[name].astype(np.float32))
+
+
+def test_adam_first_step_is_lr_against_gradient_sign(rr):
+    """One pair (batch of 1, drawn from 1 row): Adam's first update is
+    -lr * g / (|g| + eps) ~ -lr * sign(g); compared where the FP64 gradient
+    of the same normalised pair is well above BF16 rounding."""
+    k, H, lr = 50, 128, 1e-3
+    p = init(k, H, 7)
+    x = synth.normal(8, 31, k)
+    t = synth.normal(9, 32, k)
+    net = rr.mlp_create(k, H, p, max_batch=1)
+    rr.mlp_train(net, dev(x[None], torch.float32), dev(t[None], torch.float32), batch=1, steps=1,
+                 lr=lr, seed=0)
+    q = rr.mlp_get_params(net)
+    n = np.linalg.norm(x)
+    g = mlp.backward(p, (x / n)[None], (t / n)[None])
+    for name in rr.MLP_KEYS:
+        d = (q[name].astype(np.float64) - p[name].astype(np.float32)).ravel()
+        gg = g[name].ravel()
+        big = np.abs(gg) > 1e-2 * np.abs(gg).max()
+        assert np.mean(np.sign(d[big]) == -np.sign(gg[big])) >= 0.99, name
+        assert np.allclose(np.abs(d[big]), lr, rtol=1e-2), name
+
+
+def test_training_reduces_loss(rr):
+    """Pairs t = L x of a fixed linear map: the loss falls by 10x in 300 steps."""
+    k, H, n = 64, 128, 4096
+    L = synth.normal(10, 33, k * k).reshape(k, k) / np.sqrt(k)
+    Xp = synth.normal(11, 34, n * k).reshape(n, k)
+    Tp = Xp @ L.T
+    net = rr.mlp_create(k, H, init(k, H, 12), max_batch=256)
+    losses = rr.mlp_train(net, dev(Xp, torch.float32), dev(Tp, torch.float32), batch=256,
+                          steps=300, lr=2e-3, seed=5)
+    assert np.all(np.isfinite(losses))
+    assert losses[-20:].mean() <= 0.1 * losses[:5].mean()
+
+
+@pytest.fixture(scope="module")
+def small(rr):
+    X = synth.zipf_binary(2000, 1000, 0.01, 1.1, 0)
+    lam, k, seed = 1e-3, 50, 0
+    ref = twolevel.setup_binary(X.n_rows, X.n_cols, X.row_ptr, X.col_idx, lam, k, seed=seed)
+    A = osp.dense_A(ref.M, lam)
+    Lc = twolevel.cholesky(A)
+    return dict(X=X, lam=lam, k=k, seed=seed, ref=ref, Lc=Lc)
+
+
+def exact(small, y):
+    return twolevel.chol_solve(small["Lc"], osp.rhs(small["ref"].M, y))
+
+
+def test_harvest_matches_oracle(rr, small):
+    X, ref = small["X"], small["ref"]
+    Y, _ = synth.ridge_targets_many(X, [1000, 1001])
+    Wref = np.stack([exact(small, y) for y in Y])
+    h = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, small["lam"], small["k"],
+                    seed=small["seed"])
+    k = ref.k_eff
+    Xp, Tp = rr.rr_harvest(h, dev(Y), small["lam"], dev(Wref), 1e-8, 3, 6, k)
+    assert Xp.shape == (6, k)
+    Xp, Tp = Xp.cpu().numpy(), Tp.cpu().numpy()
+    for j, y in enumerate(Y):
+        xs, ts = learned.harvest_pairs(ref, osp.rhs(ref.M, y), Wref[j], 3)
+        # the GPU iterations apply the operator in FP32; on this system
+        # (lambda = 1e-3) the iterates separate from the FP64 ones by ~1e-3
+        # by the third iteration, so pairs are compared tightly on the first two
+        for it, tol in ((0, 1e-4), (1, 1e-4), (2, 1e-2)):
+            assert relerr(Xp[it * 2 + j], xs[it]) <= tol, (j, it)
+            assert relerr(Tp[it * 2 + j], ts[it]) <= tol, (j, it)
+
+
+def test_fcg_cholesky_matches_oracle(rr, small):
+    """rr_solve_fcg without a network is Algorithm 3 (m = 1) with the two-level
+    cycle: the same iterations as the oracle's FCG (FP64 handle), the same
+    solution."""
+    X, ref = small["X"], small["ref"]
+    y, _ = synth.ridge_targets(X, 100)
+    b = osp.rhs(ref.M, y)
+    h = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, small["lam"], small["k"],
+                    seed=small["seed"])
+    w = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
+    info = rr.rr_solve_fcg(h, None, dev(y), w, tol=1e-8)
+    want = krylov.fcg(ref.A, lambda r, i: ref.apply(r), b, m=1, tol=1e-8)
+    assert info["status"] == "RR_OK" and info["fallbacks"] == 0
+    assert abs(info["iters"] - want.iters) <= max(2, 0.05 * want.iters)
+    wg = w.cpu().numpy()
+    r = np.linalg.norm(b - ref.A(wg))
+    assert r <= 1e-8 * np.linalg.norm(b)
+    ws = exact(small, y)
+    assert np.linalg.norm(wg - ws) <= max(1e-6 * np.linalg.norm(ws), 1.01 * r / small["lam"])
+
+
+def test_learned_fcg_end_to_end(rr, small):
+    """Harvest pairs from training targets, train the network on the GPU, then
+    solve held-out targets with the learned coarse correction (mixed precision,
+    as the benchmark). Every solve reaches true residual 1e-8 with the oracle's
+    solution, and the iteration counts of the learned solve, the Cholesky FCG
+    and the plain two-level PCG are printed: what the trained network gains
+    (or loses) against the method without it. The Cholesky FCG must match PCG
+    (same preconditioner, so FCG(1) keeps PCG's iteration count)."""
+    X, ref = small["X"], small["ref"]
+    lam, k = small["lam"], ref.k_eff
+    h = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, lam, small["k"],
+                    seed=small["seed"], precision=rr.RR_PREC_MIXED, max_restarts=20)
+    seeds = list(range(1000, 1032))
+    Y, _ = synth.ridge_targets_many(X, seeds)
+    Wref = torch.empty((1, len(seeds), X.n_cols), dtype=torch.float64, device="cuda")
+    rr.rr_solve_batch(h, dev(Y), [lam], Wref, tol=1e-10)
+    Xp, Tp = rr.rr_harvest(h, dev(Y), lam, Wref[0].contiguous(), 1e-8, 200, 20000, k)
+    assert Xp.shape[0] > 1000
+    net = rr.mlp_create(k, 128, init(k, 128, 13), max_batch=256)
+    losses = rr.mlp_train(net, Xp, Tp, batch=256, steps=600, lr=1e-3, seed=1)
+    assert np.all(np.isfinite(losses)) and losses[-50:].mean() < losses[:10].mean()
+    w = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
+    rows = []
+    for s in (100, 101, 102, 103):
+        y, _ = synth.ridge_targets(X, s)
+        b = osp.rhs(ref.M, y)
+        ws = exact(small, y)
+        its = {}
+        for name, fn in (("learned", lambda: rr.rr_solve_fcg(h, net, dev(y), w, tol=1e-8)),
+                         ("fcg", lambda: rr.rr_solve_fcg(h, None, dev(y), w, tol=1e-8)),
+                         ("pcg", lambda: rr.rr_solve(h, dev(y), w, tol=1e-8))):
+            info = fn()
+            assert info["status"] == "RR_OK", (name, info)
+            wg = w.cpu().numpy()
+            r = np.linalg.norm(b - ref.A(wg))
+            assert r <= 1e-8 * np.linalg.norm(b), name
+            assert np.linalg.norm(wg - ws) <= max(1e-6 * np.linalg.norm(ws), 1.01 * r / lam), name
+            its[name] = (info["iters"], info.get("fallbacks", 0))
+        rows.append(its)
+    print("learned vs plain iterations (iters, fallbacks):", rows)
+    for its in rows:
+        assert abs(its["fcg"][0] - its["pcg"][0]) <= 3

@@ -265,8 +265,9 @@ def test_repeatable_bits(case, rr):
 
 
 def test_graph_loop_equals_host_loop(case, rr):
-    """The device-side while-loop graph and host-driven batches run the same
-    kernels in the same order: identical bits and iteration counts."""
+    """The device-side while-loop graphs (seeding and PCG) and host-issued
+    loops run the same kernels in the same order: identical centres, labels,
+    bits and iteration counts."""
     X = case["X"]
     h2 = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, case["lam"], case["k"],
                      seed=case["seed"], use_graphs=0, check_every=5)
@@ -274,6 +275,8 @@ def test_graph_loop_equals_host_loop(case, rr):
     w2 = torch.empty_like(w1)
     i1 = rr.rr_solve(case["h"], dev(case["y"]), w1, tol=1e-8)
     i2 = rr.rr_solve(h2, dev(case["y"]), w2, tol=1e-8)
+    assert np.array_equal(rr.rr_get_centers(case["h"], case["k"]), rr.rr_get_centers(h2, case["k"]))
+    assert np.array_equal(rr.rr_get_labels(case["h"]), rr.rr_get_labels(h2))
     assert i1["iters"] == i2["iters"] and i1["restarts"] == i2["restarts"]
     assert torch.equal(w1, w2)
 

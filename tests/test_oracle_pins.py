@@ -469,3 +469,36 @@ def test_learned_correction_positively_homogeneous():
     p = mlp.init_params(5, 4, lambda n: rng.random(n))
     rc = rng.standard_normal(5)
     assert np.allclose(mlp.coarse_correction(p, 3.5 * rc), 3.5 * mlp.coarse_correction(p, rc))
+
+
+def test_harvest_pairs_first_two_iterations_closed_form():
+    """The oracle's training pairs against the same quantities written out with
+    dense matrices: iteration 0 has w_0 = 0, r_0 = b; iteration 1 has
+    w_1 = alpha_0 z_0 with z_0 = M^-1 b and alpha_0 = <b, z_0> / <z_0, A z_0>.
+    Then z1 = omega D^-1 r, x = P^T (r - A z1), t = P^T (w* - w - z1) with the
+    dense P of Section 3.2 and w* the dense solve."""
+    from oracle import learned
+    X = synth.zipf_binary(120, 60, 0.08, 1.1, 4)
+    lam = 0.05
+    T = tl.setup_binary(X.n_rows, X.n_cols, X.row_ptr, X.col_idx, lam, 7, seed=2)
+    y, _ = synth.ridge_targets(X, 9)
+    b = osp.rhs(T.M, y)
+    A = osp.dense_A(T.M, lam)
+    P = tl.prolongation_dense(T.labels, T.s)
+    w_star = np.linalg.solve(A, b)
+    Xs, Ts = learned.harvest_pairs(T, b, w_star, 2)
+
+    def pair(w, r):
+        z1 = T.omega * r / np.diag(A)
+        return P.T @ (r - A @ z1), P.T @ (w_star - w - z1)
+
+    x0, t0 = pair(np.zeros_like(b), b)
+    z0 = T.apply(b)
+    a0 = (b @ z0) / (z0 @ A @ z0)
+    x1, t1 = pair(a0 * z0, b - a0 * (A @ z0))
+    for got, want in ((Xs[0], x0), (Ts[0], t0), (Xs[1], x1), (Ts[1], t1)):
+        assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+    # the restricted remaining error and the restricted residual are the same
+    # vector seen through A: x = P^T A u, t = P^T u with u = w* - w - z1
+    u0 = w_star - T.omega * b / np.diag(A)
+    assert np.allclose(P.T @ (A @ u0), Xs[0], rtol=1e-10, atol=1e-12 * np.linalg.norm(b))
