@@ -57,6 +57,12 @@ enum { RR_GRAM_AUTO = 0,        /* tcgen05 tensor cores (FP16 counts, exact FP32
                                    the counts allow exact chunks, else CUDA cores */
        RR_GRAM_CUDA_CORES = 1 };/* int32 products summed in int64 on CUDA cores */
 
+/* rr_options.gather — the FP32 sliced-gather kernel of the operator applies
+ * (both give identical bits: the same sums in the same order) */
+enum { RR_GATHER_AUTO = 0,      /* rr_setup times both on each pass of X and keeps the faster */
+       RR_GATHER_LANES = 1,     /* each lane sums whole pieces, index words loaded by the lanes */
+       RR_GATHER_STAGED = 2 };  /* index words streamed through shared memory by bulk copies */
+
 /* rr_options.precision */
 enum { RR_PREC_FP64 = 0,        /* every operator apply accumulates in FP64 */
        RR_PREC_MIXED = 1 };     /* the operator applies inside the CG iterations gather FP32
@@ -98,6 +104,7 @@ typedef struct {
                                    (default); 0: host-driven batches of check_every iterations and
                                    host-issued seeding rounds (same results) */
   int32_t gram;                 /* RR_GRAM_* (default RR_GRAM_AUTO) */
+  int32_t gather;               /* RR_GATHER_* (default RR_GATHER_AUTO) */
   void *stream;                 /* cudaStream_t for all work; NULL = legacy default stream */
 } rr_options;
 

@@ -84,16 +84,42 @@ __global__ void k_first_center(int64_t F, uint64_t seed, int32_t *centers, uint8
   }
 }
 
-// ov[j] += 1 for every feature j sharing a row with centre centers[t].
+// A centre with more than N/2 rows is "heavy": its overlaps are counted over
+// the rows it does NOT hold (|x_j AND x_c| = n_j - |x_j AND NOT x_c|), which
+// is the smaller set. Its rows are stamped with the round in rowmark.
+__device__ __forceinline__ bool heavy_centre(int64_t nc, int64_t N) { return 2 * nc > N; }
+
+__global__ void k_seed_mark(const int32_t *__restrict__ round, const int32_t *__restrict__ centers,
+                            int64_t N, const int64_t *__restrict__ col_ptr,
+                            const int32_t *__restrict__ row_idx, int32_t *__restrict__ rowmark) {
+  const int32_t t = *round;
+  const int64_t c = centers[t];
+  if (!heavy_centre(col_ptr[c + 1] - col_ptr[c], N)) return;
+  for (int64_t p = col_ptr[c] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < col_ptr[c + 1];
+       p += (int64_t)gridDim.x * blockDim.x)
+    rowmark[row_idx[p]] = t + 1;
+}
+
+// ov[j] += 1 for every feature j sharing a row with centre centers[t] (for a
+// heavy centre: for every row the centre does not hold).
 __global__ void k_seed_overlap(const int32_t *__restrict__ round, const int32_t *__restrict__ centers,
-                               const int64_t *__restrict__ row_ptr,
+                               int64_t N, const int64_t *__restrict__ row_ptr,
                                const int32_t *__restrict__ col_idx,
                                const int64_t *__restrict__ col_ptr,
-                               const int32_t *__restrict__ row_idx, int32_t *__restrict__ ov) {
-  const int64_t c = centers[*round];
+                               const int32_t *__restrict__ row_idx,
+                               const int32_t *__restrict__ rowmark, int32_t *__restrict__ ov) {
+  const int32_t t = *round;
+  const int64_t c = centers[t];
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  if (heavy_centre(col_ptr[c + 1] - col_ptr[c], N)) {
+    for (int64_t r = warp; r < N; r += nwarps) {
+      if (rowmark[r] == t + 1) continue;
+      for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) atomicAdd(&ov[col_idx[e]], 1);
+    }
+    return;
+  }
   for (int64_t p = col_ptr[c] + warp; p < col_ptr[c + 1]; p += nwarps) {
     const int64_t r = row_idx[p];
     for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) atomicAdd(&ov[col_idx[e]], 1);
@@ -102,7 +128,7 @@ __global__ void k_seed_overlap(const int32_t *__restrict__ round, const int32_t 
 
 // d2[i] = min(d2[i], n_i + n_c - 2 ov[i]) (plain assignment for the first centre);
 // ov reset; per-tile sums of d2.
-__global__ void k_seed_update(const int32_t *__restrict__ round, int64_t F,
+__global__ void k_seed_update(const int32_t *__restrict__ round, int64_t F, int64_t N,
                               const int32_t *__restrict__ centers,
                               const int64_t *__restrict__ col_ptr, int32_t *__restrict__ ov,
                               int64_t *__restrict__ d2, int64_t *__restrict__ tile_sum) {
@@ -110,12 +136,14 @@ __global__ void k_seed_update(const int32_t *__restrict__ round, int64_t F,
   const int32_t t = *round;
   const int64_t c = centers[t];
   const int64_t nc = col_ptr[c + 1] - col_ptr[c];
+  const bool heavy = heavy_centre(nc, N);
   int64_t s = 0;
   for (int u = threadIdx.x; u < kTile; u += kThreads) {
     const int64_t i = (int64_t)blockIdx.x * kTile + u;
     if (i < F) {
       const int64_t ni = col_ptr[i + 1] - col_ptr[i];
-      const int64_t dist = ni + nc - 2 * (int64_t)ov[i];
+      const int64_t inter = heavy ? ni - (int64_t)ov[i] : (int64_t)ov[i];
+      const int64_t dist = ni + nc - 2 * inter;
       ov[i] = 0;
       const int64_t v = (t == 0) ? dist : min(d2[i], dist);
       d2[i] = v;
@@ -490,19 +518,21 @@ __global__ void k_lloyd_argmin(int64_t F, int32_t k, const int32_t *__restrict__
 rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                         const int64_t *col_ptr, const int32_t *row_idx, int32_t k, uint64_t seed,
                         KmeansBuffers &b, cudaStream_t st, bool use_graph) {
-  (void)N;
   const int64_t ntiles = (F + kTile - 1) / kTile;
   uint8_t *chosen = reinterpret_cast<uint8_t *>(b.next);   // F bytes of the (unused yet) next[]
   RR_CUDA(cudaMemsetAsync(chosen, 0, F, st));
   RR_CUDA(cudaMemsetAsync(b.ov, 0, sizeof(int32_t) * F, st));
+  RR_CUDA(cudaMemsetAsync(b.dcount, 0, sizeof(int32_t) * N, st));   // row stamps of heavy centres
   RR_LAUNCH(k_first_center, 1, 32, 0, st, F, seed, b.centers, chosen, b.round);
   if (!use_graph) {
     // the same k rounds as the graph's while loop, issued from the host
     for (int32_t t = 0; t < k; ++t) {
-      RR_LAUNCH(k_seed_overlap, kSMs * 2, kThreads, 0, st, b.round, b.centers, row_ptr, col_idx,
-                col_ptr, row_idx, b.ov);
-      RR_LAUNCH(k_seed_update, (unsigned)ntiles, kThreads, 0, st, b.round, F, b.centers, col_ptr,
-                b.ov, b.d2, b.part_i);
+      RR_LAUNCH(k_seed_mark, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, col_ptr, row_idx,
+                b.dcount);
+      RR_LAUNCH(k_seed_overlap, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, row_ptr,
+                col_idx, col_ptr, row_idx, b.dcount, b.ov);
+      RR_LAUNCH(k_seed_update, (unsigned)ntiles, kThreads, 0, st, b.round, F, N, b.centers,
+                col_ptr, b.ov, b.d2, b.part_i);
       RR_LAUNCH(k_seed_pick, 1, kThreads, 0, st, b.round, k, F, ntiles, seed, b.d2, b.part_i,
                 b.centers, chosen);
     }
@@ -529,10 +559,12 @@ rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int3
     RR_CUDA(cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                           cudaStreamCaptureModeThreadLocal));
     auto body = [&]() -> rr_status {
-      RR_LAUNCH(k_seed_overlap, kSMs * 2, kThreads, 0, cs, b.round, b.centers, row_ptr, col_idx,
-                col_ptr, row_idx, b.ov);
-      RR_LAUNCH(k_seed_update, (unsigned)ntiles, kThreads, 0, cs, b.round, F, b.centers, col_ptr,
-                b.ov, b.d2, b.part_i);
+      RR_LAUNCH(k_seed_mark, kSMs * 2, kThreads, 0, cs, b.round, b.centers, N, col_ptr, row_idx,
+                b.dcount);
+      RR_LAUNCH(k_seed_overlap, kSMs * 2, kThreads, 0, cs, b.round, b.centers, N, row_ptr,
+                col_idx, col_ptr, row_idx, b.dcount, b.ov);
+      RR_LAUNCH(k_seed_update, (unsigned)ntiles, kThreads, 0, cs, b.round, F, N, b.centers,
+                col_ptr, b.ov, b.d2, b.part_i);
       RR_LAUNCH(k_seed_pick, 1, kThreads, 0, cs, b.round, k, F, ntiles, seed, b.d2, b.part_i,
                 b.centers, chosen);
       RR_LAUNCH(k_seed_condition, 1, 32, 0, cs, hc, b.round, k);
@@ -553,7 +585,7 @@ rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int3
     }
     RR_CUDA(cudaGraphInstantiate(&exec, g, 0));
     RR_CUDA(cudaGraphLaunch(exec, st));
-    rr_launch_counter += 4LL * k;   // the body ran k times
+    rr_launch_counter += 5LL * k;   // the body ran k times
     RR_CUDA(cudaStreamSynchronize(st));
     return RR_OK;
   };

@@ -560,7 +560,7 @@ rr_status gather_t(const SlicedPattern &P, const double *x, const SlicedPattern 
   else
     RR_LAUNCH((k_slice_prep<false, T>), grid_for(n, kThreads), kThreads, 0, st, n, x, nullptr,
               nullptr, xq, stop);
-  if (std::is_same<T, float>::value && P.chunk_p) {
+  if (std::is_same<T, float>::value && P.staged && P.chunk_p) {
     const size_t smem = staged_smem(P.W);
     static bool attr = false;
     if (!attr) {   // the largest slice any pattern can have
@@ -692,6 +692,63 @@ void sliced_free(SlicedPattern &P) {
 rr_status sliced_gather(const SlicedPattern &P, const double *x, const SlicedPattern *in,
                         const int32_t *stop, cudaStream_t st, bool fp32) {
   return fp32 ? gather_t<float>(P, x, in, stop, st) : gather_t<double>(P, x, in, stop, st);
+}
+
+rr_status sliced_choose_gather(SlicedPattern &P, int32_t mode, cudaStream_t st) {
+  if (!P.chunk_p || mode == RR_GATHER_LANES) {
+    P.staged = false;
+    return RR_OK;
+  }
+  if (mode == RR_GATHER_STAGED) {
+    P.staged = true;
+    return RR_OK;
+  }
+  // time both (after one untimed run each) on the FP32 copy of a zero vector
+  RR_CUDA(cudaMemsetAsync(P.xq, 0, sizeof(float) * P.n_inner, st));
+  float best[2] = {0.f, 0.f};
+  cudaEvent_t e0, e1;
+  RR_CUDA(cudaEventCreate(&e0));
+  RR_CUDA(cudaEventCreate(&e1));
+  rr_status s = RR_OK;
+  for (int v = 0; v < 2 && s == RR_OK; ++v) {
+    P.staged = v == 1;
+    for (int rep = 0; rep < 3 && s == RR_OK; ++rep) {
+      if (cudaEventRecord(e0, st) != cudaSuccess) s = RR_CUDA_ERROR;
+      const float *xq = reinterpret_cast<const float *>(P.xq);
+      if (s == RR_OK && P.staged) {
+        static bool attr = false;
+        if (!attr) {
+          if (cudaFuncSetAttribute(k_sliced_gather_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)staged_smem(kSliceMax)) != cudaSuccess)
+            s = RR_CUDA_ERROR;
+          attr = true;
+        }
+        if (s == RR_OK)
+          k_sliced_gather_staged<<<P.ntasks, kSliceThreads, staged_smem(P.W), st>>>(
+              P.view(), P.chunk_p, P.chunk_w, P.task_c, xq, P.psum, nullptr, P.err);
+      } else if (s == RR_OK) {
+        s = set_smem_attr<float>();
+        if (s == RR_OK)
+          k_sliced_gather<float><<<P.ntasks, kSliceThreads, slice_smem<float>(P.W), st>>>(
+              P.view(), xq, P.psum, nullptr);
+      }
+      rr_launch_counter += 1;
+      if (s == RR_OK && (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1, st) != cudaSuccess ||
+                         cudaEventSynchronize(e1) != cudaSuccess))
+        s = RR_CUDA_ERROR;
+      float ms = 0.f;
+      if (s == RR_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) s = RR_CUDA_ERROR;
+      if (rep > 0) best[v] = (rep == 1) ? ms : std::min(best[v], ms);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != RR_OK) {
+    rr_set_error("sliced_choose_gather: a timing launch failed");
+    return s;
+  }
+  P.staged = best[1] < best[0];
+  return RR_OK;
 }
 
 rr_status sliced_slot_sum(const SlicedPattern &P, double *out, cudaStream_t st) {

@@ -188,6 +188,7 @@ struct SlicedPattern {
   int64_t n_chunks = 0;          // chunks of whole pieces of the staged FP32 gather (0: none)
   int32_t *chunk_p = nullptr;    // [n_chunks+1] first piece of every chunk
   int32_t *chunk_w = nullptr;    // [n_chunks+1] first word of every chunk
+  bool staged = false;           // FP32 passes use the staged gather (needs the chunks)
   int32_t *task_c = nullptr;     // [ntasks+1]  chunks of each task
   int32_t *err = nullptr;        // device error word (DEV_TIMEOUT from a bounded wait)
   void *xq = nullptr;            // [n_inner]   the gathered vector in the accumulation type
@@ -206,6 +207,9 @@ rr_status sliced_gather(const SlicedPattern &P, const double *x, const SlicedPat
                         const int32_t *stop, cudaStream_t st, bool fp32 = false);
 // out[o] = sum of the slots of outer index o.
 rr_status sliced_slot_sum(const SlicedPattern &P, double *out, cudaStream_t st);
+// Chooses P.staged: mode RR_GATHER_LANES / RR_GATHER_STAGED, or (RR_GATHER_AUTO)
+// the faster of the two FP32 gathers on this pattern, each timed on the stream.
+rr_status sliced_choose_gather(SlicedPattern &P, int32_t mode, cudaStream_t st);
 // t_i = slot sums of feature i, then the epilogue; kVecGrid partial dots.
 rr_status sliced_epilogue(const SlicedPattern &P, const CscEpilogue &ep, cudaStream_t st);
 

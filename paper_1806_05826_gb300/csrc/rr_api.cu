@@ -330,6 +330,10 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   // ---- sliced patterns of X and X^T and the solve workspace
   RR_TRY(rr::sliced_build(N, F, h->row_ptr, h->col_idx, h->pcsr, h->err, st));
   RR_TRY(rr::sliced_build(F, N, h->col_ptr, h->row_idx, h->pcsc, h->err, st));
+  if (h->opt.precision == RR_PREC_MIXED || h->opt.gather != RR_GATHER_AUTO) {
+    RR_TRY(rr::sliced_choose_gather(h->pcsr, h->opt.gather, st));
+    RR_TRY(rr::sliced_choose_gather(h->pcsc, h->opt.gather, st));
+  }
   h->n_parts = rr::kVecGrid;
   for (double **v : {&h->b, &h->r, &h->z1, &h->z2, &h->z, &h->p, &h->q, &h->r1, &h->rt, &h->w_int})
     RR_TRY(m.alloc(v, F));
@@ -909,6 +913,7 @@ void rr_default_options(rr_options *o) {
   o->max_restarts = 5;
   o->use_graphs = 1;
   o->gram = RR_GRAM_AUTO;
+  o->gather = RR_GATHER_AUTO;
   o->stream = nullptr;
 }
 
@@ -957,6 +962,10 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
   }
   if (opt.kmeans_max_iter < 1 || opt.max_iter < 1) {
     rr_set_error("rr_setup: kmeans_max_iter and max_iter must be positive");
+    return RR_INVALID_ARG;
+  }
+  if (opt.gather < RR_GATHER_AUTO || opt.gather > RR_GATHER_STAGED) {
+    rr_set_error("rr_setup: unknown gather %d", opt.gather);
     return RR_INVALID_ARG;
   }
   rr_handle *h = new rr_handle();

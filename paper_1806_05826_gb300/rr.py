@@ -21,6 +21,7 @@ RR_CSR_BINARY, RR_DENSE_F32_ROWMAJOR = 0, 1
 RR_SOLVER_TWOLEVEL, RR_SOLVER_CG, RR_SOLVER_DCG = 0, 1, 2
 RR_PREC_FP64, RR_PREC_MIXED = 0, 1
 RR_GRAM_AUTO, RR_GRAM_CUDA_CORES = 0, 1
+RR_GATHER_AUTO, RR_GATHER_LANES, RR_GATHER_STAGED = 0, 1, 2
 
 _STATUS = {0: "RR_OK", 1: "RR_INVALID_ARG", 2: "RR_CUDA_ERROR", 3: "RR_OOM", 4: "RR_NOT_SPD",
            5: "RR_NOT_CONVERGED", 6: "RR_NONFINITE", 7: "RR_TIMEOUT", 8: "RR_UNSUPPORTED"}
@@ -39,7 +40,7 @@ class rr_options(ctypes.Structure):
                 ("solver", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("gram", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("gather", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class rr_info(ctypes.Structure):
@@ -181,7 +182,8 @@ class Handle:
 
 def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=None,
              kmeans_max_iter=50, max_iter=20000, solver=RR_SOLVER_TWOLEVEL, check_every=8,
-             max_restarts=5, use_graphs=1, gram=RR_GRAM_AUTO, precision=RR_PREC_FP64,
+             max_restarts=5, use_graphs=1, gram=RR_GRAM_AUTO, gather=RR_GATHER_AUTO,
+             precision=RR_PREC_FP64,
              stream=None) -> Handle:
     """rr_setup on a binary CSR pattern given as numpy arrays (host) or torch
     CUDA tensors (device): row_ptr int64[N+1], col_idx int32[nnz]."""
@@ -198,6 +200,7 @@ def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=N
     o = rr_default_options(kmeans_max_iter=kmeans_max_iter, max_iter=max_iter, seed=seed,
                            init_centers=_ptr(ic), solver=solver, check_every=check_every,
                            max_restarts=max_restarts, use_graphs=use_graphs, gram=gram,
+                           gather=gather,
                            precision=precision, stream=_stream_ptr(stream))
     out = _P()
     _check(lib.rr_setup(ctypes.byref(X), float(lam), int(k), ctypes.byref(o), ctypes.byref(out)))

@@ -376,3 +376,43 @@ def test_nonfinite_rhs_reported(rr):
     with pytest.raises(rr.RRError) as e:
         rr.rr_solve(h, dev(y), w, tol=1e-8)
     assert e.value.status == rr.RR_NONFINITE
+
+
+def test_gather_kernels_identical_bits(case, rr):
+    """The two FP32 gather kernels (lanes summing whole pieces; index words
+    staged through shared memory) make the same sums in the same order: the
+    mixed-precision operator and solves give identical bits with either."""
+    X = case["X"]
+    outs = []
+    for g in (rr.RR_GATHER_LANES, rr.RR_GATHER_STAGED):
+        h = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, case["lam"], case["k"],
+                        seed=case["seed"], precision=rr.RR_PREC_MIXED, gather=g)
+        v = dev(synth.normal(3, 50, X.n_cols))
+        Av = torch.empty_like(v)
+        rr.rr_apply(h, v, Av)
+        w = torch.empty_like(v)
+        info = rr.rr_solve(h, dev(case["y"]), w, tol=1e-8)
+        outs.append((Av.cpu().numpy(), w.cpu().numpy(), info["iters"]))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1]) and outs[0][2] == outs[1][2]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_kmeanspp_heavy_centres_bit_exact(rr, seed):
+    """Columns holding more than half of the rows (and one holding all of
+    them) are counted through the rows they do not hold; the draws must not
+    change: centres equal the oracle's."""
+    rng = np.random.default_rng(seed)
+    N, F = 900, 300
+    D = (rng.random((N, F)) < 0.03).astype(np.int8)
+    D[:, 5] = 1                                   # all rows
+    D[:, 17] = (rng.random(N) < 0.9)              # heavy
+    D[:, 200] = (rng.random(N) < 0.6)             # heavy
+    D[:, 201] = (rng.random(N) < 0.45)            # just below half
+    rp, ci = csr_of(D)
+    cp, ri = osp.csc_pattern(N, F, rp, ci)
+    k = 40
+    want = okm.kmeanspp_binary(N, F, rp, ci, cp, ri, k, seed)
+    for use_graphs in (1, 0):
+        h = rr.rr_setup(rp, ci, N, F, 0.1, k, seed=seed, use_graphs=use_graphs)
+        assert np.array_equal(rr.rr_get_centers(h, k), want)
