@@ -52,6 +52,14 @@ def parse():
                     help="skip the learned coarse correction section (harvest, training, solves)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-issued loops instead of CUDA graphs (every kernel visible to a profiler)")
+    ap.add_argument("--gather", default="auto", choices=["auto", "lanes", "staged"],
+                    help="FP32 gather kernel (auto: timed per pass at setup; the others force one)")
+    ap.add_argument("--only", choices=["batched", "many", "learned"],
+                    help="run one extra section alone and print it (profiling runs)")
+    ap.add_argument("--batch-targets", type=int, default=64,
+                    help="targets of the batched section (64 in the workload definition)")
+    ap.add_argument("--pairs", type=int, default=100_000,
+                    help="training pairs of the learned section (100,000 in the workload definition)")
     ap.add_argument("--roofline-only", action="store_true",
                     help="one setup, then only the operator-apply kernel timings (profiling runs)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
@@ -192,7 +200,7 @@ def measure_roofline(rr, row_ptr, col_idx, N, F, nnz, k, lams, opts, dev, stream
                       for n, t in kern.items() if n != dom}}
 
 
-def measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world):
+def measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world, n_targets=64):
     """Many targets and weights over the same X in one rr_solve_batch (the
     batched form), against the plain two-level PCG solving a sample of the same
     systems one at a time on the same GPU. One warm-up, then one timed run of
@@ -201,7 +209,9 @@ def measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world):
     from gen import synth
     name = "zipf_200000x100000_64x8"
     pb = synth.BATCH_WORKLOADS[name]
-    seeds, lams = pb["target_seeds"], list(pb["lambdas"])
+    seeds, lams = pb["target_seeds"][:n_targets], list(pb["lambdas"])
+    if n_targets != len(pb["target_seeds"]):
+        name += f" (first {n_targets} targets)"
     Y, _ = synth.ridge_targets_many(X, seeds)
     N, F = X.n_rows, X.n_cols
     Yd = torch.as_tensor(Y, device=dev)
@@ -388,12 +398,22 @@ def run_ours(args, rank, world, local):
 
     prec = rr.RR_PREC_MIXED if args.precision == "mixed" else rr.RR_PREC_FP64
     opts = dict(seed=p["seed"], stream=stream, precision=prec, max_restarts=20,
-                use_graphs=0 if args.no_graphs else 1)
+                use_graphs=0 if args.no_graphs else 1,
+                gather={"auto": rr.RR_GATHER_AUTO, "lanes": rr.RR_GATHER_LANES,
+                        "staged": rr.RR_GATHER_STAGED}[args.gather])
 
     if args.roofline_only:
         return {"workload": args.workload, "precision": args.precision,
                 "roofline": measure_roofline(rr, row_ptr, col_idx, N, F, nnz, k, lams, opts, dev,
                                              stream, args.workload)}
+    if args.only == "batched":
+        return {"batched": measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world,
+                                           args.batch_targets)}
+    if args.only == "many":
+        return {"many": measure_many(rr, dev, stream, opts)}
+    if args.only == "learned":
+        return {"learned": measure_learned(rr, X, row_ptr, col_idx, k, opts, dev, stream,
+                                           n_pairs=args.pairs)}
 
     def step(host=None):
         if host is None:
@@ -473,11 +493,12 @@ def run_ours(args, rank, world, local):
 
     batched = many = learned = None
     if not args.no_batch and args.workload == WORKLOAD:
-        batched = measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world)
+        batched = measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world,
+                                  args.batch_targets)
     if not args.no_many:
         many = measure_many(rr, dev, stream, opts)
     if not args.no_learned and args.workload == WORKLOAD:
-        learned = measure_learned(rr, X, row_ptr, col_idx, k, opts, dev, stream)
+        learned = measure_learned(rr, X, row_ptr, col_idx, k, opts, dev, stream, n_pairs=args.pairs)
 
     last = all_infos[-1]
     out = {
@@ -503,6 +524,8 @@ def run_ours(args, rank, world, local):
                       "true_rel_res": [i["true_rel_res"] for i in last],
                       "kmeans_iters": last[0]["kmeans_iters"], "k_eff": last[0]["k_eff"],
                       "gram_tensor_cores": bool(last[0]["gram_tensor_cores"]),
+                      "gather_kernel": {"X": "staged" if last[0]["gather_staged"] & 1 else "lanes",
+                                        "Xt": "staged" if last[0]["gather_staged"] & 2 else "lanes"},
                       "step_ms": [round(t, 3) for t in step_ms]},
         "e2e": e2e, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches,
         "batched": batched, "many": many, "learned": learned,

@@ -122,6 +122,8 @@ typedef struct {
   int32_t gram_tensor_cores; /* 1 if rr_setup formed the coarse Gram on the tensor cores */
   int32_t fallbacks;      /* rr_solve_fcg with a network: steps redone with the Cholesky
                              coarse solve */
+  int32_t gather_staged;  /* FP32 gather kernel in use: bit 0 set if the X pass is staged,
+                             bit 1 if the X^T pass is (see rr_options.gather) */
   double setup_phase_ms[8]; /* rr_setup wall time by phase: 0 copy + validation of X, 1 CSC
                                build, 2 k-means++ seeding, 3 Lloyd steps, 4 compaction + member
                                lists, 5 counts + coarse Gram, 6 coarse factor + smoother,

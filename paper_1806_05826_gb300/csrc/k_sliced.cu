@@ -23,6 +23,7 @@
 // sums in order: the same operations in the same order as the lane-per-piece
 // form, so both forms give identical bits.
 #include <type_traits>
+#include <vector>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -39,7 +40,7 @@ constexpr int kChunkWords = kTeamThreads;            // words of one staged chun
 constexpr int kStagesW = 4;                          // stages in each team's ring
 constexpr int kStagePtrs = kChunkWords + 8;          // staged piece pointers / slots per stage
 constexpr int kStageSmem = 16 * kChunkWords + 8 * kStagePtrs + 32;   // words, pointers, slots, meta
-constexpr int kTeamSmem = 4 * kChunkWords + kStagesW * kStageSmem + 8 * kStagesW;
+constexpr int kTeamSmem = 2 * 4 * kChunkWords + kStagesW * kStageSmem + 8 * kStagesW;
 
 // one thread per (outer o, slice b): entry range of the segment by binary search
 __global__ void k_seg_bounds(int64_t n_outer, int32_t nb, int32_t W,
@@ -187,8 +188,16 @@ __global__ void k_slice_prep(int64_t n, const double *__restrict__ x,
        i += (int64_t)gridDim.x * blockDim.x) {
     double v;
     if (kCombine) {
+      // slots in order, four loads in flight
       v = 0.0;
-      for (int32_t q = in_slot_ptr[i]; q < in_slot_ptr[i + 1]; ++q) v += in_psum[q];
+      const int32_t q1 = in_slot_ptr[i + 1];
+      for (int32_t q = in_slot_ptr[i]; q < q1; q += 4) {
+        double t[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[u] = q + u < q1 ? in_psum[q + u] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v += t[u];
+      }
     } else {
       v = x[i];
     }
@@ -307,7 +316,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather_staged(
   float *xs = reinterpret_cast<float *>(smem_raw);
   unsigned char *team_base = smem_raw + sizeof(float) * slice_floats + (size_t)team * kTeamSmem;
   float *wsum = reinterpret_cast<float *>(team_base);
-  unsigned char *stage0 = team_base + sizeof(float) * kChunkWords;
+  unsigned char *stage0 = team_base + 2 * sizeof(float) * kChunkWords;
   uint64_t *full = reinterpret_cast<uint64_t *>(stage0 + (size_t)kStagesW * kStageSmem);
   int32_t *abort_flag = reinterpret_cast<int32_t *>(smem_raw + sizeof(float) * slice_floats +
                                                     (size_t)kTeams * kTeamSmem);
@@ -379,26 +388,29 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather_staged(
       atomicExch(abort_flag, 1);
     }
     const StageMeta m = *meta_of(s);
+    float *ws = wsum + (q & 1) * kChunkWords;   // word sums: two buffers, alternating
     if (ok && tt < m.nw) {
       const uint4 w = words_of(s)[tt];
-      wsum[tt] = ((xs[w.x & 0xffffu] + xs[w.x >> 16]) + (xs[w.y & 0xffffu] + xs[w.y >> 16])) +
-                 ((xs[w.z & 0xffffu] + xs[w.z >> 16]) + (xs[w.w & 0xffffu] + xs[w.w >> 16]));
+      ws[tt] = ((xs[w.x & 0xffffu] + xs[w.x >> 16]) + (xs[w.y & 0xffffu] + xs[w.y >> 16])) +
+               ((xs[w.z & 0xffffu] + xs[w.z >> 16]) + (xs[w.w & 0xffffu] + xs[w.w >> 16]));
     }
+    // one barrier per chunk: it publishes this chunk's word sums, and every
+    // thread has finished the previous chunk's piece sums, so that chunk's
+    // stage can be refilled and its word-sum buffer reused by the next chunk
     team_sync(team);
     if (*(volatile int32_t *)abort_flag) break;
+    if (tt == 0 && q >= 1 && issued < nq) {
+      tc::fence_proxy_async_smem();
+      issue(issued);   // into the stage of chunk q - 1
+      ++issued;
+      if (issued < nq) load_meta(issued);
+    }
     const int32_t *pws = pw_of(s) - m.pal, *sls = slot_of(s) - m.pal;
     for (int32_t p = m.pa + tt; p < m.pb; p += kTeamThreads) {
       const int32_t w0 = pws[p] - m.wa, w1 = pws[p + 1] - m.wa;
-      float acc = wsum[w0];
-      for (int32_t w = w0 + 1; w < w1; ++w) acc += wsum[w];
+      float acc = ws[w0];
+      for (int32_t w = w0 + 1; w < w1; ++w) acc += ws[w];
       out_psum[sls[p]] = (double)acc;
-    }
-    team_sync(team);   // the stage and wsum are free again
-    if (tt == 0 && issued < nq) {
-      tc::fence_proxy_async_smem();
-      issue(issued);
-      ++issued;
-      if (issued < nq) load_meta(issued);
     }
   }
   if (tt == 0 && *(volatile int32_t *)abort_flag) {
@@ -495,26 +507,59 @@ __device__ __forceinline__ void epilogue(const CscEpilogue &ep, int64_t i, doubl
   }
 }
 
-// One 8-lane group per feature: t_i = sum of its slots; then the mode's epilogue;
-// per-block partial dots in a fixed order.
+// t_i = sum of the slots of feature i, then the mode's epilogue; per-block
+// partial dots in a fixed order. Features with more than kLightSlots slots
+// (the long columns, listed in heavy[]) are summed first, one warp each (32
+// lanes strided, then a fixed shuffle tree); every other feature by one 8-lane
+// group with up to 4 slot loads in flight per lane. Fixed assignment and
+// order: every run gives identical bits.
+constexpr int kLightSlots = 32;
+
 __global__ void __launch_bounds__(kThreads) k_sliced_epilogue(int64_t F, const int32_t *__restrict__ slot_ptr,
                                                               const double *__restrict__ psum,
-                                                              CscEpilogue ep) {
+                                                              const int32_t *__restrict__ heavy,
+                                                              int32_t n_heavy, CscEpilogue ep) {
   if (ep.stop && *ep.stop) return;
   __shared__ double sm[kWarps + 1];
+  const int lane = threadIdx.x & 31;
   const int lane8 = threadIdx.x & 7, gw = (threadIdx.x >> 3) & 3;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   double dot = 0.0;
+  for (int64_t h = warp; h < n_heavy; h += nwarps) {   // warp-uniform loop
+    const int32_t i = heavy[h];
+    const int32_t q0 = slot_ptr[i], q1 = slot_ptr[i + 1];
+    double s0 = 0.0, s1 = 0.0;
+    int32_t q = q0 + lane;
+    for (; q + 32 < q1; q += 64) {
+      s0 += psum[q];
+      s1 += psum[q + 32];
+    }
+    if (q < q1) s0 += psum[q];
+    double s = warp_sum(s0 + s1);
+    if (lane == 0) epilogue(ep, i, s, dot);
+  }
   for (int64_t i0 = warp * 4; i0 < F; i0 += nwarps * 4) {   // warp-uniform loop
     const int64_t i = i0 + gw;
     double s = 0.0;
-    if (i < F)
-      for (int32_t q = slot_ptr[i] + lane8; q < slot_ptr[i + 1]; q += 8) s += psum[q];
+    bool light = false;
+    if (i < F) {
+      const int32_t q0 = slot_ptr[i], q1 = slot_ptr[i + 1];
+      light = q1 - q0 <= kLightSlots;
+      if (light) {
+        double v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int32_t q = q0 + lane8 + 8 * u;
+          v[u] = q < q1 ? psum[q] : 0.0;
+        }
+        s = (v[0] + v[1]) + (v[2] + v[3]);
+      }
+    }
     s += __shfl_xor_sync(0xffffffffu, s, 4);
     s += __shfl_xor_sync(0xffffffffu, s, 2);
     s += __shfl_xor_sync(0xffffffffu, s, 1);
-    if (i < F && lane8 == 0) epilogue(ep, i, s, dot);
+    if (light && lane8 == 0) epilogue(ep, i, s, dot);
   }
   const double tot = block_sum(dot, sm);
   if (threadIdx.x == 0 && ep.dot_part) ep.dot_part[blockIdx.x] = tot;
@@ -628,6 +673,19 @@ rr_status sliced_build(int64_t n_outer, int64_t n_inner, const int64_t *outer_pt
     RR_CUDA(cudaMemcpyAsync(P.pw + P.npieces, &last, sizeof(int32_t), cudaMemcpyHostToDevice, st));
     RR_LAUNCH(k_to_i32, grid_for(n_outer + 1, kThreads), kThreads, 0, st, n_outer + 1, slot_base,
               P.slot_ptr);
+    {   // outer indices with more than kLightSlots slots (summed one warp each)
+      std::vector<int32_t> sp(n_outer + 1), hv;
+      RR_CUDA(cudaMemcpyAsync(sp.data(), P.slot_ptr, sizeof(int32_t) * (n_outer + 1),
+                              cudaMemcpyDeviceToHost, st));
+      RR_CUDA(cudaStreamSynchronize(st));
+      for (int64_t o = 0; o < n_outer; ++o)
+        if (sp[o + 1] - sp[o] > kLightSlots) hv.push_back((int32_t)o);
+      P.n_heavy = (int32_t)hv.size();
+      RR_CUDA(cudaMalloc(&P.heavy, sizeof(int32_t) * std::max<size_t>(1, hv.size())));
+      if (!hv.empty())
+        RR_CUDA(cudaMemcpyAsync(P.heavy, hv.data(), sizeof(int32_t) * hv.size(),
+                                cudaMemcpyHostToDevice, st));
+    }
     // tasks: about two CTAs per SM in total, split evenly over the slices
     P.tasks_per_slice = std::max<int32_t>(1, (2 * kSMs + P.nb - 1) / P.nb);
     P.ntasks = P.nb * P.tasks_per_slice;
@@ -684,6 +742,7 @@ void sliced_free(SlicedPattern &P) {
   cudaFree(P.order);
   cudaFree(P.chunk_p);
   cudaFree(P.chunk_w);
+  cudaFree(P.heavy);
   cudaFree(P.task_c);
   cudaFree(P.xq);
   P = SlicedPattern{};
@@ -758,7 +817,8 @@ rr_status sliced_slot_sum(const SlicedPattern &P, double *out, cudaStream_t st) 
 }
 
 rr_status sliced_epilogue(const SlicedPattern &P, const CscEpilogue &ep, cudaStream_t st) {
-  RR_LAUNCH(k_sliced_epilogue, kVecGrid, kThreads, 0, st, P.n_outer, P.slot_ptr, P.psum, ep);
+  RR_LAUNCH(k_sliced_epilogue, kVecGrid, kThreads, 0, st, P.n_outer, P.slot_ptr, P.psum, P.heavy,
+            P.n_heavy, ep);
   return RR_OK;
 }
 

@@ -189,6 +189,8 @@ struct SlicedPattern {
   int32_t *chunk_p = nullptr;    // [n_chunks+1] first piece of every chunk
   int32_t *chunk_w = nullptr;    // [n_chunks+1] first word of every chunk
   bool staged = false;           // FP32 passes use the staged gather (needs the chunks)
+  int32_t n_heavy = 0;           // outer indices with many slots (summed one warp each)
+  int32_t *heavy = nullptr;      // [n_heavy]
   int32_t *task_c = nullptr;     // [ntasks+1]  chunks of each task
   int32_t *err = nullptr;        // device error word (DEV_TIMEOUT from a bounded wait)
   void *xq = nullptr;            // [n_inner]   the gathered vector in the accumulation type

@@ -888,6 +888,7 @@ rr_status solve_many_impl(int32_t n, rr_handle *const *hs, const double *const *
     I.omega = h->omega;
     I.setup_ms = h->setup_ms;
     I.gram_tensor_cores = h->gram_on_tensor_cores ? 1 : 0;
+    I.gather_staged = (h->pcsr.staged ? 1 : 0) | (h->pcsc.staged ? 2 : 0);
     I.fallbacks = 0;
     for (int j = 0; j < 8; ++j) I.setup_phase_ms[j] = h->phase_ms[j];
   }
@@ -1022,6 +1023,7 @@ rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info
     info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     info->launches = rr_launch_counter - l0;
     info->gram_tensor_cores = h->gram_on_tensor_cores ? 1 : 0;
+    info->gather_staged = (h->pcsr.staged ? 1 : 0) | (h->pcsc.staged ? 2 : 0);
     for (int i = 0; i < 8; ++i) info->setup_phase_ms[i] = h->phase_ms[i];
   }
   return s;
@@ -1062,6 +1064,7 @@ rr_status rr_solve_fcg(rr_handle *h, const rr_mlp *net, const double *y, double 
     info->solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     info->launches = rr_launch_counter - l0;
     info->gram_tensor_cores = h->gram_on_tensor_cores ? 1 : 0;
+    info->gather_staged = (h->pcsr.staged ? 1 : 0) | (h->pcsc.staged ? 2 : 0);
     for (int i = 0; i < 8; ++i) info->setup_phase_ms[i] = h->phase_ms[i];
   }
   return s;

@@ -50,7 +50,7 @@ class rr_info(ctypes.Structure):
                 ("omega", ctypes.c_double), ("setup_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("launches", ctypes.c_int64),
                 ("gram_tensor_cores", ctypes.c_int32), ("fallbacks", ctypes.c_int32),
-                ("setup_phase_ms", ctypes.c_double * 8)]
+                ("gather_staged", ctypes.c_int32), ("setup_phase_ms", ctypes.c_double * 8)]
 
     def as_dict(self):
         d = {name: getattr(self, name) for name, _ in self._fields_}
