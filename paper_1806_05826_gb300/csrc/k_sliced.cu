@@ -6,7 +6,9 @@
 // memory; inside a slice an index is a 16-bit offset (half the bytes of an
 // int32 index). The entries of every (outer index, slice) segment are padded
 // to whole 16-byte words (8 offsets; the pad offset W reads a zero kept in
-// shared memory) and the segment is cut into pieces of at most kPieceWords
+// shared memory; the 8 offsets of word w stored rotated by (w / 4) mod 8 so
+// that dense runs gather without bank conflicts) and the segment is cut into
+// pieces of at most kPieceWords
 // words. Pieces are stored slice-major, so one CTA streams a contiguous range
 // of them against the one vector slice it holds; each piece is summed by one
 // lane (in a fixed order) into its own slot, numbered outer-major, and the
@@ -118,9 +120,15 @@ __global__ void k_fill_pieces(int64_t n_outer, int32_t nb, int32_t W,
       pw[p0 + q] = (int32_t)(w0 + q * kPieceWords);
       slot[p0 + q] = (int32_t)(slot_base[o] + pre + q);
     }
+    // entry u goes to word u / 8 at position (u + rot) mod 8, rot = (word >> 2) mod 8:
+    // in a dense run (consecutive offsets) the 8 lanes whose words are 4 apart
+    // then read 8 different shared-memory banks at every step of the gather
     uint16_t *dst = idx + w0 * 8;
-    for (int64_t u = lane; u < nw * 8; u += 32)
-      dst[u] = u < len ? (uint16_t)(inner[s + u] - key) : (uint16_t)W;
+    for (int64_t u = lane; u < nw * 8; u += 32) {
+      const int64_t wl = u >> 3;
+      const int32_t rot = (int32_t)(((w0 + wl) >> 2) & 7);
+      dst[(wl << 3) + ((u + rot) & 7)] = u < len ? (uint16_t)(inner[s + u] - key) : (uint16_t)W;
+    }
   }
 }
 
