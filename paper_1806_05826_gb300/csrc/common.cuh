@@ -41,6 +41,30 @@ extern thread_local int64_t rr_launch_counter;
     }                                                                              \
   } while (0)
 
+// Launch with programmatic dependent launch: the kernel may be scheduled while
+// its predecessor on the stream finishes; it must call rr::pdl_wait() before it
+// reads anything (every kernel launched this way does so first).
+#define RR_LAUNCH_PDL(kernel_, grid_, block_, smem_, stream_, ...)                 \
+  do {                                                                             \
+    cudaLaunchConfig_t cfg_{};                                                     \
+    cfg_.gridDim = dim3(grid_);                                                    \
+    cfg_.blockDim = dim3(block_);                                                  \
+    cfg_.dynamicSmemBytes = (smem_);                                               \
+    cfg_.stream = (stream_);                                                       \
+    cudaLaunchAttribute at_[1];                                                    \
+    at_[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;                \
+    at_[0].val.programmaticStreamSerializationAllowed = 1;                         \
+    cfg_.attrs = at_;                                                              \
+    cfg_.numAttrs = 1;                                                             \
+    cudaError_t e_ = cudaLaunchKernelEx(&cfg_, kernel_, __VA_ARGS__);              \
+    ++rr_launch_counter;                                                           \
+    if (e_ != cudaSuccess) {                                                       \
+      rr_set_error("%s:%d: launch %s: %s", __FILE__, __LINE__, #kernel_,           \
+                   cudaGetErrorString(e_));                                        \
+      return RR_CUDA_ERROR;                                                        \
+    }                                                                              \
+  } while (0)
+
 namespace rr {
 
 constexpr int kThreads = 256;
@@ -70,6 +94,10 @@ enum DevError : int32_t {
 
 #ifdef __CUDACC__
 namespace rr {
+
+// Waits until the grids this kernel depends on have completed and their
+// memory is visible (a no-op unless launched with RR_LAUNCH_PDL).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 __device__ __forceinline__ void set_dev_error(int32_t *err, int32_t code) {
   atomicCAS(err, 0, code);

@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(kThreads) k_bspmm(int64_t n_units, const int64
                                                     const T *__restrict__ V, int64_t ldv,
                                                     T *__restrict__ out, int64_t ldo,
                                                     const int32_t *__restrict__ slab_active) {
+  pdl_wait();
   using V2 = typename Vec2<T>::type;
   const int slab = blockIdx.y;
   if (slab_active && !slab_active[slab]) return;
@@ -179,6 +180,7 @@ __global__ void __launch_bounds__(kThreads) k_bepi(int64_t F, int32_t S, int64_t
                                                    const T *__restrict__ Zp,
                                                    const int64_t *__restrict__ col_ptr,
                                                    const BatchCol *__restrict__ col, BEpi ep) {
+  pdl_wait();
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
   const int64_t c = (int64_t)blockIdx.y * kSlab + tx;
   const bool valid = c < S;
@@ -231,6 +233,7 @@ __global__ void __launch_bounds__(kThreads) k_bstart(int64_t F, int32_t S, int32
                                                      double *__restrict__ b, double *__restrict__ w,
                                                      double *__restrict__ r, double *__restrict__ z1,
                                                      float *__restrict__ V, double *__restrict__ part) {
+  pdl_wait();
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
   const int64_t c = (int64_t)blockIdx.y * kSlab + tx;
   const bool valid = c < S;
@@ -270,6 +273,7 @@ __global__ void __launch_bounds__(kThreads) k_brestart(int64_t F, int32_t S, int
                                                        const double *__restrict__ rt,
                                                        double *__restrict__ r, double *__restrict__ z1,
                                                        float *__restrict__ V) {
+  pdl_wait();
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
   const int64_t c = (int64_t)blockIdx.y * kSlab + tx;
   if (c >= S || !flag[c]) return;
@@ -294,6 +298,7 @@ __global__ void __launch_bounds__(kThreads) k_brestrict(const RestrictItem *__re
                                                         const double *__restrict__ r1,
                                                         const BatchCol *__restrict__ col,
                                                         double *__restrict__ ip) {
+  pdl_wait();
   __shared__ double red[4][kSlab];
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
   const int64_t c = (int64_t)blockIdx.y * kSlab + tx;
@@ -317,6 +322,7 @@ __global__ void __launch_bounds__(kThreads) k_bcombine(int32_t k, int32_t kpad, 
                                                        const double *__restrict__ s,
                                                        const BatchCol *__restrict__ col,
                                                        double *__restrict__ rc) {
+  pdl_wait();
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
   const int64_t c = (int64_t)blockIdx.y * kSlab + tx;
   const bool active = c < S && !col[c].conv;
@@ -340,6 +346,7 @@ __global__ void __launch_bounds__(kThreads) k_brestrict_err(const RestrictItem *
                                                             const double *__restrict__ z1,
                                                             const BatchCol *__restrict__ col,
                                                             double *__restrict__ ip) {
+  pdl_wait();
   __shared__ double red[4][kSlab];
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
   const int64_t c = (int64_t)blockIdx.y * kSlab + tx;
@@ -365,6 +372,7 @@ __global__ void k_bharvest(int32_t S, int64_t ld, int32_t k, const double *__res
                            const double *__restrict__ rcE, const BatchCol *__restrict__ col,
                            const BatchGlobal *__restrict__ g, float *__restrict__ Xs,
                            float *__restrict__ Ts, int64_t *__restrict__ valid, int64_t slots) {
+  pdl_wait();
   const int64_t c = blockIdx.x;
   if (c >= S || col[c].conv) return;
   const int64_t slot = (int64_t)g->iter * S + c;
@@ -403,6 +411,7 @@ __global__ void __launch_bounds__(kThreads) k_bcoarse(int32_t k, int32_t kpad, i
                                                       const double *__restrict__ rc,
                                                       const BatchCol *__restrict__ col,
                                                       double *__restrict__ ec) {
+  pdl_wait();
   __shared__ double As[kCK][kCT + 2];
   __shared__ double Bs[kCK][kCT + 2];
   const int i0 = blockIdx.x * kCT;
@@ -464,6 +473,7 @@ __global__ void __launch_bounds__(kThreads) k_bprolong(int64_t F, int32_t S, int
                                                        const BatchCol *__restrict__ col,
                                                        const double *__restrict__ z1,
                                                        double *__restrict__ z2, float *__restrict__ V) {
+  pdl_wait();
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
   const int64_t c = (int64_t)blockIdx.y * kSlab + tx;
   if (c >= S || col[c].conv) return;
@@ -483,6 +493,7 @@ __global__ void __launch_bounds__(kThreads) k_bdirection(int64_t F, int32_t S, i
                                                          const BatchCol *__restrict__ col,
                                                          const double *__restrict__ z,
                                                          double *__restrict__ p, float *__restrict__ V) {
+  pdl_wait();
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
   const int64_t c = (int64_t)blockIdx.y * kSlab + tx;
   if (c >= S || col[c].conv) return;
@@ -509,6 +520,7 @@ __global__ void __launch_bounds__(kThreads) k_bupdate(int64_t F, int32_t S, int6
                                                       double *__restrict__ z1, float *__restrict__ V,
                                                       double *__restrict__ part, BatchGlobal *g,
                                                       int32_t *slab_active, int32_t n_slabs) {
+  pdl_wait();
   if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
     g->any_active = 0;
     for (int s = 0; s < n_slabs; ++s) slab_active[s] = 0;
@@ -540,6 +552,7 @@ __global__ void __launch_bounds__(kThreads) k_bfinish(int32_t mode, int32_t S, i
                                                       const double *__restrict__ part, int32_t nb,
                                                       double tol, BatchCol *col, BatchGlobal *g,
                                                       int32_t *slab_active) {
+  pdl_wait();
   __shared__ double red[4][kSlab];
   const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
   const int64_t c = (int64_t)blockIdx.x * kSlab + tx;
@@ -605,6 +618,7 @@ __global__ void __launch_bounds__(kThreads) k_bfinish(int32_t mode, int32_t S, i
 }
 
 __global__ void k_bloop_condition(cudaGraphConditionalHandle hc, const BatchGlobal *__restrict__ g) {
+  pdl_wait();
   if (threadIdx.x == 0) cudaGraphSetConditional(hc, (g->any_active && g->iter < g->limit) ? 1u : 0u);
 }
 
@@ -694,7 +708,7 @@ rr_status launch_bspmm(int64_t n_units, const int64_t *ubeg, const int64_t *uend
                        const int32_t *slab_active, cudaStream_t st) {
   const dim3 grid((unsigned)grid_for(n_units, kWarps), (unsigned)n_slabs);
   constexpr int kUnroll = sizeof(T) == 4 ? 8 : 4;   // row segments in flight per warp
-  RR_LAUNCH((k_bspmm<T, kUnroll>), grid, kThreads, 0, st, n_units, ubeg, uend, idx, V, ldv, out, ldo,
+  RR_LAUNCH_PDL((k_bspmm<T, kUnroll>), grid, kThreads, 0, st, n_units, ubeg, uend, idx, V, ldv, out, ldo,
             slab_active);
   return RR_OK;
 }
@@ -731,13 +745,13 @@ rr_status bapply_f32(const BatchRun &R, cudaStream_t st) {
 
 rr_status bepilogue_f32(const BatchRun &R, const BEpi &ep, cudaStream_t st) {
   const dim3 grid(kBEpiBlocks, (unsigned)R.n_slabs);
-  RR_LAUNCH(k_bepi<float>, grid, kThreads, 0, st, R.h->F, R.S, R.ld, R.B->uptr2, R.B->Zp,
+  RR_LAUNCH_PDL(k_bepi<float>, grid, kThreads, 0, st, R.h->F, R.S, R.ld, R.B->uptr2, R.B->Zp,
             R.h->col_ptr, R.B->col, ep);
   return RR_OK;
 }
 
 rr_status bfinish(const BatchRun &R, int32_t mode, cudaStream_t st) {
-  RR_LAUNCH(k_bfinish, (unsigned)R.n_slabs, kThreads, 0, st, mode, R.S, R.ld, R.B->part,
+  RR_LAUNCH_PDL(k_bfinish, (unsigned)R.n_slabs, kThreads, 0, st, mode, R.S, R.ld, R.B->part,
             kBEpiBlocks, R.tol, R.B->col, R.B->g, R.B->slab_active);
   return RR_OK;
 }
@@ -754,35 +768,35 @@ rr_status biteration(const BatchRun &R, cudaStream_t st) {
   RR_TRY(bepilogue_f32(R, BEpi{BEPI_PRE, B->z1, B->r, B->r1, nullptr}, st));
   // coarse correction: r_c = P^T r1; e_c = A_c^-1 r_c; z2 = z1 + P e_c
   const RestrictPlan &pl = h->rplan;
-  RR_LAUNCH(k_brestrict, dim3((unsigned)std::max(1, std::min(pl.n_items, kSMs * 4)), (unsigned)R.n_slabs),
+  RR_LAUNCH_PDL(k_brestrict, dim3((unsigned)std::max(1, std::min(pl.n_items, kSMs * 4)), (unsigned)R.n_slabs),
             kThreads, 0, st, pl.items, pl.n_items, R.S, R.ld, h->members, B->r1, B->col, B->ip);
-  RR_LAUNCH(k_bcombine, dim3((unsigned)((kpad + 3) / 4), (unsigned)R.n_slabs), kThreads, 0, st,
+  RR_LAUNCH_PDL(k_bcombine, dim3((unsigned)((kpad + 3) / 4), (unsigned)R.n_slabs), kThreads, 0, st,
             B->k, kpad, R.S, R.ld, pl.item_ptr, B->ip, h->s, B->col, B->rcB);
   if (R.hv) {
     const Harvest &hv = *R.hv;
-    RR_LAUNCH(k_brestrict_err, dim3((unsigned)std::max(1, std::min(pl.n_items, kSMs * 4)), (unsigned)R.n_slabs),
+    RR_LAUNCH_PDL(k_brestrict_err, dim3((unsigned)std::max(1, std::min(pl.n_items, kSMs * 4)), (unsigned)R.n_slabs),
               kThreads, 0, st, pl.items, pl.n_items, R.S, R.ld, h->members, hv.wref, B->w, B->z1,
               B->col, hv.ipE);
-    RR_LAUNCH(k_bcombine, dim3((unsigned)((kpad + 3) / 4), (unsigned)R.n_slabs), kThreads, 0, st,
+    RR_LAUNCH_PDL(k_bcombine, dim3((unsigned)((kpad + 3) / 4), (unsigned)R.n_slabs), kThreads, 0, st,
               B->k, kpad, R.S, R.ld, pl.item_ptr, hv.ipE, h->s, B->col, hv.rcE);
-    RR_LAUNCH(k_bharvest, (unsigned)R.S, kThreads, 0, st, R.S, R.ld, B->k, B->rcB, hv.rcE, B->col,
+    RR_LAUNCH_PDL(k_bharvest, (unsigned)R.S, kThreads, 0, st, R.S, R.ld, B->k, B->rcB, hv.rcE, B->col,
               B->g, hv.Xs, hv.Ts, hv.valid, hv.slots);
   }
-  RR_LAUNCH(k_bcoarse, dim3((unsigned)(kpad / kCT), (unsigned)R.n_slabs), kThreads, 0, st, B->k,
+  RR_LAUNCH_PDL(k_bcoarse, dim3((unsigned)(kpad / kCT), (unsigned)R.n_slabs), kThreads, 0, st, B->k,
             kpad, R.S, R.nrhs, R.ld, B->AinvB, B->rcB, B->col, B->ecB);
-  RR_LAUNCH(k_bprolong, vgrid, kThreads, 0, st, F, R.S, R.ld, h->labels, h->s, B->ecB, B->col,
+  RR_LAUNCH_PDL(k_bprolong, vgrid, kThreads, 0, st, F, R.S, R.ld, h->labels, h->s, B->ecB, B->col,
             B->z1, B->z2, B->V);
   // post-smoothing: r2 = r - A z2; z = z2 + omega D^-1 r2; <r, z>
   RR_TRY(bapply_f32(R, st));
   RR_TRY(bepilogue_f32(R, BEpi{BEPI_POST, B->z2, B->r, B->z, B->part}, st));
   RR_TRY(bfinish(R, BFIN_RZ, st));
   // direction and q = A p; <p, q>
-  RR_LAUNCH(k_bdirection, vgrid, kThreads, 0, st, F, R.S, R.ld, B->col, B->z, B->p, B->V);
+  RR_LAUNCH_PDL(k_bdirection, vgrid, kThreads, 0, st, F, R.S, R.ld, B->col, B->z, B->p, B->V);
   RR_TRY(bapply_f32(R, st));
   RR_TRY(bepilogue_f32(R, BEpi{BEPI_PCG, B->p, nullptr, B->q, B->part}, st));
   RR_TRY(bfinish(R, BFIN_PQ, st));
   // update; ||r||^2; stopping test
-  RR_LAUNCH(k_bupdate, vgrid, kThreads, 0, st, F, R.S, R.ld, h->col_ptr, B->col, B->p, B->q, B->w,
+  RR_LAUNCH_PDL(k_bupdate, vgrid, kThreads, 0, st, F, R.S, R.ld, h->col_ptr, B->col, B->p, B->q, B->w,
             B->r, B->z1, B->V, B->part, B->g, B->slab_active, R.n_slabs);
   RR_TRY(bfinish(R, BFIN_RR, st));
   return RR_OK;
@@ -797,7 +811,7 @@ rr_status btrue_residual(const BatchRun &R, cudaStream_t st) {
   RR_TRY(launch_bspmm<double>(B->n_units2, B->ubeg2, B->uend2, h->row_idx, B->U64, R.ld, B->Zp64,
                               R.ld, R.n_slabs, nullptr, st));
   const dim3 grid(kBEpiBlocks, (unsigned)R.n_slabs);
-  RR_LAUNCH(k_bepi<double>, grid, kThreads, 0, st, h->F, R.S, R.ld, B->uptr2, B->Zp64, h->col_ptr,
+  RR_LAUNCH_PDL(k_bepi<double>, grid, kThreads, 0, st, h->F, R.S, R.ld, B->uptr2, B->Zp64, h->col_ptr,
             B->col, BEpi{BEPI_RESID, B->w, B->b, B->rt, B->part});
   RR_TRY(bfinish(R, BFIN_TRUE, st));
   return RR_OK;
@@ -1054,7 +1068,7 @@ extern "C" rr_status rr_solve_batch(rr_handle *h, int32_t nrhs, const double *Y,
   RR_TRY(launch_bspmm<double>(B->n_units2, B->ubeg2, B->uend2, h->row_idx, B->U64, ldy, B->Zp64,
                               ldy, (int32_t)(ldy / kSlab), nullptr, st));
   const dim3 vgrid(kBEpiBlocks, (unsigned)n_slabs);
-  RR_LAUNCH(k_bstart, vgrid, kThreads, 0, st, F, S, nrhs, ld, B->uptr2, B->Zp64, ldy, h->col_ptr,
+  RR_LAUNCH_PDL(k_bstart, vgrid, kThreads, 0, st, F, S, nrhs, ld, B->uptr2, B->Zp64, ldy, h->col_ptr,
             B->col, B->b, B->w, B->r, B->z1, B->V, B->part);
   BatchGlobal G0{0, h->opt.max_iter, 0, 0};
   *B->g_host = G0;
@@ -1108,7 +1122,7 @@ extern "C" rr_status rr_solve_batch(rr_handle *h, int32_t nrhs, const double *Y,
     RR_CUDA(cudaMemcpyAsync(B->slab_active, B->slab_host, sizeof(int32_t) * n_slabs, cudaMemcpyHostToDevice, st));
     B->g_host->any_active = 1;
     RR_CUDA(cudaMemcpyAsync(B->g, B->g_host, sizeof(BatchGlobal), cudaMemcpyHostToDevice, st));
-    RR_LAUNCH(k_brestart, vgrid, kThreads, 0, st, F, S, ld, B->flag, h->col_ptr, B->col, B->rt,
+    RR_LAUNCH_PDL(k_brestart, vgrid, kThreads, 0, st, F, S, ld, B->flag, h->col_ptr, B->col, B->rt,
               B->r, B->z1, B->V);
   }
   const dim3 ogrid((unsigned)((F + 31) / 32), (unsigned)((S + 31) / 32));
@@ -1212,7 +1226,7 @@ extern "C" rr_status rr_harvest(rr_handle *h, int32_t nrhs, const double *Y, dou
   RR_TRY(launch_bspmm<double>(B->n_units2, B->ubeg2, B->uend2, h->row_idx, B->U64, ldy, B->Zp64,
                               ldy, (int32_t)(ldy / kSlab), nullptr, st));
   const dim3 vgrid(kBEpiBlocks, (unsigned)n_slabs);
-  RR_LAUNCH(k_bstart, vgrid, kThreads, 0, st, F, S, nrhs, ld, B->uptr2, B->Zp64, ldy, h->col_ptr,
+  RR_LAUNCH_PDL(k_bstart, vgrid, kThreads, 0, st, F, S, nrhs, ld, B->uptr2, B->Zp64, ldy, h->col_ptr,
             B->col, B->b, B->w, B->r, B->z1, B->V, B->part);
   BatchGlobal G0{0, max_iter, 0, 0};
   *B->g_host = G0;

@@ -21,6 +21,7 @@ __device__ __forceinline__ bool stopped(const int32_t *stop) { return stop && *s
 // partial <a, b> per block (kVecGrid blocks)
 __global__ void k_fcg_dot(int64_t F, const double *__restrict__ a, const double *__restrict__ b,
                           double *__restrict__ part, const int32_t *__restrict__ stop) {
+  pdl_wait();
   if (stopped(stop)) return;
   __shared__ double sm[kWarps + 1];
   double acc = 0.0;
@@ -36,6 +37,7 @@ __global__ void k_fcg_direction(int64_t F, const double *__restrict__ part_zq, i
                                 const FcgScalars *__restrict__ S, const double *__restrict__ z,
                                 const double *__restrict__ p_prev, double *__restrict__ p,
                                 const int32_t *__restrict__ stop) {
+  pdl_wait();
   if (stopped(stop)) return;
   __shared__ double sm[kWarps + 1];
   const bool first = S->first;
@@ -49,6 +51,7 @@ __global__ void k_fcg_direction(int64_t F, const double *__restrict__ part_zq, i
 __global__ void k_fcg_dots(int64_t F, const double *__restrict__ p, const double *__restrict__ r,
                            const double *__restrict__ q, double *__restrict__ part3, int n,
                            const int32_t *__restrict__ stop) {
+  pdl_wait();
   if (stopped(stop)) return;
   __shared__ double sm[kWarps + 1];
   double pr = 0.0, rq = 0.0, qq = 0.0;
@@ -73,6 +76,7 @@ __global__ void k_fcg_dots(int64_t F, const double *__restrict__ p, const double
 // coarse solve (skip_fb = 0) or kept (skip_fb = 1).
 __global__ void k_fcg_decide(const double *__restrict__ part_rz, const double *__restrict__ part_pq,
                              const double *__restrict__ part3, int n, FcgScalars *S) {
+  pdl_wait();
   __shared__ double sm[kWarps + 1];
   if (S->converged) {
     if (threadIdx.x == 0) S->skip_fb = 1;
@@ -102,6 +106,7 @@ __global__ void k_fcg_update(int64_t F, const double *__restrict__ part_pq,
                              double *__restrict__ z1, double *__restrict__ p_prev,
                              double *__restrict__ q_prev, double *__restrict__ part_rr,
                              const FcgScalars *__restrict__ S) {
+  pdl_wait();
   if (S->converged) return;
   __shared__ double sm[kWarps + 1];
   const double pq = sum_partials(part_pq, n, sm);
@@ -125,6 +130,7 @@ __global__ void k_fcg_update(int64_t F, const double *__restrict__ part_pq,
 
 __global__ void k_fcg_finish(const double *__restrict__ part_rr, const double *__restrict__ part_pq,
                              int n, FcgScalars *S, double *__restrict__ history, int32_t hist_cap) {
+  pdl_wait();
   if (S->converged) return;
   __shared__ double sm[kWarps + 1];
   const double rr = sum_partials(part_rr, n, sm);
@@ -149,6 +155,7 @@ __global__ void k_fcg_finish(const double *__restrict__ part_rr, const double *_
 
 __global__ void k_fcg_start(const double *__restrict__ bb_part, const double *__restrict__ rr_part,
                             int n, double tol, int32_t set_bnorm, int32_t learned, FcgScalars *S) {
+  pdl_wait();
   __shared__ double sm[kWarps + 1];
   const double bb = sum_partials(bb_part, n, sm);
   const double rr = sum_partials(rr_part, n, sm);
@@ -170,6 +177,7 @@ __global__ void k_fcg_start(const double *__restrict__ bb_part, const double *__
 }
 
 __global__ void k_fcg_condition(cudaGraphConditionalHandle hc, const FcgScalars *__restrict__ S) {
+  pdl_wait();
   if (threadIdx.x == 0)
     cudaGraphSetConditional(hc, (!S->converged && S->iter < S->limit) ? 1u : 0u);
 }
@@ -178,25 +186,25 @@ __global__ void k_fcg_condition(cudaGraphConditionalHandle hc, const FcgScalars 
 
 rr_status fcg_dot(int64_t F, const double *a, const double *b, double *part, const int32_t *stop,
                   cudaStream_t st) {
-  RR_LAUNCH(k_fcg_dot, kVecGrid, kThreads, 0, st, F, a, b, part, stop);
+  RR_LAUNCH_PDL(k_fcg_dot, kVecGrid, kThreads, 0, st, F, a, b, part, stop);
   return RR_OK;
 }
 
 rr_status fcg_direction(int64_t F, const double *part_zq, const FcgScalars *S, const double *z,
                         const double *p_prev, double *p, const int32_t *stop, cudaStream_t st) {
-  RR_LAUNCH(k_fcg_direction, kVecGrid, kThreads, 0, st, F, part_zq, kVecGrid, S, z, p_prev, p, stop);
+  RR_LAUNCH_PDL(k_fcg_direction, kVecGrid, kThreads, 0, st, F, part_zq, kVecGrid, S, z, p_prev, p, stop);
   return RR_OK;
 }
 
 rr_status fcg_dots(int64_t F, const double *p, const double *r, const double *q, double *part3,
                    const int32_t *stop, cudaStream_t st) {
-  RR_LAUNCH(k_fcg_dots, kVecGrid, kThreads, 0, st, F, p, r, q, part3, kVecGrid, stop);
+  RR_LAUNCH_PDL(k_fcg_dots, kVecGrid, kThreads, 0, st, F, p, r, q, part3, kVecGrid, stop);
   return RR_OK;
 }
 
 rr_status fcg_decide(const double *part_rz, const double *part_pq, const double *part3,
                      FcgScalars *S, cudaStream_t st) {
-  RR_LAUNCH(k_fcg_decide, 1, kThreads, 0, st, part_rz, part_pq, part3, kVecGrid, S);
+  RR_LAUNCH_PDL(k_fcg_decide, 1, kThreads, 0, st, part_rz, part_pq, part3, kVecGrid, S);
   return RR_OK;
 }
 
@@ -204,26 +212,26 @@ rr_status fcg_update(int64_t F, const double *part_pq, const double *part3, cons
                      const double *q, double *w, double *r, double omega, const double *d,
                      double *z1, double *p_prev, double *q_prev, double *part_rr,
                      const FcgScalars *S, cudaStream_t st) {
-  RR_LAUNCH(k_fcg_update, kVecGrid, kThreads, 0, st, F, part_pq, part3, kVecGrid, p, q, w, r, omega,
+  RR_LAUNCH_PDL(k_fcg_update, kVecGrid, kThreads, 0, st, F, part_pq, part3, kVecGrid, p, q, w, r, omega,
             d, z1, p_prev, q_prev, part_rr, S);
   return RR_OK;
 }
 
 rr_status fcg_finish(const double *part_rr, const double *part_pq, FcgScalars *S, double *history,
                      int32_t hist_cap, cudaStream_t st) {
-  RR_LAUNCH(k_fcg_finish, 1, kThreads, 0, st, part_rr, part_pq, kVecGrid, S, history, hist_cap);
+  RR_LAUNCH_PDL(k_fcg_finish, 1, kThreads, 0, st, part_rr, part_pq, kVecGrid, S, history, hist_cap);
   return RR_OK;
 }
 
 rr_status fcg_start(const double *bb_part, int n_bb, const double *rr_part, double tol,
                     int32_t set_bnorm, int32_t learned, FcgScalars *S, cudaStream_t st) {
   (void)n_bb;
-  RR_LAUNCH(k_fcg_start, 1, kThreads, 0, st, bb_part, rr_part, kVecGrid, tol, set_bnorm, learned, S);
+  RR_LAUNCH_PDL(k_fcg_start, 1, kThreads, 0, st, bb_part, rr_part, kVecGrid, tol, set_bnorm, learned, S);
   return RR_OK;
 }
 
 rr_status fcg_condition(cudaGraphConditionalHandle hc, const FcgScalars *S, cudaStream_t st) {
-  RR_LAUNCH(k_fcg_condition, 1, 32, 0, st, hc, S);
+  RR_LAUNCH_PDL(k_fcg_condition, 1, 32, 0, st, hc, S);
   return RR_OK;
 }
 

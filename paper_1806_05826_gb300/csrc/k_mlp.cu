@@ -383,6 +383,7 @@ __global__ void k_mlp_input(int32_t k, int32_t kp, const int32_t *__restrict__ i
                             const double *__restrict__ item_sum, const double *__restrict__ s,
                             float *__restrict__ x, double *__restrict__ nrm,
                             const int32_t *__restrict__ stop) {
+  pdl_wait();
   if (stop && *stop) return;
   __shared__ double sm[kWarps + 1];
   extern __shared__ double rcs[];
@@ -409,6 +410,7 @@ __global__ void k_mlp_gemv(int32_t rows, int32_t cols, const __nv_bfloat16 *__re
                            int32_t relu, float *__restrict__ y, int32_t n_out,
                            const double *__restrict__ scale, double *__restrict__ y64,
                            const int32_t *__restrict__ stop) {
+  pdl_wait();
   if (stop && *stop) return;
   extern __shared__ float xs[];
   for (int i = threadIdx.x; i < cols; i += blockDim.x) xs[i] = x[i];
@@ -592,15 +594,15 @@ rr_status pack_rows(rr_mlp *m, int32_t B, const int64_t *idx, const float *X, co
 rr_status mlp_coarse(const rr_mlp *m, const RestrictPlan &plan, const double *s, double *ec,
                      const int32_t *stop, cudaStream_t st) {
   const int32_t k = m->k, kp = m->kp, H = m->H;
-  RR_LAUNCH(k_mlp_input, 1, kThreads, sizeof(double) * k, st, k, kp, plan.item_ptr, plan.item_sum, s,
+  RR_LAUNCH_PDL(k_mlp_input, 1, kThreads, sizeof(double) * k, st, k, kp, plan.item_ptr, plan.item_sum, s,
             m->xin, m->nrm, stop);
   const int g1 = (H + kWarps - 1) / kWarps;
-  RR_LAUNCH(k_mlp_gemv, g1, kThreads, sizeof(float) * kp, st, H, kp, m->W1b, m->P + m->ob1, m->xin,
+  RR_LAUNCH_PDL(k_mlp_gemv, g1, kThreads, sizeof(float) * kp, st, H, kp, m->W1b, m->P + m->ob1, m->xin,
             1, m->g1, 0, (const double *)nullptr, (double *)nullptr, stop);
-  RR_LAUNCH(k_mlp_gemv, g1, kThreads, sizeof(float) * H, st, H, H, m->W2b, m->P + m->ob2, m->g1, 1,
+  RR_LAUNCH_PDL(k_mlp_gemv, g1, kThreads, sizeof(float) * H, st, H, H, m->W2b, m->P + m->ob2, m->g1, 1,
             m->g2, 0, (const double *)nullptr, (double *)nullptr, stop);
   const int g3 = (kp + kWarps - 1) / kWarps;
-  RR_LAUNCH(k_mlp_gemv, g3, kThreads, sizeof(float) * H, st, kp, H, m->W3b, m->P + m->ob3, m->g2, 0,
+  RR_LAUNCH_PDL(k_mlp_gemv, g3, kThreads, sizeof(float) * H, st, kp, H, m->W3b, m->P + m->ob3, m->g2, 0,
             (float *)nullptr, k, m->nrm, ec, stop);
   return RR_OK;
 }

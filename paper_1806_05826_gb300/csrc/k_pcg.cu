@@ -21,6 +21,7 @@ namespace {
 __global__ void k_restrict_items(const RestrictItem *__restrict__ items, int32_t n_items,
                                  const int32_t *__restrict__ members, const double *__restrict__ r1,
                                  double *__restrict__ item_sum, const int32_t *__restrict__ stop) {
+  pdl_wait();
   if (stop && *stop) return;
   __shared__ double sm[kWarps + 1];
   for (int32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -39,6 +40,7 @@ __global__ void k_coarse_matvec(int32_t k, const double *__restrict__ Ainv,
                                 const double *__restrict__ item_sum, const double *__restrict__ s,
                                 double *__restrict__ rc_out, double *__restrict__ ec,
                                 const int32_t *__restrict__ stop) {
+  pdl_wait();
   if (stop && *stop) return;
   extern __shared__ double rcs[];
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
@@ -87,6 +89,7 @@ __global__ void k_prolong_add(int64_t F, const int32_t *__restrict__ labels,
                               const double *__restrict__ s, const double *__restrict__ ec,
                               const double *__restrict__ z1, double *__restrict__ z2,
                               const int32_t *__restrict__ stop) {
+  pdl_wait();
   if (stop && *stop) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -98,6 +101,7 @@ __global__ void k_prolong_add(int64_t F, const int32_t *__restrict__ labels,
 __global__ void k_jacobi(int64_t F, double omega, const double *__restrict__ r,
                          const double *__restrict__ d, double *__restrict__ z,
                          double *__restrict__ rz_part, const int32_t *__restrict__ stop) {
+  pdl_wait();
   if (stop && *stop) return;
   __shared__ double sm[kWarps + 1];
   double dot = 0.0;
@@ -116,6 +120,7 @@ __global__ void k_jacobi(int64_t F, double omega, const double *__restrict__ r,
 __global__ void k_pcg_direction(int64_t F, const double *__restrict__ rz_part, int n_rz,
                                 const double *__restrict__ z, double *__restrict__ p,
                                 const PcgScalars *__restrict__ S) {
+  pdl_wait();
   if (S->converged) return;
   __shared__ double sm[kWarps + 1];
   const double rho = sum_partials(rz_part, n_rz, sm);
@@ -131,6 +136,7 @@ __global__ void k_pcg_update(int64_t F, const double *__restrict__ rz_part, int 
                              double *__restrict__ w, double *__restrict__ r, double omega,
                              const double *__restrict__ d, double *__restrict__ z1,
                              double *__restrict__ rr_part, const PcgScalars *__restrict__ S) {
+  pdl_wait();
   if (S->converged) return;
   __shared__ double sm[kWarps + 1];
   const double rho = sum_partials(rz_part, n_rz, sm);
@@ -152,6 +158,7 @@ __global__ void k_pcg_update(int64_t F, const double *__restrict__ rz_part, int 
 __global__ void k_pcg_finish(const double *__restrict__ rz_part, int n_rz,
                              const double *__restrict__ rr_part, int n_rr, PcgScalars *S,
                              double *__restrict__ history, int32_t hist_cap) {
+  pdl_wait();
   if (S->converged) return;
   __shared__ double sm[kWarps + 1];
   const double rho = sum_partials(rz_part, n_rz, sm);
@@ -175,6 +182,7 @@ __global__ void k_pcg_finish(const double *__restrict__ rz_part, int n_rz,
 
 __global__ void k_dot_parts(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
                             double *__restrict__ part) {
+  pdl_wait();
   __shared__ double sm[kWarps + 1];
   double acc = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -187,6 +195,7 @@ __global__ void k_dot_parts(int64_t n, const double *__restrict__ a, const doubl
 __global__ void k_pcg_start(const double *__restrict__ bb_part, int n_bb,
                             const double *__restrict__ rr_part, int n_rr, double tol,
                             int32_t set_bnorm, PcgScalars *S) {
+  pdl_wait();
   __shared__ double sm[kWarps + 1];
   const double bb = sum_partials(bb_part, n_bb, sm);
   const double rr = sum_partials(rr_part, n_rr, sm);
@@ -205,18 +214,21 @@ __global__ void k_pcg_start(const double *__restrict__ bb_part, int n_bb,
 }
 
 __global__ void k_sum_parts(const double *__restrict__ part, int n, double *out) {
+  pdl_wait();
   __shared__ double sm[kWarps + 1];
   const double v = sum_partials(part, n, sm);
   if (threadIdx.x == 0) *out = v;
 }
 
 __global__ void k_loop_condition(cudaGraphConditionalHandle hc, const PcgScalars *__restrict__ S) {
+  pdl_wait();
   if (threadIdx.x == 0)
     cudaGraphSetConditional(hc, (!S->converged && S->iter < S->limit) ? 1u : 0u);
 }
 
 __global__ void k_axpby(int64_t n, double a, const double *__restrict__ x, double b,
                         double *__restrict__ y) {
+  pdl_wait();
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (x ? a * x[i] : 0.0) + (b != 0.0 ? b * y[i] : 0.0);
@@ -254,7 +266,7 @@ void restrict_free(RestrictPlan &plan) {
 
 rr_status restrict_clusters(const RestrictPlan &plan, const int32_t *members, const double *r1,
                             const int32_t *stop, cudaStream_t st) {
-  RR_LAUNCH(k_restrict_items, std::max(1, std::min(plan.n_items, kSMs * 4)), kThreads, 0, st,
+  RR_LAUNCH_PDL(k_restrict_items, std::max(1, std::min(plan.n_items, kSMs * 4)), kThreads, 0, st,
             plan.items, plan.n_items, members, r1, plan.item_sum, stop);
   return RR_OK;
 }
@@ -268,26 +280,26 @@ rr_status coarse_matvec(int32_t k, const double *Ainv, const RestrictPlan &plan,
                                  (int)smem));
     attr_for = k;
   }
-  RR_LAUNCH(k_coarse_matvec, grid_for(k, kWarps), kThreads, smem, st, k, Ainv, plan.item_ptr,
+  RR_LAUNCH_PDL(k_coarse_matvec, grid_for(k, kWarps), kThreads, smem, st, k, Ainv, plan.item_ptr,
             plan.item_sum, s, rc, ec, stop);
   return RR_OK;
 }
 
 rr_status prolong_add(int64_t F, const int32_t *labels, const double *s, const double *ec,
                       const double *z1, double *z2, const int32_t *stop, cudaStream_t st) {
-  RR_LAUNCH(k_prolong_add, kVecGrid, kThreads, 0, st, F, labels, s, ec, z1, z2, stop);
+  RR_LAUNCH_PDL(k_prolong_add, kVecGrid, kThreads, 0, st, F, labels, s, ec, z1, z2, stop);
   return RR_OK;
 }
 
 rr_status jacobi(int64_t F, double omega, const double *r, const double *d, double *z,
                  double *rz_part, const int32_t *stop, cudaStream_t st) {
-  RR_LAUNCH(k_jacobi, kVecGrid, kThreads, 0, st, F, omega, r, d, z, rz_part, stop);
+  RR_LAUNCH_PDL(k_jacobi, kVecGrid, kThreads, 0, st, F, omega, r, d, z, rz_part, stop);
   return RR_OK;
 }
 
 rr_status pcg_direction(int64_t F, const double *rz_part, int n_rz, const double *z, double *p,
                         PcgScalars *S, cudaStream_t st) {
-  RR_LAUNCH(k_pcg_direction, kVecGrid, kThreads, 0, st, F, rz_part, n_rz, z, p, S);
+  RR_LAUNCH_PDL(k_pcg_direction, kVecGrid, kThreads, 0, st, F, rz_part, n_rz, z, p, S);
   return RR_OK;
 }
 
@@ -295,30 +307,30 @@ rr_status pcg_update(int64_t F, const double *rz_part, int n_rz, const double *p
                      const double *p, const double *q, double *w, double *r, double omega,
                      const double *d, double *z1, double *rr_part, PcgScalars *S,
                      cudaStream_t st) {
-  RR_LAUNCH(k_pcg_update, kVecGrid, kThreads, 0, st, F, rz_part, n_rz, pq_part, n_pq, p, q, w, r,
+  RR_LAUNCH_PDL(k_pcg_update, kVecGrid, kThreads, 0, st, F, rz_part, n_rz, pq_part, n_pq, p, q, w, r,
             omega, d, z1, rr_part, S);
   return RR_OK;
 }
 
 rr_status pcg_finish(const double *rz_part, int n_rz, const double *rr_part, int n_rr,
                      PcgScalars *S, double *history, int32_t hist_cap, cudaStream_t st) {
-  RR_LAUNCH(k_pcg_finish, 1, kThreads, 0, st, rz_part, n_rz, rr_part, n_rr, S, history, hist_cap);
+  RR_LAUNCH_PDL(k_pcg_finish, 1, kThreads, 0, st, rz_part, n_rz, rr_part, n_rr, S, history, hist_cap);
   return RR_OK;
 }
 
 rr_status dot_parts(int64_t n, const double *a, const double *b, double *part, cudaStream_t st) {
-  RR_LAUNCH(k_dot_parts, kVecGrid, kThreads, 0, st, n, a, b, part);
+  RR_LAUNCH_PDL(k_dot_parts, kVecGrid, kThreads, 0, st, n, a, b, part);
   return RR_OK;
 }
 
 rr_status pcg_start(const double *bb_part, int n_bb, const double *rr_part, int n_rr, double tol,
                     int32_t set_bnorm, PcgScalars *S, cudaStream_t st) {
-  RR_LAUNCH(k_pcg_start, 1, kThreads, 0, st, bb_part, n_bb, rr_part, n_rr, tol, set_bnorm, S);
+  RR_LAUNCH_PDL(k_pcg_start, 1, kThreads, 0, st, bb_part, n_bb, rr_part, n_rr, tol, set_bnorm, S);
   return RR_OK;
 }
 
 rr_status sum_parts(const double *part, int n, double *out, cudaStream_t st) {
-  RR_LAUNCH(k_sum_parts, 1, kThreads, 0, st, part, n, out);
+  RR_LAUNCH_PDL(k_sum_parts, 1, kThreads, 0, st, part, n, out);
   return RR_OK;
 }
 
@@ -328,12 +340,12 @@ rr_status copy_f64(double *dst, const double *src, int64_t n, cudaStream_t st) {
 }
 
 rr_status loop_condition(cudaGraphConditionalHandle hc, const PcgScalars *S, cudaStream_t st) {
-  RR_LAUNCH(k_loop_condition, 1, 32, 0, st, hc, S);
+  RR_LAUNCH_PDL(k_loop_condition, 1, 32, 0, st, hc, S);
   return RR_OK;
 }
 
 rr_status axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t st) {
-  RR_LAUNCH(k_axpby, kVecGrid, kThreads, 0, st, n, a, x, b, y);
+  RR_LAUNCH_PDL(k_axpby, kVecGrid, kThreads, 0, st, n, a, x, b, y);
   return RR_OK;
 }
 

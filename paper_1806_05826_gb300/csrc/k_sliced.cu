@@ -191,6 +191,7 @@ __global__ void k_slice_prep(int64_t n, const double *__restrict__ x,
                              const double *__restrict__ in_psum,
                              const int32_t *__restrict__ in_slot_ptr, T *__restrict__ xq,
                              const int32_t *__restrict__ stop) {
+  pdl_wait();
   if (stop && *stop) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -228,6 +229,7 @@ template <typename T>
 __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather(
     SlicedView P, const T *__restrict__ xq, double *__restrict__ out_psum,
     const int32_t *__restrict__ stop) {
+  pdl_wait();
   if (stop && *stop) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *xs = reinterpret_cast<T *>(smem_raw);
@@ -317,6 +319,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather_staged(
     SlicedView P, const int32_t *__restrict__ chunk_p, const int32_t *__restrict__ chunk_w,
     const int32_t *__restrict__ task_c, const float *__restrict__ xq,
     double *__restrict__ out_psum, const int32_t *__restrict__ stop, int32_t *err) {
+  pdl_wait();
   if (stop && *stop) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int slice_floats = (P.W + 1 + 3) & ~3;
@@ -474,6 +477,7 @@ __global__ void k_chunk_fill(int32_t ntasks, const int32_t *__restrict__ task_p,
 // Sum of the slots of every outer index -> out[o] (u = X v on its own).
 __global__ void k_slot_sum(int64_t n, const int32_t *__restrict__ slot_ptr,
                            const double *__restrict__ psum, double *__restrict__ out) {
+  pdl_wait();
   for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n;
        o += (int64_t)gridDim.x * blockDim.x) {
     double v = 0.0;
@@ -527,6 +531,7 @@ __global__ void __launch_bounds__(kThreads) k_sliced_epilogue(int64_t F, const i
                                                               const double *__restrict__ psum,
                                                               const int32_t *__restrict__ heavy,
                                                               int32_t n_heavy, CscEpilogue ep) {
+  pdl_wait();
   if (ep.stop && *ep.stop) return;
   __shared__ double sm[kWarps + 1];
   const int lane = threadIdx.x & 31;
@@ -608,10 +613,10 @@ rr_status gather_t(const SlicedPattern &P, const double *x, const SlicedPattern 
   const int64_t n = P.n_inner;
   T *xq = reinterpret_cast<T *>(P.xq);
   if (in)
-    RR_LAUNCH((k_slice_prep<true, T>), grid_for(n, kThreads), kThreads, 0, st, n, nullptr,
+    RR_LAUNCH_PDL((k_slice_prep<true, T>), grid_for(n, kThreads), kThreads, 0, st, n, nullptr,
               in->psum, in->slot_ptr, xq, stop);
   else
-    RR_LAUNCH((k_slice_prep<false, T>), grid_for(n, kThreads), kThreads, 0, st, n, x, nullptr,
+    RR_LAUNCH_PDL((k_slice_prep<false, T>), grid_for(n, kThreads), kThreads, 0, st, n, x, nullptr,
               nullptr, xq, stop);
   if (std::is_same<T, float>::value && P.staged && P.chunk_p) {
     const size_t smem = staged_smem(P.W);
@@ -621,12 +626,12 @@ rr_status gather_t(const SlicedPattern &P, const double *x, const SlicedPattern 
                                    (int)staged_smem(kSliceMax)));
       attr = true;
     }
-    RR_LAUNCH(k_sliced_gather_staged, P.ntasks, kSliceThreads, smem, st, P.view(), P.chunk_p,
+    RR_LAUNCH_PDL(k_sliced_gather_staged, P.ntasks, kSliceThreads, smem, st, P.view(), P.chunk_p,
               P.chunk_w, P.task_c, reinterpret_cast<const float *>(xq), P.psum, stop, P.err);
     return RR_OK;
   }
   RR_TRY(set_smem_attr<T>());
-  RR_LAUNCH(k_sliced_gather<T>, P.ntasks, kSliceThreads, slice_smem<T>(P.W), st, P.view(), xq,
+  RR_LAUNCH_PDL(k_sliced_gather<T>, P.ntasks, kSliceThreads, slice_smem<T>(P.W), st, P.view(), xq,
             P.psum, stop);
   return RR_OK;
 }
@@ -819,13 +824,13 @@ rr_status sliced_choose_gather(SlicedPattern &P, int32_t mode, cudaStream_t st) 
 }
 
 rr_status sliced_slot_sum(const SlicedPattern &P, double *out, cudaStream_t st) {
-  RR_LAUNCH(k_slot_sum, grid_for(P.n_outer, kThreads), kThreads, 0, st, P.n_outer, P.slot_ptr,
+  RR_LAUNCH_PDL(k_slot_sum, grid_for(P.n_outer, kThreads), kThreads, 0, st, P.n_outer, P.slot_ptr,
             P.psum, out);
   return RR_OK;
 }
 
 rr_status sliced_epilogue(const SlicedPattern &P, const CscEpilogue &ep, cudaStream_t st) {
-  RR_LAUNCH(k_sliced_epilogue, kVecGrid, kThreads, 0, st, P.n_outer, P.slot_ptr, P.psum, P.heavy,
+  RR_LAUNCH_PDL(k_sliced_epilogue, kVecGrid, kThreads, 0, st, P.n_outer, P.slot_ptr, P.psum, P.heavy,
             P.n_heavy, ep);
   return RR_OK;
 }
