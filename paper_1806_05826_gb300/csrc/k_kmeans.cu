@@ -75,6 +75,7 @@ __device__ int64_t block_incl_scan_i64(int64_t v, int64_t *sm, int64_t *total) {
 
 __global__ void k_first_center(int64_t F, uint64_t seed, int32_t *centers, uint8_t *chosen,
                                int32_t *round) {
+  pdl_wait();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     int64_t c = (int64_t)floor(uniform53(seed, 0) * (double)F);
     if (c >= F) c = F - 1;
@@ -92,6 +93,7 @@ __device__ __forceinline__ bool heavy_centre(int64_t nc, int64_t N) { return 2 *
 __global__ void k_seed_mark(const int32_t *__restrict__ round, const int32_t *__restrict__ centers,
                             int64_t N, const int64_t *__restrict__ col_ptr,
                             const int32_t *__restrict__ row_idx, int32_t *__restrict__ rowmark) {
+  pdl_wait();
   const int32_t t = *round;
   const int64_t c = centers[t];
   if (!heavy_centre(col_ptr[c + 1] - col_ptr[c], N)) return;
@@ -108,6 +110,7 @@ __global__ void k_seed_overlap(const int32_t *__restrict__ round, const int32_t 
                                const int64_t *__restrict__ col_ptr,
                                const int32_t *__restrict__ row_idx,
                                const int32_t *__restrict__ rowmark, int32_t *__restrict__ ov) {
+  pdl_wait();
   const int32_t t = *round;
   const int64_t c = centers[t];
   const int lane = threadIdx.x & 31;
@@ -132,6 +135,7 @@ __global__ void k_seed_update(const int32_t *__restrict__ round, int64_t F, int6
                               const int32_t *__restrict__ centers,
                               const int64_t *__restrict__ col_ptr, int32_t *__restrict__ ov,
                               int64_t *__restrict__ d2, int64_t *__restrict__ tile_sum) {
+  pdl_wait();
   __shared__ int64_t sm[kWarps + 1];
   const int32_t t = *round;
   const int64_t c = centers[t];
@@ -158,6 +162,7 @@ __global__ void k_seed_update(const int32_t *__restrict__ round, int64_t F, int6
 __global__ void k_seed_pick(int32_t *round, int32_t k, int64_t F, int64_t ntiles, uint64_t seed,
                             const int64_t *__restrict__ d2, const int64_t *__restrict__ tile_sum,
                             int32_t *centers, uint8_t *chosen) {
+  pdl_wait();
   __shared__ int64_t sm[kWarps + 1];
   __shared__ int64_t found;
   const int32_t t = *round + 1;
@@ -232,6 +237,7 @@ __global__ void k_seed_pick(int32_t *round, int32_t k, int64_t F, int64_t ntiles
 }
 
 __global__ void k_seed_condition(cudaGraphConditionalHandle hc, const int32_t *round, int32_t k) {
+  pdl_wait();
   if (threadIdx.x == 0) cudaGraphSetConditional(hc, *round < k ? 1u : 0u);
 }
 
@@ -523,17 +529,17 @@ rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int3
   RR_CUDA(cudaMemsetAsync(chosen, 0, F, st));
   RR_CUDA(cudaMemsetAsync(b.ov, 0, sizeof(int32_t) * F, st));
   RR_CUDA(cudaMemsetAsync(b.dcount, 0, sizeof(int32_t) * N, st));   // row stamps of heavy centres
-  RR_LAUNCH(k_first_center, 1, 32, 0, st, F, seed, b.centers, chosen, b.round);
+  RR_LAUNCH_PDL(k_first_center, 1, 32, 0, st, F, seed, b.centers, chosen, b.round);
   if (!use_graph) {
     // the same k rounds as the graph's while loop, issued from the host
     for (int32_t t = 0; t < k; ++t) {
-      RR_LAUNCH(k_seed_mark, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, col_ptr, row_idx,
+      RR_LAUNCH_PDL(k_seed_mark, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, col_ptr, row_idx,
                 b.dcount);
-      RR_LAUNCH(k_seed_overlap, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, row_ptr,
+      RR_LAUNCH_PDL(k_seed_overlap, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, row_ptr,
                 col_idx, col_ptr, row_idx, b.dcount, b.ov);
-      RR_LAUNCH(k_seed_update, (unsigned)ntiles, kThreads, 0, st, b.round, F, N, b.centers,
+      RR_LAUNCH_PDL(k_seed_update, (unsigned)ntiles, kThreads, 0, st, b.round, F, N, b.centers,
                 col_ptr, b.ov, b.d2, b.part_i);
-      RR_LAUNCH(k_seed_pick, 1, kThreads, 0, st, b.round, k, F, ntiles, seed, b.d2, b.part_i,
+      RR_LAUNCH_PDL(k_seed_pick, 1, kThreads, 0, st, b.round, k, F, ntiles, seed, b.d2, b.part_i,
                 b.centers, chosen);
     }
     RR_CUDA(cudaStreamSynchronize(st));
@@ -559,15 +565,15 @@ rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int3
     RR_CUDA(cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                           cudaStreamCaptureModeThreadLocal));
     auto body = [&]() -> rr_status {
-      RR_LAUNCH(k_seed_mark, kSMs * 2, kThreads, 0, cs, b.round, b.centers, N, col_ptr, row_idx,
+      RR_LAUNCH_PDL(k_seed_mark, kSMs * 2, kThreads, 0, cs, b.round, b.centers, N, col_ptr, row_idx,
                 b.dcount);
-      RR_LAUNCH(k_seed_overlap, kSMs * 2, kThreads, 0, cs, b.round, b.centers, N, row_ptr,
+      RR_LAUNCH_PDL(k_seed_overlap, kSMs * 2, kThreads, 0, cs, b.round, b.centers, N, row_ptr,
                 col_idx, col_ptr, row_idx, b.dcount, b.ov);
-      RR_LAUNCH(k_seed_update, (unsigned)ntiles, kThreads, 0, cs, b.round, F, N, b.centers,
+      RR_LAUNCH_PDL(k_seed_update, (unsigned)ntiles, kThreads, 0, cs, b.round, F, N, b.centers,
                 col_ptr, b.ov, b.d2, b.part_i);
-      RR_LAUNCH(k_seed_pick, 1, kThreads, 0, cs, b.round, k, F, ntiles, seed, b.d2, b.part_i,
+      RR_LAUNCH_PDL(k_seed_pick, 1, kThreads, 0, cs, b.round, k, F, ntiles, seed, b.d2, b.part_i,
                 b.centers, chosen);
-      RR_LAUNCH(k_seed_condition, 1, 32, 0, cs, hc, b.round, k);
+      RR_LAUNCH_PDL(k_seed_condition, 1, 32, 0, cs, hc, b.round, k);
       return RR_OK;
     };
     const int64_t l0 = rr_launch_counter;

@@ -56,8 +56,17 @@ __global__ void k_coarse_matvec(int32_t k, const double *__restrict__ Ainv,
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t S = warp; S < k; S += nwarps) {
     const double *row = Ainv + S * k;
-    double acc = 0.0;
-    for (int t = lane; t < k; t += 32) acc += row[t] * rcs[t];
+    // four row loads in flight per lane; the four partial sums are added in a fixed order
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int t = lane;
+    for (; t + 96 < k; t += 128) {
+      a0 += row[t] * rcs[t];
+      a1 += row[t + 32] * rcs[t + 32];
+      a2 += row[t + 64] * rcs[t + 64];
+      a3 += row[t + 96] * rcs[t + 96];
+    }
+    for (; t < k; t += 32) a0 += row[t] * rcs[t];
+    double acc = (a0 + a1) + (a2 + a3);
     acc = warp_sum(acc);
     if (lane == 0) ec[S] = acc;
   }

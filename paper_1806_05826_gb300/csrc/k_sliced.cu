@@ -552,27 +552,35 @@ __global__ void __launch_bounds__(kThreads) k_sliced_epilogue(int64_t F, const i
     double s = warp_sum(s0 + s1);
     if (lane == 0) epilogue(ep, i, s, dot);
   }
-  for (int64_t i0 = warp * 4; i0 < F; i0 += nwarps * 4) {   // warp-uniform loop
-    const int64_t i = i0 + gw;
-    double s = 0.0;
-    bool light = false;
-    if (i < F) {
-      const int32_t q0 = slot_ptr[i], q1 = slot_ptr[i + 1];
-      light = q1 - q0 <= kLightSlots;
-      if (light) {
-        double v[4];
+  // two features per 8-lane group at a time (feature i0 + gw and i0 + 4 + gw):
+  // their slot loads are in flight together
+  for (int64_t i0 = warp * 8; i0 < F; i0 += nwarps * 8) {   // warp-uniform loop
+    int64_t ii[2];
+    int32_t q0[2], q1[2];
+    bool light[2];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int32_t q = q0 + lane8 + 8 * u;
-          v[u] = q < q1 ? psum[q] : 0.0;
-        }
-        s = (v[0] + v[1]) + (v[2] + v[3]);
-      }
+    for (int h = 0; h < 2; ++h) {
+      ii[h] = i0 + 4 * h + gw;
+      q0[h] = ii[h] < F ? slot_ptr[ii[h]] : 0;
+      q1[h] = ii[h] < F ? slot_ptr[ii[h] + 1] : 0;
+      light[h] = ii[h] < F && q1[h] - q0[h] <= kLightSlots;
     }
-    s += __shfl_xor_sync(0xffffffffu, s, 4);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    if (light && lane8 == 0) epilogue(ep, i, s, dot);
+    double v[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int32_t q = q0[h] + lane8 + 8 * u;
+        v[h][u] = light[h] && q < q1[h] ? psum[q] : 0.0;
+      }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      double s = (v[h][0] + v[h][1]) + (v[h][2] + v[h][3]);
+      s += __shfl_xor_sync(0xffffffffu, s, 4);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      if (light[h] && lane8 == 0) epilogue(ep, ii[h], s, dot);
+    }
   }
   const double tot = block_sum(dot, sm);
   if (threadIdx.x == 0 && ep.dot_part) ep.dot_part[blockIdx.x] = tot;
