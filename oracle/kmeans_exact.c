@@ -15,8 +15,12 @@
  *   D_iS = x_i . c_S.  Scores are compared by exact 128-bit cross
  *   multiplication; ties go to the smallest cluster index; empty clusters are
  *   skipped.
- * Dense X: the same steps in FP64 with every sum taken in ascending row order,
- *   no fused multiply-add (compiled with -ffp-contract=off).
+ * Dense X: the same steps in FP64, no fused multiply-add (compiled with
+ *   -ffp-contract=off). The paper fixes no summation order; every sum over
+ *   the N rows is taken in blocks of ORACLE_ROW_BLOCK consecutive rows: each
+ *   block summed in ascending row order, then the block sums in ascending
+ *   block order. Centroids sum their member columns in ascending feature
+ *   order.
  *
  * Random draws: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) seeded with
  * `seed`; draw t is output t (counting from 0), u_t = (x_t >> 11) * 2^-53.
@@ -178,14 +182,21 @@ int oracle_lloyd_binary(int64_t N, int64_t F, const int64_t *row_ptr,
 
 /* ---------------- dense X (N x F, row-major float32 values) -------------- */
 
-/* Squared Euclidean distance between features i and j, rows in ascending order. */
+#define ORACLE_ROW_BLOCK 64
+
+/* Squared Euclidean distance between features i and j (blocked row order). */
 static double dense_d2(int64_t N, int64_t F, const float *X, int64_t i, int64_t j) {
-  double s = 0.0;
-  for (int64_t r = 0; r < N; ++r) {
-    double t = (double)X[r * F + i] - (double)X[r * F + j];
-    s = s + t * t;
+  double total = 0.0;
+  for (int64_t b0 = 0; b0 < N; b0 += ORACLE_ROW_BLOCK) {
+    const int64_t b1 = b0 + ORACLE_ROW_BLOCK < N ? b0 + ORACLE_ROW_BLOCK : N;
+    double s = 0.0;
+    for (int64_t r = b0; r < b1; ++r) {
+      double t = (double)X[r * F + i] - (double)X[r * F + j];
+      s = s + t * t;
+    }
+    total = total + s;
   }
-  return s;
+  return total;
 }
 
 int oracle_kmeanspp_dense(int64_t N, int64_t F, const float *X, int32_t k,
@@ -226,7 +237,7 @@ int oracle_kmeanspp_dense(int64_t N, int64_t F, const float *X, int32_t k,
 
 /* Dense Lloyd: centroid mu_S = (sum over members, ascending feature index) / n_S,
  * score(i, S) = ||mu_S||^2 - 2 x_i . mu_S (the common ||x_i||^2 dropped),
- * each dot product summed over rows in ascending order. */
+ * each sum over rows in the blocked order above. */
 int oracle_lloyd_dense(int64_t N, int64_t F, const float *X, int32_t k,
                        const int32_t *centers, int32_t max_iter, int32_t *labels,
                        int32_t *iters) {
@@ -254,9 +265,14 @@ int oracle_lloyd_dense(int64_t N, int64_t F, const float *X, int32_t k,
     for (int32_t s = 0; s < k; ++s) {
       double q = 0.0;
       if (n[s] > 0)
-        for (int64_t r = 0; r < N; ++r) {
-          mu[s * N + r] = mu[s * N + r] / (double)n[s];
-          q = q + mu[s * N + r] * mu[s * N + r];
+        for (int64_t b0 = 0; b0 < N; b0 += ORACLE_ROW_BLOCK) {
+          const int64_t b1 = b0 + ORACLE_ROW_BLOCK < N ? b0 + ORACLE_ROW_BLOCK : N;
+          double part = 0.0;
+          for (int64_t r = b0; r < b1; ++r) {
+            mu[s * N + r] = mu[s * N + r] / (double)n[s];
+            part = part + mu[s * N + r] * mu[s * N + r];
+          }
+          q = q + part;
         }
       mm[s] = q;
     }
@@ -266,7 +282,12 @@ int oracle_lloyd_dense(int64_t N, int64_t F, const float *X, int32_t k,
       for (int32_t s = 0; s < k; ++s) {
         if (n[s] == 0) continue;
         double dot = 0.0;
-        for (int64_t r = 0; r < N; ++r) dot = dot + (double)X[r * F + i] * mu[s * N + r];
+        for (int64_t b0 = 0; b0 < N; b0 += ORACLE_ROW_BLOCK) {
+          const int64_t b1 = b0 + ORACLE_ROW_BLOCK < N ? b0 + ORACLE_ROW_BLOCK : N;
+          double part = 0.0;
+          for (int64_t r = b0; r < b1; ++r) part = part + (double)X[r * F + i] * mu[s * N + r];
+          dot = dot + part;
+        }
         double v = mm[s] - 2.0 * dot;
         if (best < 0 || v < best_v) { best = s; best_v = v; }
       }
