@@ -76,7 +76,12 @@ enum { RR_PREC_FP64 = 0,        /* every operator apply accumulates in FP64 */
  *  CSR_BINARY: row_ptr int64[N+1] (row_ptr[0] = 0, non-decreasing,
  *    row_ptr[N] = nnz) and col_idx int32[nnz], strictly increasing within each
  *    row, each in [0, F). values must be NULL.
- *  DENSE_F32_ROWMAJOR: values float[N*F], row-major; row_ptr/col_idx NULL.
+ *  DENSE_F32_ROWMAJOR: values float[N*F], row-major; row_ptr/col_idx NULL;
+ *    N*F < 2^34, N <= 4,194,240 and F <= 25600 (the operator stages a whole
+ *    vector of F FP64 values in shared memory), else RR_UNSUPPORTED. The clustering runs in
+ *    FP64 on the FP32 values (row sums in blocks of 64 rows, ascending).
+ *  An unknown layout, or pointers that do not match the layout, give
+ *  RR_INVALID_ARG.
  *  on_device = 1: the pointers are device pointers; 0: host pointers (copied
  *  inside rr_setup). rr_setup copies X into the handle; the caller may free
  *  its copy when rr_setup returns. */
@@ -188,8 +193,9 @@ rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info
  * The handle's own lambda and rr_solve state are untouched. Device work
  * space of about 13 F + 3 N doubles per system is kept in the handle and
  * reused by later calls with as many or fewer systems and weights.
- * Requires RR_SOLVER_TWOLEVEL. Synchronises the stream before returning.
- * Errors: RR_INVALID_ARG, RR_UNSUPPORTED (other solver), RR_OOM, RR_NOT_SPD,
+ * Requires RR_SOLVER_TWOLEVEL and binary X. Synchronises the stream before
+ * returning.
+ * Errors: RR_INVALID_ARG, RR_UNSUPPORTED (other solver, dense X), RR_OOM, RR_NOT_SPD,
  * RR_NOT_CONVERGED (some system hit a cap; W holds the last iterates and
  * infos say which), RR_NONFINITE, RR_CUDA_ERROR. */
 rr_status rr_solve_batch(rr_handle *h, int32_t nrhs, const double *Y, int32_t nlam,
@@ -243,7 +249,8 @@ rr_status rr_solve_fcg(rr_handle *h, const rr_mlp *net, const double *y, double 
  *   n_pairs (host) receives the number of pairs written: every (j, i) with
  *   i below max_iter and system j still iterating (its recurrence residual
  *   above tol ||X^T y_j||), in order of i then j, cut at max_pairs.
- * Runs at most max_iter iterations (no refinement restarts). Synchronises. */
+ * Runs at most max_iter iterations (no refinement restarts). Binary X only
+ * (RR_UNSUPPORTED on a dense handle). Synchronises. */
 rr_status rr_harvest(rr_handle *h, int32_t nrhs, const double *Y, double lambda, const double *Wref,
                      double tol, int32_t max_iter, float *Xp, float *Tp, int64_t max_pairs,
                      int64_t *n_pairs);
@@ -304,7 +311,8 @@ rr_status rr_get_centers(const rr_handle *h, int32_t *centers_host);
 
 /* Copies the coarse operator A_c (k_eff x k_eff, row-major, FP64, lower
  * triangle mirrored) and the exact coarse Gram G = C^T C (k_eff x k_eff,
- * int64) to host buffers; either may be NULL. Synchronises. */
+ * int64) to host buffers; either may be NULL. G exists for binary X only:
+ * a non-NULL G_host on a dense handle gives RR_UNSUPPORTED. Synchronises. */
 rr_status rr_get_coarse(const rr_handle *h, double *Ac_host, int64_t *G_host);
 
 /* Number of non-empty clusters, Jacobi damping and sizes of the handle. Any

@@ -94,6 +94,10 @@ struct rr_handle {
   int32_t *err_host = nullptr;
   int n_parts = 0;
   rr::BatchState *batch = nullptr;   // rr_solve_batch workspace (created on first use)
+  // dense X (RR_DENSE_F32_ROWMAJOR)
+  bool dense = false;
+  float *Xd = nullptr;                // [N x F] row-major
+  double *dsq = nullptr, *dgs = nullptr, *dpart = nullptr;
   // rr_solve_fcg workspace (created on first use)
   double *p_prev = nullptr, *q_prev = nullptr, *part_zq = nullptr, *part3 = nullptr;
   rr::FcgScalars *Sf = nullptr, *Sf_host = nullptr;

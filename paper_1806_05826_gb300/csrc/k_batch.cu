@@ -1019,6 +1019,10 @@ extern "C" rr_status rr_solve_batch(rr_handle *h, int32_t nrhs, const double *Y,
     rr_set_error("rr_solve_batch: more than 2^20 systems");
     return RR_INVALID_ARG;
   }
+  if (h->dense) {
+    rr_set_error("rr_solve_batch: the batched engine takes binary X only");
+    return RR_UNSUPPORTED;
+  }
   for (int32_t l = 0; l < nlam; ++l)
     if (!(lambdas[l] > 0.0) || !isfinite(lambdas[l])) {
       rr_set_error("rr_solve_batch: every lambda must be positive and finite");
@@ -1167,6 +1171,10 @@ extern "C" rr_status rr_harvest(rr_handle *h, int32_t nrhs, const double *Y, dou
   if (nrhs > (1 << 16) || (int64_t)max_iter * nrhs > ((int64_t)1 << 31)) {
     rr_set_error("rr_harvest: nrhs * max_iter too large");
     return RR_INVALID_ARG;
+  }
+  if (h->dense) {
+    rr_set_error("rr_harvest: binary X only");
+    return RR_UNSUPPORTED;
   }
   if (h->opt.solver != RR_SOLVER_TWOLEVEL) {
     rr_set_error("rr_harvest: the handle's solver must be RR_SOLVER_TWOLEVEL");

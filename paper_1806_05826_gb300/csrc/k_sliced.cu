@@ -29,6 +29,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "epilogue.cuh"
 #include "tc_common.cuh"
 
 namespace rr {
@@ -483,39 +484,6 @@ __global__ void k_slot_sum(int64_t n, const int32_t *__restrict__ slot_ptr,
     double v = 0.0;
     for (int32_t q = slot_ptr[o]; q < slot_ptr[o + 1]; ++q) v += psum[q];
     out[o] = v;
-  }
-}
-
-__device__ __forceinline__ void epilogue(const CscEpilogue &ep, int64_t i, double sum, double &dot) {
-  switch (ep.mode) {
-    case CSC_RHS:
-      ep.out[i] = sum;
-      break;
-    case CSC_APPLY:
-      ep.out[i] = sum + ep.lambda * ep.v[i];
-      break;
-    case CSC_PRE:
-      ep.out[i] = ep.r[i] - (sum + ep.lambda * ep.v[i]);
-      break;
-    case CSC_POST: {
-      const double r2 = ep.r[i] - (sum + ep.lambda * ep.v[i]);
-      const double z = ep.v[i] + ep.omega * r2 / ep.d[i];
-      ep.out[i] = z;
-      dot += ep.r[i] * z;
-      break;
-    }
-    case CSC_PCG: {
-      const double t = sum + ep.lambda * ep.v[i];
-      ep.out[i] = t;
-      dot += ep.v[i] * t;
-      break;
-    }
-    default: {  // CSC_RESID
-      const double t = ep.r[i] - (sum + ep.lambda * ep.v[i]);
-      ep.out[i] = t;
-      dot += t * t;
-      break;
-    }
   }
 }
 

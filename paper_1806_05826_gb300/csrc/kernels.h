@@ -289,4 +289,45 @@ rr_status mlp_coarse(const rr_mlp *m, const RestrictPlan &plan, const double *s,
                      const int32_t *stop, cudaStream_t st);
 int32_t mlp_k(const rr_mlp *m);
 
+// ---- k_dense.cu ---------------------------------------------------------
+// Dense X (N x F FP32 row-major): k-means in FP64 with blocked row sums (see
+// k_dense.cu), the coarse Gram from X onehot, the smoother's statistics and
+// the operator's two passes.
+struct DenseKmeansScratch {
+  int32_t *key;          // [F]
+  int64_t *iota;         // [F+1]
+  int64_t *cl_ptr;       // [k+2]
+  int32_t *members;      // [F]
+  int64_t *counts, *cursor;   // [k+1] each
+  int32_t *tmp;          // [F]
+  int64_t *scan_scratch; // scan_scratch_len(k+1)
+  double *mu;            // [k*N]
+  double *part;          // [k*nb]
+  double *mm;            // [k]
+  double *dot;           // [k*F]
+  unsigned long long *changes;
+};
+rr_status dense_kmeanspp(int64_t N, int64_t F, const float *X, int32_t k, uint64_t seed,
+                         int32_t *centers, double *d2, uint8_t *chosen, double *part, int32_t *err,
+                         cudaStream_t st);
+rr_status dense_lloyd(int64_t N, int64_t F, const float *X, int32_t k, const int32_t *centers,
+                      int32_t max_iter, int32_t *labels, DenseKmeansScratch &w, int32_t *iters,
+                      cudaStream_t st);
+// C (k_eff x N) = cluster sums of the columns (members ascending); G = C C^T.
+rr_status dense_coarse_gram(int64_t N, int64_t F, const float *X, int32_t k_eff,
+                            const int64_t *cl_ptr, const int32_t *members, double *C, double *G,
+                            cudaStream_t st);
+// sq_i = ||x_i||^2; gs_i = sum_r |x_ri| sum_j |x_rj| (>= sum_j |(X^T X)_ij|).
+rr_status dense_colstats(int64_t N, int64_t F, const float *X, double *rowabs, double *sq,
+                         double *gs, cudaStream_t st);
+rr_status dense_jacobi(int64_t F, double lambda, const double *sq, const double *gs, double *d,
+                       unsigned long long *max_bits, cudaStream_t st);
+int64_t dense_col_blocks(int64_t N);
+// u = X v (FP32 accumulation when fp32).
+rr_status dense_matvec(int64_t N, int64_t F, const float *X, const double *v, double *u,
+                       const int32_t *stop, bool fp32, cudaStream_t st);
+// t = X^T u in row-block partials, then the epilogue ep (part: [dense_col_blocks(N) * F]).
+rr_status dense_transposed(int64_t N, int64_t F, const float *X, const double *u, double *part,
+                           const CscEpilogue &ep, bool fp32, cudaStream_t st);
+
 }  // namespace rr

@@ -51,6 +51,15 @@ __global__ void k_jacobi_setup(int64_t F, double lambda, const int64_t *__restri
   if ((threadIdx.x & 31) == 0) atomicMax(max_bits, best);
 }
 
+// n_S[S] = number of features labelled S (counts: the order of the atomics does not matter).
+__global__ void k_dense_sizes(int64_t F, const int32_t *__restrict__ labels, int64_t *n_S, int32_t k) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t l = labels[i];
+    if (l >= 0 && l < k) atomicAdd((unsigned long long *)&n_S[l], 1ull);
+  }
+}
+
 __global__ void k_omega(const unsigned long long *max_bits, double *omega_out) {
   if (threadIdx.x == 0) *omega_out = 1.0 / __longlong_as_double((long long)*max_bits);
 }
@@ -96,8 +105,12 @@ rr_status build_lambda(rr_handle *h, double lambda) {
   RR_TRY(rr::cholesky(k, h->Lw, h->err, st));
   RR_TRY(rr::chol_inverse(k, h->Lw, h->Linv, h->Ainv, st));
   RR_CUDA(cudaMemsetAsync(h->max_bits, 0, sizeof(unsigned long long), st));
-  RR_LAUNCH(k_jacobi_setup, rr::grid_for(h->F, kThreads), kThreads, 0, st, h->F, lambda,
-            h->col_ptr, h->gsum, h->d, h->max_bits);
+  if (h->dense) {
+    RR_TRY(rr::dense_jacobi(h->F, lambda, h->dsq, h->dgs, h->d, h->max_bits, st));
+  } else {
+    RR_LAUNCH(k_jacobi_setup, rr::grid_for(h->F, kThreads), kThreads, 0, st, h->F, lambda,
+              h->col_ptr, h->gsum, h->d, h->max_bits);
+  }
   RR_LAUNCH(k_omega, 1, 32, 0, st, h->max_bits, h->omega_dev);
   double om = 0.0;
   RR_CUDA(cudaMemcpyAsync(&om, h->omega_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -126,6 +139,164 @@ rr_status validate_host_csr(const rr_matrix *X) {
       }
     }
   }
+  return RR_OK;
+}
+
+// Solve vectors, partial-dot buffers, scalars and the capture stream.
+rr_status alloc_solve_workspace(rr_handle *h) {
+  DevArena &m = h->mem;
+  const int64_t N = h->N, F = h->F;
+  const int32_t k_eff = h->k_eff;
+  h->n_parts = rr::kVecGrid;
+  for (double **v : {&h->b, &h->r, &h->z1, &h->z2, &h->z, &h->p, &h->q, &h->r1, &h->rt, &h->w_int})
+    RR_TRY(m.alloc(v, F));
+  RR_TRY(m.alloc(&h->u, std::max<int64_t>(N, 1)));
+  RR_TRY(m.alloc(&h->rc, k_eff));
+  RR_TRY(m.alloc(&h->ec, k_eff));
+  for (double **v : {&h->part_rz, &h->part_pq, &h->part_rr, &h->part_bb})
+    RR_TRY(m.alloc(v, h->n_parts));
+  RR_TRY(m.alloc(&h->scal, 4));
+  RR_TRY(m.alloc(&h->S, 1));
+  RR_CUDA(cudaMallocHost(&h->S_host, sizeof(rr::PcgScalars)));
+  RR_CUDA(cudaMallocHost(&h->scal_host, 4 * sizeof(double)));
+  RR_CUDA(cudaMallocHost(&h->limit_host, sizeof(int32_t)));
+  RR_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  h->hist_cap = h->opt.max_iter;
+  RR_TRY(m.alloc(&h->history, h->hist_cap));
+  return RR_OK;
+}
+
+// Setup for dense X: k-means++ and Lloyd in FP64 (k_dense.cu), member lists,
+// the coarse Gram of X onehot, the smoother's statistics, the factor.
+rr_status setup_impl_dense(rr_handle *h, const rr_matrix *X, double lambda, int32_t k) {
+  cudaStream_t st = h->st;
+  DevArena &m = h->mem;
+  auto t_last = std::chrono::steady_clock::now();
+  auto phase = [&](int i) -> rr_status {
+    RR_CUDA(cudaStreamSynchronize(st));
+    const auto now = std::chrono::steady_clock::now();
+    h->phase_ms[i] += std::chrono::duration<double, std::milli>(now - t_last).count();
+    t_last = now;
+    return RR_OK;
+  };
+  const int64_t N = X->n_rows, F = X->n_cols;
+  if (N * F >= (1LL << 34) || F > 25600 || N > 65535LL * 64) {
+    rr_set_error("rr_setup: dense X needs N*F < 2^34, F <= 25600 and N <= 4194240");
+    return RR_UNSUPPORTED;
+  }
+  h->dense = true;
+  h->N = N;
+  h->F = F;
+  h->nnz = N * F;
+  h->k_req = k;
+  RR_TRY(m.alloc(&h->err, 1));
+  RR_CUDA(cudaMallocHost(&h->err_host, sizeof(int32_t)));
+  RR_CUDA(cudaMemsetAsync(h->err, 0, sizeof(int32_t), st));
+  RR_TRY(m.alloc(&h->Xd, N * F));
+  RR_CUDA(cudaMemcpyAsync(h->Xd, X->values, sizeof(float) * (size_t)(N * F),
+                          X->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  RR_TRY(phase(0));
+  RR_TRY(phase(1));
+  // ---- k-means++ and Lloyd (FP64, blocked row sums)
+  const int64_t nb = (N + 63) / 64;
+  RR_TRY(m.alloc(&h->centers, k));
+  RR_TRY(m.alloc(&h->labels, F));
+  RR_TRY(m.alloc(&h->n_S, 2 * (int64_t)k));
+  if (h->opt.init_centers) {
+    std::vector<char> seen(F, 0);
+    for (int32_t s = 0; s < k; ++s) {
+      const int32_t c = h->opt.init_centers[s];
+      if (c < 0 || c >= F || seen[c]) {
+        rr_set_error("init_centers[%d] = %d is out of range or repeated", s, c);
+        return RR_INVALID_ARG;
+      }
+      seen[c] = 1;
+    }
+    RR_CUDA(cudaMemcpyAsync(h->centers, h->opt.init_centers, sizeof(int32_t) * k,
+                            cudaMemcpyHostToDevice, st));
+  } else {
+    double *d2 = nullptr, *part = nullptr;
+    uint8_t *chosen = nullptr;
+    RR_TRY(m.alloc(&d2, F));
+    RR_TRY(m.alloc(&chosen, F));
+    RR_TRY(m.alloc(&part, nb * F));
+    RR_TRY(rr::dense_kmeanspp(N, F, h->Xd, k, h->opt.seed, h->centers, d2, chosen, part, h->err, st));
+    RR_TRY(check_dev_error(h, "k-means++"));
+    m.release(d2);
+    m.release(chosen);
+    m.release(part);
+  }
+  RR_TRY(phase(2));
+  rr::DenseKmeansScratch w{};
+  RR_TRY(m.alloc(&w.key, F));
+  RR_TRY(m.alloc(&w.iota, F + 1));
+  RR_TRY(m.alloc(&w.cl_ptr, k + 2));
+  RR_TRY(m.alloc(&w.members, F));
+  RR_TRY(m.alloc(&w.counts, k + 2));
+  RR_TRY(m.alloc(&w.cursor, k + 2));
+  RR_TRY(m.alloc(&w.tmp, F));
+  RR_TRY(m.alloc(&w.scan_scratch, rr::scan_scratch_len(k + 2) + 8));
+  RR_TRY(m.alloc(&w.mu, (int64_t)k * N));
+  RR_TRY(m.alloc(&w.part, (int64_t)k * nb));
+  RR_TRY(m.alloc(&w.mm, k));
+  RR_TRY(m.alloc(&w.dot, (int64_t)k * F));
+  RR_TRY(m.alloc(&w.changes, 1));
+  RR_TRY(rr::iota_i64(w.iota, F + 1, st));
+  int32_t iters = 0;
+  RR_TRY(rr::dense_lloyd(N, F, h->Xd, k, h->centers, h->opt.kmeans_max_iter, h->labels, w, &iters, st));
+  h->kmeans_iters = iters;
+  // cluster sizes of the final labels
+  RR_CUDA(cudaMemsetAsync(h->n_S, 0, sizeof(int64_t) * 2 * (size_t)k, st));
+  RR_LAUNCH(k_dense_sizes, rr::grid_for(F, kThreads), kThreads, 0, st, F, h->labels, h->n_S, k);
+  m.release(w.mu);
+  m.release(w.part);
+  m.release(w.dot);
+  RR_TRY(phase(3));
+  // ---- compaction, member lists, prolongation scale
+  int32_t *remap = nullptr;
+  RR_TRY(m.alloc(&remap, k + 1));
+  int32_t k_eff = 0;
+  RR_TRY(rr::compact_clusters(F, k, h->labels, h->n_S, remap, &k_eff, st));
+  h->k_eff = k_eff;
+  RR_TRY(m.alloc(&h->cl_ptr, k_eff + 1));
+  RR_TRY(m.alloc(&h->members, F));
+  const int64_t big = std::max<int64_t>(F, k_eff) + 1;
+  int64_t *scratch64 = nullptr;
+  RR_TRY(m.alloc(&scratch64, 2 * big + rr::scan_scratch_len(big) + 256));
+  RR_TRY(rr::transpose_pattern(F, k_eff, F, w.iota, h->labels, h->cl_ptr, h->members, scratch64,
+                               scratch64 + big, w.tmp, scratch64 + 2 * big, st));
+  RR_TRY(m.alloc(&h->s, k_eff));
+  RR_TRY(rr::prolong_scale(k_eff, h->n_S, h->s, st));
+  RR_TRY(rr::restrict_plan(k_eff, h->cl_ptr, h->rplan, scratch64, st));
+  RR_TRY(phase(4));
+  // ---- coarse Gram G = (X onehot)^T (X onehot) (FP64), smoother statistics
+  double *C = nullptr, *rowabs = nullptr;
+  RR_TRY(m.alloc(&C, (int64_t)k_eff * N));
+  RR_TRY(m.alloc(&h->G, (int64_t)k_eff * k_eff));
+  RR_TRY(rr::dense_coarse_gram(N, F, h->Xd, k_eff, h->cl_ptr, h->members, C, h->G, st));
+  RR_TRY(m.alloc(&rowabs, N));
+  RR_TRY(m.alloc(&h->dsq, F));
+  RR_TRY(m.alloc(&h->dgs, F));
+  RR_TRY(rr::dense_colstats(N, F, h->Xd, rowabs, h->dsq, h->dgs, st));
+  RR_TRY(phase(5));
+  const int64_t kk = (int64_t)k_eff * k_eff;
+  RR_TRY(m.alloc(&h->Ac, kk));
+  RR_TRY(m.alloc(&h->Lw, kk));
+  RR_TRY(m.alloc(&h->Linv, kk));
+  RR_TRY(m.alloc(&h->Ainv, kk));
+  RR_TRY(m.alloc(&h->d, F));
+  RR_TRY(m.alloc(&h->omega_dev, 1));
+  RR_TRY(m.alloc(&h->max_bits, 1));
+  RR_TRY(build_lambda(h, lambda));
+  RR_TRY(phase(6));
+  RR_TRY(m.alloc(&h->dpart, rr::dense_col_blocks(N) * F));
+  RR_TRY(alloc_solve_workspace(h));
+  for (void *p : {(void *)C, (void *)rowabs, (void *)scratch64, (void *)remap, (void *)w.key,
+                  (void *)w.iota, (void *)w.cl_ptr, (void *)w.members, (void *)w.counts,
+                  (void *)w.cursor, (void *)w.tmp, (void *)w.scan_scratch, (void *)w.mm,
+                  (void *)w.changes})
+    m.release(p);
+  RR_TRY(phase(7));
   return RR_OK;
 }
 
@@ -334,22 +505,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
     RR_TRY(rr::sliced_choose_gather(h->pcsr, h->opt.gather, st));
     RR_TRY(rr::sliced_choose_gather(h->pcsc, h->opt.gather, st));
   }
-  h->n_parts = rr::kVecGrid;
-  for (double **v : {&h->b, &h->r, &h->z1, &h->z2, &h->z, &h->p, &h->q, &h->r1, &h->rt, &h->w_int})
-    RR_TRY(m.alloc(v, F));
-  RR_TRY(m.alloc(&h->u, std::max<int64_t>(N, 1)));
-  RR_TRY(m.alloc(&h->rc, k_eff));
-  RR_TRY(m.alloc(&h->ec, k_eff));
-  for (double **v : {&h->part_rz, &h->part_pq, &h->part_rr, &h->part_bb})
-    RR_TRY(m.alloc(v, h->n_parts));
-  RR_TRY(m.alloc(&h->scal, 4));
-  RR_TRY(m.alloc(&h->S, 1));
-  RR_CUDA(cudaMallocHost(&h->S_host, sizeof(rr::PcgScalars)));
-  RR_CUDA(cudaMallocHost(&h->scal_host, 4 * sizeof(double)));
-  RR_CUDA(cudaMallocHost(&h->limit_host, sizeof(int32_t)));
-  RR_CUDA(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
-  h->hist_cap = h->opt.max_iter;
-  RR_TRY(m.alloc(&h->history, h->hist_cap));
+  RR_TRY(alloc_solve_workspace(h));
   m.release(tmp32);
   m.release(scratch64);
   m.release(iota);
@@ -367,9 +523,22 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
 // ---- the operator: t = X^T (X v) + lambda v, finished by the epilogue ep.
 rr_status op_apply(rr_handle *h, const double *v, const rr::CscEpilogue &ep, const int32_t *stop,
                    cudaStream_t st, bool fp32 = false) {
+  if (h->dense) {
+    RR_TRY(rr::dense_matvec(h->N, h->F, h->Xd, v, h->u, stop, fp32, st));
+    return rr::dense_transposed(h->N, h->F, h->Xd, h->u, h->dpart, ep, fp32, st);
+  }
   RR_TRY(rr::sliced_gather(h->pcsr, v, nullptr, stop, st, fp32));
   RR_TRY(rr::sliced_gather(h->pcsc, nullptr, &h->pcsr, stop, st, fp32));
   RR_TRY(rr::sliced_epilogue(h->pcsc, ep, st));
+  return RR_OK;
+}
+
+// b = X^T y (FP64).
+rr_status rhs_apply(rr_handle *h, const double *y, double *b, cudaStream_t st) {
+  rr::CscEpilogue rhs{rr::CSC_RHS, 0.0, 0.0, nullptr, nullptr, nullptr, b, nullptr, nullptr};
+  if (h->dense) return rr::dense_transposed(h->N, h->F, h->Xd, y, h->dpart, rhs, false, st);
+  RR_TRY(rr::sliced_gather(h->pcsc, y, nullptr, nullptr, st));
+  RR_TRY(rr::sliced_epilogue(h->pcsc, rhs, st));
   return RR_OK;
 }
 
@@ -504,9 +673,7 @@ rr_status run_iterations(rr_handle *h, int32_t limit) {
 // b = X^T y; w = 0; r = b; ||b||; z1 = omega D^-1 r (no synchronisation).
 rr_status solve_start(rr_handle *h, const double *y, double tol, cudaStream_t st) {
   const int64_t F = h->F;
-  rr::CscEpilogue rhs{rr::CSC_RHS, 0.0, 0.0, nullptr, nullptr, nullptr, h->b, nullptr, nullptr};
-  RR_TRY(rr::sliced_gather(h->pcsc, y, nullptr, nullptr, st));
-  RR_TRY(rr::sliced_epilogue(h->pcsc, rhs, st));
+  RR_TRY(rhs_apply(h, y, h->b, st));
   RR_CUDA(cudaMemsetAsync(h->w_int, 0, sizeof(double) * F, st));
   RR_TRY(rr::copy_f64(h->r, h->b, F, st));
   RR_TRY(rr::dot_parts(F, h->b, h->b, h->part_bb, st));
@@ -703,9 +870,7 @@ rr_status solve_fcg_impl(rr_handle *h, const rr_mlp *net, const double *y, doubl
   cudaStream_t st = h->st;
   const int64_t F = h->F;
   RR_TRY(fcg_reserve(h));
-  rr::CscEpilogue rhs{rr::CSC_RHS, 0.0, 0.0, nullptr, nullptr, nullptr, h->b, nullptr, nullptr};
-  RR_TRY(rr::sliced_gather(h->pcsc, y, nullptr, nullptr, st));
-  RR_TRY(rr::sliced_epilogue(h->pcsc, rhs, st));
+  RR_TRY(rhs_apply(h, y, h->b, st));
   RR_CUDA(cudaMemsetAsync(h->w_int, 0, sizeof(double) * F, st));
   RR_CUDA(cudaMemsetAsync(h->p_prev, 0, sizeof(double) * F, st));
   RR_CUDA(cudaMemsetAsync(h->q_prev, 0, sizeof(double) * F, st));
@@ -930,13 +1095,19 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
     return RR_INVALID_ARG;
   }
   *out = nullptr;
-  if (X->layout != RR_CSR_BINARY) {
-    rr_set_error("rr_setup: only the binary CSR layout is supported by this build");
-    return RR_UNSUPPORTED;
+  if (X->layout != RR_CSR_BINARY && X->layout != RR_DENSE_F32_ROWMAJOR) {
+    rr_set_error("rr_setup: unknown layout %d", X->layout);
+    return RR_INVALID_ARG;
   }
-  if (X->n_rows < 1 || X->n_cols < 1 || X->nnz < 0 || !X->row_ptr || (X->nnz > 0 && !X->col_idx) ||
-      X->values) {
+  if (X->layout == RR_CSR_BINARY &&
+      (X->n_rows < 1 || X->n_cols < 1 || X->nnz < 0 || !X->row_ptr || (X->nnz > 0 && !X->col_idx) ||
+       X->values)) {
     rr_set_error("rr_setup: bad matrix description");
+    return RR_INVALID_ARG;
+  }
+  if (X->layout == RR_DENSE_F32_ROWMAJOR &&
+      (X->n_rows < 1 || X->n_cols < 1 || !X->values || X->row_ptr || X->col_idx)) {
+    rr_set_error("rr_setup: a dense X needs values and no row_ptr / col_idx");
     return RR_INVALID_ARG;
   }
   if (!(lambda > 0.0) || !isfinite(lambda)) {
@@ -975,7 +1146,8 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
   h->st = static_cast<cudaStream_t>(opt.stream);
   const auto t0 = std::chrono::steady_clock::now();
   h->opt.init_centers = opt.init_centers;
-  rr_status s = setup_impl(h, X, lambda, k);
+  rr_status s = X->layout == RR_DENSE_F32_ROWMAJOR ? setup_impl_dense(h, X, lambda, k)
+                                                   : setup_impl(h, X, lambda, k);
   h->opt.init_centers = nullptr;
   if (s != RR_OK) {
     rr_free(h);
@@ -1128,6 +1300,9 @@ rr_status rr_precondition(rr_handle *h, const double *r, double *z) {
 rr_status rr_rhs(rr_handle *h, const double *y, double *b) {
   if (!h || !y || !b) return RR_INVALID_ARG;
   rr::CscEpilogue ep{rr::CSC_RHS, 0.0, 0.0, nullptr, nullptr, nullptr, b, nullptr, nullptr};
+  if (h->dense)
+    return rr::dense_transposed(h->N, h->F, h->Xd, y, h->dpart, ep,
+                                h->opt.precision == RR_PREC_MIXED, h->st);
   RR_TRY(rr::sliced_gather(h->pcsc, y, nullptr, nullptr, h->st, h->opt.precision == RR_PREC_MIXED));
   RR_TRY(rr::sliced_epilogue(h->pcsc, ep, h->st));
   return RR_OK;
@@ -1135,6 +1310,9 @@ rr_status rr_rhs(rr_handle *h, const double *y, double *b) {
 
 rr_status rr_matvec(rr_handle *h, const double *v, double *u) {
   if (!h || !v || !u) return RR_INVALID_ARG;
+  if (h->dense)
+    return rr::dense_matvec(h->N, h->F, h->Xd, v, u, nullptr, h->opt.precision == RR_PREC_MIXED,
+                            h->st);
   RR_TRY(rr::sliced_gather(h->pcsr, v, nullptr, nullptr, h->st, h->opt.precision == RR_PREC_MIXED));
   RR_TRY(rr::sliced_slot_sum(h->pcsr, u, h->st));
   return RR_OK;
@@ -1156,6 +1334,10 @@ rr_status rr_get_centers(const rr_handle *h, int32_t *centers_host) {
 
 rr_status rr_get_coarse(const rr_handle *h, double *Ac_host, int64_t *G_host) {
   if (!h) return RR_INVALID_ARG;
+  if (h->dense && G_host) {
+    rr_set_error("rr_get_coarse: the integer Gram exists for binary X only");
+    return RR_UNSUPPORTED;
+  }
   const size_t kk = (size_t)h->k_eff * h->k_eff;
   if (Ac_host)
     RR_CUDA(cudaMemcpyAsync(Ac_host, h->Ac, sizeof(double) * kk, cudaMemcpyDeviceToHost, h->st));

@@ -169,6 +169,7 @@ class Handle:
     def __init__(self, ptr, F, N, keepalive):
         self.ptr = ptr
         self.F, self.N = F, N
+        self.dense = False
         self._keep = keepalive
 
     def __del__(self):
@@ -205,6 +206,32 @@ def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=N
     out = _P()
     _check(lib.rr_setup(ctypes.byref(X), float(lam), int(k), ctypes.byref(o), ctypes.byref(out)))
     return Handle(out, n_cols, n_rows, (ic,))
+
+
+def rr_setup_dense(X, lam, k, *, seed=0, init_centers=None, kmeans_max_iter=50, max_iter=20000,
+                   solver=RR_SOLVER_TWOLEVEL, check_every=8, max_restarts=5, use_graphs=1,
+                   precision=RR_PREC_FP64, stream=None) -> Handle:
+    """rr_setup on a dense X (N x F, float32 row-major) given as a numpy array
+    (host) or a torch CUDA tensor (device)."""
+    lib = load()
+    on_device = 0 if isinstance(X, np.ndarray) else 1
+    if on_device == 0:
+        X = np.ascontiguousarray(X, dtype=np.float32)
+    n_rows, n_cols = int(X.shape[0]), int(X.shape[1])
+    M = rr_matrix(n_rows, n_cols, n_rows * n_cols, None, None, _ptr(X), RR_DENSE_F32_ROWMAJOR,
+                  on_device)
+    ic = None
+    if init_centers is not None:
+        ic = np.ascontiguousarray(init_centers, dtype=np.int32)
+    o = rr_default_options(kmeans_max_iter=kmeans_max_iter, max_iter=max_iter, seed=seed,
+                           init_centers=_ptr(ic), solver=solver, check_every=check_every,
+                           max_restarts=max_restarts, use_graphs=use_graphs,
+                           precision=precision, stream=_stream_ptr(stream))
+    out = _P()
+    _check(lib.rr_setup(ctypes.byref(M), float(lam), int(k), ctypes.byref(o), ctypes.byref(out)))
+    h = Handle(out, n_cols, n_rows, (ic,))
+    h.dense = True
+    return h
 
 
 def rr_set_lambda(h: Handle, lam: float):
@@ -403,10 +430,11 @@ def rr_query(h: Handle) -> dict:
 
 
 def rr_get_coarse(h: Handle):
+    """(A_c, G): G is the exact integer Gram for binary X, None for dense X."""
     k = rr_query(h)["k_eff"]
     Ac = np.empty((k, k), dtype=np.float64)
-    G = np.empty((k, k), dtype=np.int64)
-    _check(load().rr_get_coarse(h.ptr, Ac.ctypes.data, G.ctypes.data))
+    G = None if h.dense else np.empty((k, k), dtype=np.int64)
+    _check(load().rr_get_coarse(h.ptr, Ac.ctypes.data, None if G is None else G.ctypes.data))
     return Ac, G
 
 

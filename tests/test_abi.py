@@ -57,4 +57,7 @@ def test_default_options_and_invalid_args_without_gpu(lib):
     assert L.rr_setup(ctypes.byref(X), 1.0, 0, None, ctypes.byref(out)) == rr.RR_INVALID_ARG
     assert L.rr_setup(ctypes.byref(X), 1.0, 4, None, ctypes.byref(out)) == rr.RR_INVALID_ARG
     X.layout = 7
-    assert L.rr_setup(ctypes.byref(X), 1.0, 1, None, ctypes.byref(out)) == rr.RR_UNSUPPORTED
+    assert L.rr_setup(ctypes.byref(X), 1.0, 1, None, ctypes.byref(out)) == rr.RR_INVALID_ARG
+    # a dense X needs values and no CSR arrays
+    X.layout = rr.RR_DENSE_F32_ROWMAJOR
+    assert L.rr_setup(ctypes.byref(X), 1.0, 1, None, ctypes.byref(out)) == rr.RR_INVALID_ARG
