@@ -264,10 +264,18 @@ def measure_many(rr, dev, stream, opts):
     excluded from both; they are reported apart)."""
     import torch
     from gen import synth
-    name = "uneven_12"
+    name = "uneven_12_dense4"
     probs = synth.many_workload(name)
     hs, ys, ws, setup_ms = [], [], [], []
     for X, y, p in probs:
+        if p.get("dense"):
+            o = {key: v for key, v in opts.items() if key not in ("gram", "gather")}
+            h = rr.rr_setup_dense(torch.as_tensor(X, device=dev), p["lam"], p["k"],
+                                  **dict(o, seed=p["seed"]))
+            hs.append(h)
+            ys.append(torch.as_tensor(y, device=dev))
+            ws.append(torch.empty(X.shape[1], dtype=torch.float64, device=dev))
+            continue
         rp = torch.as_tensor(X.row_ptr, device=dev)
         ci = torch.as_tensor(X.col_idx, device=dev)
         h = rr.rr_setup(rp, ci, X.n_rows, X.n_cols, p["lam"], p["k"], **dict(opts, seed=p["seed"]))
@@ -287,7 +295,33 @@ def measure_many(rr, dev, stream, opts):
     e[3].record(stream)
     torch.cuda.synchronize(dev)
     t_many, t_seq = e[0].elapsed_time(e[1]) / 1e3, e[2].elapsed_time(e[3]) / 1e3
-    sizes = [(X.n_rows, X.n_cols, X.nnz) for X, _, _ in probs]
+    sizes = [(X.shape[0], X.shape[1], X.size) if p.get("dense") else (X.n_rows, X.n_cols, X.nnz)
+             for X, _, p in probs]
+    # the dense operator apply X^T X v + lambda v on the first dense problem, in
+    # the handle's precision (the one the CG iterations use): X is read once
+    # (N F 4 bytes) plus v and the result (16 F bytes)
+    dense_apply = None
+    for h, (X, _, p) in zip(hs, probs):
+        if not p.get("dense"):
+            continue
+        n, f = X.shape
+        v = torch.randn(f, dtype=torch.float64, device=dev)
+        o = torch.empty_like(v)
+        for _ in range(3):
+            rr.rr_apply(h, v, o)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        reps = 20
+        for _ in range(reps):
+            rr.rr_apply(h, v, o)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = ev[0].elapsed_time(ev[1]) / reps
+        alg = 4 * n * f + 16 * f
+        dense_apply = {"n": n, "d": f, "ms": round(ms, 4), "algorithmic_bytes": alg,
+                       "achieved_gbs": round(alg / ms / 1e6, 1)}
+        break
     for h in hs:
         rr.rr_free(h)
     return {"workload": name, "problems": len(probs), "value": round(t_many, 4), "unit": "s",
@@ -295,7 +329,7 @@ def measure_many(rr, dev, stream, opts):
             "setup_s_total": round(sum(i["setup_ms"] for i in singles) / 1e3, 3),
             "iters": [i["iters"] for i in out["infos"]],
             "true_rel_res_max": max(i["true_rel_res"] for i in out["infos"]),
-            "sizes_n_d_nnz": sizes}
+            "sizes_n_d_nnz": sizes, "dense_apply": dense_apply}
 
 
 def measure_learned(rr, X, row_ptr, col_idx, k, opts, dev, stream, n_pairs=100_000,

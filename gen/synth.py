@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import os
 
 import numpy as np
 
@@ -58,11 +59,30 @@ def uniform(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
     return (raw64(seed, stream, n, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
 
 
-def normal(seed: int, stream: int, n: int) -> np.ndarray:
-    """Standard normals by the Box-Muller transform of two uniform streams."""
-    u1 = 1.0 - uniform(seed, stream, n, 0)          # (0, 1]
-    u2 = uniform(seed, stream, n, 1 << 40)
+def _normal_range(seed: int, stream: int, offset: int, n: int) -> np.ndarray:
+    u1 = 1.0 - uniform(seed, stream, n, offset)          # (0, 1]
+    u2 = uniform(seed, stream, n, (1 << 40) + offset)
     return np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * math.pi * u2)
+
+
+def normal(seed: int, stream: int, n: int) -> np.ndarray:
+    """Standard normals by the Box-Muller transform of two uniform streams
+    (normal i from uniforms i and 2^40 + i). Large draws are split into
+    ranges computed on several threads (numpy releases the GIL in its
+    element-wise loops); the values do not depend on the split."""
+    chunk = 1 << 22
+    if n <= 2 * chunk:
+        return _normal_range(seed, stream, 0, n)
+    import concurrent.futures as cf
+    out = np.empty(n, dtype=np.float64)
+
+    def fill(a):
+        out[a:a + min(chunk, n - a)] = _normal_range(seed, stream, a, min(chunk, n - a))
+
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        list(ex.map(fill, range(0, n, chunk)))
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -210,7 +230,16 @@ def dense_ar1(n_rows: int, n_cols: int, rho: float = 0.9, seed: int = 0) -> np.n
     c = math.sqrt(1.0 - rho * rho)
     for j in range(1, n_cols):
         out[j] = rho * out[j - 1] + c * eps[j]
-    return np.ascontiguousarray(out.T).astype(np.float32)
+    # X = out^T rounded to float32, by blocks of rows on several threads
+    X = np.empty((n_rows, n_cols), dtype=np.float32)
+
+    def put(r0):
+        X[r0:r0 + 256] = out[:, r0:r0 + 256].T
+
+    import concurrent.futures as cf
+    with cf.ThreadPoolExecutor(max(1, min(16, os.cpu_count() or 1))) as ex:
+        list(ex.map(put, range(0, n_rows, 256)))
+    return X
 
 
 def duplicated_features(base: np.ndarray, counts) -> tuple[np.ndarray, np.ndarray]:
@@ -246,12 +275,18 @@ BATCH_WORKLOADS = {
 # k = d // 100): n ~ U[10k, 100k], d ~ U[5k, 40k], density ~ U[0.1%, 1%],
 # problem i drawn from seed i (a scaled stand-in of 28 problems up to
 # 400,000 x 150,000, whose generation on the host alone would take minutes)
+# "uneven_12_dense4" adds the four dense problems at full size: 50,000 x 4,000
+# float32 AR(1) (rho = 0.9), k = 40, drawn from seeds 12..15.
 MANY_WORKLOADS = {"uneven_12": dict(n_problems=12, n=(10_000, 100_000), d=(5_000, 40_000),
-                                    density=(0.001, 0.01), lam=1e-2)}
+                                    density=(0.001, 0.01), lam=1e-2),
+                  "uneven_12_dense4": dict(n_problems=12, n=(10_000, 100_000), d=(5_000, 40_000),
+                                           density=(0.001, 0.01), lam=1e-2,
+                                           n_dense=4, dense=(50_000, 4_000), rho=0.9)}
 
 
 def many_workload(name: str):
-    """[(X, y, params)] of a named set of independent problems."""
+    """[(X, y, params)] of a named set of independent problems (X a CSR
+    pattern, or a dense float32 array when params["dense"])."""
     p = MANY_WORKLOADS[name]
     out = []
     for i in range(p["n_problems"]):
@@ -262,6 +297,13 @@ def many_workload(name: str):
         X = zipf_binary(n, d, dens, 1.1, i)
         y, _ = ridge_targets(X, i)
         out.append((X, y, dict(n=n, d=d, density=dens, k=max(2, d // 100), lam=p["lam"], seed=i)))
+    for j in range(p.get("n_dense", 0)):
+        i = p["n_problems"] + j
+        n, d = p["dense"]
+        X = dense_ar1(n, d, p["rho"], i)
+        y, _ = ridge_targets(X, i)
+        out.append((X, y, dict(n=n, d=d, density=1.0, k=max(2, d // 100), lam=p["lam"], seed=i,
+                               dense=True)))
     return out
 
 

@@ -14,11 +14,18 @@
 // lowest unchosen one if every D2 is 0). Lloyd: score(i, S) = ||mu_S||^2 -
 // 2 x_i . mu_S, the smallest S on ties, empty clusters skipped.
 //
-// Operator: u = X v by one warp per row (FP32 or FP64 accumulation); X^T u by
-// column partial sums over row blocks (one thread per column and block),
-// then the epilogue sums the block partials in order and applies the PCG
-// epilogue. X is read twice per apply (the memory roofline of the dense form).
+// Operator X^T X v: one pass over X when F is a multiple of 4 and at most
+// 8192 (k_dfused): each thread owns the same 4-column groups of every row,
+// keeps v and its column sums in registers, and for each tile of R rows loads
+// its x values once, forms its share of the R row dots, the block sums them
+// (u_r = x_r . v, one barrier per tile), and adds x_ri u_r to its column sums;
+// tiles go to the blocks round-robin, so the per-block partials and their
+// in-order sum in the epilogue repeat bit for bit. Otherwise two passes: u =
+// X v by one warp per row, X^T u by column partial sums over row blocks.
 #include <math.h>
+
+#include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "epilogue.cuh"
@@ -176,43 +183,48 @@ __global__ void k_dmm(int32_t k, int64_t nb, const double *__restrict__ part,
   }
 }
 
-// dot[s F + i] = x_i . mu_s in the blocked order, for the kDotS clusters of
-// blockIdx.y; the block's mu rows are staged in shared memory per row block.
+// The row-block partial dots of the kDotS clusters s0 .. s0 + kDotS - 1:
+// part[(b kDotS + j) F + i] = sum over the rows of block b, ascending, of
+// x_ri mu_(s0+j),r. One block of threads per (128 columns, row block); the
+// block's mu rows are staged in shared memory.
 constexpr int kDotS = 8, kDotThreads = 128;
-__global__ void __launch_bounds__(kDotThreads) k_ddot(int64_t N, int64_t F, int32_t k,
-                                                      const float *__restrict__ X,
-                                                      const double *__restrict__ mu,
-                                                      double *__restrict__ dot) {
+__global__ void __launch_bounds__(kDotThreads) k_ddot_part(int64_t N, int64_t F, int32_t k, int32_t s0,
+                                                           const float *__restrict__ X,
+                                                           const double *__restrict__ mu,
+                                                           double *__restrict__ part) {
   __shared__ double mus[kDotS][kRowBlock];
   const int64_t i = (int64_t)blockIdx.x * kDotThreads + threadIdx.x;
-  const int32_t s0 = blockIdx.y * kDotS;
+  const int64_t b = blockIdx.y;
+  const int64_t r0 = b * kRowBlock;
+  const int rn = (int)min((int64_t)kRowBlock, N - r0);
   const int ns = min(kDotS, k - s0);
-  double tot[kDotS];
-#pragma unroll
-  for (int j = 0; j < kDotS; ++j) tot[j] = 0.0;
-  for (int64_t r0 = 0; r0 < N; r0 += kRowBlock) {
-    const int rn = (int)min((int64_t)kRowBlock, N - r0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < kDotS * kRowBlock; e += kDotThreads) {
-      const int j = e / kRowBlock, rr = e % kRowBlock;
-      mus[j][rr] = (j < ns && rr < rn) ? mu[(int64_t)(s0 + j) * N + r0 + rr] : 0.0;
-    }
-    __syncthreads();
-    if (i < F) {
-      double part[kDotS];
-#pragma unroll
-      for (int j = 0; j < kDotS; ++j) part[j] = 0.0;
-      for (int rr = 0; rr < rn; ++rr) {
-        const double x = (double)X[(r0 + rr) * F + i];
-#pragma unroll
-        for (int j = 0; j < kDotS; ++j) part[j] = __dadd_rn(part[j], __dmul_rn(x, mus[j][rr]));
-      }
-#pragma unroll
-      for (int j = 0; j < kDotS; ++j) tot[j] = __dadd_rn(tot[j], part[j]);
-    }
+  for (int e = threadIdx.x; e < kDotS * kRowBlock; e += kDotThreads) {
+    const int j = e / kRowBlock, rr = e % kRowBlock;
+    mus[j][rr] = (j < ns && rr < rn) ? mu[(int64_t)(s0 + j) * N + r0 + rr] : 0.0;
   }
-  if (i < F)
-    for (int j = 0; j < ns; ++j) dot[(int64_t)(s0 + j) * F + i] = tot[j];
+  __syncthreads();
+  if (i >= F) return;
+  double p[kDotS];
+#pragma unroll
+  for (int j = 0; j < kDotS; ++j) p[j] = 0.0;
+  for (int rr = 0; rr < rn; ++rr) {
+    const double x = (double)X[(r0 + rr) * F + i];
+#pragma unroll
+    for (int j = 0; j < kDotS; ++j) p[j] = __dadd_rn(p[j], __dmul_rn(x, mus[j][rr]));
+  }
+#pragma unroll
+  for (int j = 0; j < kDotS; ++j) part[(b * kDotS + j) * F + i] = p[j];
+}
+
+// dot[(s0 + j) F + i] = the block partials summed in ascending block order.
+__global__ void k_ddot_chain(int64_t F, int64_t nb, int32_t ns, int32_t s0,
+                             const double *__restrict__ part, double *__restrict__ dot) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)ns * F) return;
+  const int64_t j = e / F, i = e % F;
+  double t = 0.0;
+  for (int64_t b = 0; b < nb; ++b) t = __dadd_rn(t, part[(b * kDotS + j) * F + i]);
+  dot[(s0 + j) * F + i] = t;
 }
 
 // next label: argmin over non-empty S of mm_S - 2 dot_S,i (first minimum); changes counted.
@@ -267,17 +279,31 @@ __global__ void k_drowabs(int64_t N, int64_t F, const float *__restrict__ X, dou
     if (lane == 0) ra[r] = s;
   }
 }
-// per column: sq[i] = sum_r x^2, gs[i] = sum_r |x_ri| ra[r]  (sum_j |(X^T X)_ij| <= gs[i])
-__global__ void k_dcolstats(int64_t N, int64_t F, const float *__restrict__ X,
-                            const double *__restrict__ ra, double *__restrict__ sq,
-                            double *__restrict__ gs) {
+// per column and block of kColRows rows: part[(2 b) F + i] = sum x^2,
+// part[(2 b + 1) F + i] = sum |x_ri| ra[r]  (sum_j |(X^T X)_ij| <= gs[i]).
+__global__ void k_dcolstats_part(int64_t N, int64_t F, const float *__restrict__ X,
+                                 const double *__restrict__ ra, double *__restrict__ part) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t b = blockIdx.y;
   if (i >= F) return;
+  const int64_t r0 = b * kColRows, r1 = min(N, r0 + kColRows);
   double a = 0.0, g = 0.0;
-  for (int64_t r = 0; r < N; ++r) {
+  for (int64_t r = r0; r < r1; ++r) {
     const double x = (double)X[r * F + i];
     a += x * x;
     g += fabs(x) * ra[r];
+  }
+  part[(2 * b) * F + i] = a;
+  part[(2 * b + 1) * F + i] = g;
+}
+__global__ void k_dcolstats(int64_t F, int64_t nb, const double *__restrict__ part,
+                            double *__restrict__ sq, double *__restrict__ gs) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= F) return;
+  double a = 0.0, g = 0.0;
+  for (int64_t b = 0; b < nb; ++b) {
+    a += part[(2 * b) * F + i];
+    g += part[(2 * b + 1) * F + i];
   }
   sq[i] = a;
   gs[i] = g;
@@ -350,18 +376,127 @@ __global__ void __launch_bounds__(kThreads) k_dxtu(int64_t N, int64_t F, const f
   part[(int64_t)blockIdx.y * F + i] = (double)acc;
 }
 
-// t_i = sum of the row-block partials (in order), then the epilogue; kVecGrid partial dots.
+// One pass of X^T X v (see the file header). R rows per tile, G 4-column
+// groups per thread (columns 4 (tid + 256 g) .. +3); every product and sum,
+// the row dots' reductions included, in T (FP32 here keeps the FP64 pipe,
+// a small fraction of the FP32 rate on this part, out of the loop);
+// part[blockIdx.x * F + i] receives the block's sum for column i.
+template <typename T, int R, int G>
+__global__ void __launch_bounds__(kThreads) k_dfused(int64_t N, int64_t F, const float *__restrict__ X,
+                                                     const double *__restrict__ v,
+                                                     double *__restrict__ part,
+                                                     const int32_t *__restrict__ stop) {
+  pdl_wait();
+  if (stop && *stop) return;
+  __shared__ T red[2][R][kWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t F4 = F >> 2;
+  const float4 *X4 = reinterpret_cast<const float4 *>(X);
+  T vr[G][4], acc[G][4];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int64_t c4 = tid + (int64_t)g * kThreads;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      vr[g][j] = c4 < F4 ? (T)v[4 * c4 + j] : (T)0;
+      acc[g][j] = (T)0;
+    }
+  }
+  const int64_t n_tiles = (N + R - 1) / R;
+  int par = 0;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t r0 = tile * R;
+    float4 x[R][G];
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int64_t c4 = tid + (int64_t)g * kThreads;
+        x[r][g] = (r0 + r < N && c4 < F4) ? __ldcs(X4 + (r0 + r) * F4 + c4)
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    T pr[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T sdot = (T)0;
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        sdot += (T)x[r][g].x * vr[g][0];
+        sdot += (T)x[r][g].y * vr[g][1];
+        sdot += (T)x[r][g].z * vr[g][2];
+        sdot += (T)x[r][g].w * vr[g][3];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
+      pr[r] = sdot;
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) red[par][r][warp] = pr[r];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T u = (T)0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) u += red[par][r][w];
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        acc[g][0] += (T)x[r][g].x * u;
+        acc[g][1] += (T)x[r][g].y * u;
+        acc[g][2] += (T)x[r][g].z * u;
+        acc[g][3] += (T)x[r][g].w * u;
+      }
+    }
+    par ^= 1;
+  }
+  double *out = part + (int64_t)blockIdx.x * F;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int64_t c4 = tid + (int64_t)g * kThreads;
+    if (c4 < F4) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) out[4 * c4 + j] = (double)acc[g][j];
+    }
+  }
+}
+
+// t_i = sum of the nb row-block partials of column i, then the epilogue;
+// kVecGrid partial dots. A block takes 32 columns at a time: warp g sums the
+// partials b = g, g + 8, ... (four loads in flight), warp 0 adds the eight
+// warp sums in order, so the bits do not depend on the launch.
 __global__ void __launch_bounds__(kThreads) k_depi(int64_t F, int64_t nb,
                                                    const double *__restrict__ part, CscEpilogue ep) {
   pdl_wait();
   if (ep.stop && *ep.stop) return;
+  __shared__ double red[kWarps][33];
   __shared__ double sm[kWarps + 1];
+  const int c = threadIdx.x & 31, g = threadIdx.x >> 5;
   double dot = 0.0;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t c0 = (int64_t)blockIdx.x * 32; c0 < F; c0 += (int64_t)gridDim.x * 32) {
+    const int64_t i = c0 + c;
     double s = 0.0;
-    for (int64_t b = 0; b < nb; ++b) s += part[b * F + i];
-    epilogue(ep, i, s, dot);
+    if (i < F) {
+      int64_t b = g;
+      for (; b + 3 * kWarps < nb; b += 4 * kWarps) {
+        const double a0 = part[b * F + i], a1 = part[(b + kWarps) * F + i];
+        const double a2 = part[(b + 2 * kWarps) * F + i], a3 = part[(b + 3 * kWarps) * F + i];
+        s += a0;
+        s += a1;
+        s += a2;
+        s += a3;
+      }
+      for (; b < nb; b += kWarps) s += part[b * F + i];
+    }
+    red[g][c] = s;
+    __syncthreads();
+    if (g == 0 && i < F) {
+      double t = 0.0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) t += red[w][c];
+      epilogue(ep, i, t, dot);
+    }
+    __syncthreads();
   }
   const double tot = block_sum(dot, sm);
   if (threadIdx.x == 0 && ep.dot_part) ep.dot_part[blockIdx.x] = tot;
@@ -404,8 +539,13 @@ rr_status dense_lloyd(int64_t N, int64_t F, const float *X, int32_t k, const int
     RR_LAUNCH(k_dmm_part, dim3((unsigned)((nb + kThreads - 1) / kThreads), (unsigned)k), kThreads,
               0, st, N, nb, w.mu, w.part);
     RR_LAUNCH(k_dmm, 1, 64, 0, st, k, nb, w.part, w.mm);
-    RR_LAUNCH(k_ddot, dim3((unsigned)((F + kDotThreads - 1) / kDotThreads), (unsigned)((k + kDotS - 1) / kDotS)),
-              kDotThreads, 0, st, N, F, k, X, w.mu, w.dot);
+    for (int32_t s0 = 0; s0 < k; s0 += kDotS) {
+      RR_LAUNCH(k_ddot_part, dim3((unsigned)((F + kDotThreads - 1) / kDotThreads), (unsigned)nb),
+                kDotThreads, 0, st, N, F, k, s0, X, w.mu, w.dpart);
+      const int32_t ns = std::min(kDotS, k - s0);
+      RR_LAUNCH(k_ddot_chain, grid_for((int64_t)ns * F, kThreads), kThreads, 0, st, F, nb, ns, s0,
+                w.dpart, w.dot);
+    }
     RR_CUDA(cudaMemsetAsync(w.changes, 0, sizeof(unsigned long long), st));
     RR_LAUNCH(k_dargmin, grid_for(F, kThreads), kThreads, 0, st, F, k, w.cl_ptr, w.mm, w.dot,
               labels, w.changes);
@@ -426,12 +566,19 @@ rr_status dense_coarse_gram(int64_t N, int64_t F, const float *X, int32_t k_eff,
   return RR_OK;
 }
 
-rr_status dense_colstats(int64_t N, int64_t F, const float *X, double *rowabs, double *sq,
-                         double *gs, cudaStream_t st) {
+rr_status dense_colstats(int64_t N, int64_t F, const float *X, double *rowabs, double *part,
+                         double *sq, double *gs, cudaStream_t st) {
+  const int64_t nb = dense_col_blocks(N);
   RR_LAUNCH(k_drowabs, grid_for(N, kWarps), kThreads, 0, st, N, F, X, rowabs);
-  RR_LAUNCH(k_dcolstats, (unsigned)((F + kThreads - 1) / kThreads), kThreads, 0, st, N, F, X,
-            rowabs, sq, gs);
+  RR_LAUNCH(k_dcolstats_part, dim3((unsigned)((F + kThreads - 1) / kThreads), (unsigned)nb),
+            kThreads, 0, st, N, F, X, rowabs, part);
+  RR_LAUNCH(k_dcolstats, (unsigned)((F + kThreads - 1) / kThreads), kThreads, 0, st, F, nb, part,
+            sq, gs);
   return RR_OK;
+}
+
+int64_t dense_dot_part_len(int64_t N, int64_t F) {
+  return ((N + kRowBlock - 1) / kRowBlock) * kDotS * F;
 }
 
 rr_status dense_jacobi(int64_t F, double lambda, const double *sq, const double *gs, double *d,
@@ -473,6 +620,100 @@ rr_status dense_transposed(int64_t N, int64_t F, const float *X, const double *u
     RR_LAUNCH_PDL(k_dxtu<double>, g, kThreads, 0, st, N, F, X, u, part, ep.stop);
   RR_LAUNCH_PDL(k_depi, kVecGrid, kThreads, 0, st, F, nb, part, ep);
   return RR_OK;
+}
+
+namespace {
+
+// 4-column groups per thread for F columns (0: no one-pass kernel for this F).
+int fused_groups(int64_t F) {
+  if (F % 4 != 0) return 0;
+  const int64_t g = (F / 4 + kThreads - 1) / kThreads;
+  return g <= 1 ? 1 : g <= 2 ? 2 : g <= 4 ? 4 : g <= 8 ? 8 : 0;
+}
+
+// Blocks of the one-pass kernel: all that fit on the device at once.
+template <typename T, int R, int G>
+int fused_grid() {
+  static int grid = 0;
+  if (grid == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dfused<T, R, G>, kThreads, 0) !=
+            cudaSuccess)
+      return 0;
+    grid = std::max(1, sms * std::max(1, per_sm));
+  }
+  return grid;
+}
+
+// The (T, R, G) instantiation for 4-column groups G: R rows per tile keep the
+// x values of a tile at <= 64 registers (FP32) or the accumulators and v
+// within the register file (FP64).
+template <typename Fn>
+rr_status with_fused(int G, bool fp32, Fn &&fn) {
+  if (fp32) {
+    switch (G) {
+      case 1: return fn(std::integral_constant<int, 0>{});
+      case 2: return fn(std::integral_constant<int, 1>{});
+      case 4: return fn(std::integral_constant<int, 2>{});
+      default: return fn(std::integral_constant<int, 3>{});
+    }
+  }
+  switch (G) {
+    case 1: return fn(std::integral_constant<int, 4>{});
+    case 2: return fn(std::integral_constant<int, 5>{});
+    case 4: return fn(std::integral_constant<int, 6>{});
+    default: return fn(std::integral_constant<int, 7>{});
+  }
+}
+template <int V> struct Fused;
+template <> struct Fused<0> { using T = float; static constexpr int R = 4, G = 1; };
+template <> struct Fused<1> { using T = float; static constexpr int R = 4, G = 2; };
+template <> struct Fused<2> { using T = float; static constexpr int R = 4, G = 4; };
+template <> struct Fused<3> { using T = float; static constexpr int R = 2, G = 8; };
+template <> struct Fused<4> { using T = double; static constexpr int R = 4, G = 1; };
+template <> struct Fused<5> { using T = double; static constexpr int R = 4, G = 2; };
+template <> struct Fused<6> { using T = double; static constexpr int R = 2, G = 4; };
+template <> struct Fused<7> { using T = double; static constexpr int R = 1, G = 8; };
+
+}  // namespace
+
+int64_t dense_part_rows(int64_t N, int64_t F) {
+  int64_t rows = dense_col_blocks(N);
+  const int G = fused_groups(F);
+  if (G == 0) return rows;
+  for (bool fp32 : {true, false}) {
+    int grid = 0;
+    with_fused(G, fp32, [&](auto v) -> rr_status {
+      using C = Fused<decltype(v)::value>;
+      grid = fused_grid<typename C::T, C::R, C::G>();
+      return RR_OK;
+    });
+    rows = std::max<int64_t>(rows, grid);
+  }
+  return rows;
+}
+
+rr_status dense_operator(int64_t N, int64_t F, const float *X, const double *v, double *u,
+                         double *part, const CscEpilogue &ep, bool fp32, cudaStream_t st) {
+  const int G = fused_groups(F);
+  if (G == 0) {
+    RR_TRY(dense_matvec(N, F, X, v, u, ep.stop, fp32, st));
+    return dense_transposed(N, F, X, u, part, ep, fp32, st);
+  }
+  return with_fused(G, fp32, [&](auto tag) -> rr_status {
+    using C = Fused<decltype(tag)::value>;
+    const int grid = fused_grid<typename C::T, C::R, C::G>();
+    if (grid == 0) {
+      rr_set_error("dense operator: occupancy query failed");
+      return RR_CUDA_ERROR;
+    }
+    RR_LAUNCH_PDL((k_dfused<typename C::T, C::R, C::G>), grid, kThreads, 0, st, N, F, X, v, part,
+                  ep.stop);
+    RR_LAUNCH_PDL(k_depi, kVecGrid, kThreads, 0, st, F, (int64_t)grid, part, ep);
+    return RR_OK;
+  });
 }
 
 }  // namespace rr

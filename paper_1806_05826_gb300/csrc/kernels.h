@@ -305,8 +305,10 @@ struct DenseKmeansScratch {
   double *part;          // [k*nb]
   double *mm;            // [k]
   double *dot;           // [k*F]
+  double *dpart;         // dense_dot_part_len(N, F): row-block partial dots
   unsigned long long *changes;
 };
+int64_t dense_dot_part_len(int64_t N, int64_t F);
 rr_status dense_kmeanspp(int64_t N, int64_t F, const float *X, int32_t k, uint64_t seed,
                          int32_t *centers, double *d2, uint8_t *chosen, double *part, int32_t *err,
                          cudaStream_t st);
@@ -318,14 +320,22 @@ rr_status dense_coarse_gram(int64_t N, int64_t F, const float *X, int32_t k_eff,
                             const int64_t *cl_ptr, const int32_t *members, double *C, double *G,
                             cudaStream_t st);
 // sq_i = ||x_i||^2; gs_i = sum_r |x_ri| sum_j |x_rj| (>= sum_j |(X^T X)_ij|).
-rr_status dense_colstats(int64_t N, int64_t F, const float *X, double *rowabs, double *sq,
-                         double *gs, cudaStream_t st);
+// rowabs: [N]; part: [2 dense_col_blocks(N) F].
+rr_status dense_colstats(int64_t N, int64_t F, const float *X, double *rowabs, double *part,
+                         double *sq, double *gs, cudaStream_t st);
 rr_status dense_jacobi(int64_t F, double lambda, const double *sq, const double *gs, double *d,
                        unsigned long long *max_bits, cudaStream_t st);
 int64_t dense_col_blocks(int64_t N);
 // u = X v (FP32 accumulation when fp32).
 rr_status dense_matvec(int64_t N, int64_t F, const float *X, const double *v, double *u,
                        const int32_t *stop, bool fp32, cudaStream_t st);
+// Rows of the partial-sum buffer that dense_operator and dense_transposed
+// need: part holds dense_part_rows(N, F) * F doubles.
+int64_t dense_part_rows(int64_t N, int64_t F);
+// X^T X v, then the epilogue ep (one pass over X when F % 4 == 0 and F <= 8192;
+// else u = X v into u and X^T u).
+rr_status dense_operator(int64_t N, int64_t F, const float *X, const double *v, double *u,
+                         double *part, const CscEpilogue &ep, bool fp32, cudaStream_t st);
 // t = X^T u in row-block partials, then the epilogue ep (part: [dense_col_blocks(N) * F]).
 rr_status dense_transposed(int64_t N, int64_t F, const float *X, const double *u, double *part,
                            const CscEpilogue &ep, bool fp32, cudaStream_t st);

@@ -240,6 +240,7 @@ rr_status setup_impl_dense(rr_handle *h, const rr_matrix *X, double lambda, int3
   RR_TRY(m.alloc(&w.part, (int64_t)k * nb));
   RR_TRY(m.alloc(&w.mm, k));
   RR_TRY(m.alloc(&w.dot, (int64_t)k * F));
+  RR_TRY(m.alloc(&w.dpart, rr::dense_dot_part_len(N, F)));
   RR_TRY(m.alloc(&w.changes, 1));
   RR_TRY(rr::iota_i64(w.iota, F + 1, st));
   int32_t iters = 0;
@@ -251,6 +252,7 @@ rr_status setup_impl_dense(rr_handle *h, const rr_matrix *X, double lambda, int3
   m.release(w.mu);
   m.release(w.part);
   m.release(w.dot);
+  m.release(w.dpart);
   RR_TRY(phase(3));
   // ---- compaction, member lists, prolongation scale
   int32_t *remap = nullptr;
@@ -277,7 +279,9 @@ rr_status setup_impl_dense(rr_handle *h, const rr_matrix *X, double lambda, int3
   RR_TRY(m.alloc(&rowabs, N));
   RR_TRY(m.alloc(&h->dsq, F));
   RR_TRY(m.alloc(&h->dgs, F));
-  RR_TRY(rr::dense_colstats(N, F, h->Xd, rowabs, h->dsq, h->dgs, st));
+  double *cs_part = nullptr;
+  RR_TRY(m.alloc(&cs_part, 2 * rr::dense_col_blocks(N) * F));
+  RR_TRY(rr::dense_colstats(N, F, h->Xd, rowabs, cs_part, h->dsq, h->dgs, st));
   RR_TRY(phase(5));
   const int64_t kk = (int64_t)k_eff * k_eff;
   RR_TRY(m.alloc(&h->Ac, kk));
@@ -289,9 +293,9 @@ rr_status setup_impl_dense(rr_handle *h, const rr_matrix *X, double lambda, int3
   RR_TRY(m.alloc(&h->max_bits, 1));
   RR_TRY(build_lambda(h, lambda));
   RR_TRY(phase(6));
-  RR_TRY(m.alloc(&h->dpart, rr::dense_col_blocks(N) * F));
+  RR_TRY(m.alloc(&h->dpart, rr::dense_part_rows(N, F) * F));
   RR_TRY(alloc_solve_workspace(h));
-  for (void *p : {(void *)C, (void *)rowabs, (void *)scratch64, (void *)remap, (void *)w.key,
+  for (void *p : {(void *)C, (void *)rowabs, (void *)cs_part, (void *)scratch64, (void *)remap, (void *)w.key,
                   (void *)w.iota, (void *)w.cl_ptr, (void *)w.members, (void *)w.counts,
                   (void *)w.cursor, (void *)w.tmp, (void *)w.scan_scratch, (void *)w.mm,
                   (void *)w.changes})
@@ -523,10 +527,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
 // ---- the operator: t = X^T (X v) + lambda v, finished by the epilogue ep.
 rr_status op_apply(rr_handle *h, const double *v, const rr::CscEpilogue &ep, const int32_t *stop,
                    cudaStream_t st, bool fp32 = false) {
-  if (h->dense) {
-    RR_TRY(rr::dense_matvec(h->N, h->F, h->Xd, v, h->u, stop, fp32, st));
-    return rr::dense_transposed(h->N, h->F, h->Xd, h->u, h->dpart, ep, fp32, st);
-  }
+  if (h->dense) return rr::dense_operator(h->N, h->F, h->Xd, v, h->u, h->dpart, ep, fp32, st);
   RR_TRY(rr::sliced_gather(h->pcsr, v, nullptr, stop, st, fp32));
   RR_TRY(rr::sliced_gather(h->pcsc, nullptr, &h->pcsr, stop, st, fp32));
   RR_TRY(rr::sliced_epilogue(h->pcsc, ep, st));

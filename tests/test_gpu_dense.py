@@ -89,6 +89,34 @@ def test_dense_operator_rhs_matvec(case, rr):
     assert np.max(np.abs(u.cpu().numpy() - uw)) <= 1e-12 * np.abs(uw).max()
 
 
+@pytest.mark.parametrize("F", [8192, 8196, 8200])
+def test_dense_operator_one_and_two_pass(rr, F):
+    """F = 8192 takes the one-pass kernel with 8 column groups per thread;
+    8196 and 8200 have too many groups and take the two-pass form (and 8196
+    is a multiple of 4, 8200 too: the group count decides). Both precisions
+    against X^T (X v) + lambda v in FP64."""
+    X = synth.dense_ar1(333, F, 0.9, 6)
+    v = np.random.default_rng(3).standard_normal(F)
+    want = X.T.astype(np.float64) @ (X.astype(np.float64) @ v) + 0.5 * v
+    for prec, tol in ((rr.RR_PREC_FP64, 1e-12), (rr.RR_PREC_MIXED, 1e-5)):
+        h = rr.rr_setup_dense(X, 0.5, 2, seed=0, precision=prec)
+        out = torch.empty(F, dtype=torch.float64, device="cuda")
+        rr.rr_apply(h, dev(v), out)
+        assert np.linalg.norm(out.cpu().numpy() - want) <= tol * np.linalg.norm(want)
+
+
+def test_dense_operator_mixed_precision(case, rr):
+    """FP32 products and sums inside each block, FP64 across blocks: relative
+    error of a few FP32 roundings per term times the growth of the sums."""
+    X, ref = case["X"], case["ref"]
+    h = rr.rr_setup_dense(X, case["lam"], case["k"], seed=case["seed"], precision=rr.RR_PREC_MIXED)
+    v = np.random.default_rng(4).standard_normal(X.shape[1])
+    out = torch.empty(X.shape[1], dtype=torch.float64, device="cuda")
+    rr.rr_apply(h, dev(v), out)
+    want = ref.A(v)
+    assert np.linalg.norm(out.cpu().numpy() - want) <= 1e-5 * np.linalg.norm(want)
+
+
 def test_dense_preconditioner(case, rr):
     ref = case["ref"]
     r = np.random.default_rng(2).standard_normal(case["X"].shape[1])
