@@ -10,6 +10,8 @@
 // unchosen feature if every D2 is zero.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -17,7 +19,7 @@ namespace rr {
 
 namespace {
 
-constexpr int kTile = 1024;   // features per block in the seeding pass
+constexpr int kTile = kThreads;   // features per block in the seeding pass (one each)
 // below this many (row entry x delta pair) updates a Lloyd step pushes the
 // changes with global atomics instead of re-gathering every feature
 constexpr unsigned long long kPushWorkLimit = 200ull * 1000 * 1000;
@@ -90,89 +92,161 @@ __global__ void k_first_center(int64_t F, uint64_t seed, int32_t *centers, uint8
 // is the smaller set. Its rows are stamped with the round in rowmark.
 __device__ __forceinline__ bool heavy_centre(int64_t nc, int64_t N) { return 2 * nc > N; }
 
-__global__ void k_seed_mark(const int32_t *__restrict__ round, const int32_t *__restrict__ centers,
-                            int64_t N, const int64_t *__restrict__ col_ptr,
-                            const int32_t *__restrict__ row_idx, int32_t *__restrict__ rowmark) {
-  pdl_wait();
-  const int32_t t = *round;
-  const int64_t c = centers[t];
+// Stamps the rows of a heavy centre c with t + 1 (grid-stride over its column).
+__device__ __forceinline__ void seed_mark(int32_t t, int64_t c, int64_t N,
+                                          const int64_t *__restrict__ col_ptr,
+                                          const int32_t *__restrict__ row_idx,
+                                          int32_t *__restrict__ rowmark) {
   if (!heavy_centre(col_ptr[c + 1] - col_ptr[c], N)) return;
   for (int64_t p = col_ptr[c] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < col_ptr[c + 1];
        p += (int64_t)gridDim.x * blockDim.x)
     rowmark[row_idx[p]] = t + 1;
 }
 
-// ov[j] += 1 for every feature j sharing a row with centre centers[t] (for a
-// heavy centre: for every row the centre does not hold).
-__global__ void k_seed_overlap(const int32_t *__restrict__ round, const int32_t *__restrict__ centers,
-                               int64_t N, const int64_t *__restrict__ row_ptr,
-                               const int32_t *__restrict__ col_idx,
-                               const int64_t *__restrict__ col_ptr,
-                               const int32_t *__restrict__ row_idx,
-                               const int32_t *__restrict__ rowmark, int32_t *__restrict__ ov) {
+__global__ void k_seed_mark(const int32_t *__restrict__ round, const int32_t *__restrict__ centers,
+                            int64_t N, const int64_t *__restrict__ col_ptr,
+                            const int32_t *__restrict__ row_idx, int32_t *__restrict__ rowmark) {
   pdl_wait();
   const int32_t t = *round;
-  const int64_t c = centers[t];
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  if (heavy_centre(col_ptr[c + 1] - col_ptr[c], N)) {
-    for (int64_t r = warp; r < N; r += nwarps) {
-      if (rowmark[r] == t + 1) continue;
-      for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) atomicAdd(&ov[col_idx[e]], 1);
+  seed_mark(t, centers[t], N, col_ptr, row_idx, rowmark);
+}
+
+// Frequent features (at least kHotMin and N/128 rows; at most kHotBins of them)
+// get a bin of a per-block shared histogram in the overlap pass: every row of a
+// large centre holds most of them, and counting them in shared memory first
+// keeps those increments off a few global addresses.
+constexpr int kHotBins = 2048;
+constexpr int64_t kHotMin = 64;
+
+__global__ void k_hot_assign(int64_t F, int64_t N, const int64_t *__restrict__ col_ptr,
+                             uint16_t *__restrict__ hot, int32_t *__restrict__ hot_col,
+                             int32_t *__restrict__ hot_n) {
+  const int64_t thr = max(kHotMin, N / 128);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint16_t bin = 0xFFFF;
+    if (col_ptr[i + 1] - col_ptr[i] >= thr) {
+      const int32_t s = atomicAdd(hot_n, 1);
+      if (s < kHotBins) {
+        bin = (uint16_t)s;
+        hot_col[s] = (int32_t)i;
+      }
     }
-    return;
-  }
-  for (int64_t p = col_ptr[c] + warp; p < col_ptr[c + 1]; p += nwarps) {
-    const int64_t r = row_idx[p];
-    for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) atomicAdd(&ov[col_idx[e]], 1);
+    hot[i] = bin;
   }
 }
 
+// ov[j] += 1 for every feature j sharing a row with centre c (for a heavy
+// centre: for every row the centre does not hold). Integer counts, so the
+// order of the increments does not matter. hist: kHotBins shared ints.
+// rowmark is read through L2 (another block of the same launch may have
+// written it).
+__device__ __forceinline__ void seed_overlap(int32_t t, int64_t c, int64_t N,
+                                             const int64_t *__restrict__ row_ptr,
+                                             const int32_t *__restrict__ col_idx,
+                                             const int64_t *__restrict__ col_ptr,
+                                             const int32_t *__restrict__ row_idx,
+                                             const int32_t *rowmark,
+                                             const uint16_t *__restrict__ hot,
+                                             const int32_t *__restrict__ hot_col, int32_t nh,
+                                             int32_t *ov, int32_t *hist) {
+  for (int s = threadIdx.x; s < kHotBins; s += blockDim.x) hist[s] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // eight entries per lane at a time: their index and bin loads in flight together
+  auto add_row = [&](int64_t r) {
+    const int64_t e1 = row_ptr[r + 1];
+    for (int64_t e0 = row_ptr[r] + lane; e0 < e1; e0 += 32 * 8) {
+      int32_t j[8];
+      uint16_t bin[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) j[u] = e0 + 32 * u < e1 ? col_idx[e0 + 32 * u] : -1;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) bin[u] = j[u] >= 0 ? hot[j[u]] : (uint16_t)0xFFFF;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (j[u] < 0) continue;
+        if (bin[u] != 0xFFFF)
+          atomicAdd(&hist[bin[u]], 1);
+        else
+          atomicAdd(&ov[j[u]], 1);
+      }
+    }
+  };
+  if (heavy_centre(col_ptr[c + 1] - col_ptr[c], N)) {
+    for (int64_t r = warp; r < N; r += nwarps)
+      if (__ldcg(&rowmark[r]) != t + 1) add_row(r);
+  } else {
+    for (int64_t p = col_ptr[c] + warp; p < col_ptr[c + 1]; p += nwarps) add_row(row_idx[p]);
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < nh; s += blockDim.x) {
+    const int32_t v = hist[s];
+    if (v) atomicAdd(&ov[hot_col[s]], v);
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_seed_overlap(
+    const int32_t *__restrict__ round, const int32_t *__restrict__ centers, int64_t N,
+    const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
+    const int64_t *__restrict__ col_ptr, const int32_t *__restrict__ row_idx,
+    const int32_t *__restrict__ rowmark, const uint16_t *__restrict__ hot,
+    const int32_t *__restrict__ hot_col, const int32_t *__restrict__ hot_n,
+    int32_t *__restrict__ ov) {
+  __shared__ int32_t hist[kHotBins];
+  pdl_wait();
+  const int32_t t = *round;
+  seed_overlap(t, centers[t], N, row_ptr, col_idx, col_ptr, row_idx, rowmark, hot, hot_col,
+               min(*hot_n, kHotBins), ov, hist);
+}
+
 // d2[i] = min(d2[i], n_i + n_c - 2 ov[i]) (plain assignment for the first centre);
-// ov reset; per-tile sums of d2.
-__global__ void k_seed_update(const int32_t *__restrict__ round, int64_t F, int64_t N,
-                              const int32_t *__restrict__ centers,
-                              const int64_t *__restrict__ col_ptr, int32_t *__restrict__ ov,
-                              int64_t *__restrict__ d2, int64_t *__restrict__ tile_sum) {
+// ov reset; tile_sum[tile] = sum of the tile's d2 (tiles of kTile features).
+__device__ __forceinline__ void seed_update_tile(int32_t t, int64_t tile, int64_t F, int64_t nc,
+                                                 bool heavy, const int64_t *__restrict__ col_ptr,
+                                                 int32_t *ov, int64_t *d2, int64_t *tile_sum,
+                                                 int64_t *sm) {
+  int64_t s = 0;
+  const int64_t i = tile * kTile + threadIdx.x;
+  if (i < F) {
+    const int64_t ni = col_ptr[i + 1] - col_ptr[i];
+    const int32_t o = __ldcg(&ov[i]);
+    const int64_t inter = heavy ? ni - (int64_t)o : (int64_t)o;
+    const int64_t dist = ni + nc - 2 * inter;
+    ov[i] = 0;
+    const int64_t v = (t == 0) ? dist : min(d2[i], dist);
+    d2[i] = v;
+    s = v;
+  }
+  s = block_sum_i64(s, sm);
+  if (threadIdx.x == 0) tile_sum[tile] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_seed_update(
+    const int32_t *__restrict__ round, int64_t F, int64_t N, const int32_t *__restrict__ centers,
+    const int64_t *__restrict__ col_ptr, int32_t *__restrict__ ov, int64_t *__restrict__ d2,
+    int64_t *__restrict__ tile_sum) {
   pdl_wait();
   __shared__ int64_t sm[kWarps + 1];
   const int32_t t = *round;
   const int64_t c = centers[t];
   const int64_t nc = col_ptr[c + 1] - col_ptr[c];
-  const bool heavy = heavy_centre(nc, N);
-  int64_t s = 0;
-  for (int u = threadIdx.x; u < kTile; u += kThreads) {
-    const int64_t i = (int64_t)blockIdx.x * kTile + u;
-    if (i < F) {
-      const int64_t ni = col_ptr[i + 1] - col_ptr[i];
-      const int64_t inter = heavy ? ni - (int64_t)ov[i] : (int64_t)ov[i];
-      const int64_t dist = ni + nc - 2 * inter;
-      ov[i] = 0;
-      const int64_t v = (t == 0) ? dist : min(d2[i], dist);
-      d2[i] = v;
-      s += v;
-    }
-  }
-  s = block_sum_i64(s, sm);
-  if (threadIdx.x == 0) tile_sum[blockIdx.x] = s;
+  seed_update_tile(t, blockIdx.x, F, nc, heavy_centre(nc, N), col_ptr, ov, d2, tile_sum, sm);
 }
 
-// Single block: draws centre t = *round + 1 (if t < k), then advances the round.
-__global__ void k_seed_pick(int32_t *round, int32_t k, int64_t F, int64_t ntiles, uint64_t seed,
-                            const int64_t *__restrict__ d2, const int64_t *__restrict__ tile_sum,
-                            int32_t *centers, uint8_t *chosen) {
-  pdl_wait();
-  __shared__ int64_t sm[kWarps + 1];
+// One block: draws centre t (1 <= t < k) from d2 and the tile sums (read
+// through L2: other blocks of the same launch may have written them); stores
+// it in centers[t] and chosen[] and returns it to every thread of the block.
+// Blocks that run it on the same data draw the same centre.
+__device__ int64_t seed_pick(int32_t t, int64_t F, int64_t ntiles, uint64_t seed, const int64_t *d2,
+                             const int64_t *tile_sum, int32_t *centers, uint8_t *chosen,
+                             int64_t *sm) {
   __shared__ int64_t found;
-  const int32_t t = *round + 1;
-  __syncthreads();
-  if (t >= k) {
-    if (threadIdx.x == 0) *round = t;
-    return;
-  }
+  __shared__ int64_t tile_found, tile_base;
   int64_t s = 0;
-  for (int64_t b = threadIdx.x; b < ntiles; b += kThreads) s += tile_sum[b];
+  for (int64_t b = threadIdx.x; b < ntiles; b += kThreads) s += __ldcg(&tile_sum[b]);
   const int64_t total = block_sum_i64(s, sm);
   if (threadIdx.x == 0) found = -1;
   __syncthreads();
@@ -181,7 +255,6 @@ __global__ void k_seed_pick(int32_t *round, int32_t k, int64_t F, int64_t ntiles
     for (int64_t base = 0; base < F; base += kThreads) {
       int64_t i = base + threadIdx.x;
       int64_t cand = (i < F && !chosen[i]) ? i : INT64_MAX;
-      // block min
       for (int o = 16; o > 0; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
       __syncthreads();
       if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = cand;
@@ -198,12 +271,11 @@ __global__ void k_seed_pick(int32_t *round, int32_t k, int64_t F, int64_t ntiles
     int64_t thr = (int64_t)floor(uniform53(seed, t) * (double)total);
     if (thr >= total) thr = total - 1;
     // tile holding the threshold
-    __shared__ int64_t tile_found, tile_base;
     if (threadIdx.x == 0) tile_found = -1;
     int64_t carry = 0;
     for (int64_t b0 = 0; b0 < ntiles; b0 += kThreads) {
       const int64_t b = b0 + threadIdx.x;
-      const int64_t v = b < ntiles ? tile_sum[b] : 0;
+      const int64_t v = b < ntiles ? __ldcg(&tile_sum[b]) : 0;
       int64_t tot;
       const int64_t inc = block_incl_scan_i64(v, sm, &tot);
       if (b < ntiles && carry + inc > thr && carry + inc - v <= thr) {
@@ -219,7 +291,7 @@ __global__ void k_seed_pick(int32_t *round, int32_t k, int64_t F, int64_t ntiles
     int64_t run = tile_base;
     for (int u0 = 0; u0 < kTile; u0 += kThreads) {
       const int64_t i = tb * kTile + u0 + threadIdx.x;
-      const int64_t v = i < F ? d2[i] : 0;
+      const int64_t v = i < F ? __ldcg(&d2[i]) : 0;
       int64_t tot;
       const int64_t inc = block_incl_scan_i64(v, sm, &tot);
       if (i < F && run + inc > thr && run + inc - v <= thr) found = i;
@@ -229,16 +301,104 @@ __global__ void k_seed_pick(int32_t *round, int32_t k, int64_t F, int64_t ntiles
     }
   }
   __syncthreads();
+  const int64_t c = found;
   if (threadIdx.x == 0) {
-    centers[t] = (int32_t)found;
-    if (found >= 0) chosen[found] = 1;
-    *round = t;
+    centers[t] = (int32_t)c;
+    if (c >= 0) chosen[c] = 1;
   }
+  __syncthreads();
+  return c;
 }
 
-__global__ void k_seed_condition(cudaGraphConditionalHandle hc, const int32_t *round, int32_t k) {
+// Single block: draws centre t = *round + 1 (if t < k), then advances the round.
+__global__ void k_seed_pick(int32_t *round, int32_t k, int64_t F, int64_t ntiles, uint64_t seed,
+                            const int64_t *__restrict__ d2, const int64_t *__restrict__ tile_sum,
+                            int32_t *centers, uint8_t *chosen) {
   pdl_wait();
-  if (threadIdx.x == 0) cudaGraphSetConditional(hc, *round < k ? 1u : 0u);
+  __shared__ int64_t sm[kWarps + 1];
+  const int32_t t = *round + 1;
+  __syncthreads();
+  if (t < k) seed_pick(t, F, ntiles, seed, d2, tile_sum, centers, chosen, sm);
+  if (threadIdx.x == 0) *round = t;
+}
+
+// ---- all k rounds in one cooperative launch (every block resident): the
+// same phases per round as the kernels above, separated by grid barriers
+// (two per round, three for a heavy centre): every block draws the next
+// centre itself from the same tile sums and d2 (identical draws), so no
+// barrier waits on the draw. Each barrier wait is bounded: on expiry the
+// block records DEV_TIMEOUT and returns, and every other block returns at its
+// next barrier.
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+};
+constexpr long long kBarSpinLimit = 1LL << 24;   // x >= 64 ns per spin: about a second
+
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ bool grid_barrier(GridBar *bar, int32_t *err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    const unsigned int g = ld_acquire_gpu(&bar->gen);
+    __threadfence();
+    if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (ld_acquire_gpu(&bar->gen) == g) {
+        if (++spins > kBarSpinLimit) {
+          set_dev_error(err, DEV_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    if (ok && atomicAdd(err, 0) != DEV_OK) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__global__ void __launch_bounds__(kThreads) k_seed_all(
+    int64_t N, int64_t F, int32_t k, uint64_t seed, const int64_t *__restrict__ row_ptr,
+    const int32_t *__restrict__ col_idx, const int64_t *__restrict__ col_ptr,
+    const int32_t *__restrict__ row_idx, int32_t *rowmark, const uint16_t *__restrict__ hot,
+    const int32_t *__restrict__ hot_col, const int32_t *__restrict__ hot_n, int32_t *ov,
+    int64_t *d2, int64_t *tile_sum, int64_t ntiles, int32_t *centers, uint8_t *chosen,
+    GridBar *bar, int32_t *err) {
+  __shared__ int32_t hist[kHotBins];
+  __shared__ int64_t sm[kWarps + 1];
+  const int32_t nh = min(*hot_n, kHotBins);
+  int64_t c = __ldcg(&centers[0]);
+  for (int32_t t = 0; t < k; ++t) {
+    if (c < 0) {   // no centre drawn (cannot happen with F >= k): stop like the host form
+      if (threadIdx.x == 0 && blockIdx.x == 0) set_dev_error(err, DEV_BAD_INDEX);
+      return;
+    }
+    const int64_t nc = col_ptr[c + 1] - col_ptr[c];
+    const bool heavy = heavy_centre(nc, N);
+    if (heavy) {
+      seed_mark(t, c, N, col_ptr, row_idx, rowmark);
+      if (!grid_barrier(bar, err)) return;
+    }
+    seed_overlap(t, c, N, row_ptr, col_idx, col_ptr, row_idx, rowmark, hot, hot_col, nh, ov, hist);
+    if (!grid_barrier(bar, err)) return;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+      seed_update_tile(t, tile, F, nc, heavy, col_ptr, ov, d2, tile_sum, sm);
+    if (!grid_barrier(bar, err)) return;
+    if (t + 1 < k) c = seed_pick(t + 1, F, ntiles, seed, d2, tile_sum, centers, chosen, sm);
+  }
 }
 
 __global__ void k_init_labels(int64_t F, int32_t k, const int32_t *__restrict__ centers,
@@ -521,86 +681,58 @@ __global__ void k_lloyd_argmin(int64_t F, int32_t k, const int32_t *__restrict__
 
 // The k rounds run as one CUDA graph: a conditional while node whose body is
 // one round (overlaps with the newest centre, distance update, next draw).
+// use_coop: all k rounds in one cooperative launch (k_seed_all); otherwise the
+// same rounds issued from the host as four kernels each. Identical results.
 rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                         const int64_t *col_ptr, const int32_t *row_idx, int32_t k, uint64_t seed,
-                        KmeansBuffers &b, cudaStream_t st, bool use_graph) {
+                        KmeansBuffers &b, int32_t *err, cudaStream_t st, bool use_coop) {
   const int64_t ntiles = (F + kTile - 1) / kTile;
   uint8_t *chosen = reinterpret_cast<uint8_t *>(b.next);   // F bytes of the (unused yet) next[]
   RR_CUDA(cudaMemsetAsync(chosen, 0, F, st));
   RR_CUDA(cudaMemsetAsync(b.ov, 0, sizeof(int32_t) * F, st));
   RR_CUDA(cudaMemsetAsync(b.dcount, 0, sizeof(int32_t) * N, st));   // row stamps of heavy centres
-  RR_LAUNCH_PDL(k_first_center, 1, 32, 0, st, F, seed, b.centers, chosen, b.round);
-  if (!use_graph) {
-    // the same k rounds as the graph's while loop, issued from the host
-    for (int32_t t = 0; t < k; ++t) {
-      RR_LAUNCH_PDL(k_seed_mark, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, col_ptr, row_idx,
-                b.dcount);
-      RR_LAUNCH_PDL(k_seed_overlap, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, row_ptr,
-                col_idx, col_ptr, row_idx, b.dcount, b.ov);
-      RR_LAUNCH_PDL(k_seed_update, (unsigned)ntiles, kThreads, 0, st, b.round, F, N, b.centers,
-                col_ptr, b.ov, b.d2, b.part_i);
-      RR_LAUNCH_PDL(k_seed_pick, 1, kThreads, 0, st, b.round, k, F, ntiles, seed, b.d2, b.part_i,
-                b.centers, chosen);
-    }
+  RR_CUDA(cudaMemsetAsync(b.hot_n, 0, sizeof(int32_t), st));
+  RR_LAUNCH(k_hot_assign, grid_for(F, kThreads), kThreads, 0, st, F, N, col_ptr, b.hot, b.hot_col,
+            b.hot_n);
+  RR_LAUNCH(k_first_center, 1, 32, 0, st, F, seed, b.centers, chosen, b.round);
+  int grid = 0;
+  if (use_coop) {
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    RR_CUDA(cudaGetDevice(&dev));
+    RR_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    RR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed_all, kThreads, 0));
+    if (coop) grid = sms * std::min(per_sm, 2);
+  }
+  if (grid > 0) {
+    RR_CUDA(cudaMemsetAsync(b.bar, 0, sizeof(GridBar), st));
+    GridBar *bar = reinterpret_cast<GridBar *>(b.bar);
+    int32_t *rowmark = b.dcount;
+    void *args[] = {(void *)&N,       (void *)&F,       (void *)&k,       (void *)&seed,
+                    (void *)&row_ptr, (void *)&col_idx, (void *)&col_ptr, (void *)&row_idx,
+                    (void *)&rowmark, (void *)&b.hot,   (void *)&b.hot_col, (void *)&b.hot_n,
+                    (void *)&b.ov,    (void *)&b.d2,    (void *)&b.part_i, (void *)&ntiles,
+                    (void *)&b.centers, (void *)&chosen, (void *)&bar,    (void *)&err};
+    RR_CUDA(cudaLaunchCooperativeKernel((const void *)k_seed_all, grid, kThreads, args, 0, st));
+    ++rr_launch_counter;
     RR_CUDA(cudaStreamSynchronize(st));
     return RR_OK;
   }
-
-  cudaGraph_t g = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  cudaStream_t cs = nullptr;
-  rr_status s = RR_OK;
-  auto build = [&]() -> rr_status {
-    RR_CUDA(cudaGraphCreate(&g, 0));
-    cudaGraphConditionalHandle hc;
-    RR_CUDA(cudaGraphConditionalHandleCreate(&hc, g, 1, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams cp{};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = hc;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    RR_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
-    RR_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-    RR_CUDA(cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeThreadLocal));
-    auto body = [&]() -> rr_status {
-      RR_LAUNCH_PDL(k_seed_mark, kSMs * 2, kThreads, 0, cs, b.round, b.centers, N, col_ptr, row_idx,
-                b.dcount);
-      RR_LAUNCH_PDL(k_seed_overlap, kSMs * 2, kThreads, 0, cs, b.round, b.centers, N, row_ptr,
-                col_idx, col_ptr, row_idx, b.dcount, b.ov);
-      RR_LAUNCH_PDL(k_seed_update, (unsigned)ntiles, kThreads, 0, cs, b.round, F, N, b.centers,
-                col_ptr, b.ov, b.d2, b.part_i);
-      RR_LAUNCH_PDL(k_seed_pick, 1, kThreads, 0, cs, b.round, k, F, ntiles, seed, b.d2, b.part_i,
-                b.centers, chosen);
-      RR_LAUNCH_PDL(k_seed_condition, 1, 32, 0, cs, hc, b.round, k);
-      return RR_OK;
-    };
-    const int64_t l0 = rr_launch_counter;
-    rr_status bs = body();
-    rr_launch_counter = l0;
-    cudaGraph_t cap = nullptr;
-    const cudaError_t ec = cudaStreamEndCapture(cs, &cap);
-    if (bs != RR_OK || ec != cudaSuccess) {
-      cudaGraphDestroy(g);
-      g = nullptr;
-      cudaGetLastError();
-      if (bs != RR_OK) return bs;
-      rr_set_error("seeding graph capture failed: %s", cudaGetErrorString(ec));
-      return RR_CUDA_ERROR;
-    }
-    RR_CUDA(cudaGraphInstantiate(&exec, g, 0));
-    RR_CUDA(cudaGraphLaunch(exec, st));
-    rr_launch_counter += 5LL * k;   // the body ran k times
-    RR_CUDA(cudaStreamSynchronize(st));
-    return RR_OK;
-  };
-  s = build();
-  if (exec) cudaGraphExecDestroy(exec);
-  if (g) cudaGraphDestroy(g);
-  if (cs) cudaStreamDestroy(cs);
-  return s;
+  for (int32_t t = 0; t < k; ++t) {
+    RR_LAUNCH_PDL(k_seed_mark, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, col_ptr, row_idx,
+                  b.dcount);
+    RR_LAUNCH_PDL(k_seed_overlap, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, row_ptr,
+                  col_idx, col_ptr, row_idx, b.dcount, b.hot, b.hot_col, b.hot_n, b.ov);
+    RR_LAUNCH_PDL(k_seed_update, (unsigned)ntiles, kThreads, 0, st, b.round, F, N, b.centers,
+                  col_ptr, b.ov, b.d2, b.part_i);
+    RR_LAUNCH_PDL(k_seed_pick, 1, kThreads, 0, st, b.round, k, F, ntiles, seed, b.d2, b.part_i,
+                  b.centers, chosen);
+  }
+  RR_CUDA(cudaStreamSynchronize(st));
+  return RR_OK;
 }
+
+int64_t kmeans_seed_tiles(int64_t F) { return (F + kTile - 1) / kTile; }
 
 rr_status kmeans_init_labels(int64_t F, int32_t k, KmeansBuffers &b, cudaStream_t st) {
   RR_LAUNCH(k_init_labels, grid_for(F, kThreads), kThreads, 0, st, F, k, b.centers, b.prev);

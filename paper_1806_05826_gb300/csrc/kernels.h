@@ -36,7 +36,7 @@ struct KmeansBuffers {
   int64_t *d2;         // [F]   seeding squared distances
   int32_t *ov;         // [F]   overlaps with the newest centre
   double *part;        // [kMaxGrid] per-block D^2 sums (exact integers in FP64 range)
-  int64_t *part_i;     // [kMaxGrid]
+  int64_t *part_i;     // [kmeans_seed_tiles(F) + 1]
   int32_t *centers;    // [k]
   int32_t *labels;     // [F]   current labels (-1: not assigned yet)
   int32_t *prev;       // [F]   labels of the previous step
@@ -54,11 +54,20 @@ struct KmeansBuffers {
   int32_t *work_ctr;   // [1]
   int32_t *order;      // [F] features by descending work (heaviest first)
   int32_t *round;      // [1] seeding round (device-side loop counter)
+  uint16_t *hot;       // [F] shared-histogram bin of a frequent feature (0xFFFF: none)
+  int32_t *hot_col;    // [2048] feature of each bin
+  int32_t *hot_n;      // [1] bins in use (capped at 2048 when read)
+  unsigned int *bar;   // [2] grid barrier of the cooperative seeding kernel
 };
+// K-means++ seeding (k centres into b.centers). use_coop: one cooperative
+// launch for all rounds (bounded grid barriers; DEV_TIMEOUT in *err on expiry);
+// else host-issued rounds. Synchronises the stream.
 rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                         const int64_t *col_ptr, const int32_t *row_idx, int32_t k, uint64_t seed,
-                        KmeansBuffers &b, cudaStream_t st, bool use_graph);
+                        KmeansBuffers &b, int32_t *err, cudaStream_t st, bool use_coop);
 // labels <- -1 except labels[centers[S]] = S; prev <- -1; D <- 0.
+// tiles of features of the seeding pass (tile sums in part_i)
+int64_t kmeans_seed_tiles(int64_t F);
 rr_status kmeans_init_labels(int64_t F, int32_t k, KmeansBuffers &b, cudaStream_t st);
 // One Lloyd assignment step; on return (stream synchronised) *changes_host holds
 // the number of labels that changed.

@@ -363,7 +363,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(phase(1));
   // ---- k-means++ seeding and Lloyd steps (Section 3.4)
   rr::KmeansBuffers kb{};
-  const int64_t ntiles = (F + 1023) / 1024;
+  const int64_t ntiles = rr::kmeans_seed_tiles(F);
   RR_TRY(m.alloc(&kb.d2, F));
   RR_TRY(m.alloc(&kb.ov, F));
   RR_TRY(m.alloc(&kb.part_i, ntiles + 1));
@@ -387,6 +387,10 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&kb.work_ctr, 1));
   RR_TRY(m.alloc(&kb.order, F));
   RR_TRY(m.alloc(&kb.round, 1));
+  RR_TRY(m.alloc(&kb.hot, F));
+  RR_TRY(m.alloc(&kb.hot_col, 2048));
+  RR_TRY(m.alloc(&kb.hot_n, 1));
+  RR_TRY(m.alloc(&kb.bar, 2));
   if (h->opt.init_centers) {
     std::vector<char> seen(F, 0);
     for (int32_t s = 0; s < k; ++s) {
@@ -401,7 +405,8 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
                             cudaMemcpyHostToDevice, st));
   } else {
     RR_TRY(rr::kmeanspp_seed(N, F, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx, k,
-                             h->opt.seed, kb, st, h->opt.use_graphs != 0));
+                             h->opt.seed, kb, h->err, st, h->opt.use_graphs != 0));
+    RR_TRY(check_dev_error(h, "k-means++ seeding"));
   }
   RR_TRY(phase(2));
   RR_TRY(rr::kmeans_init_labels(F, k, kb, st));
@@ -431,6 +436,10 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   m.release(kb.d2);
   m.release(kb.ov);
   m.release(kb.Q);
+  m.release(kb.hot);
+  m.release(kb.hot_col);
+  m.release(kb.hot_n);
+  m.release(kb.bar);
 
   RR_TRY(phase(3));
   // ---- compaction, member lists, prolongation scale

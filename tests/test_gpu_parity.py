@@ -265,9 +265,9 @@ def test_repeatable_bits(case, rr):
 
 
 def test_graph_loop_equals_host_loop(case, rr):
-    """The device-side while-loop graphs (seeding and PCG) and host-issued
-    loops run the same kernels in the same order: identical centres, labels,
-    bits and iteration counts."""
+    """The one-launch cooperative seeding and the device-side while-loop
+    graphs of PCG against host-issued loops of the same phases in the same
+    order: identical centres, labels, bits and iteration counts."""
     X = case["X"]
     h2 = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, case["lam"], case["k"],
                      seed=case["seed"], use_graphs=0, check_every=5)
@@ -416,3 +416,20 @@ def test_kmeanspp_heavy_centres_bit_exact(rr, seed):
     for use_graphs in (1, 0):
         h = rr.rr_setup(rp, ci, N, F, 0.1, k, seed=seed, use_graphs=use_graphs)
         assert np.array_equal(rr.rr_get_centers(h, k), want)
+
+
+@pytest.mark.parametrize("use_graphs", [1, 0])
+def test_kmeanspp_frequent_feature_bins_bit_exact(rr, use_graphs):
+    """Seeding counts the overlaps of frequent features (at least 64 rows)
+    in per-block shared bins, at most 2048 of them; here 3000 features
+    qualify, so 952 take the global counters instead. Centres equal the
+    oracle's."""
+    rng = np.random.default_rng(7)
+    N, F = 300, 3000
+    D = (rng.random((N, F)) < rng.uniform(0.22, 0.6, F)[None, :]).astype(np.int8)
+    rp, ci = csr_of(D)
+    cp, ri = osp.csc_pattern(N, F, rp, ci)
+    k = 25
+    want = okm.kmeanspp_binary(N, F, rp, ci, cp, ri, k, 3)
+    h = rr.rr_setup(rp, ci, N, F, 0.1, k, seed=3, use_graphs=use_graphs)
+    assert np.array_equal(rr.rr_get_centers(h, k), want)
