@@ -236,13 +236,14 @@ __global__ void __launch_bounds__(kThreads) k_seed_update(
   seed_update_tile(t, blockIdx.x, F, nc, heavy_centre(nc, N), col_ptr, ov, d2, tile_sum, sm);
 }
 
-// One block: draws centre t (1 <= t < k) from d2 and the tile sums (read
-// through L2: other blocks of the same launch may have written them); stores
-// it in centers[t] and chosen[] and returns it to every thread of the block.
-// Blocks that run it on the same data draw the same centre.
+// One block: draws centre t (1 <= t < k) from d2, the tile sums and chosen[]
+// (read through L2: other blocks of the same launch may have written them);
+// stores it in centers[t] (and chosen[] if mark_chosen) and returns it to
+// every thread of the block. Blocks that run it on the same data draw the
+// same centre.
 __device__ int64_t seed_pick(int32_t t, int64_t F, int64_t ntiles, uint64_t seed, const int64_t *d2,
                              const int64_t *tile_sum, int32_t *centers, uint8_t *chosen,
-                             int64_t *sm) {
+                             bool mark_chosen, int64_t *sm) {
   __shared__ int64_t found;
   __shared__ int64_t tile_found, tile_base;
   int64_t s = 0;
@@ -254,7 +255,7 @@ __device__ int64_t seed_pick(int32_t t, int64_t F, int64_t ntiles, uint64_t seed
     // every remaining distance is zero: lowest index not chosen yet
     for (int64_t base = 0; base < F; base += kThreads) {
       int64_t i = base + threadIdx.x;
-      int64_t cand = (i < F && !chosen[i]) ? i : INT64_MAX;
+      int64_t cand = (i < F && !__ldcg(&chosen[i])) ? i : INT64_MAX;
       for (int o = 16; o > 0; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
       __syncthreads();
       if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = cand;
@@ -304,7 +305,7 @@ __device__ int64_t seed_pick(int32_t t, int64_t F, int64_t ntiles, uint64_t seed
   const int64_t c = found;
   if (threadIdx.x == 0) {
     centers[t] = (int32_t)c;
-    if (c >= 0) chosen[c] = 1;
+    if (c >= 0 && mark_chosen) chosen[c] = 1;
   }
   __syncthreads();
   return c;
@@ -318,7 +319,7 @@ __global__ void k_seed_pick(int32_t *round, int32_t k, int64_t F, int64_t ntiles
   __shared__ int64_t sm[kWarps + 1];
   const int32_t t = *round + 1;
   __syncthreads();
-  if (t < k) seed_pick(t, F, ntiles, seed, d2, tile_sum, centers, chosen, sm);
+  if (t < k) seed_pick(t, F, ntiles, seed, d2, tile_sum, centers, chosen, true, sm);
   if (threadIdx.x == 0) *round = t;
 }
 
@@ -394,10 +395,14 @@ __global__ void __launch_bounds__(kThreads) k_seed_all(
     }
     seed_overlap(t, c, N, row_ptr, col_idx, col_ptr, row_idx, rowmark, hot, hot_col, nh, ov, hist);
     if (!grid_barrier(bar, err)) return;
+    // chosen[] gains centre t between this round's two barriers: every block
+    // has finished the previous draw, and none starts the next one before the
+    // second barrier, so no block writes chosen[] while another reads it
+    if (t > 0 && threadIdx.x == 0) chosen[c] = 1;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
       seed_update_tile(t, tile, F, nc, heavy, col_ptr, ov, d2, tile_sum, sm);
     if (!grid_barrier(bar, err)) return;
-    if (t + 1 < k) c = seed_pick(t + 1, F, ntiles, seed, d2, tile_sum, centers, chosen, sm);
+    if (t + 1 < k) c = seed_pick(t + 1, F, ntiles, seed, d2, tile_sum, centers, chosen, false, sm);
   }
 }
 
@@ -462,6 +467,41 @@ __global__ void k_bucket_scatter(int64_t F, const int64_t *__restrict__ work,
 // histogram over clusters, the pairs of all rows of its column. Exact integer
 // arithmetic: the result equals a full recomputation.
 
+// (cluster, delta) entries of the row delta lists: int2, or 32 bits (cluster
+// in the low 16, delta as int16 in the high 16) when k < 65535 and no row has
+// more than 32767 entries, so that every |delta| fits. The packed form halves
+// the bytes the pull re-reads.
+template <bool P> struct DeltaEntry;
+template <> struct DeltaEntry<false> {
+  using T = int2;
+  __device__ static T make(int32_t s, int32_t d) { return make_int2(s, d); }
+  __device__ static T none() { return make_int2(-1, 0); }
+  __device__ static int32_t cluster(T e) { return e.x; }
+  __device__ static int32_t delta(T e) { return e.y; }
+};
+template <> struct DeltaEntry<true> {
+  using T = uint32_t;
+  __device__ static T make(int32_t s, int32_t d) {
+    return (uint32_t)(uint16_t)s | ((uint32_t)(uint16_t)(int16_t)d << 16);
+  }
+  __device__ static T none() { return 0xFFFFFFFFu; }
+  __device__ static int32_t cluster(T e) {
+    const int32_t s = (int32_t)(e & 0xFFFFu);
+    return s == 0xFFFF ? -1 : s;
+  }
+  __device__ static int32_t delta(T e) { return (int32_t)(int16_t)(e >> 16); }
+};
+
+__global__ void k_max_row(int64_t N, const int64_t *__restrict__ row_ptr,
+                          unsigned long long *__restrict__ mx) {
+  unsigned long long m = 0;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < N;
+       r += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (unsigned long long)(row_ptr[r + 1] - row_ptr[r]));
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(mx, m);
+}
+
 // per row: number of entries whose feature moved
 __global__ void k_moved_count(int64_t N, const int64_t *__restrict__ row_ptr,
                               const int32_t *__restrict__ col_idx, const int32_t *__restrict__ prev,
@@ -471,9 +511,13 @@ __global__ void k_moved_count(int64_t N, const int64_t *__restrict__ row_ptr,
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = warp; r < N; r += nwarps) {
     int c = 0;
-    for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) {
-      const int32_t j = col_idx[e];
-      c += prev[j] != cur[j];
+    const int64_t e1 = row_ptr[r + 1];
+    for (int64_t e0 = row_ptr[r] + lane; e0 < e1; e0 += 32 * 8) {
+      int32_t j[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) j[u] = e0 + 32 * u < e1 ? col_idx[e0 + 32 * u] : -1;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) c += j[u] >= 0 && prev[j[u]] != cur[j[u]];
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if (lane == 0) cnt[r] = 2 * (int64_t)c;   // room for one (new) and one (old) pair each
@@ -487,11 +531,13 @@ __global__ void k_moved_count(int64_t N, const int64_t *__restrict__ row_ptr,
 // cluster; then each nonzero bin is claimed once (atomicExch back to zero,
 // which also leaves the histogram clean for the next row).
 // *work += sum over rows of rownnz_r * |list_r| (the cost of applying them).
+template <bool P>
 __global__ void k_row_delta(int64_t N, int32_t k, const int64_t *__restrict__ row_ptr,
                             const int32_t *__restrict__ col_idx, const int32_t *__restrict__ prev,
                             const int32_t *__restrict__ cur, const int64_t *__restrict__ dptr,
-                            int2 *__restrict__ dlist, int32_t *__restrict__ dcount,
-                            unsigned long long *__restrict__ work) {
+                            typename DeltaEntry<P>::T *__restrict__ dlist,
+                            int32_t *__restrict__ dcount, unsigned long long *__restrict__ work) {
+  using E = DeltaEntry<P>;
   extern __shared__ int32_t hist_all[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   int32_t *hist = hist_all + (int64_t)wib * k;
@@ -506,6 +552,42 @@ __global__ void k_row_delta(int64_t N, int32_t k, const int64_t *__restrict__ ro
       if (lane == 0) dcount[r] = 0;
       continue;
     }
+    int64_t out = dptr[r];
+    if (e1 - b <= 32 * 8) {
+      // the whole row in registers: eight entries per lane, loads in flight together
+      int32_t o[8], n[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t e = b + lane + 32 * u;
+        const int32_t j = e < e1 ? col_idx[e] : -1;
+        o[u] = j >= 0 ? prev[j] : -1;
+        n[u] = j >= 0 ? cur[j] : -1;
+        if (o[u] == n[u]) o[u] = n[u] = -1;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (n[u] >= 0) {
+          atomicAdd(&hist[n[u]], 1);
+          if (o[u] >= 0) atomicSub(&hist[o[u]], 1);
+        }
+      __syncwarp();
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int32_t vn = n[u] >= 0 ? atomicExch(&hist[n[u]], 0) : 0;
+        const unsigned mn = __ballot_sync(0xffffffffu, vn != 0);
+        if (vn != 0) dlist[out + __popc(mn & ((1u << lane) - 1u))] = E::make(n[u], vn);
+        out += __popc(mn);
+        const int32_t vo = o[u] >= 0 ? atomicExch(&hist[o[u]], 0) : 0;
+        const unsigned mo = __ballot_sync(0xffffffffu, vo != 0);
+        if (vo != 0) dlist[out + __popc(mo & ((1u << lane) - 1u))] = E::make(o[u], vo);
+        out += __popc(mo);
+      }
+      __syncwarp();
+      const int32_t cnt = (int32_t)(out - dptr[r]);
+      if (lane == 0) dcount[r] = cnt;
+      my_work += (unsigned long long)(e1 - b) * (unsigned long long)cnt;
+      continue;
+    }
     for (int64_t e = b + lane; e < e1; e += 32) {
       const int32_t j = col_idx[e];
       const int32_t o = prev[j], n = cur[j];
@@ -515,7 +597,6 @@ __global__ void k_row_delta(int64_t N, int32_t k, const int64_t *__restrict__ ro
       }
     }
     __syncwarp();
-    int64_t out = dptr[r];
     for (int64_t e0 = b; e0 < e1; e0 += 32) {
       const int64_t e = e0 + lane;
       int32_t o = -1, n = -1;
@@ -527,11 +608,11 @@ __global__ void k_row_delta(int64_t N, int32_t k, const int64_t *__restrict__ ro
       }
       const int32_t vn = n >= 0 ? atomicExch(&hist[n], 0) : 0;
       const unsigned mn = __ballot_sync(0xffffffffu, vn != 0);
-      if (vn != 0) dlist[out + __popc(mn & ((1u << lane) - 1u))] = make_int2(n, vn);
+      if (vn != 0) dlist[out + __popc(mn & ((1u << lane) - 1u))] = E::make(n, vn);
       out += __popc(mn);
       const int32_t vo = o >= 0 ? atomicExch(&hist[o], 0) : 0;
       const unsigned mo = __ballot_sync(0xffffffffu, vo != 0);
-      if (vo != 0) dlist[out + __popc(mo & ((1u << lane) - 1u))] = make_int2(o, vo);
+      if (vo != 0) dlist[out + __popc(mo & ((1u << lane) - 1u))] = E::make(o, vo);
       out += __popc(mo);
     }
     __syncwarp();
@@ -543,14 +624,24 @@ __global__ void k_row_delta(int64_t N, int32_t k, const int64_t *__restrict__ ro
 }
 
 // Pull: D[i, .] += sum over the rows of column i of their delta lists.
-// Persistent blocks take features heaviest-first from a shared counter; each
-// block gathers into a shared histogram (distinct clusters within a row, so no
-// two lanes of one instruction hit the same bin).
+// Tasks are chunks of at most kPullRows rows of one column, features
+// heaviest first (task_ptr / task_it built once per setup); persistent blocks
+// take tasks from a shared counter and gather into a shared histogram
+// (distinct clusters within a row, so no two lanes of one instruction hit the
+// same bin). A column cut into several chunks adds its sums with integer
+// atomics (exact, so the order does not matter); a one-chunk column is the
+// only writer of its D row.
+constexpr int64_t kPullRows = 1024;
+
+template <bool P>
 __global__ void __launch_bounds__(kThreads) k_lloyd_pull(
-    int64_t F, int32_t k, const int64_t *__restrict__ col_ptr, const int32_t *__restrict__ row_idx,
+    int32_t k, const int64_t *__restrict__ col_ptr, const int32_t *__restrict__ row_idx,
     const int64_t *__restrict__ dptr, const int32_t *__restrict__ dcount,
-    const int2 *__restrict__ dlist, const int32_t *__restrict__ order, int32_t *work_ctr,
-    int32_t *__restrict__ D) {
+    const typename DeltaEntry<P>::T *__restrict__ dlist, const int32_t *__restrict__ order,
+    const int64_t *__restrict__ task_ptr, const int32_t *__restrict__ task_it, int64_t n_tasks,
+    int32_t *work_ctr, int32_t *__restrict__ D) {
+  using E = DeltaEntry<P>;
+  using T = typename E::T;
   extern __shared__ int32_t acc[];
   __shared__ int32_t cur;
   __shared__ int32_t touched;
@@ -562,19 +653,41 @@ __global__ void __launch_bounds__(kThreads) k_lloyd_pull(
     }
     for (int s = threadIdx.x; s < k; s += kThreads) acc[s] = 0;
     __syncthreads();
-    const int32_t it = cur;
-    if (it >= F) break;
+    const int64_t t = cur;
+    if (t >= n_tasks) break;
+    const int32_t it = task_it[t];
     const int64_t i = order[it];
+    const int64_t chunk = t - task_ptr[it];
+    const bool shared_row = task_ptr[it + 1] - task_ptr[it] > 1;
+    const int64_t pb = col_ptr[i] + chunk * kPullRows;
+    const int64_t p1 = min(col_ptr[i + 1], pb + kPullRows);
     int any = 0;
-    for (int64_t p = col_ptr[i] + warp; p < col_ptr[i + 1]; p += kWarps) {
-      const int64_t r = row_idx[p];
-      const int32_t c = dcount[r];
-      if (c == 0) continue;
-      any = 1;
-      const int2 *lst = dlist + dptr[r];
-      for (int32_t q = lane; q < c; q += 32) {
-        const int2 pr = lst[q];
-        atomicAdd(&acc[pr.x], pr.y);
+    // two rows per warp at a time, eight list entries per lane at a time: the
+    // loads of a batch are in flight together before its shared atomics
+    for (int64_t p = pb + warp; p < p1; p += 2 * kWarps) {
+      int32_t c[2];
+      const T *lst[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t ph = p + h * kWarps;
+        const int64_t r = ph < p1 ? row_idx[ph] : -1;
+        c[h] = r >= 0 ? dcount[r] : 0;
+        lst[h] = dlist + (r >= 0 ? dptr[r] : 0);
+      }
+      if (c[0] | c[1]) any = 1;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        for (int32_t q0 = lane; q0 < c[h]; q0 += 32 * 8) {
+          T pr[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            pr[u] = q0 + 32 * u < c[h] ? lst[h][q0 + 32 * u] : E::none();
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int32_t sc = E::cluster(pr[u]);
+            if (sc >= 0) atomicAdd(&acc[sc], E::delta(pr[u]));
+          }
+        }
       }
     }
     if (any) touched = 1;   // benign race: every writer stores 1
@@ -583,32 +696,58 @@ __global__ void __launch_bounds__(kThreads) k_lloyd_pull(
       int32_t *Di = D + i * (int64_t)k;
       for (int s = threadIdx.x; s < k; s += kThreads) {
         const int32_t a = acc[s];
-        if (a) Di[s] += a;
+        if (a) {
+          if (shared_row)
+            atomicAdd(&Di[s], a);
+          else
+            Di[s] += a;
+        }
       }
     }
     __syncthreads();
   }
 }
 
+// task_ptr[it] = first pull task of the it-th feature in work order
+// (ceil(n_i / kPullRows) tasks each, at least one); task_it[t] = it.
+__global__ void k_task_count(int64_t F, const int32_t *__restrict__ order,
+                             const int64_t *__restrict__ col_ptr, int64_t *__restrict__ cnt) {
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < F;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = order[it];
+    const int64_t n = col_ptr[i + 1] - col_ptr[i];
+    cnt[it] = n <= kPullRows ? 1 : (n + kPullRows - 1) / kPullRows;
+  }
+}
+__global__ void k_task_fill(int64_t F, const int64_t *__restrict__ task_ptr,
+                            int32_t *__restrict__ task_it) {
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < F;
+       it += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t t = task_ptr[it]; t < task_ptr[it + 1]; ++t) task_it[t] = (int32_t)it;
+}
+
 // Push: for every row with a delta list, D[i, S] += delta for each feature i of
 // the row and each (S, delta) of the list (global atomics; used when few
 // labels moved, so only a few rows carry work).
+template <bool P>
 __global__ void k_lloyd_push(int64_t N, int32_t k, const int64_t *__restrict__ row_ptr,
                              const int32_t *__restrict__ col_idx, const int64_t *__restrict__ dptr,
-                             const int32_t *__restrict__ dcount, const int2 *__restrict__ dlist,
+                             const int32_t *__restrict__ dcount,
+                             const typename DeltaEntry<P>::T *__restrict__ dlist,
                              int32_t *__restrict__ D) {
+  using E = DeltaEntry<P>;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = warp; r < N; r += nwarps) {
     const int32_t c = dcount[r];
     if (c == 0) continue;
-    const int2 *lst = dlist + dptr[r];
+    const typename E::T *lst = dlist + dptr[r];
     for (int64_t e = row_ptr[r] + lane; e < row_ptr[r + 1]; e += 32) {
       int32_t *Di = D + (int64_t)col_idx[e] * k;
       for (int32_t q = 0; q < c; ++q) {
-        const int2 pr = lst[q];
-        atomicAdd(&Di[pr.x], pr.y);
+        const typename E::T pr = lst[q];
+        atomicAdd(&Di[E::cluster(pr)], E::delta(pr));
       }
     }
   }
@@ -734,6 +873,8 @@ rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int3
 
 int64_t kmeans_seed_tiles(int64_t F) { return (F + kTile - 1) / kTile; }
 
+int64_t kmeans_pull_tasks_max(int64_t F, int64_t nnz) { return F + nnz / kPullRows + 1; }
+
 rr_status kmeans_init_labels(int64_t F, int32_t k, KmeansBuffers &b, cudaStream_t st) {
   RR_LAUNCH(k_init_labels, grid_for(F, kThreads), kThreads, 0, st, F, k, b.centers, b.prev);
   RR_LAUNCH(k_init_labels, grid_for(F, kThreads), kThreads, 0, st, F, k, b.centers, b.labels);
@@ -742,9 +883,9 @@ rr_status kmeans_init_labels(int64_t F, int32_t k, KmeansBuffers &b, cudaStream_
   return RR_OK;
 }
 
-rr_status kmeans_work_order(int64_t F, const int64_t *row_ptr, const int64_t *col_ptr,
-                            const int32_t *row_idx, KmeansBuffers &b, int64_t *work,
-                            int64_t *scratch, cudaStream_t st) {
+rr_status kmeans_work_order(int64_t N, int64_t F, int32_t k, const int64_t *row_ptr,
+                            const int64_t *col_ptr, const int32_t *row_idx, KmeansBuffers &b,
+                            int64_t *work, int64_t *scratch, cudaStream_t st) {
   // scratch: >= 2 * kBuckets + 1 + scan scratch int64
   int64_t *cnt = scratch;
   int64_t *offs = cnt + kBuckets;              // kBuckets + 1
@@ -757,6 +898,55 @@ rr_status kmeans_work_order(int64_t F, const int64_t *row_ptr, const int64_t *co
   RR_TRY(scan_exclusive(cnt, offs, kBuckets, sscr, st));
   RR_LAUNCH(k_bucket_scatter, grid_for(F, kThreads), kThreads, 0, st, F, work,
             (unsigned long long *)offs, b.order);
+  // pull tasks (chunks of kPullRows rows per feature, in work order)
+  int64_t *tcnt = reinterpret_cast<int64_t *>(b.dlist);   // >= F int64 (dlist is rewritten per step)
+  RR_LAUNCH(k_task_count, grid_for(F, kThreads), kThreads, 0, st, F, b.order, col_ptr, tcnt);
+  RR_TRY(scan_exclusive(tcnt, b.task_ptr, F, sscr, st));
+  RR_CUDA(cudaMemcpyAsync(&b.n_tasks, b.task_ptr + F, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  RR_LAUNCH(k_task_fill, grid_for(F, kThreads), kThreads, 0, st, F, b.task_ptr, b.task_it);
+  // the packed delta-list form needs every |delta| <= 32767 (rows of <= 32767 entries)
+  RR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t), st));
+  RR_LAUNCH(k_max_row, grid_for(N, kThreads), kThreads, 0, st, N, row_ptr,
+            (unsigned long long *)cnt);
+  int64_t mx = 0;
+  RR_CUDA(cudaMemcpyAsync(&mx, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  b.packed = (mx <= 32767 && k < 65535) ? 1 : 0;
+  return RR_OK;
+}
+
+// Delta lists of the rows (prev -> labels), then D += delta: pull per feature
+// when much changed, push per row otherwise.
+template <bool P>
+rr_status lloyd_delta_apply(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
+                            const int64_t *col_ptr, const int32_t *row_idx, int32_t k,
+                            KmeansBuffers &b, cudaStream_t st) {
+  using T = typename DeltaEntry<P>::T;
+  T *dlist = reinterpret_cast<T *>(b.dlist);
+  const int warps_per_cta = (int)std::max<int64_t>(1, std::min<int64_t>(kWarps, (96 * 1024) / (4 * (int64_t)k)));
+  const size_t hsmem = sizeof(int32_t) * (size_t)k * warps_per_cta;
+  RR_CUDA(cudaFuncSetAttribute(k_row_delta<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
+  RR_LAUNCH(k_row_delta<P>, std::min<int64_t>((N + warps_per_cta - 1) / warps_per_cta, kSMs * 16),
+            32 * warps_per_cta, hsmem, st, N, k, row_ptr, col_idx, b.prev, b.labels, b.mptr,
+            dlist, b.dcount, (unsigned long long *)b.work);
+  unsigned long long work = 0;
+  RR_CUDA(cudaMemcpyAsync(&work, b.work, sizeof(work), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  if (work > kPushWorkLimit) {
+    RR_CUDA(cudaMemsetAsync(b.work_ctr, 0, sizeof(int32_t), st));
+    const size_t smem = sizeof(int32_t) * (size_t)k;
+    RR_CUDA(cudaFuncSetAttribute(k_lloyd_pull<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)std::max<size_t>(smem, 1)));
+    int per_sm = 0;
+    RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lloyd_pull<P>, kThreads, smem));
+    RR_LAUNCH(k_lloyd_pull<P>, kSMs * std::max(1, per_sm), kThreads, smem, st, k, col_ptr,
+              row_idx, b.mptr, b.dcount, dlist, b.order, b.task_ptr, b.task_it, b.n_tasks,
+              b.work_ctr, b.D);
+  } else if (work > 0) {
+    RR_LAUNCH(k_lloyd_push<P>, grid_for(N, kWarps), kThreads, 0, st, N, k, row_ptr, col_idx,
+              b.mptr, b.dcount, dlist, b.D);
+  }
   return RR_OK;
 }
 
@@ -768,29 +958,10 @@ rr_status kmeans_lloyd_step(int64_t N, int64_t F, const int64_t *row_ptr, const 
             b.labels, b.mcount);
   RR_TRY(scan_exclusive(b.mcount, b.mptr, N, b.scan_scratch, st));
   RR_CUDA(cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), st));
-  const int warps_per_cta = (int)std::max<int64_t>(1, std::min<int64_t>(kWarps, (96 * 1024) / (4 * (int64_t)k)));
-  const size_t hsmem = sizeof(int32_t) * (size_t)k * warps_per_cta;
-  RR_CUDA(cudaFuncSetAttribute(k_row_delta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
-  RR_LAUNCH(k_row_delta, std::min<int64_t>((N + warps_per_cta - 1) / warps_per_cta, kSMs * 16),
-            32 * warps_per_cta, hsmem, st, N, k, row_ptr, col_idx, b.prev, b.labels, b.mptr,
-            b.dlist, b.dcount, (unsigned long long *)b.work);
-  unsigned long long work = 0;
-  RR_CUDA(cudaMemcpyAsync(&work, b.work, sizeof(work), cudaMemcpyDeviceToHost, st));
-  RR_CUDA(cudaStreamSynchronize(st));
-  // (2) D += delta: pull per feature when much changed, push per row otherwise
-  if (work > kPushWorkLimit) {
-    RR_CUDA(cudaMemsetAsync(b.work_ctr, 0, sizeof(int32_t), st));
-    const size_t smem = sizeof(int32_t) * (size_t)k;
-    RR_CUDA(cudaFuncSetAttribute(k_lloyd_pull, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)std::max<size_t>(smem, 1)));
-    int per_sm = 0;
-    RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lloyd_pull, kThreads, smem));
-    RR_LAUNCH(k_lloyd_pull, kSMs * std::max(1, per_sm), kThreads, smem, st, F, k, col_ptr, row_idx,
-              b.mptr, b.dcount, b.dlist, b.order, b.work_ctr, b.D);
-  } else if (work > 0) {
-    RR_LAUNCH(k_lloyd_push, grid_for(N, kWarps), kThreads, 0, st, N, k, row_ptr, col_idx, b.mptr,
-              b.dcount, b.dlist, b.D);
-  }
+  if (b.packed)
+    RR_TRY(lloyd_delta_apply<true>(N, F, row_ptr, col_idx, col_ptr, row_idx, k, b, st));
+  else
+    RR_TRY(lloyd_delta_apply<false>(N, F, row_ptr, col_idx, col_ptr, row_idx, k, b, st));
   // (3) sizes and Q from the updated D
   RR_CUDA(cudaMemsetAsync(b.n_S, 0, sizeof(int64_t) * k, st));
   RR_CUDA(cudaMemsetAsync(b.Q, 0, sizeof(int64_t) * k, st));

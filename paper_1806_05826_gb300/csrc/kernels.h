@@ -43,7 +43,7 @@ struct KmeansBuffers {
   int32_t *next;       // [F]
   int64_t *mcount;     // [N]   room for each row's delta list (2 x moved entries)
   int64_t *mptr;       // [N+1] start of each row's delta list
-  int2 *dlist;         // [2 nnz] (cluster, delta) pairs of the rows' count changes
+  int2 *dlist;         // [max(2 nnz, F) + 1] (cluster, delta) pairs of the rows' count changes
   int32_t *dcount;     // [N]   length of each row's delta list
   int64_t *work;       // [1]   total cost of applying the delta lists
   int64_t *scan_scratch;
@@ -58,7 +58,13 @@ struct KmeansBuffers {
   int32_t *hot_col;    // [2048] feature of each bin
   int32_t *hot_n;      // [1] bins in use (capped at 2048 when read)
   unsigned int *bar;   // [2] grid barrier of the cooperative seeding kernel
+  int32_t packed;      // host: delta lists in the 32-bit form (set by kmeans_work_order)
+  int64_t *task_ptr;   // [F+1] first pull task of each feature in work order
+  int32_t *task_it;    // [kmeans_pull_tasks_max(F, nnz)] feature (work-order index) of each task
+  int64_t n_tasks;     // host: number of pull tasks (set by kmeans_work_order)
 };
+// upper bound of the pull tasks: one per feature plus one per 1024 entries
+int64_t kmeans_pull_tasks_max(int64_t F, int64_t nnz);
 // K-means++ seeding (k centres into b.centers). use_coop: one cooperative
 // launch for all rounds (bounded grid barriers; DEV_TIMEOUT in *err on expiry);
 // else host-issued rounds. Synchronises the stream.
@@ -77,9 +83,9 @@ rr_status kmeans_lloyd_step(int64_t N, int64_t F, const int64_t *row_ptr, const 
 // order[] = features by descending work_i = sum of the row lengths of column i
 // (heaviest first); work[] receives work_i, which is also the Gershgorin row
 // sum of X^T X for binary X.
-rr_status kmeans_work_order(int64_t F, const int64_t *row_ptr, const int64_t *col_ptr,
-                            const int32_t *row_idx, KmeansBuffers &b, int64_t *work,
-                            int64_t *scratch, cudaStream_t st);
+rr_status kmeans_work_order(int64_t N, int64_t F, int32_t k, const int64_t *row_ptr,
+                            const int64_t *col_ptr, const int32_t *row_idx, KmeansBuffers &b,
+                            int64_t *work, int64_t *scratch, cudaStream_t st);
 
 // ---- k_coarse.cu --------------------------------------------------------
 // Compacts labels in place to 0..k_eff-1 (order kept); n_S compacted too.

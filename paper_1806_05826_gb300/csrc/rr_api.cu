@@ -375,7 +375,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&kb.prev, F));
   RR_TRY(m.alloc(&kb.mcount, N));
   RR_TRY(m.alloc(&kb.mptr, N + 1));
-  RR_TRY(m.alloc(&kb.dlist, 2 * std::max<int64_t>(nnz, 1)));
+  RR_TRY(m.alloc(&kb.dlist, std::max<int64_t>(2 * nnz, F) + 1));
   RR_TRY(m.alloc(&kb.dcount, N));
   RR_TRY(m.alloc(&kb.work, 1));
   RR_TRY(m.alloc(&kb.scan_scratch, rr::scan_scratch_len(N) + 8));
@@ -391,6 +391,8 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&kb.hot_col, 2048));
   RR_TRY(m.alloc(&kb.hot_n, 1));
   RR_TRY(m.alloc(&kb.bar, 2));
+  RR_TRY(m.alloc(&kb.task_ptr, F + 1));
+  RR_TRY(m.alloc(&kb.task_it, rr::kmeans_pull_tasks_max(F, nnz)));
   if (h->opt.init_centers) {
     std::vector<char> seen(F, 0);
     for (int32_t s = 0; s < k; ++s) {
@@ -411,7 +413,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(phase(2));
   RR_TRY(rr::kmeans_init_labels(F, k, kb, st));
   RR_TRY(m.alloc(&h->gsum, F));
-  RR_TRY(rr::kmeans_work_order(F, h->row_ptr, h->col_ptr, h->row_idx, kb, h->gsum, scratch64, st));
+  RR_TRY(rr::kmeans_work_order(N, F, k, h->row_ptr, h->col_ptr, h->row_idx, kb, h->gsum, scratch64, st));
   int64_t *changes_host = nullptr;
   RR_CUDA(cudaMallocHost(&changes_host, sizeof(int64_t)));
   int32_t it = 0;
@@ -440,6 +442,8 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   m.release(kb.hot_col);
   m.release(kb.hot_n);
   m.release(kb.bar);
+  m.release(kb.task_ptr);
+  m.release(kb.task_it);
 
   RR_TRY(phase(3));
   // ---- compaction, member lists, prolongation scale

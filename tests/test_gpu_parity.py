@@ -433,3 +433,27 @@ def test_kmeanspp_frequent_feature_bins_bit_exact(rr, use_graphs):
     want = okm.kmeanspp_binary(N, F, rp, ci, cp, ri, k, 3)
     h = rr.rr_setup(rp, ci, N, F, 0.1, k, seed=3, use_graphs=use_graphs)
     assert np.array_equal(rr.rr_get_centers(h, k), want)
+
+
+def test_lloyd_rows_longer_than_32767_take_wide_delta_lists(rr):
+    """Lloyd's per-row (cluster, delta) lists are packed into 32 bits only when
+    every row has at most 32767 entries (so every |delta| fits in 16 bits);
+    a row holding all 32,800 features here selects the 64-bit lists. The other
+    rows split into 8 groups, each holding (with probability 0.5) the features
+    of one block of 4,100, and Lloyd starts from one centre per block, so the
+    clusters stay within the per-row count limit of the coarse level. Labels
+    after two assignment steps equal the oracle's (whose plain definition
+    costs the square of the long row's length per step)."""
+    rng = np.random.default_rng(12)
+    N, F, nb = 161, 32800, 8
+    D = np.zeros((N, F), np.int8)
+    for g in range(nb):
+        D[20 * g:20 * g + 20, 4100 * g:4100 * g + 4100] = rng.random((20, 4100)) < 0.5
+    D[N - 1] = 1
+    rp, ci = csr_of(D)
+    centers = (4100 * np.arange(nb) + 7).astype(np.int32)
+    cp, ri = osp.csc_pattern(N, F, rp, ci)
+    lab, _ = okm.lloyd_binary(N, F, rp, ci, cp, ri, centers, 2)
+    lab, _ = okm.compact(lab)
+    h = rr.rr_setup(rp, ci, N, F, 0.1, nb, init_centers=centers, kmeans_max_iter=2)
+    assert np.array_equal(rr.rr_get_labels(h), lab)
