@@ -54,7 +54,7 @@ def parse():
                     help="host-issued loops instead of CUDA graphs (every kernel visible to a profiler)")
     ap.add_argument("--gather", default="auto", choices=["auto", "lanes", "staged"],
                     help="FP32 gather kernel (auto: timed per pass at setup; the others force one)")
-    ap.add_argument("--only", choices=["batched", "many", "learned"],
+    ap.add_argument("--only", choices=["batched", "many", "learned", "dense"],
                     help="run one extra section alone and print it (profiling runs)")
     ap.add_argument("--batch-targets", type=int, default=64,
                     help="targets of the batched section (64 in the workload definition)")
@@ -258,6 +258,45 @@ def measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world, n_targ
             "note": "plain = setup + systems x mean single-solve time of target 0 at the 8 weights"}
 
 
+def measure_dense_apply(rr, h, n, f, dev, stream, reps=20):
+    """The dense operator apply X^T X v + lambda v on a dense handle, in the
+    handle's precision (the one the CG iterations use): X is read once (4 n f
+    bytes) plus v and the result (16 f bytes); X (800 MB at 50,000 x 4,000) is
+    larger than L2."""
+    import torch
+    v = torch.randn(f, dtype=torch.float64, device=dev)
+    o = torch.empty_like(v)
+    for _ in range(3):
+        rr.rr_apply(h, v, o)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize(dev)
+    ev[0].record(stream)
+    for _ in range(reps):
+        rr.rr_apply(h, v, o)
+    ev[1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = ev[0].elapsed_time(ev[1]) / reps
+    alg = 4 * n * f + 16 * f
+    return {"n": n, "d": f, "ms": round(ms, 4), "algorithmic_bytes": alg,
+            "achieved_gbs": round(alg / ms / 1e6, 1)}
+
+
+def measure_dense_only(rr, dev, stream, opts):
+    """One dense problem of the many-problem workload (50,000 x 4,000 AR(1),
+    rho = 0.9, seed 12, k = 40): setup, then the dense operator apply."""
+    import torch
+    from gen import synth
+    p = synth.MANY_WORKLOADS["uneven_12_dense4"]
+    n, f = p["dense"]
+    X = synth.dense_ar1(n, f, p["rho"], p["n_problems"])
+    o = {key: v for key, v in opts.items() if key not in ("gram", "gather", "seed")}
+    h = rr.rr_setup_dense(torch.as_tensor(X, device=dev), p["lam"], max(2, f // 100),
+                          seed=p["n_problems"], **o)
+    out = measure_dense_apply(rr, h, n, f, dev, stream)
+    rr.rr_free(h)
+    return out
+
+
 def measure_many(rr, dev, stream, opts):
     """Independent problems of uneven sizes: rr_solve_many (all PCG loops in one
     graph) against rr_solve one problem after the other, same handles (setups
@@ -297,31 +336,11 @@ def measure_many(rr, dev, stream, opts):
     t_many, t_seq = e[0].elapsed_time(e[1]) / 1e3, e[2].elapsed_time(e[3]) / 1e3
     sizes = [(X.shape[0], X.shape[1], X.size) if p.get("dense") else (X.n_rows, X.n_cols, X.nnz)
              for X, _, p in probs]
-    # the dense operator apply X^T X v + lambda v on the first dense problem, in
-    # the handle's precision (the one the CG iterations use): X is read once
-    # (N F 4 bytes) plus v and the result (16 F bytes)
     dense_apply = None
     for h, (X, _, p) in zip(hs, probs):
-        if not p.get("dense"):
-            continue
-        n, f = X.shape
-        v = torch.randn(f, dtype=torch.float64, device=dev)
-        o = torch.empty_like(v)
-        for _ in range(3):
-            rr.rr_apply(h, v, o)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-        torch.cuda.synchronize(dev)
-        ev[0].record(stream)
-        reps = 20
-        for _ in range(reps):
-            rr.rr_apply(h, v, o)
-        ev[1].record(stream)
-        torch.cuda.synchronize(dev)
-        ms = ev[0].elapsed_time(ev[1]) / reps
-        alg = 4 * n * f + 16 * f
-        dense_apply = {"n": n, "d": f, "ms": round(ms, 4), "algorithmic_bytes": alg,
-                       "achieved_gbs": round(alg / ms / 1e6, 1)}
-        break
+        if p.get("dense"):
+            dense_apply = measure_dense_apply(rr, h, X.shape[0], X.shape[1], dev, stream)
+            break
     for h in hs:
         rr.rr_free(h)
     return {"workload": name, "problems": len(probs), "value": round(t_many, 4), "unit": "s",
@@ -422,9 +441,13 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream(dev)
+    if args.only == "dense":
+        prec = rr.RR_PREC_MIXED if args.precision == "mixed" else rr.RR_PREC_FP64
+        return {"dense_apply": measure_dense_only(rr, dev, stream,
+                                                  dict(stream=stream, precision=prec))}
     X, y, _, p = synth.workload(args.workload)
     N, F, nnz, k, lams = X.n_rows, X.n_cols, X.nnz, p["k"], p["lambdas"]
-    stream = torch.cuda.current_stream(dev)
     row_ptr = torch.as_tensor(X.row_ptr, device=dev)
     col_idx = torch.as_tensor(X.col_idx, device=dev)
     y_dev = torch.as_tensor(y, device=dev)
