@@ -6,6 +6,8 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -223,8 +225,12 @@ __global__ void k_chol_diag(int32_t k, int32_t j0, double *__restrict__ L, int32
   if (threadIdx.x == 0 && bad) set_dev_error(err, DEV_NOT_SPD);
 }
 
-// Rows below the diagonal block: L21 = A21 L11^{-T}, one thread per row.
-__global__ void k_chol_panel(int32_t k, int32_t j0, double *__restrict__ L) {
+// Rows below the diagonal block: L21 = A21 L11^{-T}, one thread per row,
+// kPanelThreads rows per block (the rows spread over many SMs: each row's
+// solve is a chain of FP64 operations).
+constexpr int kPanelThreads = 32;
+__global__ void __launch_bounds__(kPanelThreads) k_chol_panel(int32_t k, int32_t j0,
+                                                              double *__restrict__ L) {
   __shared__ double l11[kNB][kNB + 1];
   const int nb = min(kNB, k - j0);
   for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
@@ -280,13 +286,19 @@ __global__ void k_chol_update(int32_t k, int32_t j0, double *__restrict__ L) {
 }
 
 // LinvT[j][i] = (L^{-1})[i][j] for i >= j: one warp per column j, forward
-// substitution with warp-parallel dot products.
-__global__ void k_tri_inverse(int32_t k, const double *__restrict__ L, double *__restrict__ LinvT) {
-  const int lane = threadIdx.x & 31;
+// substitution with warp-parallel dot products. The column being built sits in
+// shared memory (dynamic, one row of k doubles per warp of the block), so each
+// step waits on a shared-memory round trip only; written out at the end.
+constexpr int kTriWarps = 4;
+__global__ void __launch_bounds__(32 * kTriWarps) k_tri_inverse(int32_t k,
+                                                                const double *__restrict__ L,
+                                                                double *__restrict__ LinvT) {
+  extern __shared__ double xs_all[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double *x = xs_all + (int64_t)wib * k;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t j = warp; j < k; j += nwarps) {
-    double *x = LinvT + j * k;
     for (int64_t i = j; i < k; ++i) {
       const double *Li = L + i * k;
       double s = 0.0;
@@ -295,6 +307,9 @@ __global__ void k_tri_inverse(int32_t k, const double *__restrict__ L, double *_
       if (lane == 0) x[i] = ((i == j ? 1.0 : 0.0) - s) / Li[i];
       __syncwarp();
     }
+    double *out = LinvT + j * k;
+    for (int64_t i = j + lane; i < k; i += 32) out[i] = x[i];
+    __syncwarp();
   }
 }
 
@@ -398,7 +413,8 @@ rr_status cholesky(int32_t k, double *L, int32_t *err, cudaStream_t st) {
     RR_LAUNCH(k_chol_diag, 1, kThreads, 0, st, k, j0, L, err);
     const int32_t rest = k - j0 - std::min(kNB, k - j0);
     if (rest > 0) {
-      RR_LAUNCH(k_chol_panel, grid_for(rest, kThreads), kThreads, 0, st, k, j0, L);
+      RR_LAUNCH(k_chol_panel, (unsigned)((rest + kPanelThreads - 1) / kPanelThreads), kPanelThreads,
+                0, st, k, j0, L);
       const int64_t nt = (rest + 31) / 32;
       RR_LAUNCH(k_chol_update, tri_tiles(nt), kThreads, 0, st, k, j0, L);
     }
@@ -408,7 +424,12 @@ rr_status cholesky(int32_t k, double *L, int32_t *err, cudaStream_t st) {
 
 rr_status chol_inverse(int32_t k, const double *L, double *Linv, double *Ainv, cudaStream_t st) {
   RR_CUDA(cudaMemsetAsync(Linv, 0, sizeof(double) * (size_t)k * k, st));
-  RR_LAUNCH(k_tri_inverse, grid_for(k, kWarps), kThreads, 0, st, k, L, Linv);
+  // warps per block: as many as their columns fit in 200 KB of shared memory (k <= 16384: >= 1)
+  const int tw = (int)std::max<int64_t>(1, std::min<int64_t>(kTriWarps, (200 * 1024) / (8 * (int64_t)k)));
+  const size_t tsmem = sizeof(double) * (size_t)tw * k;
+  RR_CUDA(cudaFuncSetAttribute(k_tri_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               200 * 1024));
+  RR_LAUNCH(k_tri_inverse, (unsigned)((k + tw - 1) / tw), 32 * tw, tsmem, st, k, L, Linv);
   const int64_t nt = (k + 31) / 32;
   RR_LAUNCH(k_inverse_product, tri_tiles(nt), kThreads, 0, st, k, Linv, Ainv);
   return RR_OK;
