@@ -59,6 +59,20 @@ __global__ void k_coarse_matvec(int32_t k, const double *__restrict__ Ainv,
     // four row loads in flight per lane; the four partial sums are added in a fixed order
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     int t = lane;
+    // eight row loads in flight per lane (issued before the products)
+    for (; t + 224 < k; t += 256) {
+      double r8[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) r8[u] = row[t + 32 * u];
+      a0 += r8[0] * rcs[t];
+      a1 += r8[1] * rcs[t + 32];
+      a2 += r8[2] * rcs[t + 64];
+      a3 += r8[3] * rcs[t + 96];
+      a0 += r8[4] * rcs[t + 128];
+      a1 += r8[5] * rcs[t + 160];
+      a2 += r8[6] * rcs[t + 192];
+      a3 += r8[7] * rcs[t + 224];
+    }
     for (; t + 96 < k; t += 128) {
       a0 += row[t] * rcs[t];
       a1 += row[t + 32] * rcs[t + 32];

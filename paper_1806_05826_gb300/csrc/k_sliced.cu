@@ -520,29 +520,30 @@ __global__ void __launch_bounds__(kThreads) k_sliced_epilogue(int64_t F, const i
     double s = warp_sum(s0 + s1);
     if (lane == 0) epilogue(ep, i, s, dot);
   }
-  // two features per 8-lane group at a time (feature i0 + gw and i0 + 4 + gw):
+  // four features per 8-lane group at a time (features i0 + 4h + gw, h < 4):
   // their slot loads are in flight together
-  for (int64_t i0 = warp * 8; i0 < F; i0 += nwarps * 8) {   // warp-uniform loop
-    int64_t ii[2];
-    int32_t q0[2], q1[2];
-    bool light[2];
+  constexpr int kH = 4;
+  for (int64_t i0 = warp * 4 * kH; i0 < F; i0 += nwarps * 4 * kH) {   // warp-uniform loop
+    int64_t ii[kH];
+    int32_t q0[kH], q1[kH];
+    bool light[kH];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < kH; ++h) {
       ii[h] = i0 + 4 * h + gw;
       q0[h] = ii[h] < F ? slot_ptr[ii[h]] : 0;
       q1[h] = ii[h] < F ? slot_ptr[ii[h] + 1] : 0;
       light[h] = ii[h] < F && q1[h] - q0[h] <= kLightSlots;
     }
-    double v[2][4];
+    double v[kH][4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+    for (int h = 0; h < kH; ++h)
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int32_t q = q0[h] + lane8 + 8 * u;
         v[h][u] = light[h] && q < q1[h] ? psum[q] : 0.0;
       }
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < kH; ++h) {
       double s = (v[h][0] + v[h][1]) + (v[h][2] + v[h][3]);
       s += __shfl_xor_sync(0xffffffffu, s, 4);
       s += __shfl_xor_sync(0xffffffffu, s, 2);
