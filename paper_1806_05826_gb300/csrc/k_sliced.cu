@@ -475,6 +475,70 @@ __global__ void k_chunk_fill(int32_t ntasks, const int32_t *__restrict__ task_p,
   }
 }
 
+// Reorders the 8 offsets inside index words so that the staged gather's reads
+// spread over the shared-memory banks. In that kernel the 32 lanes of a warp
+// read position u of 32 consecutive words of a chunk at the same time; here one
+// warp takes such a group of 32 words and, for u = 0..7 in turn, lets the lanes
+// pick (one after the other) the remaining offset of their word whose bank
+// (offset mod 32) has been picked least often at this position, padding
+// entries (offset W, one shared address) costing nothing. A word's 8 values
+// are the same in any order, so this changes only the order of the FP32 sums
+// inside a word (both gather kernels read the same words, so they keep giving
+// identical bits).
+constexpr int kBalThreads = 64;
+__global__ void __launch_bounds__(kBalThreads) k_balance_words(int64_t n_chunks,
+                                                               const int32_t *__restrict__ chunk_w,
+                                                               int32_t W, uint4 *__restrict__ idx) {
+  // thread-private rows (padded so that the threads' rows start in different banks)
+  __shared__ uint16_t outs[kBalThreads][32 * 8 + 2];
+  __shared__ uint8_t usedm[kBalThreads][36];
+  __shared__ uint8_t cnts[kBalThreads][36];
+  const int t = threadIdx.x;
+  constexpr int kGroups = kChunkWords / 32;
+  const uint16_t padv = (uint16_t)W;
+  for (int64_t g = (int64_t)blockIdx.x * kBalThreads + t; g < n_chunks * kGroups;
+       g += (int64_t)gridDim.x * kBalThreads) {
+    const int64_t c = g / kGroups;
+    const int64_t w0 = (int64_t)chunk_w[c] + 32 * (g % kGroups), w1 = chunk_w[c + 1];
+    if (w0 >= w1) continue;
+    const int n = (int)min((int64_t)32, w1 - w0);
+    for (int l = 0; l < n; ++l) usedm[t][l] = 0;
+    for (int u = 0; u < 8; ++u) {
+      for (int bk = 0; bk < 32; ++bk) cnts[t][bk] = 0;
+      for (int l = 0; l < n; ++l) {
+        const uint4 q = idx[w0 + l];
+        const uint16_t off[8] = {(uint16_t)(q.x & 0xffffu), (uint16_t)(q.x >> 16),
+                                 (uint16_t)(q.y & 0xffffu), (uint16_t)(q.y >> 16),
+                                 (uint16_t)(q.z & 0xffffu), (uint16_t)(q.z >> 16),
+                                 (uint16_t)(q.w & 0xffffu), (uint16_t)(q.w >> 16)};
+        const uint32_t used = usedm[t][l];
+        int best = 0, best_cost = 0x7fffffff;
+        uint16_t bo = padv;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (used & (1u << j)) continue;
+          const int cost = off[j] == padv ? -1 : (int)cnts[t][off[j] & 31];
+          if (cost < best_cost) {
+            best_cost = cost;
+            best = j;
+            bo = off[j];
+          }
+        }
+        usedm[t][l] = (uint8_t)(used | (1u << best));
+        outs[t][l * 8 + u] = bo;
+        if (bo != padv) cnts[t][bo & 31] += 1;
+      }
+    }
+    for (int l = 0; l < n; ++l) {
+      const uint16_t *o = &outs[t][l * 8];
+      idx[w0 + l] = make_uint4((uint32_t)o[0] | ((uint32_t)o[1] << 16),
+                               (uint32_t)o[2] | ((uint32_t)o[3] << 16),
+                               (uint32_t)o[4] | ((uint32_t)o[5] << 16),
+                               (uint32_t)o[6] | ((uint32_t)o[7] << 16));
+    }
+  }
+}
+
 // Sum of the slots of every outer index -> out[o] (u = X v on its own).
 __global__ void k_slot_sum(int64_t n, const int32_t *__restrict__ slot_ptr,
                            const double *__restrict__ psum, double *__restrict__ out) {
@@ -705,6 +769,9 @@ rr_status sliced_build(int64_t n_outer, int64_t n_inner, const int64_t *outer_pt
         RR_CUDA(cudaMalloc(&P.task_c, sizeof(int32_t) * (P.ntasks + 1)));
         RR_LAUNCH(k_chunk_fill, grid_for(P.ntasks, kThreads), kThreads, 0, st, P.ntasks, P.task_p,
                   P.pw, coff, P.chunk_p, P.chunk_w, P.task_c, nch, (int32_t)P.npieces);
+        RR_LAUNCH(k_balance_words,
+                  (unsigned)std::max<int64_t>(1, std::min<int64_t>((nch * (kChunkWords / 32) + kBalThreads - 1) / kBalThreads, 1 << 20)),
+                  kBalThreads, 0, st, nch, P.chunk_w, P.W, P.idx);
         RR_CUDA(cudaStreamSynchronize(st));
         return RR_OK;
       };
