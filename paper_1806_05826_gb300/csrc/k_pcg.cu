@@ -108,22 +108,26 @@ __global__ void k_i64_to_i32(int64_t n, const int64_t *__restrict__ in, int32_t 
     out[i] = (int32_t)in[i];
 }
 
+// z2 = z1 + P e_c (and, if z2_32, its FP32 copy for the next operator apply).
 __global__ void k_prolong_add(int64_t F, const int32_t *__restrict__ labels,
                               const double *__restrict__ s, const double *__restrict__ ec,
                               const double *__restrict__ z1, double *__restrict__ z2,
-                              const int32_t *__restrict__ stop) {
+                              float *__restrict__ z2_32, const int32_t *__restrict__ stop) {
   pdl_wait();
   if (stop && *stop) return;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t l = labels[i];
-    z2[i] = z1[i] + s[l] * ec[l];
+    const double v = z1[i] + s[l] * ec[l];
+    z2[i] = v;
+    if (z2_32) z2_32[i] = (float)v;
   }
 }
 
 __global__ void k_jacobi(int64_t F, double omega, const double *__restrict__ r,
                          const double *__restrict__ d, double *__restrict__ z,
-                         double *__restrict__ rz_part, const int32_t *__restrict__ stop) {
+                         float *__restrict__ z32, double *__restrict__ rz_part,
+                         const int32_t *__restrict__ stop) {
   pdl_wait();
   if (stop && *stop) return;
   __shared__ double sm[kWarps + 1];
@@ -132,6 +136,7 @@ __global__ void k_jacobi(int64_t F, double omega, const double *__restrict__ r,
        i += (int64_t)gridDim.x * blockDim.x) {
     const double zi = d ? omega * r[i] / d[i] : r[i];
     z[i] = zi;
+    if (z32) z32[i] = (float)zi;
     dot += r[i] * zi;
   }
   if (rz_part) {
@@ -142,15 +147,18 @@ __global__ void k_jacobi(int64_t F, double omega, const double *__restrict__ r,
 
 __global__ void k_pcg_direction(int64_t F, const double *__restrict__ rz_part, int n_rz,
                                 const double *__restrict__ z, double *__restrict__ p,
-                                const PcgScalars *__restrict__ S) {
+                                float *__restrict__ p32, const PcgScalars *__restrict__ S) {
   pdl_wait();
   if (S->converged) return;
   __shared__ double sm[kWarps + 1];
   const double rho = sum_partials(rz_part, n_rz, sm);
   const double beta = S->first ? 0.0 : rho / S->rho_old;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F;
-       i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = S->first ? z[i] : z[i] + beta * p[i];
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = S->first ? z[i] : z[i] + beta * p[i];
+    p[i] = v;
+    if (p32) p32[i] = (float)v;
+  }
 }
 
 __global__ void k_pcg_update(int64_t F, const double *__restrict__ rz_part, int n_rz,
@@ -158,7 +166,8 @@ __global__ void k_pcg_update(int64_t F, const double *__restrict__ rz_part, int 
                              const double *__restrict__ p, const double *__restrict__ q,
                              double *__restrict__ w, double *__restrict__ r, double omega,
                              const double *__restrict__ d, double *__restrict__ z1,
-                             double *__restrict__ rr_part, const PcgScalars *__restrict__ S) {
+                             float *__restrict__ z1_32, double *__restrict__ rr_part,
+                             const PcgScalars *__restrict__ S) {
   pdl_wait();
   if (S->converged) return;
   __shared__ double sm[kWarps + 1];
@@ -172,7 +181,11 @@ __global__ void k_pcg_update(int64_t F, const double *__restrict__ rz_part, int 
     const double ri = r[i] - alpha * q[i];
     r[i] = ri;
     acc += ri * ri;
-    if (z1) z1[i] = omega * ri / d[i];
+    if (z1) {
+      const double zi = omega * ri / d[i];
+      z1[i] = zi;
+      if (z1_32) z1_32[i] = (float)zi;
+    }
   }
   const double tot = block_sum(acc, sm);
   if (threadIdx.x == 0) rr_part[blockIdx.x] = tot;
@@ -309,29 +322,30 @@ rr_status coarse_matvec(int32_t k, const double *Ainv, const RestrictPlan &plan,
 }
 
 rr_status prolong_add(int64_t F, const int32_t *labels, const double *s, const double *ec,
-                      const double *z1, double *z2, const int32_t *stop, cudaStream_t st) {
-  RR_LAUNCH_PDL(k_prolong_add, kVecGrid, kThreads, 0, st, F, labels, s, ec, z1, z2, stop);
+                      const double *z1, double *z2, const int32_t *stop, cudaStream_t st,
+                      float *z2_32) {
+  RR_LAUNCH_PDL(k_prolong_add, kVecGrid, kThreads, 0, st, F, labels, s, ec, z1, z2, z2_32, stop);
   return RR_OK;
 }
 
 rr_status jacobi(int64_t F, double omega, const double *r, const double *d, double *z,
-                 double *rz_part, const int32_t *stop, cudaStream_t st) {
-  RR_LAUNCH_PDL(k_jacobi, kVecGrid, kThreads, 0, st, F, omega, r, d, z, rz_part, stop);
+                 double *rz_part, const int32_t *stop, cudaStream_t st, float *z32) {
+  RR_LAUNCH_PDL(k_jacobi, kVecGrid, kThreads, 0, st, F, omega, r, d, z, z32, rz_part, stop);
   return RR_OK;
 }
 
 rr_status pcg_direction(int64_t F, const double *rz_part, int n_rz, const double *z, double *p,
-                        PcgScalars *S, cudaStream_t st) {
-  RR_LAUNCH_PDL(k_pcg_direction, kVecGrid, kThreads, 0, st, F, rz_part, n_rz, z, p, S);
+                        PcgScalars *S, cudaStream_t st, float *p32) {
+  RR_LAUNCH_PDL(k_pcg_direction, kVecGrid, kThreads, 0, st, F, rz_part, n_rz, z, p, p32, S);
   return RR_OK;
 }
 
 rr_status pcg_update(int64_t F, const double *rz_part, int n_rz, const double *pq_part, int n_pq,
                      const double *p, const double *q, double *w, double *r, double omega,
                      const double *d, double *z1, double *rr_part, PcgScalars *S,
-                     cudaStream_t st) {
+                     cudaStream_t st, float *z1_32) {
   RR_LAUNCH_PDL(k_pcg_update, kVecGrid, kThreads, 0, st, F, rz_part, n_rz, pq_part, n_pq, p, q, w, r,
-            omega, d, z1, rr_part, S);
+            omega, d, z1, z1_32, rr_part, S);
   return RR_OK;
 }
 

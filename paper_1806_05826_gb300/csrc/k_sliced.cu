@@ -650,10 +650,12 @@ rr_status set_smem_attr() {
 
 template <typename T>
 rr_status gather_t(const SlicedPattern &P, const double *x, const SlicedPattern *in,
-                   const int32_t *stop, cudaStream_t st) {
+                   const int32_t *stop, cudaStream_t st, bool xq_ready) {
   const int64_t n = P.n_inner;
   T *xq = reinterpret_cast<T *>(P.xq);
-  if (in)
+  if (xq_ready && !in) {
+    // the vector's producer already wrote its copy in T into P.xq
+  } else if (in)
     RR_LAUNCH_PDL((k_slice_prep<true, T>), grid_for(n, kThreads), kThreads, 0, st, n, nullptr,
               in->psum, in->slot_ptr, xq, stop);
   else
@@ -806,8 +808,9 @@ void sliced_free(SlicedPattern &P) {
 }
 
 rr_status sliced_gather(const SlicedPattern &P, const double *x, const SlicedPattern *in,
-                        const int32_t *stop, cudaStream_t st, bool fp32) {
-  return fp32 ? gather_t<float>(P, x, in, stop, st) : gather_t<double>(P, x, in, stop, st);
+                        const int32_t *stop, cudaStream_t st, bool fp32, bool x32_ready) {
+  return fp32 ? gather_t<float>(P, x, in, stop, st, x32_ready)
+              : gather_t<double>(P, x, in, stop, st, false);
 }
 
 rr_status sliced_choose_gather(SlicedPattern &P, int32_t mode, cudaStream_t st) {

@@ -219,9 +219,11 @@ rr_status sliced_build(int64_t n_outer, int64_t n_inner, const int64_t *outer_pt
 void sliced_free(SlicedPattern &P);
 // piece sums of P against x (or, when `in` is given, against the per-index
 // sums of in's slots: the output of a previous pass); fp32: accumulate in FP32
-// (the mixed-precision inner iterations), else in FP64.
+// (the mixed-precision inner iterations), else in FP64. x32_ready (fp32 only):
+// the FP32 copy of x is already in P.xq (written by the kernel that made x).
 rr_status sliced_gather(const SlicedPattern &P, const double *x, const SlicedPattern *in,
-                        const int32_t *stop, cudaStream_t st, bool fp32 = false);
+                        const int32_t *stop, cudaStream_t st, bool fp32 = false,
+                        bool x32_ready = false);
 // out[o] = sum of the slots of outer index o.
 rr_status sliced_slot_sum(const SlicedPattern &P, double *out, cudaStream_t st);
 // Chooses P.staged: mode RR_GATHER_LANES / RR_GATHER_STAGED, or (RR_GATHER_AUTO)
@@ -266,21 +268,23 @@ rr_status restrict_clusters(const RestrictPlan &plan, const int32_t *members, co
 rr_status coarse_matvec(int32_t k, const double *Ainv, const RestrictPlan &plan, const double *s,
                         double *rc, double *ec, const int32_t *stop, cudaStream_t st);
 // z2 = z1 + s[l(i)] e_c[l(i)].
+// z2_32 (optional): also the FP32 copy of z2 (for an operator apply with x32_ready).
 rr_status prolong_add(int64_t F, const int32_t *labels, const double *s, const double *ec,
-                      const double *z1, double *z2, const int32_t *stop, cudaStream_t st);
+                      const double *z1, double *z2, const int32_t *stop, cudaStream_t st,
+                      float *z2_32 = nullptr);
 // z = omega * r / d; if rz_part: per-block <r, z> into rz_part[0..kVecGrid).
 // d == nullptr means z = r (no preconditioner).
 rr_status jacobi(int64_t F, double omega, const double *r, const double *d, double *z,
-                 double *rz_part, const int32_t *stop, cudaStream_t st);
+                 double *rz_part, const int32_t *stop, cudaStream_t st, float *z32 = nullptr);
 // rho = <r,z> (from n_rz partials); beta = rho / rho_old (0 on a (re)start); p = z + beta p.
 rr_status pcg_direction(int64_t F, const double *rz_part, int n_rz, const double *z, double *p,
-                        PcgScalars *S, cudaStream_t st);
+                        PcgScalars *S, cudaStream_t st, float *p32 = nullptr);
 // alpha = rho / <p,q>; w += alpha p; r -= alpha q; partial ||r||^2;
 // z1 = omega r / d when z1 != nullptr.
 rr_status pcg_update(int64_t F, const double *rz_part, int n_rz, const double *pq_part, int n_pq,
                      const double *p, const double *q, double *w, double *r, double omega,
                      const double *d, double *z1, double *rr_part, PcgScalars *S,
-                     cudaStream_t st);
+                     cudaStream_t st, float *z1_32 = nullptr);
 // rr = sum(rr_part); rho_old = sum(rz_part); iter++; convergence and finiteness flags;
 // history[iter-1] = ||r|| / ||b|| when iter <= hist_cap.
 rr_status pcg_finish(const double *rz_part, int n_rz, const double *rr_part, int n_rr,

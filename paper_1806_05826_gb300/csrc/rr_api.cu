@@ -538,10 +538,12 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
 }
 
 // ---- the operator: t = X^T (X v) + lambda v, finished by the epilogue ep.
+// x32_ready: the FP32 copy of v is already in the X pass's vector (written by
+// the kernel that made v; sparse X, fp32 only).
 rr_status op_apply(rr_handle *h, const double *v, const rr::CscEpilogue &ep, const int32_t *stop,
-                   cudaStream_t st, bool fp32 = false) {
+                   cudaStream_t st, bool fp32 = false, bool x32_ready = false) {
   if (h->dense) return rr::dense_operator(h->N, h->F, h->Xd, v, h->u, h->dpart, ep, fp32, st);
-  RR_TRY(rr::sliced_gather(h->pcsr, v, nullptr, stop, st, fp32));
+  RR_TRY(rr::sliced_gather(h->pcsr, v, nullptr, stop, st, fp32, x32_ready));
   RR_TRY(rr::sliced_gather(h->pcsc, nullptr, &h->pcsr, stop, st, fp32));
   RR_TRY(rr::sliced_epilogue(h->pcsc, ep, st));
   return RR_OK;
@@ -557,8 +559,17 @@ rr_status rhs_apply(rr_handle *h, const double *y, double *b, cudaStream_t st) {
 }
 
 // ---- the preconditioner: z = M^{-1} r, with <r, z> partials in part_rz.
+// The X pass's FP32 vector when the PCG loop's producers can write the
+// applied vectors' FP32 copies there (mixed precision, sparse X), else nullptr.
+float *pcg_x32(rr_handle *h) {
+  return (h->opt.precision == RR_PREC_MIXED && !h->dense) ? static_cast<float *>(h->pcsr.xq)
+                                                          : nullptr;
+}
+
+// x32: where the producers of the applied vectors also write their FP32
+// copies (the X pass's vector), or nullptr; with z1_ready, z1's copy is there.
 rr_status apply_precond(rr_handle *h, const double *r, double *z, const int32_t *stop, int *n_rz,
-                        bool z1_ready, cudaStream_t st, bool fp32 = false) {
+                        bool z1_ready, cudaStream_t st, bool fp32 = false, float *x32 = nullptr) {
   const int64_t F = h->F;
   *n_rz = rr::kVecGrid;
   switch (h->opt.solver) {
@@ -571,12 +582,12 @@ rr_status apply_precond(rr_handle *h, const double *r, double *z, const int32_t 
       // z2 = z1 + P e_c; r2 = r - A z2; z = z2 + w D^-1 r2
       if (!z1_ready) RR_TRY(rr::jacobi(F, h->omega, r, h->d, h->z1, nullptr, stop, st));
       rr::CscEpilogue pre{rr::CSC_PRE, h->lambda, h->omega, h->z1, r, h->d, h->r1, nullptr, stop};
-      RR_TRY(op_apply(h, h->z1, pre, stop, st, fp32));
+      RR_TRY(op_apply(h, h->z1, pre, stop, st, fp32, x32 != nullptr && z1_ready));
       RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->r1, stop, st));
       RR_TRY(rr::coarse_matvec(h->k_eff, h->Ainv, h->rplan, h->s, nullptr, h->ec, stop, st));
-      RR_TRY(rr::prolong_add(F, h->labels, h->s, h->ec, h->z1, h->z2, stop, st));
+      RR_TRY(rr::prolong_add(F, h->labels, h->s, h->ec, h->z1, h->z2, stop, st, x32));
       rr::CscEpilogue post{rr::CSC_POST, h->lambda, h->omega, h->z2, r, h->d, z, h->part_rz, stop};
-      return op_apply(h, h->z2, post, stop, st, fp32);
+      return op_apply(h, h->z2, post, stop, st, fp32, x32 != nullptr);
     }
   }
 }
@@ -588,13 +599,15 @@ rr_status pcg_iteration(rr_handle *h, cudaStream_t st) {
   const bool twolevel = h->opt.solver == RR_SOLVER_TWOLEVEL;
   const int32_t *stop = &h->S->converged;
   const bool fp32 = h->opt.precision == RR_PREC_MIXED;
+  float *x32 = pcg_x32(h);
   int n_rz = 0;
-  RR_TRY(apply_precond(h, h->r, h->z, stop, &n_rz, twolevel, st, fp32));
-  RR_TRY(rr::pcg_direction(F, h->part_rz, n_rz, h->z, h->p, h->S, st));
+  RR_TRY(apply_precond(h, h->r, h->z, stop, &n_rz, twolevel, st, fp32, x32));
+  RR_TRY(rr::pcg_direction(F, h->part_rz, n_rz, h->z, h->p, h->S, st, x32));
   rr::CscEpilogue ap{rr::CSC_PCG, h->lambda, h->omega, h->p, nullptr, nullptr, h->q, h->part_pq, stop};
-  RR_TRY(op_apply(h, h->p, ap, stop, st, fp32));
+  RR_TRY(op_apply(h, h->p, ap, stop, st, fp32, x32 != nullptr));
   RR_TRY(rr::pcg_update(F, h->part_rz, n_rz, h->part_pq, rr::kVecGrid, h->p, h->q, h->w_int,
-                        h->r, h->omega, h->d, twolevel ? h->z1 : nullptr, h->part_rr, h->S, st));
+                        h->r, h->omega, h->d, twolevel ? h->z1 : nullptr, h->part_rr, h->S, st,
+                        twolevel ? x32 : nullptr));
   RR_TRY(rr::pcg_finish(h->part_rz, n_rz, h->part_rr, rr::kVecGrid, h->S, h->history,
                         h->hist_cap, st));
   return RR_OK;
@@ -694,7 +707,7 @@ rr_status solve_start(rr_handle *h, const double *y, double tol, cudaStream_t st
   RR_CUDA(cudaMemsetAsync(h->S, 0, sizeof(rr::PcgScalars), st));
   RR_TRY(rr::pcg_start(h->part_bb, rr::kVecGrid, h->part_bb, rr::kVecGrid, tol, 1, h->S, st));
   if (h->opt.solver == RR_SOLVER_TWOLEVEL)
-    RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st));
+    RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st, pcg_x32(h)));
   return RR_OK;
 }
 
@@ -705,7 +718,7 @@ rr_status solve_restart(rr_handle *h, double tol, cudaStream_t st) {
   RR_TRY(rr::dot_parts(F, h->r, h->r, h->part_rr, st));
   RR_TRY(rr::pcg_start(h->part_bb, 1, h->part_rr, rr::kVecGrid, tol, 0, h->S, st));
   if (h->opt.solver == RR_SOLVER_TWOLEVEL)
-    RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st));
+    RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st, pcg_x32(h)));
   return RR_OK;
 }
 
