@@ -104,10 +104,10 @@ typedef struct {
   int32_t check_every;          /* iterations between convergence read-backs when use_graphs = 0
                                    (default 8) */
   int32_t max_restarts;         /* true-residual refinement restarts at most (default 5) */
-  int32_t use_graphs;           /* 1: the iteration loop and the k-means++ seeding rounds run on
-                                   the device as CUDA graphs with a conditional while node
-                                   (default); 0: host-driven batches of check_every iterations and
-                                   host-issued seeding rounds (same results) */
+  int32_t use_graphs;           /* 1: the iteration loop runs on the device as a CUDA graph with
+                                   a conditional while node (default); 0: host-driven batches of
+                                   check_every iterations (same results). The k-means++ rounds are
+                                   host-issued kernel chains either way */
   int32_t gram;                 /* RR_GRAM_* (default RR_GRAM_AUTO) */
   int32_t gather;               /* RR_GATHER_* (default RR_GATHER_AUTO) */
   void *stream;                 /* cudaStream_t for all work; NULL = legacy default stream */

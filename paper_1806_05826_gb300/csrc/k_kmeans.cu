@@ -236,14 +236,11 @@ __global__ void __launch_bounds__(kThreads) k_seed_update(
   seed_update_tile(t, blockIdx.x, F, nc, heavy_centre(nc, N), col_ptr, ov, d2, tile_sum, sm);
 }
 
-// One block: draws centre t (1 <= t < k) from d2, the tile sums and chosen[]
-// (read through L2: other blocks of the same launch may have written them);
-// stores it in centers[t] (and chosen[] if mark_chosen) and returns it to
-// every thread of the block. Blocks that run it on the same data draw the
-// same centre.
+// One block: draws centre t (1 <= t < k) from d2, the tile sums and chosen[];
+// stores it in centers[t] and chosen[] and returns it to every thread.
 __device__ int64_t seed_pick(int32_t t, int64_t F, int64_t ntiles, uint64_t seed, const int64_t *d2,
                              const int64_t *tile_sum, int32_t *centers, uint8_t *chosen,
-                             bool mark_chosen, int64_t *sm) {
+                             int64_t *sm) {
   __shared__ int64_t found;
   __shared__ int64_t tile_found, tile_base;
   int64_t s = 0;
@@ -255,7 +252,7 @@ __device__ int64_t seed_pick(int32_t t, int64_t F, int64_t ntiles, uint64_t seed
     // every remaining distance is zero: lowest index not chosen yet
     for (int64_t base = 0; base < F; base += kThreads) {
       int64_t i = base + threadIdx.x;
-      int64_t cand = (i < F && !__ldcg(&chosen[i])) ? i : INT64_MAX;
+      int64_t cand = (i < F && !chosen[i]) ? i : INT64_MAX;
       for (int o = 16; o > 0; o >>= 1) cand = min(cand, __shfl_xor_sync(0xffffffffu, cand, o));
       __syncthreads();
       if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = cand;
@@ -305,7 +302,7 @@ __device__ int64_t seed_pick(int32_t t, int64_t F, int64_t ntiles, uint64_t seed
   const int64_t c = found;
   if (threadIdx.x == 0) {
     centers[t] = (int32_t)c;
-    if (c >= 0 && mark_chosen) chosen[c] = 1;
+    if (c >= 0) chosen[c] = 1;
   }
   __syncthreads();
   return c;
@@ -319,91 +316,8 @@ __global__ void k_seed_pick(int32_t *round, int32_t k, int64_t F, int64_t ntiles
   __shared__ int64_t sm[kWarps + 1];
   const int32_t t = *round + 1;
   __syncthreads();
-  if (t < k) seed_pick(t, F, ntiles, seed, d2, tile_sum, centers, chosen, true, sm);
+  if (t < k) seed_pick(t, F, ntiles, seed, d2, tile_sum, centers, chosen, sm);
   if (threadIdx.x == 0) *round = t;
-}
-
-// ---- all k rounds in one cooperative launch (every block resident): the
-// same phases per round as the kernels above, separated by grid barriers
-// (two per round, three for a heavy centre): every block draws the next
-// centre itself from the same tile sums and d2 (identical draws), so no
-// barrier waits on the draw. Each barrier wait is bounded: on expiry the
-// block records DEV_TIMEOUT and returns, and every other block returns at its
-// next barrier.
-struct GridBar {
-  unsigned int count;
-  unsigned int gen;
-};
-constexpr long long kBarSpinLimit = 1LL << 24;   // x >= 64 ns per spin: about a second
-
-__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ bool grid_barrier(GridBar *bar, int32_t *err) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    const unsigned int g = ld_acquire_gpu(&bar->gen);
-    __threadfence();
-    if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
-      atomicExch(&bar->count, 0u);
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      long long spins = 0;
-      while (ld_acquire_gpu(&bar->gen) == g) {
-        if (++spins > kBarSpinLimit) {
-          set_dev_error(err, DEV_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    if (ok && atomicAdd(err, 0) != DEV_OK) ok = 0;
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-__global__ void __launch_bounds__(kThreads) k_seed_all(
-    int64_t N, int64_t F, int32_t k, uint64_t seed, const int64_t *__restrict__ row_ptr,
-    const int32_t *__restrict__ col_idx, const int64_t *__restrict__ col_ptr,
-    const int32_t *__restrict__ row_idx, int32_t *rowmark, const uint16_t *__restrict__ hot,
-    const int32_t *__restrict__ hot_col, const int32_t *__restrict__ hot_n, int32_t *ov,
-    int64_t *d2, int64_t *tile_sum, int64_t ntiles, int32_t *centers, uint8_t *chosen,
-    GridBar *bar, int32_t *err) {
-  __shared__ int32_t hist[kHotBins];
-  __shared__ int64_t sm[kWarps + 1];
-  const int32_t nh = min(*hot_n, kHotBins);
-  int64_t c = __ldcg(&centers[0]);
-  for (int32_t t = 0; t < k; ++t) {
-    if (c < 0) {   // no centre drawn (cannot happen with F >= k): stop like the host form
-      if (threadIdx.x == 0 && blockIdx.x == 0) set_dev_error(err, DEV_BAD_INDEX);
-      return;
-    }
-    const int64_t nc = col_ptr[c + 1] - col_ptr[c];
-    const bool heavy = heavy_centre(nc, N);
-    if (heavy) {
-      seed_mark(t, c, N, col_ptr, row_idx, rowmark);
-      if (!grid_barrier(bar, err)) return;
-    }
-    seed_overlap(t, c, N, row_ptr, col_idx, col_ptr, row_idx, rowmark, hot, hot_col, nh, ov, hist);
-    if (!grid_barrier(bar, err)) return;
-    // chosen[] gains centre t between this round's two barriers: every block
-    // has finished the previous draw, and none starts the next one before the
-    // second barrier, so no block writes chosen[] while another reads it
-    if (t > 0 && threadIdx.x == 0) chosen[c] = 1;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-      seed_update_tile(t, tile, F, nc, heavy, col_ptr, ov, d2, tile_sum, sm);
-    if (!grid_barrier(bar, err)) return;
-    if (t + 1 < k) c = seed_pick(t + 1, F, ntiles, seed, d2, tile_sum, centers, chosen, false, sm);
-  }
 }
 
 __global__ void k_init_labels(int64_t F, int32_t k, const int32_t *__restrict__ centers,
@@ -820,11 +734,13 @@ __global__ void k_lloyd_argmin(int64_t F, int32_t k, const int32_t *__restrict__
 
 // The k rounds run as one CUDA graph: a conditional while node whose body is
 // one round (overlaps with the newest centre, distance update, next draw).
-// use_coop: all k rounds in one cooperative launch (k_seed_all); otherwise the
-// same rounds issued from the host as four kernels each. Identical results.
+// The k rounds, issued from the host as four kernels each (mark, overlap,
+// update, draw) chained by programmatic dependent launch: each kernel's
+// launch overlaps the previous one's tail, and no host synchronisation comes
+// between rounds.
 rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                         const int64_t *col_ptr, const int32_t *row_idx, int32_t k, uint64_t seed,
-                        KmeansBuffers &b, int32_t *err, cudaStream_t st, bool use_coop) {
+                        KmeansBuffers &b, cudaStream_t st) {
   const int64_t ntiles = (F + kTile - 1) / kTile;
   uint8_t *chosen = reinterpret_cast<uint8_t *>(b.next);   // F bytes of the (unused yet) next[]
   RR_CUDA(cudaMemsetAsync(chosen, 0, F, st));
@@ -834,29 +750,6 @@ rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int3
   RR_LAUNCH(k_hot_assign, grid_for(F, kThreads), kThreads, 0, st, F, N, col_ptr, b.hot, b.hot_col,
             b.hot_n);
   RR_LAUNCH(k_first_center, 1, 32, 0, st, F, seed, b.centers, chosen, b.round);
-  int grid = 0;
-  if (use_coop) {
-    int dev = 0, sms = 0, per_sm = 0, coop = 0;
-    RR_CUDA(cudaGetDevice(&dev));
-    RR_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
-    RR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_seed_all, kThreads, 0));
-    if (coop) grid = sms * std::min(per_sm, 2);
-  }
-  if (grid > 0) {
-    RR_CUDA(cudaMemsetAsync(b.bar, 0, sizeof(GridBar), st));
-    GridBar *bar = reinterpret_cast<GridBar *>(b.bar);
-    int32_t *rowmark = b.dcount;
-    void *args[] = {(void *)&N,       (void *)&F,       (void *)&k,       (void *)&seed,
-                    (void *)&row_ptr, (void *)&col_idx, (void *)&col_ptr, (void *)&row_idx,
-                    (void *)&rowmark, (void *)&b.hot,   (void *)&b.hot_col, (void *)&b.hot_n,
-                    (void *)&b.ov,    (void *)&b.d2,    (void *)&b.part_i, (void *)&ntiles,
-                    (void *)&b.centers, (void *)&chosen, (void *)&bar,    (void *)&err};
-    RR_CUDA(cudaLaunchCooperativeKernel((const void *)k_seed_all, grid, kThreads, args, 0, st));
-    ++rr_launch_counter;
-    RR_CUDA(cudaStreamSynchronize(st));
-    return RR_OK;
-  }
   for (int32_t t = 0; t < k; ++t) {
     RR_LAUNCH_PDL(k_seed_mark, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, col_ptr, row_idx,
                   b.dcount);

@@ -57,7 +57,6 @@ struct KmeansBuffers {
   uint16_t *hot;       // [F] shared-histogram bin of a frequent feature (0xFFFF: none)
   int32_t *hot_col;    // [2048] feature of each bin
   int32_t *hot_n;      // [1] bins in use (capped at 2048 when read)
-  unsigned int *bar;   // [2] grid barrier of the cooperative seeding kernel
   int32_t packed;      // host: delta lists in the 32-bit form (set by kmeans_work_order)
   int64_t *task_ptr;   // [F+1] first pull task of each feature in work order
   int32_t *task_it;    // [kmeans_pull_tasks_max(F, nnz)] feature (work-order index) of each task
@@ -65,12 +64,10 @@ struct KmeansBuffers {
 };
 // upper bound of the pull tasks: one per feature plus one per 1024 entries
 int64_t kmeans_pull_tasks_max(int64_t F, int64_t nnz);
-// K-means++ seeding (k centres into b.centers). use_coop: one cooperative
-// launch for all rounds (bounded grid barriers; DEV_TIMEOUT in *err on expiry);
-// else host-issued rounds. Synchronises the stream.
+// K-means++ seeding (k centres into b.centers). Synchronises the stream.
 rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                         const int64_t *col_ptr, const int32_t *row_idx, int32_t k, uint64_t seed,
-                        KmeansBuffers &b, int32_t *err, cudaStream_t st, bool use_coop);
+                        KmeansBuffers &b, cudaStream_t st);
 // labels <- -1 except labels[centers[S]] = S; prev <- -1; D <- 0.
 // tiles of features of the seeding pass (tile sums in part_i)
 int64_t kmeans_seed_tiles(int64_t F);

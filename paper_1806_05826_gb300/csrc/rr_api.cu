@@ -390,7 +390,6 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&kb.hot, F));
   RR_TRY(m.alloc(&kb.hot_col, 2048));
   RR_TRY(m.alloc(&kb.hot_n, 1));
-  RR_TRY(m.alloc(&kb.bar, 2));
   RR_TRY(m.alloc(&kb.task_ptr, F + 1));
   RR_TRY(m.alloc(&kb.task_it, rr::kmeans_pull_tasks_max(F, nnz)));
   if (h->opt.init_centers) {
@@ -407,8 +406,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
                             cudaMemcpyHostToDevice, st));
   } else {
     RR_TRY(rr::kmeanspp_seed(N, F, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx, k,
-                             h->opt.seed, kb, h->err, st, h->opt.use_graphs != 0));
-    RR_TRY(check_dev_error(h, "k-means++ seeding"));
+                             h->opt.seed, kb, st));
   }
   RR_TRY(phase(2));
   RR_TRY(rr::kmeans_init_labels(F, k, kb, st));
@@ -441,7 +439,6 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   m.release(kb.hot);
   m.release(kb.hot_col);
   m.release(kb.hot_n);
-  m.release(kb.bar);
   m.release(kb.task_ptr);
   m.release(kb.task_it);
 

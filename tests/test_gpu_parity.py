@@ -265,9 +265,9 @@ def test_repeatable_bits(case, rr):
 
 
 def test_graph_loop_equals_host_loop(case, rr):
-    """The one-launch cooperative seeding and the device-side while-loop
-    graphs of PCG against host-issued loops of the same phases in the same
-    order: identical centres, labels, bits and iteration counts."""
+    """The device-side while-loop graphs of PCG against host-issued loops of
+    the same kernels in the same order: identical centres, labels, bits and
+    iteration counts."""
     X = case["X"]
     h2 = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, case["lam"], case["k"],
                      seed=case["seed"], use_graphs=0, check_every=5)
