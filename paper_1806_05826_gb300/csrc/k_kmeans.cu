@@ -198,7 +198,11 @@ __global__ void __launch_bounds__(kThreads) k_seed_overlap(
   __shared__ int32_t hist[kHotBins];
   pdl_wait();
   const int32_t t = *round;
-  seed_overlap(t, centers[t], N, row_ptr, col_idx, col_ptr, row_idx, rowmark, hot, hot_col,
+  const int64_t c = centers[t];
+  const int64_t nc = col_ptr[c + 1] - col_ptr[c];
+  // a light centre's rows go one per warp: blocks past them have nothing to count
+  if (!heavy_centre(nc, N) && (int64_t)blockIdx.x * (blockDim.x >> 5) >= nc) return;
+  seed_overlap(t, c, N, row_ptr, col_idx, col_ptr, row_idx, rowmark, hot, hot_col,
                min(*hot_n, kHotBins), ov, hist);
 }
 

@@ -434,21 +434,19 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather_staged(
   }
 }
 
-// Chunks of whole pieces of at most kChunkWords words, per task (one thread
-// per task scans its pieces in order). count: chunks of each task; fill: the
-// first piece of every chunk (chunk_p[total] = npieces).
+// Chunks of whole pieces of at most kChunkWords words, per task: chunk j of
+// a task holds the pieces that start in words [w0 + j S, w0 + (j + 1) S) of it
+// (w0 its first word, S = kChunkWords - kPieceWords), so a chunk spans at most
+// S + kPieceWords words, and every chunk holds a piece (pieces are contiguous
+// and at most kPieceWords long). count: chunks of each task; fill: the first
+// piece and word of every chunk (chunk_p[total] = npieces), by a search that
+// resumes where the previous chunk's ended.
+constexpr int32_t kChunkStep = kChunkWords - kPieceWords;
 __global__ void k_chunk_count(int32_t ntasks, const int32_t *__restrict__ task_p,
                               const int32_t *__restrict__ pw, int64_t *__restrict__ cnt) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntasks; t += gridDim.x * blockDim.x) {
-    int64_t n = 0;
-    int32_t start = -1;
-    for (int32_t p = task_p[t]; p < task_p[t + 1]; ++p) {
-      if (start < 0 || pw[p + 1] - start > kChunkWords) {
-        start = pw[p];
-        ++n;
-      }
-    }
-    cnt[t] = n;
+    const int32_t p0 = task_p[t], p1 = task_p[t + 1];
+    cnt[t] = p1 > p0 ? (pw[p1 - 1] - pw[p0]) / kChunkStep + 1 : 0;
   }
 }
 
@@ -457,15 +455,20 @@ __global__ void k_chunk_fill(int32_t ntasks, const int32_t *__restrict__ task_p,
                              int32_t *__restrict__ chunk_p, int32_t *__restrict__ chunk_w,
                              int32_t *__restrict__ task_c, int64_t total, int32_t npieces) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntasks; t += gridDim.x * blockDim.x) {
-    int64_t n = off[t];
-    task_c[t] = (int32_t)n;
-    int32_t start = -1;
-    for (int32_t p = task_p[t]; p < task_p[t + 1]; ++p) {
-      if (start < 0 || pw[p + 1] - start > kChunkWords) {
-        start = pw[p];
-        chunk_w[n] = start;
-        chunk_p[n++] = p;
+    const int64_t n0 = off[t], n1 = off[t + 1];
+    task_c[t] = (int32_t)n0;
+    const int32_t p0 = task_p[t], p1 = task_p[t + 1];
+    const int32_t w0 = p1 > p0 ? pw[p0] : 0;
+    int32_t lo = p0;
+    for (int64_t n = n0; n < n1; ++n) {
+      const int32_t target = w0 + (int32_t)(n - n0) * kChunkStep;
+      int32_t hi = p1;
+      while (lo < hi) {   // first piece of the task starting at or after target
+        const int32_t mid = (lo + hi) >> 1;
+        if (pw[mid] < target) lo = mid + 1; else hi = mid;
       }
+      chunk_p[n] = lo;
+      chunk_w[n] = pw[lo];
     }
     if (t == ntasks - 1) {
       task_c[ntasks] = (int32_t)total;
