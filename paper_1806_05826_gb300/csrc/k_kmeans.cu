@@ -338,20 +338,22 @@ __global__ void k_set_center_labels(int32_t k, const int32_t *__restrict__ cente
 }
 
 // work_i = sum of the row lengths over the rows of column i (the cost of D_i.)
-__global__ void k_feature_work(int64_t F, const int64_t *__restrict__ row_ptr,
-                               const int64_t *__restrict__ col_ptr,
-                               const int32_t *__restrict__ row_idx, int64_t *__restrict__ work) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i = warp; i < F; i += nwarps) {
+// work[i] = sum over the rows of column i of their lengths (= (|X|^T |X| 1)_i):
+// one block per column, so the longest columns do not serialise on one warp.
+__global__ void __launch_bounds__(kThreads) k_feature_work(int64_t F,
+                                                          const int64_t *__restrict__ row_ptr,
+                                                          const int64_t *__restrict__ col_ptr,
+                                                          const int32_t *__restrict__ row_idx,
+                                                          int64_t *__restrict__ work) {
+  __shared__ int64_t sm[kWarps + 1];
+  for (int64_t i = blockIdx.x; i < F; i += gridDim.x) {
     int64_t s = 0;
-    for (int64_t p = col_ptr[i] + lane; p < col_ptr[i + 1]; p += 32) {
+    for (int64_t p = col_ptr[i] + threadIdx.x; p < col_ptr[i + 1]; p += kThreads) {
       const int64_t r = row_idx[p];
       s += row_ptr[r + 1] - row_ptr[r];
     }
-    s = warp_sum_i64(s);
-    if (lane == 0) work[i] = s;
+    s = block_sum_i64(s, sm);
+    if (threadIdx.x == 0) work[i] = s;
   }
 }
 
@@ -787,8 +789,8 @@ rr_status kmeans_work_order(int64_t N, int64_t F, int32_t k, const int64_t *row_
   int64_t *cnt = scratch;
   int64_t *offs = cnt + kBuckets;              // kBuckets + 1
   int64_t *sscr = offs + kBuckets + 1;
-  RR_LAUNCH(k_feature_work, grid_for(F, kWarps), kThreads, 0, st, F, row_ptr, col_ptr, row_idx,
-            work);
+  RR_LAUNCH(k_feature_work, (unsigned)std::min<int64_t>(std::max<int64_t>(F, 1), kSMs * 64), kThreads,
+            0, st, F, row_ptr, col_ptr, row_idx, work);
   RR_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int64_t) * kBuckets, st));
   RR_LAUNCH(k_bucket_count, grid_for(F, kThreads), kThreads, 0, st, F, work,
             (unsigned long long *)cnt);
