@@ -299,12 +299,19 @@ __global__ void __launch_bounds__(32 * kTriWarps) k_tri_inverse(int32_t k,
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t j = warp; j < k; j += nwarps) {
+    double rwin = 0.0;   // lane l: 1 / L[i0 + l][i0 + l] for the current window of 32 rows
     for (int64_t i = j; i < k; ++i) {
+      const int step = (int)((i - j) & 31);
+      if (step == 0) {   // the divides of the next 32 rows, off the dependent chain
+        const int64_t ii = i + lane;
+        rwin = ii < k ? 1.0 / L[ii * k + ii] : 0.0;
+      }
       const double *Li = L + i * k;
       double s = 0.0;
       for (int64_t m = j + lane; m < i; m += 32) s += Li[m] * x[m];
       s = warp_sum(s);
-      if (lane == 0) x[i] = ((i == j ? 1.0 : 0.0) - s) / Li[i];
+      const double ri = __shfl_sync(0xffffffffu, rwin, step);
+      if (lane == 0) x[i] = ((i == j ? 1.0 : 0.0) - s) * ri;
       __syncwarp();
     }
     double *out = LinvT + j * k;
