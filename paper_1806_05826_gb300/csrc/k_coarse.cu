@@ -290,6 +290,7 @@ __global__ void k_chol_update(int32_t k, int32_t j0, double *__restrict__ L) {
 // shared memory (dynamic, one row of k doubles per warp of the block), so each
 // step waits on a shared-memory round trip only; written out at the end.
 constexpr int kTriWarps = 4;
+constexpr int kTriWin = 32;   // row entries per lane held in registers (rows up to 1024 long)
 __global__ void __launch_bounds__(32 * kTriWarps) k_tri_inverse(int32_t k,
                                                                 const double *__restrict__ L,
                                                                 double *__restrict__ LinvT) {
@@ -300,19 +301,40 @@ __global__ void __launch_bounds__(32 * kTriWarps) k_tri_inverse(int32_t k,
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t j = warp; j < k; j += nwarps) {
     double rwin = 0.0;   // lane l: 1 / L[i0 + l][i0 + l] for the current window of 32 rows
+    // the first kTriWin entries of the row being summed (m = j + lane + 32 t), loaded
+    // one step ahead, so the step waits on shared memory and arithmetic only
+    double cur[kTriWin];
+#pragma unroll
+    for (int t = 0; t < kTriWin; ++t) cur[t] = 0.0;
     for (int64_t i = j; i < k; ++i) {
       const int step = (int)((i - j) & 31);
       if (step == 0) {   // the divides of the next 32 rows, off the dependent chain
         const int64_t ii = i + lane;
         rwin = ii < k ? 1.0 / L[ii * k + ii] : 0.0;
       }
+      double nxt[kTriWin];
+      const int64_t i1 = i + 1;
+#pragma unroll
+      for (int t = 0; t < kTriWin; ++t) {
+        const int64_t m = j + lane + 32 * t;
+        nxt[t] = (i1 < k && m < i1) ? L[i1 * k + m] : 0.0;
+      }
       const double *Li = L + i * k;
-      double s = 0.0;
-      for (int64_t m = j + lane; m < i; m += 32) s += Li[m] * x[m];
-      s = warp_sum(s);
+      double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+      for (int t = 0; t < kTriWin; t += 2) {
+        if (32 * t >= i - j) break;
+        const int64_t m = j + lane + 32 * t;
+        if (m < i) s0 += cur[t] * x[m];
+        if (m + 32 < i) s1 += cur[t + 1] * x[m + 32];
+      }
+      for (int64_t m = j + lane + 32 * kTriWin; m < i; m += 32) s0 += Li[m] * x[m];
+      const double s = warp_sum(s0 + s1);
       const double ri = __shfl_sync(0xffffffffu, rwin, step);
       if (lane == 0) x[i] = ((i == j ? 1.0 : 0.0) - s) * ri;
       __syncwarp();
+#pragma unroll
+      for (int t = 0; t < kTriWin; ++t) cur[t] = nxt[t];
     }
     double *out = LinvT + j * k;
     for (int64_t i = j + lane; i < k; i += 32) out[i] = x[i];
