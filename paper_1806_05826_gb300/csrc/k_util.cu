@@ -84,14 +84,16 @@ __global__ void k_scan_apply(const int64_t *__restrict__ in, int64_t n,
   if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = 0;
 }
 
-__global__ void k_validate_csr(int64_t n_rows, int64_t n_cols, const int64_t *__restrict__ row_ptr,
+__global__ void k_validate_csr(int64_t n_rows, int64_t n_cols, int64_t nnz,
+                               const int64_t *__restrict__ row_ptr,
                                const int32_t *__restrict__ col_idx, int32_t *err) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = warp; r < n_rows; r += nwarps) {
     int64_t b = row_ptr[r], e = row_ptr[r + 1];
-    bool bad = e < b;
+    // a row's bounds must lie in [0, nnz] before its indices are read
+    bool bad = e < b || b < 0 || e > nnz;
     if (!bad) {
       for (int64_t p = b + lane; p < e; p += 32) {
         int32_t c = col_idx[p];
@@ -215,10 +217,10 @@ rr_status scan_exclusive(const int64_t *in, int64_t *out, int64_t n, int64_t *sc
   return RR_OK;
 }
 
-rr_status validate_csr(int64_t n_rows, int64_t n_cols, const int64_t *row_ptr,
+rr_status validate_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int64_t *row_ptr,
                        const int32_t *col_idx, int32_t *err, cudaStream_t st) {
   if (n_rows == 0) return RR_OK;
-  RR_LAUNCH(k_validate_csr, grid_for(n_rows, kWarps), kThreads, 0, st, n_rows, n_cols, row_ptr,
+  RR_LAUNCH(k_validate_csr, grid_for(n_rows, kWarps), kThreads, 0, st, n_rows, n_cols, nnz, row_ptr,
             col_idx, err);
   return RR_OK;
 }

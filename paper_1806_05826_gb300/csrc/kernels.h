@@ -23,9 +23,9 @@ rr_status transpose_pattern(int64_t n_rows, int64_t n_cols, int64_t nnz, const i
                             int64_t *counts, int64_t *cursor, int32_t *tmp,
                             int64_t *scan_scratch, cudaStream_t st);
 
-// Records DEV_BAD_INDEX in *err unless every row's indices are strictly
-// increasing and in [0, n_cols).
-rr_status validate_csr(int64_t n_rows, int64_t n_cols, const int64_t *row_ptr,
+// Records DEV_BAD_INDEX in *err unless 0 <= row_ptr[r] <= row_ptr[r+1] <= nnz
+// and every row's indices are strictly increasing and in [0, n_cols).
+rr_status validate_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int64_t *row_ptr,
                        const int32_t *col_idx, int32_t *err, cudaStream_t st);
 
 rr_status iota_i64(int64_t *out, int64_t n, cudaStream_t st);

@@ -120,28 +120,6 @@ rr_status build_lambda(rr_handle *h, double lambda) {
   return RR_OK;
 }
 
-rr_status validate_host_csr(const rr_matrix *X) {
-  if (X->row_ptr[0] != 0 || X->row_ptr[X->n_rows] != X->nnz) {
-    rr_set_error("row_ptr[0] must be 0 and row_ptr[N] must equal nnz");
-    return RR_INVALID_ARG;
-  }
-  for (int64_t r = 0; r < X->n_rows; ++r) {
-    const int64_t b = X->row_ptr[r], e = X->row_ptr[r + 1];
-    if (e < b) {
-      rr_set_error("row_ptr decreases at row %lld", (long long)r);
-      return RR_INVALID_ARG;
-    }
-    for (int64_t p = b; p < e; ++p) {
-      const int32_t c = X->col_idx[p];
-      if (c < 0 || c >= X->n_cols || (p > b && X->col_idx[p - 1] >= c)) {
-        rr_set_error("col_idx out of range or not strictly increasing in row %lld", (long long)r);
-        return RR_INVALID_ARG;
-      }
-    }
-  }
-  return RR_OK;
-}
-
 // Solve vectors, partial-dot buffers, scalars and the capture stream.
 rr_status alloc_solve_workspace(rr_handle *h) {
   DevArena &m = h->mem;
@@ -339,12 +317,19 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
     }
     RR_CUDA(cudaMemcpyAsync(h->row_ptr, X->row_ptr, sizeof(int64_t) * (N + 1), cudaMemcpyDeviceToDevice, st));
     RR_CUDA(cudaMemcpyAsync(h->col_idx, X->col_idx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToDevice, st));
-    RR_TRY(rr::validate_csr(N, F, h->row_ptr, h->col_idx, h->err, st));
+    RR_TRY(rr::validate_csr(N, F, nnz, h->row_ptr, h->col_idx, h->err, st));
     RR_TRY(check_dev_error(h, "rr_setup"));
   } else {
-    RR_TRY(validate_host_csr(X));
+    // the ends on the host; the rest on the device after the copy (a pass over
+    // nnz indices on one host core would cost more than the copy itself)
+    if (X->row_ptr[0] != 0 || X->row_ptr[N] != nnz) {
+      rr_set_error("row_ptr[0] must be 0 and row_ptr[N] must equal nnz");
+      return RR_INVALID_ARG;
+    }
     RR_CUDA(cudaMemcpyAsync(h->row_ptr, X->row_ptr, sizeof(int64_t) * (N + 1), cudaMemcpyHostToDevice, st));
     RR_CUDA(cudaMemcpyAsync(h->col_idx, X->col_idx, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st));
+    RR_TRY(rr::validate_csr(N, F, nnz, h->row_ptr, h->col_idx, h->err, st));
+    RR_TRY(check_dev_error(h, "rr_setup"));
   }
 
   RR_TRY(phase(0));

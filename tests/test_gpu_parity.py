@@ -330,7 +330,9 @@ def test_edge_zero_rhs(rr):
     assert info["iters"] == 0 and torch.count_nonzero(w) == 0
 
 
-def test_invalid_inputs_rejected_on_host(rr):
+def test_invalid_host_inputs_rejected(rr):
+    """Host CSR input: the ends of row_ptr are checked on the host, the rest on
+    the device after the copy; every case is RR_INVALID_ARG."""
     rp = np.array([0, 2, 3], np.int64)
     ci = np.array([1, 1, 0], np.int32)       # repeated index in row 0
     with pytest.raises(rr.RRError) as e:
@@ -342,6 +344,10 @@ def test_invalid_inputs_rejected_on_host(rr):
     with pytest.raises(rr.RRError):
         rr.rr_setup(np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32), 2, 3, 1.0, 1,
                     init_centers=[5])       # centre out of range
+    # a middle row bound beyond nnz (row_ptr not monotone): caught before any index is read
+    with pytest.raises(rr.RRError) as e:
+        rr.rr_setup(np.array([0, 1000000, 3], np.int64), np.array([0, 1, 2], np.int32), 2, 3, 1.0, 1)
+    assert e.value.status == rr.RR_INVALID_ARG
     ok = rr.rr_setup(np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32), 2, 3, 1.0, 1)
     w = torch.empty(3, dtype=torch.float64, device="cuda")
     with pytest.raises(rr.RRError):
@@ -351,6 +357,11 @@ def test_invalid_inputs_rejected_on_host(rr):
 def test_invalid_device_csr_detected_by_kernel(rr):
     rp = torch.tensor([0, 2, 3], dtype=torch.int64, device="cuda")
     ci = torch.tensor([2, 1, 0], dtype=torch.int32, device="cuda")   # decreasing in row 0
+    with pytest.raises(rr.RRError) as e:
+        rr.rr_setup(rp, ci, 2, 3, 1.0, 1)
+    assert e.value.status == rr.RR_INVALID_ARG
+    rp = torch.tensor([0, 1000000, 3], dtype=torch.int64, device="cuda")   # bound beyond nnz
+    ci = torch.tensor([0, 1, 2], dtype=torch.int32, device="cuda")
     with pytest.raises(rr.RRError) as e:
         rr.rr_setup(rp, ci, 2, 3, 1.0, 1)
     assert e.value.status == rr.RR_INVALID_ARG
