@@ -423,6 +423,84 @@ def test_kmeanspp_draw_follows_d2_weights():
     assert abs(firsts / 4000 - 0.25) < 0.04
 
 
+def _brute_force_lloyd_real(X, centers, max_iter):
+    """Lloyd on real features with exact rational arithmetic (every float32
+    value is a rational), the same rules: singleton starts, means over members,
+    squared Euclidean distance, ties to the smallest cluster, empty clusters
+    skipped, stop at the first step that changes no label."""
+    X = np.asarray(X, np.float32)
+    N, F = X.shape
+    cols = [[Fraction(float(v)) for v in X[:, i]] for i in range(F)]
+    cent = [cols[c][:] for c in centers]
+    size = [1] * len(centers)
+    labels = None
+    it = 0
+    while it < max_iter:
+        it += 1
+        new = []
+        for i in range(F):
+            best, bd = None, None
+            for S in range(len(cent)):
+                if size[S] == 0:
+                    continue
+                dist = sum((cols[i][r] - cent[S][r]) ** 2 for r in range(N))
+                if bd is None or dist < bd:
+                    best, bd = S, dist
+            new.append(best)
+        if new == labels:
+            break
+        labels = new
+        size = [labels.count(S) for S in range(len(cent))]
+        cent = [[sum((cols[i][r] for i in range(F) if labels[i] == S), Fraction(0)) / size[S]
+                 if size[S] else Fraction(0) for r in range(N)] for S in range(len(cent))]
+    return np.array(labels, np.int32), it
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_lloyd_dense_matches_exact_arithmetic(seed):
+    """Section 3.4 on dense X: the FP64 Lloyd (blocked row sums) gives the
+    labels and step count of exact rational Lloyd on random data (no near
+    ties), here 70 rows (two blocks of 64 and a ragged one) and 16 features."""
+    rng = np.random.default_rng(30 + seed)
+    X = rng.standard_normal((70, 16)).astype(np.float32)
+    X[:, 8:] += 1.5 * rng.standard_normal((1, 8)).astype(np.float32)   # two loose groups
+    centers = rng.choice(16, size=4, replace=False)
+    lab, it = km.lloyd_dense(X, centers, 30)
+    ref, it_ref = _brute_force_lloyd_real(X, centers, 30)
+    assert np.array_equal(lab, ref)
+    assert it == it_ref
+
+
+def test_kmeanspp_dense_draw_follows_d2_weights():
+    """Dense k-means++: the second centre is drawn with probability
+    proportional to the squared Euclidean distance to the first."""
+    X = np.array([[1, 1, 0, 3],
+                  [0, 1, 0, 0],
+                  [0, 0, 2, 0]], np.float32)   # D^2 from feature 0: [0, 1, 5, 4]
+    counts = np.zeros(4)
+    firsts = 0
+    for seed in range(4000):
+        c = km.kmeanspp_dense(X, 2, seed)
+        if c[0] == 0:
+            firsts += 1
+            counts[c[1]] += 1
+    p = counts / counts.sum()
+    assert counts[0] == 0
+    assert np.allclose(p[1:], [0.1, 0.5, 0.4], atol=0.06)
+    assert abs(firsts / 4000 - 0.25) < 0.04
+
+
+def test_dense_omega_below_spectral_bound():
+    """The Gershgorin omega on dense correlated X: w lambda_max(D^{-1} A) <= 1."""
+    X = synth.dense_ar1(120, 30, 0.9, 4)
+    two = tl.setup_dense(X, 0.1, 3, seed=0)
+    A = osp.dense_A(two.M, 0.1)
+    Dm = np.diag(1.0 / np.sqrt(two.d))
+    lmax = np.linalg.eigvalsh(Dm @ A @ Dm).max()
+    assert two.omega * lmax <= 1.0 + 1e-12
+    assert np.allclose(two.d, np.diag(A))
+
+
 def test_dense_kmeans_recovers_groups():
     rng = np.random.default_rng(9)
     base = rng.standard_normal((20, 3)).astype(np.float32)
