@@ -161,6 +161,30 @@ class TwoLevel:
         r2 = r - self.A(z2)
         return z2 + self.omega * r2 / self.d
 
+    def apply_tlfcg(self, r, steps=2):
+        """The cycle the paper recommends for FCG (Section 3.1 and Section 4's
+        smoothing study): `steps` iterations of CG on A z = r from z = 0 as a
+        pre-smoother (the "rougher"), then the coarse correction of what is
+        left: z = z1 + P A_c^-1 P^T r1, with r1 = r - A z1 carried by the CG
+        recurrence. No post-smoothing. z depends non-linearly on r (CG), so the
+        outer method is flexible CG."""
+        r = np.asarray(r, np.float64)
+        z1 = np.zeros_like(r)
+        res = r.copy()
+        rho = float(res @ res)
+        p = res.copy()
+        for j in range(steps):
+            if rho == 0.0:
+                break
+            if j > 0:
+                p = res + (rho / rho_old) * p
+            q = self.A(p)
+            alpha = rho / float(p @ q)
+            z1 += alpha * p
+            res -= alpha * q
+            rho_old, rho = rho, float(res @ res)
+        return z1 + prolong(self.labels, self.s, self.coarse_correction(res))
+
     def with_lambda(self, lam):
         """The same clustering at another lambda: the coarse factor and the
         smoother are rebuilt, the clustering is reused (Section 4: the

@@ -292,6 +292,37 @@ def test_fcg_matches_pcg_for_fixed_spd_preconditioner():
     assert np.linalg.norm(r2.w - w) < 1e-8 * np.linalg.norm(w)
 
 
+def test_rougher_is_two_step_krylov_minimiser():
+    """Two CG steps from zero give the element of span{r, A r} that minimises
+    the A-norm of the error: z* = V (V^T A V)^-1 V^T r, V = [r, A r]; the
+    TLFCG cycle then adds the coarse correction of r - A z*."""
+    two, A = _tiny_two_level(seed=8)
+    r = np.random.default_rng(3).standard_normal(A.shape[0])
+    V = np.stack([r, A @ r], axis=1)
+    zstar = V @ np.linalg.solve(V.T @ A @ V, V.T @ r)
+    P = tl.prolongation_dense(two.labels, two.s)
+    want = zstar + P @ np.linalg.solve(P.T @ A @ P, P.T @ (r - A @ zstar))
+    got = two.apply_tlfcg(r)
+    assert np.allclose(got, want, rtol=1e-9, atol=1e-12 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_tlfcg_reaches_dense_solution(seed):
+    """FCG(1) with the rougher cycle solves Eq. (1): the same w as a dense
+    solve, in fewer iterations than plain CG (Table 2's claim for TLFCG)."""
+    rng = np.random.default_rng(20 + seed)
+    D = (rng.random((300, 120)) < 0.05).astype(np.int64)
+    n, f, rp, ci = csr_of(D)
+    two = tl.setup_binary(n, f, rp, ci, 1e-2, 12, seed=seed)
+    y = rng.standard_normal(n)
+    b = osp.rhs(two.M, y)
+    res = krylov.fcg(two.A, lambda r, i: two.apply_tlfcg(r), b, m=1, tol=1e-10)
+    w = np.linalg.solve(osp.dense_A(two.M, 1e-2), b)
+    assert np.linalg.norm(res.w - w) <= 1e-7 * np.linalg.norm(w)
+    cg = krylov.cg(two.A, b, tol=1e-10, max_iter=5000)
+    assert res.iters < cg.iters
+
+
 def test_fcg_truncation_rule():
     """m_0 = 0 and m_i = max(1, i mod (m+1)): with m = 3, FCG on an SPD system
     with the identity preconditioner is CG and converges in <= f steps."""
