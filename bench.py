@@ -48,6 +48,8 @@ def parse():
                     help="skip the batched section (64 targets x 8 weights over the same X)")
     ap.add_argument("--no-many", action="store_true",
                     help="skip the section of uneven independent problems in one graph")
+    ap.add_argument("--no-tlfcg", action="store_true",
+                    help="skip the section solving the same systems with the paper's TLFCG")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned coarse correction section (harvest, training, solves)")
     ap.add_argument("--no-graphs", action="store_true",
@@ -256,6 +258,29 @@ def measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world, n_targ
             "plain_estimate_s": round(t_plain, 3),
             "speedup_vs_plain": round(t_plain / t_batch, 2),
             "note": "plain = setup + systems x mean single-solve time of target 0 at the 8 weights"}
+
+
+def measure_tlfcg(rr, row_ptr, col_idx, N, F, k, lams, opts, y_dev, last_infos):
+    """The same systems (each lambda, same target, same clustering) solved by the
+    paper's TLFCG: flexible CG whose preconditioner is two CG rougher steps and the
+    coarse correction; against the plain two-level PCG of the timed step."""
+    import torch
+    h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], k, **dict(opts, solver=rr.RR_SOLVER_TLFCG))
+    w = torch.empty(F, dtype=torch.float64, device=y_dev.device)
+    out = {"method": "FCG(1), preconditioner: 2 CG steps on A z = r, then the coarse correction",
+           "iters": [], "solve_ms": [], "true_rel_res": []}
+    for j, lam in enumerate(lams):
+        if j:
+            rr.rr_set_lambda(h, lam)
+        info = rr.rr_solve(h, y_dev, w, tol=TOL)
+        out["iters"].append(info["iters"])
+        out["solve_ms"].append(round(info["solve_ms"], 2))
+        out["true_rel_res"].append(info["true_rel_res"])
+    rr.rr_free(h)
+    out["pcg_iters"] = [i["iters"] for i in last_infos]
+    out["pcg_solve_ms"] = [round(i["solve_ms"], 2) for i in last_infos]
+    out["speedup_vs_pcg"] = round(sum(out["pcg_solve_ms"]) / max(1e-9, sum(out["solve_ms"])), 3)
+    return out
 
 
 def measure_dense_apply(rr, h, n, f, dev, stream, reps=20):
@@ -548,7 +573,9 @@ def run_ours(args, rank, world, local):
                "h2d_bytes_per_step": 8 * (N + 1) + 4 * nnz + 8 * N,
                "d2h_bytes_per_step": 8 * F * len(lams)}
 
-    batched = many = learned = None
+    batched = many = learned = tlfcg = None
+    if not args.no_tlfcg:
+        tlfcg = measure_tlfcg(rr, row_ptr, col_idx, N, F, k, lams, opts, y_dev, last_infos=all_infos[-1])
     if not args.no_batch and args.workload == WORKLOAD:
         batched = measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world,
                                   args.batch_targets)
@@ -585,7 +612,7 @@ def run_ours(args, rank, world, local):
                                         "Xt": "staged" if last[0]["gather_staged"] & 2 else "lanes"},
                       "step_ms": [round(t, 3) for t in step_ms]},
         "e2e": e2e, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches,
-        "batched": batched, "many": many, "learned": learned,
+        "batched": batched, "many": many, "learned": learned, "tlfcg": tlfcg,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         iters = [i["iters"] for i in last]

@@ -50,7 +50,11 @@ enum { RR_CSR_BINARY = 0,       /* pattern only: every stored entry is 1 */
 /* rr_options.solver — the preconditioner inside CG */
 enum { RR_SOLVER_TWOLEVEL = 0,  /* symmetric two-level cycle (Section 3.1) in PCG */
        RR_SOLVER_CG = 1,        /* no preconditioner (Table 2, "CG") */
-       RR_SOLVER_DCG = 2 };     /* Jacobi preconditioner (Table 2, "DCG") */
+       RR_SOLVER_DCG = 2,       /* Jacobi preconditioner (Table 2, "DCG") */
+       RR_SOLVER_TLFCG = 3 };   /* the paper's TLFCG (Table 2, Section 4): flexible CG (Alg. 3,
+                                   m = 1) whose preconditioner is two CG iterations on A z = r
+                                   from z = 0 (the "rougher") followed by the coarse correction of
+                                   their residual; no post-smoothing */
 
 /* rr_options.gram — how rr_setup forms the exact coarse Gram C^T C */
 enum { RR_GRAM_AUTO = 0,        /* tcgen05 tensor cores (FP16 counts, exact FP32 chunks) when
@@ -160,7 +164,9 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
 rr_status rr_set_lambda(rr_handle *h, double lambda);
 
 /* Solves Eq. (1) for one right-hand side by CG preconditioned as
- * rr_options.solver says, from w_0 = 0 (Algorithm 3's initialisation), until
+ * rr_options.solver says (RR_SOLVER_TLFCG: flexible CG, Algorithm 3 with
+ * m = 1, as rr_solve_fcg without a network), from w_0 = 0 (Algorithm 3's
+ * initialisation), until
  * the recurrence residual satisfies ||r|| <= tol ||X^T y||; then checks the
  * true residual and restarts on the correction while it is above tol
  * (at most max_restarts times).
@@ -214,7 +220,8 @@ rr_status rr_solve_batch(rr_handle *h, int32_t nrhs, const double *Y, int32_t nl
  * each must have been set up with use_graphs = 1 or 0 alike (the graph is
  * always used). infos: host rr_info[nprob] or NULL; solve_ms is the time of
  * the whole call. Returns RR_OK when every problem reached tol, else the
- * first failing status kind (RR_NOT_CONVERGED / RR_NONFINITE). Synchronises. */
+ * first failing status kind (RR_NOT_CONVERGED / RR_NONFINITE); RR_UNSUPPORTED
+ * if a handle's solver is RR_SOLVER_TLFCG. Synchronises. */
 rr_status rr_solve_many(int32_t nprob, rr_handle *const *hs, const double *const *ys,
                         double *const *ws, double tol, void *stream, rr_info *infos);
 

@@ -101,5 +101,10 @@ struct rr_handle {
   // rr_solve_fcg workspace (created on first use)
   double *p_prev = nullptr, *q_prev = nullptr, *part_zq = nullptr, *part3 = nullptr;
   rr::FcgScalars *Sf = nullptr, *Sf_host = nullptr;
+  // TLFCG rougher (two CG steps on A z = r): iterate, residual, direction, A direction, copy of r
+  double *tz = nullptr, *tr = nullptr, *tp = nullptr, *tq = nullptr, *tzz = nullptr;
+  double *t_rz = nullptr, *t_pq = nullptr, *t_rr = nullptr;
+  rr::PcgScalars *St = nullptr;
+  void *fcg_cache = nullptr;   // the FCG loop graph without a network (kept until lambda changes)
   DevArena mem;
 };

@@ -249,6 +249,23 @@ __global__ void k_pcg_start(const double *__restrict__ bb_part, int n_bb,
   }
 }
 
+// Scalars of a fixed number of plain CG steps run inside another solver's
+// iteration: a fresh start (first direction), no stopping target, and stopped
+// at once when the outer solver has converged.
+__global__ void k_inner_start(PcgScalars *S, const int32_t *__restrict__ outer_converged) {
+  pdl_wait();
+  if (threadIdx.x == 0) {
+    S->rho_old = 0.0;
+    S->rr = 0.0;
+    S->bnorm = 1.0;
+    S->target = 0.0;
+    S->iter = 0;
+    S->nonfinite = 0;
+    S->first = 1;
+    S->converged = *outer_converged;
+  }
+}
+
 __global__ void k_sum_parts(const double *__restrict__ part, int n, double *out) {
   pdl_wait();
   __shared__ double sm[kWarps + 1];
@@ -346,6 +363,11 @@ rr_status pcg_update(int64_t F, const double *rz_part, int n_rz, const double *p
                      cudaStream_t st, float *z1_32) {
   RR_LAUNCH_PDL(k_pcg_update, kVecGrid, kThreads, 0, st, F, rz_part, n_rz, pq_part, n_pq, p, q, w, r,
             omega, d, z1, z1_32, rr_part, S);
+  return RR_OK;
+}
+
+rr_status inner_start(PcgScalars *S, const int32_t *outer_converged, cudaStream_t st) {
+  RR_LAUNCH_PDL(k_inner_start, 1, 32, 0, st, S, outer_converged);
   return RR_OK;
 }
 

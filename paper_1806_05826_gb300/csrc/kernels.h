@@ -282,6 +282,9 @@ rr_status pcg_update(int64_t F, const double *rz_part, int n_rz, const double *p
                      const double *p, const double *q, double *w, double *r, double omega,
                      const double *d, double *z1, double *rr_part, PcgScalars *S,
                      cudaStream_t st, float *z1_32 = nullptr);
+// Fresh scalars for a fixed number of plain CG steps inside another solver's
+// iteration (no stopping target; stopped when *outer_converged).
+rr_status inner_start(PcgScalars *S, const int32_t *outer_converged, cudaStream_t st);
 // rr = sum(rr_part); rho_old = sum(rz_part); iter++; convergence and finiteness flags;
 // history[iter-1] = ||r|| / ||b|| when iter <= hist_cap.
 rr_status pcg_finish(const double *rz_part, int n_rz, const double *rr_part, int n_rr,

@@ -595,7 +595,10 @@ rr_status pcg_iteration(rr_handle *h, cudaStream_t st) {
   return RR_OK;
 }
 
+void drop_fcg_cache(rr_handle *h);
+
 void destroy_graph(rr_handle *h) {
+  drop_fcg_cache(h);
   if (h->loop_exec) cudaGraphExecDestroy(h->loop_exec);
   if (h->loop_graph) cudaGraphDestroy(h->loop_graph);
   h->loop_exec = nullptr;
@@ -781,7 +784,50 @@ rr_status fcg_tail(rr_handle *h, const int32_t *stop, bool fp32, cudaStream_t st
   return RR_OK;
 }
 
+rr_status tlfcg_reserve(rr_handle *h) {
+  if (h->St) return RR_OK;
+  for (double **v : {&h->tz, &h->tr, &h->tp, &h->tq, &h->tzz}) RR_TRY(h->mem.alloc(v, h->F));
+  for (double **v : {&h->t_rz, &h->t_pq, &h->t_rr}) RR_TRY(h->mem.alloc(v, rr::kVecGrid));
+  RR_TRY(h->mem.alloc(&h->St, 1));
+  return RR_OK;
+}
+
+// One TLFCG iteration: z = z1 + P A_c^-1 P^T r1 with (z1, r1) after two plain
+// CG steps on A z1 = r from z1 = 0 (the rougher), then the FCG(1) step. The
+// rougher's kernels stop when the outer loop has converged.
+rr_status tlfcg_iteration(rr_handle *h, cudaStream_t st) {
+  const bool fp32 = h->opt.precision == RR_PREC_MIXED;
+  const int64_t F = h->F;
+  const int32_t *stop = &h->Sf->converged;
+  const int32_t *istop = &h->St->converged;
+  RR_TRY(rr::inner_start(h->St, stop, st));
+  RR_TRY(rr::copy_f64(h->tr, h->r, F, st));
+  RR_CUDA(cudaMemsetAsync(h->tz, 0, sizeof(double) * F, st));
+  for (int j = 0; j < 2; ++j) {
+    RR_TRY(rr::jacobi(F, 1.0, h->tr, nullptr, h->tzz, h->t_rz, istop, st));
+    RR_TRY(rr::pcg_direction(F, h->t_rz, rr::kVecGrid, h->tzz, h->tp, h->St, st));
+    rr::CscEpilogue ap{rr::CSC_PCG, h->lambda, h->omega, h->tp, nullptr, nullptr, h->tq, h->t_pq, istop};
+    RR_TRY(op_apply(h, h->tp, ap, istop, st, fp32));
+    RR_TRY(rr::pcg_update(F, h->t_rz, rr::kVecGrid, h->t_pq, rr::kVecGrid, h->tp, h->tq, h->tz,
+                          h->tr, 1.0, nullptr, nullptr, h->t_rr, h->St, st));
+    RR_TRY(rr::pcg_finish(h->t_rz, rr::kVecGrid, h->t_rr, rr::kVecGrid, h->St, nullptr, 0, st));
+  }
+  RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->tr, stop, st));
+  RR_TRY(rr::coarse_matvec(h->k_eff, h->Ainv, h->rplan, h->s, nullptr, h->ec, stop, st));
+  RR_TRY(rr::prolong_add(F, h->labels, h->s, h->ec, h->tz, h->z, stop, st));
+  RR_TRY(rr::fcg_dot(F, h->z, h->q_prev, h->part_zq, stop, st));
+  RR_TRY(rr::fcg_direction(F, h->part_zq, h->Sf, h->z, h->p_prev, h->p, stop, st));
+  rr::CscEpilogue ap{rr::CSC_PCG, h->lambda, h->omega, h->p, nullptr, nullptr, h->q, h->part_pq, stop};
+  RR_TRY(op_apply(h, h->p, ap, stop, st, fp32));
+  RR_TRY(rr::fcg_dots(F, h->p, h->r, h->q, h->part3, stop, st));
+  RR_TRY(rr::fcg_update(h->F, h->part_pq, h->part3, h->p, h->q, h->w_int, h->r, h->omega, h->d,
+                        h->z1, h->p_prev, h->q_prev, h->part_rr, h->Sf, st));
+  RR_TRY(rr::fcg_finish(h->part_rr, h->part_pq, h->Sf, h->history, h->hist_cap, st));
+  return RR_OK;
+}
+
 rr_status fcg_iteration(rr_handle *h, const rr_mlp *net, cudaStream_t st) {
+  if (h->opt.solver == RR_SOLVER_TLFCG) return tlfcg_iteration(h, st);
   const bool fp32 = h->opt.precision == RR_PREC_MIXED;
   const int32_t *stop = &h->Sf->converged;
   // pre-smoothing (z1 from the previous update), restriction
@@ -817,6 +863,11 @@ struct GraphExec {
     if (g) cudaGraphDestroy(g);
   }
 };
+
+void drop_fcg_cache(rr_handle *h) {
+  delete static_cast<GraphExec *>(h->fcg_cache);
+  h->fcg_cache = nullptr;
+}
 
 rr_status build_fcg_graph(rr_handle *h, const rr_mlp *net, GraphExec &G) {
   RR_CUDA(cudaGraphCreate(&G.g, 0));
@@ -879,6 +930,7 @@ rr_status solve_fcg_impl(rr_handle *h, const rr_mlp *net, const double *y, doubl
   cudaStream_t st = h->st;
   const int64_t F = h->F;
   RR_TRY(fcg_reserve(h));
+  if (h->opt.solver == RR_SOLVER_TLFCG) RR_TRY(tlfcg_reserve(h));
   RR_TRY(rhs_apply(h, y, h->b, st));
   RR_CUDA(cudaMemsetAsync(h->w_int, 0, sizeof(double) * F, st));
   RR_CUDA(cudaMemsetAsync(h->p_prev, 0, sizeof(double) * F, st));
@@ -889,14 +941,33 @@ rr_status solve_fcg_impl(rr_handle *h, const rr_mlp *net, const double *y, doubl
   RR_TRY(rr::fcg_start(h->part_bb, rr::kVecGrid, h->part_bb, tol, 1, net ? 1 : 0, h->Sf, st));
   RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st));
 
+  // the graph is kept in the handle when no network is involved (a network's
+  // buffers may be freed between calls); set_lambda drops it
   GraphExec graph;
-  if (h->opt.use_graphs) RR_TRY(build_fcg_graph(h, net, graph));
+  GraphExec *G = nullptr;
+  if (h->opt.use_graphs) {
+    if (net) {
+      RR_TRY(build_fcg_graph(h, net, graph));
+      G = &graph;
+    } else {
+      if (!h->fcg_cache) {
+        GraphExec *c = new GraphExec();
+        const rr_status bs = build_fcg_graph(h, nullptr, *c);
+        if (bs != RR_OK) {
+          delete c;
+          return bs;
+        }
+        h->fcg_cache = c;
+      }
+      G = static_cast<GraphExec *>(h->fcg_cache);
+    }
+  }
   const int32_t max_iter = h->opt.max_iter;
   int32_t restarts = 0;
   double true_rr = 0.0;
   rr_status result = RR_OK;
   for (;;) {
-    RR_TRY(fcg_run(h, net, h->opt.use_graphs ? &graph : nullptr, max_iter));
+    RR_TRY(fcg_run(h, net, G, max_iter));
     const rr::FcgScalars Sh = *h->Sf_host;
     if (Sh.nonfinite) {
       rr_set_error("rr_solve_fcg: non-finite residual or dot product");
@@ -1149,6 +1220,10 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
     rr_set_error("rr_setup: unknown gather %d", opt.gather);
     return RR_INVALID_ARG;
   }
+  if (opt.solver < RR_SOLVER_TWOLEVEL || opt.solver > RR_SOLVER_TLFCG) {
+    rr_set_error("rr_setup: unknown solver %d", opt.solver);
+    return RR_INVALID_ARG;
+  }
   rr_handle *h = new rr_handle();
   h->opt = opt;
   h->opt.init_centers = nullptr;
@@ -1190,7 +1265,8 @@ rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info
   }
   const auto t0 = std::chrono::steady_clock::now();
   const int64_t l0 = rr_launch_counter;
-  rr_status s = solve_impl(h, y, w, tol, info);
+  rr_status s = h->opt.solver == RR_SOLVER_TLFCG ? solve_fcg_impl(h, nullptr, y, w, tol, info)
+                                                 : solve_impl(h, y, w, tol, info);
   if (s == RR_OK || s == RR_NOT_CONVERGED) {
     const rr_status e = check_dev_error(h, "rr_solve");
     if (e != RR_OK) s = e;
@@ -1267,6 +1343,10 @@ rr_status rr_solve_many(int32_t nprob, rr_handle *const *hs, const double *const
         rr_set_error("rr_solve_many: problems %d and %d share a handle", j, i);
         return RR_INVALID_ARG;
       }
+    if (hs[i]->opt.solver == RR_SOLVER_TLFCG) {
+      rr_set_error("rr_solve_many: problem %d uses RR_SOLVER_TLFCG (PCG solvers only)", i);
+      return RR_UNSUPPORTED;
+    }
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const auto t0 = std::chrono::steady_clock::now();

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "librr.so")
 RR_OK, RR_INVALID_ARG, RR_CUDA_ERROR, RR_OOM, RR_NOT_SPD = 0, 1, 2, 3, 4
 RR_NOT_CONVERGED, RR_NONFINITE, RR_TIMEOUT, RR_UNSUPPORTED = 5, 6, 7, 8
 RR_CSR_BINARY, RR_DENSE_F32_ROWMAJOR = 0, 1
-RR_SOLVER_TWOLEVEL, RR_SOLVER_CG, RR_SOLVER_DCG = 0, 1, 2
+RR_SOLVER_TWOLEVEL, RR_SOLVER_CG, RR_SOLVER_DCG, RR_SOLVER_TLFCG = 0, 1, 2, 3
 RR_PREC_FP64, RR_PREC_MIXED = 0, 1
 RR_GRAM_AUTO, RR_GRAM_CUDA_CORES = 0, 1
 RR_GATHER_AUTO, RR_GATHER_LANES, RR_GATHER_STAGED = 0, 1, 2
