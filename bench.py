@@ -54,14 +54,17 @@ def parse():
                     help="skip the learned coarse correction section (harvest, training, solves)")
     ap.add_argument("--no-graphs", action="store_true",
                     help="host-issued loops instead of CUDA graphs (every kernel visible to a profiler)")
-    ap.add_argument("--gather", default="auto", choices=["auto", "lanes", "staged"],
-                    help="FP32 gather kernel (auto: timed per pass at setup; the others force one)")
+    ap.add_argument("--gather", default="auto", choices=["auto", "lanes", "staged", "lanes-staged"],
+                    help="FP32 gather kernel (auto: timed per pass at setup; the others force one; "
+                         "lanes-staged: lanes for X, staged for X^T)")
     ap.add_argument("--only", choices=["batched", "many", "learned", "dense"],
                     help="run one extra section alone and print it (profiling runs)")
     ap.add_argument("--batch-targets", type=int, default=64,
                     help="targets of the batched section (64 in the workload definition)")
     ap.add_argument("--pairs", type=int, default=100_000,
                     help="training pairs of the learned section (100,000 in the workload definition)")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="one untimed step and nothing else (for a profiler's launch list)")
     ap.add_argument("--roofline-only", action="store_true",
                     help="one setup, then only the operator-apply kernel timings (profiling runs)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
@@ -482,7 +485,8 @@ def run_ours(args, rank, world, local):
     opts = dict(seed=p["seed"], stream=stream, precision=prec, max_restarts=20,
                 use_graphs=0 if args.no_graphs else 1,
                 gather={"auto": rr.RR_GATHER_AUTO, "lanes": rr.RR_GATHER_LANES,
-                        "staged": rr.RR_GATHER_STAGED}[args.gather])
+                        "staged": rr.RR_GATHER_STAGED,
+                        "lanes-staged": rr.RR_GATHER_LANES_STAGED}[args.gather])
 
     if args.roofline_only:
         return {"workload": args.workload, "precision": args.precision,
@@ -522,6 +526,12 @@ def run_ours(args, rank, world, local):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    if args.profile_step:
+        l0 = rr.rr_launch_count()
+        infos = step()
+        torch.cuda.synchronize(dev)
+        return {"profile_step": args.workload, "gpu_launches": rr.rr_launch_count() - l0,
+                "iters": [i["iters"] for i in infos]}
     for _ in range(max(3, args.warmup)):
         infos = step()
     for inf in infos:

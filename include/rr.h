@@ -65,7 +65,10 @@ enum { RR_GRAM_AUTO = 0,        /* tcgen05 tensor cores (FP16 counts, exact FP32
  * (both give identical bits: the same sums in the same order) */
 enum { RR_GATHER_AUTO = 0,      /* rr_setup times both on each pass of X and keeps the faster */
        RR_GATHER_LANES = 1,     /* each lane sums whole pieces, index words loaded by the lanes */
-       RR_GATHER_STAGED = 2 };  /* index words streamed through shared memory by bulk copies */
+       RR_GATHER_STAGED = 2,    /* index words streamed through shared memory by bulk copies */
+       RR_GATHER_LANES_STAGED = 3 };  /* lanes for the X pass, staged for the X^T pass (the usual
+                                   timed choice on Zipf-like data; fixed, e.g. under a profiler,
+                                   whose serialisation distorts the timing) */
 
 /* rr_options.precision */
 enum { RR_PREC_FP64 = 0,        /* every operator apply accumulates in FP64 */

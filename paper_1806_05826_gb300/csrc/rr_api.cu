@@ -501,8 +501,9 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(rr::sliced_build(N, F, h->row_ptr, h->col_idx, h->pcsr, h->err, st));
   RR_TRY(rr::sliced_build(F, N, h->col_ptr, h->row_idx, h->pcsc, h->err, st));
   if (h->opt.precision == RR_PREC_MIXED || h->opt.gather != RR_GATHER_AUTO) {
-    RR_TRY(rr::sliced_choose_gather(h->pcsr, h->opt.gather, st));
-    RR_TRY(rr::sliced_choose_gather(h->pcsc, h->opt.gather, st));
+    const bool split = h->opt.gather == RR_GATHER_LANES_STAGED;
+    RR_TRY(rr::sliced_choose_gather(h->pcsr, split ? RR_GATHER_LANES : h->opt.gather, st));
+    RR_TRY(rr::sliced_choose_gather(h->pcsc, split ? RR_GATHER_STAGED : h->opt.gather, st));
   }
   RR_TRY(alloc_solve_workspace(h));
   m.release(tmp32);
@@ -1216,7 +1217,7 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
     rr_set_error("rr_setup: kmeans_max_iter and max_iter must be positive");
     return RR_INVALID_ARG;
   }
-  if (opt.gather < RR_GATHER_AUTO || opt.gather > RR_GATHER_STAGED) {
+  if (opt.gather < RR_GATHER_AUTO || opt.gather > RR_GATHER_LANES_STAGED) {
     rr_set_error("rr_setup: unknown gather %d", opt.gather);
     return RR_INVALID_ARG;
   }

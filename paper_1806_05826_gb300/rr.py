@@ -21,7 +21,7 @@ RR_CSR_BINARY, RR_DENSE_F32_ROWMAJOR = 0, 1
 RR_SOLVER_TWOLEVEL, RR_SOLVER_CG, RR_SOLVER_DCG, RR_SOLVER_TLFCG = 0, 1, 2, 3
 RR_PREC_FP64, RR_PREC_MIXED = 0, 1
 RR_GRAM_AUTO, RR_GRAM_CUDA_CORES = 0, 1
-RR_GATHER_AUTO, RR_GATHER_LANES, RR_GATHER_STAGED = 0, 1, 2
+RR_GATHER_AUTO, RR_GATHER_LANES, RR_GATHER_STAGED, RR_GATHER_LANES_STAGED = 0, 1, 2, 3
 
 _STATUS = {0: "RR_OK", 1: "RR_INVALID_ARG", 2: "RR_CUDA_ERROR", 3: "RR_OOM", 4: "RR_NOT_SPD",
            5: "RR_NOT_CONVERGED", 6: "RR_NONFINITE", 7: "RR_TIMEOUT", 8: "RR_UNSUPPORTED"}

@@ -56,6 +56,10 @@ def test_default_options_and_invalid_args_without_gpu(lib):
     assert L.rr_setup(ctypes.byref(X), -1.0, 1, None, ctypes.byref(out)) == rr.RR_INVALID_ARG
     assert L.rr_setup(ctypes.byref(X), 1.0, 0, None, ctypes.byref(out)) == rr.RR_INVALID_ARG
     assert L.rr_setup(ctypes.byref(X), 1.0, 4, None, ctypes.byref(out)) == rr.RR_INVALID_ARG
+    o_bad = rr.rr_default_options(gather=4)
+    assert L.rr_setup(ctypes.byref(X), 1.0, 1, ctypes.byref(o_bad), ctypes.byref(out)) == rr.RR_INVALID_ARG
+    o_bad = rr.rr_default_options(solver=7)
+    assert L.rr_setup(ctypes.byref(X), 1.0, 1, ctypes.byref(o_bad), ctypes.byref(out)) == rr.RR_INVALID_ARG
     X.layout = 7
     assert L.rr_setup(ctypes.byref(X), 1.0, 1, None, ctypes.byref(out)) == rr.RR_INVALID_ARG
     # a dense X needs values and no CSR arrays

@@ -443,7 +443,7 @@ def test_gather_kernels_identical_bits(case, rr):
     mixed-precision operator and solves give identical bits with either."""
     X = case["X"]
     outs = []
-    for g in (rr.RR_GATHER_LANES, rr.RR_GATHER_STAGED):
+    for g in (rr.RR_GATHER_LANES, rr.RR_GATHER_STAGED, rr.RR_GATHER_LANES_STAGED):
         h = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, case["lam"], case["k"],
                         seed=case["seed"], precision=rr.RR_PREC_MIXED, gather=g)
         v = dev(synth.normal(3, 50, X.n_cols))
@@ -451,9 +451,12 @@ def test_gather_kernels_identical_bits(case, rr):
         rr.rr_apply(h, v, Av)
         w = torch.empty_like(v)
         info = rr.rr_solve(h, dev(case["y"]), w, tol=1e-8)
-        outs.append((Av.cpu().numpy(), w.cpu().numpy(), info["iters"]))
-    assert np.array_equal(outs[0][0], outs[1][0])
-    assert np.array_equal(outs[0][1], outs[1][1]) and outs[0][2] == outs[1][2]
+        outs.append((Av.cpu().numpy(), w.cpu().numpy(), info["iters"], info["gather_staged"]))
+    for o in outs[1:]:
+        assert np.array_equal(outs[0][0], o[0])
+        assert np.array_equal(outs[0][1], o[1]) and outs[0][2] == o[2]
+    # which kernel ran on each pass (bit 0: X, bit 1: X^T; staged needs its chunks to fit)
+    assert outs[0][3] == 0 and outs[2][3] & 1 == 0
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
