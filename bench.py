@@ -79,6 +79,18 @@ def dist_env():
     return rank, world, local
 
 
+def slowest_over_ranks(ms, world, device=None):
+    """The largest of the ranks' values (the slowest replica sets a step's time);
+    the value itself on one rank. Needs the process group when world > 1."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -552,11 +564,7 @@ def run_ours(args, rank, world, local):
     barrier()
     step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
     total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = slowest_over_ranks(total_ms, world, dev)
     value = total_ms / 1000.0 / args.steps
 
     roofline = measure_roofline(rr, row_ptr, col_idx, N, F, nnz, k, lams, opts, dev, stream,
@@ -578,7 +586,7 @@ def run_ours(args, rank, world, local):
             step(host)
         t1.record(stream)
         torch.cuda.synchronize(dev)
-        e_ms = t0.elapsed_time(t1) / args.steps
+        e_ms = slowest_over_ranks(t0.elapsed_time(t1) / args.steps, world, dev)
         e2e = {"value": round(e_ms / 1000.0, 5), "unit": "s",
                "h2d_bytes_per_step": 8 * (N + 1) + 4 * nnz + 8 * N,
                "d2h_bytes_per_step": 8 * F * len(lams)}
@@ -727,8 +735,8 @@ def run_reference(args, rank, world):
     X, y, _, p = synth.workload(args.workload)
     # iteration counts of the oracle's own two-level PCG are those of the
     # method; the GPU run records them, and so does a previous oracle run.
-    iters = [int(v) for v in os.environ.get("RR_REF_ITERS", "60,40,12").split(",")]
-    km_iters = int(os.environ.get("RR_REF_KMEANS_ITERS", "50"))
+    iters = [int(v) for v in os.environ.get("RR_REF_ITERS", "75,76,58").split(",")]
+    km_iters = int(os.environ.get("RR_REF_KMEANS_ITERS", "16"))
     vals, last = [], None
     for _ in range(args.steps):
         last = cpu_baseline(X, y, p, iters, km_iters, p["k"])
