@@ -60,9 +60,9 @@ def parse():
     ap.add_argument("--only", choices=["batched", "many", "learned", "dense"],
                     help="run one extra section alone and print it (profiling runs)")
     ap.add_argument("--batch-targets", type=int, default=64,
-                    help="targets of the batched section (64 in the workload definition)")
+                    help="targets of the batched section (64: the zipf_200000x100000_64x8 workload)")
     ap.add_argument("--pairs", type=int, default=100_000,
-                    help="training pairs of the learned section (100,000 in the workload definition)")
+                    help="training pairs of the learned section (100,000 by default)")
     ap.add_argument("--profile-step", action="store_true",
                     help="one untimed step and nothing else (for a profiler's launch list)")
     ap.add_argument("--roofline-only", action="store_true",
