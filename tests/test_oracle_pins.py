@@ -611,3 +611,23 @@ def test_harvest_pairs_first_two_iterations_closed_form():
     # vector seen through A: x = P^T A u, t = P^T u with u = w* - w - z1
     u0 = w_star - T.omega * b / np.diag(A)
     assert np.allclose(P.T @ (A @ u0), Xs[0], rtol=1e-10, atol=1e-12 * np.linalg.norm(b))
+
+
+def test_compact_drops_empty_clusters_in_order():
+    """Empty clusters are dropped and the others renumbered in their order."""
+    labels, n_S = km.compact(np.array([4, 1, 4, 7, 1, 4], np.int32))
+    assert labels.tolist() == [1, 0, 1, 2, 0, 1]
+    assert n_S.tolist() == [2, 3, 1]
+
+
+def test_with_lambda_equals_fresh_setup_with_same_clustering():
+    """Section 4: at another lambda only the coarse factor and the smoother
+    change; a fresh setup from the same initial centres gives the same."""
+    two, _ = _tiny_two_level(seed=9)
+    D = two.M.X.toarray()
+    n, f, rp, ci = csr_of(D)
+    other = two.with_lambda(0.5)
+    fresh = tl.setup_binary(n, f, rp, ci, 0.5, len(two.centers), centers=two.centers)
+    assert np.array_equal(other.labels, fresh.labels)
+    assert np.array_equal(other.Ac, fresh.Ac)
+    assert np.array_equal(other.d, fresh.d) and other.omega == fresh.omega
