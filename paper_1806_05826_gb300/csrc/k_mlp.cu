@@ -692,7 +692,10 @@ rr_status rr_mlp_create(int32_t k, int32_t hidden, int32_t max_batch, const floa
 }
 
 rr_status rr_mlp_set_params(rr_mlp *m, const float *params_host) {
-  if (!m || !params_host) return RR_INVALID_ARG;
+  if (!m || !params_host) {
+    rr_set_error("rr_mlp_set_params: NULL argument");
+    return RR_INVALID_ARG;
+  }
   std::vector<float> pad;
   to_padded(m, params_host, pad);
   RR_CUDA(cudaMemcpyAsync(m->P, pad.data(), sizeof(float) * m->n_params, cudaMemcpyHostToDevice, m->st));
@@ -702,7 +705,10 @@ rr_status rr_mlp_set_params(rr_mlp *m, const float *params_host) {
 }
 
 rr_status rr_mlp_get_params(const rr_mlp *m, float *params_host) {
-  if (!m || !params_host) return RR_INVALID_ARG;
+  if (!m || !params_host) {
+    rr_set_error("rr_mlp_get_params: NULL argument");
+    return RR_INVALID_ARG;
+  }
   std::vector<float> pad(m->n_params);
   RR_CUDA(cudaMemcpyAsync(pad.data(), m->P, sizeof(float) * m->n_params, cudaMemcpyDeviceToHost, m->st));
   RR_CUDA(cudaStreamSynchronize(m->st));
@@ -715,7 +721,10 @@ int64_t rr_mlp_param_count(int32_t k, int32_t hidden) {
 }
 
 rr_status rr_mlp_forward(rr_mlp *m, int32_t B, const float *X, float *out) {
-  if (!m || !X || !out || B < 1 || B > m->max_batch) return RR_INVALID_ARG;
+  if (!m || !X || !out || B < 1 || B > m->max_batch) {
+    rr_set_error("rr_mlp_forward: NULL argument or batch outside [1, max_batch]");
+    return RR_INVALID_ARG;
+  }
   const int32_t Bp = round128(B);
   RR_TRY(pack_rows(m, B, nullptr, X, nullptr, 0));
   RR_TRY(forward(m, Bp));
@@ -726,7 +735,10 @@ rr_status rr_mlp_forward(rr_mlp *m, int32_t B, const float *X, float *out) {
 
 rr_status rr_mlp_grad(rr_mlp *m, int32_t B, const float *X, const float *T, float *grads_host,
                       float *loss_host) {
-  if (!m || !X || !T || B < 1 || B > m->max_batch) return RR_INVALID_ARG;
+  if (!m || !X || !T || B < 1 || B > m->max_batch) {
+    rr_set_error("rr_mlp_grad: NULL argument or batch outside [1, max_batch]");
+    return RR_INVALID_ARG;
+  }
   const int32_t Bp = round128(B);
   RR_TRY(pack_rows(m, B, nullptr, X, T, 0));
   RR_TRY(forward(m, Bp));

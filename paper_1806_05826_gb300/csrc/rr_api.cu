@@ -1244,7 +1244,10 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
 }
 
 rr_status rr_set_lambda(rr_handle *h, double lambda) {
-  if (!h) return RR_INVALID_ARG;
+  if (!h) {
+    rr_set_error("rr_set_lambda: NULL handle");
+    return RR_INVALID_ARG;
+  }
   if (!(lambda > 0.0) || !isfinite(lambda)) {
     rr_set_error("rr_set_lambda: lambda must be positive and finite");
     return RR_INVALID_ARG;
@@ -1353,9 +1356,11 @@ rr_status rr_solve_many(int32_t nprob, rr_handle *const *hs, const double *const
   const auto t0 = std::chrono::steady_clock::now();
   const int64_t l0 = rr_launch_counter;
   // every problem's work is issued on `stream` for the duration of the call
+  // (every handle's own stream is drained before any handle is switched, so
+  // that an error return leaves all handles on their own streams)
+  for (int32_t i = 0; i < nprob; ++i) RR_CUDA(cudaStreamSynchronize(hs[i]->st));
   std::vector<cudaStream_t> saved(nprob);
   for (int32_t i = 0; i < nprob; ++i) {
-    RR_CUDA(cudaStreamSynchronize(hs[i]->st));
     saved[i] = hs[i]->st;
     hs[i]->st = st;
   }
@@ -1374,21 +1379,30 @@ rr_status rr_solve_many(int32_t nprob, rr_handle *const *hs, const double *const
 }
 
 rr_status rr_apply(rr_handle *h, const double *v, double *out) {
-  if (!h || !v || !out || v == out) return RR_INVALID_ARG;
+  if (!h || !v || !out || v == out) {
+    rr_set_error("rr_apply: NULL argument, or v and out alias");
+    return RR_INVALID_ARG;
+  }
   rr::CscEpilogue ep{rr::CSC_APPLY, h->lambda, h->omega, v, nullptr, nullptr, out, nullptr, nullptr};
   RR_TRY(op_apply(h, v, ep, nullptr, h->st, h->opt.precision == RR_PREC_MIXED));
   return RR_OK;
 }
 
 rr_status rr_precondition(rr_handle *h, const double *r, double *z) {
-  if (!h || !r || !z || r == z) return RR_INVALID_ARG;
+  if (!h || !r || !z || r == z) {
+    rr_set_error("rr_precondition: NULL argument, or r and z alias");
+    return RR_INVALID_ARG;
+  }
   int n = 0;
   RR_TRY(apply_precond(h, r, z, nullptr, &n, false, h->st));
   return RR_OK;
 }
 
 rr_status rr_rhs(rr_handle *h, const double *y, double *b) {
-  if (!h || !y || !b) return RR_INVALID_ARG;
+  if (!h || !y || !b) {
+    rr_set_error("rr_rhs: NULL argument");
+    return RR_INVALID_ARG;
+  }
   rr::CscEpilogue ep{rr::CSC_RHS, 0.0, 0.0, nullptr, nullptr, nullptr, b, nullptr, nullptr};
   if (h->dense)
     return rr::dense_transposed(h->N, h->F, h->Xd, y, h->dpart, ep,
@@ -1399,7 +1413,10 @@ rr_status rr_rhs(rr_handle *h, const double *y, double *b) {
 }
 
 rr_status rr_matvec(rr_handle *h, const double *v, double *u) {
-  if (!h || !v || !u) return RR_INVALID_ARG;
+  if (!h || !v || !u) {
+    rr_set_error("rr_matvec: NULL argument");
+    return RR_INVALID_ARG;
+  }
   if (h->dense)
     return rr::dense_matvec(h->N, h->F, h->Xd, v, u, nullptr, h->opt.precision == RR_PREC_MIXED,
                             h->st);
@@ -1409,21 +1426,30 @@ rr_status rr_matvec(rr_handle *h, const double *v, double *u) {
 }
 
 rr_status rr_get_labels(const rr_handle *h, int32_t *labels_host) {
-  if (!h || !labels_host) return RR_INVALID_ARG;
+  if (!h || !labels_host) {
+    rr_set_error("rr_get_labels: NULL argument");
+    return RR_INVALID_ARG;
+  }
   RR_CUDA(cudaMemcpyAsync(labels_host, h->labels, sizeof(int32_t) * h->F, cudaMemcpyDeviceToHost, h->st));
   RR_CUDA(cudaStreamSynchronize(h->st));
   return RR_OK;
 }
 
 rr_status rr_get_centers(const rr_handle *h, int32_t *centers_host) {
-  if (!h || !centers_host) return RR_INVALID_ARG;
+  if (!h || !centers_host) {
+    rr_set_error("rr_get_centers: NULL argument");
+    return RR_INVALID_ARG;
+  }
   RR_CUDA(cudaMemcpyAsync(centers_host, h->centers, sizeof(int32_t) * h->k_req, cudaMemcpyDeviceToHost, h->st));
   RR_CUDA(cudaStreamSynchronize(h->st));
   return RR_OK;
 }
 
 rr_status rr_get_coarse(const rr_handle *h, double *Ac_host, int64_t *G_host) {
-  if (!h) return RR_INVALID_ARG;
+  if (!h) {
+    rr_set_error("rr_get_coarse: NULL handle");
+    return RR_INVALID_ARG;
+  }
   if (h->dense && G_host) {
     rr_set_error("rr_get_coarse: the integer Gram exists for binary X only");
     return RR_UNSUPPORTED;
@@ -1444,7 +1470,10 @@ rr_status rr_get_coarse(const rr_handle *h, double *Ac_host, int64_t *G_host) {
 
 rr_status rr_query(const rr_handle *h, int64_t *n_rows, int64_t *n_cols, int32_t *k_eff,
                    double *omega, double *lambda) {
-  if (!h) return RR_INVALID_ARG;
+  if (!h) {
+    rr_set_error("rr_query: NULL handle");
+    return RR_INVALID_ARG;
+  }
   if (n_rows) *n_rows = h->N;
   if (n_cols) *n_cols = h->F;
   if (k_eff) *k_eff = h->k_eff;
