@@ -284,9 +284,10 @@ MANY_WORKLOADS = {"uneven_12": dict(n_problems=12, n=(10_000, 100_000), d=(5_000
                                            n_dense=4, dense=(50_000, 4_000), rho=0.9)}
 
 
-def many_workload(name: str):
-    """[(X, y, params)] of a named set of independent problems (X a CSR
-    pattern, or a dense float32 array when params["dense"])."""
+def many_params(name: str):
+    """The parameters of each problem of a named set of independent problems:
+    n, d and density drawn uniformly in their ranges from seed i (binary
+    problems), then the dense problems; k = max(2, d // 100)."""
     p = MANY_WORKLOADS[name]
     out = []
     for i in range(p["n_problems"]):
@@ -294,16 +295,25 @@ def many_workload(name: str):
         n = int(p["n"][0] + u[0] * (p["n"][1] - p["n"][0]))
         d = int(p["d"][0] + u[1] * (p["d"][1] - p["d"][0]))
         dens = p["density"][0] + u[2] * (p["density"][1] - p["density"][0])
-        X = zipf_binary(n, d, dens, 1.1, i)
-        y, _ = ridge_targets(X, i)
-        out.append((X, y, dict(n=n, d=d, density=dens, k=max(2, d // 100), lam=p["lam"], seed=i)))
+        out.append(dict(n=n, d=d, density=dens, k=max(2, d // 100), lam=p["lam"], seed=i))
     for j in range(p.get("n_dense", 0)):
-        i = p["n_problems"] + j
         n, d = p["dense"]
-        X = dense_ar1(n, d, p["rho"], i)
-        y, _ = ridge_targets(X, i)
-        out.append((X, y, dict(n=n, d=d, density=1.0, k=max(2, d // 100), lam=p["lam"], seed=i,
-                               dense=True)))
+        out.append(dict(n=n, d=d, density=1.0, k=max(2, d // 100), lam=p["lam"],
+                        seed=p["n_problems"] + j, dense=True, rho=p["rho"]))
+    return out
+
+
+def many_workload(name: str):
+    """[(X, y, params)] of a named set of independent problems (X a CSR
+    pattern, or a dense float32 array when params["dense"])."""
+    out = []
+    for q in many_params(name):
+        if q.get("dense"):
+            X = dense_ar1(q["n"], q["d"], q["rho"], q["seed"])
+        else:
+            X = zipf_binary(q["n"], q["d"], q["density"], 1.1, q["seed"])
+        y, _ = ridge_targets(X, q["seed"])
+        out.append((X, y, q))
     return out
 
 
