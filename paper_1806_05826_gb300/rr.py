@@ -2,8 +2,8 @@
 
 Every computation happens in librr.so's CUDA kernels. Device vectors are
 torch CUDA tensors (FP64) passed by pointer on the current torch stream.
-Importing this module without a built librr.so raises at once: there is no
-fallback path.
+Without a built librr.so every call raises at once (the first one loads the
+library): there is no fallback path.
 """
 from __future__ import annotations
 
