@@ -326,12 +326,11 @@ def measure_dense_only(rr, dev, stream, opts):
     rho = 0.9, seed 12, k = 40): setup, then the dense operator apply."""
     import torch
     from gen import synth
-    p = synth.MANY_WORKLOADS["uneven_12_dense4"]
-    n, f = p["dense"]
-    X = synth.dense_ar1(n, f, p["rho"], p["n_problems"])
+    p = next(q for q in synth.many_params("uneven_12_dense4") if q.get("dense"))
+    n, f = p["n"], p["d"]
+    X = synth.dense_ar1(n, f, p["rho"], p["seed"])
     o = {key: v for key, v in opts.items() if key not in ("gram", "gather", "seed")}
-    h = rr.rr_setup_dense(torch.as_tensor(X, device=dev), p["lam"], max(2, f // 100),
-                          seed=p["n_problems"], **o)
+    h = rr.rr_setup_dense(torch.as_tensor(X, device=dev), p["lam"], p["k"], seed=p["seed"], **o)
     out = measure_dense_apply(rr, h, n, f, dev, stream)
     rr.rr_free(h)
     return out
