@@ -83,7 +83,7 @@ enum { RR_PREC_FP64 = 0,        /* every operator apply accumulates in FP64 */
  *  CSR_BINARY: row_ptr int64[N+1] (row_ptr[0] = 0, non-decreasing,
  *    row_ptr[N] = nnz) and col_idx int32[nnz], strictly increasing within each
  *    row, each in [0, F). values must be NULL.
- *  DENSE_F32_ROWMAJOR: values float[N*F], row-major; row_ptr/col_idx NULL;
+ *  DENSE_F32_ROWMAJOR: values float[N*F], row-major; row_ptr/col_idx NULL; nnz ignored;
  *    N*F < 2^34, N <= 4,194,240 and F <= 25600 (the operator stages a whole
  *    vector of F FP64 values in shared memory), else RR_UNSUPPORTED. The clustering runs in
  *    FP64 on the FP32 values (row sums in blocks of 64 rows, ascending).

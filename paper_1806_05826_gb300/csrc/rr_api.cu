@@ -1199,8 +1199,9 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
     rr_set_error("rr_setup: k must be in [1, F]");
     return RR_INVALID_ARG;
   }
-  if (X->nnz >= (1LL << 31) || X->n_rows >= (1LL << 31) || X->n_cols >= (1LL << 31)) {
-    rr_set_error("rr_setup: nnz, N and F must be below 2^31");
+  if ((X->layout == RR_CSR_BINARY && X->nnz >= (1LL << 31)) || X->n_rows >= (1LL << 31) ||
+      X->n_cols >= (1LL << 31)) {
+    rr_set_error("rr_setup: nnz (CSR), N and F must be below 2^31");
     return RR_UNSUPPORTED;
   }
   if (k > 16384) {
