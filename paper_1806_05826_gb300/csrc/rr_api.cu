@@ -1068,10 +1068,17 @@ rr_status solve_many_impl(int32_t n, rr_handle *const *hs, const double *const *
   ManyGraph G;
   std::vector<int64_t> body;
   RR_TRY(build_many_graph(n, hs, G, body));
+  static const int32_t kStopped = 1;
   for (;;) {
     std::vector<int32_t> it0(n);
     for (int32_t i = 0; i < n; ++i) {
       rr_handle *h = hs[i];
+      // a while node runs its body once per launch before testing the
+      // condition: a finished problem that stopped on its iteration cap is
+      // marked converged so that a relaunch for the others leaves it as it is
+      if (done[i] && !h->S_host->converged)
+        RR_CUDA(cudaMemcpyAsync(&h->S->converged, &kStopped, sizeof(int32_t),
+                                cudaMemcpyHostToDevice, st));
       *h->limit_host = h->opt.max_iter;
       RR_CUDA(cudaMemcpyAsync(&h->S->limit, h->limit_host, sizeof(int32_t), cudaMemcpyHostToDevice, st));
       RR_CUDA(cudaMemcpyAsync(h->S_host, h->S, sizeof(rr::PcgScalars), cudaMemcpyDeviceToHost, st));

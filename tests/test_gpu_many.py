@@ -77,3 +77,29 @@ def test_many_rejects_shared_handles(many, rr):
     w = torch.empty(p["X"].n_cols, dtype=torch.float64, device="cuda")
     with pytest.raises(rr.RRError):
         rr.rr_solve_many([p["h"], p["h"]], [dev(p["y"])] * 2, [w, w], tol=1e-8)
+
+
+def test_capped_problem_keeps_its_cap_when_others_restart(rr):
+    """A problem that stops on its iteration cap is left as it is while the
+    graph is relaunched for the refinement restarts of the others: its
+    iterate and count equal those of rr_solve with the same cap."""
+    hs, ys, ws, Xs = [], [], [], []
+    for j, (n, d, dens, seed) in enumerate(PROBLEMS[:2]):
+        X = synth.zipf_binary(n, d, dens, 1.1, seed)
+        y, _ = synth.ridge_targets(X, 100 + seed)
+        hs.append(rr.rr_setup(X.row_ptr, X.col_idx, n, d, 1e-2, max(2, d // 100), seed=seed,
+                              precision=rr.RR_PREC_MIXED, max_restarts=20,
+                              max_iter=5 if j == 0 else 20000))
+        ys.append(dev(y))
+        ws.append(torch.empty(d, dtype=torch.float64, device="cuda"))
+        Xs.append(X)
+    out = rr.rr_solve_many(hs, ys, ws, tol=1e-8)
+    capped, free = out["infos"]
+    assert out["status"] == "RR_NOT_CONVERGED"
+    assert capped["iters"] == 5 and free["true_rel_res"] <= 1e-8
+    w = torch.empty(Xs[0].n_cols, dtype=torch.float64, device="cuda")
+    single = rr.rr_solve(hs[0], ys[0], w, tol=1e-8)
+    assert single["status"] == "RR_NOT_CONVERGED" and single["iters"] == 5
+    assert np.array_equal(w.cpu().numpy(), ws[0].cpu().numpy())
+    if free["restarts"] == 0:
+        pytest.skip("the uncapped problem took no restart, so the graph was not relaunched")
