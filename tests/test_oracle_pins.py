@@ -631,3 +631,58 @@ def test_with_lambda_equals_fresh_setup_with_same_clustering():
     assert np.array_equal(other.labels, fresh.labels)
     assert np.array_equal(other.Ac, fresh.Ac)
     assert np.array_equal(other.d, fresh.d) and other.omega == fresh.omega
+
+
+def test_coarse_counts_and_integer_gram_by_brute_force():
+    """Section 3.2: C = X onehot(labels) counts a row's features per cluster and
+    G = C^T C (X_c = X P = C D_s); checked by loops over Python integers, and
+    by the invariant sum_{S,T} G[S,T] = sum_r (row length)^2."""
+    D = random_binary(23, 17, 0.35, 8)
+    n, f, rp, ci = csr_of(D)
+    labels = np.array([2, 0, 1, 2, 3, 0, 1, 1, 3, 2, 0, 3, 1, 2, 0, 0, 3], np.int32)
+    k = 4
+    C = tl.coarse_counts(n, f, rp, ci, labels, k).toarray()
+    G = tl.coarse_gram_binary(n, f, rp, ci, labels, k)
+    Cb = [[sum(int(D[r, j]) for j in range(f) if labels[j] == S) for S in range(k)]
+          for r in range(n)]
+    Gb = [[sum(Cb[r][S] * Cb[r][T] for r in range(n)) for T in range(k)] for S in range(k)]
+    assert C.tolist() == Cb
+    assert G.dtype == np.int64 and G.tolist() == Gb
+    assert int(G.sum()) == int((D.sum(axis=1) ** 2).sum())
+
+
+def test_gershgorin_rowsums_by_brute_force():
+    """Section 3.1's damping bound uses the row sums of |X^T X|, here summed
+    entry by entry from the dense product, for binary and signed dense X."""
+    D = random_binary(15, 9, 0.4, 9)
+    M = osp.from_csr(*csr_of(D))
+    A = D.T @ D
+    assert np.array_equal(osp.gershgorin_rowsums(M), np.abs(A).sum(axis=1).astype(float))
+    Xd = np.random.default_rng(2).standard_normal((12, 7))
+    Md = osp.from_dense(Xd)
+    brute = [sum(abs(sum(Xd[r, i] * Xd[r, j] for r in range(12))) for j in range(7))
+             for i in range(7)]
+    # |X|^T |X| 1 bounds the row sums of |X^T X| from above (equal for X >= 0)
+    assert np.all(osp.gershgorin_rowsums(Md) >= np.array(brute) - 1e-12)
+
+
+def test_triangular_solves_against_library():
+    """Section 4's coarse solve as two triangular solves, checked against
+    scipy.linalg.solve_triangular."""
+    from scipy.linalg import solve_triangular
+    rng = np.random.default_rng(11)
+    L = np.tril(rng.standard_normal((12, 12))) + 6 * np.eye(12)
+    b = rng.standard_normal(12)
+    assert np.allclose(tl.forward_sub(L, b), solve_triangular(L, b, lower=True), rtol=1e-13)
+    assert np.allclose(tl.back_sub_t(L, b), solve_triangular(L.T, b, lower=False), rtol=1e-13)
+
+
+def test_dense_matrix_products_match_numpy():
+    """Eq. (1)'s operator for a dense X: X v, X^T u and (X^T X + lambda I) v."""
+    rng = np.random.default_rng(12)
+    Xd = rng.standard_normal((9, 5))
+    M = osp.from_dense(Xd)
+    v, u = rng.standard_normal(5), rng.standard_normal(9)
+    assert np.allclose(osp.X_mv(M, v), Xd @ v, rtol=1e-14)
+    assert np.allclose(osp.Xt_mv(M, u), Xd.T @ u, rtol=1e-14)
+    assert np.allclose(osp.apply_A(M, 0.2, v), (Xd.T @ Xd + 0.2 * np.eye(5)) @ v, rtol=1e-13)
