@@ -574,9 +574,17 @@ def test_adam_first_step_is_lr_times_sign():
 
 
 def test_learned_correction_positively_homogeneous():
+    """e_c = ||r_c|| net(r_c / ||r_c||) scales with r_c even though the network
+    itself does not (nonzero biases: a bias-free ReLU network would be
+    homogeneous on its own and hide a missing rescaling)."""
     rng = np.random.default_rng(12)
     p = mlp.init_params(5, 4, lambda n: rng.random(n))
+    for name in ("b1", "b2", "b3"):
+        p[name] = 0.3 * rng.standard_normal(p[name].shape)
     rc = rng.standard_normal(5)
+    o1, _ = mlp.forward(p, rc[None, :])
+    o2, _ = mlp.forward(p, 3.5 * rc[None, :])
+    assert not np.allclose(o2, 3.5 * o1)          # the network alone is not homogeneous
     assert np.allclose(mlp.coarse_correction(p, 3.5 * rc), 3.5 * mlp.coarse_correction(p, rc))
 
 
