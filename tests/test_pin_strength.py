@@ -232,8 +232,27 @@ def _harvest_target_without_smoothing(mp):
     mp.setattr(learned, "harvest_pairs", bad)
 
 
+def _dense_seeding_uniform(mp):
+    def uniform(X, k, seed):
+        return np.random.default_rng(seed).choice(np.shape(X)[1], size=k,
+                                                  replace=False).astype(np.int32)
+    mp.setattr(km, "kmeanspp_dense", uniform)
+
+
+def _dense_coarse_operator_with_averaging(mp):
+    def bad(X, labels, s, lam):
+        n_S = np.rint(1.0 / s ** 2).astype(np.int64)
+        Xc = X @ tl.averaging_dense(labels, n_S)     # the mistake: P~ (1/n_S) in place of P
+        return Xc.T @ Xc + lam * np.eye(len(s))
+    mp.setattr(tl, "coarse_operator_dense", bad)
+
+
 P = pins
 CASES = [
+    ("dense seeding uniform instead of D^2", _dense_seeding_uniform,
+     [P.test_kmeanspp_dense_draw_follows_d2_weights]),
+    ("dense coarse operator from the averaging operator", _dense_coarse_operator_with_averaging,
+     [lambda: P.test_galerkin_coarse_operator(0)]),
     ("FCG without A-orthogonalisation", _fcg_without_orthogonalisation,
      [P.test_fcg_truncation_rule, P.test_fcg_matches_pcg_for_fixed_spd_preconditioner]),
     ("harvest target without the smoothing step", _harvest_target_without_smoothing,
@@ -273,7 +292,7 @@ CASES = [
     ("Lloyd stops after one step", _lloyd_one_step,
      [P.test_lloyd_fixed_point_at_exit, lambda: P.test_lloyd_matches_brute_force(0)]),
     ("dense Lloyd stops after one step", _lloyd_dense_one_step,
-     [lambda: P.test_lloyd_dense_matches_exact_arithmetic(0)]),
+     [lambda: P.test_lloyd_dense_matches_exact_arithmetic(0), P.test_dense_kmeans_recovers_groups]),
     ("seeding uniform instead of D^2", _seeding_uniform,
      [P.test_kmeanspp_picks_other_group, P.test_kmeanspp_draw_follows_d2_weights]),
     ("compaction reverses the cluster order", _compact_reversed,
