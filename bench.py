@@ -726,16 +726,42 @@ def cpu_baseline(X, y, p, iters, kmeans_iters, k_eff, quiet=False):
             "parts_s": {k2: round(v, 4) for k2, v in r["parts"].items()}}
 
 
+# Lloyd steps and PCG iterations per lambda of the bench workload, as its GPU
+# runs record them (the oracle's own two-level PCG takes the same counts up to
+# rounding); the oracle counts them itself on workloads small enough to solve.
+REF_COUNTS = {"zipf_200000x100000": ([75, 76, 58], 16)}
+
+
+def oracle_counts(X, y, p):
+    """PCG iterations per lambda and Lloyd steps of the oracle's full solve."""
+    from oracle import krylov, twolevel
+    from oracle import sparse as osp
+    two = twolevel.setup_binary(X.n_rows, X.n_cols, X.row_ptr, X.col_idx, p["lambdas"][0], p["k"],
+                                seed=p["seed"])
+    b = osp.rhs(two.M, y)
+    iters = []
+    for lam in p["lambdas"]:
+        t = two if lam == two.lam else two.with_lambda(lam)
+        iters.append(krylov.pcg(t.A, t.apply, b, tol=TOL).iters)
+    return iters, two.kmeans_iters
+
+
 def run_reference(args, rank, world):
     """The oracle arm: each timed step re-measures the bounded sample."""
     if rank != 0:
         return None
     from gen import synth
     X, y, _, p = synth.workload(args.workload)
-    # iteration counts of the oracle's own two-level PCG are those of the
-    # method; the GPU run records them, and so does a previous oracle run.
-    iters = [int(v) for v in os.environ.get("RR_REF_ITERS", "75,76,58").split(",")]
-    km_iters = int(os.environ.get("RR_REF_KMEANS_ITERS", "16"))
+    if "RR_REF_ITERS" in os.environ:
+        iters = [int(v) for v in os.environ["RR_REF_ITERS"].split(",")]
+        km_iters = int(os.environ.get("RR_REF_KMEANS_ITERS", "16"))
+        source = "RR_REF_ITERS"
+    elif args.workload in REF_COUNTS:
+        iters, km_iters = REF_COUNTS[args.workload]
+        source = "recorded GPU runs"
+    else:
+        iters, km_iters = oracle_counts(X, y, p)
+        source = "oracle solve"
     vals, last = [], None
     for _ in range(args.steps):
         last = cpu_baseline(X, y, p, iters, km_iters, p["k"])
@@ -746,7 +772,8 @@ def run_reference(args, rank, world):
             "ms_per_step": round(v * 1000, 1), "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "k": p["k"], "lambdas": list(p["lambdas"]),
-                       "tol": TOL, "iters_assumed": iters, "kmeans_iters_assumed": km_iters},
+                       "tol": TOL, "iters_assumed": iters, "kmeans_iters_assumed": km_iters,
+                       "counts_from": source},
             "cpu_baseline": dict(last, value=round(v, 3)),
             "e2e": {"value": round(v, 3), "unit": "s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
