@@ -149,6 +149,28 @@ def _ptr(t):
     return t.data_ptr()
 
 
+def _dev(t, dtype, n, name, device="cuda"):
+    """Device pointer of a contiguous CUDA tensor of `dtype` holding at least
+    n elements. Anything else raises here, before the library could read or
+    write past a buffer or treat a host address as a device one."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.device.type != device:
+        raise TypeError(f"{name}: a {device.upper()} tensor is required, got {type(t).__name__}"
+                        + ("" if not isinstance(t, torch.Tensor) else f" on {t.device}"))
+    if t.dtype != dtype:
+        raise TypeError(f"{name}: dtype {t.dtype}, {dtype} required")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: a contiguous tensor is required")
+    if t.numel() < n:
+        raise ValueError(f"{name}: {t.numel()} elements, at least {n} required")
+    return t.data_ptr()
+
+
+def _torch():
+    import torch
+    return torch
+
+
 def _stream_ptr(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -166,9 +188,9 @@ def rr_default_options(**kw) -> rr_options:
 class Handle:
     """Owns an rr_handle; the functions below take it as their first argument."""
 
-    def __init__(self, ptr, F, N, keepalive):
+    def __init__(self, ptr, F, N, keepalive, k=None):
         self.ptr = ptr
-        self.F, self.N = F, N
+        self.F, self.N, self.k = F, N, k
         self.dense = False
         self._keep = keepalive
 
@@ -188,13 +210,23 @@ def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=N
              stream=None) -> Handle:
     """rr_setup on a binary CSR pattern given as numpy arrays (host) or torch
     CUDA tensors (device): row_ptr int64[N+1], col_idx int32[nnz]."""
-    lib = load()
     on_device = 0 if isinstance(row_ptr, np.ndarray) else 1
     if on_device == 0:
         row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
         col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
-    X = rr_matrix(n_rows, n_cols, int(row_ptr[-1]) if on_device == 0 else int(col_idx.numel()),
-                  _ptr(row_ptr), _ptr(col_idx), None, RR_CSR_BINARY, on_device)
+        if row_ptr.ndim != 1 or row_ptr.size != n_rows + 1:
+            raise ValueError(f"row_ptr: {row_ptr.size} entries, n_rows + 1 = {n_rows + 1} required")
+        nnz = int(row_ptr[-1])
+        if col_idx.size < nnz:
+            raise ValueError(f"col_idx: {col_idx.size} entries, row_ptr[-1] = {nnz} required")
+        rp, ci = _ptr(row_ptr), _ptr(col_idx)
+    else:
+        torch = _torch()
+        rp = _dev(row_ptr, torch.int64, n_rows + 1, "row_ptr")
+        ci = _dev(col_idx, torch.int32, 0, "col_idx")
+        nnz = int(col_idx.numel())
+    lib = load()
+    X = rr_matrix(n_rows, n_cols, nnz, rp, ci, None, RR_CSR_BINARY, on_device)
     ic = None
     if init_centers is not None:
         ic = np.ascontiguousarray(init_centers, dtype=np.int32)
@@ -205,7 +237,7 @@ def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=N
                            precision=precision, stream=_stream_ptr(stream))
     out = _P()
     _check(lib.rr_setup(ctypes.byref(X), float(lam), int(k), ctypes.byref(o), ctypes.byref(out)))
-    return Handle(out, n_cols, n_rows, (ic,))
+    return Handle(out, n_cols, n_rows, (ic,), int(k))
 
 
 def rr_setup_dense(X, lam, k, *, seed=0, init_centers=None, kmeans_max_iter=50, max_iter=20000,
@@ -213,12 +245,15 @@ def rr_setup_dense(X, lam, k, *, seed=0, init_centers=None, kmeans_max_iter=50, 
                    precision=RR_PREC_FP64, stream=None) -> Handle:
     """rr_setup on a dense X (N x F, float32 row-major) given as a numpy array
     (host) or a torch CUDA tensor (device)."""
-    lib = load()
     on_device = 0 if isinstance(X, np.ndarray) else 1
     if on_device == 0:
         X = np.ascontiguousarray(X, dtype=np.float32)
+    if X.ndim != 2:
+        raise ValueError("X: a two-dimensional (N, F) array is required")
     n_rows, n_cols = int(X.shape[0]), int(X.shape[1])
-    M = rr_matrix(n_rows, n_cols, n_rows * n_cols, None, None, _ptr(X), RR_DENSE_F32_ROWMAJOR,
+    xp = _ptr(X) if on_device == 0 else _dev(X, _torch().float32, n_rows * n_cols, "X")
+    lib = load()
+    M = rr_matrix(n_rows, n_cols, n_rows * n_cols, None, None, xp, RR_DENSE_F32_ROWMAJOR,
                   on_device)
     ic = None
     if init_centers is not None:
@@ -229,7 +264,7 @@ def rr_setup_dense(X, lam, k, *, seed=0, init_centers=None, kmeans_max_iter=50, 
                            precision=precision, stream=_stream_ptr(stream))
     out = _P()
     _check(lib.rr_setup(ctypes.byref(M), float(lam), int(k), ctypes.byref(o), ctypes.byref(out)))
-    h = Handle(out, n_cols, n_rows, (ic,))
+    h = Handle(out, n_cols, n_rows, (ic,), int(k))
     h.dense = True
     return h
 
@@ -239,8 +274,10 @@ def rr_set_lambda(h: Handle, lam: float):
 
 
 def rr_solve(h: Handle, y, w, tol=1e-8) -> dict:
+    f64 = _torch().float64
+    yp, wp = _dev(y, f64, h.N, "y"), _dev(w, f64, h.F, "w")
     info = rr_info()
-    st = load().rr_solve(h.ptr, _ptr(y), _ptr(w), float(tol), ctypes.byref(info))
+    st = load().rr_solve(h.ptr, yp, wp, float(tol), ctypes.byref(info))
     d = info.as_dict()
     d["status"] = _STATUS[st]
     if st not in (RR_OK, RR_NOT_CONVERGED):
@@ -254,8 +291,11 @@ def rr_solve_batch(h: Handle, Y, lambdas, W, tol=1e-8) -> dict:
     nrhs = int(Y.shape[0])
     lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64).ravel())
     nlam = int(lam.size)
+    f64 = _torch().float64
+    yp = _dev(Y, f64, nrhs * h.N, "Y")
+    wp = _dev(W, f64, nlam * nrhs * h.F, "W")
     infos = (rr_info * (nrhs * nlam))()
-    st = load().rr_solve_batch(h.ptr, nrhs, _ptr(Y), nlam, lam.ctypes.data, _ptr(W), float(tol),
+    st = load().rr_solve_batch(h.ptr, nrhs, yp, nlam, lam.ctypes.data, wp, float(tol),
                                ctypes.cast(infos, _P))
     if st not in (RR_OK, RR_NOT_CONVERGED):
         raise RRError(st, rr_last_error())
@@ -266,9 +306,12 @@ def rr_solve_batch(h: Handle, Y, lambdas, W, tol=1e-8) -> dict:
 def rr_solve_many(hs, ys, ws, tol=1e-8, stream=None) -> dict:
     """rr_solve_many over handles hs, device targets ys and solutions ws (lists)."""
     n = len(hs)
+    if len(ys) != n or len(ws) != n:
+        raise ValueError("hs, ys and ws must have the same length")
+    f64 = _torch().float64
     H = (_P * n)(*[h.ptr for h in hs])
-    Y = (_P * n)(*[_ptr(y) for y in ys])
-    W = (_P * n)(*[_ptr(w) for w in ws])
+    Y = (_P * n)(*[_dev(y, f64, h.N, f"ys[{i}]") for i, (h, y) in enumerate(zip(hs, ys))])
+    W = (_P * n)(*[_dev(w, f64, h.F, f"ws[{i}]") for i, (h, w) in enumerate(zip(hs, ws))])
     infos = (rr_info * n)()
     st = load().rr_solve_many(n, ctypes.cast(H, _P), ctypes.cast(Y, _P), ctypes.cast(W, _P),
                               float(tol), _stream_ptr(stream), ctypes.cast(infos, _P))
@@ -280,8 +323,10 @@ def rr_solve_many(hs, ys, ws, tol=1e-8, stream=None) -> dict:
 def rr_solve_fcg(h: Handle, net, y, w, tol=1e-8) -> dict:
     """rr_solve_fcg: flexible CG with the Cholesky coarse solve (net None) or the
     learned correction of an Mlp."""
+    f64 = _torch().float64
+    yp, wp = _dev(y, f64, h.N, "y"), _dev(w, f64, h.F, "w")
     info = rr_info()
-    st = load().rr_solve_fcg(h.ptr, net.ptr if net is not None else None, _ptr(y), _ptr(w),
+    st = load().rr_solve_fcg(h.ptr, net.ptr if net is not None else None, yp, wp,
                              float(tol), ctypes.byref(info))
     d = info.as_dict()
     d["status"] = _STATUS[st]
@@ -293,11 +338,17 @@ def rr_solve_fcg(h: Handle, net, y, w, tol=1e-8) -> dict:
 def rr_harvest(h: Handle, Y, lam, Wref, tol, max_iter, max_pairs, k):
     """rr_harvest into new device float32 tensors (max_pairs, k); returns the
     (Xp, Tp) rows written."""
-    import torch
+    torch = _torch()
+    nrhs = int(Y.shape[0])
+    yp = _dev(Y, torch.float64, nrhs * h.N, "Y")
+    wp = _dev(Wref, torch.float64, nrhs * h.F, "Wref")
+    k_eff = rr_query(h)["k_eff"]
+    if k != k_eff:
+        raise ValueError(f"k = {k}: the pairs have the handle's k_eff = {k_eff} entries")
     Xp = torch.empty((max_pairs, k), dtype=torch.float32, device=Y.device)
     Tp = torch.empty((max_pairs, k), dtype=torch.float32, device=Y.device)
     n = ctypes.c_int64()
-    _check(load().rr_harvest(h.ptr, int(Y.shape[0]), _ptr(Y), float(lam), _ptr(Wref), float(tol),
+    _check(load().rr_harvest(h.ptr, nrhs, yp, float(lam), wp, float(tol),
                              int(max_iter), _ptr(Xp), _ptr(Tp), int(max_pairs), ctypes.byref(n)))
     return Xp[:n.value], Tp[:n.value]
 
@@ -361,50 +412,78 @@ def mlp_set_params(m: Mlp, params: dict):
 
 def mlp_forward(m: Mlp, X):
     """X: device float32 (B, k) -> device float32 (B, k)."""
-    import torch
+    torch = _torch()
+    B = int(X.shape[0])
+    if X.ndim != 2 or int(X.shape[1]) != m.k:
+        raise ValueError(f"X: shape (B, {m.k}) required, got {tuple(X.shape)}")
+    xp = _dev(X, torch.float32, B * m.k, "X")
     out = torch.empty_like(X)
-    _check(load().rr_mlp_forward(m.ptr, int(X.shape[0]), _ptr(X), _ptr(out)))
+    _check(load().rr_mlp_forward(m.ptr, B, xp, _ptr(out)))
     return out
 
 
 def mlp_grad(m: Mlp, X, T):
     """Loss and gradients (dict of numpy arrays) for device float32 rows X, T."""
+    f32 = _torch().float32
+    B = int(X.shape[0])
+    for name, t in (("X", X), ("T", T)):
+        if t.ndim != 2 or tuple(t.shape) != (B, m.k):
+            raise ValueError(f"{name}: shape ({B}, {m.k}) required, got {tuple(t.shape)}")
+    xp, tp = _dev(X, f32, B * m.k, "X"), _dev(T, f32, B * m.k, "T")
     flat = np.empty(mlp_param_count(m.k, m.H), dtype=np.float32)
     loss = ctypes.c_float()
-    _check(load().rr_mlp_grad(m.ptr, int(X.shape[0]), _ptr(X), _ptr(T), flat.ctypes.data,
-                              ctypes.byref(loss)))
+    _check(load().rr_mlp_grad(m.ptr, B, xp, tp, flat.ctypes.data, ctypes.byref(loss)))
     return float(loss.value), mlp_unpack(flat, m.k, m.H)
 
 
 def mlp_train(m: Mlp, Xp, Tp, batch=256, steps=100, lr=1e-3, seed=0):
     """Adam steps on pairs (device float32 (n, k)); returns the batch losses."""
+    f32 = _torch().float32
+    n = int(Xp.shape[0])
+    for name, t in (("Xp", Xp), ("Tp", Tp)):
+        if t.ndim != 2 or tuple(t.shape) != (n, m.k):
+            raise ValueError(f"{name}: shape ({n}, {m.k}) required, got {tuple(t.shape)}")
+    xp, tp = _dev(Xp, f32, n * m.k, "Xp"), _dev(Tp, f32, n * m.k, "Tp")
     losses = np.empty(max(1, steps), dtype=np.float32)
-    _check(load().rr_mlp_train(m.ptr, int(Xp.shape[0]), _ptr(Xp), _ptr(Tp), int(batch),
+    _check(load().rr_mlp_train(m.ptr, n, xp, tp, int(batch),
                                int(steps), float(lr), int(seed), losses.ctypes.data))
     return losses[:steps]
 
 
 def rr_apply(h: Handle, v, out):
-    _check(load().rr_apply(h.ptr, _ptr(v), _ptr(out)))
+    f64 = _torch().float64
+    vp, op = _dev(v, f64, h.F, "v"), _dev(out, f64, h.F, "out")
+    _check(load().rr_apply(h.ptr, vp, op))
 
 
 def rr_precondition(h: Handle, r, z):
-    _check(load().rr_precondition(h.ptr, _ptr(r), _ptr(z)))
+    f64 = _torch().float64
+    rp, zp = _dev(r, f64, h.F, "r"), _dev(z, f64, h.F, "z")
+    _check(load().rr_precondition(h.ptr, rp, zp))
 
 
 def rr_rhs(h: Handle, y, b):
-    _check(load().rr_rhs(h.ptr, _ptr(y), _ptr(b)))
+    f64 = _torch().float64
+    yp, bp = _dev(y, f64, h.N, "y"), _dev(b, f64, h.F, "b")
+    _check(load().rr_rhs(h.ptr, yp, bp))
 
 
 def rr_matvec(h: Handle, v, u):
-    _check(load().rr_matvec(h.ptr, _ptr(v), _ptr(u)))
+    f64 = _torch().float64
+    vp, up = _dev(v, f64, h.F, "v"), _dev(u, f64, h.N, "u")
+    _check(load().rr_matvec(h.ptr, vp, up))
 
 
 def rr_apply_noalloc(n_rows, n_cols, row_ptr, col_idx, col_ptr, row_idx, lam, v, out,
                      stream=None):
     """out = (X^T X + lam I) v from device CSR/CSC tensors; allocates nothing."""
-    _check(load().rr_apply_noalloc(int(n_rows), int(n_cols), _ptr(row_ptr), _ptr(col_idx),
-                                   _ptr(col_ptr), _ptr(row_idx), float(lam), _ptr(v), _ptr(out),
+    torch = _torch()
+    ptrs = (_dev(row_ptr, torch.int64, n_rows + 1, "row_ptr"), _dev(col_idx, torch.int32, 0, "col_idx"),
+            _dev(col_ptr, torch.int64, n_cols + 1, "col_ptr"), _dev(row_idx, torch.int32, 0, "row_idx"))
+    if col_idx.numel() != row_idx.numel():
+        raise ValueError("col_idx and row_idx must hold the same number of entries")
+    vp, op = _dev(v, torch.float64, n_cols, "v"), _dev(out, torch.float64, n_cols, "out")
+    _check(load().rr_apply_noalloc(int(n_rows), int(n_cols), *ptrs, float(lam), vp, op,
                                    _stream_ptr(stream)))
 
 
@@ -415,6 +494,8 @@ def rr_get_labels(h: Handle) -> np.ndarray:
 
 
 def rr_get_centers(h: Handle, k: int) -> np.ndarray:
+    if h.k is not None and k != h.k:
+        raise ValueError(f"k = {k}: the handle was set up with k = {h.k} centres")
     out = np.empty(k, dtype=np.int32)
     _check(load().rr_get_centers(h.ptr, out.ctypes.data))
     return out
