@@ -726,10 +726,11 @@ def cpu_baseline(X, y, p, iters, kmeans_iters, k_eff, quiet=False):
             "parts_s": {k2: round(v, 4) for k2, v in r["parts"].items()}}
 
 
-# Lloyd steps and PCG iterations per lambda of the bench workload, as its GPU
-# runs record them (the oracle's own two-level PCG takes the same counts up to
-# rounding); the oracle counts them itself on workloads small enough to solve.
-REF_COUNTS = {"zipf_200000x100000": ([75, 76, 58], 16)}
+# Lloyd steps and FP64 two-level PCG iterations per lambda of the oracle's own
+# full solve of the bench workload (a ten-minute run: 16 Lloyd steps, k_eff =
+# 1000, 65 / 65 / 50 iterations, no refinement restart); the oracle counts them
+# itself on workloads small enough to solve within the arm's run.
+REF_COUNTS = {"zipf_200000x100000": ([65, 65, 50], 16)}
 
 
 def oracle_counts(X, y, p):
@@ -758,7 +759,7 @@ def run_reference(args, rank, world):
         source = "RR_REF_ITERS"
     elif args.workload in REF_COUNTS:
         iters, km_iters = REF_COUNTS[args.workload]
-        source = "recorded GPU runs"
+        source = "recorded oracle solve"
     else:
         iters, km_iters = oracle_counts(X, y, p)
         source = "oracle solve"
