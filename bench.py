@@ -632,9 +632,11 @@ def run_ours(args, rank, world, local):
         "batched": batched, "many": many, "learned": learned, "tlfcg": tlfcg,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        iters = [i["iters"] for i in last]
-        out["cpu_baseline"] = cpu_baseline(X, y, p, iters, last[0]["kmeans_iters"],
-                                           last[0]["k_eff"])
+        # the oracle's own counts where recorded (its FP64 PCG needs fewer
+        # iterations than the mixed-precision GPU solves), else the GPU's
+        iters, km_iters = REF_COUNTS.get(args.workload, ([i["iters"] for i in last],
+                                                         last[0]["kmeans_iters"]))
+        out["cpu_baseline"] = cpu_baseline(X, y, p, iters, km_iters, last[0]["k_eff"])
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
