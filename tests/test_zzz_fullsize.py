@@ -14,8 +14,10 @@ oracle quantity computed by the oracle from the oracle's own labels:
 - the operator: the FP64 handle to 1e-13 of the largest entry, the mixed
   handle within the FP32 summation bound;
 - the preconditioner (FP64 handle) to cond(A_c) * 1e-15;
-- the solves: the true residual recomputed by the oracle's FP64 operator is
-  <= 1e-8 (up to the rounding bound of the two FP64 recomputations).
+- the solves, mixed precision and FP64: the true residual recomputed by the
+  oracle's FP64 operator is <= 1e-8 (up to the rounding bound of the two FP64
+  recomputations), and the two solutions agree to 1e-6 or to the bound their
+  residuals give.
 """
 import numpy as np
 import pytest
@@ -141,12 +143,19 @@ def test_full_solves_reach_tolerance(full, rr):
     w = torch.empty(X.n_cols, dtype=torch.float64, device="cuda")
     yd = dev(y)
     for lam in p["lambdas"]:
-        rr.rr_set_lambda(full["hm"], lam)
-        info = rr.rr_solve(full["hm"], yd, w, tol=1e-8)
-        assert info["status"] == "RR_OK" and info["true_rel_res"] <= 1e-8
-        wg = w.cpu().numpy()
-        res = np.linalg.norm(b - osp.apply_A(M, lam, wg))
-        # two FP64 evaluations of b - A w in different orders differ by at most
-        # about n eps (|X|^T |X| |w| + lambda |w| + |b|) per entry
-        slack = 2 * n * EPS * np.linalg.norm(osp.apply_A(M, lam, np.abs(wg)) + np.abs(b))
-        assert res <= 1e-8 * bn + slack, (lam, res / bn, slack / bn)
+        sols = []
+        for h in (full["hm"], full["h64"]):       # mixed precision (as timed), then FP64
+            rr.rr_set_lambda(h, lam)
+            info = rr.rr_solve(h, yd, w, tol=1e-8)
+            assert info["status"] == "RR_OK" and info["true_rel_res"] <= 1e-8
+            wg = w.cpu().numpy()
+            res = np.linalg.norm(b - osp.apply_A(M, lam, wg))
+            # two FP64 evaluations of b - A w in different orders differ by at
+            # most about n eps (|X|^T |X| |w| + lambda |w| + |b|) per entry
+            slack = 2 * n * EPS * np.linalg.norm(osp.apply_A(M, lam, np.abs(wg)) + np.abs(b))
+            assert res <= 1e-8 * bn + slack, (lam, res / bn, slack / bn)
+            sols.append((wg, res + slack))
+        # the two solvers agree: to 1e-6, or to the bound their residuals give,
+        # ||w1 - w2|| <= (||r1|| + ||r2||) / lambda
+        (w1, r1), (w2, r2) = sols
+        assert np.linalg.norm(w1 - w2) <= max(1e-6 * np.linalg.norm(w2), (r1 + r2) / lam)
