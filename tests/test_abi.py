@@ -65,3 +65,76 @@ def test_default_options_and_invalid_args_without_gpu(lib):
     # a dense X needs values and no CSR arrays
     X.layout = rr.RR_DENSE_F32_ROWMAJOR
     assert L.rr_setup(ctypes.byref(X), 1.0, 1, None, ctypes.byref(out)) == rr.RR_INVALID_ARG
+
+
+def header_prototypes():
+    """{name: number of parameters} of every function include/rr.h declares."""
+    text = open(os.path.join(ROOT, "include", "rr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = {}
+    for name, params in re.findall(r"\b(rr_[a-z_]+)\s*\(([^;{]*?)\)\s*;", text, flags=re.S):
+        params = params.strip()
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every ctypes signature of the binding takes as many arguments as the
+    header's prototype (a mismatch would pass garbage across the C ABI)."""
+    from paper_1806_05826_gb300 import rr
+    protos = header_prototypes()
+    assert len(protos) == len(header_functions())
+    for name, (_, argtypes) in rr._SIGS.items():
+        assert name in protos, name
+        assert len(argtypes) == protos[name], (name, len(argtypes), protos[name])
+
+
+def test_struct_layouts_match_the_header():
+    """The binding's ctypes structures list the header's fields in order."""
+    from paper_1806_05826_gb300 import rr
+    text = open(os.path.join(ROOT, "include", "rr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    for cname, py in (("rr_matrix", rr.rr_matrix), ("rr_options", rr.rr_options),
+                      ("rr_info", rr.rr_info)):
+        body = re.search(r"typedef struct \{([^{}]*)\}\s*" + cname + r"\s*;", text).group(1)
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            names = decl.split(None, 1)[1] if not decl.startswith("const ") else decl.split(None, 2)[2]
+            for n in names.split(","):
+                fields.append(re.sub(r"[\s*]|\[.*\]", "", n))
+        assert [f[0] for f in py._fields_] == fields, cname
+
+
+def test_struct_offsets_match_the_c_compiler(tmp_path):
+    """Field offsets and sizes of the binding's structures equal those gcc
+    gives the header's structures (the layout the library was built with)."""
+    import shutil
+    import subprocess
+    from paper_1806_05826_gb300 import rr
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = (("rr_matrix", rr.rr_matrix), ("rr_options", rr.rr_options), ("rr_info", rr.rr_info))
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rr.h"', "int main(void) {"]
+    for cname, py in structs:
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'  printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    want = {}
+    for line in got:
+        if line:
+            cname, field, value = line.split()
+            want[(cname, field)] = int(value)
+    for cname, py in structs:
+        assert ctypes.sizeof(py) == want[(cname, "size")], cname
+        for f in py._fields_:
+            assert getattr(py, f[0]).offset == want[(cname, f[0])], (cname, f[0])
