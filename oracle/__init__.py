@@ -1,7 +1,7 @@
 """FP64 CPU oracle for two-level preconditioned CG on (X^T X + lambda I) w = X^T y.
 
 TEST INFRASTRUCTURE ONLY. Only tests/, __graft_entry__.smoke() and bench.py's
-CPU-baseline leg may import this package; the library under
+CPU-baseline leg and reference arm may import this package; the library under
 paper_1806_05826_gb300/ never does, and the two share no code.
 
 Follows Tavernier, Simm, Meerbergen & Moreau, "Two-level preconditioning for
