@@ -342,17 +342,27 @@ rr_status rr_query(const rr_handle *h, int64_t *n_rows, int64_t *n_cols, int32_t
  * cannot afford cudaMalloc's implicit device synchronisation. rr_apply needs a
  * handle, and rr_setup allocates.
  *
- * The intermediate u = X v is kept in a fixed array inside the library (32 MiB
- * on every GPU that loads the library, held until the process exits), so
- * n_rows may not exceed 4,194,304 (RR_UNSUPPORTED beyond). The first call on a
- * device looks up that array's device address (cudaGetSymbolAddress), so make
- * the first call before any stream capture. All calls share the array: calls
- * whose work overlaps on the GPU (different streams, or different host threads
- * on the same device) race on it and must be serialised by the caller. Every
- * call writes u[0, n_rows) before reading it, so no state carries over.
+ * The intermediate u = X v is kept in a fixed 32 MiB array inside the library,
+ * so n_rows may not exceed 4,194,304 (RR_UNSUPPORTED beyond). With CUDA's lazy
+ * module loading (the default), that array is reserved on a device when the
+ * first call on that device loads this part of the library and looks up the
+ * array's address (cudaGetSymbolAddress); it then stays reserved until the
+ * process exits. So make one warm-up call on each device before a memory pool
+ * takes the device's memory and before any stream capture; every later call
+ * allocates nothing. All calls share the array: calls whose work overlaps on
+ * the GPU (different streams, or different host threads on the same device)
+ * race on it and must be serialised by the caller. Every call writes
+ * u[0, n_rows) before reading it, so no state carries over.
+ *
+ * Preconditions the library does not check: row_ptr and col_ptr are
+ * non-decreasing from 0 to the same nnz, and every col_idx lies in
+ * [0, n_cols) and every row_idx in [0, n_rows). An index outside its range is
+ * skipped (never read past a vector), so such input gives an undefined result
+ * but no out-of-bounds access; pointer arrays that run past their index
+ * arrays are undefined behaviour. The Python binding checks the lengths.
  * v, out: device double[n_cols], may not alias. stream: cudaStream_t or NULL.
- * Returns before the work completes. Errors: RR_INVALID_ARG, RR_UNSUPPORTED,
- * RR_CUDA_ERROR. */
+ * Returns before the work completes. Errors: RR_INVALID_ARG (sizes < 1, a NULL
+ * pointer, v == out), RR_UNSUPPORTED, RR_CUDA_ERROR. */
 rr_status rr_apply_noalloc(int64_t n_rows, int64_t n_cols, const int64_t *row_ptr,
                            const int32_t *col_idx, const int64_t *col_ptr, const int32_t *row_idx,
                            double lambda, const double *v, double *out, void *stream);

@@ -5,7 +5,9 @@
 // In host code the name of that array is only a host-side stand-in, so its
 // device address is looked up once per device (cudaGetSymbolAddress, with the
 // device current) and passed to the kernels. Every call overwrites u[0, N)
-// before reading it, so nothing has to be cleared between calls.
+// before reading it, so nothing has to be cleared between calls. An index
+// outside its range is skipped rather than read, so a bad index gives a wrong
+// result but never an access outside the vectors or the array.
 #include <mutex>
 
 #include "common.cuh"
@@ -22,7 +24,7 @@ std::mutex g_mu;
 double *g_scratch_ptr[kMaxDevices] = {};
 
 // u[r] = sum of v over the columns of row r (one warp per row).
-__global__ void k_na_rows(int64_t N, const int64_t *__restrict__ row_ptr,
+__global__ void k_na_rows(int64_t N, int64_t F, const int64_t *__restrict__ row_ptr,
                           const int32_t *__restrict__ col_idx, const double *__restrict__ v,
                           double *__restrict__ u) {
   const int lane = threadIdx.x & 31;
@@ -30,14 +32,17 @@ __global__ void k_na_rows(int64_t N, const int64_t *__restrict__ row_ptr,
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = warp; r < N; r += nwarps) {
     double s = 0.0;
-    for (int64_t p = row_ptr[r] + lane; p < row_ptr[r + 1]; p += 32) s += v[col_idx[p]];
+    for (int64_t p = row_ptr[r] + lane; p < row_ptr[r + 1]; p += 32) {
+      const int32_t c = col_idx[p];
+      if (c >= 0 && c < F) s += v[c];
+    }
     s = rr::warp_sum(s);
     if (lane == 0) u[r] = s;
   }
 }
 
 // out[i] = sum of u over the rows of column i + lambda v[i] (one warp per column).
-__global__ void k_na_cols(int64_t F, const int64_t *__restrict__ col_ptr,
+__global__ void k_na_cols(int64_t N, int64_t F, const int64_t *__restrict__ col_ptr,
                           const int32_t *__restrict__ row_idx, const double *__restrict__ u,
                           double lambda, const double *__restrict__ v, double *__restrict__ out) {
   const int lane = threadIdx.x & 31;
@@ -45,7 +50,10 @@ __global__ void k_na_cols(int64_t F, const int64_t *__restrict__ col_ptr,
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = warp; i < F; i += nwarps) {
     double s = 0.0;
-    for (int64_t p = col_ptr[i] + lane; p < col_ptr[i + 1]; p += 32) s += u[row_idx[p]];
+    for (int64_t p = col_ptr[i] + lane; p < col_ptr[i + 1]; p += 32) {
+      const int32_t r = row_idx[p];
+      if (r >= 0 && r < N) s += u[r];
+    }
     s = rr::warp_sum(s);
     if (lane == 0) out[i] = s + lambda * v[i];
   }
@@ -75,7 +83,8 @@ extern "C" rr_status rr_apply_noalloc(int64_t n_rows, int64_t n_cols, const int6
                                       const int32_t *col_idx, const int64_t *col_ptr,
                                       const int32_t *row_idx, double lambda, const double *v,
                                       double *out, void *stream) {
-  if (n_rows < 1 || n_cols < 1 || !row_ptr || !col_ptr || !v || !out || v == out) {
+  if (n_rows < 1 || n_cols < 1 || !row_ptr || !col_idx || !col_ptr || !row_idx || !v || !out ||
+      v == out) {
     rr_set_error("rr_apply_noalloc: bad sizes or NULL pointers");
     return RR_INVALID_ARG;
   }
@@ -87,9 +96,9 @@ extern "C" rr_status rr_apply_noalloc(int64_t n_rows, int64_t n_cols, const int6
   double *u = nullptr;
   RR_TRY(scratch_address(&u));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  RR_LAUNCH(k_na_rows, rr::grid_for(n_rows, rr::kWarps), rr::kThreads, 0, st, n_rows, row_ptr,
-            col_idx, v, u);
-  RR_LAUNCH(k_na_cols, rr::grid_for(n_cols, rr::kWarps), rr::kThreads, 0, st, n_cols, col_ptr,
-            row_idx, u, lambda, v, out);
+  RR_LAUNCH(k_na_rows, rr::grid_for(n_rows, rr::kWarps), rr::kThreads, 0, st, n_rows, n_cols,
+            row_ptr, col_idx, v, u);
+  RR_LAUNCH(k_na_cols, rr::grid_for(n_cols, rr::kWarps), rr::kThreads, 0, st, n_rows, n_cols,
+            col_ptr, row_idx, u, lambda, v, out);
   return RR_OK;
 }

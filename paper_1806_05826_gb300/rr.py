@@ -476,12 +476,27 @@ def rr_matvec(h: Handle, v, u):
 
 def rr_apply_noalloc(n_rows, n_cols, row_ptr, col_idx, col_ptr, row_idx, lam, v, out,
                      stream=None):
-    """out = (X^T X + lam I) v from device CSR/CSC tensors; allocates nothing."""
+    """out = (X^T X + lam I) v from device CSR/CSC tensors; allocates nothing.
+
+    The pattern's lengths are checked before anything reaches the library:
+    row_ptr and col_ptr must end at the same nnz, which must equal the
+    lengths of col_idx and row_idx (reading the two end entries waits for the
+    device, but allocates nothing on it)."""
     torch = _torch()
-    ptrs = (_dev(row_ptr, torch.int64, n_rows + 1, "row_ptr"), _dev(col_idx, torch.int32, 0, "col_idx"),
-            _dev(col_ptr, torch.int64, n_cols + 1, "col_ptr"), _dev(row_idx, torch.int32, 0, "row_idx"))
-    if col_idx.numel() != row_idx.numel():
-        raise ValueError("col_idx and row_idx must hold the same number of entries")
+    for name, t, n in (("row_ptr", row_ptr, n_rows + 1), ("col_ptr", col_ptr, n_cols + 1)):
+        if not isinstance(t, torch.Tensor) or t.ndim != 1 or t.numel() != n:
+            raise ValueError(f"{name}: a one-dimensional tensor of {n} entries is required")
+    nnz_r, nnz_c = int(row_ptr[n_rows]), int(col_ptr[n_cols])
+    for name, t in (("col_idx", col_idx), ("row_idx", row_idx)):
+        if not isinstance(t, torch.Tensor) or t.numel() != nnz_r:
+            raise ValueError(f"{name}: row_ptr ends at nnz = {nnz_r}, so {nnz_r} entries are "
+                             f"required, got {getattr(t, 'numel', lambda: None)()}")
+    if nnz_c != nnz_r:
+        raise ValueError(f"col_ptr ends at {nnz_c}, row_ptr at {nnz_r}: not the same pattern")
+    ptrs = (_dev(row_ptr, torch.int64, n_rows + 1, "row_ptr"),
+            _dev(col_idx, torch.int32, nnz_r, "col_idx"),
+            _dev(col_ptr, torch.int64, n_cols + 1, "col_ptr"),
+            _dev(row_idx, torch.int32, nnz_r, "row_idx"))
     vp, op = _dev(v, torch.float64, n_cols, "v"), _dev(out, torch.float64, n_cols, "out")
     _check(load().rr_apply_noalloc(int(n_rows), int(n_cols), *ptrs, float(lam), vp, op,
                                    _stream_ptr(stream)))

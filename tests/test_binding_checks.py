@@ -65,3 +65,23 @@ def test_counts_and_shapes_match_the_handle():
         rr.mlp_grad(m, torch.zeros((2, 5)), torch.zeros((3, 5)))
     with pytest.raises(ValueError, match="shape"):
         rr.mlp_train(m, torch.zeros((8, 5)), torch.zeros((8, 4)))
+
+
+def test_noalloc_checks_pattern_lengths():
+    # 3 rows, 2 columns, nnz = 3; the length checks fire before the device
+    # checks, so host tensors reach them here
+    rp = torch.tensor([0, 1, 2, 3], dtype=torch.int64)
+    cp = torch.tensor([0, 2, 3], dtype=torch.int64)
+    idx = torch.tensor([0, 1, 0], dtype=torch.int32)
+    short = idx[:2].clone()
+    v, out = torch.zeros(2, dtype=torch.float64), torch.zeros(2, dtype=torch.float64)
+    with pytest.raises(ValueError, match="col_idx"):
+        rr.rr_apply_noalloc(3, 2, rp, short, cp, idx, 1.0, v, out)
+    with pytest.raises(ValueError, match="row_idx"):
+        rr.rr_apply_noalloc(3, 2, rp, idx, cp, short, 1.0, v, out)
+    with pytest.raises(ValueError, match="same pattern"):
+        rr.rr_apply_noalloc(3, 2, rp, idx, torch.tensor([0, 2, 4]), idx, 1.0, v, out)
+    with pytest.raises(ValueError, match="row_ptr"):
+        rr.rr_apply_noalloc(4, 2, rp, idx, cp, idx, 1.0, v, out)
+    with pytest.raises(TypeError, match="CUDA tensor"):   # lengths right: the device check
+        rr.rr_apply_noalloc(3, 2, rp, idx, cp, idx, 1.0, v, out)
