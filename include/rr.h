@@ -117,6 +117,15 @@ typedef struct {
                                    host-issued kernel chains either way */
   int32_t gram;                 /* RR_GRAM_* (default RR_GRAM_AUTO) */
   int32_t gather;               /* RR_GATHER_* (default RR_GATHER_AUTO) */
+  int32_t wait_limit;           /* test hook: spin iterations of the coarse Gram kernel's bounded
+                                   mbarrier waits; 0 = default (2^22); negative = each such wait
+                                   gives up at once, so rr_setup returns RR_TIMEOUT (the kernel
+                                   still waits, with the default limit, for its own copies in
+                                   flight, and frees its tensor memory, before it exits) */
+  int64_t lloyd_pull_work;      /* a Lloyd step whose count updates (row entries x changed
+                                   clusters) exceed this re-gathers the affected features per
+                                   feature (pull), else it pushes the updates with integer atomics;
+                                   0 = default (2e8). Labels are identical either way */
   void *stream;                 /* cudaStream_t for all work; NULL = legacy default stream */
 } rr_options;
 

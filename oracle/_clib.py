@@ -2,7 +2,9 @@
 
 Test infrastructure only. Compiled without fused multiply-add
 (-ffp-contract=off) so that the dense FP64 sums are plain IEEE additions and
-multiplications in the order the source writes them.
+multiplications in the order the source writes them. Built with OpenMP when
+gcc supports it (only the Lloyd assignment step uses threads, and its results
+do not depend on their number), else without.
 """
 from __future__ import annotations
 
@@ -22,8 +24,10 @@ def build(force: bool = False) -> str:
     """Compile kmeans_exact.c into _oracle_c.so (next to the source)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                        "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"], check=True)
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                "-shared", "-o", tmp, _SRC, "-lm"]
+        if subprocess.run(base[:-1] + ["-fopenmp", "-lm"], capture_output=True).returncode:
+            subprocess.run(base, check=True)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -35,6 +39,8 @@ def lib() -> ctypes.CDLL:
             _handle = ctypes.CDLL(build())
             P = ctypes.c_void_p
             i64, i32, u64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+            _handle.oracle_set_threads.restype = ctypes.c_int
+            _handle.oracle_set_threads.argtypes = [ctypes.c_int]
             _handle.oracle_splitmix64.restype = u64
             _handle.oracle_splitmix64.argtypes = [u64, i64]
             _handle.oracle_u53.restype = ctypes.c_double

@@ -18,6 +18,11 @@ def _p(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+def set_threads(n: int) -> int:
+    """Threads of the Lloyd assignment step (n < 1: all cores); returns the count."""
+    return int(_clib.lib().oracle_set_threads(int(n)))
+
+
 def splitmix64(seed: int, t: int) -> int:
     """Output t (from 0) of SplitMix64 seeded with `seed`."""
     return int(_clib.lib().oracle_splitmix64(seed & 0xFFFFFFFFFFFFFFFF, t))

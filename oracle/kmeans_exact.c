@@ -27,14 +27,34 @@
  *   first centre:  floor(u_0 * F)
  *   centre t >= 1: first i with cumsum(D2)_i > floor(u_t * sum(D2)); if every
  *                  D2 is zero, the lowest index not yet chosen.
- * Plain loops, single thread: slow and obviously correct on purpose.
+ * Plain loops: slow and obviously correct on purpose. The Lloyd assignment
+ * step, where each feature's argmin is independent of the others and computed
+ * in exact integers, may run its features on several OpenMP threads (one
+ * feature per thread at a time, each with its own accumulator), which cannot
+ * change any result; oracle_set_threads(n) sets the count (1 = one thread).
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 typedef __int128 i128;
+
+/* Threads of the Lloyd assignment step (1 when built without OpenMP). */
+int oracle_set_threads(int n) {
+#ifdef _OPENMP
+  if (n < 1) n = omp_get_num_procs();
+  omp_set_num_threads(n);
+  return n;
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 static uint64_t mix64(uint64_t z) {
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
@@ -146,27 +166,37 @@ int oracle_lloyd_binary(int64_t N, int64_t F, const int64_t *row_ptr,
         if (l >= 0 && acc[l] != 0) { Q[l] += acc[l] * acc[l]; acc[l] = 0; }
       }
     }
-    /* assignment: argmin_S (Q_S - 2 n_S D_iS) / n_S^2 */
-    for (int64_t i = 0; i < F; ++i) {
-      memset(acc, 0, sizeof(int64_t) * k);
-      for (int64_t p = col_ptr[i]; p < col_ptr[i + 1]; ++p) {
-        int64_t r = row_idx[p];
-        for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
-          int32_t l = labels[col_idx[e]];
-          if (l >= 0) acc[l] += 1;
+    /* assignment: argmin_S (Q_S - 2 n_S D_iS) / n_S^2, feature by feature */
+#ifdef _OPENMP
+#pragma omp parallel
+#endif
+    {
+      int64_t *dacc = (int64_t *)malloc(sizeof(int64_t) * k);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 64)
+#endif
+      for (int64_t i = 0; i < F; ++i) {
+        memset(dacc, 0, sizeof(int64_t) * k);
+        for (int64_t p = col_ptr[i]; p < col_ptr[i + 1]; ++p) {
+          int64_t r = row_idx[p];
+          for (int64_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+            int32_t l = labels[col_idx[e]];
+            if (l >= 0) dacc[l] += 1;
+          }
         }
-      }
-      int32_t best = -1;
-      int64_t best_a = 0, best_n = 0;
-      for (int32_t s = 0; s < k; ++s) {
-        if (n[s] == 0) continue;
-        int64_t a = Q[s] - 2 * n[s] * acc[s];
-        if (best < 0 ||
-            (i128)a * (i128)(best_n * best_n) < (i128)best_a * (i128)(n[s] * n[s])) {
-          best = s; best_a = a; best_n = n[s];
+        int32_t best = -1;
+        int64_t best_a = 0, best_n = 0;
+        for (int32_t s = 0; s < k; ++s) {
+          if (n[s] == 0) continue;
+          int64_t a = Q[s] - 2 * n[s] * dacc[s];
+          if (best < 0 ||
+              (i128)a * (i128)(best_n * best_n) < (i128)best_a * (i128)(n[s] * n[s])) {
+            best = s; best_a = a; best_n = n[s];
+          }
         }
+        next[i] = best;
       }
-      next[i] = best;
+      free(dacc);
     }
     int64_t changes = 0;
     for (int64_t i = 0; i < F; ++i) {

@@ -29,9 +29,20 @@ class Result:
     true_rel_res: float     # ||b - A w|| / ||b||
     history: list           # recurrence ||r_i|| / ||b|| after every iteration
     restarts: int = 0
+    snapshots: dict = dataclasses.field(default_factory=dict)   # tol -> first iterate below it
 
 
-def _pcg_core(A, Minv, b, target, max_iter, history, bnorm):
+def _snap(snaps, pending, w, rel):
+    """Copies w for every pending tolerance the recurrence residual has reached."""
+    for t in [t for t in pending if rel <= t]:
+        snaps[t] = w.copy()
+        pending.remove(t)
+
+
+def _pcg_core(A, Minv, b, target, max_iter, history, bnorm, snap=None):
+    """snap: optional (snapshots, pending tolerances, offset w0): the iterate
+    w0 + x is recorded at the first iteration whose recurrence residual is
+    below each pending tolerance times ||b||."""
     x = np.zeros_like(b)
     r = b.copy()
     if np.linalg.norm(r) <= target:
@@ -46,6 +57,8 @@ def _pcg_core(A, Minv, b, target, max_iter, history, bnorm):
         r -= alpha * q
         rn = np.linalg.norm(r)
         history.append(rn / bnorm)
+        if snap is not None and snap[1]:
+            _snap(snap[0], snap[1], snap[2] + x, rn / bnorm)
         if rn <= target:
             return x, r, it
         z = Minv(r)
@@ -55,26 +68,33 @@ def _pcg_core(A, Minv, b, target, max_iter, history, bnorm):
     return x, r, max_iter
 
 
-def pcg(A, Minv, b, tol=1e-8, max_iter=10000, max_restarts=5):
-    """PCG with the stopping rule and true-residual refinement above."""
+def pcg(A, Minv, b, tol=1e-8, max_iter=10000, max_restarts=5, snap_tols=()):
+    """PCG with the stopping rule and true-residual refinement above.
+    snap_tols: looser tolerances at which the iterate is also recorded
+    (Result.snapshots), at the first iteration whose recurrence residual
+    reaches each: the iterate a solve to that tolerance stops at, when that
+    solve needs no refinement restart."""
     b = np.asarray(b, np.float64)
     bnorm = float(np.linalg.norm(b))
     hist = []
     if bnorm == 0.0:
         return Result(np.zeros_like(b), 0, 0.0, 0.0, hist)
     target = tol * bnorm
-    w, r, its = _pcg_core(A, Minv, b, target, max_iter, hist, bnorm)
+    snaps, pending = {}, [t for t in snap_tols if t > tol]
+    w, r, its = _pcg_core(A, Minv, b, target, max_iter, hist, bnorm,
+                          (snaps, pending, np.zeros_like(b)))
     rel = float(np.linalg.norm(r)) / bnorm
     true_r = b - A(w)
     restarts = 0
     while np.linalg.norm(true_r) > target and restarts < max_restarts and its < max_iter:
         restarts += 1
-        dw, r, more = _pcg_core(A, Minv, true_r, target, max_iter - its, hist, bnorm)
+        dw, r, more = _pcg_core(A, Minv, true_r, target, max_iter - its, hist, bnorm,
+                                (snaps, pending, w))
         its += more
         w = w + dw
         rel = float(np.linalg.norm(r)) / bnorm
         true_r = b - A(w)
-    return Result(w, its, rel, float(np.linalg.norm(true_r)) / bnorm, hist, restarts)
+    return Result(w, its, rel, float(np.linalg.norm(true_r)) / bnorm, hist, restarts, snaps)
 
 
 def cg(A, b, **kw):

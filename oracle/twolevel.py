@@ -207,13 +207,19 @@ def setup_binary(n_rows, n_cols, row_ptr, col_idx, lam, k, seed=0, centers=None,
                  kmeans_max_iter=50):
     """Clustering, prolongation, Galerkin coarse operator and its Cholesky
     factor, and the Jacobi smoother, for binary X given as a CSR pattern."""
-    M = osp.from_csr(n_rows, n_cols, row_ptr, col_idx)
     col_ptr, row_idx = osp.csc_pattern(n_rows, n_cols, row_ptr, col_idx)
     if centers is None:
         centers = km.kmeanspp_binary(n_rows, n_cols, row_ptr, col_idx, col_ptr, row_idx, k, seed)
     raw, iters = km.lloyd_binary(n_rows, n_cols, row_ptr, col_idx, col_ptr, row_idx,
                                  centers, kmeans_max_iter)
-    labels, n_S = km.compact(raw)
+    return from_labels(n_rows, n_cols, row_ptr, col_idx, lam, raw, centers, iters)
+
+
+def from_labels(n_rows, n_cols, row_ptr, col_idx, lam, raw_labels, centers=(), iters=0):
+    """The steps of setup_binary after the clustering, from given (raw) cluster
+    labels: compaction, P, the exact Gram, A_c and its factor, the smoother."""
+    M = osp.from_csr(n_rows, n_cols, row_ptr, col_idx)
+    labels, n_S = km.compact(raw_labels)
     s = prolong_scale(n_S)
     G = coarse_gram_binary(n_rows, n_cols, row_ptr, col_idx, labels, len(n_S))
     Ac = coarse_operator_binary(G, s, lam)

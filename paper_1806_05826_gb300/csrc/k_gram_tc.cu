@@ -43,7 +43,8 @@ constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kTN >> 3) << 17) | ((uint32_
 // blockIdx.x / n_tiles.
 __global__ void __launch_bounds__(kGramThreads, 1)
     k_gram_tc(const __grid_constant__ CUtensorMap tmap, int32_t k, int32_t n_tiles_lower,
-              int64_t n_pad, int64_t k_chunk, double *__restrict__ G, int32_t *err) {
+              int64_t n_pad, int64_t k_chunk, double *__restrict__ G, int32_t *err,
+              uint32_t wait_limit) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte alignment of the tile ring (the 128-byte swizzle repeats every 1024 bytes)
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -92,7 +93,8 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     int issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % kStages;
-      if (kb >= kStages && !mbar_wait(&empty[s], ((kb / kStages) + 1) & 1, abort_flag)) {
+      if (kb >= kStages &&
+          !mbar_wait(&empty[s], ((kb / kStages) + 1) & 1, abort_flag, wait_limit)) {
         set_dev_error(err, DEV_TIMEOUT);
         atomicExch(abort_flag, 1);
         break;
@@ -116,7 +118,8 @@ __global__ void __launch_bounds__(kGramThreads, 1)
     bool ok = true;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % kStages;
-      if (!mbar_wait(&full[s], (kb / kStages) & 1, abort_flag) || *(volatile int32_t *)abort_flag) {
+      if (!mbar_wait(&full[s], (kb / kStages) & 1, abort_flag, wait_limit) ||
+          *(volatile int32_t *)abort_flag) {
         set_dev_error(err, DEV_TIMEOUT);
         atomicExch(abort_flag, 1);
         ok = false;
@@ -138,7 +141,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
 
   // epilogue: all four warps; warp w owns accumulator rows 32w..32w+31
   bool have = !*(volatile int32_t *)abort_flag && nk > 0;
-  if (have && !mbar_wait(done, 0, abort_flag)) {
+  if (have && !mbar_wait(done, 0, abort_flag, wait_limit)) {
     set_dev_error(err, DEV_TIMEOUT);
     have = false;
   }
@@ -181,8 +184,11 @@ int64_t gram_tc_chunk(int32_t max_count) {
 }
 
 rr_status gram_tensor_cores(int32_t k, int32_t k_pad, int64_t n_pad, const void *Ct,
-                            int32_t max_count, double *G, int32_t *err, cudaStream_t st) {
+                            int32_t max_count, double *G, int32_t *err, cudaStream_t st,
+                            int32_t wait_limit) {
   const int64_t chunk = gram_tc_chunk(max_count);
+  // the pipeline's waits (the drain of copies in flight keeps the default)
+  const uint32_t limit = wait_limit == 0 ? tc::kSpinLimit : wait_limit < 0 ? 0u : (uint32_t)wait_limit;
   if (chunk < kTK || k_pad % kTM != 0 || n_pad % kTK != 0) {
     rr_set_error("tensor-core Gram: counts too large for exact FP32 chunks");
     return RR_UNSUPPORTED;
@@ -216,7 +222,7 @@ rr_status gram_tensor_cores(int32_t k, int32_t k_pad, int64_t n_pad, const void 
   }
   RR_CUDA(cudaMemsetAsync(G, 0, sizeof(double) * (size_t)k * k, st));
   RR_LAUNCH(k_gram_tc, (unsigned)(n_lower * n_chunks), kGramThreads, smem, st, map, k, n_lower,
-            n_pad, chunk, G, err);
+            n_pad, chunk, G, err, limit);
   return RR_OK;
 }
 

@@ -820,7 +820,7 @@ rr_status kmeans_work_order(int64_t N, int64_t F, int32_t k, const int64_t *row_
 template <bool P>
 rr_status lloyd_delta_apply(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                             const int64_t *col_ptr, const int32_t *row_idx, int32_t k,
-                            KmeansBuffers &b, cudaStream_t st) {
+                            KmeansBuffers &b, unsigned long long pull_work, cudaStream_t st) {
   using T = typename DeltaEntry<P>::T;
   T *dlist = reinterpret_cast<T *>(b.dlist);
   const int warps_per_cta = (int)std::max<int64_t>(1, std::min<int64_t>(kWarps, (96 * 1024) / (4 * (int64_t)k)));
@@ -832,7 +832,7 @@ rr_status lloyd_delta_apply(int64_t N, int64_t F, const int64_t *row_ptr, const 
   unsigned long long work = 0;
   RR_CUDA(cudaMemcpyAsync(&work, b.work, sizeof(work), cudaMemcpyDeviceToHost, st));
   RR_CUDA(cudaStreamSynchronize(st));
-  if (work > kPushWorkLimit) {
+  if (work > pull_work) {
     RR_CUDA(cudaMemsetAsync(b.work_ctr, 0, sizeof(int32_t), st));
     const size_t smem = sizeof(int32_t) * (size_t)k;
     RR_CUDA(cudaFuncSetAttribute(k_lloyd_pull<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -851,16 +851,18 @@ rr_status lloyd_delta_apply(int64_t N, int64_t F, const int64_t *row_ptr, const 
 
 rr_status kmeans_lloyd_step(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                             const int64_t *col_ptr, const int32_t *row_idx, int32_t k,
-                            KmeansBuffers &b, int64_t *changes_host, cudaStream_t st) {
+                            KmeansBuffers &b, int64_t *changes_host, int64_t pull_work,
+                            cudaStream_t st) {
+  const unsigned long long pw = pull_work > 0 ? (unsigned long long)pull_work : kPushWorkLimit;
   // (1) per-row delta lists of the cluster counts (prev -> labels)
   RR_LAUNCH(k_moved_count, grid_for(N, kWarps), kThreads, 0, st, N, row_ptr, col_idx, b.prev,
             b.labels, b.mcount);
   RR_TRY(scan_exclusive(b.mcount, b.mptr, N, b.scan_scratch, st));
   RR_CUDA(cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), st));
   if (b.packed)
-    RR_TRY(lloyd_delta_apply<true>(N, F, row_ptr, col_idx, col_ptr, row_idx, k, b, st));
+    RR_TRY(lloyd_delta_apply<true>(N, F, row_ptr, col_idx, col_ptr, row_idx, k, b, pw, st));
   else
-    RR_TRY(lloyd_delta_apply<false>(N, F, row_ptr, col_idx, col_ptr, row_idx, k, b, st));
+    RR_TRY(lloyd_delta_apply<false>(N, F, row_ptr, col_idx, col_ptr, row_idx, k, b, pw, st));
   // (3) sizes and Q from the updated D
   RR_CUDA(cudaMemsetAsync(b.n_S, 0, sizeof(int64_t) * k, st));
   RR_CUDA(cudaMemsetAsync(b.Q, 0, sizeof(int64_t) * k, st));

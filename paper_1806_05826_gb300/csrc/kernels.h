@@ -73,10 +73,12 @@ rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int3
 int64_t kmeans_seed_tiles(int64_t F);
 rr_status kmeans_init_labels(int64_t F, int32_t k, KmeansBuffers &b, cudaStream_t st);
 // One Lloyd assignment step; on return (stream synchronised) *changes_host holds
-// the number of labels that changed.
+// the number of labels that changed. pull_work: count updates above which the
+// step pulls per feature instead of pushing per row (<= 0: the default).
 rr_status kmeans_lloyd_step(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                             const int64_t *col_ptr, const int32_t *row_idx, int32_t k,
-                            KmeansBuffers &b, int64_t *changes_host, cudaStream_t st);
+                            KmeansBuffers &b, int64_t *changes_host, int64_t pull_work,
+                            cudaStream_t st);
 // order[] = features by descending work_i = sum of the row lengths of column i
 // (heaviest first); work[] receives work_i, which is also the Gershgorin row
 // sum of X^T X for binary X.
@@ -103,8 +105,11 @@ rr_status counts_to_half(int64_t n, const int32_t *C32, void *C16, cudaStream_t 
 // for counts up to max_count; < 64 means the tensor-core path cannot be exact.
 int64_t gram_tc_chunk(int32_t max_count);
 // G = Ct Ct^T (k x k, FP64, exact) with tcgen05 MMAs; k_pad % 128 == 0, n_pad % 64 == 0.
+// wait_limit: spin iterations of the kernel's bounded waits on its pipeline
+// (0: the default; negative: none, a test hook that makes them expire).
 rr_status gram_tensor_cores(int32_t k, int32_t k_pad, int64_t n_pad, const void *Ct,
-                            int32_t max_count, double *G, int32_t *err, cudaStream_t st);
+                            int32_t max_count, double *G, int32_t *err, cudaStream_t st,
+                            int32_t wait_limit = 0);
 // G = C32 C32^T exact (CUDA cores, int32 steps summed in int64) -> G as FP64 (k x k).
 rr_status gram_exact_cuda_cores(int32_t k, int32_t k_pad, int64_t n_pad, const int32_t *C32,
                                 double *G, cudaStream_t st);

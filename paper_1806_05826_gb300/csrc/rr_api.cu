@@ -404,7 +404,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   while (it < h->opt.kmeans_max_iter) {
     ++it;
     ks = rr::kmeans_lloyd_step(N, F, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx, k, kb,
-                               changes_host, st);
+                               changes_host, h->opt.lloyd_pull_work, st);
     if (ks != RR_OK || *changes_host == 0) break;
   }
   cudaFreeHost(changes_host);
@@ -475,7 +475,9 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
     gs = m.alloc(reinterpret_cast<uint16_t **>(&C16), ncount);
     if (gs == RR_OK) gs = rr::counts_to_half((int64_t)ncount, C32, C16, st);
     if (gs == RR_OK) m.release(C32), C32 = nullptr;
-    if (gs == RR_OK) gs = rr::gram_tensor_cores(k_eff, k_pad, n_pad, C16, max_count, h->G, h->err, st);
+    if (gs == RR_OK)
+      gs = rr::gram_tensor_cores(k_eff, k_pad, n_pad, C16, max_count, h->G, h->err, st,
+                                 h->opt.wait_limit);
   } else if (gs == RR_OK) {
     gs = rr::gram_exact_cuda_cores(k_eff, k_pad, n_pad, C32, h->G, st);
   }

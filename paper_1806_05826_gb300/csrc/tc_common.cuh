@@ -41,8 +41,9 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 // Bounded wait: false when the limit expired or another thread of the CTA
 // gave up (abort flag set).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
-                                          const int32_t *abort_flag) {
-  for (uint32_t i = 0; i < kSpinLimit; ++i) {
+                                          const int32_t *abort_flag,
+                                          uint32_t limit = kSpinLimit) {
+  for (uint32_t i = 0; i < limit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 255u) == 255u && *(volatile const int32_t *)abort_flag) return false;
   }

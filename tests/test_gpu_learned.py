@@ -18,6 +18,8 @@ import pytest
 from gen import synth
 from oracle import krylov, learned, mlp
 from oracle import sparse as osp
+
+import solution_ref
 from oracle import twolevel
 
 torch = pytest.importorskip("torch")
@@ -153,6 +155,12 @@ def exact(small, y):
     return twolevel.chol_solve(small["Lc"], osp.rhs(small["ref"].M, y))
 
 
+def oracle_pcg(small, y):
+    """The oracle's two-level PCG solution at 1e-8 (its own answer there)."""
+    ref = small["ref"]
+    return krylov.pcg(ref.A, ref.apply, osp.rhs(ref.M, y), tol=1e-8).w
+
+
 def test_harvest_matches_oracle(rr, small):
     X, ref = small["X"], small["ref"]
     Y, _ = synth.ridge_targets_many(X, [1000, 1001])
@@ -190,8 +198,7 @@ def test_fcg_cholesky_matches_oracle(rr, small):
     wg = w.cpu().numpy()
     r = np.linalg.norm(b - ref.A(wg))
     assert r <= 1e-8 * np.linalg.norm(b)
-    ws = exact(small, y)
-    assert np.linalg.norm(wg - ws) <= max(1e-6 * np.linalg.norm(ws), 1.01 * r / small["lam"])
+    solution_ref.check(wg, exact(small, y), want.w, "Cholesky FCG")
 
 
 def test_learned_fcg_end_to_end(rr, small):
@@ -220,7 +227,7 @@ def test_learned_fcg_end_to_end(rr, small):
     for s in (100, 101, 102, 103):
         y, _ = synth.ridge_targets(X, s)
         b = osp.rhs(ref.M, y)
-        ws = exact(small, y)
+        ws, wo = exact(small, y), oracle_pcg(small, y)
         its = {}
         for name, fn in (("learned", lambda: rr.rr_solve_fcg(h, net, dev(y), w, tol=1e-8)),
                          ("fcg", lambda: rr.rr_solve_fcg(h, None, dev(y), w, tol=1e-8)),
@@ -230,7 +237,7 @@ def test_learned_fcg_end_to_end(rr, small):
             wg = w.cpu().numpy()
             r = np.linalg.norm(b - ref.A(wg))
             assert r <= 1e-8 * np.linalg.norm(b), name
-            assert np.linalg.norm(wg - ws) <= max(1e-6 * np.linalg.norm(ws), 1.01 * r / lam), name
+            solution_ref.check(wg, ws, wo, name)
             its[name] = (info["iters"], info.get("fallbacks", 0))
         rows.append(its)
     print("learned vs plain iterations (iters, fallbacks):", rows)

@@ -8,6 +8,8 @@ import pytest
 
 from gen import synth
 from oracle import sparse as osp
+
+import solution_ref
 from oracle import twolevel
 
 torch = pytest.importorskip("torch")
@@ -43,7 +45,7 @@ def many(request, rr):
         y, _ = synth.ridge_targets(X, 100 + seed)
         h = rr.rr_setup(X.row_ptr, X.col_idx, n, d, 1e-2, max(2, d // 100), seed=seed,
                         precision=prec, max_restarts=20)
-        probs.append(dict(X=X, y=y, h=h))
+        probs.append(dict(X=X, y=y, h=h, seed=seed))
     ys = [dev(p["y"]) for p in probs]
     ws = [torch.empty(p["X"].n_cols, dtype=torch.float64, device="cuda") for p in probs]
     out = rr.rr_solve_many([p["h"] for p in probs], ys, ws, tol=1e-8)
@@ -66,10 +68,11 @@ def test_many_matches_exact_solutions(many):
         X = p["X"]
         M = osp.from_csr(X.n_rows, X.n_cols, X.row_ptr, X.col_idx)
         b = osp.rhs(M, p["y"])
-        ws = twolevel.chol_solve(twolevel.cholesky(osp.dense_A(M, 1e-2)), b)
         r = np.linalg.norm(b - osp.apply_A(M, 1e-2, p["w"]))
         assert r <= 1e-8 * np.linalg.norm(b) and info["true_rel_res"] <= 1e-8
-        assert np.linalg.norm(p["w"] - ws) <= max(1e-6 * np.linalg.norm(ws), 1.01 * r / 1e-2)
+        w_ref, snaps = solution_ref.for_problem(X, p["y"], 1e-2, max(2, X.n_cols // 100),
+                                                p["seed"])
+        solution_ref.check(p["w"], w_ref, snaps[1e-8], f"problem {p['seed']}")
 
 
 def test_many_rejects_shared_handles(many, rr):

@@ -694,3 +694,40 @@ def test_dense_matrix_products_match_numpy():
     assert np.allclose(osp.X_mv(M, v), Xd @ v, rtol=1e-14)
     assert np.allclose(osp.Xt_mv(M, u), Xd.T @ u, rtol=1e-14)
     assert np.allclose(osp.apply_A(M, 0.2, v), (Xd.T @ Xd + 0.2 * np.eye(5)) @ v, rtol=1e-13)
+
+
+def test_lloyd_threads_do_not_change_labels():
+    """The Lloyd assignment step may run on several threads; each feature's
+    argmin is exact integer arithmetic of its own, so the labels and the step
+    count are the same on one thread and on all of them."""
+    X = synth.zipf_binary(3001, 1777, 0.006, 1.1, 5)
+    cp, ri = osp.csc_pattern(X.n_rows, X.n_cols, X.row_ptr, X.col_idx)
+    c = km.kmeanspp_binary(X.n_rows, X.n_cols, X.row_ptr, X.col_idx, cp, ri, 37, 5)
+    out = []
+    for t in (1, 0):
+        km.set_threads(t)
+        out.append(km.lloyd_binary(X.n_rows, X.n_cols, X.row_ptr, X.col_idx, cp, ri, c, 50))
+    km.set_threads(0)
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+
+
+def test_reference_solutions_are_the_dense_solution():
+    """oracle.reference (exact solutions in spawned processes, the
+    preconditioner rebuilt from given labels) against a dense Cholesky solve,
+    and its 1e-8 snapshot against the oracle's own PCG run to 1e-8."""
+    from oracle import reference
+    spec = (2000, 1000, 0.01, 1.1, 0)
+    X = synth.zipf_binary(*spec)
+    Y, _ = synth.ridge_targets_many(X, [0, 1])
+    _, raw, _ = reference.oracle_labels(spec, 50, 0)
+    lams = (1e-2, 1.0)
+    out = reference.exact_solutions(spec, raw, [(lams[0], Y[0]), (lams[1], Y[1])], processes=2)
+    M = osp.from_csr(*spec[:2], X.row_ptr, X.col_idx)
+    for (w, snaps, iters, rel), lam, y in zip(out, lams, Y):
+        b = osp.rhs(M, y)
+        ws = np.linalg.solve(osp.dense_A(M, lam), b)
+        assert rel <= reference.TOL_REF
+        assert np.linalg.norm(w - ws) <= 1e-8 * np.linalg.norm(ws)
+        two = tl.from_labels(*spec[:2], X.row_ptr, X.col_idx, lam, raw)
+        want = krylov.pcg(two.A, two.apply, b, tol=1e-8)
+        assert want.restarts == 0 and np.array_equal(snaps[1e-8], want.w)
