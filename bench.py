@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-parity", action="store_true",
+                    help="skip the oracle's exact solutions of the workload (error of each solve)")
+    ap.add_argument("--no-small", action="store_true",
+                    help="skip the small FP64 configuration (2,000 x 1,000, us per iteration)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched section (64 targets x 8 weights over the same X)")
     ap.add_argument("--no-many", action="store_true",
@@ -171,6 +175,94 @@ def profiled_traffic(kernel, workload):
     except OSError:
         pass
     return None
+
+
+# ---------------------------------------------------------------- parity leg
+
+def _parity_worker(spec, k, seed, lams, y, out_path, threads):
+    """Runs in a spawned process: the oracle's clustering, then the exact
+    solution of every lambda (the oracle's PCG to 1e-12, one process each),
+    saved to out_path."""
+    sys.path.insert(0, ROOT)
+    from oracle import reference
+    _, raw, iters = reference.oracle_labels(spec, k, seed, threads=threads)
+    res = reference.exact_solutions(spec, raw, [(lam, y) for lam in lams],
+                                    snap_tols=(TOL,), processes=len(lams))
+    np.savez(out_path, w_ref=np.stack([r[0] for r in res]),
+             w_orc=np.stack([r[1][TOL] for r in res]),
+             iters=np.array([r[2] for r in res]), rel=np.array([r[3] for r in res]),
+             kmeans_iters=iters)
+
+
+def start_parity(X, y, p, tmpdir):
+    """Starts the oracle's exact solutions in the background (before any GPU
+    work is timed; the process is spawned, so it shares nothing with the CUDA
+    context). Returns (process, output path)."""
+    import multiprocessing as mp
+    spec = (X.n_rows, X.n_cols, p["density"], p["s"], p["seed"])
+    path = os.path.join(tmpdir, "parity.npz")
+    threads = max(1, (os.cpu_count() or 4) // 2 - 1)
+    proc = mp.get_context("spawn").Process(
+        target=_parity_worker, args=(spec, p["k"], p["seed"], list(p["lambdas"]), y, path,
+                                     threads), daemon=False)
+    proc.start()
+    return proc, path
+
+
+def finish_parity(proc, path, W, lams, timeout_s=900):
+    """||w - w_ref|| / ||w_ref|| of the timed step's solutions, with the
+    oracle's own error at the same tolerance for context."""
+    proc.join(timeout_s)
+    if proc.is_alive() or not os.path.exists(path):
+        if proc.is_alive():
+            proc.terminate()
+        return {"error": "the oracle's reference solve did not finish"}
+    d = np.load(path)
+    out = {"reference": "oracle two-level PCG (its own k-means++ clustering) to relative residual "
+                        "1e-12", "tol": TOL, "lambdas": list(lams),
+           "err_vs_oracle": [], "oracle_err_at_tol": [], "bar": [], "within_bar": []}
+    for j in range(len(lams)):
+        wr = d["w_ref"][j]
+        e = float(np.linalg.norm(W[j] - wr) / np.linalg.norm(wr))
+        eo = float(np.linalg.norm(d["w_orc"][j] - wr) / np.linalg.norm(wr))
+        bar = max(1e-6, 4.0 * eo)
+        out["err_vs_oracle"].append(e)
+        out["oracle_err_at_tol"].append(eo)
+        out["bar"].append(bar)
+        out["within_bar"].append(bool(e <= bar))
+    out["oracle_ref_iters"] = [int(v) for v in d["iters"]]
+    out["oracle_kmeans_iters"] = int(d["kmeans_iters"])
+    return out
+
+
+def measure_small_fp64(rr, dev):
+    """The small plain FP64 configuration (2,000 x 1,000, 1%, k = 50,
+    lambda = 1e-2, seed 0): latency-bound, so reported as microseconds per
+    PCG iteration, with the error against a dense solve."""
+    import torch
+    from gen import synth
+    from oracle import sparse as osp
+    X, y, _, p = synth.workload("zipf_2000x1000")
+    lam = p["lambdas"][0]
+    h = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, lam, p["k"], seed=p["seed"])
+    yd = torch.as_tensor(y, device=dev)
+    w = torch.empty(X.n_cols, dtype=torch.float64, device=dev)
+    for _ in range(3):
+        info = rr.rr_solve(h, yd, w, tol=TOL)
+    ms = []
+    for _ in range(5):
+        info = rr.rr_solve(h, yd, w, tol=TOL)
+        ms.append(info["solve_ms"])
+    M = osp.from_csr(X.n_rows, X.n_cols, X.row_ptr, X.col_idx)
+    wr = np.linalg.solve(osp.dense_A(M, lam), osp.rhs(M, y))
+    err = float(np.linalg.norm(w.cpu().numpy() - wr) / np.linalg.norm(wr))
+    rr.rr_free(h)
+    med = statistics.median(ms)
+    return {"workload": "zipf_2000x1000", "precision": "fp64", "setup_ms": round(info["setup_ms"], 2),
+            "solve_ms": round(med, 3), "iters": info["iters"],
+            "us_per_iter": round(1000 * med / max(1, info["iters"]), 2),
+            "err_vs_dense_solve": err, "true_rel_res": info["true_rel_res"],
+            "note": "latency bound (0.5 MB per iteration, L2 resident): no HBM fraction"}
 
 
 # ---------------------------------------------------------------- our arm
@@ -543,6 +635,10 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize(dev)
         return {"profile_step": args.workload, "gpu_launches": rr.rr_launch_count() - l0,
                 "iters": [i["iters"] for i in infos]}
+    parity_proc = None
+    tmpdir = tempfile.mkdtemp(prefix="rr_parity_")
+    if rank == 0 and args.workload == WORKLOAD and not args.no_parity:
+        parity_proc, parity_path = start_parity(X, y, p, tmpdir)
     for _ in range(max(3, args.warmup)):
         infos = step()
     for inf in infos:
@@ -601,6 +697,10 @@ def run_ours(args, rank, world, local):
     if not args.no_learned and args.workload == WORKLOAD:
         learned = measure_learned(rr, X, row_ptr, col_idx, k, opts, dev, stream, n_pairs=args.pairs)
 
+    small = measure_small_fp64(rr, dev) if not args.no_small else None
+    parity = None
+    if parity_proc is not None:
+        parity = finish_parity(parity_proc, parity_path, [w.cpu().numpy() for w in W], lams)
     last = all_infos[-1]
     out = {
         "metric": METRIC, "value": round(value, 5), "unit": "s", "n_gpus": world,
@@ -630,6 +730,7 @@ def run_ours(args, rank, world, local):
                       "step_ms": [round(t, 3) for t in step_ms]},
         "e2e": e2e, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches,
         "batched": batched, "many": many, "learned": learned, "tlfcg": tlfcg,
+        "parity": parity, "small_fp64": small,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle's own counts where recorded (its FP64 PCG needs fewer
@@ -637,6 +738,9 @@ def run_ours(args, rank, world, local):
         iters, km_iters = REF_COUNTS.get(args.workload, ([i["iters"] for i in last],
                                                          last[0]["kmeans_iters"]))
         out["cpu_baseline"] = cpu_baseline(X, y, p, iters, km_iters, last[0]["k_eff"])
+        allc = cpu_baseline(X, y, p, iters, km_iters, last[0]["k_eff"], cores=os.cpu_count() or 1)
+        out["cpu_baseline"]["all_cores"] = {key: allc.get(key) for key in
+                                            ("value", "cores", "sample_wall_s", "parts_s")}
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -703,13 +807,15 @@ def _oracle_sample(npz_path, k, lam, iters, kmeans_iters, k_eff, seed):
     return total, T
 
 
-def cpu_baseline(X, y, p, iters, kmeans_iters, k_eff, quiet=False):
-    """Times the oracle sample in a child process pinned to one thread."""
+def cpu_baseline(X, y, p, iters, kmeans_iters, k_eff, quiet=False, cores=1):
+    """Times the oracle sample in a child process with `cores` threads (the
+    oracle's only threaded part is the Lloyd assignment step; numpy's BLAS
+    gets the same count)."""
     with tempfile.TemporaryDirectory() as tmp:
         path = os.path.join(tmp, "x.npz")
         np.savez(path, row_ptr=X.row_ptr, col_idx=X.col_idx, y=y, n_cols=X.n_cols)
-        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1",
-                   MKL_NUM_THREADS="1", CUDA_VISIBLE_DEVICES="")
+        env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores),
+                   MKL_NUM_THREADS=str(cores), CUDA_VISIBLE_DEVICES="")
         code = ("import json,sys; sys.path.insert(0, %r); import bench; "
                 "tot, T = bench._oracle_sample(%r, %d, %r, %r, %d, %d, %d); "
                 "print(json.dumps({'total': tot, 'parts': T}))" %
@@ -720,10 +826,11 @@ def cpu_baseline(X, y, p, iters, kmeans_iters, k_eff, quiet=False):
                              cwd=ROOT)
         wall = time.perf_counter() - t0
     if res.returncode != 0:
-        return {"value": None, "unit": "s", "cores": 1, "kind": "oracle",
+        return {"value": None, "unit": "s", "cores": cores, "kind": "oracle",
                 "error": res.stderr.strip().splitlines()[-1:] if res.stderr else "failed"}
     r = json.loads(res.stdout.strip().splitlines()[-1])
-    return {"value": round(r["total"], 3), "unit": "s", "cores": 1, "kind": "oracle",
+    return {"value": round(r["total"], 3), "unit": "s", "cores": cores, "kind": "oracle",
+            "nproc": os.cpu_count(),
             "sample": SAMPLE_NOTE, "sample_wall_s": round(wall, 1),
             "parts_s": {k2: round(v, 4) for k2, v in r["parts"].items()}}
 
