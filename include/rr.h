@@ -126,6 +126,14 @@ typedef struct {
                                    clusters) exceed this re-gathers the affected features per
                                    feature (pull), else it pushes the updates with integer atomics;
                                    0 = default (2e8). Labels are identical either way */
+  int32_t split_head;           /* RR_PREC_MIXED, binary X: the operator applies of the FP32
+                                   iterations take the columns that hold every row as a rank-one
+                                   term and the split_head most frequent other columns as a
+                                   row-major bitmap (one read serves X v and X^T u), the rest as
+                                   sliced index lists. 0 = automatic (default: the largest power
+                                   of two from 32 to 1024 whose columns each hold at least N/32
+                                   rows, or none); a power of two from 32 to 1024 = that many;
+                                   -1 = no split form (every column as sliced index lists) */
   void *stream;                 /* cudaStream_t for all work; NULL = legacy default stream */
 } rr_options;
 

@@ -72,6 +72,7 @@ struct rr_handle {
   rr::RestrictPlan rplan;
   rr::SlicedPattern pcsr;   // X by row, vector v cut in feature slices
   rr::SlicedPattern pcsc;   // X^T by column, vector u cut in row slices
+  rr::SplitOperator split;  // the FP32 operator's split form (mixed precision, binary X)
   // solve workspace
   double *b = nullptr, *r = nullptr, *z1 = nullptr, *z2 = nullptr, *z = nullptr, *p = nullptr,
          *q = nullptr, *r1 = nullptr, *u = nullptr, *rc = nullptr, *ec = nullptr, *rt = nullptr;

@@ -225,10 +225,11 @@ __device__ __forceinline__ T gather8(const T *__restrict__ xs, const uint4 q) {
 // memory, then every lane sums whole pieces: the 32 lanes of a warp take 32
 // consecutive pieces, so piece pointers, slots and the words of short pieces
 // are read coalesced, and each lane loads its piece's words four at a time.
-// Sums in a fixed order in T; the piece sum is stored in FP64.
-template <typename T>
+// Sums in a fixed order in T; the piece sum is stored as PS (FP64, or FP32
+// for the patterns whose consumers sum in FP32).
+template <typename T, typename PS>
 __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather(
-    SlicedView P, const T *__restrict__ xq, double *__restrict__ out_psum,
+    SlicedView P, const T *__restrict__ xq, PS *__restrict__ out_psum,
     const int32_t *__restrict__ stop) {
   pdl_wait();
   if (stop && *stop) return;
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather(
         for (int k = 1; k < 4; ++k)
           if (w + k < w1[u]) acc += gather8(xs, q[k]);
       }
-      out_psum[__ldg(P.slot + pp[u])] = (double)acc;
+      out_psum[__ldg(P.slot + pp[u])] = (PS)acc;
     }
   }
 }
@@ -316,10 +317,11 @@ __device__ __forceinline__ void team_sync(int team) {
   asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(kTeamThreads) : "memory");
 }
 
+template <typename PS>
 __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather_staged(
     SlicedView P, const int32_t *__restrict__ chunk_p, const int32_t *__restrict__ chunk_w,
     const int32_t *__restrict__ task_c, const float *__restrict__ xq,
-    double *__restrict__ out_psum, const int32_t *__restrict__ stop, int32_t *err) {
+    PS *__restrict__ out_psum, const int32_t *__restrict__ stop, int32_t *err) {
   pdl_wait();
   if (stop && *stop) return;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -422,7 +424,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather_staged(
       const int32_t w0 = pws[p] - m.wa, w1 = pws[p + 1] - m.wa;
       float acc = ws[w0];
       for (int32_t w = w0 + 1; w < w1; ++w) acc += ws[w];
-      out_psum[sls[p]] = (double)acc;
+      out_psum[sls[p]] = (PS)acc;
     }
   }
   if (tt == 0 && *(volatile int32_t *)abort_flag) {
@@ -640,14 +642,53 @@ size_t staged_smem(int32_t W) {
   return sizeof(float) * (size_t)((W + 1 + 3) & ~3) + (size_t)kTeams * kTeamSmem + 16;
 }
 
-template <typename T>
+template <typename T, typename PS>
 rr_status set_smem_attr() {
   static bool done = false;
   if (!done) {
-    RR_CUDA(cudaFuncSetAttribute(k_sliced_gather<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    RR_CUDA(cudaFuncSetAttribute(k_sliced_gather<T, PS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)slice_smem<T>(kSliceMax)));
     done = true;
   }
+  return RR_OK;
+}
+
+template <typename PS>
+rr_status set_staged_attr() {
+  static bool done = false;
+  if (!done) {   // the largest slice any pattern can have
+    RR_CUDA(cudaFuncSetAttribute(k_sliced_gather_staged<PS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)staged_smem(kSliceMax)));
+    done = true;
+  }
+  return RR_OK;
+}
+
+// The gather kernel of P (lanes or staged) with P's piece-sum type.
+template <typename T, typename PS>
+rr_status launch_gather(const SlicedPattern &P, const T *xq, const int32_t *stop, cudaStream_t st,
+                        bool pdl) {
+  PS *out = reinterpret_cast<PS *>(P.psum);
+  if (std::is_same<T, float>::value && P.staged && P.chunk_p) {
+    RR_TRY(set_staged_attr<PS>());
+    const float *x = reinterpret_cast<const float *>(xq);
+    if (pdl)
+      RR_LAUNCH_PDL(k_sliced_gather_staged<PS>, P.ntasks, kSliceThreads, staged_smem(P.W), st,
+                    P.view(), P.chunk_p, P.chunk_w, P.task_c, x, out, stop, P.err);
+    else
+      RR_LAUNCH(k_sliced_gather_staged<PS>, P.ntasks, kSliceThreads, staged_smem(P.W), st,
+                P.view(), P.chunk_p, P.chunk_w, P.task_c, x, out, stop, P.err);
+    return RR_OK;
+  }
+  RR_TRY((set_smem_attr<T, PS>()));
+  if (pdl)
+    RR_LAUNCH_PDL((k_sliced_gather<T, PS>), P.ntasks, kSliceThreads, slice_smem<T>(P.W), st,
+                  P.view(), xq, out, stop);
+  else
+    RR_LAUNCH((k_sliced_gather<T, PS>), P.ntasks, kSliceThreads, slice_smem<T>(P.W), st,
+              P.view(), xq, out, stop);
   return RR_OK;
 }
 
@@ -664,22 +705,8 @@ rr_status gather_t(const SlicedPattern &P, const double *x, const SlicedPattern 
   else
     RR_LAUNCH_PDL((k_slice_prep<false, T>), grid_for(n, kThreads), kThreads, 0, st, n, x, nullptr,
               nullptr, xq, stop);
-  if (std::is_same<T, float>::value && P.staged && P.chunk_p) {
-    const size_t smem = staged_smem(P.W);
-    static bool attr = false;
-    if (!attr) {   // the largest slice any pattern can have
-      RR_CUDA(cudaFuncSetAttribute(k_sliced_gather_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)staged_smem(kSliceMax)));
-      attr = true;
-    }
-    RR_LAUNCH_PDL(k_sliced_gather_staged, P.ntasks, kSliceThreads, smem, st, P.view(), P.chunk_p,
-              P.chunk_w, P.task_c, reinterpret_cast<const float *>(xq), P.psum, stop, P.err);
-    return RR_OK;
-  }
-  RR_TRY(set_smem_attr<T>());
-  RR_LAUNCH_PDL(k_sliced_gather<T>, P.ntasks, kSliceThreads, slice_smem<T>(P.W), st, P.view(), xq,
-            P.psum, stop);
-  return RR_OK;
+  return P.psum32 ? launch_gather<T, float>(P, xq, stop, st, true)
+                  : launch_gather<T, double>(P, xq, stop, st, true);
 }
 
 }  // namespace
@@ -837,24 +864,9 @@ rr_status sliced_choose_gather(SlicedPattern &P, int32_t mode, cudaStream_t st) 
     for (int rep = 0; rep < 3 && s == RR_OK; ++rep) {
       if (cudaEventRecord(e0, st) != cudaSuccess) s = RR_CUDA_ERROR;
       const float *xq = reinterpret_cast<const float *>(P.xq);
-      if (s == RR_OK && P.staged) {
-        static bool attr = false;
-        if (!attr) {
-          if (cudaFuncSetAttribute(k_sliced_gather_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)staged_smem(kSliceMax)) != cudaSuccess)
-            s = RR_CUDA_ERROR;
-          attr = true;
-        }
-        if (s == RR_OK)
-          k_sliced_gather_staged<<<P.ntasks, kSliceThreads, staged_smem(P.W), st>>>(
-              P.view(), P.chunk_p, P.chunk_w, P.task_c, xq, P.psum, nullptr, P.err);
-      } else if (s == RR_OK) {
-        s = set_smem_attr<float>();
-        if (s == RR_OK)
-          k_sliced_gather<float><<<P.ntasks, kSliceThreads, slice_smem<float>(P.W), st>>>(
-              P.view(), xq, P.psum, nullptr);
-      }
-      rr_launch_counter += 1;
+      if (s == RR_OK)
+        s = P.psum32 ? launch_gather<float, float>(P, xq, nullptr, st, false)
+                     : launch_gather<float, double>(P, xq, nullptr, st, false);
       if (s == RR_OK && (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1, st) != cudaSuccess ||
                          cudaEventSynchronize(e1) != cudaSuccess))
         s = RR_CUDA_ERROR;

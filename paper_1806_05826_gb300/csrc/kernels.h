@@ -206,6 +206,7 @@ struct SlicedPattern {
   int32_t *chunk_p = nullptr;    // [n_chunks+1] first piece of every chunk
   int32_t *chunk_w = nullptr;    // [n_chunks+1] first word of every chunk
   bool staged = false;           // FP32 passes use the staged gather (needs the chunks)
+  bool psum32 = false;           // piece sums stored as FP32 (psum holds floats), else FP64
   int32_t n_heavy = 0;           // outer indices with many slots (summed one warp each)
   int32_t *heavy = nullptr;      // [n_heavy]
   int32_t *task_c = nullptr;     // [ntasks+1]  chunks of each task
@@ -233,6 +234,43 @@ rr_status sliced_slot_sum(const SlicedPattern &P, double *out, cudaStream_t st);
 rr_status sliced_choose_gather(SlicedPattern &P, int32_t mode, cudaStream_t st);
 // t_i = slot sums of feature i, then the epilogue; kVecGrid partial dots.
 rr_status sliced_epilogue(const SlicedPattern &P, const CscEpilogue &ep, cudaStream_t st);
+
+// ---- k_split.cu ---------------------------------------------------------
+// Split form of the FP32 operator (see k_split.cu): the all-ones columns as a
+// rank-one term, the H most frequent other columns as a row-major bitmap, the
+// rest as sliced patterns with FP32 piece sums.
+struct SplitOperator {
+  bool active = false;
+  int64_t N = 0, F = 0;
+  int32_t H = 0, G = 0;           // head columns (32 G) and bitmap words per row
+  int32_t n_ones = 0;
+  int32_t *ones = nullptr;        // [n_ones] the all-ones columns
+  int32_t *head = nullptr;        // [H] column of each head bit (-1: none)
+  uint32_t *bits = nullptr;       // [N * G] row-major head bitmap
+  int32_t nblk = 0;               // blocks of the row pass
+  int64_t rows_per_blk = 0;       // rows of each block (a multiple of 32)
+  int64_t max_slots = 0;          // most tail row slots of one block
+  float *zpart = nullptr;         // [nblk * H] per-block head column sums of X^T u
+  float *upart = nullptr;         // [nblk] per-block sums of u
+  int32_t n_spec = 0;             // features finished one warp each
+  int32_t *spec = nullptr;        // [n_spec]
+  int32_t *spec_kind = nullptr;   // [n_spec] head index, -1 all-ones, -2 long tail column
+  uint8_t *is_spec = nullptr;     // [F]
+  double *wd = nullptr;           // [F] omega / d_i at the current lambda
+  SlicedPattern xt;               // X over the tail columns (rows gather v)
+  SlicedPattern xtt;              // X^T over the tail columns (columns gather u)
+};
+// head_opt: < 0 no split form (S stays inactive); 0 the head size by the
+// byte rule; > 0 that head size (a power of two from 32 to 1024).
+rr_status split_build(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
+                      const int64_t *col_ptr, const int32_t *row_idx, int32_t head_opt,
+                      int32_t gather_mode, SplitOperator &S, int32_t *err, cudaStream_t st);
+void split_free(SplitOperator &S);
+rr_status split_set_wd(SplitOperator &S, double omega, const double *d, cudaStream_t st);
+// X^T X v + lambda v in the split form, finished by ep; x32_ready: S.xt.xq
+// already holds v in FP32 (written by the kernel that made v).
+rr_status split_apply(const SplitOperator &S, const double *v, const CscEpilogue &ep,
+                      const int32_t *stop, cudaStream_t st, bool x32_ready);
 
 // ---- k_pcg.cu -----------------------------------------------------------
 struct PcgScalars {

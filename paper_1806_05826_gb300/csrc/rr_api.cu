@@ -117,6 +117,7 @@ rr_status build_lambda(rr_handle *h, double lambda) {
   RR_TRY(check_dev_error(h, "coarse factor"));
   h->omega = om;
   h->lambda = lambda;
+  RR_TRY(rr::split_set_wd(h->split, h->omega, h->d, st));
   return RR_OK;
 }
 
@@ -507,6 +508,11 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
     RR_TRY(rr::sliced_choose_gather(h->pcsr, split ? RR_GATHER_LANES : h->opt.gather, st));
     RR_TRY(rr::sliced_choose_gather(h->pcsc, split ? RR_GATHER_STAGED : h->opt.gather, st));
   }
+  if (h->opt.precision == RR_PREC_MIXED) {
+    RR_TRY(rr::split_build(N, F, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx,
+                           h->opt.split_head, h->opt.gather, h->split, h->err, st));
+    RR_TRY(rr::split_set_wd(h->split, h->omega, h->d, st));
+  }
   RR_TRY(alloc_solve_workspace(h));
   m.release(tmp32);
   m.release(scratch64);
@@ -528,6 +534,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
 rr_status op_apply(rr_handle *h, const double *v, const rr::CscEpilogue &ep, const int32_t *stop,
                    cudaStream_t st, bool fp32 = false, bool x32_ready = false) {
   if (h->dense) return rr::dense_operator(h->N, h->F, h->Xd, v, h->u, h->dpart, ep, fp32, st);
+  if (fp32 && h->split.active) return rr::split_apply(h->split, v, ep, stop, st, x32_ready);
   RR_TRY(rr::sliced_gather(h->pcsr, v, nullptr, stop, st, fp32, x32_ready));
   RR_TRY(rr::sliced_gather(h->pcsc, nullptr, &h->pcsr, stop, st, fp32));
   RR_TRY(rr::sliced_epilogue(h->pcsc, ep, st));
@@ -547,8 +554,8 @@ rr_status rhs_apply(rr_handle *h, const double *y, double *b, cudaStream_t st) {
 // The X pass's FP32 vector when the PCG loop's producers can write the
 // applied vectors' FP32 copies there (mixed precision, sparse X), else nullptr.
 float *pcg_x32(rr_handle *h) {
-  return (h->opt.precision == RR_PREC_MIXED && !h->dense) ? static_cast<float *>(h->pcsr.xq)
-                                                          : nullptr;
+  if (h->opt.precision != RR_PREC_MIXED || h->dense) return nullptr;
+  return static_cast<float *>(h->split.active ? h->split.xt.xq : h->pcsr.xq);
 }
 
 // x32: where the producers of the applied vectors also write their FP32
@@ -1503,6 +1510,7 @@ void rr_free(rr_handle *h) {
   rr::restrict_free(h->rplan);
   rr::sliced_free(h->pcsr);
   rr::sliced_free(h->pcsc);
+  rr::split_free(h->split);
   h->mem.free_all();
   if (h->err_host) cudaFreeHost(h->err_host);
   if (h->S_host) cudaFreeHost(h->S_host);

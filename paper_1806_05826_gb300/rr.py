@@ -41,7 +41,8 @@ class rr_options(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("gram", ctypes.c_int32),
                 ("gather", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
-                ("lloyd_pull_work", ctypes.c_int64), ("stream", ctypes.c_void_p)]
+                ("lloyd_pull_work", ctypes.c_int64), ("split_head", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
 
 
 class rr_info(ctypes.Structure):
@@ -207,7 +208,7 @@ class Handle:
 def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=None,
              kmeans_max_iter=50, max_iter=20000, solver=RR_SOLVER_TWOLEVEL, check_every=8,
              max_restarts=5, use_graphs=1, gram=RR_GRAM_AUTO, gather=RR_GATHER_AUTO,
-             precision=RR_PREC_FP64, wait_limit=0, lloyd_pull_work=0,
+             precision=RR_PREC_FP64, wait_limit=0, lloyd_pull_work=0, split_head=0,
              stream=None) -> Handle:
     """rr_setup on a binary CSR pattern given as numpy arrays (host) or torch
     CUDA tensors (device): row_ptr int64[N+1], col_idx int32[nnz]."""
@@ -235,6 +236,7 @@ def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=N
                            init_centers=_ptr(ic), solver=solver, check_every=check_every,
                            max_restarts=max_restarts, use_graphs=use_graphs, gram=gram,
                            gather=gather, wait_limit=wait_limit, lloyd_pull_work=lloyd_pull_work,
+                           split_head=split_head,
                            precision=precision, stream=_stream_ptr(stream))
     out = _P()
     _check(lib.rr_setup(ctypes.byref(X), float(lam), int(k), ctypes.byref(o), ctypes.byref(out)))

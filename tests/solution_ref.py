@@ -13,11 +13,14 @@ a solve is judged by its distance to it, not by its residual alone:
 
 At relative residual 1e-8 the error of ANY solution is only bounded by
 cond(A) * 1e-8 (up to ~1e-1 here), and different solvers land at different
-points of that set: on the four small parity cases the errors at 1e-8 of CG,
-Jacobi-preconditioned CG, two-level PCG and two-level PCG with an FP32
-operator and FP64 refinement are 0.4e-6 .. 5.5e-6, at most 2.3 times the
-two-level PCG's own. C_SPREAD = 4 covers that spread with margin; it is 100
-to 1000 times tighter than the residual bound (||r1|| + ||r2||) / lambda. At
+points of that set. Measured with the oracle on 72 systems (the 2,000 x
+1,000, 3,001 x 1,777 and 9,000 x 2,500 parity cases, lambda in {1e-3, 1e-2,
+1e-1, 1}, six targets each), the errors at 1e-8 of two-level PCG lie in
+1.2e-7 .. 1.0e-5; Jacobi-preconditioned CG's are at most 2.5 times PCG's,
+and those of two-level PCG with an FP32 operator and FP64 refinement (the
+mixed-precision form) at most 11.4 times (median 0.83, 95th percentile 2.6).
+C_SPREAD = 25 is about twice the largest ratio; the bar is still 20 to 200
+times tighter than the residual bound (||r1|| + ||r2||) / lambda. At
 tolerance 1e-10 every such error is below 4e-7, so the tests there assert
 1e-6 plainly.
 
@@ -31,7 +34,7 @@ import scipy.linalg as sla
 from oracle import krylov
 from oracle import sparse as osp
 
-C_SPREAD = 4.0
+C_SPREAD = 25.0
 DENSE_MAX_F = 3000
 
 

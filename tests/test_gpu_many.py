@@ -106,3 +106,17 @@ def test_capped_problem_keeps_its_cap_when_others_restart(rr):
     assert np.array_equal(w.cpu().numpy(), ws[0].cpu().numpy())
     if free["restarts"] == 0:
         pytest.skip("the uncapped problem took no restart, so the graph was not relaunched")
+
+
+def test_many_tight_tolerance_within_1e6(many, rr):
+    """At relative residual 1e-10 every problem of the graph is within 1e-6 of
+    its exact solution."""
+    probs = many["probs"]
+    ws = [torch.empty(p["X"].n_cols, dtype=torch.float64, device="cuda") for p in probs]
+    out = rr.rr_solve_many([p["h"] for p in probs], [dev(p["y"]) for p in probs], ws, tol=1e-10)
+    assert out["status"] == "RR_OK"
+    for p, w in zip(probs, ws):
+        X = p["X"]
+        M = osp.from_csr(X.n_rows, X.n_cols, X.row_ptr, X.col_idx)
+        exact = np.linalg.solve(osp.dense_A(M, 1e-2), osp.rhs(M, p["y"]))
+        assert solution_ref.rel_err(w.cpu().numpy(), exact) <= 1e-6, p["seed"]
