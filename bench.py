@@ -71,6 +71,9 @@ def parse():
                     help="one untimed step and nothing else (for a profiler's launch list)")
     ap.add_argument("--roofline-only", action="store_true",
                     help="one setup, then only the operator-apply kernel timings (profiling runs)")
+    ap.add_argument("--profile-apply", type=int, default=0, metavar="K",
+                    help="one setup and three warm-up applies, then K operator applies between "
+                         "cudaProfilerStart/Stop (ncu --profile-from-start off); nothing timed")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="mixed: FP32 operator inside CG + FP64 refinement; fp64: FP64 throughout")
     return ap.parse_args()
@@ -306,11 +309,15 @@ def measure_roofline(rr, row_ptr, col_idx, N, F, nnz, k, lams, opts, dev, stream
     dom = "A_v"
     peak, peak_kind = peaks()
     achieved = algo[dom] / (kern[dom] * 1e-3) / 1e9
-    return {"bound": "hbm", "kernel": "operator apply (k_sliced_gather x2 + k_sliced_epilogue)",
+    return {"bound": "hbm",
+            "kernel": "operator apply, split form (tail gathers x2, k_split_rows, k_split_epilogue)"
+                      if opts.get("precision") == rr.RR_PREC_MIXED else
+                      "operator apply (k_sliced_gather x2 + k_sliced_epilogue)",
             "achieved": round(achieved, 1), "peak": peak,
             "peak_kind": f"{peak_kind} (burst copy)", "unit": "GB/s",
             "frac": round(achieved / peak, 4),
-            "traffic": profiled_traffic("operator_apply", workload),
+            "traffic": profiled_traffic("operator_apply_split" if opts.get("precision") ==
+                                        rr.RR_PREC_MIXED else "operator_apply", workload),
             "algorithmic_bytes": algo[dom], "launch_ms": round(kern[dom], 4),
             "parts": {n: {"ms": round(t, 4), "achieved_gbs": round(algo[n] / (t * 1e-3) / 1e9, 1)}
                       for n, t in kern.items() if n != dom}}
@@ -349,17 +356,41 @@ def measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world, n_targ
     t_batch = e0.elapsed_time(e1) / 1000.0
     infos = [i for row in out["infos"] for i in row]
     assert out["status"] == "RR_OK" and max(i["true_rel_res"] for i in infos) <= TOL
-    # plain two-level PCG on a sample: target 0 at every weight, one solve each
+    # the plain two-level PCG on every system, one solve after the other on the
+    # same handle (the same setup; rr_set_lambda per weight), timed with events
     w = torch.empty(F, dtype=torch.float64, device=dev)
-    plain_ms = []
+    plain_ms, e2 = [], [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     for lam in lams:
         rr.rr_set_lambda(h, lam)
-        inf = rr.rr_solve(h, Yd[0], w, tol=TOL)
-        assert inf["status"] == "RR_OK"
-        plain_ms.append(inf["solve_ms"])
+        e2[0].record(stream)
+        for j in range(len(seeds)):
+            inf = rr.rr_solve(h, Yd[j], w, tol=TOL)
+            assert inf["status"] == "RR_OK"
+        e2[1].record(stream)
+        torch.cuda.synchronize(dev)
+        plain_ms.append(e2[0].elapsed_time(e2[1]))
     n_sys = len(infos)
     setup_s = infos[0]["setup_ms"] / 1000.0
-    t_plain = setup_s + n_sys * statistics.mean(plain_ms) / 1000.0
+    t_plain = setup_s + sum(plain_ms) / 1000.0
+    # the operator apply of the whole batch (both FP32 passes over every slab,
+    # the autotuned variant), against its algorithmic bytes: the two index
+    # streams once per slab, V read, U written and read, Z written; and the
+    # row-segment gathers (every index fetches 4 bytes per system of its slab)
+    q = rr.rr_query_batch(h)
+    ld = -(-n_sys // 64) * 64
+    nnz = X.nnz
+    slabs = -(-ld // q["slab_width"])
+    alg = slabs * 8 * nnz + 4 * F * ld + 8 * N * ld + 4 * F * ld
+    peak, peak_kind = peaks()
+    sec = q["apply_ms"] * 1e-3
+    batched_roofline = {
+        "bound": "l2 (row-segment gathers)", "kernel": "batched SpMM apply (k_bspmm x2)",
+        "slab_width": q["slab_width"], "unroll": q["unroll"], "apply_ms": round(q["apply_ms"], 4),
+        "algorithmic_bytes": alg, "achieved": round(alg / sec / 1e9, 1), "unit": "GB/s",
+        "peak": peak, "peak_kind": f"{peak_kind} (burst copy)",
+        "frac": round(alg / sec / 1e9 / peak, 4),
+        "l2_gather_bytes": 2 * nnz * ld * 4, "l2_gather_tbs": round(2 * nnz * ld * 4 / sec / 1e12, 2),
+        "per_system_apply_us": round(q["apply_ms"] * 1e3 / n_sys, 2)}
     rr.rr_free(h)
     its = sorted(i["iters"] for i in infos)
     return {"workload": name, "systems": n_sys, "targets": len(seeds), "lambdas": lams,
@@ -368,10 +399,11 @@ def measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world, n_targ
             "iters_min_median_max": [its[0], its[len(its) // 2], its[-1]],
             "restarts_max": max(i["restarts"] for i in infos),
             "true_rel_res_max": max(i["true_rel_res"] for i in infos),
-            "plain_sampled_solve_ms": [round(t, 2) for t in plain_ms],
-            "plain_estimate_s": round(t_plain, 3),
+            "plain_solve_ms_per_lambda": [round(t, 2) for t in plain_ms],
+            "plain_s": round(t_plain, 3),
             "speedup_vs_plain": round(t_plain / t_batch, 2),
-            "note": "plain = setup + systems x mean single-solve time of target 0 at the 8 weights"}
+            "roofline": batched_roofline,
+            "note": "plain = one setup + rr_solve of every system one after the other"}
 
 
 def measure_tlfcg(rr, row_ptr, col_idx, N, F, k, lams, opts, y_dev, last_infos):
@@ -598,6 +630,20 @@ def run_ours(args, rank, world, local):
                         "staged": rr.RR_GATHER_STAGED,
                         "lanes-staged": rr.RR_GATHER_LANES_STAGED}[args.gather])
 
+    if args.profile_apply:
+        h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], k, **opts)
+        v = torch.randn(F, dtype=torch.float64, device=dev)
+        z = torch.empty(F, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            rr.rr_apply(h, v, z)
+        torch.cuda.synchronize(dev)
+        torch.cuda.cudart().cudaProfilerStart()
+        for _ in range(args.profile_apply):
+            rr.rr_apply(h, v, z)
+        torch.cuda.synchronize(dev)
+        torch.cuda.cudart().cudaProfilerStop()
+        rr.rr_free(h)
+        return {"profile_apply": args.profile_apply, "workload": args.workload}
     if args.roofline_only:
         return {"workload": args.workload, "precision": args.precision,
                 "roofline": measure_roofline(rr, row_ptr, col_idx, N, F, nnz, k, lams, opts, dev,

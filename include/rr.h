@@ -384,6 +384,19 @@ rr_status rr_apply_noalloc(int64_t n_rows, int64_t n_cols, const int64_t *row_pt
                            const int32_t *col_idx, const int64_t *col_ptr, const int32_t *row_idx,
                            double lambda, const double *v, double *out, void *stream);
 
+/* The batched engine's sparse-times-dense variant chosen by its autotuner for
+ * the last rr_solve_batch (or rr_harvest) on h: systems per slab (32, 64 or
+ * 128: the columns one warp carries through a pass over X) and row segments
+ * in flight per warp (4 or 8). Every candidate is timed on the two FP32
+ * passes of one operator apply over all slabs at the first batched call for
+ * a given (N, F, nnz, padded batch width) in the process, and the fastest is
+ * kept; apply_ms is its time (both passes, every system of the batch). All
+ * variants sum in the same order, so the choice does not change results.
+ * (No counterpart in the paper.) Any output pointer may be NULL. Errors:
+ * RR_INVALID_ARG (NULL handle, or no batched call yet). */
+rr_status rr_query_batch(const rr_handle *h, int32_t *slab_width, int32_t *unroll,
+                         double *apply_ms);
+
 /* Number of kernels the library has launched from the calling thread since it
  * was loaded (counts every launch of every call, setup included). */
 int64_t rr_launch_count(void);

@@ -25,6 +25,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -45,7 +48,7 @@ struct BatchCol {   // CG state of one system
   int32_t conv, first, iters, nonfinite;
 };
 struct BatchGlobal {
-  int32_t iter, limit, any_active, pad;
+  int32_t iter, limit, any_active, rounds;   // rounds: refinement rounds run by the graph
 };
 
 enum BEpiMode : int32_t { BEPI_PRE = 0, BEPI_POST = 1, BEPI_PCG = 2, BEPI_RESID = 3 };
@@ -57,6 +60,13 @@ struct BEpi {
   double *part;      // [kBEpiBlocks][ld] partial dots: <r,z> (POST), <p,q> (PCG), ||rt||^2 (RESID)
 };
 enum BFinMode : int32_t { BFIN_BNORM = 0, BFIN_RZ = 1, BFIN_PQ = 2, BFIN_RR = 3, BFIN_TRUE = 4 };
+
+// The SpMM variant: C columns per lane (slabs of 32 C systems), UNROLL row
+// segments in flight per warp. Every variant sums every column in the same
+// order, so the choice changes the speed only.
+struct SpmmConfig {
+  int32_t C = 2, unroll = 8;
+};
 
 struct BatchState {
   int32_t cap_ld = 0, cap_lam = 0;     // workspace capacity (columns, weights)
@@ -74,31 +84,52 @@ struct BatchState {
   BatchCol *col = nullptr, *col_host = nullptr;
   BatchGlobal *g = nullptr, *g_host = nullptr;
   int32_t *slab_active = nullptr, *slab_host = nullptr, *flag = nullptr, *flag_host = nullptr;
+  int32_t *state = nullptr, *restarts = nullptr;      // [ld] refinement state on the device
+  int32_t *state_host = nullptr, *restarts_host = nullptr;
   cudaStream_t cs = nullptr;
+  SpmmConfig spmm;                     // the FP32 SpMM variant in use (autotuned)
+  double spmm_ms = 0.0;                // its time for one apply (both passes, all slabs)
   DevArena mem;
 };
 
 namespace {
 
-template <class T>
-struct Vec2;
-template <>
-struct Vec2<float> {
-  using type = float2;
+// C consecutive values of T loaded and stored together (C = 1, 2 or 4).
+template <class T, int C>
+struct Pack {
+  T v[C];
 };
-template <>
-struct Vec2<double> {
-  using type = double2;
-};
+template <class T, int C>
+__device__ __forceinline__ Pack<T, C> load_pack(const T *p) {
+  Pack<T, C> r;
+  if constexpr (C == 4 && sizeof(T) == 4) {
+    const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+  } else if constexpr (C == 2 && sizeof(T) == 4) {
+    const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+    r.v[0] = t.x; r.v[1] = t.y;
+  } else if constexpr (C == 2 && sizeof(T) == 8) {
+    const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+    r.v[0] = t.x; r.v[1] = t.y;
+  } else {
+#pragma unroll
+    for (int q = 0; q < C; ++q) r.v[q] = __ldg(p + q);
+  }
+  return r;
+}
 
 // ---------------------------------------------------------------- sparse x dense passes
 
 // out[u, slab] = sum over the indices of unit u of V[index, slab]. Units are
 // [ubeg[u], uend[u]) ranges of idx (rows of the CSR for pass 1, column chunks
-// of the CSC for pass 2). The 32 indices of a step are loaded once, coalesced,
-// and broadcast by shuffles; UNROLL row segments are in flight per warp.
-// Sums run in index order (deterministic).
-template <class T, int UNROLL>
+// of the CSC for pass 2). A slab is 32 C columns (lane l holds columns
+// C l .. C l + C - 1); grid.y walks the slabs. The 32 indices of a step are
+// loaded once, coalesced, and broadcast by shuffles; UNROLL row segments are
+// in flight per warp. Every column is summed in index order, whatever C and
+// UNROLL (deterministic, and the same bits for every variant the autotuner
+// may pick). A slab runs when one of the 64-column activity flags it covers
+// is set (slab_active: per 64 columns; null = all).
+template <class T, int UNROLL, int C>
 __global__ void __launch_bounds__(kThreads) k_bspmm(int64_t n_units, const int64_t *__restrict__ ubeg,
                                                     const int64_t *__restrict__ uend,
                                                     const int32_t *__restrict__ idx,
@@ -106,45 +137,48 @@ __global__ void __launch_bounds__(kThreads) k_bspmm(int64_t n_units, const int64
                                                     T *__restrict__ out, int64_t ldo,
                                                     const int32_t *__restrict__ slab_active) {
   pdl_wait();
-  using V2 = typename Vec2<T>::type;
-  const int slab = blockIdx.y;
-  if (slab_active && !slab_active[slab]) return;
+  constexpr int W = 32 * C;
+  const int64_t col0 = (int64_t)blockIdx.y * W;
+  if (slab_active) {
+    bool any = false;
+    for (int64_t s = col0 / kSlab; s <= (col0 + W - 1) / kSlab; ++s) any |= slab_active[s] != 0;
+    if (!any) return;
+  }
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const V2 *Vs = reinterpret_cast<const V2 *>(V + (int64_t)slab * kSlab) + lane;
-  const int64_t ldv2 = ldv >> 1;
+  const T *Vs = V + col0 + C * lane;
   for (int64_t u = warp; u < n_units; u += nwarps) {
     const int64_t b = ubeg[u], e = uend[u];
-    T ax = 0, ay = 0;
+    T a[C];
+#pragma unroll
+    for (int q = 0; q < C; ++q) a[q] = 0;
     for (int64_t p0 = b; p0 < e; p0 += 32) {
       const int cnt = (int)min((int64_t)32, e - p0);
       const int32_t mine = lane < cnt ? __ldg(idx + p0 + lane) : 0;
       int j = 0;
       for (; j + UNROLL <= cnt; j += UNROLL) {
-        V2 t[UNROLL];
+        Pack<T, C> t[UNROLL];
 #pragma unroll
         for (int s = 0; s < UNROLL; ++s) {
           const int32_t i = __shfl_sync(0xffffffffu, mine, j + s);
-          t[s] = __ldg(Vs + (int64_t)i * ldv2);
+          t[s] = load_pack<T, C>(Vs + (int64_t)i * ldv);
         }
 #pragma unroll
-        for (int s = 0; s < UNROLL; ++s) {
-          ax += t[s].x;
-          ay += t[s].y;
-        }
+        for (int s = 0; s < UNROLL; ++s)
+#pragma unroll
+          for (int q = 0; q < C; ++q) a[q] += t[s].v[q];
       }
       for (; j < cnt; ++j) {
         const int32_t i = __shfl_sync(0xffffffffu, mine, j);
-        const V2 t = __ldg(Vs + (int64_t)i * ldv2);
-        ax += t.x;
-        ay += t.y;
+        const Pack<T, C> t = load_pack<T, C>(Vs + (int64_t)i * ldv);
+#pragma unroll
+        for (int q = 0; q < C; ++q) a[q] += t.v[q];
       }
     }
-    V2 o;
-    o.x = ax;
-    o.y = ay;
-    reinterpret_cast<V2 *>(out + u * ldo + (int64_t)slab * kSlab)[lane] = o;
+    T *o = out + u * ldo + col0 + C * lane;
+#pragma unroll
+    for (int q = 0; q < C; ++q) o[q] = a[q];
   }
 }
 
@@ -622,6 +656,59 @@ __global__ void k_bloop_condition(cudaGraphConditionalHandle hc, const BatchGlob
   if (threadIdx.x == 0) cudaGraphSetConditional(hc, (g->any_active && g->iter < g->limit) ? 1u : 0u);
 }
 
+// ---- iterative refinement on the device (the rules of the host-driven loop)
+
+__global__ void k_brefine_clear(BatchGlobal *g, int32_t *slab_active, int32_t n_slabs) {
+  pdl_wait();
+  if (threadIdx.x == 0) g->any_active = 0;
+  for (int32_t s = threadIdx.x; s < n_slabs; s += blockDim.x) slab_active[s] = 0;
+}
+
+// After a true residual: a system is done when ||b - A w|| meets its target;
+// it has failed on a non-finite value or at the iteration or restart cap;
+// otherwise it restarts CG from w on the true residual with a fresh direction
+// (flag[c] = 1, its slab and the loop marked active). state: 0 running, 1
+// done, 2 failed.
+__global__ void k_brefine(int32_t S, BatchCol *col, int32_t *state, int32_t *restarts,
+                          int32_t max_restarts, int32_t max_iter, BatchGlobal *g, int32_t *flag,
+                          int32_t *slab_active) {
+  pdl_wait();
+  const int32_t iter = g->iter;
+  for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < S; c += gridDim.x * blockDim.x) {
+    flag[c] = 0;
+    if (state[c] != 0) continue;
+    BatchCol &C = col[c];
+    if (C.nonfinite || !isfinite(C.true_rr)) {
+      state[c] = 2;
+      continue;
+    }
+    if (sqrt(C.true_rr) <= C.target) {
+      state[c] = 1;
+      continue;
+    }
+    if (iter >= max_iter || restarts[c] >= max_restarts) {
+      state[c] = 2;
+      continue;
+    }
+    restarts[c] += 1;
+    C.conv = 0;
+    C.first = 1;
+    C.rr = C.true_rr;
+    flag[c] = 1;
+    atomicOr(&slab_active[c / kSlab], 1);
+    atomicOr(&g->any_active, 1);
+  }
+}
+
+// End of a refinement round: another round while a system restarted.
+__global__ void k_bround_condition(cudaGraphConditionalHandle outer, BatchGlobal *g) {
+  pdl_wait();
+  if (threadIdx.x == 0) {
+    g->rounds += 1;
+    cudaGraphSetConditional(outer, g->any_active ? 1u : 0u);
+  }
+}
+
 // Y (nrhs targets of length N, target j at Y + j N) -> Yr (N x ldy row-major, zero padding).
 __global__ void k_btranspose_in(int64_t N, int32_t nrhs, int64_t ldy, const double *__restrict__ Y,
                                 double *__restrict__ Yr) {
@@ -702,15 +789,33 @@ __global__ void k_binv_pad(int32_t k, int32_t kpad, const double *__restrict__ A
 
 inline int64_t round_up64(int64_t a) { return (a + kSlab - 1) / kSlab * kSlab; }
 
+template <class T, int U, int C>
+rr_status launch_bspmm_v(int64_t n_units, const int64_t *ubeg, const int64_t *uend,
+                         const int32_t *idx, const T *V, int64_t ldv, T *out, int64_t ldo,
+                         int64_t ld, const int32_t *slab_active, cudaStream_t st) {
+  const dim3 grid((unsigned)grid_for(n_units, kWarps), (unsigned)(ld / (32 * C)));
+  RR_LAUNCH_PDL((k_bspmm<T, U, C>), grid, kThreads, 0, st, n_units, ubeg, uend, idx, V, ldv, out,
+                ldo, slab_active);
+  return RR_OK;
+}
+
+// ld columns (a multiple of 64; of 128 when C = 4) of V through the pattern.
 template <class T>
 rr_status launch_bspmm(int64_t n_units, const int64_t *ubeg, const int64_t *uend, const int32_t *idx,
-                       const T *V, int64_t ldv, T *out, int64_t ldo, int32_t n_slabs,
-                       const int32_t *slab_active, cudaStream_t st) {
-  const dim3 grid((unsigned)grid_for(n_units, kWarps), (unsigned)n_slabs);
-  constexpr int kUnroll = sizeof(T) == 4 ? 8 : 4;   // row segments in flight per warp
-  RR_LAUNCH_PDL((k_bspmm<T, kUnroll>), grid, kThreads, 0, st, n_units, ubeg, uend, idx, V, ldv, out, ldo,
-            slab_active);
-  return RR_OK;
+                       const T *V, int64_t ldv, T *out, int64_t ldo, int64_t ld,
+                       const int32_t *slab_active, cudaStream_t st,
+                       SpmmConfig cfg = SpmmConfig{2, sizeof(T) == 4 ? 8 : 4}) {
+#define RR_BSPMM(U_, C_)                                                                    \
+  if (cfg.unroll == U_ && cfg.C == C_)                                                      \
+    return launch_bspmm_v<T, U_, C_>(n_units, ubeg, uend, idx, V, ldv, out, ldo, ld,        \
+                                     slab_active, st);
+  RR_BSPMM(4, 1) RR_BSPMM(4, 2) RR_BSPMM(8, 1) RR_BSPMM(8, 2)
+  if constexpr (sizeof(T) == 4) {
+    RR_BSPMM(4, 4) RR_BSPMM(8, 4)
+  }
+#undef RR_BSPMM
+  rr_set_error("batched SpMM: no variant with %d columns per lane, unroll %d", cfg.C, cfg.unroll);
+  return RR_UNSUPPORTED;
 }
 
 // Training-pair capture of rr_harvest (see include/rr.h): slot it * S + c
@@ -737,9 +842,9 @@ rr_status bapply_f32(const BatchRun &R, cudaStream_t st) {
   rr_handle *h = R.h;
   BatchState *B = R.B;
   RR_TRY(launch_bspmm<float>(h->N, h->row_ptr, h->row_ptr + 1, h->col_idx, B->V, R.ld, B->U, R.ld,
-                             R.n_slabs, B->slab_active, st));
+                             R.ld, B->slab_active, st, B->spmm));
   RR_TRY(launch_bspmm<float>(B->n_units2, B->ubeg2, B->uend2, h->row_idx, B->U, R.ld, B->Zp, R.ld,
-                             R.n_slabs, B->slab_active, st));
+                             R.ld, B->slab_active, st, B->spmm));
   return RR_OK;
 }
 
@@ -807,9 +912,9 @@ rr_status btrue_residual(const BatchRun &R, cudaStream_t st) {
   rr_handle *h = R.h;
   BatchState *B = R.B;
   RR_TRY(launch_bspmm<double>(h->N, h->row_ptr, h->row_ptr + 1, h->col_idx, B->w, R.ld, B->U64,
-                              R.ld, R.n_slabs, nullptr, st));
+                              R.ld, R.ld, nullptr, st));
   RR_TRY(launch_bspmm<double>(B->n_units2, B->ubeg2, B->uend2, h->row_idx, B->U64, R.ld, B->Zp64,
-                              R.ld, R.n_slabs, nullptr, st));
+                              R.ld, R.ld, nullptr, st));
   const dim3 grid(kBEpiBlocks, (unsigned)R.n_slabs);
   RR_LAUNCH_PDL(k_bepi<double>, grid, kThreads, 0, st, h->F, R.S, R.ld, B->uptr2, B->Zp64, h->col_ptr,
             B->col, BEpi{BEPI_RESID, B->w, B->b, B->rt, B->part});
@@ -886,6 +991,10 @@ rr_status batch_reserve(rr_handle *h, int64_t ld, int32_t nlam) {
   RR_TRY(B->mem.alloc(&B->g, 1));
   RR_TRY(B->mem.alloc(&B->slab_active, ld / kSlab));
   RR_TRY(B->mem.alloc(&B->flag, ld));
+  RR_TRY(B->mem.alloc(&B->state, ld));
+  RR_TRY(B->mem.alloc(&B->restarts, ld));
+  RR_CUDA(cudaMallocHost(&B->state_host, sizeof(int32_t) * ld));
+  RR_CUDA(cudaMallocHost(&B->restarts_host, sizeof(int32_t) * ld));
   RR_CUDA(cudaMallocHost(&B->col_host, sizeof(BatchCol) * ld));
   RR_CUDA(cudaMallocHost(&B->g_host, sizeof(BatchGlobal)));
   RR_CUDA(cudaMallocHost(&B->slab_host, sizeof(int32_t) * (ld / kSlab)));
@@ -973,6 +1082,167 @@ rr_status build_loop(const BatchRun &R, LoopGraph &L) {
   return RR_OK;
 }
 
+// The whole batched solve as one graph: an outer conditional while node (one
+// refinement round per run) whose body is the iteration loop (an inner
+// conditional while node, the single-level loop's body) followed by the FP64
+// true residual of every system, the refinement decisions (k_brefine), the
+// restarts and the two loop conditions. One launch runs every round; the
+// host reads the systems' state once at the end.
+struct SolveGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t body_kernels = 0, round_kernels = 0;
+  ~SolveGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (g) cudaGraphDestroy(g);
+  }
+};
+
+rr_status build_solve_graph(const BatchRun &R, SolveGraph &L) {
+  BatchState *B = R.B;
+  rr_handle *h = R.h;
+  cudaStream_t cs = B->cs;
+  const int64_t l0 = rr_launch_counter;
+  RR_CUDA(cudaGraphCreate(&L.g, 0));
+  cudaGraphConditionalHandle ho, hi;
+  RR_CUDA(cudaGraphConditionalHandleCreate(&ho, L.g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams op{};
+  op.type = cudaGraphNodeTypeConditional;
+  op.conditional.handle = ho;
+  op.conditional.type = cudaGraphCondTypeWhile;
+  op.conditional.size = 1;
+  cudaGraphNode_t onode, inode;
+  RR_CUDA(cudaGraphAddNode(&onode, L.g, nullptr, nullptr, 0, &op));
+  cudaGraph_t obody = op.conditional.phGraph_out[0];
+  RR_CUDA(cudaGraphConditionalHandleCreate(&hi, obody, 1, cudaGraphCondAssignDefault));
+  auto fail = [&](rr_status s, cudaError_t ec) -> rr_status {
+    cudaGraphDestroy(L.g);
+    L.g = nullptr;
+    cudaGetLastError();
+    rr_launch_counter = l0;
+    if (s != RR_OK) return s;
+    rr_set_error("batched solve graph capture failed: %s", cudaGetErrorString(ec));
+    return RR_CUDA_ERROR;
+  };
+  // a round starts by setting the loop's condition (the loop runs while a
+  // system is active and below the limit, as the host-driven form)
+  RR_CUDA(cudaStreamBeginCaptureToGraph(cs, obody, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal));
+  k_bloop_condition<<<1, 32, 0, cs>>>(hi, B->g);
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t ec = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+  std::vector<cudaGraphNode_t> first(deps, deps + (ec == cudaSuccess ? ndeps : 0));
+  cudaGraph_t cap = nullptr;
+  const cudaError_t ec2 = cudaStreamEndCapture(cs, &cap);
+  if (ec != cudaSuccess || ec2 != cudaSuccess || first.size() != 1)
+    return fail(RR_OK, ec != cudaSuccess ? ec : ec2 != cudaSuccess ? ec2 : cudaErrorUnknown);
+  cudaGraphNodeParams ip{};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = hi;
+  ip.conditional.type = cudaGraphCondTypeWhile;
+  ip.conditional.size = 1;
+  RR_CUDA(cudaGraphAddNode(&inode, obody, first.data(), nullptr, 1, &ip));
+  // the iteration loop
+  RR_CUDA(cudaStreamBeginCaptureToGraph(cs, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal));
+  int64_t c0 = rr_launch_counter;
+  rr_status s = biteration(R, cs);
+  if (s == RR_OK) {
+    k_bloop_condition<<<1, 32, 0, cs>>>(hi, B->g);
+    ++rr_launch_counter;
+  }
+  L.body_kernels = rr_launch_counter - c0;
+  ec = cudaStreamEndCapture(cs, &cap);
+  if (s != RR_OK || ec != cudaSuccess) return fail(s, ec);
+  // the end of a round, after the loop
+  RR_CUDA(cudaStreamBeginCaptureToGraph(cs, obody, &inode, nullptr, 1,
+                                        cudaStreamCaptureModeThreadLocal));
+  c0 = rr_launch_counter;
+  s = btrue_residual(R, cs);
+  if (s == RR_OK) {
+    k_brefine_clear<<<1, 256, 0, cs>>>(B->g, B->slab_active, R.n_slabs);
+    k_brefine<<<(unsigned)((R.S + 255) / 256), 256, 0, cs>>>(
+        R.S, B->col, B->state, B->restarts, h->opt.max_restarts, h->opt.max_iter, B->g, B->flag,
+        B->slab_active);
+    rr_launch_counter += 2;
+    const dim3 vgrid(kBEpiBlocks, (unsigned)R.n_slabs);
+    k_brestart<<<vgrid, kThreads, 0, cs>>>(h->F, R.S, R.ld, B->flag, h->col_ptr, B->col, B->rt,
+                                           B->r, B->z1, B->V);
+    k_bround_condition<<<1, 32, 0, cs>>>(ho, B->g);
+    rr_launch_counter += 3;   // with the loop condition set at the start of the round
+    if (cudaGetLastError() != cudaSuccess) s = RR_CUDA_ERROR;
+  }
+  L.round_kernels = rr_launch_counter - c0;
+  ec = cudaStreamEndCapture(cs, &cap);
+  if (s != RR_OK || ec != cudaSuccess) return fail(s, ec);
+  rr_launch_counter = l0;   // recorded, not launched
+  RR_CUDA(cudaGraphInstantiate(&L.exec, L.g, 0));
+  return RR_OK;
+}
+
+// The fastest SpMM variant for this pattern and batch width: every candidate
+// (columns per lane x row segments in flight) timed on the operator's two
+// FP32 passes over all slabs, once per (N, F, nnz, ld) in the process.
+rr_status batch_autotune(const BatchRun &R, cudaStream_t st) {
+  static std::mutex mu;
+  static std::map<std::array<int64_t, 4>, std::pair<SpmmConfig, double>> cache;
+  rr_handle *h = R.h;
+  BatchState *B = R.B;
+  const std::array<int64_t, 4> key{h->N, h->F, h->nnz, R.ld};
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      B->spmm = it->second.first;
+      B->spmm_ms = it->second.second;
+      return RR_OK;
+    }
+  }
+  std::vector<SpmmConfig> cands;
+  for (int32_t c : {1, 2, 4})
+    for (int32_t u : {4, 8})
+      if (c < 4 || R.ld % 128 == 0) cands.push_back(SpmmConfig{c, u});
+  cudaEvent_t e0, e1;
+  RR_CUDA(cudaEventCreate(&e0));
+  RR_CUDA(cudaEventCreate(&e1));
+  SpmmConfig best = B->spmm;
+  float best_ms = 0.f;
+  rr_status s = RR_OK;
+  for (const SpmmConfig &c : cands) {
+    float t = 0.f;
+    for (int rep = 0; rep < 3 && s == RR_OK; ++rep) {
+      if (cudaEventRecord(e0, st) != cudaSuccess) s = RR_CUDA_ERROR;
+      if (s == RR_OK)
+        s = launch_bspmm<float>(h->N, h->row_ptr, h->row_ptr + 1, h->col_idx, B->V, R.ld, B->U,
+                                R.ld, R.ld, nullptr, st, c);
+      if (s == RR_OK)
+        s = launch_bspmm<float>(B->n_units2, B->ubeg2, B->uend2, h->row_idx, B->U, R.ld, B->Zp,
+                                R.ld, R.ld, nullptr, st, c);
+      float ms = 0.f;
+      if (s == RR_OK && (cudaEventRecord(e1, st) != cudaSuccess ||
+                         cudaEventSynchronize(e1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        s = RR_CUDA_ERROR;
+      if (rep == 1 || (rep > 1 && ms < t)) t = ms;   // the first run is a warm-up
+    }
+    if (s != RR_OK) break;
+    if (best_ms == 0.f || t < best_ms) {
+      best_ms = t;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  RR_TRY(s);
+  B->spmm = best;
+  B->spmm_ms = best_ms;
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = {best, (double)best_ms};
+  return RR_OK;
+}
+
 // Runs batched iterations until every system has stopped or the limit.
 rr_status brun(const BatchRun &R, LoopGraph *L, int32_t check_every) {
   BatchState *B = R.B;
@@ -1003,6 +1273,8 @@ void batch_free(BatchState *B) {
   if (B->g_host) cudaFreeHost(B->g_host);
   if (B->slab_host) cudaFreeHost(B->slab_host);
   if (B->flag_host) cudaFreeHost(B->flag_host);
+  if (B->state_host) cudaFreeHost(B->state_host);
+  if (B->restarts_host) cudaFreeHost(B->restarts_host);
   delete B;
 }
 
@@ -1070,7 +1342,7 @@ extern "C" rr_status rr_solve_batch(rr_handle *h, int32_t nrhs, const double *Y,
   const dim3 tgrid((unsigned)((N + 31) / 32), (unsigned)(ldy / 32));
   RR_LAUNCH(k_btranspose_in, tgrid, dim3(32, 8), 0, st, N, nrhs, ldy, Y, B->U64);
   RR_TRY(launch_bspmm<double>(B->n_units2, B->ubeg2, B->uend2, h->row_idx, B->U64, ldy, B->Zp64,
-                              ldy, (int32_t)(ldy / kSlab), nullptr, st));
+                              ldy, ldy, nullptr, st));
   const dim3 vgrid(kBEpiBlocks, (unsigned)n_slabs);
   RR_LAUNCH_PDL(k_bstart, vgrid, kThreads, 0, st, F, S, nrhs, ld, B->uptr2, B->Zp64, ldy, h->col_ptr,
             B->col, B->b, B->w, B->r, B->z1, B->V, B->part);
@@ -1083,51 +1355,72 @@ extern "C" rr_status rr_solve_batch(rr_handle *h, int32_t nrhs, const double *Y,
   RR_CUDA(cudaMemcpyAsync(B->g_host, B->g, sizeof(BatchGlobal), cudaMemcpyDeviceToHost, st));
   RR_CUDA(cudaStreamSynchronize(st));
 
+  RR_TRY(batch_autotune(R, st));
   std::vector<int32_t> restarts(S, 0), state(S, 0);   // state: 0 running, 1 done, 2 failed
-  LoopGraph graph;
-  if (h->opt.use_graphs) RR_TRY(build_loop(R, graph));
   rr_status result = RR_OK;
-  for (;;) {
-    if (B->g_host->any_active) RR_TRY(brun(R, h->opt.use_graphs ? &graph : nullptr, h->opt.check_every));
-    RR_TRY(btrue_residual(R, st));
+  if (h->opt.use_graphs) {
+    // every refinement round in one graph launch; the state is read once at the end
+    RR_CUDA(cudaMemsetAsync(B->state, 0, sizeof(int32_t) * S, st));
+    RR_CUDA(cudaMemsetAsync(B->restarts, 0, sizeof(int32_t) * S, st));
+    SolveGraph graph;
+    RR_TRY(build_solve_graph(R, graph));
+    RR_CUDA(cudaGraphLaunch(graph.exec, st));
     RR_CUDA(cudaMemcpyAsync(B->col_host, B->col, sizeof(BatchCol) * ld, cudaMemcpyDeviceToHost, st));
     RR_CUDA(cudaMemcpyAsync(B->g_host, B->g, sizeof(BatchGlobal), cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaMemcpyAsync(B->state_host, B->state, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaMemcpyAsync(B->restarts_host, B->restarts, sizeof(int32_t) * S,
+                            cudaMemcpyDeviceToHost, st));
     RR_CUDA(cudaStreamSynchronize(st));
-    bool any = false;
-    for (int64_t s = 0; s < n_slabs; ++s) B->slab_host[s] = 0;
+    rr_launch_counter += 1 + graph.body_kernels * (int64_t)B->g_host->iter +
+                         graph.round_kernels * (int64_t)B->g_host->rounds;
     for (int32_t c = 0; c < S; ++c) {
-      BatchCol &C = B->col_host[c];
-      B->flag_host[c] = 0;
-      if (state[c] != 0) continue;
-      if (C.nonfinite || !isfinite(C.true_rr)) {
-        state[c] = 2;
-        continue;
-      }
-      if (sqrt(C.true_rr) <= C.target) {
-        state[c] = 1;
-        continue;
-      }
-      if (B->g_host->iter >= h->opt.max_iter || restarts[c] >= h->opt.max_restarts) {
-        state[c] = 2;
-        continue;
-      }
-      // refinement: continue from w on the true residual with a fresh direction
-      ++restarts[c];
-      C.conv = 0;
-      C.first = 1;
-      C.rr = C.true_rr;
-      B->flag_host[c] = 1;
-      B->slab_host[c / kSlab] = 1;
-      any = true;
+      state[c] = B->state_host[c];
+      restarts[c] = B->restarts_host[c];
     }
-    if (!any) break;
-    RR_CUDA(cudaMemcpyAsync(B->col, B->col_host, sizeof(BatchCol) * ld, cudaMemcpyHostToDevice, st));
-    RR_CUDA(cudaMemcpyAsync(B->flag, B->flag_host, sizeof(int32_t) * S, cudaMemcpyHostToDevice, st));
-    RR_CUDA(cudaMemcpyAsync(B->slab_active, B->slab_host, sizeof(int32_t) * n_slabs, cudaMemcpyHostToDevice, st));
-    B->g_host->any_active = 1;
-    RR_CUDA(cudaMemcpyAsync(B->g, B->g_host, sizeof(BatchGlobal), cudaMemcpyHostToDevice, st));
-    RR_LAUNCH_PDL(k_brestart, vgrid, kThreads, 0, st, F, S, ld, B->flag, h->col_ptr, B->col, B->rt,
-              B->r, B->z1, B->V);
+  } else {
+    for (;;) {
+      if (B->g_host->any_active) RR_TRY(brun(R, nullptr, h->opt.check_every));
+      RR_TRY(btrue_residual(R, st));
+      RR_CUDA(cudaMemcpyAsync(B->col_host, B->col, sizeof(BatchCol) * ld, cudaMemcpyDeviceToHost, st));
+      RR_CUDA(cudaMemcpyAsync(B->g_host, B->g, sizeof(BatchGlobal), cudaMemcpyDeviceToHost, st));
+      RR_CUDA(cudaStreamSynchronize(st));
+      bool any = false;
+      for (int64_t s = 0; s < n_slabs; ++s) B->slab_host[s] = 0;
+      for (int32_t c = 0; c < S; ++c) {
+        BatchCol &C = B->col_host[c];
+        B->flag_host[c] = 0;
+        if (state[c] != 0) continue;
+        if (C.nonfinite || !isfinite(C.true_rr)) {
+          state[c] = 2;
+          continue;
+        }
+        if (sqrt(C.true_rr) <= C.target) {
+          state[c] = 1;
+          continue;
+        }
+        if (B->g_host->iter >= h->opt.max_iter || restarts[c] >= h->opt.max_restarts) {
+          state[c] = 2;
+          continue;
+        }
+        // refinement: continue from w on the true residual with a fresh direction
+        ++restarts[c];
+        C.conv = 0;
+        C.first = 1;
+        C.rr = C.true_rr;
+        B->flag_host[c] = 1;
+        B->slab_host[c / kSlab] = 1;
+        any = true;
+      }
+      if (!any) break;
+      RR_CUDA(cudaMemcpyAsync(B->col, B->col_host, sizeof(BatchCol) * ld, cudaMemcpyHostToDevice, st));
+      RR_CUDA(cudaMemcpyAsync(B->flag, B->flag_host, sizeof(int32_t) * S, cudaMemcpyHostToDevice, st));
+      RR_CUDA(cudaMemcpyAsync(B->slab_active, B->slab_host, sizeof(int32_t) * n_slabs,
+                              cudaMemcpyHostToDevice, st));
+      B->g_host->any_active = 1;
+      RR_CUDA(cudaMemcpyAsync(B->g, B->g_host, sizeof(BatchGlobal), cudaMemcpyHostToDevice, st));
+      RR_LAUNCH_PDL(k_brestart, vgrid, kThreads, 0, st, F, S, ld, B->flag, h->col_ptr, B->col,
+                    B->rt, B->r, B->z1, B->V);
+    }
   }
   const dim3 ogrid((unsigned)((F + 31) / 32), (unsigned)((S + 31) / 32));
   RR_LAUNCH(k_btranspose_out, ogrid, dim3(32, 8), 0, st, F, S, ld, B->w, W);
@@ -1232,7 +1525,7 @@ extern "C" rr_status rr_harvest(rr_handle *h, int32_t nrhs, const double *Y, dou
   const dim3 tgrid((unsigned)((N + 31) / 32), (unsigned)(ldy / 32));
   RR_LAUNCH(k_btranspose_in, tgrid, dim3(32, 8), 0, st, N, nrhs, ldy, Y, B->U64);
   RR_TRY(launch_bspmm<double>(B->n_units2, B->ubeg2, B->uend2, h->row_idx, B->U64, ldy, B->Zp64,
-                              ldy, (int32_t)(ldy / kSlab), nullptr, st));
+                              ldy, ldy, nullptr, st));
   const dim3 vgrid(kBEpiBlocks, (unsigned)n_slabs);
   RR_LAUNCH_PDL(k_bstart, vgrid, kThreads, 0, st, F, S, nrhs, ld, B->uptr2, B->Zp64, ldy, h->col_ptr,
             B->col, B->b, B->w, B->r, B->z1, B->V, B->part);
@@ -1244,6 +1537,7 @@ extern "C" rr_status rr_harvest(rr_handle *h, int32_t nrhs, const double *Y, dou
   RR_CUDA(cudaMemcpyAsync(B->g_host, B->g, sizeof(BatchGlobal), cudaMemcpyDeviceToHost, st));
   RR_CUDA(cudaStreamSynchronize(st));
   if (B->g_host->any_active) {
+    RR_TRY(batch_autotune(R, st));
     LoopGraph graph;
     if (h->opt.use_graphs) RR_TRY(build_loop(R, graph));
     RR_TRY(brun(R, h->opt.use_graphs ? &graph : nullptr, h->opt.check_every));
@@ -1255,5 +1549,21 @@ extern "C" rr_status rr_harvest(rr_handle *h, int32_t nrhs, const double *Y, dou
   RR_CUDA(cudaMemcpyAsync(&total, pos + slots, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   RR_CUDA(cudaStreamSynchronize(st));
   *n_pairs = std::min(total, max_pairs);
+  return RR_OK;
+}
+
+extern "C" rr_status rr_query_batch(const rr_handle *h, int32_t *slab_width, int32_t *unroll,
+                                    double *apply_ms) {
+  if (!h) {
+    rr_set_error("rr_query_batch: NULL handle");
+    return RR_INVALID_ARG;
+  }
+  if (!h->batch) {
+    rr_set_error("rr_query_batch: no batched solve has run on this handle");
+    return RR_INVALID_ARG;
+  }
+  if (slab_width) *slab_width = 32 * h->batch->spmm.C;
+  if (unroll) *unroll = h->batch->spmm.unroll;
+  if (apply_ms) *apply_ms = h->batch->spmm_ms;
   return RR_OK;
 }

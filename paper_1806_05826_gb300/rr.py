@@ -103,6 +103,7 @@ _SIGS = {
     "rr_query": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
     "rr_free": (None, [_P]),
     "rr_last_error": (ctypes.c_char_p, []),
+    "rr_query_batch": (ctypes.c_int, [_P, _P, _P, _P]),
     "rr_launch_count": (ctypes.c_int64, []),
     "rr_apply_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P,
                                         ctypes.c_double, _P, _P, _P]),
@@ -526,6 +527,13 @@ def rr_query(h: Handle) -> dict:
                            ctypes.byref(om), ctypes.byref(lam)))
     return {"n_rows": n.value, "n_cols": f.value, "k_eff": k.value, "omega": om.value,
             "lambda": lam.value}
+
+
+def rr_query_batch(h: Handle) -> dict:
+    """The batched engine's autotuned SpMM variant and its apply time."""
+    w, u, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(load().rr_query_batch(h.ptr, ctypes.byref(w), ctypes.byref(u), ctypes.byref(ms)))
+    return {"slab_width": w.value, "unroll": u.value, "apply_ms": ms.value}
 
 
 def rr_get_coarse(h: Handle):
