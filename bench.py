@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--profile-apply", type=int, default=0, metavar="K",
                     help="one setup and three warm-up applies, then K operator applies between "
                          "cudaProfilerStart/Stop (ncu --profile-from-start off); nothing timed")
+    ap.add_argument("--split-head", type=int, default=0,
+                    help="head columns of the FP32 operator's split form (0: automatic, -1: none)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="mixed: FP32 operator inside CG + FP64 refinement; fp64: FP64 throughout")
     return ap.parse_args()
@@ -460,7 +462,7 @@ def measure_dense_only(rr, dev, stream, opts):
     p = next(q for q in synth.many_params("uneven_12_dense4") if q.get("dense"))
     n, f = p["n"], p["d"]
     X = synth.dense_ar1(n, f, p["rho"], p["seed"])
-    o = {key: v for key, v in opts.items() if key not in ("gram", "gather", "seed")}
+    o = {key: v for key, v in opts.items() if key not in ("gram", "gather", "seed", "split_head")}
     h = rr.rr_setup_dense(torch.as_tensor(X, device=dev), p["lam"], p["k"], seed=p["seed"], **o)
     out = measure_dense_apply(rr, h, n, f, dev, stream)
     rr.rr_free(h)
@@ -478,7 +480,7 @@ def measure_many(rr, dev, stream, opts):
     hs, ys, ws, setup_ms = [], [], [], []
     for X, y, p in probs:
         if p.get("dense"):
-            o = {key: v for key, v in opts.items() if key not in ("gram", "gather")}
+            o = {key: v for key, v in opts.items() if key not in ("gram", "gather", "split_head")}
             h = rr.rr_setup_dense(torch.as_tensor(X, device=dev), p["lam"], p["k"],
                                   **dict(o, seed=p["seed"]))
             hs.append(h)
@@ -625,6 +627,7 @@ def run_ours(args, rank, world, local):
 
     prec = rr.RR_PREC_MIXED if args.precision == "mixed" else rr.RR_PREC_FP64
     opts = dict(seed=p["seed"], stream=stream, precision=prec, max_restarts=20,
+                split_head=args.split_head,
                 use_graphs=0 if args.no_graphs else 1,
                 gather={"auto": rr.RR_GATHER_AUTO, "lanes": rr.RR_GATHER_LANES,
                         "staged": rr.RR_GATHER_STAGED,

@@ -295,6 +295,116 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather(
   }
 }
 
+// The streaming gather (FP32 piece sums). One CTA per task: the vector slice
+// in shared memory, then each of the 32 warps streams its own contiguous
+// range of the task's words (ranges start at piece boundaries), 32 words per
+// step and kStreamUnroll steps loaded ahead: lane i loads word i of the step
+// (a coalesced 512-byte load per warp) and its metadata, sums the word's 8
+// gathered values, and a segmented inclusive scan over the 32 lanes (segments
+// = pieces; a piece may continue from the previous step, whose running sum is
+// carried) gives each piece's sum at its last word, which stores it in the
+// piece's slot. No indirection before the loads: every load is coalesced and
+// many are in flight per warp. The sums have a fixed order (each word's 8
+// values as in gather8, then the scan tree, then the carry), so every run
+// gives identical bits.
+constexpr int kStreamUnroll = 4;
+__global__ void __launch_bounds__(kSliceThreads, 1) k_stream_gather(
+    SlicedView P, const int32_t *__restrict__ wmeta, const int32_t *__restrict__ wstart,
+    const float *__restrict__ xq, float *__restrict__ out, const int32_t *__restrict__ stop) {
+  pdl_wait();
+  if (stop && *stop) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *xs = reinterpret_cast<float *>(smem_raw);
+  const int task = blockIdx.x;
+  const int32_t b = P.task_slice[task];
+  const int64_t base = (int64_t)b * P.W;
+  const int64_t width = min((int64_t)P.W, P.n_inner - base);
+  for (int i0 = threadIdx.x; i0 <= P.W; i0 += 4 * kSliceThreads) {
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * kSliceThreads;
+      v[u] = i < width ? xq[base + i] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * kSliceThreads;
+      if (i <= P.W) xs[i] = v[u];
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int32_t w0 = wstart[task * 33 + warp], w1 = wstart[task * 33 + warp + 1];
+  const uint4 pad = make_uint4(P.W | (P.W << 16), P.W | (P.W << 16), P.W | (P.W << 16),
+                               P.W | (P.W << 16));
+  float carry = 0.f;   // running sum of the piece open at the end of the previous step
+  bool open = false;
+  for (int32_t c = w0; c < w1; c += 32 * kStreamUnroll) {   // warp-uniform
+    uint4 q[kStreamUnroll];
+    int32_t m[kStreamUnroll];
+#pragma unroll
+    for (int u = 0; u < kStreamUnroll; ++u) {
+      const int32_t w = c + 32 * u + lane;
+      q[u] = w < w1 ? __ldg(P.idx + w) : pad;
+      m[u] = w < w1 ? __ldg(wmeta + w) : -2;   // -2: past the range
+    }
+#pragma unroll
+    for (int u = 0; u < kStreamUnroll; ++u) {
+      if (c + 32 * u >= w1) break;   // warp-uniform
+      float x = gather8(xs, q[u]);
+      const int32_t mp = __shfl_up_sync(0xffffffffu, m[u], 1);
+      int f = lane == 0 ? (open ? 0 : 1) : (mp >= 0 ? 1 : 0);   // a piece starts here
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const float xy = __shfl_up_sync(0xffffffffu, x, d);
+        const int fy = __shfl_up_sync(0xffffffffu, f, d);
+        if (lane >= d) {
+          if (!f) x = xy + x;
+          f |= fy;
+        }
+      }
+      if (!f) x = carry + x;   // still in the piece carried from the previous step
+      if (m[u] >= 0) out[m[u]] = x;
+      const float xl = __shfl_sync(0xffffffffu, x, 31);
+      const int32_t ml = __shfl_sync(0xffffffffu, m[u], 31);
+      open = ml == -1;
+      carry = open ? xl : 0.f;
+    }
+  }
+}
+
+// wmeta: the slot of each piece at its last word (-1 elsewhere, set before)
+__global__ void k_word_meta(int64_t npieces, const int32_t *__restrict__ pw,
+                            const int32_t *__restrict__ slot, int32_t *__restrict__ wmeta) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npieces;
+       p += (int64_t)gridDim.x * blockDim.x)
+    wmeta[pw[p + 1] - 1] = slot[p];
+}
+
+// wstart[t * 33 + w]: the first word of warp w's range in task t, the first
+// piece start at or after an even split of the task's words (33rd: the end)
+__global__ void k_warp_ranges(int32_t ntasks, const int32_t *__restrict__ task_p,
+                              const int32_t *__restrict__ pw, int32_t *__restrict__ wstart) {
+  const int64_t total = (int64_t)ntasks * 33;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t t = (int32_t)(e / 33), w = (int32_t)(e % 33);
+    const int32_t p0 = task_p[t], p1 = task_p[t + 1];
+    const int32_t wb = pw[p0], we = pw[p1];
+    if (w == 32) {
+      wstart[e] = we;
+      continue;
+    }
+    const int64_t target = wb + (int64_t)(we - wb) * w / 32;
+    int32_t lo = p0, hi = p1;
+    while (lo < hi) {
+      const int32_t mid = (lo + hi) >> 1;
+      if (pw[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    wstart[e] = lo < p1 ? pw[lo] : we;
+  }
+}
+
 // The staged gather (see the file comment). The CTA's 32 warps form kTeams
 // independent teams of 8 warps; team j consumes chunks j, j + kTeams, ... of
 // the task through its own ring of kStagesW stages and syncs only its own 256
@@ -671,6 +781,23 @@ template <typename T, typename PS>
 rr_status launch_gather(const SlicedPattern &P, const T *xq, const int32_t *stop, cudaStream_t st,
                         bool pdl) {
   PS *out = reinterpret_cast<PS *>(P.psum);
+  if constexpr (std::is_same<T, float>::value && std::is_same<PS, float>::value) {
+    if (P.wmeta) {
+      static bool attr = false;
+      if (!attr) {
+        RR_CUDA(cudaFuncSetAttribute(k_stream_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)slice_smem<float>(kSliceMax)));
+        attr = true;
+      }
+      if (pdl)
+        RR_LAUNCH_PDL(k_stream_gather, P.ntasks, kSliceThreads, slice_smem<float>(P.W), st,
+                      P.view(), P.wmeta, P.wstart, xq, out, stop);
+      else
+        RR_LAUNCH(k_stream_gather, P.ntasks, kSliceThreads, slice_smem<float>(P.W), st, P.view(),
+                  P.wmeta, P.wstart, xq, out, stop);
+      return RR_OK;
+    }
+  }
   if (std::is_same<T, float>::value && P.staged && P.chunk_p) {
     RR_TRY(set_staged_attr<PS>());
     const float *x = reinterpret_cast<const float *>(xq);
@@ -834,6 +961,8 @@ void sliced_free(SlicedPattern &P) {
   cudaFree(P.heavy);
   cudaFree(P.task_c);
   cudaFree(P.xq);
+  cudaFree(P.wmeta);
+  cudaFree(P.wstart);
   P = SlicedPattern{};
 }
 
@@ -841,6 +970,23 @@ rr_status sliced_gather(const SlicedPattern &P, const double *x, const SlicedPat
                         const int32_t *stop, cudaStream_t st, bool fp32, bool x32_ready) {
   return fp32 ? gather_t<float>(P, x, in, stop, st, x32_ready)
               : gather_t<double>(P, x, in, stop, st, false);
+}
+
+rr_status sliced_build_stream(SlicedPattern &P, cudaStream_t st) {
+  if (!P.psum32) {
+    rr_set_error("sliced_build_stream: the streaming gather stores FP32 piece sums");
+    return RR_UNSUPPORTED;
+  }
+  RR_CUDA(cudaMalloc(&P.wmeta, sizeof(int32_t) * std::max<int64_t>(1, P.nwords)));
+  RR_CUDA(cudaMalloc(&P.wstart, sizeof(int32_t) * (size_t)P.ntasks * 33));
+  RR_CUDA(cudaMemsetAsync(P.wmeta, 0xFF, sizeof(int32_t) * std::max<int64_t>(1, P.nwords), st));
+  if (P.npieces > 0)
+    RR_LAUNCH(k_word_meta, grid_for(P.npieces, kThreads), kThreads, 0, st, P.npieces, P.pw, P.slot,
+              P.wmeta);
+  RR_LAUNCH(k_warp_ranges, grid_for((int64_t)P.ntasks * 33, kThreads), kThreads, 0, st, P.ntasks,
+            P.task_p, P.pw, P.wstart);
+  RR_CUDA(cudaStreamSynchronize(st));
+  return RR_OK;
 }
 
 rr_status sliced_choose_gather(SlicedPattern &P, int32_t mode, cudaStream_t st) {

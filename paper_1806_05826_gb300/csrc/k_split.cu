@@ -440,10 +440,15 @@ rr_status split_build(int64_t N, int64_t F, const int64_t *row_ptr, const int32_
     RR_TRY(sliced_build(N, F, t_ptr, t_idx, S.xt, err, st));
     RR_TRY(sliced_build(F, N, tt_ptr, tt_idx, S.xtt, err, st));
     S.xt.psum32 = S.xtt.psum32 = true;
-    RR_TRY(sliced_choose_gather(S.xt, gather_mode == RR_GATHER_LANES_STAGED ? RR_GATHER_LANES
-                                                                            : gather_mode, st));
-    RR_TRY(sliced_choose_gather(S.xtt, gather_mode == RR_GATHER_LANES_STAGED ? RR_GATHER_STAGED
-                                                                             : gather_mode, st));
+    if (gather_mode == RR_GATHER_AUTO) {   // the streaming gather on both passes
+      RR_TRY(sliced_build_stream(S.xt, st));
+      RR_TRY(sliced_build_stream(S.xtt, st));
+    } else {   // a gather kernel named by the caller (comparisons, profiling)
+      RR_TRY(sliced_choose_gather(S.xt, gather_mode == RR_GATHER_LANES_STAGED ? RR_GATHER_LANES
+                                                                              : gather_mode, st));
+      RR_TRY(sliced_choose_gather(S.xtt, gather_mode == RR_GATHER_LANES_STAGED ? RR_GATHER_STAGED
+                                                                               : gather_mode, st));
+    }
     // row blocks: about two per SM, a multiple of 32 rows each, their staged
     // inputs within the shared-memory budget
     std::vector<int32_t> sp(N + 1);

@@ -212,6 +212,9 @@ struct SlicedPattern {
   int32_t *task_c = nullptr;     // [ntasks+1]  chunks of each task
   int32_t *err = nullptr;        // device error word (DEV_TIMEOUT from a bounded wait)
   void *xq = nullptr;            // [n_inner]   the gathered vector in the accumulation type
+  // streaming gather (FP32 piece sums only; see sliced_build_stream)
+  int32_t *wmeta = nullptr;      // [nwords] slot of the piece that ends at this word, else -1
+  int32_t *wstart = nullptr;     // [ntasks * 33] first word of each warp's range of a task
   SlicedView view() const {
     return SlicedView{W, n_inner, pw, slot, idx, task_slice, task_p, order};
   }
@@ -229,6 +232,9 @@ rr_status sliced_gather(const SlicedPattern &P, const double *x, const SlicedPat
                         bool x32_ready = false);
 // out[o] = sum of the slots of outer index o.
 rr_status sliced_slot_sum(const SlicedPattern &P, double *out, cudaStream_t st);
+// Metadata of the streaming gather for P (FP32 piece sums): then every FP32
+// gather of P streams the task's words warp by warp (see k_sliced.cu).
+rr_status sliced_build_stream(SlicedPattern &P, cudaStream_t st);
 // Chooses P.staged: mode RR_GATHER_LANES / RR_GATHER_STAGED, or (RR_GATHER_AUTO)
 // the faster of the two FP32 gathers on this pattern, each timed on the stream.
 rr_status sliced_choose_gather(SlicedPattern &P, int32_t mode, cudaStream_t st);
