@@ -131,7 +131,7 @@ typedef struct {
                                    term and the split_head most frequent other columns as a
                                    row-major bitmap (one read serves X v and X^T u), the rest as
                                    sliced index lists. 0 = automatic (default: the largest power
-                                   of two from 32 to 1024 whose columns each hold at least N/32
+                                   of two from 32 to 1024 whose columns each hold at least N/8
                                    rows, or none); a power of two from 32 to 1024 = that many;
                                    -1 = no split form (every column as sliced index lists) */
   void *stream;                 /* cudaStream_t for all work; NULL = legacy default stream */

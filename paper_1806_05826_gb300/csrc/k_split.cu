@@ -362,12 +362,15 @@ rr_status split_build(int64_t N, int64_t F, const int64_t *row_ptr, const int32_
     }
   } else {
     // the largest power-of-two multiple of 32 whose last column holds at
-    // least N / 32 rows: a bitmap column (N / 8 bytes, read once per apply)
-    // then costs no more than its two 16-bit index passes (4 bytes per entry)
+    // least N / 8 rows: a bitmap column costs two predicated adds per row in
+    // the row pass whether its bit is set or not, a tail entry one gather in
+    // each of the two streamed passes; on GB300 the two break even near a
+    // column density of 1/8 (measured at 200,000 x 100,000: 128 head columns
+    // 77.5 us per apply, 64: 79.2, 256: 81.6, 512: 93.9, none: 128.5)
     for (int32_t h = 1024; h >= 32; h >>= 1) {
       if ((size_t)h <= cand.size()) {
         const int32_t c = cand[h - 1];
-        if (32 * (cp[c + 1] - cp[c]) >= N) {
+        if (8 * (cp[c + 1] - cp[c]) >= N) {
           H = h;
           break;
         }
