@@ -13,7 +13,9 @@ Ridge Regression" (arXiv 1806.05826):
   cycle       Section 3.1: T = (I - w A)(I - P A_c^{-1} P^T A)(I - w A),
               with the Richardson smoother generalised to damped Jacobi.
   clustering  Section 3.4: k-means++ on the features, Euclidean distance.
-  coarse solve Section 4: Cholesky factorisation of the coarse operator.
+  coarse solve Section 4: Cholesky factorisation of the coarse operator; or the
+              eigendecomposition of X_c^T X_c, reused for every lambda
+              (eigen.py, cyclic Jacobi).
   Krylov      CG, Jacobi-preconditioned CG (DCG), PCG, and flexible CG
               (Algorithm 3) with truncation m_i = max(1, i mod (m+1)).
   residual    Section 4 figures: ||X^T b - (X^T X + beta I) x|| / ||X^T b||.
@@ -25,4 +27,4 @@ Parity unpinned: iteration counts and speed-ups against the paper's tables
 (its datasets are not available), and k-means labels beyond "same initial
 centres give the same labels" (Lloyd's optimum is not unique).
 """
-from . import sparse, kmeans, twolevel, krylov, mlp, learned  # noqa: F401
+from . import sparse, kmeans, twolevel, krylov, mlp, learned, eigen  # noqa: F401

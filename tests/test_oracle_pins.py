@@ -731,3 +731,56 @@ def test_reference_solutions_are_the_dense_solution():
         two = tl.from_labels(*spec[:2], X.row_ptr, X.col_idx, lam, raw)
         want = krylov.pcg(two.A, two.apply, b, tol=1e-8)
         assert want.restarts == 0 and np.array_equal(snaps[1e-8], want.w)
+
+
+# ---------------------------------------------------------------- eigen coarse solve (Section 4)
+
+def test_jacobi_eigh_against_library_eigh():
+    """The cyclic Jacobi eigendecomposition against numpy.linalg.eigh: the
+    same spectrum, Q orthogonal, Q diag(mu) Q^T = S."""
+    from oracle import eigen
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((40, 25))
+    S = B.T @ B
+    mu, Q, sweeps = eigen.jacobi_eigh(S)
+    assert 3 <= sweeps <= 15
+    assert np.allclose(np.sort(mu), np.linalg.eigvalsh(S), rtol=1e-12, atol=1e-12 * mu.max())
+    assert np.allclose(Q.T @ Q, np.eye(25), atol=1e-13)
+    assert np.allclose((Q * mu) @ Q.T, S, atol=1e-12 * np.abs(S).max())
+
+
+def test_eigen_coarse_inverse_equals_cholesky_solve_at_every_lambda():
+    """Section 4: one decomposition of X_c^T X_c serves every lambda; the coarse
+    solve Q diag(1/(mu+lambda)) Q^T r equals the Cholesky solve of A_c(lambda)."""
+    from oracle import eigen
+    D = random_binary(60, 30, 0.2, 4)
+    n, f, rp, ci = csr_of(D)
+    two = tl.setup_binary(n, f, rp, ci, 0.1, 8, seed=2)
+    mu, Q, _ = eigen.jacobi_eigh(eigen.coarse_gram_scaled(two.G, two.s))
+    rc = np.random.default_rng(5).standard_normal(two.k_eff)
+    for lam in (1e-4, 0.1, 3.0, 1e3):
+        t = two.with_lambda(lam)
+        want = tl.chol_solve(t.L, rc)
+        got = eigen.coarse_solve(mu, Q, lam, rc)
+        # both solves are backward stable: they agree to about cond(A_c) eps
+        tol = max(1e-13, 1e-15 * np.linalg.cond(t.Ac))
+        assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want), lam
+        assert np.allclose(eigen.coarse_inverse(mu, Q, lam) @ t.Ac, np.eye(two.k_eff),
+                           atol=100 * tol)
+
+
+def test_eigen_theorem1_spectrum():
+    """Theorem 1: on duplicated features the eigenvalues of X_c^T X_c (computed
+    by the oracle's Jacobi) are the non-zero eigenvalues of X^T X."""
+    from oracle import eigen
+    rng = np.random.default_rng(1)
+    base = (rng.random((30, 5)) < 0.5).astype(np.int64)
+    base[0] = 1
+    X, groups = synth.duplicated_features(base, [2, 3, 1, 4, 2])
+    centers = [int(np.nonzero(groups == g)[0][0]) for g in range(5)]
+    n, f, rp, ci = csr_of(X)
+    two = tl.setup_binary(n, f, rp, ci, 1e-6, 5, centers=centers)
+    mu, _, _ = eigen.jacobi_eigh(eigen.coarse_gram_scaled(two.G, two.s))
+    ev = np.linalg.eigvalsh((X.T @ X).astype(float))
+    nz = np.sort(ev[ev > 1e-9 * ev.max()])
+    assert np.allclose(np.sort(mu[mu > 1e-9 * mu.max()]), nz, rtol=1e-11)

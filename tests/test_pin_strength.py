@@ -247,8 +247,63 @@ def _dense_coarse_operator_with_averaging(mp):
     mp.setattr(tl, "coarse_operator_dense", bad)
 
 
+def _eigen_inverse_without_lambda(mp):
+    from oracle import eigen
+    mp.setattr(eigen, "coarse_solve", lambda mu, Q, lam, rc: Q @ ((Q.T @ rc) / mu))
+    mp.setattr(eigen, "coarse_inverse", lambda mu, Q, lam: (Q / mu[None, :]) @ Q.T)
+
+
+def _jacobi_stops_on_cancelled_norm(mp):
+    """The off-diagonal norm taken as ||A||^2 - sum diag^2 (cancellation: a
+    premature stop), a mistake the oracle once made: the oracle's own loop,
+    with that one line changed."""
+    import inspect
+    import textwrap
+    from oracle import eigen
+    src = textwrap.dedent(inspect.getsource(eigen.jacobi_eigh))
+    good = "off = np.linalg.norm(A - np.diag(np.diag(A)))"
+    assert good in src
+    src = src.replace(good, "off = np.sqrt(max(0.0, np.sum(A * A) - np.sum(np.diag(A) ** 2)))")
+    ns = {"np": np}
+    exec(src, ns)
+    mp.setattr(eigen, "jacobi_eigh", ns["jacobi_eigh"])
+
+
+def _jacobi_rotation_sign(mp):
+    from oracle import eigen
+    orig_sqrt = np.sqrt
+
+    def bad(S, tol=1e-15, max_sweeps=50):
+        A = np.array(S, dtype=np.float64, copy=True)
+        n = A.shape[0]
+        Q = np.eye(n)
+        for _ in range(max_sweeps):
+            for p in range(n - 1):
+                for q in range(p + 1, n):
+                    if A[p, q] == 0.0:
+                        continue
+                    tau = (A[q, q] - A[p, p]) / (2.0 * A[p, q])
+                    t = -(1.0 if tau >= 0.0 else -1.0) / (abs(tau) + orig_sqrt(1.0 + tau * tau))
+                    c = 1.0 / orig_sqrt(1.0 + t * t)
+                    s = t * c
+                    J = np.eye(n)
+                    J[p, p] = J[q, q] = c
+                    J[p, q], J[q, p] = s, -s
+                    A = J.T @ A @ J
+                    Q = Q @ J
+        return np.diag(A).copy(), Q, max_sweeps
+    mp.setattr(eigen, "jacobi_eigh", lambda S, tol=1e-15, max_sweeps=50: bad(S, tol, 3))
+
+
 P = pins
 CASES = [
+    ("eigen coarse inverse without lambda", _eigen_inverse_without_lambda,
+     [P.test_eigen_coarse_inverse_equals_cholesky_solve_at_every_lambda]),
+    ("Jacobi stops on a cancelled off-diagonal norm", _jacobi_stops_on_cancelled_norm,
+     [P.test_jacobi_eigh_against_library_eigh,
+      P.test_eigen_coarse_inverse_equals_cholesky_solve_at_every_lambda]),
+    ("Jacobi rotation angle of the wrong sign", _jacobi_rotation_sign,
+     [P.test_jacobi_eigh_against_library_eigh, P.test_eigen_theorem1_spectrum]),
     ("dense seeding uniform instead of D^2", _dense_seeding_uniform,
      [P.test_kmeanspp_dense_draw_follows_d2_weights]),
     ("dense coarse operator from the averaging operator", _dense_coarse_operator_with_averaging,
