@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-parity", action="store_true",
                     help="skip the oracle's exact solutions of the workload (error of each solve)")
+    ap.add_argument("--no-eigen", action="store_true",
+                    help="skip the section comparing the eigendecomposition coarse solve")
+    ap.add_argument("--only-eigen", action="store_true",
+                    help="run the eigendecomposition section alone (profiling runs)")
     ap.add_argument("--no-small", action="store_true",
                     help="skip the small FP64 configuration (2,000 x 1,000, us per iteration)")
     ap.add_argument("--no-batch", action="store_true",
@@ -408,6 +412,47 @@ def measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world, n_targ
             "note": "plain = one setup + rr_solve of every system one after the other"}
 
 
+def measure_eigen(rr, row_ptr, col_idx, N, F, k, lams, opts, dev, stream, y_dev):
+    """The coarse solve by eigendecomposition (RR_COARSE_EIGEN) against the
+    Cholesky form on the same workload: the setup's coarse-factor phase (the
+    Jacobi eigendecomposition once, against one Cholesky factorisation), the
+    cost of one lambda change (rr_set_lambda, the 8 weights of the batched
+    workload, CUDA events) and a solve at each lambda of the step."""
+    import torch
+    from gen import synth
+    out = {}
+    weights = list(synth.BATCH_WORKLOADS["zipf_200000x100000_64x8"]["lambdas"])
+    w = torch.empty(F, dtype=torch.float64, device=dev)
+    for name, coarse in (("cholesky", rr.RR_COARSE_CHOLESKY), ("eigen", rr.RR_COARSE_EIGEN)):
+        h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], k, **dict(opts, coarse=coarse))
+        info = rr.rr_solve(h, y_dev, w, tol=TOL)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize(dev)
+        ev[0].record(stream)
+        for lam in weights:
+            rr.rr_set_lambda(h, lam)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        iters = []
+        for lam in lams:
+            rr.rr_set_lambda(h, lam)
+            inf = rr.rr_solve(h, y_dev, w, tol=TOL)
+            assert inf["status"] == "RR_OK" and inf["true_rel_res"] <= TOL
+            iters.append(inf["iters"])
+        out[name] = {"coarse_factor_phase_ms": round(info["setup_phase_ms"][6], 2),
+                     "setup_ms": round(info["setup_ms"], 2),
+                     "set_lambda_ms": round(ev[0].elapsed_time(ev[1]) / len(weights), 3),
+                     "iters": iters}
+        if coarse == rr.RR_COARSE_EIGEN:
+            out[name]["jacobi_sweeps"] = rr.rr_get_eigen(h)[2]
+        rr.rr_free(h)
+    ch, eg = out["cholesky"], out["eigen"]
+    extra = eg["coarse_factor_phase_ms"] - ch["coarse_factor_phase_ms"]
+    saved = ch["set_lambda_ms"] - eg["set_lambda_ms"]
+    out["break_even_lambdas"] = round(extra / saved, 1) if saved > 0 else None
+    return out
+
+
 def measure_tlfcg(rr, row_ptr, col_idx, N, F, k, lams, opts, y_dev, last_infos):
     """The same systems (each lambda, same target, same clustering) solved by the
     paper's TLFCG: flexible CG whose preconditioner is two CG rougher steps and the
@@ -651,6 +696,9 @@ def run_ours(args, rank, world, local):
         return {"workload": args.workload, "precision": args.precision,
                 "roofline": measure_roofline(rr, row_ptr, col_idx, N, F, nnz, k, lams, opts, dev,
                                              stream, args.workload)}
+    if args.only_eigen:
+        return {"coarse_eigen": measure_eigen(rr, row_ptr, col_idx, N, F, k, lams, opts, dev,
+                                              stream, y_dev)}
     if args.only == "batched":
         return {"batched": measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world,
                                            args.batch_targets)}
@@ -742,7 +790,9 @@ def run_ours(args, rank, world, local):
                "h2d_bytes_per_step": 8 * (N + 1) + 4 * nnz + 8 * N,
                "d2h_bytes_per_step": 8 * F * len(lams)}
 
-    batched = many = learned = tlfcg = None
+    batched = many = learned = tlfcg = eig = None
+    if not args.no_eigen and args.workload == WORKLOAD:
+        eig = measure_eigen(rr, row_ptr, col_idx, N, F, k, lams, opts, dev, stream, y_dev)
     if not args.no_tlfcg:
         tlfcg = measure_tlfcg(rr, row_ptr, col_idx, N, F, k, lams, opts, y_dev, last_infos=all_infos[-1])
     if not args.no_batch and args.workload == WORKLOAD:
@@ -786,7 +836,7 @@ def run_ours(args, rank, world, local):
                       "step_ms": [round(t, 3) for t in step_ms]},
         "e2e": e2e, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches,
         "batched": batched, "many": many, "learned": learned, "tlfcg": tlfcg,
-        "parity": parity, "small_fp64": small,
+        "parity": parity, "small_fp64": small, "coarse_eigen": eig,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle's own counts where recorded (its FP64 PCG needs fewer

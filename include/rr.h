@@ -70,6 +70,15 @@ enum { RR_GATHER_AUTO = 0,      /* rr_setup times both on each pass of X and kee
                                    timed choice on Zipf-like data; fixed, e.g. under a profiler,
                                    whose serialisation distorts the timing) */
 
+/* rr_options.coarse — how A_c(lambda)^-1 is formed (Section 4) */
+enum { RR_COARSE_CHOLESKY = 0,  /* per lambda: Cholesky factor of A_c, its triangular inverse,
+                                   A_c^-1 = L^-T L^-1 */
+       RR_COARSE_EIGEN = 1 };   /* once per clustering: X_c^T X_c = Q diag(mu) Q^T (parallel
+                                   cyclic Jacobi, FP64); per lambda only the product
+                                   A_c^-1 = Q diag(1 / (mu + lambda)) Q^T, so rr_set_lambda
+                                   and the weights of rr_solve_batch cost one k x k x k product
+                                   each instead of a factorisation */
+
 /* rr_options.precision */
 enum { RR_PREC_FP64 = 0,        /* every operator apply accumulates in FP64 */
        RR_PREC_MIXED = 1 };     /* the operator applies inside the CG iterations gather FP32
@@ -126,6 +135,7 @@ typedef struct {
                                    clusters) exceed this re-gathers the affected features per
                                    feature (pull), else it pushes the updates with integer atomics;
                                    0 = default (2e8). Labels are identical either way */
+  int32_t coarse;               /* RR_COARSE_* (default RR_COARSE_CHOLESKY) */
   int32_t split_head;           /* RR_PREC_MIXED, binary X: the operator applies of the FP32
                                    iterations take the columns that hold every row as a rank-one
                                    term and the split_head most frequent other columns as a
@@ -383,6 +393,14 @@ rr_status rr_query(const rr_handle *h, int64_t *n_rows, int64_t *n_cols, int32_t
 rr_status rr_apply_noalloc(int64_t n_rows, int64_t n_cols, const int64_t *row_ptr,
                            const int32_t *col_idx, const int64_t *col_ptr, const int32_t *row_idx,
                            double lambda, const double *v, double *out, void *stream);
+
+/* The coarse eigendecomposition of an RR_COARSE_EIGEN handle (Section 4: a
+ * decomposition of X_c reused for every lambda): mu_host[k_eff] the
+ * eigenvalues of X_c^T X_c (unordered), Q_host[k_eff x k_eff] row-major with
+ * column e the eigenvector of mu[e], *sweeps the Jacobi sweeps taken. Any
+ * output may be NULL. Errors: RR_INVALID_ARG (NULL handle or no eigen
+ * decomposition), RR_CUDA_ERROR. */
+rr_status rr_get_eigen(const rr_handle *h, double *mu_host, double *Q_host, int32_t *sweeps);
 
 /* The batched engine's sparse-times-dense variant chosen by its autotuner for
  * the last rr_solve_batch (or rr_harvest) on h: systems per slab (32, 64 or

@@ -64,6 +64,8 @@ struct rr_handle {
   double *s = nullptr;
   // coarse level
   double *G = nullptr, *Ac = nullptr, *Lw = nullptr, *Linv = nullptr, *Ainv = nullptr;
+  double *mu = nullptr, *Qv = nullptr;   // RR_COARSE_EIGEN: eigenvalues, eigenvector rows
+  int32_t eig_sweeps = 0;
   // smoother
   double *d = nullptr;
   int64_t *gsum = nullptr;   // sum_j |(X^T X)_ij| = sum of the row lengths over column i

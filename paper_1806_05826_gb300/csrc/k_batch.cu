@@ -1010,10 +1010,14 @@ rr_status batch_factors(rr_handle *h, BatchState *B, int32_t nlam, const double 
   const int32_t k = h->k_eff;
   const int32_t kpad = (int32_t)round_up64(k);
   for (int32_t l = 0; l < nlam; ++l) {
-    RR_TRY(coarse_operator(k, h->G, h->s, lambdas[l], B->Ac, st));
-    RR_CUDA(cudaMemcpyAsync(B->Lw, B->Ac, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, st));
-    RR_TRY(cholesky(k, B->Lw, h->err, st));
-    RR_TRY(chol_inverse(k, B->Lw, B->Linv, B->Ainv, st));
+    if (h->mu) {   // the handle's eigendecomposition, reused for every weight
+      RR_TRY(eig_inverse(k, h->mu, h->Qv, lambdas[l], B->Ainv, st));
+    } else {
+      RR_TRY(coarse_operator(k, h->G, h->s, lambdas[l], B->Ac, st));
+      RR_CUDA(cudaMemcpyAsync(B->Lw, B->Ac, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, st));
+      RR_TRY(cholesky(k, B->Lw, h->err, st));
+      RR_TRY(chol_inverse(k, B->Lw, B->Linv, B->Ainv, st));
+    }
     RR_LAUNCH(k_binv_pad, grid_for((int64_t)kpad * kpad, kThreads), kThreads, 0, st, k, kpad,
               B->Ainv, B->AinvB + (size_t)l * kpad * kpad);
   }

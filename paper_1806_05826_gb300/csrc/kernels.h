@@ -241,6 +241,15 @@ rr_status sliced_choose_gather(SlicedPattern &P, int32_t mode, cudaStream_t st);
 // t_i = slot sums of feature i, then the epilogue; kVecGrid partial dots.
 rr_status sliced_epilogue(const SlicedPattern &P, const CscEpilogue &ep, cudaStream_t st);
 
+// ---- k_eigen.cu ---------------------------------------------------------
+// G_s = D_s G D_s = Q diag(mu) Q^T by parallel cyclic Jacobi (FP64): mu[k],
+// Vk (k x k, row e = eigenvector e); *sweeps_out the sweeps taken.
+rr_status coarse_eigen(int32_t k, const double *G, const double *s, double *mu, double *Vk,
+                       int32_t *sweeps_out, cudaStream_t st);
+// Ainv = Q diag(1 / (mu + lambda)) Q^T (exactly symmetric).
+rr_status eig_inverse(int32_t k, const double *mu, const double *Vk, double lambda, double *Ainv,
+                      cudaStream_t st);
+
 // ---- k_split.cu ---------------------------------------------------------
 // Split form of the FP32 operator (see k_split.cu): the all-ones columns as a
 // rank-one term, the H most frequent other columns as a row-major bitmap, the

@@ -97,13 +97,27 @@ rr_status check_dev_error(rr_handle *h, const char *where) {
 }
 
 // Coarse operator, its factor and inverse, Jacobi diagonal and damping at lambda.
+// The eigendecomposition of the lambda-free coarse operator (RR_COARSE_EIGEN),
+// once per clustering.
+rr_status coarse_eigen_setup(rr_handle *h) {
+  if (h->opt.coarse != RR_COARSE_EIGEN) return RR_OK;
+  const int32_t k = h->k_eff;
+  RR_TRY(h->mem.alloc(&h->mu, k));
+  RR_TRY(h->mem.alloc(&h->Qv, (int64_t)k * k));
+  return rr::coarse_eigen(k, h->G, h->s, h->mu, h->Qv, &h->eig_sweeps, h->st);
+}
+
 rr_status build_lambda(rr_handle *h, double lambda) {
   cudaStream_t st = h->st;
   const int32_t k = h->k_eff;
   RR_TRY(rr::coarse_operator(k, h->G, h->s, lambda, h->Ac, st));
-  RR_CUDA(cudaMemcpyAsync(h->Lw, h->Ac, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, st));
-  RR_TRY(rr::cholesky(k, h->Lw, h->err, st));
-  RR_TRY(rr::chol_inverse(k, h->Lw, h->Linv, h->Ainv, st));
+  if (h->mu) {   // A_c^-1 = Q diag(1 / (mu + lambda)) Q^T
+    RR_TRY(rr::eig_inverse(k, h->mu, h->Qv, lambda, h->Ainv, st));
+  } else {
+    RR_CUDA(cudaMemcpyAsync(h->Lw, h->Ac, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, st));
+    RR_TRY(rr::cholesky(k, h->Lw, h->err, st));
+    RR_TRY(rr::chol_inverse(k, h->Lw, h->Linv, h->Ainv, st));
+  }
   RR_CUDA(cudaMemsetAsync(h->max_bits, 0, sizeof(unsigned long long), st));
   if (h->dense) {
     RR_TRY(rr::dense_jacobi(h->F, lambda, h->dsq, h->dgs, h->d, h->max_bits, st));
@@ -270,6 +284,7 @@ rr_status setup_impl_dense(rr_handle *h, const rr_matrix *X, double lambda, int3
   RR_TRY(m.alloc(&h->d, F));
   RR_TRY(m.alloc(&h->omega_dev, 1));
   RR_TRY(m.alloc(&h->max_bits, 1));
+  RR_TRY(coarse_eigen_setup(h));
   RR_TRY(build_lambda(h, lambda));
   RR_TRY(phase(6));
   RR_TRY(m.alloc(&h->dpart, rr::dense_part_rows(N, F) * F));
@@ -497,6 +512,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&h->d, F));
   RR_TRY(m.alloc(&h->omega_dev, 1));
   RR_TRY(m.alloc(&h->max_bits, 1));
+  RR_TRY(coarse_eigen_setup(h));
   RR_TRY(build_lambda(h, lambda));
 
   RR_TRY(phase(6));
@@ -1238,6 +1254,10 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
     rr_set_error("rr_setup: unknown gather %d", opt.gather);
     return RR_INVALID_ARG;
   }
+  if (opt.coarse != RR_COARSE_CHOLESKY && opt.coarse != RR_COARSE_EIGEN) {
+    rr_set_error("rr_setup: unknown coarse %d", opt.coarse);
+    return RR_INVALID_ARG;
+  }
   if (opt.solver < RR_SOLVER_TWOLEVEL || opt.solver > RR_SOLVER_TLFCG) {
     rr_set_error("rr_setup: unknown solver %d", opt.solver);
     return RR_INVALID_ARG;
@@ -1482,6 +1502,26 @@ rr_status rr_get_coarse(const rr_handle *h, double *Ac_host, int64_t *G_host) {
   RR_CUDA(cudaStreamSynchronize(h->st));
   if (G_host)
     for (size_t i = 0; i < kk; ++i) G_host[i] = (int64_t)g[i];
+  return RR_OK;
+}
+
+rr_status rr_get_eigen(const rr_handle *h, double *mu_host, double *Q_host, int32_t *sweeps) {
+  if (!h || !h->mu) {
+    rr_set_error("rr_get_eigen: NULL handle or a handle without the eigen coarse solve");
+    return RR_INVALID_ARG;
+  }
+  const int32_t k = h->k_eff;
+  if (mu_host)
+    RR_CUDA(cudaMemcpyAsync(mu_host, h->mu, sizeof(double) * k, cudaMemcpyDeviceToHost, h->st));
+  if (Q_host) {   // Q[i][e] = component i of eigenvector e (the rows of Qv transposed)
+    std::vector<double> v((size_t)k * k);
+    RR_CUDA(cudaMemcpyAsync(v.data(), h->Qv, sizeof(double) * v.size(), cudaMemcpyDeviceToHost, h->st));
+    RR_CUDA(cudaStreamSynchronize(h->st));
+    for (int64_t e = 0; e < k; ++e)
+      for (int64_t i = 0; i < k; ++i) Q_host[i * k + e] = v[e * k + i];
+  }
+  RR_CUDA(cudaStreamSynchronize(h->st));
+  if (sweeps) *sweeps = h->eig_sweeps;
   return RR_OK;
 }
 

@@ -22,6 +22,7 @@ RR_SOLVER_TWOLEVEL, RR_SOLVER_CG, RR_SOLVER_DCG, RR_SOLVER_TLFCG = 0, 1, 2, 3
 RR_PREC_FP64, RR_PREC_MIXED = 0, 1
 RR_GRAM_AUTO, RR_GRAM_CUDA_CORES = 0, 1
 RR_GATHER_AUTO, RR_GATHER_LANES, RR_GATHER_STAGED, RR_GATHER_LANES_STAGED = 0, 1, 2, 3
+RR_COARSE_CHOLESKY, RR_COARSE_EIGEN = 0, 1
 
 _STATUS = {0: "RR_OK", 1: "RR_INVALID_ARG", 2: "RR_CUDA_ERROR", 3: "RR_OOM", 4: "RR_NOT_SPD",
            5: "RR_NOT_CONVERGED", 6: "RR_NONFINITE", 7: "RR_TIMEOUT", 8: "RR_UNSUPPORTED"}
@@ -41,7 +42,8 @@ class rr_options(ctypes.Structure):
                 ("check_every", ctypes.c_int32), ("max_restarts", ctypes.c_int32),
                 ("use_graphs", ctypes.c_int32), ("gram", ctypes.c_int32),
                 ("gather", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
-                ("lloyd_pull_work", ctypes.c_int64), ("split_head", ctypes.c_int32),
+                ("lloyd_pull_work", ctypes.c_int64), ("coarse", ctypes.c_int32),
+                ("split_head", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -104,6 +106,7 @@ _SIGS = {
     "rr_free": (None, [_P]),
     "rr_last_error": (ctypes.c_char_p, []),
     "rr_query_batch": (ctypes.c_int, [_P, _P, _P, _P]),
+    "rr_get_eigen": (ctypes.c_int, [_P, _P, _P, _P]),
     "rr_launch_count": (ctypes.c_int64, []),
     "rr_apply_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P,
                                         ctypes.c_double, _P, _P, _P]),
@@ -210,7 +213,7 @@ def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=N
              kmeans_max_iter=50, max_iter=20000, solver=RR_SOLVER_TWOLEVEL, check_every=8,
              max_restarts=5, use_graphs=1, gram=RR_GRAM_AUTO, gather=RR_GATHER_AUTO,
              precision=RR_PREC_FP64, wait_limit=0, lloyd_pull_work=0, split_head=0,
-             stream=None) -> Handle:
+             coarse=0, stream=None) -> Handle:
     """rr_setup on a binary CSR pattern given as numpy arrays (host) or torch
     CUDA tensors (device): row_ptr int64[N+1], col_idx int32[nnz]."""
     on_device = 0 if isinstance(row_ptr, np.ndarray) else 1
@@ -237,7 +240,7 @@ def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=N
                            init_centers=_ptr(ic), solver=solver, check_every=check_every,
                            max_restarts=max_restarts, use_graphs=use_graphs, gram=gram,
                            gather=gather, wait_limit=wait_limit, lloyd_pull_work=lloyd_pull_work,
-                           split_head=split_head,
+                           split_head=split_head, coarse=coarse,
                            precision=precision, stream=_stream_ptr(stream))
     out = _P()
     _check(lib.rr_setup(ctypes.byref(X), float(lam), int(k), ctypes.byref(o), ctypes.byref(out)))
@@ -246,7 +249,7 @@ def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=N
 
 def rr_setup_dense(X, lam, k, *, seed=0, init_centers=None, kmeans_max_iter=50, max_iter=20000,
                    solver=RR_SOLVER_TWOLEVEL, check_every=8, max_restarts=5, use_graphs=1,
-                   precision=RR_PREC_FP64, stream=None) -> Handle:
+                   precision=RR_PREC_FP64, coarse=RR_COARSE_CHOLESKY, stream=None) -> Handle:
     """rr_setup on a dense X (N x F, float32 row-major) given as a numpy array
     (host) or a torch CUDA tensor (device)."""
     on_device = 0 if isinstance(X, np.ndarray) else 1
@@ -265,7 +268,7 @@ def rr_setup_dense(X, lam, k, *, seed=0, init_centers=None, kmeans_max_iter=50, 
     o = rr_default_options(kmeans_max_iter=kmeans_max_iter, max_iter=max_iter, seed=seed,
                            init_centers=_ptr(ic), solver=solver, check_every=check_every,
                            max_restarts=max_restarts, use_graphs=use_graphs,
-                           precision=precision, stream=_stream_ptr(stream))
+                           precision=precision, stream=_stream_ptr(stream), coarse=coarse)
     out = _P()
     _check(lib.rr_setup(ctypes.byref(M), float(lam), int(k), ctypes.byref(o), ctypes.byref(out)))
     h = Handle(out, n_cols, n_rows, (ic,), int(k))
@@ -534,6 +537,16 @@ def rr_query_batch(h: Handle) -> dict:
     w, u, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
     _check(load().rr_query_batch(h.ptr, ctypes.byref(w), ctypes.byref(u), ctypes.byref(ms)))
     return {"slab_width": w.value, "unroll": u.value, "apply_ms": ms.value}
+
+
+def rr_get_eigen(h: Handle):
+    """(mu, Q, sweeps) of an RR_COARSE_EIGEN handle: X_c^T X_c = Q diag(mu) Q^T."""
+    k = rr_query(h)["k_eff"]
+    mu = np.empty(k, dtype=np.float64)
+    Q = np.empty((k, k), dtype=np.float64)
+    sw = ctypes.c_int32()
+    _check(load().rr_get_eigen(h.ptr, mu.ctypes.data, Q.ctypes.data, ctypes.byref(sw)))
+    return mu, Q, sw.value
 
 
 def rr_get_coarse(h: Handle):
