@@ -56,4 +56,40 @@ __device__ __forceinline__ void epilogue(const CscEpilogue &ep, int64_t i, doubl
   epilogue(ep, i, sum, dot, nullptr);
 }
 
+// The same epilogue on values loaded by the caller: vi = v[i], ri = r[i] and
+// wdi = omega / d_i (POST), with the same operations in the same order.
+__device__ __forceinline__ void epilogue_values(const CscEpilogue &ep, int64_t i, double sum,
+                                                double vi, double ri, double wdi, double &dot) {
+  switch (ep.mode) {
+    case CSC_RHS:
+      ep.out[i] = sum;
+      break;
+    case CSC_APPLY:
+      ep.out[i] = sum + ep.lambda * vi;
+      break;
+    case CSC_PRE:
+      ep.out[i] = ri - (sum + ep.lambda * vi);
+      break;
+    case CSC_POST: {
+      const double r2 = ri - (sum + ep.lambda * vi);
+      const double z = vi + r2 * wdi;
+      ep.out[i] = z;
+      dot += ri * z;
+      break;
+    }
+    case CSC_PCG: {
+      const double t = sum + ep.lambda * vi;
+      ep.out[i] = t;
+      dot += vi * t;
+      break;
+    }
+    default: {  // CSC_RESID
+      const double t = ri - (sum + ep.lambda * vi);
+      ep.out[i] = t;
+      dot += t * t;
+      break;
+    }
+  }
+}
+
 }  // namespace rr

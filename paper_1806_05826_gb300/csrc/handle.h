@@ -65,6 +65,7 @@ struct rr_handle {
   // coarse level
   double *G = nullptr, *Ac = nullptr, *Lw = nullptr, *Linv = nullptr, *Ainv = nullptr;
   double *mu = nullptr, *Qv = nullptr;   // RR_COARSE_EIGEN: eigenvalues, eigenvector rows
+  double *Qt = nullptr, *dvec = nullptr, *ec_tmp = nullptr;   // Q row-major, 1/(mu+lambda)
   int32_t eig_sweeps = 0;
   // smoother
   double *d = nullptr;

@@ -307,6 +307,30 @@ rr_status coarse_eigen(int32_t k, const double *G, const double *s, double *mu, 
   return s_;
 }
 
+namespace {
+__global__ void k_eig_transpose(int32_t k, const double *__restrict__ Vk, double *__restrict__ Qt) {
+  const int64_t kk = (int64_t)k * k;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < kk;
+       e += (int64_t)gridDim.x * blockDim.x)
+    Qt[e] = Vk[(e % k) * k + e / k];
+}
+__global__ void k_eig_dvec(int32_t k, const double *__restrict__ mu, double lambda,
+                           double *__restrict__ d) {
+  for (int32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < k; e += gridDim.x * blockDim.x)
+    d[e] = 1.0 / (mu[e] + lambda);
+}
+}  // namespace
+
+rr_status eig_transpose(int32_t k, const double *Vk, double *Qt, cudaStream_t st) {
+  RR_LAUNCH(k_eig_transpose, grid_for((int64_t)k * k, kThreads), kThreads, 0, st, k, Vk, Qt);
+  return RR_OK;
+}
+
+rr_status eig_dvec(int32_t k, const double *mu, double lambda, double *d, cudaStream_t st) {
+  RR_LAUNCH(k_eig_dvec, grid_for(k, kThreads), kThreads, 0, st, k, mu, lambda, d);
+  return RR_OK;
+}
+
 rr_status eig_inverse(int32_t k, const double *mu, const double *Vk, double lambda, double *Ainv,
                       cudaStream_t st) {
   const unsigned t = (unsigned)((k + kET - 1) / kET);

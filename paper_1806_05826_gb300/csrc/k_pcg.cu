@@ -35,18 +35,26 @@ __global__ void k_restrict_items(const RestrictItem *__restrict__ items, int32_t
 
 // Restriction, pass 2 fused with the coarse solve: r_c[S] = s_S * (sum of the
 // item sums of S, in order) is staged in shared memory, then e_c = Ainv r_c.
+// With item_ptr == nullptr the input vector is item_sum itself (a plain
+// mat-vec ec = Ainv x); with scale, ec[S] is multiplied by scale[S].
 __global__ void k_coarse_matvec(int32_t k, const double *__restrict__ Ainv,
                                 const int32_t *__restrict__ item_ptr,
                                 const double *__restrict__ item_sum, const double *__restrict__ s,
                                 double *__restrict__ rc_out, double *__restrict__ ec,
-                                const int32_t *__restrict__ stop) {
+                                const int32_t *__restrict__ stop,
+                                const double *__restrict__ scale) {
   pdl_wait();
   if (stop && *stop) return;
   extern __shared__ double rcs[];
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
-    double acc = 0.0;
-    for (int32_t q = item_ptr[i]; q < item_ptr[i + 1]; ++q) acc += item_sum[q];
-    const double v = s[i] * acc;
+    double v;
+    if (item_ptr) {
+      double acc = 0.0;
+      for (int32_t q = item_ptr[i]; q < item_ptr[i + 1]; ++q) acc += item_sum[q];
+      v = s[i] * acc;
+    } else {
+      v = item_sum[i];
+    }
     rcs[i] = v;
     if (blockIdx.x == 0 && rc_out) rc_out[i] = v;
   }
@@ -82,7 +90,7 @@ __global__ void k_coarse_matvec(int32_t k, const double *__restrict__ Ainv,
     for (; t < k; t += 32) a0 += row[t] * rcs[t];
     double acc = (a0 + a1) + (a2 + a3);
     acc = warp_sum(acc);
-    if (lane == 0) ec[S] = acc;
+    if (lane == 0) ec[S] = scale ? acc * scale[S] : acc;
   }
 }
 
@@ -334,7 +342,26 @@ rr_status coarse_matvec(int32_t k, const double *Ainv, const RestrictPlan &plan,
     attr_for = k;
   }
   RR_LAUNCH_PDL(k_coarse_matvec, grid_for(k, kWarps), kThreads, smem, st, k, Ainv, plan.item_ptr,
-            plan.item_sum, s, rc, ec, stop);
+            plan.item_sum, s, rc, ec, stop, (const double *)nullptr);
+  return RR_OK;
+}
+
+rr_status coarse_matvec_eigen(int32_t k, const double *Vk, const double *Qt, const double *dvec,
+                              const RestrictPlan &plan, const double *s, double *tmp, double *ec,
+                              const int32_t *stop, cudaStream_t st) {
+  const size_t smem = sizeof(double) * (size_t)k;
+  static int attr_for = -1;
+  if (smem > 48 * 1024 && attr_for < k) {
+    RR_CUDA(cudaFuncSetAttribute(k_coarse_matvec, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    attr_for = k;
+  }
+  // t = diag(1 / (mu + lambda)) Q^T r_c (rows of Vk are the eigenvectors), then e_c = Q t
+  RR_LAUNCH_PDL(k_coarse_matvec, grid_for(k, kWarps), kThreads, smem, st, k, Vk, plan.item_ptr,
+                plan.item_sum, s, (double *)nullptr, tmp, stop, dvec);
+  RR_LAUNCH_PDL(k_coarse_matvec, grid_for(k, kWarps), kThreads, smem, st, k, Qt,
+                (const int32_t *)nullptr, (const double *)tmp, s, (double *)nullptr, ec, stop,
+                (const double *)nullptr);
   return RR_OK;
 }
 

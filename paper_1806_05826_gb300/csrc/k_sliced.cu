@@ -308,7 +308,9 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather(
 // values as in gather8, then the scan tree, then the carry), so every run
 // gives identical bits.
 constexpr int kStreamUnroll = 4;
-__global__ void __launch_bounds__(kSliceThreads, 1) k_stream_gather(
+constexpr int kStreamThreads = 512;   // 16 warps, two CTAs per SM (two slices resident)
+constexpr int kStreamRanges = 32;     // word ranges per task (each warp takes two)
+__global__ void __launch_bounds__(kStreamThreads, 2) k_stream_gather(
     SlicedView P, const int32_t *__restrict__ wmeta, const int32_t *__restrict__ wstart,
     const float *__restrict__ xq, float *__restrict__ out, const int32_t *__restrict__ stop) {
   pdl_wait();
@@ -319,24 +321,26 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_stream_gather(
   const int32_t b = P.task_slice[task];
   const int64_t base = (int64_t)b * P.W;
   const int64_t width = min((int64_t)P.W, P.n_inner - base);
-  for (int i0 = threadIdx.x; i0 <= P.W; i0 += 4 * kSliceThreads) {
-    float v[4];
+  for (int i0 = threadIdx.x; i0 <= P.W; i0 += 8 * kStreamThreads) {
+    float v[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * kSliceThreads;
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * kStreamThreads;
       v[u] = i < width ? xq[base + i] : 0.f;
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = i0 + u * kSliceThreads;
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * kStreamThreads;
       if (i <= P.W) xs[i] = v[u];
     }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int32_t w0 = wstart[task * 33 + warp], w1 = wstart[task * 33 + warp + 1];
   const uint4 pad = make_uint4(P.W | (P.W << 16), P.W | (P.W << 16), P.W | (P.W << 16),
                                P.W | (P.W << 16));
+  for (int rg = warp; rg < kStreamRanges; rg += kStreamThreads / 32) {
+  const int32_t w0 = wstart[task * (kStreamRanges + 1) + rg];
+  const int32_t w1 = wstart[task * (kStreamRanges + 1) + rg + 1];
   float carry = 0.f;   // running sum of the piece open at the end of the previous step
   bool open = false;
   for (int32_t c = w0; c < w1; c += 32 * kStreamUnroll) {   // warp-uniform
@@ -370,6 +374,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_stream_gather(
       open = ml == -1;
       carry = open ? xl : 0.f;
     }
+  }
   }
 }
 
@@ -787,13 +792,15 @@ rr_status launch_gather(const SlicedPattern &P, const T *xq, const int32_t *stop
       if (!attr) {
         RR_CUDA(cudaFuncSetAttribute(k_stream_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)slice_smem<float>(kSliceMax)));
+        RR_CUDA(cudaFuncSetAttribute(k_stream_gather,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, 100));
         attr = true;
       }
       if (pdl)
-        RR_LAUNCH_PDL(k_stream_gather, P.ntasks, kSliceThreads, slice_smem<float>(P.W), st,
+        RR_LAUNCH_PDL(k_stream_gather, P.ntasks, kStreamThreads, slice_smem<float>(P.W), st,
                       P.view(), P.wmeta, P.wstart, xq, out, stop);
       else
-        RR_LAUNCH(k_stream_gather, P.ntasks, kSliceThreads, slice_smem<float>(P.W), st, P.view(),
+        RR_LAUNCH(k_stream_gather, P.ntasks, kStreamThreads, slice_smem<float>(P.W), st, P.view(),
                   P.wmeta, P.wstart, xq, out, stop);
       return RR_OK;
     }

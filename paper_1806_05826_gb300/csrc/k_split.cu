@@ -141,9 +141,11 @@ __global__ void __launch_bounds__(kThreads) k_split_rows(
       const int32_t q1 = sptr[lr + 1] - qbase;
       for (int32_t q = sptr[lr] - qbase + sub; q < q1; q += G) s += sslot[q];
     }
+    float hs[4] = {0.f, 0.f, 0.f, 0.f};   // four independent chains of adds
 #pragma unroll
     for (int b = 0; b < 32; ++b)
-      if (w & (1u << b)) s += vh[b];
+      if (w & (1u << b)) hs[b & 3] += vh[b];
+    s += (hs[0] + hs[1]) + (hs[2] + hs[3]);
 #pragma unroll
     for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     const float u = s + so;
@@ -214,21 +216,26 @@ __global__ void __launch_bounds__(kThreads) k_split_epilogue(
     s = warp_sum(s);
     if (lane == 0) epilogue(ep, i, s, dot, wd);
   }
+  // every other feature: one lane each; the feature's vectors are loaded
+  // before its slot sums (eight slot loads in flight), so the two
+  // dependent rounds of loads overlap
+  const bool need_r = ep.mode == CSC_PRE || ep.mode == CSC_POST || ep.mode == CSC_RESID;
   for (int64_t i0 = warp * 32; i0 < F; i0 += nwarps * 32) {   // warp-uniform
     const int64_t i = i0 + lane;
     if (i < F && !is_spec[i]) {
       const int32_t q0 = slot_ptr[i], q1 = slot_ptr[i + 1];
+      const double vi = ep.mode != CSC_RHS ? ep.v[i] : 0.0;
+      const double ri = need_r ? ep.r[i] : 0.0;
+      const double wdi = ep.mode == CSC_POST ? wd[i] : 0.0;
       float s = 0.f;
-      int32_t q = q0;
-      for (; q + 4 <= q1; q += 4) {
-        const float a = tsum[q], b = tsum[q + 1], c = tsum[q + 2], d = tsum[q + 3];
-        s += a;
-        s += b;
-        s += c;
-        s += d;
+      for (int32_t q = q0; q < q1; q += 8) {
+        float t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = q + u < q1 ? tsum[q + u] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += t[u];
       }
-      for (; q < q1; ++q) s += tsum[q];
-      epilogue(ep, i, (double)s, dot, wd);
+      epilogue_values(ep, i, (double)s, vi, ri, wdi, dot);
     }
   }
   const double tot = block_sum(dot, sm);

@@ -246,6 +246,9 @@ rr_status sliced_epilogue(const SlicedPattern &P, const CscEpilogue &ep, cudaStr
 // Vk (k x k, row e = eigenvector e); *sweeps_out the sweeps taken.
 rr_status coarse_eigen(int32_t k, const double *G, const double *s, double *mu, double *Vk,
                        int32_t *sweeps_out, cudaStream_t st);
+// Qt = Vk^T (Q row-major); d = 1 / (mu + lambda).
+rr_status eig_transpose(int32_t k, const double *Vk, double *Qt, cudaStream_t st);
+rr_status eig_dvec(int32_t k, const double *mu, double lambda, double *d, cudaStream_t st);
 // Ainv = Q diag(1 / (mu + lambda)) Q^T (exactly symmetric).
 rr_status eig_inverse(int32_t k, const double *mu, const double *Vk, double lambda, double *Ainv,
                       cudaStream_t st);
@@ -320,6 +323,11 @@ void restrict_free(RestrictPlan &plan);
 rr_status restrict_clusters(const RestrictPlan &plan, const int32_t *members, const double *r1,
                             const int32_t *stop, cudaStream_t st);
 // r_c from the item sums (also written to rc when non-null), then e_c = Ainv r_c.
+// The same with the eigendecomposition: e_c = Q (dvec * (Q^T r_c)), Vk = Q^T
+// (rows: eigenvectors), Qt = Q (row-major), dvec = 1 / (mu + lambda); tmp[k].
+rr_status coarse_matvec_eigen(int32_t k, const double *Vk, const double *Qt, const double *dvec,
+                              const RestrictPlan &plan, const double *s, double *tmp, double *ec,
+                              const int32_t *stop, cudaStream_t st);
 rr_status coarse_matvec(int32_t k, const double *Ainv, const RestrictPlan &plan, const double *s,
                         double *rc, double *ec, const int32_t *stop, cudaStream_t st);
 // z2 = z1 + s[l(i)] e_c[l(i)].

@@ -104,15 +104,28 @@ rr_status coarse_eigen_setup(rr_handle *h) {
   const int32_t k = h->k_eff;
   RR_TRY(h->mem.alloc(&h->mu, k));
   RR_TRY(h->mem.alloc(&h->Qv, (int64_t)k * k));
-  return rr::coarse_eigen(k, h->G, h->s, h->mu, h->Qv, &h->eig_sweeps, h->st);
+  RR_TRY(h->mem.alloc(&h->Qt, (int64_t)k * k));
+  RR_TRY(h->mem.alloc(&h->dvec, k));
+  RR_TRY(h->mem.alloc(&h->ec_tmp, k));
+  RR_TRY(rr::coarse_eigen(k, h->G, h->s, h->mu, h->Qv, &h->eig_sweeps, h->st));
+  return rr::eig_transpose(k, h->Qv, h->Qt, h->st);
+}
+
+// e_c = A_c^-1 P^T r1 (restriction item sums already in the plan): the
+// explicit inverse, or the eigendecomposition's two mat-vecs.
+rr_status coarse_step(rr_handle *h, const int32_t *stop, cudaStream_t st) {
+  if (h->mu)
+    return rr::coarse_matvec_eigen(h->k_eff, h->Qv, h->Qt, h->dvec, h->rplan, h->s, h->ec_tmp,
+                                   h->ec, stop, st);
+  return rr::coarse_matvec(h->k_eff, h->Ainv, h->rplan, h->s, nullptr, h->ec, stop, st);
 }
 
 rr_status build_lambda(rr_handle *h, double lambda) {
   cudaStream_t st = h->st;
   const int32_t k = h->k_eff;
   RR_TRY(rr::coarse_operator(k, h->G, h->s, lambda, h->Ac, st));
-  if (h->mu) {   // A_c^-1 = Q diag(1 / (mu + lambda)) Q^T
-    RR_TRY(rr::eig_inverse(k, h->mu, h->Qv, lambda, h->Ainv, st));
+  if (h->mu) {   // A_c^-1 = Q diag(1 / (mu + lambda)) Q^T, applied as two mat-vecs
+    RR_TRY(rr::eig_dvec(k, h->mu, lambda, h->dvec, st));
   } else {
     RR_CUDA(cudaMemcpyAsync(h->Lw, h->Ac, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, st));
     RR_TRY(rr::cholesky(k, h->Lw, h->err, st));
@@ -592,7 +605,7 @@ rr_status apply_precond(rr_handle *h, const double *r, double *z, const int32_t 
       rr::CscEpilogue pre{rr::CSC_PRE, h->lambda, h->omega, h->z1, r, h->d, h->r1, nullptr, stop};
       RR_TRY(op_apply(h, h->z1, pre, stop, st, fp32, x32 != nullptr && z1_ready));
       RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->r1, stop, st));
-      RR_TRY(rr::coarse_matvec(h->k_eff, h->Ainv, h->rplan, h->s, nullptr, h->ec, stop, st));
+      RR_TRY(coarse_step(h, stop, st));
       RR_TRY(rr::prolong_add(F, h->labels, h->s, h->ec, h->z1, h->z2, stop, st, x32));
       rr::CscEpilogue post{rr::CSC_POST, h->lambda, h->omega, h->z2, r, h->d, z, h->part_rz, stop};
       return op_apply(h, h->z2, post, stop, st, fp32, x32 != nullptr);
@@ -839,7 +852,7 @@ rr_status tlfcg_iteration(rr_handle *h, cudaStream_t st) {
     RR_TRY(rr::pcg_finish(h->t_rz, rr::kVecGrid, h->t_rr, rr::kVecGrid, h->St, nullptr, 0, st));
   }
   RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->tr, stop, st));
-  RR_TRY(rr::coarse_matvec(h->k_eff, h->Ainv, h->rplan, h->s, nullptr, h->ec, stop, st));
+  RR_TRY(coarse_step(h, stop, st));
   RR_TRY(rr::prolong_add(F, h->labels, h->s, h->ec, h->tz, h->z, stop, st));
   RR_TRY(rr::fcg_dot(F, h->z, h->q_prev, h->part_zq, stop, st));
   RR_TRY(rr::fcg_direction(F, h->part_zq, h->Sf, h->z, h->p_prev, h->p, stop, st));
@@ -863,7 +876,7 @@ rr_status fcg_iteration(rr_handle *h, const rr_mlp *net, cudaStream_t st) {
   if (net) {
     RR_TRY(rr::mlp_coarse(net, h->rplan, h->s, h->ec, stop, st));
   } else {
-    RR_TRY(rr::coarse_matvec(h->k_eff, h->Ainv, h->rplan, h->s, nullptr, h->ec, stop, st));
+    RR_TRY(coarse_step(h, stop, st));
   }
   RR_TRY(fcg_tail(h, stop, fp32, st));
   if (net) {
@@ -871,7 +884,7 @@ rr_status fcg_iteration(rr_handle *h, const rr_mlp *net, cudaStream_t st) {
     // redone with the Cholesky coarse solve (same restriction)
     RR_TRY(rr::fcg_decide(h->part_rz, h->part_pq, h->part3, h->Sf, st));
     const int32_t *fb = &h->Sf->skip_fb;
-    RR_TRY(rr::coarse_matvec(h->k_eff, h->Ainv, h->rplan, h->s, nullptr, h->ec, fb, st));
+    RR_TRY(coarse_step(h, fb, st));
     RR_TRY(fcg_tail(h, fb, fp32, st));
   }
   RR_TRY(rr::fcg_update(h->F, h->part_pq, h->part3, h->p, h->q, h->w_int, h->r, h->omega, h->d,
