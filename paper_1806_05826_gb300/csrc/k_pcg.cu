@@ -175,7 +175,7 @@ __global__ void k_pcg_update(int64_t F, const double *__restrict__ rz_part, int 
                              double *__restrict__ w, double *__restrict__ r, double omega,
                              const double *__restrict__ d, double *__restrict__ z1,
                              float *__restrict__ z1_32, double *__restrict__ rr_part,
-                             const PcgScalars *__restrict__ S) {
+                             const PcgScalars *__restrict__ S, const double *__restrict__ wd) {
   pdl_wait();
   if (S->converged) return;
   __shared__ double sm[kWarps + 1];
@@ -190,7 +190,7 @@ __global__ void k_pcg_update(int64_t F, const double *__restrict__ rz_part, int 
     r[i] = ri;
     acc += ri * ri;
     if (z1) {
-      const double zi = omega * ri / d[i];
+      const double zi = wd ? ri * wd[i] : omega * ri / d[i];
       z1[i] = zi;
       if (z1_32) z1_32[i] = (float)zi;
     }
@@ -387,9 +387,9 @@ rr_status pcg_direction(int64_t F, const double *rz_part, int n_rz, const double
 rr_status pcg_update(int64_t F, const double *rz_part, int n_rz, const double *pq_part, int n_pq,
                      const double *p, const double *q, double *w, double *r, double omega,
                      const double *d, double *z1, double *rr_part, PcgScalars *S,
-                     cudaStream_t st, float *z1_32) {
+                     cudaStream_t st, float *z1_32, const double *wd) {
   RR_LAUNCH_PDL(k_pcg_update, kVecGrid, kThreads, 0, st, F, rz_part, n_rz, pq_part, n_pq, p, q, w, r,
-            omega, d, z1, z1_32, rr_part, S);
+            omega, d, z1, z1_32, rr_part, S, wd);
   return RR_OK;
 }
 

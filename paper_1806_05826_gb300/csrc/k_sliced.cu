@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather(
 // many are in flight per warp. The sums have a fixed order (each word's 8
 // values as in gather8, then the scan tree, then the carry), so every run
 // gives identical bits.
-constexpr int kStreamUnroll = 4;
+constexpr int kStreamUnroll = 2;   // steps per prefetched group
 constexpr int kStreamThreads = 512;   // 16 warps, two CTAs per SM (two slices resident)
 constexpr int kStreamRanges = 32;     // word ranges per task (each warp takes two)
 __global__ void __launch_bounds__(kStreamThreads, 2) k_stream_gather(
@@ -343,36 +343,46 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_stream_gather(
   const int32_t w1 = wstart[task * (kStreamRanges + 1) + rg + 1];
   float carry = 0.f;   // running sum of the piece open at the end of the previous step
   bool open = false;
-  for (int32_t c = w0; c < w1; c += 32 * kStreamUnroll) {   // warp-uniform
-    uint4 q[kStreamUnroll];
-    int32_t m[kStreamUnroll];
+  // two steps per group; the next group's loads are issued before this
+  // group is summed
+  uint4 qa[kStreamUnroll], qn[kStreamUnroll];
+  int32_t ma[kStreamUnroll], mn[kStreamUnroll];
+  auto load = [&](int32_t c, uint4 *q, int32_t *m) {
 #pragma unroll
     for (int u = 0; u < kStreamUnroll; ++u) {
       const int32_t w = c + 32 * u + lane;
       q[u] = w < w1 ? __ldg(P.idx + w) : pad;
       m[u] = w < w1 ? __ldg(wmeta + w) : -2;   // -2: past the range
     }
+  };
+  if (w0 < w1) load(w0, qa, ma);
+  for (int32_t c = w0; c < w1; c += 32 * kStreamUnroll) {   // warp-uniform
+    if (c + 32 * kStreamUnroll < w1) load(c + 32 * kStreamUnroll, qn, mn);
 #pragma unroll
     for (int u = 0; u < kStreamUnroll; ++u) {
       if (c + 32 * u >= w1) break;   // warp-uniform
-      float x = gather8(xs, q[u]);
-      const int32_t mp = __shfl_up_sync(0xffffffffu, m[u], 1);
-      int f = lane == 0 ? (open ? 0 : 1) : (mp >= 0 ? 1 : 0);   // a piece starts here
+      float x = gather8(xs, qa[u]);
+      // pieces of this step: word i starts one when word i - 1 ended one (or
+      // i = 0 and no piece is open); dist = lanes since this lane's piece began
+      const uint32_t ends = __ballot_sync(0xffffffffu, ma[u] >= 0);
+      const uint32_t starts = (ends << 1) | (open ? 0u : 1u);
+      const uint32_t upto = starts & (0xffffffffu >> (31 - lane));
+      const int dist = upto ? lane - (31 - __clz((int)upto)) : 32;   // 32: began earlier
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
         const float xy = __shfl_up_sync(0xffffffffu, x, d);
-        const int fy = __shfl_up_sync(0xffffffffu, f, d);
-        if (lane >= d) {
-          if (!f) x = xy + x;
-          f |= fy;
-        }
+        if (lane >= d && dist >= d) x = xy + x;
       }
-      if (!f) x = carry + x;   // still in the piece carried from the previous step
-      if (m[u] >= 0) out[m[u]] = x;
-      const float xl = __shfl_sync(0xffffffffu, x, 31);
-      const int32_t ml = __shfl_sync(0xffffffffu, m[u], 31);
-      open = ml == -1;
-      carry = open ? xl : 0.f;
+      if (!upto) x = carry + x;   // still in the piece carried from the previous step
+      if (ma[u] >= 0) out[ma[u]] = x;
+      carry = __shfl_sync(0xffffffffu, x, 31);
+      open = (__ballot_sync(0xffffffffu, ma[u] == -1) >> 31) & 1u;
+      if (!open) carry = 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kStreamUnroll; ++u) {
+      qa[u] = qn[u];
+      ma[u] = mn[u];
     }
   }
   }

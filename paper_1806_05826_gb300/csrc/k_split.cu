@@ -207,12 +207,27 @@ __global__ void __launch_bounds__(kThreads) k_split_epilogue(
   for (int64_t h = warp; h < n_spec; h += nwarps) {   // warp-uniform
     const int32_t i = spec[h], kind = spec_kind[h];
     double s = 0.0;
-    if (kind >= 0) {
-      for (int32_t b = lane; b < nblk; b += 32) s += (double)zpart[(int64_t)b * H + kind];
-    } else if (kind == -1) {
-      for (int32_t b = lane; b < nblk; b += 32) s += (double)upart[b];
+    // eight loads in flight per lane (block partials, then tail slots)
+    if (kind != -2) {
+      for (int32_t b0 = lane; b0 < nblk; b0 += 8 * 32) {
+        float t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int32_t b = b0 + 32 * u;
+          t[u] = b < nblk ? (kind >= 0 ? zpart[(int64_t)b * H + kind] : upart[b]) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += (double)t[u];
+      }
     }
-    for (int32_t q = slot_ptr[i] + lane; q < slot_ptr[i + 1]; q += 32) s += (double)tsum[q];
+    const int32_t sq1 = slot_ptr[i + 1];
+    for (int32_t q0 = slot_ptr[i] + lane; q0 < sq1; q0 += 8 * 32) {
+      float t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = q0 + 32 * u < sq1 ? tsum[q0 + 32 * u] : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += (double)t[u];
+    }
     s = warp_sum(s);
     if (lane == 0) epilogue(ep, i, s, dot, wd);
   }

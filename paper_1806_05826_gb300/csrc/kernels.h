@@ -347,7 +347,8 @@ rr_status pcg_direction(int64_t F, const double *rz_part, int n_rz, const double
 rr_status pcg_update(int64_t F, const double *rz_part, int n_rz, const double *pq_part, int n_pq,
                      const double *p, const double *q, double *w, double *r, double omega,
                      const double *d, double *z1, double *rr_part, PcgScalars *S,
-                     cudaStream_t st, float *z1_32 = nullptr);
+                     cudaStream_t st, float *z1_32 = nullptr,
+                     const double *wd = nullptr);
 // Fresh scalars for a fixed number of plain CG steps inside another solver's
 // iteration (no stopping target; stopped when *outer_converged).
 rr_status inner_start(PcgScalars *S, const int32_t *outer_converged, cudaStream_t st);

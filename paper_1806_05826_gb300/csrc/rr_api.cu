@@ -628,7 +628,8 @@ rr_status pcg_iteration(rr_handle *h, cudaStream_t st) {
   RR_TRY(op_apply(h, h->p, ap, stop, st, fp32, x32 != nullptr));
   RR_TRY(rr::pcg_update(F, h->part_rz, n_rz, h->part_pq, rr::kVecGrid, h->p, h->q, h->w_int,
                         h->r, h->omega, h->d, twolevel ? h->z1 : nullptr, h->part_rr, h->S, st,
-                        twolevel ? x32 : nullptr));
+                        twolevel ? x32 : nullptr,
+                        (fp32 && h->split.active) ? h->split.wd : nullptr));
   RR_TRY(rr::pcg_finish(h->part_rz, n_rz, h->part_rr, rr::kVecGrid, h->S, h->history,
                         h->hist_cap, st));
   return RR_OK;
