@@ -66,6 +66,7 @@ struct rr_handle {
   double *G = nullptr, *Ac = nullptr, *Lw = nullptr, *Linv = nullptr, *Ainv = nullptr;
   double *mu = nullptr, *Qv = nullptr;   // RR_COARSE_EIGEN: eigenvalues, eigenvector rows
   double *Qt = nullptr, *dvec = nullptr, *ec_tmp = nullptr;   // Q row-major, 1/(mu+lambda)
+  float *Ainv32 = nullptr;               // RR_PREC_MIXED: FP32 copy of Ainv, rows padded to 4
   int32_t eig_sweeps = 0;
   // smoother
   double *d = nullptr;

@@ -16,20 +16,33 @@ namespace rr {
 
 namespace {
 
-// Restriction, pass 1: one block per work item, an item being a range of at
-// most kRestrictItem members of one cluster (large clusters have several).
+// Restriction, pass 1: one warp per work item, an item being a range of at
+// most kRestrictItem members of one cluster (large clusters have several);
+// the lanes stride over the members with four loads in flight, then a fixed
+// shuffle tree.
 __global__ void k_restrict_items(const RestrictItem *__restrict__ items, int32_t n_items,
                                  const int32_t *__restrict__ members, const double *__restrict__ r1,
                                  double *__restrict__ item_sum, const int32_t *__restrict__ stop) {
   pdl_wait();
   if (stop && *stop) return;
-  __shared__ double sm[kWarps + 1];
-  for (int32_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t it = warp; it < n_items; it += nwarps) {
     const RestrictItem w = items[it];
     double acc = 0.0;
-    for (int32_t m = w.begin + threadIdx.x; m < w.end; m += blockDim.x) acc += r1[members[m]];
-    const double tot = block_sum(acc, sm);
-    if (threadIdx.x == 0) item_sum[it] = tot;
+    for (int32_t m0 = w.begin + lane; m0 < w.end; m0 += 4 * 32) {
+      double t[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int32_t m = m0 + 32 * u;
+        t[u] = m < w.end ? r1[members[m]] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc += t[u];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) item_sum[it] = acc;
   }
 }
 
@@ -91,6 +104,59 @@ __global__ void k_coarse_matvec(int32_t k, const double *__restrict__ Ainv,
     double acc = (a0 + a1) + (a2 + a3);
     acc = warp_sum(acc);
     if (lane == 0) ec[S] = scale ? acc * scale[S] : acc;
+  }
+}
+
+// The same coarse step in FP32 (the FP32 inner iterations' preconditioner):
+// r_c staged as FP32, Ainv32 (FP32 copy of the FP64 inverse, k padded to a
+// multiple of 4 per row: ld) read four entries per load, FP32 products and
+// sums, e_c stored in FP64.
+__global__ void k_coarse_matvec32(int32_t k, int32_t ld, const float *__restrict__ Ainv32,
+                                  const int32_t *__restrict__ item_ptr,
+                                  const double *__restrict__ item_sum, const double *__restrict__ s,
+                                  double *__restrict__ ec, const int32_t *__restrict__ stop) {
+  pdl_wait();
+  if (stop && *stop) return;
+  extern __shared__ float rcs32[];
+  for (int i = threadIdx.x; i < ld; i += blockDim.x) {
+    double acc = 0.0;
+    if (i < k)
+      for (int32_t q = item_ptr[i]; q < item_ptr[i + 1]; ++q) acc += item_sum[q];
+    rcs32[i] = i < k ? (float)(s[i] * acc) : 0.f;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float4 *x4 = reinterpret_cast<const float4 *>(rcs32);
+  for (int64_t S = warp; S < k; S += nwarps) {
+    const float4 *row = reinterpret_cast<const float4 *>(Ainv32 + S * ld);
+    float a0 = 0.f, a1 = 0.f;
+    int t = lane;
+    for (; t + 32 < ld / 4; t += 64) {
+      const float4 r0 = __ldg(row + t), r1 = __ldg(row + t + 32);
+      const float4 v0 = x4[t], v1 = x4[t + 32];
+      a0 += r0.x * v0.x + r0.y * v0.y + r0.z * v0.z + r0.w * v0.w;
+      a1 += r1.x * v1.x + r1.y * v1.y + r1.z * v1.z + r1.w * v1.w;
+    }
+    for (; t < ld / 4; t += 32) {
+      const float4 r0 = __ldg(row + t), v0 = x4[t];
+      a0 += r0.x * v0.x + r0.y * v0.y + r0.z * v0.z + r0.w * v0.w;
+    }
+    float acc = a0 + a1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) ec[S] = (double)acc;
+  }
+}
+
+__global__ void k_to_f32_padded(int32_t k, int32_t ld, const double *__restrict__ A,
+                                float *__restrict__ A32) {
+  const int64_t n = (int64_t)k * ld;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / ld, j = e % ld;
+    A32[e] = j < k ? (float)A[i * k + j] : 0.f;
   }
 }
 
@@ -327,8 +393,8 @@ void restrict_free(RestrictPlan &plan) {
 
 rr_status restrict_clusters(const RestrictPlan &plan, const int32_t *members, const double *r1,
                             const int32_t *stop, cudaStream_t st) {
-  RR_LAUNCH_PDL(k_restrict_items, std::max(1, std::min(plan.n_items, kSMs * 4)), kThreads, 0, st,
-            plan.items, plan.n_items, members, r1, plan.item_sum, stop);
+  RR_LAUNCH_PDL(k_restrict_items, grid_for(plan.n_items, kWarps), kThreads, 0, st, plan.items,
+                plan.n_items, members, r1, plan.item_sum, stop);
   return RR_OK;
 }
 
@@ -343,6 +409,28 @@ rr_status coarse_matvec(int32_t k, const double *Ainv, const RestrictPlan &plan,
   }
   RR_LAUNCH_PDL(k_coarse_matvec, grid_for(k, kWarps), kThreads, smem, st, k, Ainv, plan.item_ptr,
             plan.item_sum, s, rc, ec, stop, (const double *)nullptr);
+  return RR_OK;
+}
+
+rr_status coarse_to_f32(int32_t k, const double *Ainv, float *Ainv32, cudaStream_t st) {
+  const int32_t ld = (k + 3) & ~3;
+  RR_LAUNCH(k_to_f32_padded, grid_for((int64_t)k * ld, kThreads), kThreads, 0, st, k, ld, Ainv,
+            Ainv32);
+  return RR_OK;
+}
+
+rr_status coarse_matvec32(int32_t k, const float *Ainv32, const RestrictPlan &plan,
+                          const double *s, double *ec, const int32_t *stop, cudaStream_t st) {
+  const int32_t ld = (k + 3) & ~3;
+  const size_t smem = sizeof(float) * (size_t)ld;
+  static int attr_for = -1;
+  if (smem > 48 * 1024 && attr_for < k) {
+    RR_CUDA(cudaFuncSetAttribute(k_coarse_matvec32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    attr_for = k;
+  }
+  RR_LAUNCH_PDL(k_coarse_matvec32, grid_for(k, kWarps), kThreads, smem, st, k, ld, Ainv32,
+                plan.item_ptr, plan.item_sum, s, ec, stop);
   return RR_OK;
 }
 

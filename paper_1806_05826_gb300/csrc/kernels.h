@@ -302,7 +302,7 @@ struct PcgScalars {
   int32_t first;     // 1 before the first direction of a (re)start
   int32_t limit;     // iteration limit of the device-side loop
 };
-constexpr int kVecGrid = kSMs * 4;   // fixed grid of the vector kernels (deterministic partials)
+constexpr int kVecGrid = kSMs * 2;   // fixed grid of the vector kernels (deterministic partials)
 
 // Restriction r_c[S] = s_S * sum_{i in S} r1[i] over the member list (members of
 // S ascending). Large clusters are cut into items of <= kRestrictItem members;
@@ -323,6 +323,11 @@ void restrict_free(RestrictPlan &plan);
 rr_status restrict_clusters(const RestrictPlan &plan, const int32_t *members, const double *r1,
                             const int32_t *stop, cudaStream_t st);
 // r_c from the item sums (also written to rc when non-null), then e_c = Ainv r_c.
+// FP32 form for the FP32 inner iterations: Ainv32 = FP32 copy of Ainv with
+// rows padded to a multiple of 4 (coarse_to_f32), FP32 products and sums.
+rr_status coarse_to_f32(int32_t k, const double *Ainv, float *Ainv32, cudaStream_t st);
+rr_status coarse_matvec32(int32_t k, const float *Ainv32, const RestrictPlan &plan,
+                          const double *s, double *ec, const int32_t *stop, cudaStream_t st);
 // The same with the eigendecomposition: e_c = Q (dvec * (Q^T r_c)), Vk = Q^T
 // (rows: eigenvectors), Qt = Q (row-major), dvec = 1 / (mu + lambda); tmp[k].
 rr_status coarse_matvec_eigen(int32_t k, const double *Vk, const double *Qt, const double *dvec,

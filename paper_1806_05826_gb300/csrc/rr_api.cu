@@ -113,7 +113,9 @@ rr_status coarse_eigen_setup(rr_handle *h) {
 
 // e_c = A_c^-1 P^T r1 (restriction item sums already in the plan): the
 // explicit inverse, or the eigendecomposition's two mat-vecs.
-rr_status coarse_step(rr_handle *h, const int32_t *stop, cudaStream_t st) {
+rr_status coarse_step(rr_handle *h, const int32_t *stop, cudaStream_t st, bool fp32) {
+  if (fp32 && h->Ainv32 && !h->mu)   // the FP32 inner iterations' coarse step
+    return rr::coarse_matvec32(h->k_eff, h->Ainv32, h->rplan, h->s, h->ec, stop, st);
   if (h->mu)
     return rr::coarse_matvec_eigen(h->k_eff, h->Qv, h->Qt, h->dvec, h->rplan, h->s, h->ec_tmp,
                                    h->ec, stop, st);
@@ -130,6 +132,7 @@ rr_status build_lambda(rr_handle *h, double lambda) {
     RR_CUDA(cudaMemcpyAsync(h->Lw, h->Ac, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, st));
     RR_TRY(rr::cholesky(k, h->Lw, h->err, st));
     RR_TRY(rr::chol_inverse(k, h->Lw, h->Linv, h->Ainv, st));
+    if (h->Ainv32) RR_TRY(rr::coarse_to_f32(k, h->Ainv, h->Ainv32, st));
   }
   RR_CUDA(cudaMemsetAsync(h->max_bits, 0, sizeof(unsigned long long), st));
   if (h->dense) {
@@ -298,6 +301,8 @@ rr_status setup_impl_dense(rr_handle *h, const rr_matrix *X, double lambda, int3
   RR_TRY(m.alloc(&h->omega_dev, 1));
   RR_TRY(m.alloc(&h->max_bits, 1));
   RR_TRY(coarse_eigen_setup(h));
+  if (h->opt.precision == RR_PREC_MIXED && !h->mu)
+    RR_TRY(m.alloc(&h->Ainv32, (int64_t)k_eff * ((k_eff + 3) & ~3)));
   RR_TRY(build_lambda(h, lambda));
   RR_TRY(phase(6));
   RR_TRY(m.alloc(&h->dpart, rr::dense_part_rows(N, F) * F));
@@ -526,6 +531,8 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&h->omega_dev, 1));
   RR_TRY(m.alloc(&h->max_bits, 1));
   RR_TRY(coarse_eigen_setup(h));
+  if (h->opt.precision == RR_PREC_MIXED && !h->mu)
+    RR_TRY(m.alloc(&h->Ainv32, (int64_t)k_eff * ((k_eff + 3) & ~3)));
   RR_TRY(build_lambda(h, lambda));
 
   RR_TRY(phase(6));
@@ -605,7 +612,7 @@ rr_status apply_precond(rr_handle *h, const double *r, double *z, const int32_t 
       rr::CscEpilogue pre{rr::CSC_PRE, h->lambda, h->omega, h->z1, r, h->d, h->r1, nullptr, stop};
       RR_TRY(op_apply(h, h->z1, pre, stop, st, fp32, x32 != nullptr && z1_ready));
       RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->r1, stop, st));
-      RR_TRY(coarse_step(h, stop, st));
+      RR_TRY(coarse_step(h, stop, st, fp32));
       RR_TRY(rr::prolong_add(F, h->labels, h->s, h->ec, h->z1, h->z2, stop, st, x32));
       rr::CscEpilogue post{rr::CSC_POST, h->lambda, h->omega, h->z2, r, h->d, z, h->part_rz, stop};
       return op_apply(h, h->z2, post, stop, st, fp32, x32 != nullptr);
@@ -853,7 +860,7 @@ rr_status tlfcg_iteration(rr_handle *h, cudaStream_t st) {
     RR_TRY(rr::pcg_finish(h->t_rz, rr::kVecGrid, h->t_rr, rr::kVecGrid, h->St, nullptr, 0, st));
   }
   RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->tr, stop, st));
-  RR_TRY(coarse_step(h, stop, st));
+  RR_TRY(coarse_step(h, stop, st, fp32));
   RR_TRY(rr::prolong_add(F, h->labels, h->s, h->ec, h->tz, h->z, stop, st));
   RR_TRY(rr::fcg_dot(F, h->z, h->q_prev, h->part_zq, stop, st));
   RR_TRY(rr::fcg_direction(F, h->part_zq, h->Sf, h->z, h->p_prev, h->p, stop, st));
@@ -877,7 +884,7 @@ rr_status fcg_iteration(rr_handle *h, const rr_mlp *net, cudaStream_t st) {
   if (net) {
     RR_TRY(rr::mlp_coarse(net, h->rplan, h->s, h->ec, stop, st));
   } else {
-    RR_TRY(coarse_step(h, stop, st));
+    RR_TRY(coarse_step(h, stop, st, fp32));
   }
   RR_TRY(fcg_tail(h, stop, fp32, st));
   if (net) {
@@ -885,7 +892,7 @@ rr_status fcg_iteration(rr_handle *h, const rr_mlp *net, cudaStream_t st) {
     // redone with the Cholesky coarse solve (same restriction)
     RR_TRY(rr::fcg_decide(h->part_rz, h->part_pq, h->part3, h->Sf, st));
     const int32_t *fb = &h->Sf->skip_fb;
-    RR_TRY(coarse_step(h, fb, st));
+    RR_TRY(coarse_step(h, fb, st, fp32));
     RR_TRY(fcg_tail(h, fb, fp32, st));
   }
   RR_TRY(rr::fcg_update(h->F, h->part_pq, h->part3, h->p, h->q, h->w_int, h->r, h->omega, h->d,
