@@ -402,6 +402,45 @@ rr_status rr_apply_noalloc(int64_t n_rows, int64_t n_cols, const int64_t *row_pt
  * decomposition), RR_CUDA_ERROR. */
 rr_status rr_get_eigen(const rr_handle *h, double *mu_host, double *Q_host, int32_t *sweeps);
 
+/* ---- Bayesian ridge regression by Gibbs sampling (Section 2, Eq. (ni_xtx)).
+ * Likelihood y ~ N(X w, tau^-1 I), prior w ~ N(0, lambda^-1 I), hyperpriors
+ * lambda ~ Gamma(alpha, beta) and tau ~ Gamma(a_tau, b_tau) (shape, rate).
+ * Sample t draws w given (lambda, tau) by noise injection, solving
+ *   (X^T X + (lambda/tau) I) w = X^T (y + e1) + e2 / tau,
+ *   e1 ~ N(0, tau^-1 I_N), e2 ~ N(0, lambda I_F),
+ * with the handle's solver (the clustering is kept; the coarse operator is
+ * rebuilt at lambda/tau, which an RR_COARSE_EIGEN handle does with two
+ * mat-vec scalings and no factorisation), then lambda | w ~ Gamma(alpha +
+ * F/2, beta + ||w||^2 / 2) and, unless a_tau <= 0 (tau fixed at tau0),
+ * tau | w ~ Gamma(a_tau + N/2, b_tau + ||y - X w||^2 / 2). All draws come
+ * from a counter-based generator on (seed, stream, index): SplitMix64 (Steele,
+ * Lea & Flood 2014) with the stream base mix(mix(seed) xor stream *
+ * 0xD1B54A32D192ED03) and uniform i = (mix(base + (i + 1) * 0x9E3779B97F4A7C15)
+ * >> 11) 2^-53; normal i by Box-Muller from the uniforms i and 2^40 + i; e1 of
+ * sample t on stream 2t, e2 on stream 2t + 1; Gamma by Marsaglia & Tsang
+ * (2000) on stream 2^20 + 2t (lambda) and 2^20 + 2t + 1 (tau), attempt j
+ * taking its normal from the uniforms 2j, 2j + 1 and its u from 2^32 + j. */
+typedef struct {
+  double alpha, beta;     /* lambda ~ Gamma(alpha, beta); alpha + F/2 >= 1 */
+  double a_tau, b_tau;    /* tau ~ Gamma(a_tau, b_tau); a_tau <= 0: tau fixed */
+  double lambda0, tau0;   /* the chain's starting values, > 0 */
+  uint64_t seed;
+  double tol;             /* each solve's relative residual, in (0, 1) */
+} rr_bayes_params;
+
+/* Runs n_samples Gibbs steps. y: device double[n_rows]. w_mean: device
+ * double[n_cols] or NULL, the mean of w over the samples t >= burnin.
+ * lam_trace, tau_trace: host double[n_samples] or NULL, lambda and tau drawn
+ * at each step (after its solve); iters: host int32[n_samples] or NULL, the
+ * PCG iterations of each solve. The handle's lambda is restored before
+ * returning. Synchronous. Errors: RR_INVALID_ARG (NULL handle or y, a
+ * parameter out of range, n_samples < 1, burnin outside [0, n_samples)),
+ * RR_NOT_CONVERGED or RR_NONFINITE from a solve (the chain stops there, the
+ * traces hold the steps done), RR_CUDA_ERROR. */
+rr_status rr_bayes(rr_handle *h, const double *y, const rr_bayes_params *p, int32_t n_samples,
+                   int32_t burnin, double *w_mean, double *lam_trace, double *tau_trace,
+                   int32_t *iters);
+
 /* The batched engine's sparse-times-dense variant chosen by its autotuner for
  * the last rr_solve_batch (or rr_harvest) on h: systems per slab (32, 64 or
  * 128: the columns one warp carries through a pass over X) and row segments

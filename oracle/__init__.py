@@ -27,4 +27,4 @@ Parity unpinned: iteration counts and speed-ups against the paper's tables
 (its datasets are not available), and k-means labels beyond "same initial
 centres give the same labels" (Lloyd's optimum is not unique).
 """
-from . import sparse, kmeans, twolevel, krylov, mlp, learned, eigen  # noqa: F401
+from . import sparse, kmeans, twolevel, krylov, mlp, learned, eigen, bayes  # noqa: F401

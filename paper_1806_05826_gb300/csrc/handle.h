@@ -83,6 +83,7 @@ struct rr_handle {
   double *part_rz = nullptr, *part_pq = nullptr, *part_rr = nullptr, *part_bb = nullptr;
   double *scal = nullptr;
   double *w_int = nullptr;         // the iterate (graphs capture fixed pointers)
+  double *bayes_y = nullptr;       // rr_bayes: y + e1, then y - X w (N)
   cudaStream_t cap_stream = nullptr;
   cudaGraph_t loop_graph = nullptr;
   cudaGraphExec_t loop_exec = nullptr;

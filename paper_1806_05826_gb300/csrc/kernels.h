@@ -253,6 +253,18 @@ rr_status eig_dvec(int32_t k, const double *mu, double lambda, double *d, cudaSt
 rr_status eig_inverse(int32_t k, const double *mu, const double *Vk, double lambda, double *Ainv,
                       cudaStream_t st);
 
+// ---- k_bayes.cu ---------------------------------------------------------
+// Gibbs sampling with noise injection (see k_bayes.cu for the draws).
+rr_status bayes_noise_y(int64_t N, const double *y, uint64_t seed, int64_t step, double tau,
+                        double *yt, cudaStream_t st);
+rr_status bayes_add_e2(int64_t F, double *b, uint64_t seed, int64_t step, double lam, double tau,
+                       cudaStream_t st);
+rr_status bayes_resid(int64_t N, const double *y, const double *u, double *r, cudaStream_t st);
+rr_status bayes_gamma(double a, double rate0, const double *part, int n_part, uint64_t seed,
+                      uint64_t stream, double *out, cudaStream_t st);
+rr_status bayes_accum(int64_t F, const double *w, double *acc, cudaStream_t st);
+rr_status bayes_scale(int64_t F, double s, double *v, cudaStream_t st);
+
 // ---- k_split.cu ---------------------------------------------------------
 // Split form of the FP32 operator (see k_split.cu): the all-ones columns as a
 // rank-one term, the H most frequent other columns as a row-major bitmap, the

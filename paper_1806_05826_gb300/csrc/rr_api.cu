@@ -729,10 +729,11 @@ rr_status run_iterations(rr_handle *h, int32_t limit) {
   return RR_OK;
 }
 
-// b = X^T y; w = 0; r = b; ||b||; z1 = omega D^-1 r (no synchronisation).
+// b = X^T y (y == NULL: b is already set); w = 0; r = b; ||b||;
+// z1 = omega D^-1 r (no synchronisation).
 rr_status solve_start(rr_handle *h, const double *y, double tol, cudaStream_t st) {
   const int64_t F = h->F;
-  RR_TRY(rhs_apply(h, y, h->b, st));
+  if (y) RR_TRY(rhs_apply(h, y, h->b, st));
   RR_CUDA(cudaMemsetAsync(h->w_int, 0, sizeof(double) * F, st));
   RR_TRY(rr::copy_f64(h->r, h->b, F, st));
   RR_TRY(rr::dot_parts(F, h->b, h->b, h->part_bb, st));
@@ -789,7 +790,7 @@ rr_status solve_impl(rr_handle *h, const double *y, double *w, double tol, rr_in
     ++restarts;
     RR_TRY(solve_restart(h, tol, st));
   }
-  RR_TRY(rr::copy_f64(w, h->w_int, F, st));
+  if (w) RR_TRY(rr::copy_f64(w, h->w_int, F, st));
   RR_CUDA(cudaMemcpyAsync(h->S_host, h->S, sizeof(rr::PcgScalars), cudaMemcpyDeviceToHost, st));
   RR_CUDA(cudaStreamSynchronize(st));
   if (info) {
@@ -978,7 +979,7 @@ rr_status solve_fcg_impl(rr_handle *h, const rr_mlp *net, const double *y, doubl
   const int64_t F = h->F;
   RR_TRY(fcg_reserve(h));
   if (h->opt.solver == RR_SOLVER_TLFCG) RR_TRY(tlfcg_reserve(h));
-  RR_TRY(rhs_apply(h, y, h->b, st));
+  if (y) RR_TRY(rhs_apply(h, y, h->b, st));
   RR_CUDA(cudaMemsetAsync(h->w_int, 0, sizeof(double) * F, st));
   RR_CUDA(cudaMemsetAsync(h->p_prev, 0, sizeof(double) * F, st));
   RR_CUDA(cudaMemsetAsync(h->q_prev, 0, sizeof(double) * F, st));
@@ -1039,7 +1040,7 @@ rr_status solve_fcg_impl(rr_handle *h, const rr_mlp *net, const double *y, doubl
     RR_TRY(rr::fcg_start(h->part_bb, 1, h->part_rr, tol, 0, net ? 1 : 0, h->Sf, st));
     RR_TRY(rr::jacobi(F, h->omega, h->r, h->d, h->z1, nullptr, nullptr, st));
   }
-  RR_TRY(rr::copy_f64(w, h->w_int, F, st));
+  if (w) RR_TRY(rr::copy_f64(w, h->w_int, F, st));
   RR_CUDA(cudaMemcpyAsync(h->Sf_host, h->Sf, sizeof(rr::FcgScalars), cudaMemcpyDeviceToHost, st));
   RR_CUDA(cudaStreamSynchronize(st));
   if (info) {
@@ -1196,6 +1197,75 @@ rr_status solve_many_impl(int32_t n, rr_handle *const *hs, const double *const *
   return worst;
 }
 
+
+// ---- Bayesian regression by Gibbs sampling with noise injection (Section 2,
+// Eq. (ni_xtx)); the draws are k_bayes.cu's.
+constexpr uint64_t kStreamGamma = 1ULL << 20;
+
+// u = X v in FP64 (the residual y - X w that tau is drawn from).
+rr_status matvec_f64(rr_handle *h, const double *v, double *u, cudaStream_t st) {
+  if (h->dense) return rr::dense_matvec(h->N, h->F, h->Xd, v, u, nullptr, false, st);
+  RR_TRY(rr::sliced_gather(h->pcsr, v, nullptr, nullptr, st, false));
+  RR_TRY(rr::sliced_slot_sum(h->pcsr, u, st));
+  return RR_OK;
+}
+
+rr_status bayes_impl(rr_handle *h, const double *y, const rr_bayes_params &p, int32_t n_samples,
+                     int32_t burnin, double *w_mean, double *lam_trace, double *tau_trace,
+                     int32_t *iters) {
+  cudaStream_t st = h->st;
+  const int64_t N = h->N, F = h->F;
+  if (!h->bayes_y) RR_TRY(h->mem.alloc(&h->bayes_y, std::max<int64_t>(N, 1)));
+  if (w_mean) RR_CUDA(cudaMemsetAsync(w_mean, 0, sizeof(double) * F, st));
+  const bool draw_tau = p.a_tau > 0.0;
+  double lam = p.lambda0, tau = p.tau0;
+  rr_status result = RR_OK;
+  for (int32_t t = 0; t < n_samples; ++t) {
+    // b = X^T (y + e1) + e2 / tau
+    RR_TRY(rr::bayes_noise_y(N, y, p.seed, t, tau, h->bayes_y, st));
+    RR_TRY(rhs_apply(h, h->bayes_y, h->b, st));
+    RR_TRY(rr::bayes_add_e2(F, h->b, p.seed, t, lam, tau, st));
+    // the system at lambda / tau, solved from that b
+    destroy_graph(h);
+    RR_TRY(build_lambda(h, lam / tau));
+    rr_info info{};
+    result = h->opt.solver == RR_SOLVER_TLFCG ? solve_fcg_impl(h, nullptr, nullptr, nullptr, p.tol, &info)
+                                             : solve_impl(h, nullptr, nullptr, p.tol, &info);
+    if (result != RR_OK) break;
+    if (iters) iters[t] = info.iters;
+    if (w_mean && t >= burnin) RR_TRY(rr::bayes_accum(F, h->w_int, w_mean, st));
+    // lambda | w, then tau | w
+    RR_TRY(rr::dot_parts(F, h->w_int, h->w_int, h->part_rr, st));
+    RR_TRY(rr::bayes_gamma(p.alpha + 0.5 * (double)F, p.beta, h->part_rr, rr::kVecGrid, p.seed,
+                           kStreamGamma + 2 * (uint64_t)t, h->scal, st));
+    if (draw_tau) {
+      RR_TRY(matvec_f64(h, h->w_int, h->u, st));
+      RR_TRY(rr::bayes_resid(N, y, h->u, h->bayes_y, st));
+      RR_TRY(rr::dot_parts(N, h->bayes_y, h->bayes_y, h->part_rr, st));
+      RR_TRY(rr::bayes_gamma(p.a_tau + 0.5 * (double)N, p.b_tau, h->part_rr, rr::kVecGrid, p.seed,
+                             kStreamGamma + 2 * (uint64_t)t + 1, h->scal + 2, st));
+    }
+    RR_CUDA(cudaMemcpyAsync(h->scal_host, h->scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RR_CUDA(cudaStreamSynchronize(st));
+    if (h->scal_host[1] != 1.0 || (draw_tau && h->scal_host[3] != 1.0)) {
+      rr_set_error("rr_bayes: no gamma draw accepted in 1000 attempts at sample %d", t);
+      result = RR_NONFINITE;
+      break;
+    }
+    lam = h->scal_host[0];
+    if (draw_tau) tau = h->scal_host[2];
+    if (!(lam > 0.0) || !isfinite(lam) || !(tau > 0.0) || !isfinite(tau)) {
+      rr_set_error("rr_bayes: lambda or tau not positive and finite at sample %d", t);
+      result = RR_NONFINITE;
+      break;
+    }
+    if (lam_trace) lam_trace[t] = lam;
+    if (tau_trace) tau_trace[t] = tau;
+  }
+  if (w_mean && n_samples > burnin)
+    RR_TRY(rr::bayes_scale(F, 1.0 / (double)(n_samples - burnin), w_mean, st));
+  return result;
+}
 }  // namespace
 
 extern "C" {
@@ -1524,6 +1594,46 @@ rr_status rr_get_coarse(const rr_handle *h, double *Ac_host, int64_t *G_host) {
   if (G_host)
     for (size_t i = 0; i < kk; ++i) G_host[i] = (int64_t)g[i];
   return RR_OK;
+}
+
+rr_status rr_bayes(rr_handle *h, const double *y, const rr_bayes_params *p, int32_t n_samples,
+                   int32_t burnin, double *w_mean, double *lam_trace, double *tau_trace,
+                   int32_t *iters) {
+  if (!h || !y || !p) {
+    rr_set_error("rr_bayes: handle, y and params must not be NULL");
+    return RR_INVALID_ARG;
+  }
+  if (n_samples < 1 || burnin < 0 || burnin >= n_samples) {
+    rr_set_error("rr_bayes: need n_samples >= 1 and 0 <= burnin < n_samples");
+    return RR_INVALID_ARG;
+  }
+  const bool ok = p->alpha > 0.0 && isfinite(p->alpha) && p->beta >= 0.0 && isfinite(p->beta) &&
+                  p->alpha + 0.5 * (double)h->F >= 1.0 && p->lambda0 > 0.0 &&
+                  isfinite(p->lambda0) && p->tau0 > 0.0 && isfinite(p->tau0) && p->tol > 0.0 &&
+                  p->tol < 1.0 && isfinite(p->a_tau) &&
+                  (p->a_tau <= 0.0 || (p->b_tau >= 0.0 && isfinite(p->b_tau) &&
+                                       p->a_tau + 0.5 * (double)h->N >= 1.0));
+  if (!ok) {
+    rr_set_error("rr_bayes: parameters out of range (alpha > 0, beta >= 0, lambda0, tau0 > 0, "
+                 "tol in (0, 1), b_tau >= 0 when a_tau > 0)");
+    return RR_INVALID_ARG;
+  }
+  const double lam_keep = h->lambda;
+  rr_status s = bayes_impl(h, y, *p, n_samples, burnin, w_mean, lam_trace, tau_trace, iters);
+  // the handle's own lambda back
+  destroy_graph(h);
+  const rr_status s2 = build_lambda(h, lam_keep);
+  if (s == RR_OK) s = s2;
+  const cudaError_t ce = cudaStreamSynchronize(h->st);
+  if (ce != cudaSuccess && s == RR_OK) {
+    rr_set_error("rr_bayes: %s", cudaGetErrorString(ce));
+    s = RR_CUDA_ERROR;
+  }
+  if (s == RR_OK || s == RR_NOT_CONVERGED || s == RR_NONFINITE) {
+    const rr_status e = check_dev_error(h, "rr_bayes");
+    if (e != RR_OK) s = e;
+  }
+  return s;
 }
 
 rr_status rr_get_eigen(const rr_handle *h, double *mu_host, double *Q_host, int32_t *sweeps) {

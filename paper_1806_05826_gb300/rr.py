@@ -62,6 +62,13 @@ class rr_info(ctypes.Structure):
         return d
 
 
+class rr_bayes_params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("a_tau", ctypes.c_double), ("b_tau", ctypes.c_double),
+                ("lambda0", ctypes.c_double), ("tau0", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("tol", ctypes.c_double)]
+
+
 class RRError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{_STATUS.get(status, status)}: {msg}")
@@ -107,6 +114,8 @@ _SIGS = {
     "rr_last_error": (ctypes.c_char_p, []),
     "rr_query_batch": (ctypes.c_int, [_P, _P, _P, _P]),
     "rr_get_eigen": (ctypes.c_int, [_P, _P, _P, _P]),
+    "rr_bayes": (ctypes.c_int, [_P, _P, ctypes.POINTER(rr_bayes_params), ctypes.c_int32,
+                                ctypes.c_int32, _P, _P, _P, _P]),
     "rr_launch_count": (ctypes.c_int64, []),
     "rr_apply_noalloc": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P,
                                         ctypes.c_double, _P, _P, _P]),
@@ -547,6 +556,26 @@ def rr_get_eigen(h: Handle):
     sw = ctypes.c_int32()
     _check(load().rr_get_eigen(h.ptr, mu.ctypes.data, Q.ctypes.data, ctypes.byref(sw)))
     return mu, Q, sw.value
+
+
+def rr_bayes(h: Handle, y, n_samples, burnin=0, w_mean=None, alpha=1.0, beta=1.0, a_tau=1.0,
+             b_tau=1.0, lambda0=1.0, tau0=1.0, seed=0, tol=1e-8):
+    """Gibbs sampling with noise injection: returns (lambda trace, tau trace,
+    iterations per solve); w_mean (device float64[F] or None) receives the
+    mean of w over the samples after burnin."""
+    f64 = _torch().float64
+    yp = _dev(y, f64, h.N, "y")
+    wp = None if w_mean is None else _dev(w_mean, f64, h.F, "w_mean")
+    n = int(n_samples)
+    if n < 1:
+        raise ValueError("n_samples must be >= 1")
+    p = rr_bayes_params(float(alpha), float(beta), float(a_tau), float(b_tau), float(lambda0),
+                        float(tau0), int(seed), float(tol))
+    lam, tau = np.zeros(n), np.zeros(n)
+    iters = np.zeros(n, dtype=np.int32)
+    _check(load().rr_bayes(h.ptr, yp, ctypes.byref(p), n, int(burnin), wp, lam.ctypes.data,
+                           tau.ctypes.data, iters.ctypes.data))
+    return lam, tau, iters
 
 
 def rr_get_coarse(h: Handle):

@@ -784,3 +784,95 @@ def test_eigen_theorem1_spectrum():
     ev = np.linalg.eigvalsh((X.T @ X).astype(float))
     nz = np.sort(ev[ev > 1e-9 * ev.max()])
     assert np.allclose(np.sort(mu[mu > 1e-9 * mu.max()]), nz, rtol=1e-11)
+
+
+# ---------------------------------------------------------------- Bayesian regression
+
+def test_counter_normals_are_standard_normal():
+    """The Box-Muller normals of the counter-based generator: a
+    Kolmogorov-Smirnov test against the library normal, and independence of
+    neighbouring draws (their correlation)."""
+    from scipy import stats
+    z = synth.normal(21, 5, 20000)
+    assert stats.kstest(z, stats.norm.cdf).pvalue > 1e-3
+    assert abs(np.corrcoef(z[:-1], z[1:])[0, 1]) <= 5 / np.sqrt(len(z))
+
+
+def test_gamma_draw_distribution():
+    """Marsaglia & Tsang on the counter-based uniforms draws Gamma(shape a,
+    rate): a Kolmogorov-Smirnov test against the library's gamma law and the
+    first two moments (a / rate, a / rate^2), at the method's boundary a = 1
+    and above."""
+    from scipy import stats
+    from oracle import bayes
+    n = 2000
+    for a, rate in ((1.0, 2.0), (3.7, 0.5), (250.5, 40.0)):
+        x = np.array([bayes.gamma_draw(a, rate, 11, bayes.STREAM_GAMMA + s) for s in range(n)])
+        assert stats.kstest(x, stats.gamma(a, scale=1.0 / rate).cdf).pvalue > 1e-3
+        m, v = a / rate, a / rate ** 2
+        assert abs(x.mean() - m) <= 5 * np.sqrt(v / n)
+        # the sample variance's spread follows from the gamma law's kurtosis 6/a
+        assert abs(x.var() / v - 1) <= 5 * np.sqrt((2 + 6 / a) / n)
+
+
+def _bayes_small():
+    X = random_binary(60, 6, 0.3, 8)
+    n, f, rp, ci = csr_of(X)
+    y = synth.normal(8, 77, n)
+    return X, y, tl.setup_binary(n, f, rp, ci, 1.0, 2, seed=0)
+
+
+def test_noise_injected_sample_has_the_conditional_posterior_moments():
+    """Section 2, Eq. (ni_xtx): over the draws of e1 and e2 the solution of the
+    noise-injected system has mean (X^T X + (lambda/tau) I)^-1 X^T y and
+    covariance (tau X^T X + lambda I)^-1, the conditional posterior of w given
+    lambda and tau (Gaussian prior and likelihood; the normal equations in
+    closed form with the library solver), checked by sampling."""
+    from oracle import bayes
+    X, y, two = _bayes_small()
+    lam, tau = 20.0, 2.0
+    G = (X.T @ X).astype(float)
+    f = G.shape[0]
+    mean = np.linalg.solve(G + (lam / tau) * np.eye(f), X.T @ y)
+    cov = np.linalg.inv(tau * G + lam * np.eye(f))
+    n = 3000
+    W = np.array([bayes.noise_sample(two, y, lam, tau, 5, t, 1e-12).w for t in range(n)])
+    assert np.all(np.abs(W.mean(0) - mean) <= 5 * np.sqrt(np.diag(cov) / n))
+    S = np.cov(W.T)
+    assert np.linalg.norm(S - cov) / np.linalg.norm(cov) <= 0.15
+
+
+def test_gibbs_chain_recovers_the_generating_precisions():
+    """Section 2's conjugate updates: on data drawn from the model (w with
+    precision lambda = 4, noise with precision tau = 100) the chain's draws
+    of lambda and tau settle around the generating values (their posteriors
+    have relative spread about sqrt(2/F) and sqrt(2/N)), and its mean of w
+    is within a few posterior standard deviations of the generating w."""
+    from oracle import bayes
+    N, F = 4000, 200
+    lam_true, tau_true = 4.0, 100.0
+    Xs = synth.zipf_binary(N, F, 0.05, 1.1, 5)
+    M = osp.from_csr(N, F, Xs.row_ptr, Xs.col_idx)
+    w_true = synth.normal(5, 900, F) / np.sqrt(lam_true)
+    y = osp.X_mv(M, w_true) + synth.normal(5, 901, N) / np.sqrt(tau_true)
+    two = tl.setup_binary(N, F, Xs.row_ptr, Xs.col_idx, 1.0, 20, seed=0)
+    p = bayes.Params(alpha=1.0, beta=1.0, a_tau=1.0, b_tau=1.0, lambda0=1.0, tau0=1.0, seed=7,
+                     tol=1e-10)
+    lams, taus, wmean, _ = bayes.gibbs(two, y, p, n_samples=30, burnin=10)
+    assert 0.85 * tau_true <= taus[10:].mean() <= 1.15 * tau_true
+    assert 0.6 * lam_true <= lams[10:].mean() <= 1.6 * lam_true
+    # the mean of 20 draws is within a few posterior standard deviations,
+    # diag((tau X^T X + lambda I)^-1)^1/2, of the generating w
+    G = osp.dense_A(M, 0.0)
+    sd = np.sqrt(np.diag(np.linalg.inv(tau_true * G + lam_true * np.eye(F))))
+    assert np.all(np.abs(wmean - w_true) <= 5 * sd * np.sqrt(1 + 1 / 20))
+
+
+def test_gibbs_with_fixed_tau():
+    """a_tau <= 0 keeps tau at tau0; lambda is still drawn every step."""
+    from oracle import bayes
+    X, y, two = _bayes_small()
+    p = bayes.Params(a_tau=0.0, tau0=3.0, lambda0=2.0, seed=1, tol=1e-10)
+    lams, taus, _, _ = bayes.gibbs(two, y, p, n_samples=4)
+    assert np.all(taus == 3.0)
+    assert len(set(lams.tolist())) == 4

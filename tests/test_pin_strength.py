@@ -295,8 +295,55 @@ def _jacobi_rotation_sign(mp):
     mp.setattr(eigen, "jacobi_eigh", lambda S, tol=1e-15, max_sweeps=50: bad(S, tol, 3))
 
 
+def _bayes_patched(mp, fn_name, good, bad):
+    """One line of an oracle/bayes.py function changed, the rest as it is."""
+    import inspect
+    import textwrap
+    from oracle import bayes
+    src = textwrap.dedent(inspect.getsource(getattr(bayes, fn_name)))
+    assert good in src
+    ns = dict(vars(bayes))
+    exec(src.replace(good, bad), ns)
+    mp.setattr(bayes, fn_name, ns[fn_name])
+
+
+def _gamma_times_rate(mp):
+    _bayes_patched(mp, "gamma_draw", "return d * v / rate", "return d * v * rate")
+
+
+def _gamma_without_cube(mp):
+    _bayes_patched(mp, "gamma_draw", "v = t * t * t", "v = t * t")
+
+
+def _noise_e2_times_tau(mp):
+    _bayes_patched(mp, "noise_sample", "+ e2 / tau", "+ e2 * tau")
+
+
+def _noise_e1_unscaled(mp):
+    _bayes_patched(mp, "noise_sample", "synth.normal(seed, 2 * step, N) / math.sqrt(tau)",
+                   "synth.normal(seed, 2 * step, N)")
+
+
+def _lambda_rate_without_half(mp):
+    _bayes_patched(mp, "gibbs", "p.beta + 0.5 * float(w @ w)", "p.beta + float(w @ w)")
+
+
+def _tau_shape_without_half_n(mp):
+    _bayes_patched(mp, "gibbs", "p.a_tau + 0.5 * N", "p.a_tau + N")
+
+
 P = pins
 CASES = [
+    ("gamma draw multiplied by the rate", _gamma_times_rate, [P.test_gamma_draw_distribution]),
+    ("gamma draw with (1 + c x)^2", _gamma_without_cube, [P.test_gamma_draw_distribution]),
+    ("noise e2 multiplied by tau", _noise_e2_times_tau,
+     [P.test_noise_injected_sample_has_the_conditional_posterior_moments]),
+    ("noise e1 without the tau^-1/2 scale", _noise_e1_unscaled,
+     [P.test_noise_injected_sample_has_the_conditional_posterior_moments]),
+    ("lambda rate without the 1/2", _lambda_rate_without_half,
+     [P.test_gibbs_chain_recovers_the_generating_precisions]),
+    ("tau shape with N instead of N/2", _tau_shape_without_half_n,
+     [P.test_gibbs_chain_recovers_the_generating_precisions]),
     ("eigen coarse inverse without lambda", _eigen_inverse_without_lambda,
      [P.test_eigen_coarse_inverse_equals_cholesky_solve_at_every_lambda]),
     ("Jacobi stops on a cancelled off-diagonal norm", _jacobi_stops_on_cancelled_norm,
