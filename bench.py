@@ -48,6 +48,10 @@ def parse():
                     help="skip the oracle's exact solutions of the workload (error of each solve)")
     ap.add_argument("--no-eigen", action="store_true",
                     help="skip the section comparing the eigendecomposition coarse solve")
+    ap.add_argument("--no-bayes", action="store_true",
+                    help="skip the Gibbs-sampling (rr_bayes) section")
+    ap.add_argument("--only-bayes", action="store_true",
+                    help="only the Gibbs-sampling section")
     ap.add_argument("--only-eigen", action="store_true",
                     help="run the eigendecomposition section alone (profiling runs)")
     ap.add_argument("--no-small", action="store_true",
@@ -453,6 +457,33 @@ def measure_eigen(rr, row_ptr, col_idx, N, F, k, lams, opts, dev, stream, y_dev)
     return out
 
 
+def measure_bayes(rr, row_ptr, col_idx, N, F, k, lam, opts, dev, y_dev, n_samples=8, burnin=2):
+    """Bayesian ridge regression by Gibbs sampling with noise injection
+    (rr_bayes): every sample solves the system at a new lambda / tau, so the
+    coarse solve is rebuilt each time; Cholesky (a factorisation per sample)
+    against the eigendecomposition (two mat-vec scalings per sample). Wall
+    time of the synchronous call over n_samples, per sample."""
+    import time
+    import torch
+    out = {"n_samples": n_samples, "burnin": burnin,
+           "prior": {"alpha": 1.0, "beta": 1.0, "a_tau": 1.0, "b_tau": 1.0}, "tol": TOL}
+    wm = torch.empty(F, dtype=torch.float64, device=dev)
+    for name, coarse in (("cholesky", rr.RR_COARSE_CHOLESKY), ("eigen", rr.RR_COARSE_EIGEN)):
+        h = rr.rr_setup(row_ptr, col_idx, N, F, lam, k, **dict(opts, coarse=coarse))
+        rr.rr_bayes(h, y_dev, 2, 0, wm, tol=TOL, seed=1)          # warm-up
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        lams, taus, iters = rr.rr_bayes(h, y_dev, n_samples, burnin, wm, tol=TOL, seed=2)
+        torch.cuda.synchronize(dev)
+        ms = (time.perf_counter() - t0) * 1e3
+        out[name] = {"ms_per_sample": round(ms / n_samples, 2), "iters": [int(i) for i in iters],
+                     "lambda_last": float(lams[-1]), "tau_last": float(taus[-1])}
+        rr.rr_free(h)
+    out["speedup_eigen"] = round(out["cholesky"]["ms_per_sample"] /
+                                 max(1e-9, out["eigen"]["ms_per_sample"]), 3)
+    return out
+
+
 def measure_tlfcg(rr, row_ptr, col_idx, N, F, k, lams, opts, y_dev, last_infos):
     """The same systems (each lambda, same target, same clustering) solved by the
     paper's TLFCG: flexible CG whose preconditioner is two CG rougher steps and the
@@ -699,6 +730,8 @@ def run_ours(args, rank, world, local):
     if args.only_eigen:
         return {"coarse_eigen": measure_eigen(rr, row_ptr, col_idx, N, F, k, lams, opts, dev,
                                               stream, y_dev)}
+    if args.only_bayes:
+        return {"bayes": measure_bayes(rr, row_ptr, col_idx, N, F, k, lams[0], opts, dev, y_dev)}
     if args.only == "batched":
         return {"batched": measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world,
                                            args.batch_targets)}
@@ -790,9 +823,11 @@ def run_ours(args, rank, world, local):
                "h2d_bytes_per_step": 8 * (N + 1) + 4 * nnz + 8 * N,
                "d2h_bytes_per_step": 8 * F * len(lams)}
 
-    batched = many = learned = tlfcg = eig = None
+    batched = many = learned = tlfcg = eig = bayes = None
     if not args.no_eigen and args.workload == WORKLOAD:
         eig = measure_eigen(rr, row_ptr, col_idx, N, F, k, lams, opts, dev, stream, y_dev)
+    if not args.no_bayes and args.workload == WORKLOAD:
+        bayes = measure_bayes(rr, row_ptr, col_idx, N, F, k, lams[0], opts, dev, y_dev)
     if not args.no_tlfcg:
         tlfcg = measure_tlfcg(rr, row_ptr, col_idx, N, F, k, lams, opts, y_dev, last_infos=all_infos[-1])
     if not args.no_batch and args.workload == WORKLOAD:
@@ -836,7 +871,7 @@ def run_ours(args, rank, world, local):
                       "step_ms": [round(t, 3) for t in step_ms]},
         "e2e": e2e, "roofline": roofline, "clocks": clk.summary(), "gpu_launches": launches,
         "batched": batched, "many": many, "learned": learned, "tlfcg": tlfcg,
-        "parity": parity, "small_fp64": small, "coarse_eigen": eig,
+        "parity": parity, "small_fp64": small, "coarse_eigen": eig, "bayes": bayes,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle's own counts where recorded (its FP64 PCG needs fewer

@@ -73,7 +73,8 @@ struct rr_handle {
   int64_t *gsum = nullptr;   // sum_j |(X^T X)_ij| = sum of the row lengths over column i
   double *omega_dev = nullptr;
   unsigned long long *max_bits = nullptr;
-  rr::RestrictPlan rplan;
+  rr::RestrictPlan rplan;   // restriction items of the single-system path
+  rr::RestrictPlan bplan;   // the batched path's (larger) items
   rr::SlicedPattern pcsr;   // X by row, vector v cut in feature slices
   rr::SlicedPattern pcsc;   // X^T by column, vector u cut in row slices
   rr::SplitOperator split;  // the FP32 operator's split form (mixed precision, binary X)

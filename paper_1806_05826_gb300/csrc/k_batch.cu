@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kThreads) k_brestart(int64_t F, int32_t S, int
 }
 
 // Restriction, pass 1: item partials ip[item, c] = sum over the item's members
-// of r1[member, c] (items: ranges of at most kRestrictItem members of one cluster).
+// of r1[member, c] (items: ranges of at most kRestrictItemBatch members of one cluster).
 __global__ void __launch_bounds__(kThreads) k_brestrict(const RestrictItem *__restrict__ items,
                                                         int32_t n_items, int32_t S, int64_t ld,
                                                         const int32_t *__restrict__ members,
@@ -872,7 +872,7 @@ rr_status biteration(const BatchRun &R, cudaStream_t st) {
   RR_TRY(bapply_f32(R, st));
   RR_TRY(bepilogue_f32(R, BEpi{BEPI_PRE, B->z1, B->r, B->r1, nullptr}, st));
   // coarse correction: r_c = P^T r1; e_c = A_c^-1 r_c; z2 = z1 + P e_c
-  const RestrictPlan &pl = h->rplan;
+  const RestrictPlan &pl = h->bplan;
   RR_LAUNCH_PDL(k_brestrict, dim3((unsigned)std::max(1, std::min(pl.n_items, kSMs * 4)), (unsigned)R.n_slabs),
             kThreads, 0, st, pl.items, pl.n_items, R.S, R.ld, h->members, B->r1, B->col, B->ip);
   RR_LAUNCH_PDL(k_bcombine, dim3((unsigned)((kpad + 3) / 4), (unsigned)R.n_slabs), kThreads, 0, st,
@@ -970,7 +970,7 @@ rr_status batch_reserve(rr_handle *h, int64_t ld, int32_t nlam) {
   double **vecs[] = {&B->b, &B->w, &B->r, &B->r1, &B->z1, &B->z2, &B->z, &B->p, &B->q, &B->rt};
   for (double **v : vecs) RR_TRY(B->mem.alloc(v, fv));
   RR_TRY(B->mem.alloc(&B->part, (size_t)kBEpiBlocks * ld));
-  RR_TRY(B->mem.alloc(&B->ip, (size_t)std::max(1, h->rplan.n_items) * ld));
+  RR_TRY(B->mem.alloc(&B->ip, (size_t)std::max(1, h->bplan.n_items) * ld));
   RR_TRY(B->mem.alloc(&B->U64, (size_t)N * ld));
   RR_TRY(B->mem.alloc(&B->Zp64, (size_t)std::max<int64_t>(1, B->n_units2) * ld));
   RR_TRY(B->mem.alloc(&B->V, fv));
@@ -1511,7 +1511,7 @@ extern "C" rr_status rr_harvest(rr_handle *h, int32_t nrhs, const double *Y, dou
   double *wrefT = nullptr;
   int64_t *pos = nullptr, *scr = nullptr;
   RR_TRY(tmp.alloc(&wrefT, (size_t)F * ld));
-  RR_TRY(tmp.alloc(&hv.ipE, (size_t)std::max(1, h->rplan.n_items) * ld));
+  RR_TRY(tmp.alloc(&hv.ipE, (size_t)std::max(1, h->bplan.n_items) * ld));
   RR_TRY(tmp.alloc(&hv.rcE, (size_t)kpad * ld));
   RR_TRY(tmp.alloc(&hv.Xs, (size_t)slots * k));
   RR_TRY(tmp.alloc(&hv.Ts, (size_t)slots * k));

@@ -376,11 +376,9 @@ __global__ void k_draw_rows(int32_t B, int64_t n, uint64_t seed, int64_t base, i
 
 // ---------------------------------------------------------------- inference
 
-// x = r_c / ||r_c|| (FP32, zero padded to kp) from the restriction's item sums
-// (r_c[S] = s_S * sum of the items of S, in order); nrm = ||r_c|| in FP64.
-// One block.
-__global__ void k_mlp_input(int32_t k, int32_t kp, const int32_t *__restrict__ item_ptr,
-                            const double *__restrict__ item_sum, const double *__restrict__ s,
+// x = r_c / ||r_c|| (FP32, zero padded to kp) from the restricted vector;
+// nrm = ||r_c|| in FP64. One block.
+__global__ void k_mlp_input(int32_t k, int32_t kp, const double *__restrict__ rc,
                             float *__restrict__ x, double *__restrict__ nrm,
                             const int32_t *__restrict__ stop) {
   pdl_wait();
@@ -389,9 +387,7 @@ __global__ void k_mlp_input(int32_t k, int32_t kp, const int32_t *__restrict__ i
   extern __shared__ double rcs[];
   double acc = 0.0;
   for (int S = threadIdx.x; S < k; S += blockDim.x) {
-    double t = 0.0;
-    for (int32_t q = item_ptr[S]; q < item_ptr[S + 1]; ++q) t += item_sum[q];
-    t *= s[S];
+    const double t = rc[S];
     rcs[S] = t;
     acc += t * t;
   }
@@ -594,8 +590,9 @@ rr_status pack_rows(rr_mlp *m, int32_t B, const int64_t *idx, const float *X, co
 rr_status mlp_coarse(const rr_mlp *m, const RestrictPlan &plan, const double *s, double *ec,
                      const int32_t *stop, cudaStream_t st) {
   const int32_t k = m->k, kp = m->kp, H = m->H;
-  RR_LAUNCH_PDL(k_mlp_input, 1, kThreads, sizeof(double) * k, st, k, kp, plan.item_ptr, plan.item_sum, s,
-            m->xin, m->nrm, stop);
+  (void)s;
+  RR_LAUNCH_PDL(k_mlp_input, 1, kThreads, sizeof(double) * k, st, k, kp, (const double *)plan.rc,
+                m->xin, m->nrm, stop);
   const int g1 = (H + kWarps - 1) / kWarps;
   RR_LAUNCH_PDL(k_mlp_gemv, g1, kThreads, sizeof(float) * kp, st, H, kp, m->W1b, m->P + m->ob1, m->xin,
             1, m->g1, 0, (const double *)nullptr, (double *)nullptr, stop);

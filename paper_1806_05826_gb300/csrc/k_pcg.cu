@@ -46,8 +46,28 @@ __global__ void k_restrict_items(const RestrictItem *__restrict__ items, int32_t
   }
 }
 
-// Restriction, pass 2 fused with the coarse solve: r_c[S] = s_S * (sum of the
-// item sums of S, in order) is staged in shared memory, then e_c = Ainv r_c.
+// Restriction, pass 2: r_c[S] = s_S * (the item sums of S), one warp per
+// cluster, lanes strided over the items, a fixed shuffle tree.
+__global__ void k_restrict_combine(int32_t k, const int32_t *__restrict__ item_ptr,
+                                   const double *__restrict__ item_sum,
+                                   const double *__restrict__ s, double *__restrict__ rc,
+                                   const int32_t *__restrict__ stop) {
+  pdl_wait();
+  if (stop && *stop) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t S = warp; S < k; S += nwarps) {
+    double acc = 0.0;
+    for (int32_t q = item_ptr[S] + lane; q < item_ptr[S + 1]; q += 32) acc += item_sum[q];
+    acc = warp_sum(acc);
+    if (lane == 0) rc[S] = s[S] * acc;
+  }
+}
+
+// The coarse solve e_c = Ainv r_c with r_c staged in shared memory: r_c from
+// the item sums (r_c[S] = s_S * (sum of the item sums of S, in order)), or,
+// with item_ptr == nullptr, item_sum itself.
 // With item_ptr == nullptr the input vector is item_sum itself (a plain
 // mat-vec ec = Ainv x); with scale, ec[S] is multiplied by scale[S].
 __global__ void k_coarse_matvec(int32_t k, const double *__restrict__ Ainv,
@@ -112,18 +132,12 @@ __global__ void k_coarse_matvec(int32_t k, const double *__restrict__ Ainv,
 // multiple of 4 per row: ld) read four entries per load, FP32 products and
 // sums, e_c stored in FP64.
 __global__ void k_coarse_matvec32(int32_t k, int32_t ld, const float *__restrict__ Ainv32,
-                                  const int32_t *__restrict__ item_ptr,
-                                  const double *__restrict__ item_sum, const double *__restrict__ s,
-                                  double *__restrict__ ec, const int32_t *__restrict__ stop) {
+                                  const double *__restrict__ rc, double *__restrict__ ec,
+                                  const int32_t *__restrict__ stop) {
   pdl_wait();
   if (stop && *stop) return;
   extern __shared__ float rcs32[];
-  for (int i = threadIdx.x; i < ld; i += blockDim.x) {
-    double acc = 0.0;
-    if (i < k)
-      for (int32_t q = item_ptr[i]; q < item_ptr[i + 1]; ++q) acc += item_sum[q];
-    rcs32[i] = i < k ? (float)(s[i] * acc) : 0.f;
-  }
+  for (int i = threadIdx.x; i < ld; i += blockDim.x) rcs32[i] = i < k ? (float)rc[i] : 0.f;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -160,20 +174,20 @@ __global__ void k_to_f32_padded(int32_t k, int32_t ld, const double *__restrict_
   }
 }
 
-__global__ void k_restrict_plan(int32_t k, const int64_t *__restrict__ cl_ptr,
+__global__ void k_restrict_plan(int32_t k, const int64_t *__restrict__ cl_ptr, int32_t item_size,
                                 const int32_t *__restrict__ item_ptr, RestrictItem *__restrict__ items) {
   for (int32_t S = blockIdx.x * blockDim.x + threadIdx.x; S < k; S += gridDim.x * blockDim.x) {
     const int64_t b = cl_ptr[S], e = cl_ptr[S + 1];
     int32_t q = item_ptr[S];
-    for (int64_t m = b; m < e; m += kRestrictItem, ++q)
-      items[q] = RestrictItem{(int32_t)m, (int32_t)min(e, m + kRestrictItem)};
+    for (int64_t m = b; m < e; m += item_size, ++q)
+      items[q] = RestrictItem{(int32_t)m, (int32_t)min(e, m + item_size)};
   }
 }
 
-__global__ void k_restrict_counts(int32_t k, const int64_t *__restrict__ cl_ptr,
+__global__ void k_restrict_counts(int32_t k, const int64_t *__restrict__ cl_ptr, int32_t item_size,
                                   int64_t *__restrict__ cnt) {
   for (int32_t S = blockIdx.x * blockDim.x + threadIdx.x; S < k; S += gridDim.x * blockDim.x)
-    cnt[S] = (cl_ptr[S + 1] - cl_ptr[S] + kRestrictItem - 1) / kRestrictItem;
+    cnt[S] = (cl_ptr[S + 1] - cl_ptr[S] + item_size - 1) / item_size;
 }
 
 __global__ void k_i64_to_i32(int64_t n, const int64_t *__restrict__ in, int32_t *__restrict__ out) {
@@ -364,22 +378,24 @@ __global__ void k_axpby(int64_t n, double a, const double *__restrict__ x, doubl
 }  // namespace
 
 rr_status restrict_plan(int32_t k, const int64_t *cl_ptr, RestrictPlan &plan, int64_t *scratch,
-                        cudaStream_t st) {
+                        cudaStream_t st, int32_t item_size) {
   // scratch: >= 2 (k + 1) + scan scratch int64
   int64_t *cnt = scratch, *off = scratch + (k + 1), *scr = scratch + 2 * (k + 1);
-  RR_LAUNCH(k_restrict_counts, grid_for(k, kThreads), kThreads, 0, st, k, cl_ptr, cnt);
+  RR_LAUNCH(k_restrict_counts, grid_for(k, kThreads), kThreads, 0, st, k, cl_ptr, item_size, cnt);
   RR_TRY(scan_exclusive(cnt, off, k, scr, st));
   int64_t n = 0;
   RR_CUDA(cudaMemcpyAsync(&n, off + k, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
   RR_CUDA(cudaStreamSynchronize(st));
   plan.n_items = (int32_t)n;
+  plan.k = k;
   RR_CUDA(cudaMalloc(&plan.item_ptr, sizeof(int32_t) * (k + 1)));
   RR_CUDA(cudaMalloc(&plan.items, sizeof(RestrictItem) * std::max<int64_t>(1, n)));
   RR_CUDA(cudaMalloc(&plan.item_sum, sizeof(double) * std::max<int64_t>(1, n)));
+  RR_CUDA(cudaMalloc(&plan.rc, sizeof(double) * std::max<int32_t>(1, k)));
   RR_LAUNCH(k_i64_to_i32, grid_for(k + 1, kThreads), kThreads, 0, st, (int64_t)k + 1, off,
             plan.item_ptr);
-  RR_LAUNCH(k_restrict_plan, grid_for(k, kThreads), kThreads, 0, st, k, cl_ptr, plan.item_ptr,
-            plan.items);
+  RR_LAUNCH(k_restrict_plan, grid_for(k, kThreads), kThreads, 0, st, k, cl_ptr, item_size,
+            plan.item_ptr, plan.items);
   RR_CUDA(cudaStreamSynchronize(st));
   return RR_OK;
 }
@@ -388,13 +404,16 @@ void restrict_free(RestrictPlan &plan) {
   cudaFree(plan.item_ptr);
   cudaFree(plan.items);
   cudaFree(plan.item_sum);
+  cudaFree(plan.rc);
   plan = RestrictPlan{};
 }
 
 rr_status restrict_clusters(const RestrictPlan &plan, const int32_t *members, const double *r1,
-                            const int32_t *stop, cudaStream_t st) {
+                            const double *s, const int32_t *stop, cudaStream_t st) {
   RR_LAUNCH_PDL(k_restrict_items, grid_for(plan.n_items, kWarps), kThreads, 0, st, plan.items,
                 plan.n_items, members, r1, plan.item_sum, stop);
+  RR_LAUNCH_PDL(k_restrict_combine, grid_for(plan.k, kWarps), kThreads, 0, st, plan.k,
+                plan.item_ptr, plan.item_sum, s, plan.rc, stop);
   return RR_OK;
 }
 
@@ -407,8 +426,10 @@ rr_status coarse_matvec(int32_t k, const double *Ainv, const RestrictPlan &plan,
                                  (int)smem));
     attr_for = k;
   }
-  RR_LAUNCH_PDL(k_coarse_matvec, grid_for(k, kWarps), kThreads, smem, st, k, Ainv, plan.item_ptr,
-            plan.item_sum, s, rc, ec, stop, (const double *)nullptr);
+  (void)s;
+  RR_LAUNCH_PDL(k_coarse_matvec, grid_for(k, kWarps), kThreads, smem, st, k, Ainv,
+                (const int32_t *)nullptr, (const double *)plan.rc, s, rc, ec, stop,
+                (const double *)nullptr);
   return RR_OK;
 }
 
@@ -429,8 +450,9 @@ rr_status coarse_matvec32(int32_t k, const float *Ainv32, const RestrictPlan &pl
                                  (int)smem));
     attr_for = k;
   }
+  (void)s;
   RR_LAUNCH_PDL(k_coarse_matvec32, grid_for(k, kWarps), kThreads, smem, st, k, ld, Ainv32,
-                plan.item_ptr, plan.item_sum, s, ec, stop);
+                (const double *)plan.rc, ec, stop);
   return RR_OK;
 }
 
@@ -445,8 +467,9 @@ rr_status coarse_matvec_eigen(int32_t k, const double *Vk, const double *Qt, con
     attr_for = k;
   }
   // t = diag(1 / (mu + lambda)) Q^T r_c (rows of Vk are the eigenvectors), then e_c = Q t
-  RR_LAUNCH_PDL(k_coarse_matvec, grid_for(k, kWarps), kThreads, smem, st, k, Vk, plan.item_ptr,
-                plan.item_sum, s, (double *)nullptr, tmp, stop, dvec);
+  RR_LAUNCH_PDL(k_coarse_matvec, grid_for(k, kWarps), kThreads, smem, st, k, Vk,
+                (const int32_t *)nullptr, (const double *)plan.rc, s, (double *)nullptr, tmp, stop,
+                dvec);
   RR_LAUNCH_PDL(k_coarse_matvec, grid_for(k, kWarps), kThreads, smem, st, k, Qt,
                 (const int32_t *)nullptr, (const double *)tmp, s, (double *)nullptr, ec, stop,
                 (const double *)nullptr);

@@ -317,24 +317,32 @@ struct PcgScalars {
 constexpr int kVecGrid = kSMs * 2;   // fixed grid of the vector kernels (deterministic partials)
 
 // Restriction r_c[S] = s_S * sum_{i in S} r1[i] over the member list (members of
-// S ascending). Large clusters are cut into items of <= kRestrictItem members;
-// item sums are combined per cluster, in order, inside coarse_matvec.
-constexpr int kRestrictItem = 4096;
+// S ascending). Clusters are cut into items of <= item_size members (one warp
+// each: kRestrictItem = 256 members, two rounds of four loads per lane, for the
+// single-system path; kRestrictItemBatch for the batched path, a block per
+// item over a slab of systems); a second kernel sums each cluster's item sums
+// (one warp per cluster, lanes strided over the items, a fixed shuffle tree)
+// and scales them by s_S into rc.
+constexpr int kRestrictItem = 256;
+constexpr int kRestrictItemBatch = 4096;
 struct RestrictItem {
   int32_t begin, end;   // range in the member list
 };
 struct RestrictPlan {
+  int32_t k = 0;
   int32_t n_items = 0;
   int32_t *item_ptr = nullptr;    // [k+1] items of each cluster
   RestrictItem *items = nullptr;  // [n_items]
   double *item_sum = nullptr;     // [n_items]
+  double *rc = nullptr;           // [k] the restricted vector
 };
 rr_status restrict_plan(int32_t k, const int64_t *cl_ptr, RestrictPlan &plan, int64_t *scratch,
-                        cudaStream_t st);
+                        cudaStream_t st, int32_t item_size = kRestrictItem);
 void restrict_free(RestrictPlan &plan);
+// plan.rc = P^T r1 (scaled by s)
 rr_status restrict_clusters(const RestrictPlan &plan, const int32_t *members, const double *r1,
-                            const int32_t *stop, cudaStream_t st);
-// r_c from the item sums (also written to rc when non-null), then e_c = Ainv r_c.
+                            const double *s, const int32_t *stop, cudaStream_t st);
+// e_c = Ainv r_c from plan.rc (also written to rc when non-null).
 // FP32 form for the FP32 inner iterations: Ainv32 = FP32 copy of Ainv with
 // rows padded to a multiple of 4 (coarse_to_f32), FP32 products and sums.
 rr_status coarse_to_f32(int32_t k, const double *Ainv, float *Ainv32, cudaStream_t st);

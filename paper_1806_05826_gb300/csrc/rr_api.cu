@@ -279,6 +279,7 @@ rr_status setup_impl_dense(rr_handle *h, const rr_matrix *X, double lambda, int3
   RR_TRY(m.alloc(&h->s, k_eff));
   RR_TRY(rr::prolong_scale(k_eff, h->n_S, h->s, st));
   RR_TRY(rr::restrict_plan(k_eff, h->cl_ptr, h->rplan, scratch64, st));
+  RR_TRY(rr::restrict_plan(k_eff, h->cl_ptr, h->bplan, scratch64, st, rr::kRestrictItemBatch));
   RR_TRY(phase(4));
   // ---- coarse Gram G = (X onehot)^T (X onehot) (FP64), smoother statistics
   double *C = nullptr, *rowabs = nullptr;
@@ -478,6 +479,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&h->s, k_eff));
   RR_TRY(rr::prolong_scale(k_eff, h->n_S, h->s, st));
   RR_TRY(rr::restrict_plan(k_eff, h->cl_ptr, h->rplan, scratch64, st));
+  RR_TRY(rr::restrict_plan(k_eff, h->cl_ptr, h->bplan, scratch64, st, rr::kRestrictItemBatch));
 
   RR_TRY(phase(4));
   // ---- exact coarse Gram G = C^T C (C = X * onehot(labels), integer counts)
@@ -611,7 +613,7 @@ rr_status apply_precond(rr_handle *h, const double *r, double *z, const int32_t 
       if (!z1_ready) RR_TRY(rr::jacobi(F, h->omega, r, h->d, h->z1, nullptr, stop, st));
       rr::CscEpilogue pre{rr::CSC_PRE, h->lambda, h->omega, h->z1, r, h->d, h->r1, nullptr, stop};
       RR_TRY(op_apply(h, h->z1, pre, stop, st, fp32, x32 != nullptr && z1_ready));
-      RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->r1, stop, st));
+      RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->r1, h->s, stop, st));
       RR_TRY(coarse_step(h, stop, st, fp32));
       RR_TRY(rr::prolong_add(F, h->labels, h->s, h->ec, h->z1, h->z2, stop, st, x32));
       rr::CscEpilogue post{rr::CSC_POST, h->lambda, h->omega, h->z2, r, h->d, z, h->part_rz, stop};
@@ -860,7 +862,7 @@ rr_status tlfcg_iteration(rr_handle *h, cudaStream_t st) {
                           h->tr, 1.0, nullptr, nullptr, h->t_rr, h->St, st));
     RR_TRY(rr::pcg_finish(h->t_rz, rr::kVecGrid, h->t_rr, rr::kVecGrid, h->St, nullptr, 0, st));
   }
-  RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->tr, stop, st));
+  RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->tr, h->s, stop, st));
   RR_TRY(coarse_step(h, stop, st, fp32));
   RR_TRY(rr::prolong_add(F, h->labels, h->s, h->ec, h->tz, h->z, stop, st));
   RR_TRY(rr::fcg_dot(F, h->z, h->q_prev, h->part_zq, stop, st));
@@ -881,7 +883,7 @@ rr_status fcg_iteration(rr_handle *h, const rr_mlp *net, cudaStream_t st) {
   // pre-smoothing (z1 from the previous update), restriction
   rr::CscEpilogue pre{rr::CSC_PRE, h->lambda, h->omega, h->z1, h->r, h->d, h->r1, nullptr, stop};
   RR_TRY(op_apply(h, h->z1, pre, stop, st, fp32));
-  RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->r1, stop, st));
+  RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->r1, h->s, stop, st));
   if (net) {
     RR_TRY(rr::mlp_coarse(net, h->rplan, h->s, h->ec, stop, st));
   } else {
@@ -1679,6 +1681,7 @@ void rr_free(rr_handle *h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->limit_host) cudaFreeHost(h->limit_host);
   rr::restrict_free(h->rplan);
+  rr::restrict_free(h->bplan);
   rr::sliced_free(h->pcsr);
   rr::sliced_free(h->pcsc);
   rr::split_free(h->split);
