@@ -647,6 +647,13 @@ def measure_learned(rr, X, row_ptr, col_idx, k, opts, dev, stream, n_pairs=100_0
     e1.record(stream)
     torch.cuda.synchronize(dev)
     t_train = e0.elapsed_time(e1) / 1e3
+    # the same pairs and steps with the loss weighted by A_c (scaled by its
+    # largest diagonal entry): the error of a coarse correction in the energy
+    # norm of the coarse space
+    Ac, _ = rr.rr_get_coarse(h)
+    net_w = rr.mlp_create(k_eff, hidden, params, max_batch=512, stream=stream)
+    rr.mlp_set_metric(net_w, Ac / np.abs(np.diag(Ac)).max())
+    losses_w = rr.mlp_train(net_w, Xp, Tp, batch=512, steps=steps, lr=1e-3, seed=3)
     w = torch.empty(F, dtype=torch.float64, device=dev)
     rows = []
     for s in eval_seeds:
@@ -654,12 +661,14 @@ def measure_learned(rr, X, row_ptr, col_idx, k, opts, dev, stream, n_pairs=100_0
         a = rr.rr_solve_fcg(h, net, yd, w, tol=TOL)
         b = rr.rr_solve(h, yd, w, tol=TOL)
         c = rr.rr_solve_fcg(h, None, yd, w, tol=TOL)
-        for inf in (a, b, c):
+        d = rr.rr_solve_fcg(h, net_w, yd, w, tol=TOL)
+        for inf in (a, b, c, d):
             assert inf["status"] == "RR_OK" and inf["true_rel_res"] <= TOL
         rows.append((a["solve_ms"], a["iters"], a["fallbacks"], b["solve_ms"], b["iters"],
-                     c["solve_ms"], c["iters"]))
+                     c["solve_ms"], c["iters"], d["solve_ms"], d["iters"], d["fallbacks"]))
     r = np.array(rows, dtype=np.float64)
     net.close()
+    net_w.close()
     rr.rr_free(h)
     return {"workload": "zipf_200000x100000 lambda=1e-3", "pairs": int(Xp.shape[0]),
             "net": f"{k_eff}-{hidden}-{hidden}-{k_eff} BF16 (tcgen05 training)",
@@ -674,7 +683,16 @@ def measure_learned(rr, X, row_ptr, col_idx, k, opts, dev, stream, n_pairs=100_0
             "plain_pcg_iters_mean": round(r[:, 4].mean(), 1),
             "cholesky_fcg_s_mean": round(r[:, 5].mean() / 1e3, 4),
             "cholesky_fcg_iters_mean": round(r[:, 6].mean(), 1),
-            "speedup_vs_plain": round(r[:, 3].mean() / r[:, 0].mean(), 3)}
+            "speedup_vs_plain": round(r[:, 3].mean() / r[:, 0].mean(), 3),
+            "ac_weighted_loss": {
+                "loss": "0.5/B sum (o - t)^T (A_c / max diag A_c) (o - t)",
+                "loss_first_last": [float(losses_w[:20].mean()), float(losses_w[-20:].mean())],
+                "learned_fcg_s_mean": round(r[:, 7].mean() / 1e3, 4),
+                "learned_fcg_iters_mean": round(r[:, 8].mean(), 1),
+                "learned_fallbacks_mean": round(r[:, 9].mean(), 1),
+                "fallback_rate": round(r[:, 9].sum() / max(1.0, r[:, 8].sum()), 3),
+                "speedup_vs_plain": round(r[:, 3].mean() / r[:, 7].mean(), 3)},
+            "fallback_rate": round(r[:, 2].sum() / max(1.0, r[:, 1].sum()), 3)}
 
 
 def run_ours(args, rank, world, local):

@@ -305,6 +305,14 @@ rr_status rr_mlp_create(int32_t k, int32_t hidden, int32_t max_batch, const floa
                         void *stream, rr_mlp **out);
 rr_status rr_mlp_set_params(rr_mlp *m, const float *params_host);
 rr_status rr_mlp_get_params(const rr_mlp *m, float *params_host);
+/* The loss metric (no counterpart in the paper): with W_host (host float[k x k]
+ * row-major, symmetric, e.g. the coarse operator A_c scaled), rr_mlp_grad and
+ * rr_mlp_train minimise 0.5/B sum_b (o_b - t_b)^T W (o_b - t_b), whose output
+ * gradient W (o - t) / B is one more tensor-core product per batch (W in
+ * BF16); NULL restores the plain loss. Errors: RR_INVALID_ARG (NULL network,
+ * a non-finite entry, W not symmetric to 1e-6 of its largest entry),
+ * RR_OOM, RR_CUDA_ERROR. */
+rr_status rr_mlp_set_metric(rr_mlp *m, const float *W_host);
 /* out (device float[B x k]) = o for the rows of X (device float[B x k]), as given. */
 rr_status rr_mlp_forward(rr_mlp *m, int32_t B, const float *X, float *out);
 /* Loss and its gradient for the rows of X with targets T (device float[B x k]),

@@ -7,6 +7,12 @@ correction: h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), o = W3 h2 + b3, with
 the squared-error loss 0.5/B sum ||o - t||^2 over a batch of B rows, its
 gradients by the chain rule, and one Adam step (Kingma & Ba, ICLR 2015).
 Row-major batches: X is (B, k), W1 is (H, k), W2 is (H, H), W3 is (k, H).
+
+A metric W (symmetric positive definite k x k, e.g. the coarse operator A_c)
+weights the loss: 0.5/B sum (o - t)^T W (o - t); the output gradient is then
+W (o - t) / B per row. With W = A_c the error of a coarse correction is
+measured in the energy norm of the coarse space, the norm in which the
+Galerkin coarse solve is optimal.
 """
 from __future__ import annotations
 
@@ -33,16 +39,21 @@ def forward(p, X):
     return o, (X, a1, h1, a2, h2)
 
 
-def loss(p, X, T):
+def loss(p, X, T, W=None):
     o, _ = forward(p, X)
-    return 0.5 * np.sum((o - T) ** 2) / X.shape[0]
+    D = o - T
+    if W is None:
+        return 0.5 * np.sum(D ** 2) / X.shape[0]
+    return 0.5 * np.sum((D @ W) * D) / X.shape[0]
 
 
-def backward(p, X, T):
+def backward(p, X, T, W=None):
     """Gradients of loss() with respect to every parameter."""
     o, (X, a1, h1, a2, h2) = forward(p, X)
     B = X.shape[0]
     do = (o - T) / B
+    if W is not None:
+        do = do @ W
     g = {"W3": do.T @ h2, "b3": do.sum(0)}
     dh2 = do @ p["W3"]
     da2 = dh2 * (a2 > 0.0)

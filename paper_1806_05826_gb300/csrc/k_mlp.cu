@@ -47,6 +47,11 @@ struct rr_mlp {
   int64_t *bidx = nullptr;
   float *xin = nullptr, *g1 = nullptr, *g2 = nullptr;
   double *nrm = nullptr;
+  // the loss metric W (rr_mlp_set_metric): BF16 [kp x kp] zero padded, and
+  // the FP32 output differences of a batch [Bp x kp]; null: the plain loss
+  __nv_bfloat16 *Wm = nullptr;
+  float *dm = nullptr;
+  bool metric = false;
   int32_t *err = nullptr;
   cudaStream_t st = nullptr;
   DevArena mem;
@@ -295,6 +300,47 @@ __global__ void k_mlp_dout(int32_t B, int32_t Bp, int32_t k, int32_t kp, float *
   }
 }
 
+// With a metric W, pass 1: d = o - t for the B real rows (zero elsewhere) in
+// FP32 (dm) and BF16 (dob), the left operand of d W^T = d W (W symmetric).
+__global__ void k_mlp_diff(int32_t B, int32_t k, int32_t kp, const float *__restrict__ o,
+                           const float *__restrict__ Tn, float *__restrict__ dm,
+                           __nv_bfloat16 *__restrict__ dob) {
+  const int b = blockIdx.x;
+  for (int i = threadIdx.x; i < kp; i += blockDim.x) {
+    const int64_t e = (int64_t)b * kp + i;
+    const float d = (b < B && i < k) ? o[e] - Tn[e] : 0.0f;
+    dm[e] = d;
+    dob[e] = __float2bfloat16(d);
+  }
+}
+
+// Pass 2, after g = d W (FP32, in o): do = g / B in place and its BF16
+// copies; per-row d^T W d = sum_i d_i g_i.
+__global__ void k_mlp_dout_w(int32_t B, int32_t Bp, int32_t kp, float *__restrict__ o,
+                             const float *__restrict__ dm, __nv_bfloat16 *__restrict__ dob,
+                             __nv_bfloat16 *__restrict__ doT, float *__restrict__ rowloss) {
+  __shared__ float red[32];
+  const int b = blockIdx.x;
+  float acc = 0.0f;
+  for (int i = threadIdx.x; i < kp; i += blockDim.x) {
+    const int64_t e = (int64_t)b * kp + i;
+    const float g = b < B ? o[e] : 0.0f;
+    acc += dm[e] * g;
+    const float d = g / (float)B;
+    o[e] = d;
+    dob[e] = __float2bfloat16(d);
+    doT[(int64_t)i * Bp + b] = __float2bfloat16(d);
+  }
+  for (int w = 16; w > 0; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    rowloss[b] = t;
+  }
+}
+
 // da = dh * (a > 0) in place; optional BF16 copy and BF16 transposed copy.
 __global__ void k_mlp_relu_back(int32_t Bp, int32_t H, float *__restrict__ dh,
                                 const float *__restrict__ a, __nv_bfloat16 *__restrict__ dab,
@@ -519,8 +565,15 @@ rr_status forward(rr_mlp *m, int32_t Bp) {
 rr_status backward(rr_mlp *m, int32_t B, int32_t Bp) {
   cudaStream_t st = m->st;
   const int32_t H = m->H, kp = m->kp;
-  RR_LAUNCH(k_mlp_dout, Bp, kThreads, 0, st, B, Bp, m->k, kp, m->o, m->Tn, m->dob, m->doT,
-            m->rowloss);
+  if (m->metric) {
+    RR_LAUNCH(k_mlp_diff, Bp, kThreads, 0, st, B, m->k, kp, m->o, m->Tn, m->dm, m->dob);
+    RR_TRY(gemm_nt(Bp, kp, kp, m->dob, m->Wm, GemmEpi{nullptr, m->o, nullptr, 0, kp}, m->err, st));
+    RR_LAUNCH(k_mlp_dout_w, Bp, kThreads, 0, st, B, Bp, kp, m->o, m->dm, m->dob, m->doT,
+              m->rowloss);
+  } else {
+    RR_LAUNCH(k_mlp_dout, Bp, kThreads, 0, st, B, Bp, m->k, kp, m->o, m->Tn, m->dob, m->doT,
+              m->rowloss);
+  }
   const dim3 tb(32, 8);
   RR_LAUNCH(k_transpose_bf16, dim3((unsigned)(H / 32), (unsigned)(Bp / 32)), tb, 0, st, Bp, H,
             m->h2b, m->h2T);
@@ -685,6 +738,46 @@ rr_status rr_mlp_create(int32_t k, int32_t hidden, int32_t max_batch, const floa
   }
   if ((s = rr_mlp_set_params(m, params_host)) != RR_OK) return fail(s);
   *out = m;
+  return RR_OK;
+}
+
+rr_status rr_mlp_set_metric(rr_mlp *m, const float *W_host) {
+  if (!m) {
+    rr_set_error("rr_mlp_set_metric: NULL network");
+    return RR_INVALID_ARG;
+  }
+  if (!W_host) {
+    m->metric = false;
+    return RR_OK;
+  }
+  const int32_t k = m->k, kp = m->kp;
+  float wmax = 0.0f, asym = 0.0f;
+  for (int64_t e = 0; e < (int64_t)k * k; ++e) {
+    if (!isfinite(W_host[e])) {
+      rr_set_error("rr_mlp_set_metric: non-finite entry");
+      return RR_INVALID_ARG;
+    }
+    wmax = fmaxf(wmax, fabsf(W_host[e]));
+  }
+  for (int32_t i = 0; i < k; ++i)
+    for (int32_t j = 0; j < i; ++j)
+      asym = fmaxf(asym, fabsf(W_host[(int64_t)i * k + j] - W_host[(int64_t)j * k + i]));
+  if (asym > 1e-6f * wmax) {
+    rr_set_error("rr_mlp_set_metric: W must be symmetric");
+    return RR_INVALID_ARG;
+  }
+  if (!m->Wm) {
+    RR_TRY(m->mem.alloc(&m->Wm, (int64_t)kp * kp));
+    RR_TRY(m->mem.alloc(&m->dm, (int64_t)m->Bp_max * kp));
+  }
+  std::vector<__nv_bfloat16> pad((size_t)kp * kp, __float2bfloat16(0.0f));
+  for (int32_t i = 0; i < k; ++i)
+    for (int32_t j = 0; j < k; ++j)
+      pad[(size_t)i * kp + j] = __float2bfloat16(W_host[(int64_t)i * k + j]);
+  RR_CUDA(cudaMemcpyAsync(m->Wm, pad.data(), sizeof(__nv_bfloat16) * pad.size(),
+                          cudaMemcpyHostToDevice, m->st));
+  RR_CUDA(cudaStreamSynchronize(m->st));
+  m->metric = true;
   return RR_OK;
 }
 

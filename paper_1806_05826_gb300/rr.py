@@ -96,6 +96,7 @@ _SIGS = {
     "rr_mlp_create": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P, _P,
                                      ctypes.POINTER(_P)]),
     "rr_mlp_set_params": (ctypes.c_int, [_P, _P]),
+    "rr_mlp_set_metric": (ctypes.c_int, [_P, _P]),
     "rr_mlp_get_params": (ctypes.c_int, [_P, _P]),
     "rr_mlp_forward": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P]),
     "rr_mlp_grad": (ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P, _P]),
@@ -424,6 +425,17 @@ def mlp_get_params(m: Mlp) -> dict:
 def mlp_set_params(m: Mlp, params: dict):
     flat = np.ascontiguousarray(mlp_pack(params))
     _check(load().rr_mlp_set_params(m.ptr, flat.ctypes.data))
+
+
+def mlp_set_metric(m: Mlp, W=None):
+    """Loss metric W (symmetric k x k, host array) or None for the plain loss."""
+    if W is None:
+        _check(load().rr_mlp_set_metric(m.ptr, None))
+        return
+    Wf = np.ascontiguousarray(W, dtype=np.float32)
+    if Wf.shape != (m.k, m.k):
+        raise ValueError(f"W: shape ({m.k}, {m.k}) required, got {Wf.shape}")
+    _check(load().rr_mlp_set_metric(m.ptr, Wf.ctypes.data))
 
 
 def mlp_forward(m: Mlp, X):

@@ -97,6 +97,43 @@ def test_mlp_gradients_match_oracle(rr, k, H, B):
         assert relerr(a, b) <= 2e-2, (name, relerr(a, b))
 
 
+@pytest.mark.parametrize("k,H,B", [(50, 128, 40), (300, 256, 200)])
+def test_mlp_metric_gradients_match_oracle(rr, k, H, B):
+    """The loss weighted by a metric W (rr_mlp_set_metric): against the oracle
+    on the BF16 grid with W rounded to BF16 as the kernels round it; the
+    output differences are rounded to BF16 too before the product with W, so
+    the bars are those of the plain loss. Clearing the metric restores the
+    plain gradients bit for bit."""
+    p = init(k, H, 13)
+    X = synth.normal(14, 31, B * k).reshape(B, k)
+    T = synth.normal(15, 32, B * k).reshape(B, k)
+    C = synth.normal(16, 33, k * k).reshape(k, k) / np.sqrt(k)
+    W = C.T @ C + 0.5 * np.eye(k)
+    W = 0.5 * (W + W.T)
+    net = rr.mlp_create(k, H, p, max_batch=B)
+    loss0, g0 = rr.mlp_grad(net, dev(X, torch.float32), dev(T, torch.float32))
+    rr.mlp_set_metric(net, W)
+    loss, g = rr.mlp_grad(net, dev(X, torch.float32), dev(T, torch.float32))
+    pq, Xq, Wq = on_bf16_grid(p), bf16(X), bf16(W.astype(np.float32))
+    want = mlp.backward(pq, Xq, T, Wq)
+    want_loss = mlp.loss(pq, Xq, T, Wq)
+    assert abs(loss - want_loss) <= 1e-2 * want_loss
+    for name in rr.MLP_KEYS:
+        a, b = g[name].astype(np.float64).ravel(), want[name].ravel()
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+        assert cos >= 0.999, (name, cos)
+        assert relerr(a, b) <= 2e-2, (name, relerr(a, b))
+    rr.mlp_set_metric(net, None)
+    loss1, g1 = rr.mlp_grad(net, dev(X, torch.float32), dev(T, torch.float32))
+    assert loss1 == loss0
+    for name in rr.MLP_KEYS:
+        assert np.array_equal(g1[name], g0[name])
+    bad = W.copy()
+    bad[0, 1] += 1.0
+    with pytest.raises(rr.RRError):
+        rr.mlp_set_metric(net, bad)
+
+
 def test_params_round_trip(rr):
     k, H = 37, 128
     p = init(k, H, 6)

@@ -566,6 +566,47 @@ def test_mlp_gradients_finite_differences():
             assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd))
 
 
+def _metric_case():
+    rng = np.random.default_rng(12)
+    p = mlp.init_params(6, 5, lambda n: rng.random(n))
+    for name in ("b1", "b2", "b3"):
+        p[name] = 0.1 * rng.standard_normal(p[name].shape)
+    X = rng.standard_normal((4, 6))
+    T = rng.standard_normal((4, 6))
+    C = rng.standard_normal((6, 6))
+    return p, X, T, C
+
+
+def test_mlp_metric_loss_is_plain_loss_of_transformed_output():
+    """With W = C^T C the weighted loss 0.5/B sum (o - t)^T W (o - t) is the
+    plain loss of the network whose output layer is multiplied by C, against
+    the targets C t (an invariant: ||C d||^2 = d^T C^T C d)."""
+    p, X, T, C = _metric_case()
+    q = dict(p, W3=C @ p["W3"], b3=C @ p["b3"])
+    assert np.isclose(mlp.loss(p, X, T, C.T @ C), mlp.loss(q, X, T @ C.T), rtol=1e-12)
+    assert mlp.loss(p, X, T, np.eye(6)) == pytest.approx(mlp.loss(p, X, T), rel=1e-14)
+
+
+def test_mlp_metric_gradients_finite_differences():
+    """The weighted loss's gradients against central finite differences."""
+    p, X, T, C = _metric_case()
+    W = C.T @ C + np.eye(6)
+    g = mlp.backward(p, X, T, W)
+    h = 1e-6
+    for name in p:
+        flat = p[name].reshape(-1)
+        for idx in range(0, flat.size, max(1, flat.size // 7)):
+            old = flat[idx]
+            flat[idx] = old + h
+            lp = mlp.loss(p, X, T, W)
+            flat[idx] = old - h
+            lm = mlp.loss(p, X, T, W)
+            flat[idx] = old
+            fd = (lp - lm) / (2 * h)
+            an = g[name].reshape(-1)[idx]
+            assert abs(fd - an) <= 1e-6 * max(1.0, abs(fd))
+
+
 def test_adam_first_step_is_lr_times_sign():
     p = {"W": np.array([1.0, -2.0, 3.0])}
     g = {"W": np.array([0.5, -7.0, 1e-3])}

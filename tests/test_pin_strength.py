@@ -332,6 +332,23 @@ def _tau_shape_without_half_n(mp):
     _bayes_patched(mp, "gibbs", "p.a_tau + 0.5 * N", "p.a_tau + N")
 
 
+def _metric_gradient_ignored(mp):
+    _orig = mlp.backward
+    mp.setattr(mlp, "backward", lambda p, X, T, W=None: _orig(p, X, T))
+
+
+def _metric_loss_transposed_side(mp):
+    _orig = mlp.loss
+
+    def bad(p, X, T, W=None):
+        if W is None:
+            return _orig(p, X, T)
+        o, _ = mlp.forward(p, X)
+        D = o - T
+        return 0.5 * np.sum(D @ W) / X.shape[0]   # sums W's rows instead of the quadratic form
+    mp.setattr(mlp, "loss", bad)
+
+
 P = pins
 CASES = [
     ("gamma draw multiplied by the rate", _gamma_times_rate, [P.test_gamma_draw_distribution]),
@@ -399,6 +416,10 @@ CASES = [
      [P.test_kmeanspp_picks_other_group, P.test_kmeanspp_draw_follows_d2_weights]),
     ("compaction reverses the cluster order", _compact_reversed,
      [P.test_compact_drops_empty_clusters_in_order]),
+    ("metric ignored in the gradient", _metric_gradient_ignored,
+     [P.test_mlp_metric_gradients_finite_differences]),
+    ("metric loss without the quadratic form", _metric_loss_transposed_side,
+     [P.test_mlp_metric_loss_is_plain_loss_of_transformed_output]),
     ("a bias gradient with the wrong sign", _mlp_gradient_sign,
      [P.test_mlp_gradients_finite_differences]),
     ("Adam without bias correction", _adam_without_bias_correction,
