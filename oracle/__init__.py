@@ -12,7 +12,8 @@ Ridge Regression" (arXiv 1806.05826):
   coarse      Section 3.2: Galerkin P^T (X^T X + beta I) P = X_c^T X_c + beta I.
   cycle       Section 3.1: T = (I - w A)(I - P A_c^{-1} P^T A)(I - w A),
               with the Richardson smoother generalised to damped Jacobi.
-  clustering  Section 3.4: k-means++ on the features, Euclidean distance.
+  clustering  Section 3.4: k-means++ on the features, Euclidean distance; or
+              leader-follower clustering (Algorithm 1, leader.py).
   coarse solve Section 4: Cholesky factorisation of the coarse operator; or the
               eigendecomposition of X_c^T X_c, reused for every lambda
               (eigen.py, cyclic Jacobi).
@@ -27,4 +28,4 @@ Parity unpinned: iteration counts and speed-ups against the paper's tables
 (its datasets are not available), and k-means labels beyond "same initial
 centres give the same labels" (Lloyd's optimum is not unique).
 """
-from . import sparse, kmeans, twolevel, krylov, mlp, learned, eigen, bayes  # noqa: F401
+from . import sparse, kmeans, twolevel, krylov, mlp, learned, eigen, bayes, leader  # noqa: F401

@@ -917,3 +917,77 @@ def test_gibbs_with_fixed_tau():
     lams, taus, _, _ = bayes.gibbs(two, y, p, n_samples=4)
     assert np.all(taus == 3.0)
     assert len(set(lams.tolist())) == 4
+
+
+# ---------------------------------------------------------------- leader-follower clustering
+
+def _lf_hand_example():
+    # 4 rows, 5 features: f0 = {0, 1}, f1 = {0, 1}, f2 = {2}, f3 = {0, 1, 2}, f4 = {3}
+    X = np.zeros((4, 5), dtype=np.int64)
+    for j, rows in enumerate(([0, 1], [0, 1], [2], [0, 1, 2], [3])):
+        X[rows, j] = 1
+    return X
+
+
+@pytest.mark.parametrize("tol2,leaders,labels", [
+    # f0 leads; d2(f1, f0) = 0; d2(f2, f0) = 3; d2(f3, f0) = 1, d2(f3, f2) = 2;
+    # d2(f4, f0) = 3, d2(f4, f2) = 2
+    (1.5, [0, 2, 4], [0, 0, 1, 0, 2]),
+    (2.0, [0, 2, 4], [0, 0, 1, 0, 2]),     # d2 = 2 is not below 2: f4 leads
+    (2.5, [0, 2], [0, 0, 1, 0, 1]),
+    (3.5, [0], [0, 0, 0, 0, 0]),
+    (0.0, [0, 1, 2, 3, 4], [0, 1, 2, 3, 4]),  # nothing is below 0: every feature leads
+])
+def test_leader_follower_worked_example(tol2, leaders, labels):
+    """Algorithm 1 worked by hand on five binary features (squared Euclidean
+    distances in the comments), including the strict comparison at d^2 = tol2."""
+    from oracle import leader
+    n, f, rp, ci = csr_of(_lf_hand_example())
+    L, lab = leader.leader_follower_binary(n, f, rp, ci, tol2)
+    assert L.tolist() == leaders and lab.tolist() == labels
+
+
+def test_leader_follower_characterisation():
+    """The output of Algorithm 1 is fixed by two properties, checked against a
+    brute-force distance matrix (n_i + n_j - 2 X^T X): a leader is at distance
+    >= tol from every earlier leader; a follower's nearest earlier leader (the
+    earliest on ties) is below tol and is its label."""
+    from oracle import leader
+    for seed, (n, f, p) in enumerate(((40, 30, 0.2), (60, 80, 0.05), (25, 50, 0.4))):
+        X = random_binary(n, f, p, 100 + seed)
+        D2 = X.sum(0)[:, None] + X.sum(0)[None, :] - 2 * (X.T @ X)
+        nr, nc, rp, ci = csr_of(X)
+        for tol2 in (1.0, 3.0, 6.5, 12.0):
+            L, lab = leader.leader_follower_binary(nr, nc, rp, ci, tol2)
+            Ls = list(L)
+            assert Ls == sorted(Ls) and Ls[0] == 0
+            for i in range(f):
+                earlier = [s for s, c in enumerate(Ls) if c < i]
+                if i in Ls:
+                    assert lab[i] == Ls.index(i)
+                    assert all(D2[i, Ls[s]] >= tol2 for s in earlier)
+                else:
+                    d = [D2[i, Ls[s]] for s in earlier]
+                    best = int(np.argmin(d))
+                    assert d[best] < tol2 and lab[i] == earlier[best]
+
+
+def test_leader_follower_recovers_duplicated_features():
+    """Definition 1's duplicated features: with tol2 = 0.5 identical columns
+    (d^2 = 0) follow the first of their group and distinct columns (d^2 >= 1)
+    never join, so the clusters are the groups, led by their first members."""
+    from oracle import leader
+    rng = np.random.default_rng(5)
+    while True:
+        base = (rng.random((30, 6)) < 0.5).astype(np.int64)
+        if len({tuple(c) for c in base.T}) == 6 and base.sum(0).min() > 0:
+            break
+    X, groups = synth.duplicated_features(base, [3, 1, 4, 2, 2, 5])
+    n, f, rp, ci = csr_of(X)
+    L, lab = leader.leader_follower_binary(n, f, rp, ci, 0.5)
+    first = {}
+    for j, g in enumerate(groups):
+        first.setdefault(int(g), j)
+    assert sorted(L.tolist()) == sorted(first.values())
+    for j, g in enumerate(groups):
+        assert L[lab[j]] == first[int(g)]

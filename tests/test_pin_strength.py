@@ -349,8 +349,37 @@ def _metric_loss_transposed_side(mp):
     mp.setattr(mlp, "loss", bad)
 
 
+def _leader_patched(mp, good, bad):
+    import inspect
+    import textwrap
+    from oracle import leader
+    src = textwrap.dedent(inspect.getsource(leader.leader_follower_binary))
+    assert good in src
+    ns = dict(vars(leader))
+    exec(src.replace(good, bad), ns)
+    mp.setattr(leader, "leader_follower_binary", ns["leader_follower_binary"])
+
+
+def _leader_non_strict(mp):
+    _leader_patched(mp, "if float(d2[s]) < tol2:", "if float(d2[s]) <= tol2:")
+
+
+def _leader_last_minimum(mp):
+    _leader_patched(mp, "s = int(np.argmin(d2))", "s = int(len(d2) - 1 - np.argmin(d2[::-1]))")
+
+
+def _leader_without_overlap(mp):
+    _leader_patched(mp, "d2 = n_i + n_lead[:L] - 2 * overlap", "d2 = n_i + n_lead[:L] - overlap")
+
+
 P = pins
 CASES = [
+    ("leader-follower joins at d^2 = tol^2", _leader_non_strict,
+     [lambda: P.test_leader_follower_worked_example(2.0, [0, 2, 4], [0, 0, 1, 0, 2])]),
+    ("leader-follower takes the last of tied leaders", _leader_last_minimum,
+     [P.test_leader_follower_characterisation]),
+    ("leader-follower distance with a single overlap term", _leader_without_overlap,
+     [P.test_leader_follower_characterisation, P.test_leader_follower_recovers_duplicated_features]),
     ("gamma draw multiplied by the rate", _gamma_times_rate, [P.test_gamma_draw_distribution]),
     ("gamma draw with (1 + c x)^2", _gamma_without_cube, [P.test_gamma_draw_distribution]),
     ("noise e2 multiplied by tau", _noise_e2_times_tau,
