@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "s to rel. residual 1e-8: batched/learned vs plain two-level PCG, same GB300"
 WORKLOAD = "zipf_200000x100000"
 TOL = 1e-8
+LEADER_TOL2 = (100.0,)   # the leader-follower section's squared tolerance(s)
 
 
 def parse():
@@ -52,6 +53,10 @@ def parse():
                     help="skip the Gibbs-sampling (rr_bayes) section")
     ap.add_argument("--only-bayes", action="store_true",
                     help="only the Gibbs-sampling section")
+    ap.add_argument("--only-leader", action="store_true",
+                    help="only the leader-follower section (--leader-tol2 list)")
+    ap.add_argument("--leader-tol2", default="",
+                    help="comma-separated squared tolerances of the leader-follower section")
     ap.add_argument("--only-eigen", action="store_true",
                     help="run the eigendecomposition section alone (profiling runs)")
     ap.add_argument("--no-small", action="store_true",
@@ -484,6 +489,51 @@ def measure_bayes(rr, row_ptr, col_idx, N, F, k, lam, opts, dev, y_dev, n_sample
     return out
 
 
+def measure_leader(rr, row_ptr, col_idx, N, F, lams, opts, dev, y_dev, tol2s, cap=16384,
+                   tlfcg=True):
+    """Leader-follower clustering (Algorithm 1, RR_CLUSTER_LEADER) in place of
+    k-means++ on the step's matrix: for each squared tolerance, the number of
+    leaders (the coarse size F_C), the clustering's time, the setup, and the
+    two-level PCG (and, with tlfcg, the paper's TLFCG) at each lambda of the
+    step, against the k-means++ numbers of the timed step."""
+    import torch
+    out = {"tol2": [], "cap": cap}
+    w = torch.empty(F, dtype=torch.float64, device=dev)
+    for tol2 in tol2s:
+        row = {"tol2": tol2}
+        try:
+            h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], cap,
+                            **dict(opts, clustering=rr.RR_CLUSTER_LEADER, lf_tol2=tol2))
+        except rr.RRError as e:
+            row["error"] = str(e)[:120]
+            out["tol2"].append(row)
+            continue
+        row["k_eff"] = rr.rr_query(h)["k_eff"]
+        row["pcg_iters"], row["pcg_solve_ms"] = [], []
+        info = None
+        for j, lam in enumerate(lams):
+            if j:
+                rr.rr_set_lambda(h, lam)
+            info = rr.rr_solve(h, y_dev, w, tol=TOL)
+            assert info["status"] == "RR_OK" and info["true_rel_res"] <= TOL
+            row["pcg_iters"].append(info["iters"])
+            row["pcg_solve_ms"].append(round(info["solve_ms"], 2))
+        row["setup_ms"] = round(info["setup_ms"], 2)
+        row["cluster_ms"] = round(info["setup_phase_ms"][2] + info["setup_phase_ms"][3], 2)
+        rr.rr_free(h)
+        if tlfcg:
+            h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], cap,
+                            **dict(opts, clustering=rr.RR_CLUSTER_LEADER, lf_tol2=tol2,
+                                   solver=rr.RR_SOLVER_TLFCG))
+            inf = rr.rr_solve(h, y_dev, w, tol=TOL)
+            assert inf["status"] == "RR_OK" and inf["true_rel_res"] <= TOL
+            row["tlfcg_iters_lam0"] = inf["iters"]
+            row["tlfcg_solve_ms_lam0"] = round(inf["solve_ms"], 2)
+            rr.rr_free(h)
+        out["tol2"].append(row)
+    return out
+
+
 def measure_tlfcg(rr, row_ptr, col_idx, N, F, k, lams, opts, y_dev, last_infos):
     """The same systems (each lambda, same target, same clustering) solved by the
     paper's TLFCG: flexible CG whose preconditioner is two CG rougher steps and the
@@ -748,6 +798,10 @@ def run_ours(args, rank, world, local):
     if args.only_eigen:
         return {"coarse_eigen": measure_eigen(rr, row_ptr, col_idx, N, F, k, lams, opts, dev,
                                               stream, y_dev)}
+    if args.only_leader:
+        tol2s = [float(t) for t in args.leader_tol2.split(",") if t] or LEADER_TOL2
+        return {"leader": measure_leader(rr, row_ptr, col_idx, N, F, lams, opts, dev, y_dev,
+                                         tol2s)}
     if args.only_bayes:
         return {"bayes": measure_bayes(rr, row_ptr, col_idx, N, F, k, lams[0], opts, dev, y_dev)}
     if args.only == "batched":

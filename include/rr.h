@@ -74,10 +74,19 @@ enum { RR_GATHER_AUTO = 0,      /* rr_setup times both on each pass of X and kee
 enum { RR_COARSE_CHOLESKY = 0,  /* per lambda: Cholesky factor of A_c, its triangular inverse,
                                    A_c^-1 = L^-T L^-1 */
        RR_COARSE_EIGEN = 1 };   /* once per clustering: X_c^T X_c = Q diag(mu) Q^T (parallel
-                                   cyclic Jacobi, FP64); per lambda only the product
-                                   A_c^-1 = Q diag(1 / (mu + lambda)) Q^T, so rr_set_lambda
-                                   and the weights of rr_solve_batch cost one k x k x k product
-                                   each instead of a factorisation */
+                                   cyclic Jacobi, FP64); the coarse solve is then applied as
+                                   Q (diag(1 / (mu + lambda)) (Q^T r_c)), two mat-vecs, so
+                                   rr_set_lambda only rescales a vector (rr_solve_batch forms
+                                   Q diag(1 / (mu + lambda)) Q^T once per weight) */
+
+/* rr_options.clustering (Section 3.4) */
+enum { RR_CLUSTER_KMEANS = 0,   /* k-means++ seeding and Lloyd steps into k clusters */
+       RR_CLUSTER_LEADER = 1 }; /* leader-follower clustering (Algorithm 1), binary X only:
+                                   features in index order join the nearest leader (squared
+                                   Euclidean distance, the earliest leader on ties) when that
+                                   distance is below lf_tol2, else become leaders; leaders are not
+                                   updated; k bounds the number of leaders (RR_UNSUPPORTED if more
+                                   would be needed) */
 
 /* rr_options.precision */
 enum { RR_PREC_FP64 = 0,        /* every operator apply accumulates in FP64 */
@@ -144,6 +153,9 @@ typedef struct {
                                    of two from 32 to 1024 whose columns each hold at least N/8
                                    rows, or none); a power of two from 32 to 1024 = that many;
                                    -1 = no split form (every column as sliced index lists) */
+  int32_t clustering;           /* RR_CLUSTER_* (default RR_CLUSTER_KMEANS) */
+  double lf_tol2;               /* RR_CLUSTER_LEADER: the squared distance tolerance (a feature
+                                   follows when d^2 < lf_tol2); default 1.0 */
   void *stream;                 /* cudaStream_t for all work; NULL = legacy default stream */
 } rr_options;
 

@@ -34,7 +34,7 @@ def leader_follower_binary(n_rows, n_cols, row_ptr, col_idx, tol2, max_leaders=N
     col_ptr = np.asarray(col_ptr, np.int64)
     row_idx = np.asarray(row_idx, np.int64)
     cap = n_cols if max_leaders is None else max_leaders
-    member = np.zeros((n_rows, min(cap, n_cols)), dtype=np.int64)   # member[r, s]: r in R_leader(s)
+    member = np.zeros((n_rows, min(cap, n_cols)), dtype=np.uint8)   # member[r, s]: r in R_leader(s)
     n_lead = np.zeros(min(cap, n_cols), dtype=np.int64)
     leaders = []
     labels = np.empty(n_cols, dtype=np.int32)
@@ -43,7 +43,7 @@ def leader_follower_binary(n_rows, n_cols, row_ptr, col_idx, tol2, max_leaders=N
         n_i = len(rows)
         L = len(leaders)
         if L:
-            overlap = member[rows, :L].sum(axis=0)
+            overlap = member[rows, :L].sum(axis=0, dtype=np.int64)
             d2 = n_i + n_lead[:L] - 2 * overlap
             s = int(np.argmin(d2))            # the first minimum: the earliest leader
             if float(d2[s]) < tol2:

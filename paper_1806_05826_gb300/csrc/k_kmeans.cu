@@ -782,6 +782,13 @@ rr_status kmeans_init_labels(int64_t F, int32_t k, KmeansBuffers &b, cudaStream_
   return RR_OK;
 }
 
+rr_status feature_work(int64_t F, const int64_t *row_ptr, const int64_t *col_ptr,
+                       const int32_t *row_idx, int64_t *work, cudaStream_t st) {
+  RR_LAUNCH(k_feature_work, (unsigned)std::min<int64_t>(std::max<int64_t>(F, 1), kSMs * 64), kThreads,
+            0, st, F, row_ptr, col_ptr, row_idx, work);
+  return RR_OK;
+}
+
 rr_status kmeans_work_order(int64_t N, int64_t F, int32_t k, const int64_t *row_ptr,
                             const int64_t *col_ptr, const int32_t *row_idx, KmeansBuffers &b,
                             int64_t *work, int64_t *scratch, cudaStream_t st) {

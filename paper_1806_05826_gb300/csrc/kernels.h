@@ -31,6 +31,32 @@ rr_status validate_csr(int64_t n_rows, int64_t n_cols, int64_t nnz, const int64_
 rr_status iota_i64(int64_t *out, int64_t n, cudaStream_t st);
 rr_status fill_f64(double *out, double v, int64_t n, cudaStream_t st);
 
+// ---- k_leader.cu --------------------------------------------------------
+// Leader-follower clustering (Algorithm 1), binary X, in steps of 64 features.
+constexpr int32_t kLfMaxLeaders = 16384;   // the count kernel's shared-memory counters
+struct LfState {
+  int32_t L;            // leaders so far
+  int32_t nnew;         // leaders made by the current step
+  int32_t min_n, min_s; // the smallest leader size and the earliest leader of that size
+  int32_t overflow;     // 1 once more than the capacity would be needed
+  int32_t newpos[64];   // the current step's new leaders (positions in the step)
+};
+struct LfBuffers {
+  int32_t *rl = nullptr;                  // [nnz] per-row leader lists, laid out like col_idx
+  int32_t *rl_cnt = nullptr;              // [N]
+  unsigned long long *rowmask = nullptr;  // [N] the step features holding each row
+  int32_t *nlead = nullptr;               // [cap] leader sizes
+  unsigned long long *best = nullptr;     // [64] nearest committed leader of each step feature
+  int32_t *pair = nullptr;                // [64 x 64] overlaps among the step's features
+  LfState *S = nullptr;
+};
+// labels[F] (cluster = leader index), centers[cap] (the leaders' feature ids);
+// RR_UNSUPPORTED when more than cap leaders would be needed.
+rr_status leader_follower(int64_t N, int64_t F, const int64_t *row_ptr, const int64_t *col_ptr,
+                          const int32_t *row_idx, double tol2, int32_t cap, LfBuffers &lb,
+                          int32_t *labels, int32_t *centers, int32_t *n_lead_out, int32_t *err,
+                          cudaStream_t st);
+
 // ---- k_kmeans.cu --------------------------------------------------------
 struct KmeansBuffers {
   int64_t *d2;         // [F]   seeding squared distances
@@ -82,6 +108,9 @@ rr_status kmeans_lloyd_step(int64_t N, int64_t F, const int64_t *row_ptr, const 
 // order[] = features by descending work_i = sum of the row lengths of column i
 // (heaviest first); work[] receives work_i, which is also the Gershgorin row
 // sum of X^T X for binary X.
+// work[i] = sum over the rows of column i of their lengths (= sum_j |(X^T X)_ij|)
+rr_status feature_work(int64_t F, const int64_t *row_ptr, const int64_t *col_ptr,
+                       const int32_t *row_idx, int64_t *work, cudaStream_t st);
 rr_status kmeans_work_order(int64_t N, int64_t F, int32_t k, const int64_t *row_ptr,
                             const int64_t *col_ptr, const int32_t *row_idx, KmeansBuffers &b,
                             int64_t *work, int64_t *scratch, cudaStream_t st);

@@ -381,8 +381,39 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
                                scratch64, scratch64 + big, tmp32, scratch64 + 2 * big, st));
 
   RR_TRY(phase(1));
-  // ---- k-means++ seeding and Lloyd steps (Section 3.4)
   rr::KmeansBuffers kb{};
+  if (h->opt.clustering == RR_CLUSTER_LEADER) {
+    // ---- leader-follower clustering (Section 3.4, Algorithm 1)
+    rr::LfBuffers lb{};
+    RR_TRY(m.alloc(&lb.rl, std::max<int64_t>(nnz, 1)));
+    RR_TRY(m.alloc(&lb.rl_cnt, N));
+    RR_TRY(m.alloc(&lb.rowmask, N));
+    RR_TRY(m.alloc(&lb.nlead, k));
+    RR_TRY(m.alloc(&lb.best, 64));
+    RR_TRY(m.alloc(&lb.pair, 64 * 64));
+    RR_TRY(m.alloc(&lb.S, 1));
+    RR_TRY(m.alloc(&h->centers, k));
+    RR_TRY(m.alloc(&h->labels, F));
+    RR_TRY(m.alloc(&h->n_S, 2 * (int64_t)k));
+    RR_CUDA(cudaMemsetAsync(h->centers, 0xff, sizeof(int32_t) * k, st));
+    int32_t n_lead = 0;
+    RR_TRY(rr::leader_follower(N, F, h->row_ptr, h->col_ptr, h->row_idx, h->opt.lf_tol2, k, lb,
+                               h->labels, h->centers, &n_lead, h->err, st));
+    RR_TRY(check_dev_error(h, "rr_setup (leader-follower)"));
+    h->kmeans_iters = 0;
+    RR_TRY(m.alloc(&h->gsum, F));
+    RR_TRY(rr::feature_work(F, h->row_ptr, h->col_ptr, h->row_idx, h->gsum, st));
+    m.release(lb.rl);
+    m.release(lb.rl_cnt);
+    m.release(lb.rowmask);
+    m.release(lb.nlead);
+    m.release(lb.best);
+    m.release(lb.pair);
+    m.release(lb.S);
+    RR_TRY(phase(2));
+    RR_TRY(phase(3));
+  } else {
+  // ---- k-means++ seeding and Lloyd steps (Section 3.4)
   const int64_t ntiles = rr::kmeans_seed_tiles(F);
   RR_TRY(m.alloc(&kb.d2, F));
   RR_TRY(m.alloc(&kb.ov, F));
@@ -463,6 +494,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   m.release(kb.task_it);
 
   RR_TRY(phase(3));
+  }
   // ---- compaction, member lists, prolongation scale
   int32_t *remap = nullptr;
   RR_TRY(m.alloc(&remap, k + 1));
@@ -1286,6 +1318,8 @@ void rr_default_options(rr_options *o) {
   o->use_graphs = 1;
   o->gram = RR_GRAM_AUTO;
   o->gather = RR_GATHER_AUTO;
+  o->clustering = RR_CLUSTER_KMEANS;
+  o->lf_tol2 = 1.0;
   o->stream = nullptr;
 }
 
@@ -1353,6 +1387,16 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
   }
   if (opt.solver < RR_SOLVER_TWOLEVEL || opt.solver > RR_SOLVER_TLFCG) {
     rr_set_error("rr_setup: unknown solver %d", opt.solver);
+    return RR_INVALID_ARG;
+  }
+  if (opt.clustering != RR_CLUSTER_KMEANS && opt.clustering != RR_CLUSTER_LEADER) {
+    rr_set_error("rr_setup: unknown clustering %d", opt.clustering);
+    return RR_INVALID_ARG;
+  }
+  if (opt.clustering == RR_CLUSTER_LEADER &&
+      (X->layout != RR_CSR_BINARY || opt.init_centers || !isfinite(opt.lf_tol2))) {
+    rr_set_error("rr_setup: leader-follower clustering needs binary X, no init_centers and a "
+                 "finite lf_tol2");
     return RR_INVALID_ARG;
   }
   rr_handle *h = new rr_handle();

@@ -23,6 +23,7 @@ RR_PREC_FP64, RR_PREC_MIXED = 0, 1
 RR_GRAM_AUTO, RR_GRAM_CUDA_CORES = 0, 1
 RR_GATHER_AUTO, RR_GATHER_LANES, RR_GATHER_STAGED, RR_GATHER_LANES_STAGED = 0, 1, 2, 3
 RR_COARSE_CHOLESKY, RR_COARSE_EIGEN = 0, 1
+RR_CLUSTER_KMEANS, RR_CLUSTER_LEADER = 0, 1
 
 _STATUS = {0: "RR_OK", 1: "RR_INVALID_ARG", 2: "RR_CUDA_ERROR", 3: "RR_OOM", 4: "RR_NOT_SPD",
            5: "RR_NOT_CONVERGED", 6: "RR_NONFINITE", 7: "RR_TIMEOUT", 8: "RR_UNSUPPORTED"}
@@ -43,7 +44,8 @@ class rr_options(ctypes.Structure):
                 ("use_graphs", ctypes.c_int32), ("gram", ctypes.c_int32),
                 ("gather", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
                 ("lloyd_pull_work", ctypes.c_int64), ("coarse", ctypes.c_int32),
-                ("split_head", ctypes.c_int32),
+                ("split_head", ctypes.c_int32), ("clustering", ctypes.c_int32),
+                ("lf_tol2", ctypes.c_double),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -223,9 +225,10 @@ def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=N
              kmeans_max_iter=50, max_iter=20000, solver=RR_SOLVER_TWOLEVEL, check_every=8,
              max_restarts=5, use_graphs=1, gram=RR_GRAM_AUTO, gather=RR_GATHER_AUTO,
              precision=RR_PREC_FP64, wait_limit=0, lloyd_pull_work=0, split_head=0,
-             coarse=0, stream=None) -> Handle:
+             coarse=0, clustering=RR_CLUSTER_KMEANS, lf_tol2=1.0, stream=None) -> Handle:
     """rr_setup on a binary CSR pattern given as numpy arrays (host) or torch
-    CUDA tensors (device): row_ptr int64[N+1], col_idx int32[nnz]."""
+    CUDA tensors (device): row_ptr int64[N+1], col_idx int32[nnz]. With
+    clustering = RR_CLUSTER_LEADER, k is the largest number of leaders."""
     on_device = 0 if isinstance(row_ptr, np.ndarray) else 1
     if on_device == 0:
         row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
@@ -250,7 +253,8 @@ def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=N
                            init_centers=_ptr(ic), solver=solver, check_every=check_every,
                            max_restarts=max_restarts, use_graphs=use_graphs, gram=gram,
                            gather=gather, wait_limit=wait_limit, lloyd_pull_work=lloyd_pull_work,
-                           split_head=split_head, coarse=coarse,
+                           split_head=split_head, coarse=coarse, clustering=clustering,
+                           lf_tol2=float(lf_tol2),
                            precision=precision, stream=_stream_ptr(stream))
     out = _P()
     _check(lib.rr_setup(ctypes.byref(X), float(lam), int(k), ctypes.byref(o), ctypes.byref(out)))

@@ -60,6 +60,11 @@ def test_default_options_and_invalid_args_without_gpu(lib):
     assert L.rr_setup(ctypes.byref(X), 1.0, 1, ctypes.byref(o_bad), ctypes.byref(out)) == rr.RR_INVALID_ARG
     o_bad = rr.rr_default_options(solver=7)
     assert L.rr_setup(ctypes.byref(X), 1.0, 1, ctypes.byref(o_bad), ctypes.byref(out)) == rr.RR_INVALID_ARG
+    o_bad = rr.rr_default_options(clustering=2)
+    assert L.rr_setup(ctypes.byref(X), 1.0, 1, ctypes.byref(o_bad), ctypes.byref(out)) == rr.RR_INVALID_ARG
+    o_bad = rr.rr_default_options(clustering=rr.RR_CLUSTER_LEADER, lf_tol2=float("nan"))
+    assert L.rr_setup(ctypes.byref(X), 1.0, 1, ctypes.byref(o_bad), ctypes.byref(out)) == rr.RR_INVALID_ARG
+    assert "leader-follower" in rr.rr_last_error()
     X.layout = 7
     assert L.rr_setup(ctypes.byref(X), 1.0, 1, None, ctypes.byref(out)) == rr.RR_INVALID_ARG
     # a dense X needs values and no CSR arrays
