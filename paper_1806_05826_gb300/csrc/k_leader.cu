@@ -64,7 +64,8 @@ __global__ void k_lf_count(int64_t F, int64_t f0, const int64_t *__restrict__ co
   for (int64_t e = col_ptr[i] + threadIdx.x; e < col_ptr[i + 1]; e += blockDim.x) {
     const int32_t r = row_idx[e];
     const int64_t q0 = row_ptr[r];
-    const int32_t qn = rl_cnt[r];
+    const int64_t len = row_ptr[r + 1] - q0;
+    const int32_t qn = (int32_t)min((int64_t)rl_cnt[r], len);
     for (int32_t q = 0; q < qn; ++q) {
       const int32_t s = rl[q0 + q];
       if (s >= 0 && s < L0) atomicAdd(&cnt[s], 1);
