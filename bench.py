@@ -490,7 +490,7 @@ def measure_bayes(rr, row_ptr, col_idx, N, F, k, lam, opts, dev, y_dev, n_sample
 
 
 def measure_leader(rr, row_ptr, col_idx, N, F, lams, opts, dev, y_dev, tol2s, cap=16384,
-                   tlfcg=True):
+                   tlfcg=True, kmeans_same_k=False):
     """Leader-follower clustering (Algorithm 1, RR_CLUSTER_LEADER) in place of
     k-means++ on the step's matrix: for each squared tolerance, the number of
     leaders (the coarse size F_C), the clustering's time, the setup, and the
@@ -530,6 +530,22 @@ def measure_leader(rr, row_ptr, col_idx, N, F, lams, opts, dev, y_dev, tol2s, ca
             row["tlfcg_iters_lam0"] = inf["iters"]
             row["tlfcg_solve_ms_lam0"] = round(inf["solve_ms"], 2)
             rr.rr_free(h)
+        if kmeans_same_k:
+            # k-means++ into as many clusters as there are leaders: the coarse
+            # size and the clustering method told apart
+            km = {"k": row["k_eff"]}
+            h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], row["k_eff"], **opts)
+            inf = rr.rr_solve(h, y_dev, w, tol=TOL)
+            km["pcg_iters_lam0"] = inf["iters"]
+            km["setup_ms"] = round(inf["setup_ms"], 2)
+            km["cluster_ms"] = round(inf["setup_phase_ms"][2] + inf["setup_phase_ms"][3], 2)
+            rr.rr_free(h)
+            h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], row["k_eff"],
+                            **dict(opts, solver=rr.RR_SOLVER_TLFCG))
+            inf = rr.rr_solve(h, y_dev, w, tol=TOL)
+            km["tlfcg_iters_lam0"] = inf["iters"]
+            rr.rr_free(h)
+            row["kmeans_same_k"] = km
         out["tol2"].append(row)
     return out
 
@@ -801,7 +817,7 @@ def run_ours(args, rank, world, local):
     if args.only_leader:
         tol2s = [float(t) for t in args.leader_tol2.split(",") if t] or LEADER_TOL2
         return {"leader": measure_leader(rr, row_ptr, col_idx, N, F, lams, opts, dev, y_dev,
-                                         tol2s)}
+                                         tol2s, kmeans_same_k=True)}
     if args.only_bayes:
         return {"bayes": measure_bayes(rr, row_ptr, col_idx, N, F, k, lams[0], opts, dev, y_dev)}
     if args.only == "batched":

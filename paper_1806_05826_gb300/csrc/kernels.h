@@ -32,7 +32,8 @@ rr_status iota_i64(int64_t *out, int64_t n, cudaStream_t st);
 rr_status fill_f64(double *out, double v, int64_t n, cudaStream_t st);
 
 // ---- k_leader.cu --------------------------------------------------------
-// Leader-follower clustering (Algorithm 1), binary X, in steps of 64 features.
+// Leader-follower clustering (Algorithm 1), binary X, in steps of 64 features
+// (each feature's rows in tasks of at most 2048).
 constexpr int32_t kLfMaxLeaders = 16384;   // the count kernel's shared-memory counters
 struct LfState {
   int32_t L;            // leaders so far
@@ -47,7 +48,6 @@ struct LfBuffers {
   unsigned long long *rowmask = nullptr;  // [N] the step features holding each row
   int32_t *nlead = nullptr;               // [cap] leader sizes
   unsigned long long *best = nullptr;     // [64] nearest committed leader of each step feature
-  int32_t *pair = nullptr;                // [64 x 64] overlaps among the step's features
   LfState *S = nullptr;
 };
 // labels[F] (cluster = leader index), centers[cap] (the leaders' feature ids);

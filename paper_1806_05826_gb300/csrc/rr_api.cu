@@ -390,7 +390,6 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
     RR_TRY(m.alloc(&lb.rowmask, N));
     RR_TRY(m.alloc(&lb.nlead, k));
     RR_TRY(m.alloc(&lb.best, 64));
-    RR_TRY(m.alloc(&lb.pair, 64 * 64));
     RR_TRY(m.alloc(&lb.S, 1));
     RR_TRY(m.alloc(&h->centers, k));
     RR_TRY(m.alloc(&h->labels, F));
@@ -408,7 +407,6 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
     m.release(lb.rowmask);
     m.release(lb.nlead);
     m.release(lb.best);
-    m.release(lb.pair);
     m.release(lb.S);
     RR_TRY(phase(2));
     RR_TRY(phase(3));
