@@ -5,8 +5,11 @@
 //
 //   A_c(lambda)^{-1} = Q diag(1 / (mu + lambda)) Q^T,
 //
-// one FP64 product per lambda instead of a Cholesky factorisation, its
-// triangular inverse and their product.
+// applied in the solve loop as Q (diag(1 / (mu + lambda)) (Q^T r_c)), two
+// mat-vecs, so a lambda change only rescales a vector (eig_dvec); the batched
+// solve forms Q diag(1 / (mu + lambda)) Q^T once per weight (eig_inverse).
+// Either replaces a Cholesky factorisation, its triangular inverse and their
+// product.
 //
 // The eigendecomposition is the parallel cyclic Jacobi method: each sweep is
 // n - 1 rounds of n / 2 disjoint plane rotations (the round-robin tournament
