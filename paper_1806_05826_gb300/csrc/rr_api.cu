@@ -9,6 +9,8 @@
 #include <string.h>
 
 #include <chrono>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -317,6 +319,63 @@ rr_status setup_impl_dense(rr_handle *h, const rr_matrix *X, double lambda, int3
   return RR_OK;
 }
 
+// The sliced patterns of X and X^T and, in mixed precision, the split form:
+// they depend on X alone, so rr_setup builds them on a second stream from a
+// second host thread while the clustering, the coarse Gram and the factor run
+// on the first.
+rr_status build_patterns(rr_handle *h, cudaStream_t st) {
+  const int64_t N = h->N, F = h->F;
+  RR_TRY(rr::sliced_build(N, F, h->row_ptr, h->col_idx, h->pcsr, h->err, st));
+  RR_TRY(rr::sliced_build(F, N, h->col_ptr, h->row_idx, h->pcsc, h->err, st));
+  if (h->opt.precision == RR_PREC_MIXED || h->opt.gather != RR_GATHER_AUTO) {
+    const bool split = h->opt.gather == RR_GATHER_LANES_STAGED;
+    RR_TRY(rr::sliced_choose_gather(h->pcsr, split ? RR_GATHER_LANES : h->opt.gather, st));
+    RR_TRY(rr::sliced_choose_gather(h->pcsc, split ? RR_GATHER_STAGED : h->opt.gather, st));
+  }
+  if (h->opt.precision == RR_PREC_MIXED)
+    RR_TRY(rr::split_build(N, F, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx,
+                           h->opt.split_head, h->opt.gather, h->split, h->err, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  return RR_OK;
+}
+
+struct PatternJob {
+  cudaStream_t st = nullptr;
+  cudaEvent_t ready = nullptr;
+  std::thread worker;
+  rr_status status = RR_OK;
+  std::string err;
+  int64_t launches = 0;
+  // waits for the worker and adds its launches to this thread's count
+  rr_status finish() {
+    if (worker.joinable()) {
+      worker.join();
+      rr_launch_counter += launches;
+      launches = 0;
+    }
+    if (status != RR_OK) rr_set_error("%s", err.c_str());
+    return status;
+  }
+  ~PatternJob() {
+    if (worker.joinable()) worker.join();
+    if (ready) cudaEventDestroy(ready);
+    if (st) cudaStreamDestroy(st);
+  }
+  rr_status start(rr_handle *h, cudaStream_t main) {
+    RR_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    RR_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    RR_CUDA(cudaEventRecord(ready, main));
+    RR_CUDA(cudaStreamWaitEvent(st, ready, 0));
+    worker = std::thread([this, h] {
+      const int64_t l0 = rr_launch_counter;
+      status = build_patterns(h, st);
+      if (status != RR_OK) err = rr_last_error();
+      launches = rr_launch_counter - l0;
+    });
+    return RR_OK;
+  }
+};
+
 rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k) {
   cudaStream_t st = h->st;
   DevArena &m = h->mem;
@@ -381,6 +440,8 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
                                scratch64, scratch64 + big, tmp32, scratch64 + 2 * big, st));
 
   RR_TRY(phase(1));
+  PatternJob patterns;
+  RR_TRY(patterns.start(h, st));
   rr::KmeansBuffers kb{};
   if (h->opt.clustering == RR_CLUSTER_LEADER) {
     // ---- leader-follower clustering (Section 3.4, Algorithm 1)
@@ -568,19 +629,10 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(build_lambda(h, lambda));
 
   RR_TRY(phase(6));
-  // ---- sliced patterns of X and X^T and the solve workspace
-  RR_TRY(rr::sliced_build(N, F, h->row_ptr, h->col_idx, h->pcsr, h->err, st));
-  RR_TRY(rr::sliced_build(F, N, h->col_ptr, h->row_idx, h->pcsc, h->err, st));
-  if (h->opt.precision == RR_PREC_MIXED || h->opt.gather != RR_GATHER_AUTO) {
-    const bool split = h->opt.gather == RR_GATHER_LANES_STAGED;
-    RR_TRY(rr::sliced_choose_gather(h->pcsr, split ? RR_GATHER_LANES : h->opt.gather, st));
-    RR_TRY(rr::sliced_choose_gather(h->pcsc, split ? RR_GATHER_STAGED : h->opt.gather, st));
-  }
-  if (h->opt.precision == RR_PREC_MIXED) {
-    RR_TRY(rr::split_build(N, F, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx,
-                           h->opt.split_head, h->opt.gather, h->split, h->err, st));
-    RR_TRY(rr::split_set_wd(h->split, h->omega, h->d, st));
-  }
+  // ---- the patterns (built alongside) and the solve workspace
+  RR_TRY(patterns.finish());
+  RR_TRY(check_dev_error(h, "rr_setup (patterns)"));
+  if (h->opt.precision == RR_PREC_MIXED) RR_TRY(rr::split_set_wd(h->split, h->omega, h->d, st));
   RR_TRY(alloc_solve_workspace(h));
   m.release(tmp32);
   m.release(scratch64);
