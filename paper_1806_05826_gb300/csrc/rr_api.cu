@@ -327,11 +327,6 @@ rr_status build_patterns(rr_handle *h, cudaStream_t st) {
   const int64_t N = h->N, F = h->F;
   RR_TRY(rr::sliced_build(N, F, h->row_ptr, h->col_idx, h->pcsr, h->err, st));
   RR_TRY(rr::sliced_build(F, N, h->col_ptr, h->row_idx, h->pcsc, h->err, st));
-  if (h->opt.precision == RR_PREC_MIXED || h->opt.gather != RR_GATHER_AUTO) {
-    const bool split = h->opt.gather == RR_GATHER_LANES_STAGED;
-    RR_TRY(rr::sliced_choose_gather(h->pcsr, split ? RR_GATHER_LANES : h->opt.gather, st));
-    RR_TRY(rr::sliced_choose_gather(h->pcsc, split ? RR_GATHER_STAGED : h->opt.gather, st));
-  }
   if (h->opt.precision == RR_PREC_MIXED)
     RR_TRY(rr::split_build(N, F, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx,
                            h->opt.split_head, h->opt.gather, h->split, h->err, st));
@@ -632,6 +627,12 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   // ---- the patterns (built alongside) and the solve workspace
   RR_TRY(patterns.finish());
   RR_TRY(check_dev_error(h, "rr_setup (patterns)"));
+  // the gather kernels are timed here, with nothing else running
+  if (h->opt.precision == RR_PREC_MIXED || h->opt.gather != RR_GATHER_AUTO) {
+    const bool split = h->opt.gather == RR_GATHER_LANES_STAGED;
+    RR_TRY(rr::sliced_choose_gather(h->pcsr, split ? RR_GATHER_LANES : h->opt.gather, st));
+    RR_TRY(rr::sliced_choose_gather(h->pcsc, split ? RR_GATHER_STAGED : h->opt.gather, st));
+  }
   if (h->opt.precision == RR_PREC_MIXED) RR_TRY(rr::split_set_wd(h->split, h->omega, h->d, st));
   RR_TRY(alloc_solve_workspace(h));
   m.release(tmp32);
