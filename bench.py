@@ -838,6 +838,8 @@ def run_ours(args, rank, world, local):
         else:
             h = rr.rr_setup(host["rp"], host["ci"], N, F, lams[0], k, **opts)
             yd = host["y"].to(dev, non_blocking=True)
+        # the coarse levels of the other weights, built while the first one solves
+        rr.rr_prepare_lambdas(h, lams[1:])
         infos = []
         for j, lam in enumerate(lams):
             if j:

@@ -205,6 +205,20 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
  * factor must be recomputed when beta changes). Synchronises the stream. */
 rr_status rr_set_lambda(rr_handle *h, double lambda);
 
+/* Prepares the coarse level of up to 8 further lambdas ahead of time (no
+ * counterpart in the paper, which refactors the coarse operator whenever beta
+ * changes, Section 4): the Cholesky factor, its inverse and the smoother of
+ * each lambda are computed on a second stream, overlapping whatever the
+ * handle's stream runs meanwhile (a solve); rr_set_lambda to exactly one of
+ * these lambdas then waits for its work and swaps it in instead of
+ * factoring. Returns without waiting for the factors; a later call replaces
+ * the prepared set (after the earlier one has finished); an RR_COARSE_EIGEN
+ * handle needs none (a no-op). lambdas: host double[n], each positive and
+ * finite. Errors: RR_INVALID_ARG (NULL handle, n outside [0, 8], a bad
+ * lambda), RR_OOM, RR_CUDA_ERROR; a factor that meets a non-positive pivot
+ * is reported by the rr_set_lambda that installs it (RR_NOT_SPD). */
+rr_status rr_prepare_lambdas(rr_handle *h, const double *lambdas, int32_t n);
+
 /* Solves Eq. (1) for one right-hand side by CG preconditioned as
  * rr_options.solver says (RR_SOLVER_TLFCG: flexible CG, Algorithm 3 with
  * m = 1, as rr_solve_fcg without a network), from w_0 = 0 (Algorithm 3's

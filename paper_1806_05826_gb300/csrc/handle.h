@@ -68,6 +68,20 @@ struct rr_handle {
   double *Qt = nullptr, *dvec = nullptr, *ec_tmp = nullptr;   // Q row-major, 1/(mu+lambda)
   float *Ainv32 = nullptr;               // RR_PREC_MIXED: FP32 copy of Ainv, rows padded to 4
   int32_t eig_sweeps = 0;
+  // coarse levels prepared ahead for other lambdas (rr_prepare_lambdas): built
+  // on prep_st; rr_set_lambda to one of them swaps its buffers in
+  struct Prepared {
+    double lambda = 0.0;
+    bool valid = false;
+    double *Ainv = nullptr, *d = nullptr, *omega_dev = nullptr;
+    float *Ainv32 = nullptr;
+    unsigned long long *max_bits = nullptr;
+    cudaEvent_t done = nullptr;
+  };
+  static constexpr int kPrepared = 8;
+  Prepared prep[kPrepared];
+  cudaStream_t prep_st = nullptr;
+  double *prep_Ac = nullptr, *prep_Lw = nullptr, *prep_Linv = nullptr;   // shared scratch
   // smoother
   double *d = nullptr;
   int64_t *gsum = nullptr;   // sum_j |(X^T X)_ij| = sum of the row lengths over column i

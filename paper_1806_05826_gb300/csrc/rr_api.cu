@@ -153,6 +153,68 @@ rr_status build_lambda(rr_handle *h, double lambda) {
   return RR_OK;
 }
 
+// The coarse inverse and the smoother at lambda into a prepared slot, on the
+// prepare stream (the Cholesky form; the same operations as build_lambda).
+rr_status prepare_one(rr_handle *h, rr_handle::Prepared &P, double lambda) {
+  cudaStream_t st = h->prep_st;
+  const int32_t k = h->k_eff;
+  const int64_t kk = (int64_t)k * k;
+  DevArena &m = h->mem;
+  if (!P.Ainv) {
+    RR_TRY(m.alloc(&P.Ainv, kk));
+    if (h->Ainv32) RR_TRY(m.alloc(&P.Ainv32, (int64_t)k * ((k + 3) & ~3)));
+    RR_TRY(m.alloc(&P.d, h->F));
+    RR_TRY(m.alloc(&P.omega_dev, 1));
+    RR_TRY(m.alloc(&P.max_bits, 1));
+    RR_CUDA(cudaEventCreateWithFlags(&P.done, cudaEventDisableTiming));
+  }
+  P.valid = false;
+  RR_TRY(rr::coarse_operator(k, h->G, h->s, lambda, h->prep_Ac, st));
+  RR_CUDA(cudaMemcpyAsync(h->prep_Lw, h->prep_Ac, sizeof(double) * kk, cudaMemcpyDeviceToDevice, st));
+  RR_TRY(rr::cholesky(k, h->prep_Lw, h->err, st));
+  RR_TRY(rr::chol_inverse(k, h->prep_Lw, h->prep_Linv, P.Ainv, st));
+  if (P.Ainv32) RR_TRY(rr::coarse_to_f32(k, P.Ainv, P.Ainv32, st));
+  RR_CUDA(cudaMemsetAsync(P.max_bits, 0, sizeof(unsigned long long), st));
+  if (h->dense) {
+    RR_TRY(rr::dense_jacobi(h->F, lambda, h->dsq, h->dgs, P.d, P.max_bits, st));
+  } else {
+    RR_LAUNCH(k_jacobi_setup, rr::grid_for(h->F, kThreads), kThreads, 0, st, h->F, lambda,
+              h->col_ptr, h->gsum, P.d, P.max_bits);
+  }
+  RR_LAUNCH(k_omega, 1, 32, 0, st, P.max_bits, P.omega_dev);
+  RR_CUDA(cudaEventRecord(P.done, st));
+  P.lambda = lambda;
+  P.valid = true;
+  return RR_OK;
+}
+
+// rr_set_lambda's fast path: a prepared slot for exactly this lambda is swapped
+// in (its buffers and the handle's trade places); returns false if none.
+rr_status install_prepared(rr_handle *h, double lambda, bool *found) {
+  *found = false;
+  for (auto &P : h->prep) {
+    if (!P.valid || P.lambda != lambda) continue;
+    RR_CUDA(cudaEventSynchronize(P.done));
+    RR_TRY(check_dev_error(h, "prepared coarse factor"));
+    double om = 0.0;
+    RR_CUDA(cudaMemcpyAsync(&om, P.omega_dev, sizeof(double), cudaMemcpyDeviceToHost, h->prep_st));
+    RR_CUDA(cudaStreamSynchronize(h->prep_st));
+    std::swap(h->Ainv, P.Ainv);
+    std::swap(h->Ainv32, P.Ainv32);
+    std::swap(h->d, P.d);
+    std::swap(h->omega_dev, P.omega_dev);
+    std::swap(h->max_bits, P.max_bits);
+    P.valid = false;
+    RR_TRY(rr::coarse_operator(h->k_eff, h->G, h->s, lambda, h->Ac, h->st));
+    h->omega = om;
+    h->lambda = lambda;
+    RR_TRY(rr::split_set_wd(h->split, h->omega, h->d, h->st));
+    *found = true;
+    return RR_OK;
+  }
+  return RR_OK;
+}
+
 // Solve vectors, partial-dot buffers, scalars and the capture stream.
 rr_status alloc_solve_workspace(rr_handle *h) {
   DevArena &m = h->mem;
@@ -1478,8 +1540,36 @@ rr_status rr_set_lambda(rr_handle *h, double lambda) {
     return RR_INVALID_ARG;
   }
   destroy_graph(h);   // the captured kernels hold lambda and omega by value
-  RR_TRY(build_lambda(h, lambda));
+  bool found = false;
+  if (!h->mu) RR_TRY(install_prepared(h, lambda, &found));
+  if (!found) RR_TRY(build_lambda(h, lambda));
   RR_CUDA(cudaStreamSynchronize(h->st));
+  return RR_OK;
+}
+
+rr_status rr_prepare_lambdas(rr_handle *h, const double *lambdas, int32_t n) {
+  if (!h || (n > 0 && !lambdas) || n < 0 || n > rr_handle::kPrepared) {
+    rr_set_error("rr_prepare_lambdas: need a handle and 0 <= n <= %d lambdas",
+                 rr_handle::kPrepared);
+    return RR_INVALID_ARG;
+  }
+  for (int32_t i = 0; i < n; ++i)
+    if (!(lambdas[i] > 0.0) || !isfinite(lambdas[i])) {
+      rr_set_error("rr_prepare_lambdas: every lambda must be positive and finite");
+      return RR_INVALID_ARG;
+    }
+  if (h->mu || n == 0) return RR_OK;   // the eigen form's lambda change is one vector rescale
+  const int64_t kk = (int64_t)h->k_eff * h->k_eff;
+  if (!h->prep_st) {
+    RR_CUDA(cudaStreamCreateWithFlags(&h->prep_st, cudaStreamNonBlocking));
+    RR_TRY(h->mem.alloc(&h->prep_Ac, kk));
+    RR_TRY(h->mem.alloc(&h->prep_Lw, kk));
+    RR_TRY(h->mem.alloc(&h->prep_Linv, kk));
+  }
+  // the previous preparations' buffers are reused: let them finish first
+  RR_CUDA(cudaStreamSynchronize(h->prep_st));
+  for (auto &P : h->prep) P.valid = false;
+  for (int32_t i = 0; i < n; ++i) RR_TRY(prepare_one(h, h->prep[i], lambdas[i]));
   return RR_OK;
 }
 
@@ -1775,6 +1865,12 @@ void rr_free(rr_handle *h) {
   h->batch = nullptr;
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->limit_host) cudaFreeHost(h->limit_host);
+  if (h->prep_st) {
+    cudaStreamSynchronize(h->prep_st);
+    cudaStreamDestroy(h->prep_st);
+  }
+  for (auto &P : h->prep)
+    if (P.done) cudaEventDestroy(P.done);
   rr::restrict_free(h->rplan);
   rr::restrict_free(h->bplan);
   rr::sliced_free(h->pcsr);

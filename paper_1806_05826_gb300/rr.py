@@ -86,6 +86,7 @@ _SIGS = {
     "rr_setup": (ctypes.c_int, [ctypes.POINTER(rr_matrix), ctypes.c_double, ctypes.c_int32,
                                 ctypes.POINTER(rr_options), ctypes.POINTER(_P)]),
     "rr_set_lambda": (ctypes.c_int, [_P, ctypes.c_double]),
+    "rr_prepare_lambdas": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
     "rr_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.POINTER(rr_info)]),
     "rr_solve_batch": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P,
                                       ctypes.c_double, _P]),
@@ -288,6 +289,12 @@ def rr_setup_dense(X, lam, k, *, seed=0, init_centers=None, kmeans_max_iter=50, 
     h = Handle(out, n_cols, n_rows, (ic,), int(k))
     h.dense = True
     return h
+
+
+def rr_prepare_lambdas(h: Handle, lambdas):
+    """Coarse levels of further lambdas built ahead on a second stream."""
+    lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64).ravel())
+    _check(load().rr_prepare_lambdas(h.ptr, lam.ctypes.data, int(lam.size)))
 
 
 def rr_set_lambda(h: Handle, lam: float):

@@ -561,3 +561,36 @@ def test_bounded_wait_expiry_returns_timeout(rr):
     info = rr.rr_solve(h, dev(y), w, tol=1e-8)
     assert info["status"] == "RR_OK" and info["gram_tensor_cores"] == 1
     rr.rr_free(h)
+
+
+def test_prepared_lambdas_give_identical_bits(rr):
+    """rr_prepare_lambdas builds the coarse levels of further weights on a
+    second stream; installing one by rr_set_lambda gives the same bits as
+    factoring it there (the same kernels in the same order), in both
+    precisions; an unprepared weight still factors; bad arguments fail."""
+    X = synth.zipf_binary(2000, 1000, 0.01, 1.1, 0)
+    y, _ = synth.ridge_targets(X, 0)
+    lams = (1e-2, 1e-3, 0.3)
+    for prec in (rr.RR_PREC_FP64, rr.RR_PREC_MIXED):
+        ws = []
+        for prepare in (False, True):
+            h = rr.rr_setup(X.row_ptr, X.col_idx, 2000, 1000, lams[0], 50, precision=prec)
+            if prepare:
+                rr.rr_prepare_lambdas(h, lams[1:])
+            out = []
+            for j, lam in enumerate(lams + (5.0,)):
+                if j:
+                    rr.rr_set_lambda(h, lam)
+                w = torch.empty(1000, dtype=torch.float64, device="cuda")
+                info = rr.rr_solve(h, dev(y), w, tol=1e-8)
+                assert info["status"] == "RR_OK"
+                out.append(w.cpu().numpy())
+            ws.append(out)
+            if prepare:
+                with pytest.raises(rr.RRError):
+                    rr.rr_prepare_lambdas(h, [1.0] * 9)
+                with pytest.raises(rr.RRError):
+                    rr.rr_prepare_lambdas(h, [-1.0])
+            rr.rr_free(h)
+        for a, b in zip(*ws):
+            assert np.array_equal(a, b)
