@@ -419,7 +419,9 @@ struct PatternJob {
     if (st) cudaStreamDestroy(st);
   }
   rr_status start(rr_handle *h, cudaStream_t main) {
-    RR_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    int least = 0, greatest = 0;
+    RR_CUDA(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    RR_CUDA(cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, least));
     RR_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
     RR_CUDA(cudaEventRecord(ready, main));
     RR_CUDA(cudaStreamWaitEvent(st, ready, 0));
@@ -1518,9 +1520,36 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
   h->st = static_cast<cudaStream_t>(opt.stream);
   const auto t0 = std::chrono::steady_clock::now();
   h->opt.init_centers = opt.init_centers;
+  // the setup runs on a stream of the highest priority (after the caller's
+  // stream's earlier work), so that its latency-bound k-means++ rounds go
+  // first while the pattern build runs beside them at the lowest priority;
+  // it is synchronised before rr_setup returns
+  cudaStream_t user = h->st, hp = nullptr;
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess &&
+      cudaStreamCreateWithPriority(&hp, cudaStreamNonBlocking, greatest) == cudaSuccess) {
+    cudaEvent_t ev = nullptr;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ev, user) != cudaSuccess || cudaStreamWaitEvent(hp, ev, 0) != cudaSuccess) {
+      cudaStreamDestroy(hp);
+      hp = nullptr;
+    } else {
+      h->st = hp;
+    }
+    if (ev) cudaEventDestroy(ev);
+  }
+  cudaGetLastError();
   rr_status s = X->layout == RR_DENSE_F32_ROWMAJOR ? setup_impl_dense(h, X, lambda, k)
                                                    : setup_impl(h, X, lambda, k);
   h->opt.init_centers = nullptr;
+  if (hp) {
+    if (cudaStreamSynchronize(hp) != cudaSuccess && s == RR_OK) {
+      rr_set_error("rr_setup: %s", cudaGetErrorString(cudaGetLastError()));
+      s = RR_CUDA_ERROR;
+    }
+    h->st = user;
+    cudaStreamDestroy(hp);
+  }
   if (s != RR_OK) {
     rr_free(h);
     return s;
