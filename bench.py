@@ -199,32 +199,45 @@ def profiled_traffic(kernel, workload):
 
 # ---------------------------------------------------------------- parity leg
 
-def _parity_worker(spec, k, seed, lams, y, out_path, threads):
+def _parity_worker(spec, k, seed, jobs, out_path, threads):
     """Runs in a spawned process: the oracle's clustering, then the exact
-    solution of every lambda (the oracle's PCG to 1e-12, one process each),
-    saved to out_path."""
+    solution of every (lambda, y) job (the oracle's PCG to 1e-12, one process
+    each), saved to out_path."""
     sys.path.insert(0, ROOT)
     from oracle import reference
     _, raw, iters = reference.oracle_labels(spec, k, seed, threads=threads)
-    res = reference.exact_solutions(spec, raw, [(lam, y) for lam in lams],
-                                    snap_tols=(TOL,), processes=len(lams))
+    res = reference.exact_solutions(spec, raw, list(jobs), snap_tols=(TOL,),
+                                    processes=len(jobs))
     np.savez(out_path, w_ref=np.stack([r[0] for r in res]),
              w_orc=np.stack([r[1][TOL] for r in res]),
              iters=np.array([r[2] for r in res]), rel=np.array([r[3] for r in res]),
              kmeans_iters=iters)
 
 
-def start_parity(X, y, p, tmpdir):
+# systems of the batched workload checked against the oracle: (weight index,
+# target index) of zipf_200000x100000_64x8
+BATCH_SAMPLES = ((0, 0), (7, 63))
+
+
+def start_parity(X, y, p, tmpdir, batch=True):
     """Starts the oracle's exact solutions in the background (before any GPU
     work is timed; the process is spawned, so it shares nothing with the CUDA
-    context). Returns (process, output path)."""
+    context): the step's systems, then (batch) the sampled batched systems.
+    Returns (process, output path)."""
     import multiprocessing as mp
+    from gen import synth
     spec = (X.n_rows, X.n_cols, p["density"], p["s"], p["seed"])
     path = os.path.join(tmpdir, "parity.npz")
     threads = max(1, (os.cpu_count() or 4) // 2 - 1)
+    jobs = [(lam, y) for lam in p["lambdas"]]
+    if batch:
+        pb = synth.BATCH_WORKLOADS["zipf_200000x100000_64x8"]
+        for l, j in BATCH_SAMPLES:
+            yj, _ = synth.ridge_targets_many(X, [pb["target_seeds"][j]])
+            jobs.append((float(pb["lambdas"][l]), yj[0]))
     proc = mp.get_context("spawn").Process(
-        target=_parity_worker, args=(spec, p["k"], p["seed"], list(p["lambdas"]), y, path,
-                                     threads), daemon=False)
+        target=_parity_worker, args=(spec, p["k"], p["seed"], jobs, path, threads),
+        daemon=False)
     proc.start()
     return proc, path
 
@@ -236,30 +249,41 @@ def start_parity(X, y, p, tmpdir):
 SOLUTION_SPREAD = 25.0
 
 
-def finish_parity(proc, path, W, lams, timeout_s=900):
-    """||w - w_ref|| / ||w_ref|| of the timed step's solutions, with the
-    oracle's own error at the same tolerance for context."""
+def finish_parity(proc, path, W, lams, timeout_s=900, W_batch=None):
+    """||w - w_ref|| / ||w_ref|| of the timed step's solutions (and of the
+    sampled batched systems, when given), with the oracle's own error at the
+    same tolerance for context. Returns (step parity, batched parity)."""
     proc.join(timeout_s)
     if proc.is_alive() or not os.path.exists(path):
         if proc.is_alive():
             proc.terminate()
-        return {"error": "the oracle's reference solve did not finish"}
+        return {"error": "the oracle's reference solve did not finish"}, None
     d = np.load(path)
+
+    def compare(ws, idx):
+        o = {"err_vs_oracle": [], "oracle_err_at_tol": [], "bar": [], "within_bar": []}
+        for w, j in zip(ws, idx):
+            wr = d["w_ref"][j]
+            e = float(np.linalg.norm(w - wr) / np.linalg.norm(wr))
+            eo = float(np.linalg.norm(d["w_orc"][j] - wr) / np.linalg.norm(wr))
+            bar = max(1e-6, SOLUTION_SPREAD * eo)
+            o["err_vs_oracle"].append(e)
+            o["oracle_err_at_tol"].append(eo)
+            o["bar"].append(bar)
+            o["within_bar"].append(bool(e <= bar))
+        return o
+
     out = {"reference": "oracle two-level PCG (its own k-means++ clustering) to relative residual "
-                        "1e-12", "tol": TOL, "lambdas": list(lams),
-           "err_vs_oracle": [], "oracle_err_at_tol": [], "bar": [], "within_bar": []}
-    for j in range(len(lams)):
-        wr = d["w_ref"][j]
-        e = float(np.linalg.norm(W[j] - wr) / np.linalg.norm(wr))
-        eo = float(np.linalg.norm(d["w_orc"][j] - wr) / np.linalg.norm(wr))
-        bar = max(1e-6, SOLUTION_SPREAD * eo)
-        out["err_vs_oracle"].append(e)
-        out["oracle_err_at_tol"].append(eo)
-        out["bar"].append(bar)
-        out["within_bar"].append(bool(e <= bar))
-    out["oracle_ref_iters"] = [int(v) for v in d["iters"]]
+                        "1e-12", "tol": TOL, "lambdas": list(lams)}
+    out.update(compare(W, range(len(lams))))
+    out["oracle_ref_iters"] = [int(v) for v in d["iters"][:len(lams)]]
     out["oracle_kmeans_iters"] = int(d["kmeans_iters"])
-    return out
+    bout = None
+    if W_batch is not None and len(d["w_ref"]) >= len(lams) + len(BATCH_SAMPLES):
+        bout = {"systems": [list(s) for s in BATCH_SAMPLES],
+                "note": "(weight index, target index) of the batched workload"}
+        bout.update(compare(W_batch, range(len(lams), len(lams) + len(BATCH_SAMPLES))))
+    return out, bout
 
 
 def measure_small_fp64(rr, dev):
@@ -410,7 +434,9 @@ def measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world, n_targ
         "per_system_apply_us": round(q["apply_ms"] * 1e3 / n_sys, 2)}
     rr.rr_free(h)
     its = sorted(i["iters"] for i in infos)
+    samples = [Wb[l, j].cpu().numpy() for l, j in BATCH_SAMPLES if j < len(seeds)]
     return {"workload": name, "systems": n_sys, "targets": len(seeds), "lambdas": lams,
+            "_samples": samples if len(samples) == len(BATCH_SAMPLES) else None,
             "value": round(t_batch, 4), "unit": "s", "s_per_system": round(t_batch / n_sys, 6),
             "setup_s": round(setup_s, 4), "solve_s": round(infos[0]["solve_ms"] / 1000.0, 4),
             "iters_min_median_max": [its[0], its[len(its) // 2], its[-1]],
@@ -823,8 +849,10 @@ def run_ours(args, rank, world, local):
     if args.only_bayes:
         return {"bayes": measure_bayes(rr, row_ptr, col_idx, N, F, k, lams[0], opts, dev, y_dev)}
     if args.only == "batched":
-        return {"batched": measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world,
-                                           args.batch_targets)}
+        b = measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world,
+                            args.batch_targets)
+        b.pop("_samples", None)
+        return {"batched": b}
     if args.only == "many":
         return {"many": measure_many(rr, dev, stream, opts)}
     if args.only == "learned":
@@ -867,7 +895,7 @@ def run_ours(args, rank, world, local):
     parity_proc = None
     tmpdir = tempfile.mkdtemp(prefix="rr_parity_")
     if rank == 0 and args.workload == WORKLOAD and not args.no_parity:
-        parity_proc, parity_path = start_parity(X, y, p, tmpdir)
+        parity_proc, parity_path = start_parity(X, y, p, tmpdir, batch=not args.no_batch)
     for _ in range(max(3, args.warmup)):
         infos = step()
     for inf in infos:
@@ -935,7 +963,13 @@ def run_ours(args, rank, world, local):
     small = measure_small_fp64(rr, dev) if not args.no_small else None
     parity = None
     if parity_proc is not None:
-        parity = finish_parity(parity_proc, parity_path, [w.cpu().numpy() for w in W], lams)
+        samples = batched.pop("_samples", None) if batched else None
+        parity, bpar = finish_parity(parity_proc, parity_path, [w.cpu().numpy() for w in W], lams,
+                                     W_batch=samples)
+        if batched is not None:
+            batched["parity"] = bpar
+    elif batched is not None:
+        batched.pop("_samples", None)
     last = all_infos[-1]
     out = {
         "metric": METRIC, "value": round(value, 5), "unit": "s", "n_gpus": world,
