@@ -55,6 +55,9 @@ def parse():
                     help="only the Gibbs-sampling section")
     ap.add_argument("--no-leader", action="store_true",
                     help="skip the leader-follower section")
+    ap.add_argument("--many-workload", default="uneven_12_dense4",
+                    help="the independent-problem set of --only many (uneven_28_dense4: the "
+                         "specified 28 + 4 problems, minutes of host generation)")
     ap.add_argument("--only-leader", action="store_true",
                     help="only the leader-follower section (--leader-tol2 list)")
     ap.add_argument("--leader-tol2", default="",
@@ -639,16 +642,36 @@ def measure_dense_only(rr, dev, stream, opts):
     return out
 
 
-def measure_many(rr, dev, stream, opts):
+def measure_many(rr, dev, stream, opts, name="uneven_12_dense4"):
     """Independent problems of uneven sizes: rr_solve_many (all PCG loops in one
     graph) against rr_solve one problem after the other, same handles (setups
-    excluded from both; they are reported apart)."""
+    excluded from both; they are reported apart). The problems are generated
+    one at a time and only their handles kept. The binary problem with the
+    fewest nonzeros is checked against the oracle's exact solution (its own
+    clustering, PCG to 1e-12, in a spawned process that runs meanwhile)."""
+    import multiprocessing as mp
     import torch
     from gen import synth
-    name = "uneven_12_dense4"
-    probs = synth.many_workload(name)
+    params = synth.many_params(name)
+    binary = [q for q in params if not q.get("dense")]
+    q0 = min(binary, key=lambda q: q["n"] * q["d"] * q["density"])
+    X0, y0 = synth.many_problem(q0)
+    tmpdir = tempfile.mkdtemp(prefix="rr_many_")
+    ppath = os.path.join(tmpdir, "parity.npz")
+    pproc = mp.get_context("spawn").Process(
+        target=_parity_worker,
+        args=((q0["n"], q0["d"], q0["density"], 1.1, q0["seed"]), q0["k"], q0["seed"],
+              [(q0["lam"], y0)], ppath, max(1, (os.cpu_count() or 4) // 2 - 1)), daemon=False)
+    pproc.start()
+    del X0
+    probs = []
     hs, ys, ws, setup_ms = [], [], [], []
-    for X, y, p in probs:
+    t_gen = 0.0
+    for p in params:
+        t0 = time.time()
+        X, y = synth.many_problem(p)
+        t_gen += time.time() - t0
+        probs.append((X.shape if p.get("dense") else (X.n_rows, X.n_cols, X.nnz), p))
         if p.get("dense"):
             o = {key: v for key, v in opts.items() if key not in ("gram", "gather", "split_head")}
             h = rr.rr_setup_dense(torch.as_tensor(X, device=dev), p["lam"], p["k"],
@@ -660,9 +683,11 @@ def measure_many(rr, dev, stream, opts):
         rp = torch.as_tensor(X.row_ptr, device=dev)
         ci = torch.as_tensor(X.col_idx, device=dev)
         h = rr.rr_setup(rp, ci, X.n_rows, X.n_cols, p["lam"], p["k"], **dict(opts, seed=p["seed"]))
+        del rp, ci
         hs.append(h)
         ys.append(torch.as_tensor(y, device=dev))
         ws.append(torch.empty(X.n_cols, dtype=torch.float64, device=dev))
+        del X
     out = rr.rr_solve_many(hs, ys, ws, tol=TOL, stream=stream)   # warm-up
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     torch.cuda.synchronize(dev)
@@ -676,16 +701,30 @@ def measure_many(rr, dev, stream, opts):
     e[3].record(stream)
     torch.cuda.synchronize(dev)
     t_many, t_seq = e[0].elapsed_time(e[1]) / 1e3, e[2].elapsed_time(e[3]) / 1e3
-    sizes = [(X.shape[0], X.shape[1], X.size) if p.get("dense") else (X.n_rows, X.n_cols, X.nnz)
-             for X, _, p in probs]
+    sizes = [(s[0], s[1], s[0] * s[1]) if p.get("dense") else tuple(s) for s, p in probs]
     dense_apply = None
-    for h, (X, _, p) in zip(hs, probs):
+    for h, (s, p) in zip(hs, probs):
         if p.get("dense"):
-            dense_apply = measure_dense_apply(rr, h, X.shape[0], X.shape[1], dev, stream)
+            dense_apply = measure_dense_apply(rr, h, s[0], s[1], dev, stream)
             break
+    i0 = params.index(q0)
+    w0 = ws[i0].cpu().numpy()
     for h in hs:
         rr.rr_free(h)
+    pproc.join(900)
+    parity = {"error": "the oracle's reference solve did not finish"}
+    if not pproc.is_alive() and os.path.exists(ppath):
+        d = np.load(ppath)
+        wr = d["w_ref"][0]
+        err = float(np.linalg.norm(w0 - wr) / np.linalg.norm(wr))
+        eo = float(np.linalg.norm(d["w_orc"][0] - wr) / np.linalg.norm(wr))
+        parity = {"problem": i0, "n_d": [q0["n"], q0["d"]], "err_vs_oracle": err,
+                  "oracle_err_at_tol": eo, "bar": max(1e-6, SOLUTION_SPREAD * eo),
+                  "within_bar": bool(err <= max(1e-6, SOLUTION_SPREAD * eo))}
+    elif pproc.is_alive():
+        pproc.terminate()
     return {"workload": name, "problems": len(probs), "value": round(t_many, 4), "unit": "s",
+            "generation_s": round(t_gen, 1), "parity": parity,
             "sequential_s": round(t_seq, 4), "speedup_vs_sequential": round(t_seq / t_many, 2),
             "setup_s_total": round(sum(i["setup_ms"] for i in singles) / 1e3, 3),
             "iters": [i["iters"] for i in out["infos"]],
@@ -854,7 +893,7 @@ def run_ours(args, rank, world, local):
         b.pop("_samples", None)
         return {"batched": b}
     if args.only == "many":
-        return {"many": measure_many(rr, dev, stream, opts)}
+        return {"many": measure_many(rr, dev, stream, opts, args.many_workload)}
     if args.only == "learned":
         return {"learned": measure_learned(rr, X, row_ptr, col_idx, k, opts, dev, stream,
                                            n_pairs=args.pairs)}

@@ -272,15 +272,21 @@ BATCH_WORKLOADS = {
 
 
 # independent problems of uneven sizes (Zipf s = 1.1 binary X, lambda = 1e-2,
-# k = d // 100): n ~ U[10k, 100k], d ~ U[5k, 40k], density ~ U[0.1%, 1%],
-# problem i drawn from seed i (a scaled stand-in of 28 problems up to
-# 400,000 x 150,000, whose generation on the host alone would take minutes)
-# "uneven_12_dense4" adds the four dense problems at full size: 50,000 x 4,000
-# float32 AR(1) (rho = 0.9), k = 40, drawn from seeds 12..15.
+# k = d // 100), problem i drawn from seed i, density ~ U[0.1%, 1%]:
+#   "uneven_28_dense4": 28 binary problems, n ~ U[10k, 400k], d ~ U[5k, 150k]
+#     (about 2.55e9 nonzeros in all: minutes of host generation), and four
+#     dense problems of 50,000 x 4,000 float32 AR(1) (rho = 0.9), k = 40,
+#     seeds 28..31;
+#   "uneven_12_dense4": a scaled stand-in, 12 binary problems with
+#     n ~ U[10k, 100k], d ~ U[5k, 40k], and the same four dense problems
+#     (seeds 12..15).
 MANY_WORKLOADS = {"uneven_12": dict(n_problems=12, n=(10_000, 100_000), d=(5_000, 40_000),
                                     density=(0.001, 0.01), lam=1e-2),
                   "uneven_12_dense4": dict(n_problems=12, n=(10_000, 100_000), d=(5_000, 40_000),
                                            density=(0.001, 0.01), lam=1e-2,
+                                           n_dense=4, dense=(50_000, 4_000), rho=0.9),
+                  "uneven_28_dense4": dict(n_problems=28, n=(10_000, 400_000),
+                                           d=(5_000, 150_000), density=(0.001, 0.01), lam=1e-2,
                                            n_dense=4, dense=(50_000, 4_000), rho=0.9)}
 
 
@@ -303,18 +309,20 @@ def many_params(name: str):
     return out
 
 
+def many_problem(q):
+    """(X, y) of one problem of a set (params from many_params)."""
+    if q.get("dense"):
+        X = dense_ar1(q["n"], q["d"], q["rho"], q["seed"])
+    else:
+        X = zipf_binary(q["n"], q["d"], q["density"], 1.1, q["seed"])
+    y, _ = ridge_targets(X, q["seed"])
+    return X, y
+
+
 def many_workload(name: str):
     """[(X, y, params)] of a named set of independent problems (X a CSR
     pattern, or a dense float32 array when params["dense"])."""
-    out = []
-    for q in many_params(name):
-        if q.get("dense"):
-            X = dense_ar1(q["n"], q["d"], q["rho"], q["seed"])
-        else:
-            X = zipf_binary(q["n"], q["d"], q["density"], 1.1, q["seed"])
-        y, _ = ridge_targets(X, q["seed"])
-        out.append((X, y, q))
-    return out
+    return [many_problem(q) + (q,) for q in many_params(name)]
 
 
 def batch_workload(name: str):
