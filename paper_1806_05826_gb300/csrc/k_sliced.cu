@@ -308,6 +308,22 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather(
 // values as in gather8, then the scan tree, then the carry), so every run
 // gives identical bits.
 constexpr int kStreamUnroll = 2;   // steps per prefetched group
+constexpr int kStreamAhead = 3;    // groups whose words are prefetched into L2 ahead (0: none)
+
+// A bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// The words [a, b) of a range: their index words and their metadata (the
+// latter rounded inward to 16-byte boundaries, never past the array's end).
+__device__ __forceinline__ void prefetch_words(const uint4 *idx, const int32_t *wmeta, int32_t a,
+                                               int32_t b) {
+  if (a >= b) return;
+  prefetch_l2(idx + a, (uint32_t)(b - a) * 16u);
+  const int32_t ma = (a + 3) & ~3, mb = b & ~3;
+  if (ma < mb) prefetch_l2(wmeta + ma, (uint32_t)(mb - ma) * 4u);
+}
 constexpr int kStreamThreads = 512;   // 16 warps, two CTAs per SM (two slices resident)
 constexpr int kStreamRanges = 32;     // word ranges per task (each warp takes two)
 __global__ void __launch_bounds__(kStreamThreads, 2) k_stream_gather(
@@ -355,9 +371,16 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_stream_gather(
       m[u] = w < w1 ? __ldg(wmeta + w) : -2;   // -2: past the range
     }
   };
+  constexpr int32_t kGroup = 32 * kStreamUnroll;
+  if (kStreamAhead > 0 && lane == 0)
+    prefetch_words(P.idx, wmeta, min(w1, w0 + kGroup), min(w1, w0 + kGroup * (kStreamAhead + 1)));
   if (w0 < w1) load(w0, qa, ma);
-  for (int32_t c = w0; c < w1; c += 32 * kStreamUnroll) {   // warp-uniform
-    if (c + 32 * kStreamUnroll < w1) load(c + 32 * kStreamUnroll, qn, mn);
+  for (int32_t c = w0; c < w1; c += kGroup) {   // warp-uniform
+    if (kStreamAhead > 0 && lane == 0) {
+      const int32_t a = c + kGroup * (kStreamAhead + 1);
+      prefetch_words(P.idx, wmeta, min(w1, a), min(w1, a + kGroup));
+    }
+    if (c + kGroup < w1) load(c + kGroup, qn, mn);
 #pragma unroll
     for (int u = 0; u < kStreamUnroll; ++u) {
       if (c + 32 * u >= w1) break;   // warp-uniform
