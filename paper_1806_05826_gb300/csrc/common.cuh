@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -27,6 +28,29 @@ extern thread_local int64_t rr_launch_counter;
     rr_status s_ = (call);               \
     if (s_ != RR_OK) return s_;          \
   } while (0)
+
+// A named NVTX range over a scope (for nsys and ncu's NVTX filters; a no-op
+// without a tool attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
+// The setup's phases as consecutive NVTX ranges: next(name) closes the open
+// one and opens the next; the last one closes with the object.
+struct NvtxPhases {
+  bool open = false;
+  void next(const char *name) {
+    if (open) nvtxRangePop();
+    nvtxRangePushA(name);
+    open = true;
+  }
+  ~NvtxPhases() {
+    if (open) nvtxRangePop();
+  }
+};
 
 // Every kernel launch goes through this so launches can be counted.
 #define RR_LAUNCH(kernel, grid, block, smem, stream, ...)                          \

@@ -1286,6 +1286,7 @@ void batch_free(BatchState *B) {
 
 extern "C" rr_status rr_solve_batch(rr_handle *h, int32_t nrhs, const double *Y, int32_t nlam,
                                     const double *lambdas, double *W, double tol, rr_info *infos) {
+  NvtxRange nvtx_range("rr_solve_batch");
   using namespace rr;
   if (!h || !Y || !W || !lambdas || nrhs < 1 || nlam < 1 || !(tol > 0.0 && tol < 1.0)) {
     rr_set_error("rr_solve_batch: NULL pointer, nrhs or nlam < 1, or tol not in (0, 1)");
@@ -1459,6 +1460,7 @@ extern "C" rr_status rr_solve_batch(rr_handle *h, int32_t nrhs, const double *Y,
 extern "C" rr_status rr_harvest(rr_handle *h, int32_t nrhs, const double *Y, double lambda,
                                 const double *Wref, double tol, int32_t max_iter, float *Xp,
                                 float *Tp, int64_t max_pairs, int64_t *n_pairs) {
+  NvtxRange nvtx_range("rr_harvest");
   using namespace rr;
   if (!h || !Y || !Wref || !Xp || !Tp || !n_pairs || nrhs < 1 || max_iter < 1 || max_pairs < 1 ||
       !(lambda > 0.0) || !isfinite(lambda) || !(tol > 0.0 && tol < 1.0)) {

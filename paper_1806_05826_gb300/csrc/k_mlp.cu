@@ -849,6 +849,7 @@ rr_status rr_mlp_grad(rr_mlp *m, int32_t B, const float *X, const float *T, floa
 
 rr_status rr_mlp_train(rr_mlp *m, int64_t n_pairs, const float *Xp, const float *Tp, int32_t batch,
                        int32_t steps, float lr, uint64_t seed, float *loss_host) {
+  NvtxRange nvtx_range("rr_mlp_train");
   if (!m || !Xp || !Tp || n_pairs < 1 || batch < 1 || batch > m->max_batch || steps < 0 ||
       !(lr > 0.0f)) {
     rr_set_error("rr_mlp_train: bad arguments");

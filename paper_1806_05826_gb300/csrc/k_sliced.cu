@@ -24,6 +24,7 @@
 // offsets of one word of the chunk, then every piece sums its words' partial
 // sums in order: the same operations in the same order as the lane-per-piece
 // form, so both forms give identical bits.
+#include <cmath>
 #include <type_traits>
 #include <vector>
 
@@ -135,16 +136,22 @@ __global__ void k_fill_pieces(int64_t n_outer, int32_t nb, int32_t W,
 
 // task t of slice b starts at the first piece whose start word reaches
 // word_begin(b) + t * words(b) / T
-__global__ void k_tasks(int32_t nb, int32_t T, int64_t n_outer, const int64_t *__restrict__ word_off,
+__global__ void k_tasks(int32_t nb, const int32_t *__restrict__ task_base, int64_t n_outer,
+                        const int64_t *__restrict__ word_off,
                         const int64_t *__restrict__ piece_off, const int32_t *__restrict__ pw,
                         int32_t *__restrict__ task_slice, int32_t *__restrict__ task_p) {
-  const int32_t total = nb * T;
+  const int32_t total = task_base[nb];
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= total; i += gridDim.x * blockDim.x) {
     if (i == total) {
       task_p[total] = (int32_t)piece_off[(int64_t)nb * n_outer];
       continue;
     }
-    const int32_t b = i / T, t = i % T;
+    int32_t bl = 0, bh = nb - 1;   // the slice: the last b with task_base[b] <= i
+    while (bl < bh) {
+      const int32_t mid = (bl + bh + 1) >> 1;
+      if (task_base[mid] <= i) bl = mid; else bh = mid - 1;
+    }
+    const int32_t b = bl, t = i - task_base[b], T = task_base[b + 1] - task_base[b];
     const int64_t wb = word_off[(int64_t)b * n_outer], we = word_off[(int64_t)(b + 1) * n_outer];
     const int64_t pb = piece_off[(int64_t)b * n_outer], pe = piece_off[(int64_t)(b + 1) * n_outer];
     const int64_t target = wb + (we - wb) * t / T;
@@ -308,22 +315,7 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather(
 // values as in gather8, then the scan tree, then the carry), so every run
 // gives identical bits.
 constexpr int kStreamUnroll = 2;   // steps per prefetched group
-constexpr int kStreamAhead = 3;    // groups whose words are prefetched into L2 ahead (0: none)
 
-// A bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
-__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-// The words [a, b) of a range: their index words and their metadata (the
-// latter rounded inward to 16-byte boundaries, never past the array's end).
-__device__ __forceinline__ void prefetch_words(const uint4 *idx, const int32_t *wmeta, int32_t a,
-                                               int32_t b) {
-  if (a >= b) return;
-  prefetch_l2(idx + a, (uint32_t)(b - a) * 16u);
-  const int32_t ma = (a + 3) & ~3, mb = b & ~3;
-  if (ma < mb) prefetch_l2(wmeta + ma, (uint32_t)(mb - ma) * 4u);
-}
 constexpr int kStreamThreads = 512;   // 16 warps, two CTAs per SM (two slices resident)
 constexpr int kStreamRanges = 32;     // word ranges per task (each warp takes two)
 __global__ void __launch_bounds__(kStreamThreads, 2) k_stream_gather(
@@ -372,14 +364,8 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_stream_gather(
     }
   };
   constexpr int32_t kGroup = 32 * kStreamUnroll;
-  if (kStreamAhead > 0 && lane == 0)
-    prefetch_words(P.idx, wmeta, min(w1, w0 + kGroup), min(w1, w0 + kGroup * (kStreamAhead + 1)));
   if (w0 < w1) load(w0, qa, ma);
   for (int32_t c = w0; c < w1; c += kGroup) {   // warp-uniform
-    if (kStreamAhead > 0 && lane == 0) {
-      const int32_t a = c + kGroup * (kStreamAhead + 1);
-      prefetch_words(P.idx, wmeta, min(w1, a), min(w1, a + kGroup));
-    }
     if (c + kGroup < w1) load(c + kGroup, qn, mn);
 #pragma unroll
     for (int u = 0; u < kStreamUnroll; ++u) {
@@ -939,13 +925,32 @@ rr_status sliced_build(int64_t n_outer, int64_t n_inner, const int64_t *outer_pt
         RR_CUDA(cudaMemcpyAsync(P.heavy, hv.data(), sizeof(int32_t) * hv.size(),
                                 cudaMemcpyHostToDevice, st));
     }
-    // tasks: about two CTAs per SM in total, split evenly over the slices
-    P.tasks_per_slice = std::max<int32_t>(1, (2 * kSMs + P.nb - 1) / P.nb);
-    P.ntasks = P.nb * P.tasks_per_slice;
+    // tasks: about two CTAs per SM in total, given to the slices in proportion
+    // to their words (at least one each), so that the tasks are of one size
+    std::vector<int32_t> task_base(P.nb + 1, 0);
+    {
+      std::vector<int64_t> wsl(P.nb + 1);
+      for (int32_t b = 0; b <= P.nb; ++b)
+        RR_CUDA(cudaMemcpyAsync(&wsl[b], word_off + (int64_t)b * n_outer, sizeof(int64_t),
+                                cudaMemcpyDeviceToHost, st));
+      RR_CUDA(cudaStreamSynchronize(st));
+      const double per_task = (double)std::max<int64_t>(1, P.nwords) / (2.0 * kSMs);
+      for (int32_t b = 0; b < P.nb; ++b) {
+        const int64_t t = llround((double)(wsl[b + 1] - wsl[b]) / per_task);
+        task_base[b + 1] = task_base[b] + (int32_t)std::max<int64_t>(1, t);
+      }
+    }
+    P.ntasks = task_base[P.nb];
     RR_CUDA(cudaMalloc(&P.task_slice, sizeof(int32_t) * P.ntasks));
     RR_CUDA(cudaMalloc(&P.task_p, sizeof(int32_t) * (P.ntasks + 1)));
-    RR_LAUNCH(k_tasks, grid_for(P.ntasks + 1, kThreads), kThreads, 0, st, P.nb,
-              P.tasks_per_slice, n_outer, word_off, piece_off, P.pw, P.task_slice, P.task_p);
+    int32_t *d_base = nullptr;
+    RR_CUDA(cudaMalloc(&d_base, sizeof(int32_t) * (P.nb + 1)));
+    RR_CUDA(cudaMemcpyAsync(d_base, task_base.data(), sizeof(int32_t) * (P.nb + 1),
+                            cudaMemcpyHostToDevice, st));
+    RR_LAUNCH(k_tasks, grid_for(P.ntasks + 1, kThreads), kThreads, 0, st, P.nb, d_base, n_outer,
+              word_off, piece_off, P.pw, P.task_slice, P.task_p);
+    RR_CUDA(cudaStreamSynchronize(st));
+    cudaFree(d_base);
     RR_CUDA(cudaMalloc(&P.order, sizeof(int32_t) * std::max<int64_t>(1, P.npieces)));
     RR_LAUNCH(k_order_pieces, P.ntasks, kThreads, 0, st, P.task_p, P.pw, P.order);
     // chunks of the staged (FP32) gather, when its shared memory fits

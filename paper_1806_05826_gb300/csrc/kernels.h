@@ -222,7 +222,7 @@ struct SlicedView {
 };
 struct SlicedPattern {
   int64_t n_outer = 0, n_inner = 0, nwords = 0, npieces = 0;
-  int32_t nb = 0, W = 0, ntasks = 0, tasks_per_slice = 0;
+  int32_t nb = 0, W = 0, ntasks = 0;
   int32_t *pw = nullptr;         // [npieces+1] first word of each piece (slice-major)
   int32_t *slot = nullptr;       // [npieces]   sum slot of each piece (outer-major)
   int32_t *slot_ptr = nullptr;   // [n_outer+1] slots of each outer index

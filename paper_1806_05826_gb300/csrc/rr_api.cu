@@ -245,11 +245,18 @@ rr_status setup_impl_dense(rr_handle *h, const rr_matrix *X, double lambda, int3
   cudaStream_t st = h->st;
   DevArena &m = h->mem;
   auto t_last = std::chrono::steady_clock::now();
+  static const char *const kPhaseNames[8] = {
+      "rr_setup: copy and validate", "rr_setup: CSC build", "rr_setup: clustering (seeding)",
+      "rr_setup: clustering (Lloyd)", "rr_setup: clusters", "rr_setup: coarse Gram",
+      "rr_setup: coarse factor", "rr_setup: patterns and workspace"};
+  NvtxPhases ranges;
+  ranges.next(kPhaseNames[0]);
   auto phase = [&](int i) -> rr_status {
     RR_CUDA(cudaStreamSynchronize(st));
     const auto now = std::chrono::steady_clock::now();
     h->phase_ms[i] += std::chrono::duration<double, std::milli>(now - t_last).count();
     t_last = now;
+    if (i + 1 < 8) ranges.next(kPhaseNames[i + 1]);
     return RR_OK;
   };
   const int64_t N = X->n_rows, F = X->n_cols;
@@ -440,11 +447,18 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   DevArena &m = h->mem;
   auto t_last = std::chrono::steady_clock::now();
   // wall time of a finished phase (the stream is drained so device work counts)
+  static const char *const kPhaseNames[8] = {
+      "rr_setup: copy and validate", "rr_setup: CSC build", "rr_setup: clustering (seeding)",
+      "rr_setup: clustering (Lloyd)", "rr_setup: clusters", "rr_setup: coarse Gram",
+      "rr_setup: coarse factor", "rr_setup: patterns and workspace"};
+  NvtxPhases ranges;
+  ranges.next(kPhaseNames[0]);
   auto phase = [&](int i) -> rr_status {
     RR_CUDA(cudaStreamSynchronize(st));
     const auto now = std::chrono::steady_clock::now();
     h->phase_ms[i] += std::chrono::duration<double, std::milli>(now - t_last).count();
     t_last = now;
+    if (i + 1 < 8) ranges.next(kPhaseNames[i + 1]);
     return RR_OK;
   };
   const int64_t N = X->n_rows, F = X->n_cols, nnz = X->nnz;
@@ -1444,6 +1458,7 @@ int64_t rr_launch_count(void) { return rr_launch_counter; }
 
 rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_options *o,
                    rr_handle **out) {
+  NvtxRange nvtx_range("rr_setup");
   g_err[0] = 0;
   if (!X || !out) {
     rr_set_error("rr_setup: X and out must not be NULL");
@@ -1560,6 +1575,7 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
 }
 
 rr_status rr_set_lambda(rr_handle *h, double lambda) {
+  NvtxRange nvtx_range("rr_set_lambda");
   if (!h) {
     rr_set_error("rr_set_lambda: NULL handle");
     return RR_INVALID_ARG;
@@ -1577,6 +1593,7 @@ rr_status rr_set_lambda(rr_handle *h, double lambda) {
 }
 
 rr_status rr_prepare_lambdas(rr_handle *h, const double *lambdas, int32_t n) {
+  NvtxRange nvtx_range("rr_prepare_lambdas");
   if (!h || (n > 0 && !lambdas) || n < 0 || n > rr_handle::kPrepared) {
     rr_set_error("rr_prepare_lambdas: need a handle and 0 <= n <= %d lambdas",
                  rr_handle::kPrepared);
@@ -1603,6 +1620,7 @@ rr_status rr_prepare_lambdas(rr_handle *h, const double *lambdas, int32_t n) {
 }
 
 rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info *info) {
+  NvtxRange nvtx_range("rr_solve");
   if (!h || !y || !w) {
     rr_set_error("rr_solve: handle, y and w must not be NULL");
     return RR_INVALID_ARG;
@@ -1636,6 +1654,7 @@ rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info
 
 rr_status rr_solve_fcg(rr_handle *h, const rr_mlp *net, const double *y, double *w, double tol,
                        rr_info *info) {
+  NvtxRange nvtx_range("rr_solve_fcg");
   if (!h || !y || !w) {
     rr_set_error("rr_solve_fcg: handle, y and w must not be NULL");
     return RR_INVALID_ARG;
@@ -1677,6 +1696,7 @@ rr_status rr_solve_fcg(rr_handle *h, const rr_mlp *net, const double *y, double 
 
 rr_status rr_solve_many(int32_t nprob, rr_handle *const *hs, const double *const *ys,
                         double *const *ws, double tol, void *stream, rr_info *infos) {
+  NvtxRange nvtx_range("rr_solve_many");
   if (nprob < 1 || !hs || !ys || !ws || !(tol > 0.0 && tol < 1.0)) {
     rr_set_error("rr_solve_many: nprob < 1, NULL arrays or tol not in (0, 1)");
     return RR_INVALID_ARG;
@@ -1815,6 +1835,7 @@ rr_status rr_get_coarse(const rr_handle *h, double *Ac_host, int64_t *G_host) {
 rr_status rr_bayes(rr_handle *h, const double *y, const rr_bayes_params *p, int32_t n_samples,
                    int32_t burnin, double *w_mean, double *lam_trace, double *tau_trace,
                    int32_t *iters) {
+  NvtxRange nvtx_range("rr_bayes");
   if (!h || !y || !p) {
     rr_set_error("rr_bayes: handle, y and params must not be NULL");
     return RR_INVALID_ARG;
