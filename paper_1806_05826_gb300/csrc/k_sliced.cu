@@ -320,29 +320,41 @@ constexpr int kStreamThreads = 512;   // 16 warps, two CTAs per SM (two slices r
 constexpr int kStreamRanges = 32;     // word ranges per task (each warp takes two)
 __global__ void __launch_bounds__(kStreamThreads, 2) k_stream_gather(
     SlicedView P, const int32_t *__restrict__ wmeta, const int32_t *__restrict__ wstart,
-    const float *__restrict__ xq, float *__restrict__ out, const int32_t *__restrict__ stop) {
+    const float *__restrict__ xq, float *__restrict__ out, const int32_t *__restrict__ stop,
+    int32_t *err) {
   pdl_wait();
   if (stop && *stop) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float *xs = reinterpret_cast<float *>(smem_raw);
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw + sizeof(float) * ((P.W + 1 + 3) & ~3));
+  int32_t *abort_flag = reinterpret_cast<int32_t *>(bar + 1);
   const int task = blockIdx.x;
   const int32_t b = P.task_slice[task];
   const int64_t base = (int64_t)b * P.W;
   const int64_t width = min((int64_t)P.W, P.n_inner - base);
-  for (int i0 = threadIdx.x; i0 <= P.W; i0 += 8 * kStreamThreads) {
-    float v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int i = i0 + u * kStreamThreads;
-      v[u] = i < width ? xq[base + i] : 0.f;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int i = i0 + u * kStreamThreads;
-      if (i <= P.W) xs[i] = v[u];
+  // the vector slice: its 16-byte aligned head by one bulk copy (completing on
+  // an mbarrier), the rest and the zero padding by plain loads meanwhile
+  const int64_t nbulk = (base & 3) == 0 ? (width & ~(int64_t)3) : 0;
+  if (threadIdx.x == 0) {
+    *abort_flag = 0;
+    if (nbulk > 0) {
+      tc::mbar_init(bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      tc::mbar_expect_tx(bar, (uint32_t)(nbulk * 4));
+      tc::bulk_load(xs, xq + base, (uint32_t)(nbulk * 4), bar);
     }
   }
+  for (int i = (int)nbulk + threadIdx.x; i <= P.W; i += kStreamThreads)
+    xs[i] = i < width ? xq[base + i] : 0.f;
   __syncthreads();
+  if (nbulk > 0 && !tc::mbar_wait(bar, 0, abort_flag)) {
+    set_dev_error(err, DEV_TIMEOUT);
+    atomicExch(abort_flag, 1);
+    // the copy lands before this thread leaves the CTA's shared memory
+    const int32_t never = 0;
+    (void)tc::mbar_wait(bar, 0, &never);
+    return;
+  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint4 pad = make_uint4(P.W | (P.W << 16), P.W | (P.W << 16), P.W | (P.W << 16),
                                P.W | (P.W << 16));
@@ -767,6 +779,10 @@ __global__ void k_to_i32(int64_t n, const int64_t *__restrict__ in, int32_t *__r
 template <typename T>
 size_t slice_smem(int32_t W) { return sizeof(T) * ((size_t)W + 1); }
 
+// the stream gather: the FP32 slice (rounded up to 16 bytes), its mbarrier and
+// an abort flag
+inline size_t stream_smem(int32_t W) { return sizeof(float) * (size_t)((W + 1 + 3) & ~3) + 16; }
+
 template <typename T>
 size_t staged_smem(int32_t W) {
   return sizeof(float) * (size_t)((W + 1 + 3) & ~3) + (size_t)kTeams * kTeamSmem + 16;
@@ -810,17 +826,17 @@ rr_status launch_gather(const SlicedPattern &P, const T *xq, const int32_t *stop
       static bool attr = false;
       if (!attr) {
         RR_CUDA(cudaFuncSetAttribute(k_stream_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)slice_smem<float>(kSliceMax)));
+                                     (int)stream_smem(kSliceMax)));
         RR_CUDA(cudaFuncSetAttribute(k_stream_gather,
                                      cudaFuncAttributePreferredSharedMemoryCarveout, 100));
         attr = true;
       }
       if (pdl)
-        RR_LAUNCH_PDL(k_stream_gather, P.ntasks, kStreamThreads, slice_smem<float>(P.W), st,
-                      P.view(), P.wmeta, P.wstart, xq, out, stop);
+        RR_LAUNCH_PDL(k_stream_gather, P.ntasks, kStreamThreads, stream_smem(P.W), st,
+                      P.view(), P.wmeta, P.wstart, xq, out, stop, P.err);
       else
-        RR_LAUNCH(k_stream_gather, P.ntasks, kStreamThreads, slice_smem<float>(P.W), st, P.view(),
-                  P.wmeta, P.wstart, xq, out, stop);
+        RR_LAUNCH(k_stream_gather, P.ntasks, kStreamThreads, stream_smem(P.W), st, P.view(),
+                  P.wmeta, P.wstart, xq, out, stop, P.err);
       return RR_OK;
     }
   }
