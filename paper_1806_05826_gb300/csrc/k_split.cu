@@ -113,10 +113,13 @@ __global__ void __launch_bounds__(kThreads) k_split_rows(
     for (int64_t i = threadIdx.x; i < qend - qbase; i += blockDim.x)
       cp_async4(sslot + i, tsum + qbase + i);
   }
-  if (threadIdx.x == 0) {   // sum of v over the all-ones columns, in their order
+  if (warp == 0) {   // sum of v over the all-ones columns: the lanes' loads in
+                     // flight together, then a fixed shuffle tree
     float a = 0.f;
-    for (int32_t i = 0; i < n_ones; ++i) a += x32[ones[i]];
-    s_ones = a;
+    for (int32_t i = lane; i < n_ones; i += 32) a += x32[ones[i]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) s_ones = a;
   }
   float vh[32];
 #pragma unroll
@@ -231,27 +234,48 @@ __global__ void __launch_bounds__(kThreads) k_split_epilogue(
     s = warp_sum(s);
     if (lane == 0) epilogue(ep, i, s, dot, wd);
   }
-  // every other feature: one lane each; the feature's vectors are loaded
-  // before its slot sums (eight slot loads in flight), so the two
-  // dependent rounds of loads overlap
+  // every other feature: one lane each, two features per lane at a time
+  // (feature i and i + stride, in that order, as the plain loop takes them);
+  // the features' vectors are loaded before their slot sums (eight slot loads
+  // in flight per feature), so the dependent rounds of loads overlap
   const bool need_r = ep.mode == CSC_PRE || ep.mode == CSC_POST || ep.mode == CSC_RESID;
-  for (int64_t i0 = warp * 32; i0 < F; i0 += nwarps * 32) {   // warp-uniform
-    const int64_t i = i0 + lane;
-    if (i < F && !is_spec[i]) {
-      const int32_t q0 = slot_ptr[i], q1 = slot_ptr[i + 1];
-      const double vi = ep.mode != CSC_RHS ? ep.v[i] : 0.0;
-      const double ri = need_r ? ep.r[i] : 0.0;
-      const double wdi = ep.mode == CSC_POST ? wd[i] : 0.0;
-      float s = 0.f;
-      for (int32_t q = q0; q < q1; q += 8) {
-        float t[8];
+  const int64_t stride = nwarps * 32;
+  for (int64_t i0 = warp * 32; i0 < F; i0 += 2 * stride) {   // warp-uniform
+    int64_t ii[2];
+    bool act[2];
+    int32_t q0[2], q1[2];
+    double vi[2], ri[2], wdi[2];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) t[u] = q + u < q1 ? tsum[q + u] : 0.f;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) s += t[u];
-      }
-      epilogue_values(ep, i, (double)s, vi, ri, wdi, dot);
+    for (int h = 0; h < 2; ++h) {
+      ii[h] = i0 + h * stride + lane;
+      act[h] = ii[h] < F && !is_spec[ii[h]];
+      q0[h] = act[h] ? slot_ptr[ii[h]] : 0;
+      q1[h] = act[h] ? slot_ptr[ii[h] + 1] : 0;
+      vi[h] = act[h] && ep.mode != CSC_RHS ? ep.v[ii[h]] : 0.0;
+      ri[h] = act[h] && need_r ? ep.r[ii[h]] : 0.0;
+      wdi[h] = act[h] && ep.mode == CSC_POST ? wd[ii[h]] : 0.0;
     }
+    float s[2] = {0.f, 0.f};
+    float t[2][8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[h][u] = q0[h] + u < q1[h] ? tsum[q0[h] + u] : 0.f;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s[h] += t[h][u];
+      for (int32_t q = q0[h] + 8; q < q1[h]; q += 8) {   // features with more than 8 slots
+        float w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) w[u] = q + u < q1[h] ? tsum[q + u] : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s[h] += w[u];
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (act[h]) epilogue_values(ep, ii[h], (double)s[h], vi[h], ri[h], wdi[h], dot);
   }
   const double tot = block_sum(dot, sm);
   if (threadIdx.x == 0 && ep.dot_part) ep.dot_part[blockIdx.x] = tot;
