@@ -304,17 +304,18 @@ __global__ void __launch_bounds__(kSliceThreads, 1) k_sliced_gather(
 
 // The streaming gather (FP32 piece sums). One CTA per task: the vector slice
 // in shared memory, then each of the 32 warps streams its own contiguous
-// range of the task's words (ranges start at piece boundaries), 32 words per
-// step and kStreamUnroll steps loaded ahead: lane i loads word i of the step
-// (a coalesced 512-byte load per warp) and its metadata, sums the word's 8
-// gathered values, and a segmented inclusive scan over the 32 lanes (segments
-// = pieces; a piece may continue from the previous step, whose running sum is
-// carried) gives each piece's sum at its last word, which stores it in the
-// piece's slot. No indirection before the loads: every load is coalesced and
-// many are in flight per warp. The sums have a fixed order (each word's 8
-// values as in gather8, then the scan tree, then the carry), so every run
-// gives identical bits.
-constexpr int kStreamUnroll = 2;   // steps per prefetched group
+// range of the task's words (ranges start at piece boundaries), 64 words per
+// step, the next step loaded ahead: lane l loads words 2l and 2l + 1 of the
+// step (coalesced) and their metadata, sums each word's 8 gathered values,
+// folds its two words into the sum of its open tail, and a segmented
+// inclusive scan of the tails over the 32 lanes (segments = pieces; a piece
+// may continue from the previous step, whose running sum is carried) gives the
+// running sum entering each lane, from which each piece's sum at its last word
+// follows; that word's lane stores it in the piece's slot. No indirection
+// before the loads: every load is coalesced and many are in flight per warp.
+// The sums have a fixed order (each word's 8 values as in gather8, then the
+// lane's two words, the scan tree and the carry), so every run gives
+// identical bits.
 
 constexpr int kStreamThreads = 512;   // 16 warps, two CTAs per SM (two slices resident)
 constexpr int kStreamRanges = 32;     // word ranges per task (each warp takes two)
@@ -363,47 +364,54 @@ __global__ void __launch_bounds__(kStreamThreads, 2) k_stream_gather(
   const int32_t w1 = wstart[task * (kStreamRanges + 1) + rg + 1];
   float carry = 0.f;   // running sum of the piece open at the end of the previous step
   bool open = false;
-  // two steps per group; the next group's loads are issued before this
-  // group is summed
-  uint4 qa[kStreamUnroll], qn[kStreamUnroll];
-  int32_t ma[kStreamUnroll], mn[kStreamUnroll];
+  // one step = 64 words, lane l taking words 2l and 2l + 1; the next step's
+  // loads are issued before this step is summed
+  uint4 qa[2], qn[2];
+  int32_t ma[2], mn[2];
   auto load = [&](int32_t c, uint4 *q, int32_t *m) {
 #pragma unroll
-    for (int u = 0; u < kStreamUnroll; ++u) {
-      const int32_t w = c + 32 * u + lane;
-      q[u] = w < w1 ? __ldg(P.idx + w) : pad;
-      m[u] = w < w1 ? __ldg(wmeta + w) : -2;   // -2: past the range
+    for (int h = 0; h < 2; ++h) {
+      const int32_t w = c + 2 * lane + h;
+      q[h] = w < w1 ? __ldg(P.idx + w) : pad;
+      m[h] = w < w1 ? __ldg(wmeta + w) : -2;   // -2: past the range
     }
   };
-  constexpr int32_t kGroup = 32 * kStreamUnroll;
   if (w0 < w1) load(w0, qa, ma);
-  for (int32_t c = w0; c < w1; c += kGroup) {   // warp-uniform
-    if (c + kGroup < w1) load(c + kGroup, qn, mn);
+  for (int32_t c = w0; c < w1; c += 64) {   // warp-uniform
+    if (c + 64 < w1) load(c + 64, qn, mn);
+    const float x0 = gather8(xs, qa[0]), x1 = gather8(xs, qa[1]);
+    // starts: element 0 of lane l starts a piece when element 1 of lane l - 1
+    // ended one (lane 0: when no piece is open); element 1 when element 0 did
+    const uint32_t ends1 = __ballot_sync(0xffffffffu, ma[1] >= 0);
+    const bool s0 = lane == 0 ? !open : ((ends1 >> (lane - 1)) & 1u) != 0;
+    const bool s1 = ma[0] >= 0;
+    // the lane's open tail (the sum since its last start, or of both words),
+    // then a segmented inclusive scan of the tails over the lanes (a segment
+    // begins at a lane holding a start; dist = lanes since it began)
+    float v = s1 ? x1 : x0 + x1;
+    const uint32_t starts = __ballot_sync(0xffffffffu, s0 || s1);
+    const uint32_t upto = starts & (0xffffffffu >> (31 - lane));
+    const int dist = upto ? lane - (31 - __clz((int)upto)) : 32;   // 32: began earlier
 #pragma unroll
-    for (int u = 0; u < kStreamUnroll; ++u) {
-      if (c + 32 * u >= w1) break;   // warp-uniform
-      float x = gather8(xs, qa[u]);
-      // pieces of this step: word i starts one when word i - 1 ended one (or
-      // i = 0 and no piece is open); dist = lanes since this lane's piece began
-      const uint32_t ends = __ballot_sync(0xffffffffu, ma[u] >= 0);
-      const uint32_t starts = (ends << 1) | (open ? 0u : 1u);
-      const uint32_t upto = starts & (0xffffffffu >> (31 - lane));
-      const int dist = upto ? lane - (31 - __clz((int)upto)) : 32;   // 32: began earlier
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const float xy = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d && dist >= d) x = xy + x;
-      }
-      if (!upto) x = carry + x;   // still in the piece carried from the previous step
-      if (ma[u] >= 0) out[ma[u]] = x;
-      carry = __shfl_sync(0xffffffffu, x, 31);
-      open = (__ballot_sync(0xffffffffu, ma[u] == -1) >> 31) & 1u;
-      if (!open) carry = 0.f;
+    for (int d = 1; d < 32; d <<= 1) {
+      const float vy = __shfl_up_sync(0xffffffffu, v, d);
+      if (lane >= d && dist >= d) v = vy + v;
     }
+    if (!upto) v = carry + v;   // still in the piece carried from the previous step
+    // the running sum entering this lane, then each word's running sum
+    float excl = __shfl_up_sync(0xffffffffu, v, 1);
+    if (lane == 0) excl = open ? carry : 0.f;
+    const float inc0 = s0 ? x0 : excl + x0;
+    const float inc1 = s1 ? x1 : inc0 + x1;
+    if (ma[0] >= 0) out[ma[0]] = inc0;
+    if (ma[1] >= 0) out[ma[1]] = inc1;
+    carry = __shfl_sync(0xffffffffu, inc1, 31);
+    open = (__ballot_sync(0xffffffffu, ma[1] == -1) >> 31) & 1u;
+    if (!open) carry = 0.f;
 #pragma unroll
-    for (int u = 0; u < kStreamUnroll; ++u) {
-      qa[u] = qn[u];
-      ma[u] = mn[u];
+    for (int h = 0; h < 2; ++h) {
+      qa[h] = qn[h];
+      ma[h] = mn[h];
     }
   }
   }
