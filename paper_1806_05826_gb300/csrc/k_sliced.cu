@@ -645,6 +645,47 @@ __global__ void k_chunk_fill(int32_t ntasks, const int32_t *__restrict__ task_p,
 // inside a word (both gather kernels read the same words, so they keep giving
 // identical bits).
 constexpr int kBalThreads = 64;
+// One group of n <= 32 words idx[w0 + stride l], the words one warp
+// instruction reads at once (thread-private rows of the block's shared arrays).
+__device__ void balance_group(uint4 *__restrict__ idx, int64_t w0, int stride, int n, int32_t W,
+                              uint16_t *outs, uint8_t *usedm, uint8_t *cnts) {
+  const uint16_t padv = (uint16_t)W;
+  for (int l = 0; l < n; ++l) usedm[l] = 0;
+  for (int u = 0; u < 8; ++u) {
+    for (int bk = 0; bk < 32; ++bk) cnts[bk] = 0;
+    for (int l = 0; l < n; ++l) {
+      const uint4 q = idx[w0 + (int64_t)stride * l];
+      const uint16_t off[8] = {(uint16_t)(q.x & 0xffffu), (uint16_t)(q.x >> 16),
+                               (uint16_t)(q.y & 0xffffu), (uint16_t)(q.y >> 16),
+                               (uint16_t)(q.z & 0xffffu), (uint16_t)(q.z >> 16),
+                               (uint16_t)(q.w & 0xffffu), (uint16_t)(q.w >> 16)};
+      const uint32_t used = usedm[l];
+      int best = 0, best_cost = 0x7fffffff;
+      uint16_t bo = padv;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (used & (1u << j)) continue;
+        const int cost = off[j] == padv ? -1 : (int)cnts[off[j] & 31];
+        if (cost < best_cost) {
+          best_cost = cost;
+          best = j;
+          bo = off[j];
+        }
+      }
+      usedm[l] = (uint8_t)(used | (1u << best));
+      outs[l * 8 + u] = bo;
+      if (bo != padv) cnts[bo & 31] += 1;
+    }
+  }
+  for (int l = 0; l < n; ++l) {
+    const uint16_t *o = &outs[l * 8];
+    idx[w0 + (int64_t)stride * l] = make_uint4((uint32_t)o[0] | ((uint32_t)o[1] << 16),
+                                               (uint32_t)o[2] | ((uint32_t)o[3] << 16),
+                                               (uint32_t)o[4] | ((uint32_t)o[5] << 16),
+                                               (uint32_t)o[6] | ((uint32_t)o[7] << 16));
+  }
+}
+
 __global__ void __launch_bounds__(kBalThreads) k_balance_words(int64_t n_chunks,
                                                                const int32_t *__restrict__ chunk_w,
                                                                int32_t W, uint4 *__restrict__ idx) {
@@ -654,47 +695,36 @@ __global__ void __launch_bounds__(kBalThreads) k_balance_words(int64_t n_chunks,
   __shared__ uint8_t cnts[kBalThreads][36];
   const int t = threadIdx.x;
   constexpr int kGroups = kChunkWords / 32;
-  const uint16_t padv = (uint16_t)W;
   for (int64_t g = (int64_t)blockIdx.x * kBalThreads + t; g < n_chunks * kGroups;
        g += (int64_t)gridDim.x * kBalThreads) {
     const int64_t c = g / kGroups;
     const int64_t w0 = (int64_t)chunk_w[c] + 32 * (g % kGroups), w1 = chunk_w[c + 1];
     if (w0 >= w1) continue;
     const int n = (int)min((int64_t)32, w1 - w0);
-    for (int l = 0; l < n; ++l) usedm[t][l] = 0;
-    for (int u = 0; u < 8; ++u) {
-      for (int bk = 0; bk < 32; ++bk) cnts[t][bk] = 0;
-      for (int l = 0; l < n; ++l) {
-        const uint4 q = idx[w0 + l];
-        const uint16_t off[8] = {(uint16_t)(q.x & 0xffffu), (uint16_t)(q.x >> 16),
-                                 (uint16_t)(q.y & 0xffffu), (uint16_t)(q.y >> 16),
-                                 (uint16_t)(q.z & 0xffffu), (uint16_t)(q.z >> 16),
-                                 (uint16_t)(q.w & 0xffffu), (uint16_t)(q.w >> 16)};
-        const uint32_t used = usedm[t][l];
-        int best = 0, best_cost = 0x7fffffff;
-        uint16_t bo = padv;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          if (used & (1u << j)) continue;
-          const int cost = off[j] == padv ? -1 : (int)cnts[t][off[j] & 31];
-          if (cost < best_cost) {
-            best_cost = cost;
-            best = j;
-            bo = off[j];
-          }
-        }
-        usedm[t][l] = (uint8_t)(used | (1u << best));
-        outs[t][l * 8 + u] = bo;
-        if (bo != padv) cnts[t][bo & 31] += 1;
+    balance_group(idx, w0, 1, n, W, outs[t], usedm[t], cnts[t]);
+  }
+}
+
+// The same for the streaming gather's reads: in every 64-word step of a warp's
+// range, lane l reads words 2l and 2l + 1, so the even and the odd words of
+// the step are the groups (one thread per range, its steps in turn).
+__global__ void __launch_bounds__(kBalThreads) k_balance_stream(int64_t n_ranges,
+                                                                const int32_t *__restrict__ wstart,
+                                                                int32_t W, uint4 *__restrict__ idx) {
+  __shared__ uint16_t outs[kBalThreads][32 * 8 + 2];
+  __shared__ uint8_t usedm[kBalThreads][36];
+  __shared__ uint8_t cnts[kBalThreads][36];
+  const int t = threadIdx.x;
+  for (int64_t g = (int64_t)blockIdx.x * kBalThreads + t; g < n_ranges;
+       g += (int64_t)gridDim.x * kBalThreads) {
+    const int64_t task = g / kStreamRanges, rg = g % kStreamRanges;
+    const int32_t w0 = wstart[task * (kStreamRanges + 1) + rg];
+    const int32_t w1 = wstart[task * (kStreamRanges + 1) + rg + 1];
+    for (int32_t c = w0; c < w1; c += 64)
+      for (int h = 0; h < 2; ++h) {
+        const int n = (int)min(32, (w1 - c - h + 1) / 2);
+        if (n > 0) balance_group(idx, c + h, 2, n, W, outs[t], usedm[t], cnts[t]);
       }
-    }
-    for (int l = 0; l < n; ++l) {
-      const uint16_t *o = &outs[t][l * 8];
-      idx[w0 + l] = make_uint4((uint32_t)o[0] | ((uint32_t)o[1] << 16),
-                               (uint32_t)o[2] | ((uint32_t)o[3] << 16),
-                               (uint32_t)o[4] | ((uint32_t)o[5] << 16),
-                               (uint32_t)o[6] | ((uint32_t)o[7] << 16));
-    }
   }
 }
 
@@ -889,7 +919,8 @@ rr_status gather_t(const SlicedPattern &P, const double *x, const SlicedPattern 
 }  // namespace
 
 rr_status sliced_build(int64_t n_outer, int64_t n_inner, const int64_t *outer_ptr,
-                       const int32_t *inner, SlicedPattern &P, int32_t *err, cudaStream_t st) {
+                       const int32_t *inner, SlicedPattern &P, int32_t *err, cudaStream_t st,
+                       bool chunks) {
   P = SlicedPattern{};
   P.err = err;
   P.n_outer = n_outer;
@@ -978,7 +1009,7 @@ rr_status sliced_build(int64_t n_outer, int64_t n_inner, const int64_t *outer_pt
     RR_CUDA(cudaMalloc(&P.order, sizeof(int32_t) * std::max<int64_t>(1, P.npieces)));
     RR_LAUNCH(k_order_pieces, P.ntasks, kThreads, 0, st, P.task_p, P.pw, P.order);
     // chunks of the staged (FP32) gather, when its shared memory fits
-    if (staged_smem(P.W) <= 227 * 1024) {
+    if (chunks && staged_smem(P.W) <= 227 * 1024) {
       int64_t *cbuf = nullptr;
       const int64_t nt1 = (int64_t)P.ntasks + 1;
       RR_CUDA(cudaMalloc(&cbuf, sizeof(int64_t) * (2 * nt1 + scan_scratch_len(nt1) + 8)));
@@ -1054,6 +1085,10 @@ rr_status sliced_build_stream(SlicedPattern &P, cudaStream_t st) {
               P.wmeta);
   RR_LAUNCH(k_warp_ranges, grid_for((int64_t)P.ntasks * 33, kThreads), kThreads, 0, st, P.ntasks,
             P.task_p, P.pw, P.wstart);
+  // the words' offsets ordered for the streaming gather's reads
+  const int64_t n_ranges = (int64_t)P.ntasks * kStreamRanges;
+  RR_LAUNCH(k_balance_stream, (unsigned)((n_ranges + kBalThreads - 1) / kBalThreads), kBalThreads,
+            0, st, n_ranges, P.wstart, P.W, P.idx);
   RR_CUDA(cudaStreamSynchronize(st));
   return RR_OK;
 }

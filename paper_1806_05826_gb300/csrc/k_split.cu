@@ -486,8 +486,10 @@ rr_status split_build(int64_t N, int64_t F, const int64_t *row_ptr, const int32_
     RR_CUDA(cudaMemcpyAsync(tt_ptr, tptr.data(), sizeof(int64_t) * (F + 1), cudaMemcpyHostToDevice, st));
     RR_LAUNCH(k_tail_csc, grid_for(F, kWarps), kThreads, 0, st, F, col_ptr, row_idx, tt_ptr, tt_idx);
     // sliced patterns of the tail, FP32 piece sums
-    RR_TRY(sliced_build(N, F, t_ptr, t_idx, S.xt, err, st));
-    RR_TRY(sliced_build(F, N, tt_ptr, tt_idx, S.xtt, err, st));
+    // (the streaming gather, the automatic choice, needs no staged chunks)
+    const bool chunks = gather_mode != RR_GATHER_AUTO;
+    RR_TRY(sliced_build(N, F, t_ptr, t_idx, S.xt, err, st, chunks));
+    RR_TRY(sliced_build(F, N, tt_ptr, tt_idx, S.xtt, err, st, chunks));
     S.xt.psum32 = S.xtt.psum32 = true;
     if (gather_mode == RR_GATHER_AUTO) {   // the streaming gather on both passes
       RR_TRY(sliced_build_stream(S.xt, st));

@@ -249,8 +249,11 @@ struct SlicedPattern {
   }
 };
 // outer_ptr/inner: a pattern with inner indices ascending within each outer index.
+// chunks: build the staged gather's chunks (and balance the words for it);
+// false for a pattern only the streaming gather reads.
 rr_status sliced_build(int64_t n_outer, int64_t n_inner, const int64_t *outer_ptr,
-                       const int32_t *inner, SlicedPattern &P, int32_t *err, cudaStream_t st);
+                       const int32_t *inner, SlicedPattern &P, int32_t *err, cudaStream_t st,
+                       bool chunks = true);
 void sliced_free(SlicedPattern &P);
 // piece sums of P against x (or, when `in` is given, against the per-index
 // sums of in's slots: the output of a previous pass); fp32: accumulate in FP32
