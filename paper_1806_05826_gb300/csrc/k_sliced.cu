@@ -707,24 +707,25 @@ __global__ void __launch_bounds__(kBalThreads) k_balance_words(int64_t n_chunks,
 
 // The same for the streaming gather's reads: in every 64-word step of a warp's
 // range, lane l reads words 2l and 2l + 1, so the even and the odd words of
-// the step are the groups (one thread per range, its steps in turn).
-__global__ void __launch_bounds__(kBalThreads) k_balance_stream(int64_t n_ranges,
+// the step are the groups (one thread per group: range, step, half).
+__global__ void __launch_bounds__(kBalThreads) k_balance_stream(int64_t n_ranges, int32_t max_steps,
                                                                 const int32_t *__restrict__ wstart,
                                                                 int32_t W, uint4 *__restrict__ idx) {
   __shared__ uint16_t outs[kBalThreads][32 * 8 + 2];
   __shared__ uint8_t usedm[kBalThreads][36];
   __shared__ uint8_t cnts[kBalThreads][36];
   const int t = threadIdx.x;
-  for (int64_t g = (int64_t)blockIdx.x * kBalThreads + t; g < n_ranges;
+  const int64_t total = n_ranges * max_steps * 2;
+  for (int64_t g = (int64_t)blockIdx.x * kBalThreads + t; g < total;
        g += (int64_t)gridDim.x * kBalThreads) {
-    const int64_t task = g / kStreamRanges, rg = g % kStreamRanges;
+    const int h = (int)(g & 1);
+    const int64_t j = (g >> 1) % max_steps, r = (g >> 1) / max_steps;
+    const int64_t task = r / kStreamRanges, rg = r % kStreamRanges;
     const int32_t w0 = wstart[task * (kStreamRanges + 1) + rg];
     const int32_t w1 = wstart[task * (kStreamRanges + 1) + rg + 1];
-    for (int32_t c = w0; c < w1; c += 64)
-      for (int h = 0; h < 2; ++h) {
-        const int n = (int)min(32, (w1 - c - h + 1) / 2);
-        if (n > 0) balance_group(idx, c + h, 2, n, W, outs[t], usedm[t], cnts[t]);
-      }
+    const int64_t c = (int64_t)w0 + 64 * j;
+    const int n = (int)min((int64_t)32, ((int64_t)w1 - c - h + 1) / 2);
+    if (n > 0) balance_group(idx, c + h, 2, n, W, outs[t], usedm[t], cnts[t]);
   }
 }
 
@@ -1086,9 +1087,23 @@ rr_status sliced_build_stream(SlicedPattern &P, cudaStream_t st) {
   RR_LAUNCH(k_warp_ranges, grid_for((int64_t)P.ntasks * 33, kThreads), kThreads, 0, st, P.ntasks,
             P.task_p, P.pw, P.wstart);
   // the words' offsets ordered for the streaming gather's reads
+  std::vector<int32_t> ws((size_t)P.ntasks * (kStreamRanges + 1));
+  RR_CUDA(cudaMemcpyAsync(ws.data(), P.wstart, sizeof(int32_t) * ws.size(), cudaMemcpyDeviceToHost,
+                          st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  int32_t max_words = 0;
+  for (int32_t t = 0; t < P.ntasks; ++t)
+    for (int r = 0; r < kStreamRanges; ++r)
+      max_words = std::max(max_words, ws[(size_t)t * (kStreamRanges + 1) + r + 1] -
+                                          ws[(size_t)t * (kStreamRanges + 1) + r]);
   const int64_t n_ranges = (int64_t)P.ntasks * kStreamRanges;
-  RR_LAUNCH(k_balance_stream, (unsigned)((n_ranges + kBalThreads - 1) / kBalThreads), kBalThreads,
-            0, st, n_ranges, P.wstart, P.W, P.idx);
+  const int32_t max_steps = (max_words + 63) / 64;
+  if (max_steps > 0) {
+    const int64_t groups = n_ranges * max_steps * 2;
+    RR_LAUNCH(k_balance_stream,
+              (unsigned)std::min<int64_t>((groups + kBalThreads - 1) / kBalThreads, 1 << 20),
+              kBalThreads, 0, st, n_ranges, max_steps, P.wstart, P.W, P.idx);
+  }
   RR_CUDA(cudaStreamSynchronize(st));
   return RR_OK;
 }
