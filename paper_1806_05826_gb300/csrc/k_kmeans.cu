@@ -312,15 +312,24 @@ __device__ int64_t seed_pick(int32_t t, int64_t F, int64_t ntiles, uint64_t seed
   return c;
 }
 
-// Single block: draws centre t = *round + 1 (if t < k), then advances the round.
+// Single block: draws centre t = *round + 1 (if t < k), stamps its rows when it
+// is heavy (so that the next round needs no marking launch), then advances the
+// round.
 __global__ void k_seed_pick(int32_t *round, int32_t k, int64_t F, int64_t ntiles, uint64_t seed,
                             const int64_t *__restrict__ d2, const int64_t *__restrict__ tile_sum,
-                            int32_t *centers, uint8_t *chosen) {
+                            int32_t *centers, uint8_t *chosen, int64_t N,
+                            const int64_t *__restrict__ col_ptr,
+                            const int32_t *__restrict__ row_idx, int32_t *__restrict__ rowmark) {
   pdl_wait();
   __shared__ int64_t sm[kWarps + 1];
   const int32_t t = *round + 1;
   __syncthreads();
-  if (t < k) seed_pick(t, F, ntiles, seed, d2, tile_sum, centers, chosen, sm);
+  if (t < k) {
+    const int64_t c = seed_pick(t, F, ntiles, seed, d2, tile_sum, centers, chosen, sm);
+    if (c >= 0 && heavy_centre(col_ptr[c + 1] - col_ptr[c], N))
+      for (int64_t p = col_ptr[c] + threadIdx.x; p < col_ptr[c + 1]; p += blockDim.x)
+        rowmark[row_idx[p]] = t + 1;
+  }
   if (threadIdx.x == 0) *round = t;
 }
 
@@ -738,12 +747,11 @@ __global__ void k_lloyd_argmin(int64_t F, int32_t k, const int32_t *__restrict__
 
 }  // namespace
 
-// The k rounds run as one CUDA graph: a conditional while node whose body is
-// one round (overlaps with the newest centre, distance update, next draw).
-// The k rounds, issued from the host as four kernels each (mark, overlap,
-// update, draw) chained by programmatic dependent launch: each kernel's
-// launch overlaps the previous one's tail, and no host synchronisation comes
-// between rounds.
+// The k rounds, issued from the host as three kernels each (overlaps with the
+// newest centre, distance update, draw of the next centre, which also stamps
+// that centre's rows when it is heavy) chained by programmatic dependent
+// launch: each kernel's launch overlaps the previous one's tail, and no host
+// synchronisation comes between rounds.
 rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                         const int64_t *col_ptr, const int32_t *row_idx, int32_t k, uint64_t seed,
                         KmeansBuffers &b, cudaStream_t st) {
@@ -756,15 +764,17 @@ rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int3
   RR_LAUNCH(k_hot_assign, grid_for(F, kThreads), kThreads, 0, st, F, N, col_ptr, b.hot, b.hot_col,
             b.hot_n);
   RR_LAUNCH(k_first_center, 1, 32, 0, st, F, seed, b.centers, chosen, b.round);
+  // the first centre's rows, if it is heavy; every later centre's are stamped
+  // by the round that draws it
+  RR_LAUNCH_PDL(k_seed_mark, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, col_ptr, row_idx,
+                b.dcount);
   for (int32_t t = 0; t < k; ++t) {
-    RR_LAUNCH_PDL(k_seed_mark, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, col_ptr, row_idx,
-                  b.dcount);
     RR_LAUNCH_PDL(k_seed_overlap, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, row_ptr,
                   col_idx, col_ptr, row_idx, b.dcount, b.hot, b.hot_col, b.hot_n, b.ov);
     RR_LAUNCH_PDL(k_seed_update, (unsigned)ntiles, kThreads, 0, st, b.round, F, N, b.centers,
                   col_ptr, b.ov, b.d2, b.part_i);
     RR_LAUNCH_PDL(k_seed_pick, 1, kThreads, 0, st, b.round, k, F, ntiles, seed, b.d2, b.part_i,
-                  b.centers, chosen);
+                  b.centers, chosen, N, col_ptr, row_idx, b.dcount);
   }
   RR_CUDA(cudaStreamSynchronize(st));
   return RR_OK;
