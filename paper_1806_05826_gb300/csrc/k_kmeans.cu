@@ -75,40 +75,22 @@ __device__ int64_t block_incl_scan_i64(int64_t v, int64_t *sm, int64_t *total) {
   return sm[warp] + inc;
 }
 
-__global__ void k_first_center(int64_t F, uint64_t seed, int32_t *centers, uint8_t *chosen,
-                               int32_t *round) {
-  pdl_wait();
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    int64_t c = (int64_t)floor(uniform53(seed, 0) * (double)F);
-    if (c >= F) c = F - 1;
-    centers[0] = (int32_t)c;
-    chosen[c] = 1;
-    *round = 0;
-  }
-}
+// Overlaps of the newest centre c with every feature, |x_i AND x_c|, are
+// counted in one of two ways (the same integers either way):
+//  push: for every row of c, ov[j] += 1 for each feature j of that row (cost:
+//        the entries of c's rows, about n_c nnz / N, as atomic increments);
+//  pull: c's rows set in a bitmap of N bits, then every listed feature's
+//        column is read in chunks of kSeedChunk entries and its rows tested
+//        against the bitmap (cost: the listed columns' entries, read in order).
+// Only features whose distance can still drop are listed for a pull. Since
+// D2(i, c) = |x_i XOR x_c| >= |n_i - n_c|, a feature with d2[i] <= |n_i - n_c|
+// keeps d2[i] = min(d2[i], D2(i, c)) whatever its overlap; its ov stays 0, and
+// the update's n_i + n_c - 2 ov >= d2[i] leaves d2[i] as it is.
+constexpr int kSeedChunk = 1024;            // CSC entries per pull chunk (32 per lane)
+constexpr double kSeedPullWork = 500000.0;  // push entries above which a centre is pulled
 
-// A centre with more than N/2 rows is "heavy": its overlaps are counted over
-// the rows it does NOT hold (|x_j AND x_c| = n_j - |x_j AND NOT x_c|), which
-// is the smaller set. Its rows are stamped with the round in rowmark.
-__device__ __forceinline__ bool heavy_centre(int64_t nc, int64_t N) { return 2 * nc > N; }
-
-// Stamps the rows of a heavy centre c with t + 1 (grid-stride over its column).
-__device__ __forceinline__ void seed_mark(int32_t t, int64_t c, int64_t N,
-                                          const int64_t *__restrict__ col_ptr,
-                                          const int32_t *__restrict__ row_idx,
-                                          int32_t *__restrict__ rowmark) {
-  if (!heavy_centre(col_ptr[c + 1] - col_ptr[c], N)) return;
-  for (int64_t p = col_ptr[c] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < col_ptr[c + 1];
-       p += (int64_t)gridDim.x * blockDim.x)
-    rowmark[row_idx[p]] = t + 1;
-}
-
-__global__ void k_seed_mark(const int32_t *__restrict__ round, const int32_t *__restrict__ centers,
-                            int64_t N, const int64_t *__restrict__ col_ptr,
-                            const int32_t *__restrict__ row_idx, int32_t *__restrict__ rowmark) {
-  pdl_wait();
-  const int32_t t = *round;
-  seed_mark(t, centers[t], N, col_ptr, row_idx, rowmark);
+__device__ __forceinline__ bool seed_pulls(int64_t nc, int64_t N, int64_t nnz) {
+  return (double)nc * (double)nnz > kSeedPullWork * (double)N;
 }
 
 // Frequent features (at least kHotMin and N/128 rows; at most kHotBins of them)
@@ -136,28 +118,25 @@ __global__ void k_hot_assign(int64_t F, int64_t N, const int64_t *__restrict__ c
   }
 }
 
-// ov[j] += 1 for every feature j sharing a row with centre c (for a heavy
-// centre: for every row the centre does not hold). Integer counts, so the
-// order of the increments does not matter. hist: kHotBins shared ints.
-// rowmark is read through L2 (another block of the same launch may have
-// written it).
-__device__ __forceinline__ void seed_overlap(int32_t t, int64_t c, int64_t N,
-                                             const int64_t *__restrict__ row_ptr,
-                                             const int32_t *__restrict__ col_idx,
-                                             const int64_t *__restrict__ col_ptr,
-                                             const int32_t *__restrict__ row_idx,
-                                             const int32_t *rowmark,
-                                             const uint16_t *__restrict__ hot,
-                                             const int32_t *__restrict__ hot_col, int32_t nh,
-                                             int32_t *ov, int32_t *hist) {
+// Push: ov[j] += 1 for every feature j sharing a row with centre c, one row
+// per warp. Integer counts, so the order of the increments does not matter.
+// hist: kHotBins shared ints.
+__device__ __forceinline__ void seed_overlap_push(int64_t c, const int64_t *__restrict__ row_ptr,
+                                                  const int32_t *__restrict__ col_idx,
+                                                  const int64_t *__restrict__ col_ptr,
+                                                  const int32_t *__restrict__ row_idx,
+                                                  const uint16_t *__restrict__ hot,
+                                                  const int32_t *__restrict__ hot_col, int32_t nh,
+                                                  int32_t *ov, int32_t *hist) {
   for (int s = threadIdx.x; s < kHotBins; s += blockDim.x) hist[s] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  // eight entries per lane at a time: their index and bin loads in flight together
-  auto add_row = [&](int64_t r) {
+  for (int64_t p = col_ptr[c] + warp; p < col_ptr[c + 1]; p += nwarps) {
+    const int64_t r = row_idx[p];
     const int64_t e1 = row_ptr[r + 1];
+    // eight entries per lane at a time: their index and bin loads in flight together
     for (int64_t e0 = row_ptr[r] + lane; e0 < e1; e0 += 32 * 8) {
       int32_t j[8];
       uint16_t bin[8];
@@ -174,12 +153,6 @@ __device__ __forceinline__ void seed_overlap(int32_t t, int64_t c, int64_t N,
           atomicAdd(&ov[j[u]], 1);
       }
     }
-  };
-  if (heavy_centre(col_ptr[c + 1] - col_ptr[c], N)) {
-    for (int64_t r = warp; r < N; r += nwarps)
-      if (__ldcg(&rowmark[r]) != t + 1) add_row(r);
-  } else {
-    for (int64_t p = col_ptr[c] + warp; p < col_ptr[c + 1]; p += nwarps) add_row(row_idx[p]);
   }
   __syncthreads();
   for (int s = threadIdx.x; s < nh; s += blockDim.x) {
@@ -188,37 +161,66 @@ __device__ __forceinline__ void seed_overlap(int32_t t, int64_t c, int64_t N,
   }
 }
 
+// Pull: one listed chunk (feature, chunk number) per warp at a time; each lane
+// loads 32 of the chunk's row indices together, then tests them in rowbits.
+__device__ __forceinline__ void seed_overlap_pull(const int64_t *__restrict__ col_ptr,
+                                                  const int32_t *__restrict__ row_idx,
+                                                  const uint32_t *__restrict__ rowbits,
+                                                  const int2 *__restrict__ tasks, int32_t ntasks,
+                                                  int32_t *ov) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = warp; q < ntasks; q += nwarps) {
+    const int2 tk = tasks[q];
+    const int64_t e = col_ptr[tk.x + 1];
+    const int64_t s = col_ptr[tk.x] + (int64_t)tk.y * kSeedChunk + lane;
+    int32_t r[kSeedChunk / 32];
+#pragma unroll
+    for (int u = 0; u < kSeedChunk / 32; ++u)
+      r[u] = s + 32 * u < e ? __ldg(&row_idx[s + 32 * u]) : -1;
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int u = 0; u < kSeedChunk / 32; ++u)
+      if (r[u] >= 0) cnt += (__ldg(&rowbits[r[u] >> 5]) >> (r[u] & 31)) & 1u;
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if (lane == 0 && cnt) atomicAdd(&ov[tk.x], (int32_t)cnt);
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_seed_overlap(
-    const int32_t *__restrict__ round, const int32_t *__restrict__ centers, int64_t N,
+    int32_t t, const int32_t *__restrict__ centers, int64_t N, int64_t nnz,
     const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
     const int64_t *__restrict__ col_ptr, const int32_t *__restrict__ row_idx,
-    const int32_t *__restrict__ rowmark, const uint16_t *__restrict__ hot,
+    const uint32_t *__restrict__ rowbits, const int2 *__restrict__ tasks,
+    const int32_t *__restrict__ ntasks, const uint16_t *__restrict__ hot,
     const int32_t *__restrict__ hot_col, const int32_t *__restrict__ hot_n,
     int32_t *__restrict__ ov) {
   __shared__ int32_t hist[kHotBins];
   pdl_wait();
-  const int32_t t = *round;
   const int64_t c = centers[t];
+  if (c < 0) return;
   const int64_t nc = col_ptr[c + 1] - col_ptr[c];
-  // a light centre's rows go one per warp: blocks past them have nothing to count
-  if (!heavy_centre(nc, N) && (int64_t)blockIdx.x * (blockDim.x >> 5) >= nc) return;
-  seed_overlap(t, c, N, row_ptr, col_idx, col_ptr, row_idx, rowmark, hot, hot_col,
-               min(*hot_n, kHotBins), ov, hist);
+  if (seed_pulls(nc, N, nnz)) {
+    seed_overlap_pull(col_ptr, row_idx, rowbits, tasks, *ntasks, ov);
+    return;
+  }
+  // a pushed centre's rows go one per warp: blocks past them have nothing to count
+  if ((int64_t)blockIdx.x * (blockDim.x >> 5) >= nc) return;
+  seed_overlap_push(c, row_ptr, col_idx, col_ptr, row_idx, hot, hot_col, min(*hot_n, kHotBins),
+                    ov, hist);
 }
 
 // d2[i] = min(d2[i], n_i + n_c - 2 ov[i]) (plain assignment for the first centre);
 // ov reset; tile_sum[tile] = sum of the tile's d2 (tiles of kTile features).
 __device__ __forceinline__ void seed_update_tile(int32_t t, int64_t tile, int64_t F, int64_t nc,
-                                                 bool heavy, const int64_t *__restrict__ col_ptr,
-                                                 int32_t *ov, int64_t *d2, int64_t *tile_sum,
-                                                 int64_t *sm) {
+                                                 const int64_t *__restrict__ col_ptr, int32_t *ov,
+                                                 int64_t *d2, int64_t *tile_sum, int64_t *sm) {
   int64_t s = 0;
   const int64_t i = tile * kTile + threadIdx.x;
   if (i < F) {
     const int64_t ni = col_ptr[i + 1] - col_ptr[i];
-    const int32_t o = __ldcg(&ov[i]);
-    const int64_t inter = heavy ? ni - (int64_t)o : (int64_t)o;
-    const int64_t dist = ni + nc - 2 * inter;
+    const int64_t dist = ni + nc - 2 * (int64_t)__ldcg(&ov[i]);
     ov[i] = 0;
     const int64_t v = (t == 0) ? dist : min(d2[i], dist);
     d2[i] = v;
@@ -228,23 +230,33 @@ __device__ __forceinline__ void seed_update_tile(int32_t t, int64_t tile, int64_
   if (threadIdx.x == 0) tile_sum[tile] = s;
 }
 
+// Round t's distance update; also marks centre t chosen, empties the pull list
+// and, after a pull, clears the row bitmap for the next round.
 __global__ void __launch_bounds__(kThreads) k_seed_update(
-    const int32_t *__restrict__ round, int64_t F, int64_t N, const int32_t *__restrict__ centers,
+    int32_t t, int64_t F, int64_t N, int64_t nnz, const int32_t *__restrict__ centers,
     const int64_t *__restrict__ col_ptr, int32_t *__restrict__ ov, int64_t *__restrict__ d2,
-    int64_t *__restrict__ tile_sum) {
+    int64_t *__restrict__ tile_sum, uint8_t *__restrict__ chosen, uint32_t *__restrict__ rowbits,
+    int32_t *__restrict__ ntasks) {
   pdl_wait();
   __shared__ int64_t sm[kWarps + 1];
-  const int32_t t = *round;
   const int64_t c = centers[t];
+  if (c < 0) return;
   const int64_t nc = col_ptr[c + 1] - col_ptr[c];
-  seed_update_tile(t, blockIdx.x, F, nc, heavy_centre(nc, N), col_ptr, ov, d2, tile_sum, sm);
+  seed_update_tile(t, blockIdx.x, F, nc, col_ptr, ov, d2, tile_sum, sm);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    chosen[c] = 1;
+    *ntasks = 0;
+  }
+  if (seed_pulls(nc, N, nnz))
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < (N + 31) / 32;
+         w += (int64_t)gridDim.x * blockDim.x)
+      rowbits[w] = 0;
 }
 
-// One block: draws centre t (1 <= t < k) from d2, the tile sums and chosen[];
-// stores it in centers[t] and chosen[] and returns it to every thread.
+// Draws centre t (1 <= t < k) from d2, the tile sums and chosen[] (whole
+// block, reads only) and returns it to every thread of the block.
 __device__ int64_t seed_pick(int32_t t, int64_t F, int64_t ntiles, uint64_t seed, const int64_t *d2,
-                             const int64_t *tile_sum, int32_t *centers, uint8_t *chosen,
-                             int64_t *sm) {
+                             const int64_t *tile_sum, const uint8_t *chosen, int64_t *sm) {
   __shared__ int64_t found;
   __shared__ int64_t tile_found, tile_base;
   int64_t s = 0;
@@ -303,34 +315,56 @@ __device__ int64_t seed_pick(int32_t t, int64_t F, int64_t ntiles, uint64_t seed
     }
   }
   __syncthreads();
-  const int64_t c = found;
-  if (threadIdx.x == 0) {
-    centers[t] = (int32_t)c;
-    if (c >= 0) chosen[c] = 1;
-  }
-  __syncthreads();
-  return c;
+  return found;
 }
 
-// Single block: draws centre t = *round + 1 (if t < k), stamps its rows when it
-// is heavy (so that the next round needs no marking launch), then advances the
-// round.
-__global__ void k_seed_pick(int32_t *round, int32_t k, int64_t F, int64_t ntiles, uint64_t seed,
-                            const int64_t *__restrict__ d2, const int64_t *__restrict__ tile_sum,
-                            int32_t *centers, uint8_t *chosen, int64_t N,
-                            const int64_t *__restrict__ col_ptr,
-                            const int32_t *__restrict__ row_idx, int32_t *__restrict__ rowmark) {
+// Round t, every block: the block draws centre t itself (floor(u_0 F) at
+// t = 0; the same inputs and integer arithmetic give every block the same
+// centre) and block 0 stores it. When the centre's overlaps are to be pulled,
+// the grid sets its rows in rowbits and lists the chunks of every feature whose
+// distance can still drop (every feature at t = 0) in tasks[0 .. *ntasks).
+__global__ void __launch_bounds__(kThreads) k_seed_pick(
+    int32_t t, int64_t F, int64_t N, int64_t nnz, int64_t ntiles, uint64_t seed,
+    const int64_t *__restrict__ d2, const int64_t *__restrict__ tile_sum,
+    const uint8_t *__restrict__ chosen, const int64_t *__restrict__ col_ptr,
+    const int32_t *__restrict__ row_idx, int32_t *__restrict__ centers,
+    uint32_t *__restrict__ rowbits, int2 *__restrict__ tasks, int32_t *__restrict__ ntasks) {
   pdl_wait();
   __shared__ int64_t sm[kWarps + 1];
-  const int32_t t = *round + 1;
-  __syncthreads();
-  if (t < k) {
-    const int64_t c = seed_pick(t, F, ntiles, seed, d2, tile_sum, centers, chosen, sm);
-    if (c >= 0 && heavy_centre(col_ptr[c + 1] - col_ptr[c], N))
-      for (int64_t p = col_ptr[c] + threadIdx.x; p < col_ptr[c + 1]; p += blockDim.x)
-        rowmark[row_idx[p]] = t + 1;
+  __shared__ int32_t base;
+  int64_t c;
+  if (t == 0) {
+    c = (int64_t)floor(uniform53(seed, 0) * (double)F);
+    if (c >= F) c = F - 1;
+  } else {
+    c = seed_pick(t, F, ntiles, seed, d2, tile_sum, chosen, sm);
   }
-  if (threadIdx.x == 0) *round = t;
+  if (blockIdx.x == 0 && threadIdx.x == 0) centers[t] = (int32_t)c;
+  if (c < 0) return;   // block-uniform: every feature chosen already (k > F)
+  const int64_t nc = col_ptr[c + 1] - col_ptr[c];
+  if (!seed_pulls(nc, N, nnz)) return;
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = col_ptr[c] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < col_ptr[c + 1];
+       p += nthr) {
+    const int32_t r = row_idx[p];
+    atomicOr(&rowbits[r >> 5], 1u << (r & 31));
+  }
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < F; i0 += nthr) {
+    const int64_t i = i0 + threadIdx.x;
+    int64_t nch = 0;
+    if (i < F) {
+      const int64_t ni = col_ptr[i + 1] - col_ptr[i];
+      if (ni > 0 && (t == 0 || __ldcg(&d2[i]) > (ni > nc ? ni - nc : nc - ni)))
+        nch = (ni + kSeedChunk - 1) / kSeedChunk;
+    }
+    int64_t tot;
+    const int64_t inc = block_incl_scan_i64(nch, sm, &tot);
+    if (threadIdx.x == 0 && tot > 0) base = atomicAdd(ntasks, (int32_t)tot);
+    __syncthreads();
+    for (int64_t q = 0; q < nch; ++q)
+      tasks[base + inc - nch + q] = make_int2((int32_t)i, (int32_t)q);
+    __syncthreads();
+  }
 }
 
 __global__ void k_init_labels(int64_t F, int32_t k, const int32_t *__restrict__ centers,
@@ -747,34 +781,35 @@ __global__ void k_lloyd_argmin(int64_t F, int32_t k, const int32_t *__restrict__
 
 }  // namespace
 
-// The k rounds, issued from the host as three kernels each (overlaps with the
-// newest centre, distance update, draw of the next centre, which also stamps
-// that centre's rows when it is heavy) chained by programmatic dependent
-// launch: each kernel's launch overlaps the previous one's tail, and no host
-// synchronisation comes between rounds.
-rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
-                        const int64_t *col_ptr, const int32_t *row_idx, int32_t k, uint64_t seed,
-                        KmeansBuffers &b, cudaStream_t st) {
+// The k rounds, issued from the host as three kernels each (draw of centre t
+// with the pull list, overlaps with it, distance update), chained by
+// programmatic dependent launch: each kernel's launch overlaps the previous
+// one's tail, and no host synchronisation comes between rounds. The row bitmap
+// and the pull list live in buffers the Lloyd steps fill only later.
+rr_status kmeanspp_seed(int64_t N, int64_t F, int64_t nnz, const int64_t *row_ptr,
+                        const int32_t *col_idx, const int64_t *col_ptr, const int32_t *row_idx,
+                        int32_t k, uint64_t seed, KmeansBuffers &b, cudaStream_t st) {
   const int64_t ntiles = (F + kTile - 1) / kTile;
-  uint8_t *chosen = reinterpret_cast<uint8_t *>(b.next);   // F bytes of the (unused yet) next[]
+  uint8_t *chosen = reinterpret_cast<uint8_t *>(b.next);       // F bytes
+  uint32_t *rowbits = reinterpret_cast<uint32_t *>(b.mcount);  // ceil(N/32) words of N int64
+  int2 *tasks = b.dlist;     // sum over features of ceil(n_i / kSeedChunk) <= 2 nnz entries
+  int32_t *ntasks = b.work_ctr;
   RR_CUDA(cudaMemsetAsync(chosen, 0, F, st));
   RR_CUDA(cudaMemsetAsync(b.ov, 0, sizeof(int32_t) * F, st));
-  RR_CUDA(cudaMemsetAsync(b.dcount, 0, sizeof(int32_t) * N, st));   // row stamps of heavy centres
+  RR_CUDA(cudaMemsetAsync(rowbits, 0, sizeof(uint32_t) * ((N + 31) / 32), st));
+  RR_CUDA(cudaMemsetAsync(ntasks, 0, sizeof(int32_t), st));
   RR_CUDA(cudaMemsetAsync(b.hot_n, 0, sizeof(int32_t), st));
   RR_LAUNCH(k_hot_assign, grid_for(F, kThreads), kThreads, 0, st, F, N, col_ptr, b.hot, b.hot_col,
             b.hot_n);
-  RR_LAUNCH(k_first_center, 1, 32, 0, st, F, seed, b.centers, chosen, b.round);
-  // the first centre's rows, if it is heavy; every later centre's are stamped
-  // by the round that draws it
-  RR_LAUNCH_PDL(k_seed_mark, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, col_ptr, row_idx,
-                b.dcount);
   for (int32_t t = 0; t < k; ++t) {
-    RR_LAUNCH_PDL(k_seed_overlap, kSMs * 2, kThreads, 0, st, b.round, b.centers, N, row_ptr,
-                  col_idx, col_ptr, row_idx, b.dcount, b.hot, b.hot_col, b.hot_n, b.ov);
-    RR_LAUNCH_PDL(k_seed_update, (unsigned)ntiles, kThreads, 0, st, b.round, F, N, b.centers,
-                  col_ptr, b.ov, b.d2, b.part_i);
-    RR_LAUNCH_PDL(k_seed_pick, 1, kThreads, 0, st, b.round, k, F, ntiles, seed, b.d2, b.part_i,
-                  b.centers, chosen, N, col_ptr, row_idx, b.dcount);
+    RR_LAUNCH_PDL(k_seed_pick, kSMs * 2, kThreads, 0, st, t, F, N, nnz, ntiles, seed, b.d2,
+                  b.part_i, chosen, col_ptr, row_idx, b.centers, rowbits, tasks, ntasks);
+    if (t + 1 == k) break;   // the last centre's distances are not needed
+    RR_LAUNCH_PDL(k_seed_overlap, kSMs * 2, kThreads, 0, st, t, b.centers, N, nnz, row_ptr,
+                  col_idx, col_ptr, row_idx, rowbits, tasks, ntasks, b.hot, b.hot_col, b.hot_n,
+                  b.ov);
+    RR_LAUNCH_PDL(k_seed_update, (unsigned)ntiles, kThreads, 0, st, t, F, N, nnz, b.centers,
+                  col_ptr, b.ov, b.d2, b.part_i, chosen, rowbits, ntasks);
   }
   RR_CUDA(cudaStreamSynchronize(st));
   return RR_OK;

@@ -79,7 +79,6 @@ struct KmeansBuffers {
   int64_t *changes;    // [1]
   int32_t *work_ctr;   // [1]
   int32_t *order;      // [F] features by descending work (heaviest first)
-  int32_t *round;      // [1] seeding round (device-side loop counter)
   uint16_t *hot;       // [F] shared-histogram bin of a frequent feature (0xFFFF: none)
   int32_t *hot_col;    // [2048] feature of each bin
   int32_t *hot_n;      // [1] bins in use (capped at 2048 when read)
@@ -91,9 +90,9 @@ struct KmeansBuffers {
 // upper bound of the pull tasks: one per feature plus one per 1024 entries
 int64_t kmeans_pull_tasks_max(int64_t F, int64_t nnz);
 // K-means++ seeding (k centres into b.centers). Synchronises the stream.
-rr_status kmeanspp_seed(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
-                        const int64_t *col_ptr, const int32_t *row_idx, int32_t k, uint64_t seed,
-                        KmeansBuffers &b, cudaStream_t st);
+rr_status kmeanspp_seed(int64_t N, int64_t F, int64_t nnz, const int64_t *row_ptr,
+                        const int32_t *col_idx, const int64_t *col_ptr, const int32_t *row_idx,
+                        int32_t k, uint64_t seed, KmeansBuffers &b, cudaStream_t st);
 // labels <- -1 except labels[centers[S]] = S; prev <- -1; D <- 0.
 // tiles of features of the seeding pass (tile sums in part_i)
 int64_t kmeans_seed_tiles(int64_t F);

@@ -569,7 +569,6 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&kb.changes, 1));
   RR_TRY(m.alloc(&kb.work_ctr, 1));
   RR_TRY(m.alloc(&kb.order, F));
-  RR_TRY(m.alloc(&kb.round, 1));
   RR_TRY(m.alloc(&kb.hot, F));
   RR_TRY(m.alloc(&kb.hot_col, 2048));
   RR_TRY(m.alloc(&kb.hot_n, 1));
@@ -588,7 +587,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
     RR_CUDA(cudaMemcpyAsync(h->centers, h->opt.init_centers, sizeof(int32_t) * k,
                             cudaMemcpyHostToDevice, st));
   } else {
-    RR_TRY(rr::kmeanspp_seed(N, F, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx, k,
+    RR_TRY(rr::kmeanspp_seed(N, F, nnz, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx, k,
                              h->opt.seed, kb, st));
   }
   RR_TRY(phase(2));
@@ -722,7 +721,6 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   m.release(kb.changes);
   m.release(kb.work_ctr);
   m.release(kb.order);
-  m.release(kb.round);
   RR_TRY(phase(7));
   return RR_OK;
 }
