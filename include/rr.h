@@ -156,6 +156,11 @@ typedef struct {
   int32_t clustering;           /* RR_CLUSTER_* (default RR_CLUSTER_KMEANS) */
   double lf_tol2;               /* RR_CLUSTER_LEADER: the squared distance tolerance (a feature
                                    follows when d^2 < lf_tol2); default 1.0 */
+  int64_t seed_pull_work;       /* a k-means++ round whose centre c's row entries (estimated as
+                                   n_c nnz / N) exceed this counts the overlaps with c column by
+                                   column against a bitmap of c's rows (pull), else row by row
+                                   with integer atomics (push); 0 = default (5e5), negative =
+                                   always push. Centres are identical either way */
   void *stream;                 /* cudaStream_t for all work; NULL = legacy default stream */
 } rr_options;
 

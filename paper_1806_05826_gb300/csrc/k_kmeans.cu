@@ -86,11 +86,11 @@ __device__ int64_t block_incl_scan_i64(int64_t v, int64_t *sm, int64_t *total) {
 // D2(i, c) = |x_i XOR x_c| >= |n_i - n_c|, a feature with d2[i] <= |n_i - n_c|
 // keeps d2[i] = min(d2[i], D2(i, c)) whatever its overlap; its ov stays 0, and
 // the update's n_i + n_c - 2 ov >= d2[i] leaves d2[i] as it is.
-constexpr int kSeedChunk = 1024;            // CSC entries per pull chunk (32 per lane)
-constexpr double kSeedPullWork = 500000.0;  // push entries above which a centre is pulled
+constexpr int kSeedChunk = 1024;   // CSC entries per pull chunk (32 per lane)
 
-__device__ __forceinline__ bool seed_pulls(int64_t nc, int64_t N, int64_t nnz) {
-  return (double)nc * (double)nnz > kSeedPullWork * (double)N;
+// pull_work: estimated push entries above which a centre is pulled (< 0: never)
+__device__ __forceinline__ bool seed_pulls(int64_t nc, int64_t N, int64_t nnz, double pull_work) {
+  return pull_work >= 0.0 && (double)nc * (double)nnz > pull_work * (double)N;
 }
 
 // Frequent features (at least kHotMin and N/128 rows; at most kHotBins of them)
@@ -189,7 +189,7 @@ __device__ __forceinline__ void seed_overlap_pull(const int64_t *__restrict__ co
 }
 
 __global__ void __launch_bounds__(kThreads) k_seed_overlap(
-    int32_t t, const int32_t *__restrict__ centers, int64_t N, int64_t nnz,
+    int32_t t, const int32_t *__restrict__ centers, int64_t N, int64_t nnz, double pull_work,
     const int64_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
     const int64_t *__restrict__ col_ptr, const int32_t *__restrict__ row_idx,
     const uint32_t *__restrict__ rowbits, const int2 *__restrict__ tasks,
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(kThreads) k_seed_overlap(
   const int64_t c = centers[t];
   if (c < 0) return;
   const int64_t nc = col_ptr[c + 1] - col_ptr[c];
-  if (seed_pulls(nc, N, nnz)) {
+  if (seed_pulls(nc, N, nnz, pull_work)) {
     seed_overlap_pull(col_ptr, row_idx, rowbits, tasks, *ntasks, ov);
     return;
   }
@@ -233,7 +233,8 @@ __device__ __forceinline__ void seed_update_tile(int32_t t, int64_t tile, int64_
 // Round t's distance update; also marks centre t chosen, empties the pull list
 // and, after a pull, clears the row bitmap for the next round.
 __global__ void __launch_bounds__(kThreads) k_seed_update(
-    int32_t t, int64_t F, int64_t N, int64_t nnz, const int32_t *__restrict__ centers,
+    int32_t t, int64_t F, int64_t N, int64_t nnz, double pull_work,
+    const int32_t *__restrict__ centers,
     const int64_t *__restrict__ col_ptr, int32_t *__restrict__ ov, int64_t *__restrict__ d2,
     int64_t *__restrict__ tile_sum, uint8_t *__restrict__ chosen, uint32_t *__restrict__ rowbits,
     int32_t *__restrict__ ntasks) {
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(kThreads) k_seed_update(
     chosen[c] = 1;
     *ntasks = 0;
   }
-  if (seed_pulls(nc, N, nnz))
+  if (seed_pulls(nc, N, nnz, pull_work))
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < (N + 31) / 32;
          w += (int64_t)gridDim.x * blockDim.x)
       rowbits[w] = 0;
@@ -324,7 +325,7 @@ __device__ int64_t seed_pick(int32_t t, int64_t F, int64_t ntiles, uint64_t seed
 // the grid sets its rows in rowbits and lists the chunks of every feature whose
 // distance can still drop (every feature at t = 0) in tasks[0 .. *ntasks).
 __global__ void __launch_bounds__(kThreads) k_seed_pick(
-    int32_t t, int64_t F, int64_t N, int64_t nnz, int64_t ntiles, uint64_t seed,
+    int32_t t, int64_t F, int64_t N, int64_t nnz, double pull_work, int64_t ntiles, uint64_t seed,
     const int64_t *__restrict__ d2, const int64_t *__restrict__ tile_sum,
     const uint8_t *__restrict__ chosen, const int64_t *__restrict__ col_ptr,
     const int32_t *__restrict__ row_idx, int32_t *__restrict__ centers,
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(kThreads) k_seed_pick(
   if (blockIdx.x == 0 && threadIdx.x == 0) centers[t] = (int32_t)c;
   if (c < 0) return;   // block-uniform: every feature chosen already (k > F)
   const int64_t nc = col_ptr[c + 1] - col_ptr[c];
-  if (!seed_pulls(nc, N, nnz)) return;
+  if (!seed_pulls(nc, N, nnz, pull_work)) return;
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = col_ptr[c] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < col_ptr[c + 1];
        p += nthr) {
@@ -746,10 +747,39 @@ __device__ __forceinline__ bool better(const Cand &x, const Cand &y) {
   return x.s < y.s;
 }
 
+// FP32 approximations of the score's two terms per cluster S,
+//   q_S ~ Q_S / n_S^2,  r_S ~ 2 / n_S,  score(i, S) ~ q_S - r_S D_iS,
+// used only to skip clusters that cannot win (q_S = +inf for an empty one).
+// Each of Q_S, n_S^2, D_iS rounds once to FP32 and each operation adds one
+// rounding, so |computed - exact| <= 6 u (Q_S / n_S^2 + 2 D_iS / n_S) + O(u^2)
+// with u = 2^-24; kScoreTol = 2^-20 = 16 u covers that and the roundings of the
+// bounds themselves.
+constexpr float kScoreTol = 0x1.0p-20f;
+constexpr int kArgminBatch = 8;
+
+__global__ void k_score_terms(int32_t k, const unsigned long long *__restrict__ Q,
+                              const unsigned long long *__restrict__ n_S, float2 *__restrict__ qr) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= k) return;
+  const unsigned long long n = n_S[s];
+  const float nf = (float)n;
+  qr[s] = n == 0 ? make_float2(INFINITY, 0.f) : make_float2((float)Q[s] / (nf * nf), 2.f / nf);
+}
+
 // One warp per feature: next[i] = argmin_S score(i, S); counts changed labels.
+// The warp visits the clusters in batches of 32 x kArgminBatch and keeps U, the
+// least upper bound (approximate score + its error bound) of every cluster
+// seen so far, so U >= the exact score of the best of them. A cluster whose
+// lower bound (approximate score - error bound) exceeds U is strictly worse
+// than that one and is skipped (an empty cluster gives NaN and is skipped
+// too); the others, usually only the batch's best, are compared exactly and
+// kept per lane (clusters in increasing S). The exact argmin, ties to the
+// smallest S, is never skipped, so the result is exact whatever the filter
+// skips; a bound shared by the warp keeps the exact path off most batches.
 __global__ void k_lloyd_argmin(int64_t F, int32_t k, const int32_t *__restrict__ D,
                                const unsigned long long *__restrict__ Q,
                                const unsigned long long *__restrict__ n_S,
+                               const float2 *__restrict__ qr,
                                const int32_t *__restrict__ labels, int32_t *__restrict__ next,
                                unsigned long long *changes) {
   const int lane = threadIdx.x & 31;
@@ -759,11 +789,38 @@ __global__ void k_lloyd_argmin(int64_t F, int32_t k, const int32_t *__restrict__
   for (int64_t i = warp; i < F; i += nwarps) {
     const int32_t *Di = D + i * (int64_t)k;
     Cand best{0, 0, INT32_MAX};
-    for (int s = lane; s < k; s += 32) {
-      const int64_t n = (int64_t)n_S[s];
-      if (n == 0) continue;
-      Cand c{(int64_t)Q[s] - 2 * n * (int64_t)Di[s], n * n, s};
-      if (better(c, best)) best = c;
+    float U = INFINITY;
+    // eight clusters per lane at a time: their D and table loads in flight together
+    for (int s0 = lane; s0 - lane < k; s0 += 32 * kArgminBatch) {   // warp-uniform
+      int32_t d[kArgminBatch];
+      float2 t[kArgminBatch];
+#pragma unroll
+      for (int u = 0; u < kArgminBatch; ++u) {
+        const int s = s0 + 32 * u;
+        d[u] = s < k ? __ldg(&Di[s]) : 0;
+        t[u] = s < k ? __ldg(&qr[s]) : make_float2(INFINITY, 0.f);
+      }
+      float lo[kArgminBatch], hi = INFINITY;
+#pragma unroll
+      for (int u = 0; u < kArgminBatch; ++u) {
+        const float df = (float)d[u];
+        const float sc = fmaf(-t[u].y, df, t[u].x);
+        const float m = fmaf(t[u].y, df, t[u].x);
+        lo[u] = fmaf(-kScoreTol, m, sc);
+        hi = fminf(hi, fmaf(kScoreTol, m, sc));   // fminf drops the NaN of an empty cluster
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) hi = fminf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      U = fminf(U, hi);
+#pragma unroll
+      for (int u = 0; u < kArgminBatch; ++u) {
+        if (!(lo[u] <= U)) continue;
+        const int s = s0 + 32 * u;
+        const int64_t n = (int64_t)n_S[s];
+        if (n == 0) continue;
+        Cand c{(int64_t)Q[s] - 2 * n * (int64_t)d[u], n * n, s};
+        if (better(c, best)) best = c;
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -788,8 +845,10 @@ __global__ void k_lloyd_argmin(int64_t F, int32_t k, const int32_t *__restrict__
 // and the pull list live in buffers the Lloyd steps fill only later.
 rr_status kmeanspp_seed(int64_t N, int64_t F, int64_t nnz, const int64_t *row_ptr,
                         const int32_t *col_idx, const int64_t *col_ptr, const int32_t *row_idx,
-                        int32_t k, uint64_t seed, KmeansBuffers &b, cudaStream_t st) {
+                        int32_t k, uint64_t seed, int64_t pull_work, KmeansBuffers &b,
+                        cudaStream_t st) {
   const int64_t ntiles = (F + kTile - 1) / kTile;
+  const double pw = pull_work > 0 ? (double)pull_work : pull_work < 0 ? -1.0 : kSeedPullWork;
   uint8_t *chosen = reinterpret_cast<uint8_t *>(b.next);       // F bytes
   uint32_t *rowbits = reinterpret_cast<uint32_t *>(b.mcount);  // ceil(N/32) words of N int64
   int2 *tasks = b.dlist;     // sum over features of ceil(n_i / kSeedChunk) <= 2 nnz entries
@@ -802,13 +861,13 @@ rr_status kmeanspp_seed(int64_t N, int64_t F, int64_t nnz, const int64_t *row_pt
   RR_LAUNCH(k_hot_assign, grid_for(F, kThreads), kThreads, 0, st, F, N, col_ptr, b.hot, b.hot_col,
             b.hot_n);
   for (int32_t t = 0; t < k; ++t) {
-    RR_LAUNCH_PDL(k_seed_pick, kSMs * 2, kThreads, 0, st, t, F, N, nnz, ntiles, seed, b.d2,
+    RR_LAUNCH_PDL(k_seed_pick, kSMs * 2, kThreads, 0, st, t, F, N, nnz, pw, ntiles, seed, b.d2,
                   b.part_i, chosen, col_ptr, row_idx, b.centers, rowbits, tasks, ntasks);
     if (t + 1 == k) break;   // the last centre's distances are not needed
-    RR_LAUNCH_PDL(k_seed_overlap, kSMs * 2, kThreads, 0, st, t, b.centers, N, nnz, row_ptr,
+    RR_LAUNCH_PDL(k_seed_overlap, kSMs * 2, kThreads, 0, st, t, b.centers, N, nnz, pw, row_ptr,
                   col_idx, col_ptr, row_idx, rowbits, tasks, ntasks, b.hot, b.hot_col, b.hot_n,
                   b.ov);
-    RR_LAUNCH_PDL(k_seed_update, (unsigned)ntiles, kThreads, 0, st, t, F, N, nnz, b.centers,
+    RR_LAUNCH_PDL(k_seed_update, (unsigned)ntiles, kThreads, 0, st, t, F, N, nnz, pw, b.centers,
                   col_ptr, b.ov, b.d2, b.part_i, chosen, rowbits, ntasks);
   }
   RR_CUDA(cudaStreamSynchronize(st));
@@ -922,9 +981,11 @@ rr_status kmeans_lloyd_step(int64_t N, int64_t F, const int64_t *row_ptr, const 
             (unsigned long long *)b.Q, (unsigned long long *)b.n_S);
   // (4) assignment
   RR_CUDA(cudaMemsetAsync(b.changes, 0, sizeof(int64_t), st));
+  RR_LAUNCH(k_score_terms, grid_for(k, kThreads), kThreads, 0, st, k,
+            (const unsigned long long *)b.Q, (const unsigned long long *)b.n_S, b.qr);
   RR_LAUNCH(k_lloyd_argmin, grid_for(F, kWarps), kThreads, 0, st, F, k, b.D,
-            (const unsigned long long *)b.Q, (const unsigned long long *)b.n_S, b.labels, b.next,
-            (unsigned long long *)b.changes);
+            (const unsigned long long *)b.Q, (const unsigned long long *)b.n_S, b.qr, b.labels,
+            b.next, (unsigned long long *)b.changes);
   // (5) prev <- labels <- next
   RR_CUDA(cudaMemcpyAsync(b.prev, b.labels, sizeof(int32_t) * F, cudaMemcpyDeviceToDevice, st));
   RR_CUDA(cudaMemcpyAsync(b.labels, b.next, sizeof(int32_t) * F, cudaMemcpyDeviceToDevice, st));

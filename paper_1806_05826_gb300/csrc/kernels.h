@@ -75,6 +75,7 @@ struct KmeansBuffers {
   int64_t *scan_scratch;
   int64_t *n_S;        // [k]
   int64_t *Q;          // [k]
+  float2 *qr;          // [k]   FP32 approximations of the score terms (argmin filter)
   int32_t *D;          // [F*k] D[i, S] = x_i . c_S for the current labels
   int64_t *changes;    // [1]
   int32_t *work_ctr;   // [1]
@@ -90,9 +91,16 @@ struct KmeansBuffers {
 // upper bound of the pull tasks: one per feature plus one per 1024 entries
 int64_t kmeans_pull_tasks_max(int64_t F, int64_t nnz);
 // K-means++ seeding (k centres into b.centers). Synchronises the stream.
+// pull_work: a centre c is pulled when n_c nnz / N exceeds it (0: kSeedPullWork,
+// < 0: never).
 rr_status kmeanspp_seed(int64_t N, int64_t F, int64_t nnz, const int64_t *row_ptr,
                         const int32_t *col_idx, const int64_t *col_ptr, const int32_t *row_idx,
-                        int32_t k, uint64_t seed, KmeansBuffers &b, cudaStream_t st);
+                        int32_t k, uint64_t seed, int64_t pull_work, KmeansBuffers &b,
+                        cudaStream_t st);
+// default pull threshold: a centre's overlaps are pulled when pushing them
+// would take more than about 5e5 atomic increments
+constexpr double kSeedPullWork = 5.0e5;
+
 // labels <- -1 except labels[centers[S]] = S; prev <- -1; D <- 0.
 // tiles of features of the seeding pass (tile sums in part_i)
 int64_t kmeans_seed_tiles(int64_t F);

@@ -565,6 +565,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&h->n_S, 2 * (int64_t)k));
   kb.n_S = h->n_S;
   RR_TRY(m.alloc(&kb.Q, k));
+  RR_TRY(m.alloc(&kb.qr, k));
   RR_TRY(m.alloc(&kb.D, F * (int64_t)k));
   RR_TRY(m.alloc(&kb.changes, 1));
   RR_TRY(m.alloc(&kb.work_ctr, 1));
@@ -588,7 +589,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
                             cudaMemcpyHostToDevice, st));
   } else {
     RR_TRY(rr::kmeanspp_seed(N, F, nnz, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx, k,
-                             h->opt.seed, kb, st));
+                             h->opt.seed, h->opt.seed_pull_work, kb, st));
   }
   RR_TRY(phase(2));
   RR_TRY(rr::kmeans_init_labels(F, k, kb, st));
@@ -618,6 +619,7 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   m.release(kb.d2);
   m.release(kb.ov);
   m.release(kb.Q);
+  m.release(kb.qr);
   m.release(kb.hot);
   m.release(kb.hot_col);
   m.release(kb.hot_n);

@@ -45,7 +45,7 @@ class rr_options(ctypes.Structure):
                 ("gather", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
                 ("lloyd_pull_work", ctypes.c_int64), ("coarse", ctypes.c_int32),
                 ("split_head", ctypes.c_int32), ("clustering", ctypes.c_int32),
-                ("lf_tol2", ctypes.c_double),
+                ("lf_tol2", ctypes.c_double), ("seed_pull_work", ctypes.c_int64),
                 ("stream", ctypes.c_void_p)]
 
 
@@ -226,7 +226,8 @@ def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=N
              kmeans_max_iter=50, max_iter=20000, solver=RR_SOLVER_TWOLEVEL, check_every=8,
              max_restarts=5, use_graphs=1, gram=RR_GRAM_AUTO, gather=RR_GATHER_AUTO,
              precision=RR_PREC_FP64, wait_limit=0, lloyd_pull_work=0, split_head=0,
-             coarse=0, clustering=RR_CLUSTER_KMEANS, lf_tol2=1.0, stream=None) -> Handle:
+             coarse=0, clustering=RR_CLUSTER_KMEANS, lf_tol2=1.0, seed_pull_work=0,
+             stream=None) -> Handle:
     """rr_setup on a binary CSR pattern given as numpy arrays (host) or torch
     CUDA tensors (device): row_ptr int64[N+1], col_idx int32[nnz]. With
     clustering = RR_CLUSTER_LEADER, k is the largest number of leaders."""
@@ -255,7 +256,7 @@ def rr_setup(row_ptr, col_idx, n_rows, n_cols, lam, k, *, seed=0, init_centers=N
                            max_restarts=max_restarts, use_graphs=use_graphs, gram=gram,
                            gather=gather, wait_limit=wait_limit, lloyd_pull_work=lloyd_pull_work,
                            split_head=split_head, coarse=coarse, clustering=clustering,
-                           lf_tol2=float(lf_tol2),
+                           lf_tol2=float(lf_tol2), seed_pull_work=int(seed_pull_work),
                            precision=precision, stream=_stream_ptr(stream))
     out = _P()
     _check(lib.rr_setup(ctypes.byref(X), float(lam), int(k), ctypes.byref(o), ctypes.byref(out)))

@@ -547,6 +547,21 @@ def test_lloyd_pull_branch_labels_bit_exact(case, rr):
     rr.rr_free(h)
 
 
+@pytest.mark.parametrize("pull_work", [-1, 1])
+def test_seeding_push_and_pull_centres_bit_exact(case, rr, pull_work):
+    """Each k-means++ round counts the overlaps with its new centre either row
+    by row with integer atomics (push) or column by column against a bitmap of
+    the centre's rows, for only the features whose distance can still drop
+    (pull; |x_i XOR x_c| >= |n_i - n_c| rules the others out). Forcing one form
+    for every round (seed_pull_work -1: always push; 1: pull whenever the centre
+    holds a row) must give the oracle's centres bit for bit either way."""
+    X = case["X"]
+    h = rr.rr_setup(X.row_ptr, X.col_idx, X.n_rows, X.n_cols, case["lam"], case["k"],
+                    seed=case["seed"], kmeans_max_iter=1, seed_pull_work=pull_work)
+    assert np.array_equal(rr.rr_get_centers(h, case["k"]), case["ref"].centers)
+    rr.rr_free(h)
+
+
 def test_bounded_wait_expiry_returns_timeout(rr):
     """The tensor-core Gram kernel's pipeline waits are bounded; with the
     test hook that makes each of them give up at once, the kernel records the
