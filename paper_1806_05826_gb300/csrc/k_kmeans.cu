@@ -212,18 +212,23 @@ __global__ void __launch_bounds__(kThreads) k_seed_overlap(
 }
 
 // d2[i] = min(d2[i], n_i + n_c - 2 ov[i]) (plain assignment for the first centre);
-// ov reset; tile_sum[tile] = sum of the tile's d2 (tiles of kTile features).
+// near[i] = t when centre t is strictly nearer than every earlier one (so the
+// nearest centre with ties to the earliest); ov reset; tile_sum[tile] = sum of
+// the tile's d2 (tiles of kTile features).
 __device__ __forceinline__ void seed_update_tile(int32_t t, int64_t tile, int64_t F, int64_t nc,
                                                  const int64_t *__restrict__ col_ptr, int32_t *ov,
-                                                 int64_t *d2, int64_t *tile_sum, int64_t *sm) {
+                                                 int64_t *d2, int32_t *near, int64_t *tile_sum,
+                                                 int64_t *sm) {
   int64_t s = 0;
   const int64_t i = tile * kTile + threadIdx.x;
   if (i < F) {
     const int64_t ni = col_ptr[i + 1] - col_ptr[i];
     const int64_t dist = ni + nc - 2 * (int64_t)__ldcg(&ov[i]);
     ov[i] = 0;
-    const int64_t v = (t == 0) ? dist : min(d2[i], dist);
+    const int64_t old = t == 0 ? 0 : __ldcg(&d2[i]);
+    const int64_t v = (t == 0) ? dist : min(old, dist);
     d2[i] = v;
+    if (t == 0 || dist < old) near[i] = t;
     s = v;
   }
   s = block_sum_i64(s, sm);
@@ -236,14 +241,14 @@ __global__ void __launch_bounds__(kThreads) k_seed_update(
     int32_t t, int64_t F, int64_t N, int64_t nnz, double pull_work,
     const int32_t *__restrict__ centers,
     const int64_t *__restrict__ col_ptr, int32_t *__restrict__ ov, int64_t *__restrict__ d2,
-    int64_t *__restrict__ tile_sum, uint8_t *__restrict__ chosen, uint32_t *__restrict__ rowbits,
-    int32_t *__restrict__ ntasks) {
+    int32_t *__restrict__ near, int64_t *__restrict__ tile_sum, uint8_t *__restrict__ chosen,
+    uint32_t *__restrict__ rowbits, int32_t *__restrict__ ntasks) {
   pdl_wait();
   __shared__ int64_t sm[kWarps + 1];
   const int64_t c = centers[t];
   if (c < 0) return;
   const int64_t nc = col_ptr[c + 1] - col_ptr[c];
-  seed_update_tile(t, blockIdx.x, F, nc, col_ptr, ov, d2, tile_sum, sm);
+  seed_update_tile(t, blockIdx.x, F, nc, col_ptr, ov, d2, near, tile_sum, sm);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     chosen[c] = 1;
     *ntasks = 0;
@@ -467,9 +472,17 @@ __global__ void k_max_row(int64_t N, const int64_t *__restrict__ row_ptr,
 }
 
 // per row: number of entries whose feature moved
+// the moved features' columns hold few entries (sw[0] of them): rows are found
+// through those columns instead of a scan of every row
+__device__ __forceinline__ bool moved_sparse(const unsigned long long *sw, int64_t nnz) {
+  return *sw * 8ull < (unsigned long long)nnz;
+}
+
 __global__ void k_moved_count(int64_t N, const int64_t *__restrict__ row_ptr,
                               const int32_t *__restrict__ col_idx, const int32_t *__restrict__ prev,
-                              const int32_t *__restrict__ cur, int64_t *__restrict__ cnt) {
+                              const int32_t *__restrict__ cur, int64_t *__restrict__ cnt,
+                              int64_t nnz, const unsigned long long *__restrict__ sw) {
+  if (sw && moved_sparse(sw, nnz)) return;   // the scatter filled cnt
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -488,6 +501,82 @@ __global__ void k_moved_count(int64_t N, const int64_t *__restrict__ row_ptr,
   }
 }
 
+// A step that moved features holding few entries in all finds the rows holding
+// them through their columns instead of scanning every row. The choice is made
+// on the device: sw[0] = the moved features' entries; the scatter runs when
+// 8 sw[0] < nnz, the full scan otherwise (each kernel returns at once when the
+// other one is chosen).
+// moved[0 .. n[0]) = the features whose label changed (one atomic per warp).
+__global__ void k_moved_list(int64_t F, const int64_t *__restrict__ col_ptr,
+                             const int32_t *__restrict__ prev, const int32_t *__restrict__ cur,
+                             int32_t *__restrict__ moved, int32_t *__restrict__ n,
+                             unsigned long long *__restrict__ sw) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < F; i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + threadIdx.x;
+    const bool m = i < F && prev[i] != cur[i];
+    const uint32_t bal = __ballot_sync(0xffffffffu, m);
+    unsigned long long e = m ? (unsigned long long)(col_ptr[i + 1] - col_ptr[i]) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    int32_t base = 0;
+    if (lane == 0 && bal) {
+      base = atomicAdd(n, __popc(bal));
+      atomicAdd(sw, e);
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (m) moved[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)i;
+  }
+}
+
+// cnt[r] += 2 for every moved feature of row r (cnt zeroed before): one moved
+// feature per warp over its column, eight entries per lane in flight, the
+// increments without return values.
+__global__ void k_moved_rows(int64_t nnz, const unsigned long long *__restrict__ sw,
+                             const int32_t *__restrict__ moved, const int32_t *__restrict__ n,
+                             const int64_t *__restrict__ col_ptr,
+                             const int32_t *__restrict__ row_idx,
+                             unsigned long long *__restrict__ cnt) {
+  if (!moved_sparse(sw, nnz)) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int32_t nm = n[0];
+  for (int64_t q = warp; q < nm; q += nwarps) {
+    const int32_t j = moved[q];
+    const int64_t e1 = col_ptr[j + 1];
+    for (int64_t e0 = col_ptr[j] + lane; e0 < e1; e0 += 32 * 8) {
+      int32_t r[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) r[u] = e0 + 32 * u < e1 ? row_idx[e0 + 32 * u] : -1;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (r[u] >= 0) atomicAdd(&cnt[r[u]], 2ull);
+    }
+  }
+}
+
+// rows[0 .. n[1]) = the rows with cnt[r] > 0 after a scatter; n[1] = -1 (every
+// row) after a full scan.
+__global__ void k_touched_rows(int64_t N, int64_t nnz, const unsigned long long *__restrict__ sw,
+                               const int64_t *__restrict__ cnt, int32_t *__restrict__ rows,
+                               int32_t *__restrict__ n) {
+  if (!moved_sparse(sw, nnz)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) n[1] = -1;
+    return;
+  }
+  const int lane = threadIdx.x & 31;
+  for (int64_t r0 = (int64_t)blockIdx.x * blockDim.x; r0 < N; r0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = r0 + threadIdx.x;
+    const bool m = r < N && cnt[r] > 0;
+    const uint32_t bal = __ballot_sync(0xffffffffu, m);
+    int32_t base = 0;
+    if (lane == 0 && bal) base = atomicAdd(&n[1], __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (m) rows[base + __popc(bal & ((1u << lane) - 1u))] = (int32_t)r;
+  }
+}
+
 // per row r: the net change of the row's cluster counts C[r, .] between the
 // previous and the current labels, as a list of distinct (cluster, delta)
 // pairs (delta != 0). A warp owns a row and a private shared histogram over
@@ -500,7 +589,8 @@ __global__ void k_row_delta(int64_t N, int32_t k, const int64_t *__restrict__ ro
                             const int32_t *__restrict__ col_idx, const int32_t *__restrict__ prev,
                             const int32_t *__restrict__ cur, const int64_t *__restrict__ dptr,
                             typename DeltaEntry<P>::T *__restrict__ dlist,
-                            int32_t *__restrict__ dcount, unsigned long long *__restrict__ work) {
+                            int32_t *__restrict__ dcount, unsigned long long *__restrict__ work,
+                            const int32_t *__restrict__ rows, const int32_t *__restrict__ nrows) {
   using E = DeltaEntry<P>;
   extern __shared__ int32_t hist_all[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -510,7 +600,11 @@ __global__ void k_row_delta(int64_t N, int32_t k, const int64_t *__restrict__ ro
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long my_work = 0;
-  for (int64_t r = warp; r < N; r += nwarps) {
+  // every row, or only the listed ones (the others' dcount is zero already)
+  const bool listed = rows && *nrows >= 0;
+  const int64_t nr = listed ? (int64_t)*nrows : N;
+  for (int64_t q = warp; q < nr; q += nwarps) {
+    const int64_t r = listed ? (int64_t)rows[q] : q;
     const int64_t b = row_ptr[r], e1 = row_ptr[r + 1];
     if (dptr[r + 1] == dptr[r]) {      // no moved entry in this row
       if (lane == 0) dcount[r] = 0;
@@ -698,12 +792,16 @@ __global__ void k_lloyd_push(int64_t N, int32_t k, const int64_t *__restrict__ r
                              const int32_t *__restrict__ col_idx, const int64_t *__restrict__ dptr,
                              const int32_t *__restrict__ dcount,
                              const typename DeltaEntry<P>::T *__restrict__ dlist,
-                             int32_t *__restrict__ D) {
+                             int32_t *__restrict__ D, const int32_t *__restrict__ rows,
+                             const int32_t *__restrict__ nrows) {
   using E = DeltaEntry<P>;
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t r = warp; r < N; r += nwarps) {
+  const bool listed = rows && *nrows >= 0;
+  const int64_t nr = listed ? (int64_t)*nrows : N;
+  for (int64_t q = warp; q < nr; q += nwarps) {
+    const int64_t r = listed ? (int64_t)rows[q] : q;
     const int32_t c = dcount[r];
     if (c == 0) continue;
     const typename E::T *lst = dlist + dptr[r];
@@ -842,7 +940,9 @@ __global__ void k_lloyd_argmin(int64_t F, int32_t k, const int32_t *__restrict__
 // with the pull list, overlaps with it, distance update), chained by
 // programmatic dependent launch: each kernel's launch overlaps the previous
 // one's tail, and no host synchronisation comes between rounds. The row bitmap
-// and the pull list live in buffers the Lloyd steps fill only later.
+// and the pull list live in buffers the Lloyd steps fill only later. The last
+// round's distances are computed too: prev[] ends holding every feature's
+// nearest centre (ties to the earliest), the first Lloyd assignment.
 rr_status kmeanspp_seed(int64_t N, int64_t F, int64_t nnz, const int64_t *row_ptr,
                         const int32_t *col_idx, const int64_t *col_ptr, const int32_t *row_idx,
                         int32_t k, uint64_t seed, int64_t pull_work, KmeansBuffers &b,
@@ -863,12 +963,11 @@ rr_status kmeanspp_seed(int64_t N, int64_t F, int64_t nnz, const int64_t *row_pt
   for (int32_t t = 0; t < k; ++t) {
     RR_LAUNCH_PDL(k_seed_pick, kSMs * 2, kThreads, 0, st, t, F, N, nnz, pw, ntiles, seed, b.d2,
                   b.part_i, chosen, col_ptr, row_idx, b.centers, rowbits, tasks, ntasks);
-    if (t + 1 == k) break;   // the last centre's distances are not needed
     RR_LAUNCH_PDL(k_seed_overlap, kSMs * 2, kThreads, 0, st, t, b.centers, N, nnz, pw, row_ptr,
                   col_idx, col_ptr, row_idx, rowbits, tasks, ntasks, b.hot, b.hot_col, b.hot_n,
                   b.ov);
     RR_LAUNCH_PDL(k_seed_update, (unsigned)ntiles, kThreads, 0, st, t, F, N, nnz, pw, b.centers,
-                  col_ptr, b.ov, b.d2, b.part_i, chosen, rowbits, ntasks);
+                  col_ptr, b.ov, b.d2, b.prev, b.part_i, chosen, rowbits, ntasks);
   }
   RR_CUDA(cudaStreamSynchronize(st));
   return RR_OK;
@@ -877,6 +976,38 @@ rr_status kmeanspp_seed(int64_t N, int64_t F, int64_t nnz, const int64_t *row_pt
 int64_t kmeans_seed_tiles(int64_t F) { return (F + kTile - 1) / kTile; }
 
 int64_t kmeans_pull_tasks_max(int64_t F, int64_t nnz) { return F + nnz / kPullRows + 1; }
+
+// The first Lloyd step from singleton clusters {c_S}: score(i, S) =
+// n_{c_S} - 2 |x_i AND x_{c_S}| = D2(i, c_S) - n_i, so its assignment is the
+// nearest centre with ties to the smallest S, which the seeding left in prev[].
+// labels <- prev[], the count of labels that differ from the singleton
+// labelling (-1 but labels[centers[S]] = S) into *changes_host; prev <- -1 and
+// D <- 0, so that the next step builds D from scratch for these labels.
+__global__ void k_count_diff(int64_t F, const int32_t *__restrict__ a, const int32_t *__restrict__ b,
+                             unsigned long long *__restrict__ n) {
+  unsigned long long c = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < F;
+       i += (int64_t)gridDim.x * blockDim.x)
+    c += a[i] != b[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(n, c);
+}
+
+rr_status kmeans_seeded_labels(int64_t F, int32_t k, KmeansBuffers &b, int64_t *changes_host,
+                               cudaStream_t st) {
+  RR_LAUNCH(k_init_labels, grid_for(F, kThreads), kThreads, 0, st, F, k, b.centers, b.next);
+  RR_LAUNCH(k_set_center_labels, grid_for(k, kThreads), kThreads, 0, st, k, b.centers, b.next);
+  RR_CUDA(cudaMemsetAsync(b.changes, 0, sizeof(int64_t), st));
+  RR_LAUNCH(k_count_diff, grid_for(F, kThreads), kThreads, 0, st, F, b.prev, b.next,
+            (unsigned long long *)b.changes);
+  RR_CUDA(cudaMemcpyAsync(b.labels, b.prev, sizeof(int32_t) * F, cudaMemcpyDeviceToDevice, st));
+  RR_LAUNCH(k_init_labels, grid_for(F, kThreads), kThreads, 0, st, F, k, b.centers, b.prev);
+  RR_CUDA(cudaMemsetAsync(b.D, 0, sizeof(int32_t) * (size_t)F * k, st));
+  RR_CUDA(cudaMemcpyAsync(changes_host, b.changes, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  return RR_OK;
+}
 
 rr_status kmeans_init_labels(int64_t F, int32_t k, KmeansBuffers &b, cudaStream_t st) {
   RR_LAUNCH(k_init_labels, grid_for(F, kThreads), kThreads, 0, st, F, k, b.centers, b.prev);
@@ -931,7 +1062,8 @@ rr_status kmeans_work_order(int64_t N, int64_t F, int32_t k, const int64_t *row_
 template <bool P>
 rr_status lloyd_delta_apply(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
                             const int64_t *col_ptr, const int32_t *row_idx, int32_t k,
-                            KmeansBuffers &b, unsigned long long pull_work, cudaStream_t st) {
+                            KmeansBuffers &b, unsigned long long pull_work, const int32_t *rows,
+                            const int32_t *nrows, cudaStream_t st) {
   using T = typename DeltaEntry<P>::T;
   T *dlist = reinterpret_cast<T *>(b.dlist);
   const int warps_per_cta = (int)std::max<int64_t>(1, std::min<int64_t>(kWarps, (96 * 1024) / (4 * (int64_t)k)));
@@ -939,7 +1071,7 @@ rr_status lloyd_delta_apply(int64_t N, int64_t F, const int64_t *row_ptr, const 
   RR_CUDA(cudaFuncSetAttribute(k_row_delta<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsmem));
   RR_LAUNCH(k_row_delta<P>, std::min<int64_t>((N + warps_per_cta - 1) / warps_per_cta, kSMs * 16),
             32 * warps_per_cta, hsmem, st, N, k, row_ptr, col_idx, b.prev, b.labels, b.mptr,
-            dlist, b.dcount, (unsigned long long *)b.work);
+            dlist, b.dcount, (unsigned long long *)b.work, rows, nrows);
   unsigned long long work = 0;
   RR_CUDA(cudaMemcpyAsync(&work, b.work, sizeof(work), cudaMemcpyDeviceToHost, st));
   RR_CUDA(cudaStreamSynchronize(st));
@@ -955,25 +1087,48 @@ rr_status lloyd_delta_apply(int64_t N, int64_t F, const int64_t *row_ptr, const 
               b.work_ctr, b.D);
   } else if (work > 0) {
     RR_LAUNCH(k_lloyd_push<P>, grid_for(N, kWarps), kThreads, 0, st, N, k, row_ptr, col_idx,
-              b.mptr, b.dcount, dlist, b.D);
+              b.mptr, b.dcount, dlist, b.D, rows, nrows);
   }
   return RR_OK;
 }
 
-rr_status kmeans_lloyd_step(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
-                            const int64_t *col_ptr, const int32_t *row_idx, int32_t k,
-                            KmeansBuffers &b, int64_t *changes_host, int64_t pull_work,
-                            cudaStream_t st) {
+rr_status kmeans_lloyd_step(int64_t N, int64_t F, int64_t nnz, const int64_t *row_ptr,
+                            const int32_t *col_idx, const int64_t *col_ptr, const int32_t *row_idx,
+                            int32_t k, KmeansBuffers &b, int64_t *changes_host, int64_t pull_work,
+                            int64_t moved, cudaStream_t st) {
   const unsigned long long pw = pull_work > 0 ? (unsigned long long)pull_work : kPushWorkLimit;
-  // (1) per-row delta lists of the cluster counts (prev -> labels)
+  // (1) per-row delta lists of the cluster counts (prev -> labels), with
+  // cnt[r] = 2 x the moved entries of row r: after the first step the moved
+  // features are listed and, when their columns hold few entries, the rows
+  // holding them are found through those columns and only they are visited
+  // (chosen on the device); otherwise every row counts its moved entries.
+  const int32_t *rows = nullptr, *nrows = nullptr;
+  unsigned long long *sw = nullptr;
+  if (moved >= 0) {
+    sw = reinterpret_cast<unsigned long long *>(b.sparse_n + 2);
+    RR_CUDA(cudaMemsetAsync(b.sparse_n, 0, 4 * sizeof(int32_t), st));
+    RR_CUDA(cudaMemsetAsync(b.mcount, 0, sizeof(int64_t) * N, st));
+    RR_CUDA(cudaMemsetAsync(b.dcount, 0, sizeof(int32_t) * N, st));
+    RR_LAUNCH(k_moved_list, grid_for(F, kThreads), kThreads, 0, st, F, col_ptr, b.prev, b.labels,
+              b.moved, b.sparse_n, sw);
+    RR_LAUNCH(k_moved_rows, kSMs * 8, kThreads, 0, st, nnz, sw, b.moved, b.sparse_n, col_ptr,
+              row_idx, (unsigned long long *)b.mcount);
+    rows = b.touched;
+    nrows = b.sparse_n + 1;
+  }
   RR_LAUNCH(k_moved_count, grid_for(N, kWarps), kThreads, 0, st, N, row_ptr, col_idx, b.prev,
-            b.labels, b.mcount);
+            b.labels, b.mcount, nnz, sw);
+  if (sw)
+    RR_LAUNCH(k_touched_rows, grid_for(N, kThreads), kThreads, 0, st, N, nnz, sw, b.mcount,
+              b.touched, b.sparse_n);
   RR_TRY(scan_exclusive(b.mcount, b.mptr, N, b.scan_scratch, st));
   RR_CUDA(cudaMemsetAsync(b.work, 0, sizeof(unsigned long long), st));
   if (b.packed)
-    RR_TRY(lloyd_delta_apply<true>(N, F, row_ptr, col_idx, col_ptr, row_idx, k, b, pw, st));
+    RR_TRY(lloyd_delta_apply<true>(N, F, row_ptr, col_idx, col_ptr, row_idx, k, b, pw, rows, nrows,
+                                   st));
   else
-    RR_TRY(lloyd_delta_apply<false>(N, F, row_ptr, col_idx, col_ptr, row_idx, k, b, pw, st));
+    RR_TRY(lloyd_delta_apply<false>(N, F, row_ptr, col_idx, col_ptr, row_idx, k, b, pw, rows,
+                                    nrows, st));
   // (3) sizes and Q from the updated D
   RR_CUDA(cudaMemsetAsync(b.n_S, 0, sizeof(int64_t) * k, st));
   RR_CUDA(cudaMemsetAsync(b.Q, 0, sizeof(int64_t) * k, st));

@@ -87,6 +87,9 @@ struct KmeansBuffers {
   int64_t *task_ptr;   // [F+1] first pull task of each feature in work order
   int32_t *task_it;    // [kmeans_pull_tasks_max(F, nnz)] feature (work-order index) of each task
   int64_t n_tasks;     // host: number of pull tasks (set by kmeans_work_order)
+  int32_t *moved;      // [F]   features whose label changed (steps after few changes)
+  int32_t *touched;    // [N]   rows holding them
+  int32_t *sparse_n;   // [4]   lengths of moved[] and touched[], the moved columns' entries (u64)
 };
 // upper bound of the pull tasks: one per feature plus one per 1024 entries
 int64_t kmeans_pull_tasks_max(int64_t F, int64_t nnz);
@@ -105,13 +108,20 @@ constexpr double kSeedPullWork = 5.0e5;
 // tiles of features of the seeding pass (tile sums in part_i)
 int64_t kmeans_seed_tiles(int64_t F);
 rr_status kmeans_init_labels(int64_t F, int32_t k, KmeansBuffers &b, cudaStream_t st);
+// After kmeanspp_seed: the first Lloyd step's result (each feature's nearest
+// centre, left by the seeding in b.prev) as labels, prev <- -1, D <- 0, and
+// the labels that differ from the singleton labelling in *changes_host.
+rr_status kmeans_seeded_labels(int64_t F, int32_t k, KmeansBuffers &b, int64_t *changes_host,
+                               cudaStream_t st);
 // One Lloyd assignment step; on return (stream synchronised) *changes_host holds
 // the number of labels that changed. pull_work: count updates above which the
 // step pulls per feature instead of pushing per row (<= 0: the default).
-rr_status kmeans_lloyd_step(int64_t N, int64_t F, const int64_t *row_ptr, const int32_t *col_idx,
-                            const int64_t *col_ptr, const int32_t *row_idx, int32_t k,
-                            KmeansBuffers &b, int64_t *changes_host, int64_t pull_work,
-                            cudaStream_t st);
+// moved: < 0 for the first step (every label -1 before it but the centres'),
+// else the number of labels the previous step changed.
+rr_status kmeans_lloyd_step(int64_t N, int64_t F, int64_t nnz, const int64_t *row_ptr,
+                            const int32_t *col_idx, const int64_t *col_ptr, const int32_t *row_idx,
+                            int32_t k, KmeansBuffers &b, int64_t *changes_host, int64_t pull_work,
+                            int64_t moved, cudaStream_t st);
 // order[] = features by descending work_i = sum of the row lengths of column i
 // (heaviest first); work[] receives work_i, which is also the Gershgorin row
 // sum of X^T X for binary X.

@@ -575,6 +575,9 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(m.alloc(&kb.hot_n, 1));
   RR_TRY(m.alloc(&kb.task_ptr, F + 1));
   RR_TRY(m.alloc(&kb.task_it, rr::kmeans_pull_tasks_max(F, nnz)));
+  RR_TRY(m.alloc(&kb.moved, F));
+  RR_TRY(m.alloc(&kb.touched, N));
+  RR_TRY(m.alloc(&kb.sparse_n, 4));
   if (h->opt.init_centers) {
     std::vector<char> seen(F, 0);
     for (int32_t s = 0; s < k; ++s) {
@@ -592,17 +595,27 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
                              h->opt.seed, h->opt.seed_pull_work, kb, st));
   }
   RR_TRY(phase(2));
-  RR_TRY(rr::kmeans_init_labels(F, k, kb, st));
+  // seeded here: the seeding's nearest centres are the first Lloyd step's labels
+  const bool seeded = !h->opt.init_centers && h->opt.kmeans_max_iter >= 1;
+  if (!seeded) RR_TRY(rr::kmeans_init_labels(F, k, kb, st));
   RR_TRY(m.alloc(&h->gsum, F));
   RR_TRY(rr::kmeans_work_order(N, F, k, h->row_ptr, h->col_ptr, h->row_idx, kb, h->gsum, scratch64, st));
   int64_t *changes_host = nullptr;
   RR_CUDA(cudaMallocHost(&changes_host, sizeof(int64_t)));
   int32_t it = 0;
   rr_status ks = RR_OK;
-  while (it < h->opt.kmeans_max_iter) {
+  bool done = false;
+  if (seeded) {
+    ks = rr::kmeans_seeded_labels(F, k, kb, changes_host, st);
+    it = 1;
+    done = ks != RR_OK || *changes_host == 0;
+  }
+  while (!done && it < h->opt.kmeans_max_iter) {
+    // the first step's moved features are the centres (labels of -1 before)
+    const int64_t moved = it == 0 ? -1 : *changes_host;
     ++it;
-    ks = rr::kmeans_lloyd_step(N, F, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx, k, kb,
-                               changes_host, h->opt.lloyd_pull_work, st);
+    ks = rr::kmeans_lloyd_step(N, F, nnz, h->row_ptr, h->col_idx, h->col_ptr, h->row_idx, k, kb,
+                               changes_host, h->opt.lloyd_pull_work, moved, st);
     if (ks != RR_OK || *changes_host == 0) break;
   }
   cudaFreeHost(changes_host);
@@ -625,6 +638,9 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   m.release(kb.hot_n);
   m.release(kb.task_ptr);
   m.release(kb.task_it);
+  m.release(kb.moved);
+  m.release(kb.touched);
+  m.release(kb.sparse_n);
 
   RR_TRY(phase(3));
   }

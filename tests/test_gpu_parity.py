@@ -562,6 +562,21 @@ def test_seeding_push_and_pull_centres_bit_exact(case, rr, pull_work):
     rr.rr_free(h)
 
 
+def test_seeding_wide_matrix_centres_bit_exact(rr):
+    """A wide, short matrix (300,000 features, 3,000 rows, most columns empty
+    or holding one row): the seeding must give the oracle's centres bit for
+    bit with either way of counting the overlaps and with the default choice."""
+    N, F, k = 3000, 300000, 40
+    X = synth.zipf_binary(N, F, 0.0002, 1.1, 3)
+    cp, ri = osp.csc_pattern(N, F, X.row_ptr, X.col_idx)
+    ref = okm.kmeanspp_binary(N, F, X.row_ptr, X.col_idx, cp, ri, k, 3)
+    for pull_work in (0, -1, 1):
+        h = rr.rr_setup(X.row_ptr, X.col_idx, N, F, 1e-2, k, seed=3, kmeans_max_iter=1,
+                        seed_pull_work=pull_work)
+        assert np.array_equal(rr.rr_get_centers(h, k), ref), pull_work
+        rr.rr_free(h)
+
+
 def test_bounded_wait_expiry_returns_timeout(rr):
     """The tensor-core Gram kernel's pipeline waits are bounded; with the
     test hook that makes each of them give up at once, the kernel records the
