@@ -249,16 +249,22 @@ __global__ void k_pcg_direction(int64_t F, const double *__restrict__ rz_part, i
   }
 }
 
+// The update, then (in the block that arrives last) the iteration's scalars:
+// rr = ||r||^2 from the blocks' partials (read through L2, in the same fixed
+// order as any other sum of partials), rho_old, iter++, convergence and
+// finiteness flags, the residual history.
 __global__ void k_pcg_update(int64_t F, const double *__restrict__ rz_part, int n_rz,
                              const double *__restrict__ pq_part, int n_pq,
                              const double *__restrict__ p, const double *__restrict__ q,
                              double *__restrict__ w, double *__restrict__ r, double omega,
                              const double *__restrict__ d, double *__restrict__ z1,
                              float *__restrict__ z1_32, double *__restrict__ rr_part,
-                             const PcgScalars *__restrict__ S, const double *__restrict__ wd) {
+                             PcgScalars *S, const double *__restrict__ wd,
+                             double *__restrict__ history, int32_t hist_cap) {
   pdl_wait();
   if (S->converged) return;
   __shared__ double sm[kWarps + 1];
+  __shared__ int32_t last;
   const double rho = sum_partials(rz_part, n_rz, sm);
   const double pq = sum_partials(pq_part, n_pq, sm);
   const double alpha = rho / pq;
@@ -276,18 +282,19 @@ __global__ void k_pcg_update(int64_t F, const double *__restrict__ rz_part, int 
     }
   }
   const double tot = block_sum(acc, sm);
-  if (threadIdx.x == 0) rr_part[blockIdx.x] = tot;
-}
-
-__global__ void k_pcg_finish(const double *__restrict__ rz_part, int n_rz,
-                             const double *__restrict__ rr_part, int n_rr, PcgScalars *S,
-                             double *__restrict__ history, int32_t hist_cap) {
-  pdl_wait();
-  if (S->converged) return;
-  __shared__ double sm[kWarps + 1];
-  const double rho = sum_partials(rz_part, n_rz, sm);
-  const double rr = sum_partials(rr_part, n_rr, sm);
   if (threadIdx.x == 0) {
+    rr_part[blockIdx.x] = tot;
+    __threadfence();
+    last = atomicAdd(&S->arrive, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += __ldcg(&rr_part[i]);
+  const double rr = block_sum(v, sm);
+  if (threadIdx.x == 0) {
+    S->arrive = 0;
     S->rho_old = rho;
     S->rr = rr;
     S->first = 0;
@@ -498,20 +505,15 @@ rr_status pcg_direction(int64_t F, const double *rz_part, int n_rz, const double
 rr_status pcg_update(int64_t F, const double *rz_part, int n_rz, const double *pq_part, int n_pq,
                      const double *p, const double *q, double *w, double *r, double omega,
                      const double *d, double *z1, double *rr_part, PcgScalars *S,
-                     cudaStream_t st, float *z1_32, const double *wd) {
+                     cudaStream_t st, float *z1_32, const double *wd, double *history,
+                     int32_t hist_cap) {
   RR_LAUNCH_PDL(k_pcg_update, kVecGrid, kThreads, 0, st, F, rz_part, n_rz, pq_part, n_pq, p, q, w, r,
-            omega, d, z1, z1_32, rr_part, S, wd);
+            omega, d, z1, z1_32, rr_part, S, wd, history, hist_cap);
   return RR_OK;
 }
 
 rr_status inner_start(PcgScalars *S, const int32_t *outer_converged, cudaStream_t st) {
   RR_LAUNCH_PDL(k_inner_start, 1, 32, 0, st, S, outer_converged);
-  return RR_OK;
-}
-
-rr_status pcg_finish(const double *rz_part, int n_rz, const double *rr_part, int n_rr,
-                     PcgScalars *S, double *history, int32_t hist_cap, cudaStream_t st) {
-  RR_LAUNCH_PDL(k_pcg_finish, 1, kThreads, 0, st, rz_part, n_rz, rr_part, n_rr, S, history, hist_cap);
   return RR_OK;
 }
 

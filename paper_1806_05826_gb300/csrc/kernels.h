@@ -362,6 +362,7 @@ struct PcgScalars {
   int32_t nonfinite; // 1 if a NaN/Inf was met
   int32_t first;     // 1 before the first direction of a (re)start
   int32_t limit;     // iteration limit of the device-side loop
+  uint32_t arrive;   // blocks of the update kernel done (0 between launches)
 };
 constexpr int kVecGrid = kSMs * 2;   // fixed grid of the vector kernels (deterministic partials)
 
@@ -417,19 +418,17 @@ rr_status jacobi(int64_t F, double omega, const double *r, const double *d, doub
 rr_status pcg_direction(int64_t F, const double *rz_part, int n_rz, const double *z, double *p,
                         PcgScalars *S, cudaStream_t st, float *p32 = nullptr);
 // alpha = rho / <p,q>; w += alpha p; r -= alpha q; partial ||r||^2;
-// z1 = omega r / d when z1 != nullptr.
+// z1 = omega r / d when z1 != nullptr; then the iteration's scalars: rr =
+// ||r||^2, rho_old = rho, iter++, convergence and finiteness flags,
+// history[iter-1] = ||r|| / ||b|| when iter <= hist_cap.
 rr_status pcg_update(int64_t F, const double *rz_part, int n_rz, const double *pq_part, int n_pq,
                      const double *p, const double *q, double *w, double *r, double omega,
                      const double *d, double *z1, double *rr_part, PcgScalars *S,
-                     cudaStream_t st, float *z1_32 = nullptr,
-                     const double *wd = nullptr);
+                     cudaStream_t st, float *z1_32 = nullptr, const double *wd = nullptr,
+                     double *history = nullptr, int32_t hist_cap = 0);
 // Fresh scalars for a fixed number of plain CG steps inside another solver's
 // iteration (no stopping target; stopped when *outer_converged).
 rr_status inner_start(PcgScalars *S, const int32_t *outer_converged, cudaStream_t st);
-// rr = sum(rr_part); rho_old = sum(rz_part); iter++; convergence and finiteness flags;
-// history[iter-1] = ||r|| / ||b|| when iter <= hist_cap.
-rr_status pcg_finish(const double *rz_part, int n_rz, const double *rr_part, int n_rr,
-                     PcgScalars *S, double *history, int32_t hist_cap, cudaStream_t st);
 // per-block partial <a, b> into part[0..kVecGrid).
 rr_status dot_parts(int64_t n, const double *a, const double *b, double *part, cudaStream_t st);
 // (Re)starts PCG: bnorm/target from <b,b> partials if set_bnorm, rr from <r,r> partials.

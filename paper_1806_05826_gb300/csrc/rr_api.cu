@@ -230,6 +230,7 @@ rr_status alloc_solve_workspace(rr_handle *h) {
     RR_TRY(m.alloc(v, h->n_parts));
   RR_TRY(m.alloc(&h->scal, 4));
   RR_TRY(m.alloc(&h->S, 1));
+  RR_CUDA(cudaMemsetAsync(h->S, 0, sizeof(rr::PcgScalars), h->st));
   RR_CUDA(cudaMallocHost(&h->S_host, sizeof(rr::PcgScalars)));
   RR_CUDA(cudaMallocHost(&h->scal_host, 4 * sizeof(double)));
   RR_CUDA(cudaMallocHost(&h->limit_host, sizeof(int32_t)));
@@ -815,9 +816,8 @@ rr_status pcg_iteration(rr_handle *h, cudaStream_t st) {
   RR_TRY(rr::pcg_update(F, h->part_rz, n_rz, h->part_pq, rr::kVecGrid, h->p, h->q, h->w_int,
                         h->r, h->omega, h->d, twolevel ? h->z1 : nullptr, h->part_rr, h->S, st,
                         twolevel ? x32 : nullptr,
-                        (fp32 && h->split.active) ? h->split.wd : nullptr));
-  RR_TRY(rr::pcg_finish(h->part_rz, n_rz, h->part_rr, rr::kVecGrid, h->S, h->history,
-                        h->hist_cap, st));
+                        (fp32 && h->split.active) ? h->split.wd : nullptr, h->history,
+                        h->hist_cap));
   return RR_OK;
 }
 
@@ -1016,6 +1016,7 @@ rr_status tlfcg_reserve(rr_handle *h) {
   for (double **v : {&h->tz, &h->tr, &h->tp, &h->tq, &h->tzz}) RR_TRY(h->mem.alloc(v, h->F));
   for (double **v : {&h->t_rz, &h->t_pq, &h->t_rr}) RR_TRY(h->mem.alloc(v, rr::kVecGrid));
   RR_TRY(h->mem.alloc(&h->St, 1));
+  RR_CUDA(cudaMemsetAsync(h->St, 0, sizeof(rr::PcgScalars), h->st));
   return RR_OK;
 }
 
@@ -1037,7 +1038,6 @@ rr_status tlfcg_iteration(rr_handle *h, cudaStream_t st) {
     RR_TRY(op_apply(h, h->tp, ap, istop, st, fp32));
     RR_TRY(rr::pcg_update(F, h->t_rz, rr::kVecGrid, h->t_pq, rr::kVecGrid, h->tp, h->tq, h->tz,
                           h->tr, 1.0, nullptr, nullptr, h->t_rr, h->St, st));
-    RR_TRY(rr::pcg_finish(h->t_rz, rr::kVecGrid, h->t_rr, rr::kVecGrid, h->St, nullptr, 0, st));
   }
   RR_TRY(rr::restrict_clusters(h->rplan, h->members, h->tr, h->s, stop, st));
   RR_TRY(coarse_step(h, stop, st, fp32));
