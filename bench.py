@@ -581,25 +581,28 @@ def measure_leader(rr, row_ptr, col_idx, N, F, lams, opts, dev, y_dev, tol2s, ca
     return out
 
 
-def measure_tlfcg(rr, row_ptr, col_idx, N, F, k, lams, opts, y_dev, last_infos):
+def measure_tlfcg(rr, row_ptr, col_idx, N, F, k, lams, opts, y_dev):
     """The same systems (each lambda, same target, same clustering) solved by the
     paper's TLFCG: flexible CG whose preconditioner is two CG rougher steps and the
-    coarse correction; against the plain two-level PCG of the timed step."""
+    coarse correction; against the plain two-level PCG, both one weight after the
+    other on one handle (rr_set_lambda)."""
     import torch
-    h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], k, **dict(opts, solver=rr.RR_SOLVER_TLFCG))
     w = torch.empty(F, dtype=torch.float64, device=y_dev.device)
+    runs = {}
+    for name, solver in (("tlfcg", rr.RR_SOLVER_TLFCG), ("pcg", rr.RR_SOLVER_TWOLEVEL)):
+        h = rr.rr_setup(row_ptr, col_idx, N, F, lams[0], k, **dict(opts, solver=solver))
+        runs[name] = []
+        for j, lam in enumerate(lams):
+            if j:
+                rr.rr_set_lambda(h, lam)
+            runs[name].append(rr.rr_solve(h, y_dev, w, tol=TOL))
+        rr.rr_free(h)
     out = {"method": "FCG(1), preconditioner: 2 CG steps on A z = r, then the coarse correction",
-           "iters": [], "solve_ms": [], "true_rel_res": []}
-    for j, lam in enumerate(lams):
-        if j:
-            rr.rr_set_lambda(h, lam)
-        info = rr.rr_solve(h, y_dev, w, tol=TOL)
-        out["iters"].append(info["iters"])
-        out["solve_ms"].append(round(info["solve_ms"], 2))
-        out["true_rel_res"].append(info["true_rel_res"])
-    rr.rr_free(h)
-    out["pcg_iters"] = [i["iters"] for i in last_infos]
-    out["pcg_solve_ms"] = [round(i["solve_ms"], 2) for i in last_infos]
+           "iters": [i["iters"] for i in runs["tlfcg"]],
+           "solve_ms": [round(i["solve_ms"], 2) for i in runs["tlfcg"]],
+           "true_rel_res": [i["true_rel_res"] for i in runs["tlfcg"]]}
+    out["pcg_iters"] = [i["iters"] for i in runs["pcg"]]
+    out["pcg_solve_ms"] = [round(i["solve_ms"], 2) for i in runs["pcg"]]
     out["speedup_vs_pcg"] = round(sum(out["pcg_solve_ms"]) / max(1e-9, sum(out["solve_ms"])), 3)
     return out
 
@@ -905,16 +908,28 @@ def run_ours(args, rank, world, local):
         else:
             h = rr.rr_setup(host["rp"], host["ci"], N, F, lams[0], k, **opts)
             yd = host["y"].to(dev, non_blocking=True)
-        # the coarse levels of the other weights, built while the first one solves
-        rr.rr_prepare_lambdas(h, lams[1:])
-        infos = []
-        for j, lam in enumerate(lams):
-            if j:
-                rr.rr_set_lambda(h, lam)
-            infos.append(rr.rr_solve(h, yd, W[j], tol=TOL))
-            if host is not None:
-                host["w"][j].copy_(W[j], non_blocking=True)
+        if args.no_graphs:
+            # host-issued loops (the profiling form): one weight after the other,
+            # the coarse levels of the others built while the first one solves
+            rr.rr_prepare_lambdas(h, lams[1:])
+            infos = []
+            for j, lam in enumerate(lams):
+                if j:
+                    rr.rr_set_lambda(h, lam)
+                infos.append(rr.rr_solve(h, yd, W[j], tol=TOL))
+        else:
+            # a fork per further weight (its coarse factor starts at once on its
+            # own stream), then the weights' CG loops as branches of one graph
+            forks = [rr.rr_fork_lambda(h, lam) for lam in lams[1:]]
+            res = rr.rr_solve_many([h] + forks, [yd] * len(lams), W, tol=TOL, stream=stream)
+            infos = res["infos"]
+            for inf in infos:
+                inf["status"] = res["status"]   # the call's status (RR_OK: every weight converged)
+            for f in forks:
+                rr.rr_free(f)
         if host is not None:
+            for j in range(len(lams)):
+                host["w"][j].copy_(W[j], non_blocking=True)
             torch.cuda.current_stream(dev).synchronize()
         rr.rr_free(h)
         return infos
@@ -990,7 +1005,7 @@ def run_ours(args, rank, world, local):
     if not args.no_leader and args.workload == WORKLOAD:
         leader = measure_leader(rr, row_ptr, col_idx, N, F, lams, opts, dev, y_dev, LEADER_TOL2)
     if not args.no_tlfcg:
-        tlfcg = measure_tlfcg(rr, row_ptr, col_idx, N, F, k, lams, opts, y_dev, last_infos=all_infos[-1])
+        tlfcg = measure_tlfcg(rr, row_ptr, col_idx, N, F, k, lams, opts, y_dev)
     if not args.no_batch and args.workload == WORKLOAD:
         batched = measure_batched(rr, X, row_ptr, col_idx, k, opts, dev, stream, world,
                                   args.batch_targets)
@@ -1027,7 +1042,11 @@ def run_ours(args, rank, world, local):
                           ["copy_validate", "csc_build", "kmeanspp_seed", "lloyd", "clusters",
                            "coarse_gram", "coarse_factor", "sliced_patterns"],
                           [round(v, 2) for v in last[0]["setup_phase_ms"]])),
-                      "solve_ms": [round(i["solve_ms"], 2) for i in last],
+                      "solve_ms": ([round(i["solve_ms"], 2) for i in last] if args.no_graphs
+                                   else round(last[0]["solve_ms"], 2)),
+                      "solve_form": ("one weight after the other (rr_set_lambda)" if args.no_graphs
+                                     else "concurrent: rr_fork_lambda per further weight, "
+                                          "rr_solve_many over the three"),
                       "iters": [i["iters"] for i in last],
                       "restarts": [i["restarts"] for i in last],
                       "true_rel_res": [i["true_rel_res"] for i in last],

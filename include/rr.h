@@ -224,6 +224,27 @@ rr_status rr_set_lambda(rr_handle *h, double lambda);
  * is reported by the rr_set_lambda that installs it (RR_NOT_SPD). */
 rr_status rr_prepare_lambdas(rr_handle *h, const double *lambdas, int32_t n);
 
+/* A handle for another lambda on the same X (Section 2 poses one X with
+ * several beta; Section 4 refactors only the coarse operator when beta
+ * changes). The fork shares base's setup that does not depend on lambda: X
+ * and its transpose, the clustering, the coarse Gram and the operator's
+ * patterns. It owns the coarse operator, factor and inverse at `lambda`, the
+ * smoother, the solve vectors and scalars, the operator's intermediate
+ * vectors and a stream of its own (non-blocking): rr_solve and rr_set_lambda
+ * on it behave as on a handle set up at that lambda with the same clustering
+ * (the same bits), and rr_solve_many solves base and forks concurrently. The
+ * smoother is built before returning; the coarse factor is left running on
+ * the fork's stream, and rr_solve_many starts the fork's problem only once it
+ * is done (the other problems start at once). base must outlive its forks, and
+ * is not otherwise changed; a fork of a fork, or of a dense-X handle, is not
+ * supported. rr_solve_batch, rr_bayes and rr_prepare_lambdas reject forks.
+ * rr_free(fork) frees only what the fork owns. Device memory: about 13 F + 3 N
+ * doubles plus the coarse level (3 k_eff^2 doubles) and the operator's
+ * intermediate vectors. Errors: RR_INVALID_ARG (NULL argument, lambda not
+ * positive and finite), RR_UNSUPPORTED, RR_OOM, RR_CUDA_ERROR; a non-positive
+ * pivot of the fork's factor is reported by its first solve (RR_NOT_SPD). */
+rr_status rr_fork_lambda(rr_handle *base, double lambda, rr_handle **out);
+
 /* Solves Eq. (1) for one right-hand side by CG preconditioned as
  * rr_options.solver says (RR_SOLVER_TLFCG: flexible CG, Algorithm 3 with
  * m = 1, as rr_solve_fcg without a network), from w_0 = 0 (Algorithm 3's

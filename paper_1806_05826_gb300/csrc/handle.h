@@ -127,5 +127,9 @@ struct rr_handle {
   double *t_rz = nullptr, *t_pq = nullptr, *t_rr = nullptr;
   rr::PcgScalars *St = nullptr;
   void *fcg_cache = nullptr;   // the FCG loop graph without a network (kept until lambda changes)
+  // rr_fork_lambda: the handle whose X-dependent setup this one shares (nullptr:
+  // none), and the event recorded after this handle's coarse factor
+  rr_handle *fork_of = nullptr;
+  cudaEvent_t ready = nullptr;
   DevArena mem;
 };

@@ -1296,6 +1296,10 @@ extern "C" rr_status rr_solve_batch(rr_handle *h, int32_t nrhs, const double *Y,
     rr_set_error("rr_solve_batch: more than 2^20 systems");
     return RR_INVALID_ARG;
   }
+  if (h->fork_of) {
+    rr_set_error("rr_solve_batch: not supported on a handle from rr_fork_lambda");
+    return RR_UNSUPPORTED;
+  }
   if (h->dense) {
     rr_set_error("rr_solve_batch: the batched engine takes binary X only");
     return RR_UNSUPPORTED;

@@ -1257,8 +1257,9 @@ rr_status build_many_graph(int32_t n, rr_handle *const *hs, ManyGraph &G, std::v
     cp.conditional.handle = hc;
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    RR_CUDA(cudaGraphAddNode(&node, G.g, nullptr, nullptr, 0, &cp));
+    cudaGraphNode_t wait = nullptr, node;
+    if (h->fork_of && h->ready) RR_CUDA(cudaGraphAddEventWaitNode(&wait, G.g, nullptr, 0, h->ready));
+    RR_CUDA(cudaGraphAddNode(&node, G.g, wait ? &wait : nullptr, nullptr, wait ? 1 : 0, &cp));
     cudaStream_t cs = h->cap_stream;
     RR_CUDA(cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
                                           cudaStreamCaptureModeThreadLocal));
@@ -1608,6 +1609,149 @@ rr_status rr_set_lambda(rr_handle *h, double lambda) {
   return RR_OK;
 }
 
+// A handle for another lambda that shares base's X-dependent setup (X and
+// its transpose, the clustering, the coarse Gram, the operator's patterns) and
+// owns what depends on lambda or is written while it solves: the coarse
+// inverse, the smoother, the solve vectors and scalars, the operator's
+// intermediate vectors, its error word and its own stream. d and omega are
+// built first (omega is read back: the captured kernels take it by value);
+// the coarse factor then runs on the fork's stream and is marked by an event,
+// so that rr_solve_many starts the other problems at once.
+rr_status fork_impl(rr_handle *base, double lambda, rr_handle *f) {
+  DevArena &m = f->mem;
+  cudaStream_t st = f->st;
+  const int64_t F = f->F, k = f->k_eff;
+  RR_TRY(m.alloc(&f->err, 1));
+  RR_CUDA(cudaMemsetAsync(f->err, 0, sizeof(int32_t), st));
+  RR_CUDA(cudaMallocHost(&f->err_host, sizeof(int32_t)));
+  RR_TRY(alloc_solve_workspace(f));
+  RR_TRY(m.alloc(&f->d, F));
+  RR_TRY(m.alloc(&f->omega_dev, 1));
+  RR_TRY(m.alloc(&f->max_bits, 1));
+  RR_TRY(m.alloc(&f->Ac, k * k));
+  if (f->mu) {
+    RR_TRY(m.alloc(&f->dvec, k));
+    RR_TRY(m.alloc(&f->ec_tmp, k));
+  } else {
+    RR_TRY(m.alloc(&f->Lw, k * k));
+    RR_TRY(m.alloc(&f->Linv, k * k));
+    RR_TRY(m.alloc(&f->Ainv, k * k));
+    if (base->Ainv32) RR_TRY(m.alloc(&f->Ainv32, k * ((k + 3) & ~(int64_t)3)));
+  }
+  // the operator's intermediate vectors
+  auto own_pattern = [&](rr::SlicedPattern &P) -> rr_status {
+    if (!P.idx) return RR_OK;
+    double *xq = nullptr, *psum = nullptr;
+    RR_TRY(m.alloc(&xq, std::max<int64_t>(1, P.n_inner)));
+    RR_TRY(m.alloc(&psum, std::max<int64_t>(1, P.npieces)));
+    P.xq = xq;
+    P.psum = psum;
+    P.err = f->err;
+    return RR_OK;
+  };
+  RR_TRY(own_pattern(f->pcsr));
+  RR_TRY(own_pattern(f->pcsc));
+  if (f->split.active) {
+    float *zp = nullptr, *up = nullptr;
+    RR_TRY(m.alloc(&zp, (int64_t)f->split.nblk * f->split.H));
+    RR_TRY(m.alloc(&up, std::max<int32_t>(1, f->split.nblk)));
+    f->split.zpart = zp;
+    f->split.upart = up;
+    RR_TRY(m.alloc(&f->split.wd, F));
+    RR_TRY(own_pattern(f->split.xt));
+    RR_TRY(own_pattern(f->split.xtt));
+  }
+  if (f->rplan.k > 0) {
+    RR_TRY(m.alloc(&f->rplan.item_sum, std::max<int32_t>(1, f->rplan.n_items)));
+    RR_TRY(m.alloc(&f->rplan.rc, std::max<int32_t>(1, f->rplan.k)));
+  }
+  // the smoother at lambda, omega read back
+  RR_CUDA(cudaMemsetAsync(f->max_bits, 0, sizeof(unsigned long long), st));
+  RR_LAUNCH(k_jacobi_setup, rr::grid_for(F, kThreads), kThreads, 0, st, F, lambda, f->col_ptr,
+            f->gsum, f->d, f->max_bits);
+  RR_LAUNCH(k_omega, 1, 32, 0, st, f->max_bits, f->omega_dev);
+  double om = 0.0;
+  RR_CUDA(cudaMemcpyAsync(&om, f->omega_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  f->omega = om;
+  f->lambda = lambda;
+  RR_TRY(rr::split_set_wd(f->split, f->omega, f->d, st));
+  // the coarse level, left running
+  RR_TRY(rr::coarse_operator((int32_t)k, f->G, f->s, lambda, f->Ac, st));
+  if (f->mu) {
+    RR_TRY(rr::eig_dvec((int32_t)k, f->mu, lambda, f->dvec, st));
+  } else {
+    RR_CUDA(cudaMemcpyAsync(f->Lw, f->Ac, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, st));
+    RR_TRY(rr::cholesky((int32_t)k, f->Lw, f->err, st));
+    RR_TRY(rr::chol_inverse((int32_t)k, f->Lw, f->Linv, f->Ainv, st));
+    if (f->Ainv32) RR_TRY(rr::coarse_to_f32((int32_t)k, f->Ainv, f->Ainv32, st));
+  }
+  RR_CUDA(cudaEventCreateWithFlags(&f->ready, cudaEventDisableTiming));
+  RR_CUDA(cudaEventRecord(f->ready, st));
+  return RR_OK;
+}
+
+rr_status rr_fork_lambda(rr_handle *base, double lambda, rr_handle **out) {
+  NvtxRange nvtx_range("rr_fork_lambda");
+  if (!base || !out) {
+    rr_set_error("rr_fork_lambda: NULL argument");
+    return RR_INVALID_ARG;
+  }
+  *out = nullptr;
+  if (!(lambda > 0.0) || !isfinite(lambda)) {
+    rr_set_error("rr_fork_lambda: lambda must be positive and finite");
+    return RR_INVALID_ARG;
+  }
+  if (base->dense || base->fork_of) {
+    rr_set_error("rr_fork_lambda: forks of dense-X handles or of forks are not supported");
+    return RR_UNSUPPORTED;
+  }
+  RR_CUDA(cudaStreamSynchronize(base->st));
+  rr_handle *f = new rr_handle(*base);
+  // nothing of base's is owned by the fork: every owned field starts empty
+  f->mem.ptrs.clear();
+  f->fork_of = base;
+  f->ready = nullptr;
+  f->st = nullptr;
+  f->cap_stream = nullptr;
+  f->loop_graph = nullptr;
+  f->loop_exec = nullptr;
+  f->limit_host = nullptr;
+  f->body_kernels = 0;
+  f->S = f->S_host = nullptr;
+  f->scal_host = nullptr;
+  f->err = f->err_host = nullptr;
+  f->batch = nullptr;
+  f->bayes_y = nullptr;
+  for (auto &P : f->prep) P = rr_handle::Prepared{};
+  f->prep_st = nullptr;
+  f->prep_Ac = f->prep_Lw = f->prep_Linv = nullptr;
+  f->bplan = rr::RestrictPlan{};
+  f->p_prev = f->q_prev = f->part_zq = f->part3 = nullptr;
+  f->Sf = f->Sf_host = nullptr;
+  f->tz = f->tr = f->tp = f->tq = f->tzz = nullptr;
+  f->t_rz = f->t_pq = f->t_rr = nullptr;
+  f->St = nullptr;
+  f->fcg_cache = nullptr;
+  f->Lw = f->Linv = f->Ainv = nullptr;
+  f->Ainv32 = nullptr;
+  f->dvec = f->ec_tmp = nullptr;
+  if (cudaStreamCreateWithFlags(&f->st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    f->st = nullptr;
+    rr_free(f);
+    rr_set_error("rr_fork_lambda: cudaStreamCreate failed");
+    return RR_CUDA_ERROR;
+  }
+  const rr_status s = fork_impl(base, lambda, f);
+  if (s != RR_OK) {
+    rr_free(f);
+    return s;
+  }
+  *out = f;
+  return RR_OK;
+}
+
 rr_status rr_prepare_lambdas(rr_handle *h, const double *lambdas, int32_t n) {
   NvtxRange nvtx_range("rr_prepare_lambdas");
   if (!h || (n > 0 && !lambdas) || n < 0 || n > rr_handle::kPrepared) {
@@ -1620,6 +1764,10 @@ rr_status rr_prepare_lambdas(rr_handle *h, const double *lambdas, int32_t n) {
       rr_set_error("rr_prepare_lambdas: every lambda must be positive and finite");
       return RR_INVALID_ARG;
     }
+  if (h->fork_of) {
+    rr_set_error("rr_prepare_lambdas: not supported on a handle from rr_fork_lambda");
+    return RR_UNSUPPORTED;
+  }
   if (h->mu || n == 0) return RR_OK;   // the eigen form's lambda change is one vector rescale
   const int64_t kk = (int64_t)h->k_eff * h->k_eff;
   if (!h->prep_st) {
@@ -1738,7 +1886,10 @@ rr_status rr_solve_many(int32_t nprob, rr_handle *const *hs, const double *const
   // every problem's work is issued on `stream` for the duration of the call
   // (every handle's own stream is drained before any handle is switched, so
   // that an error return leaves all handles on their own streams)
-  for (int32_t i = 0; i < nprob; ++i) RR_CUDA(cudaStreamSynchronize(hs[i]->st));
+  // (a fork's coarse factor may still run on its stream: the fork's branch of
+  // the graph waits on its event instead, so the other problems start at once)
+  for (int32_t i = 0; i < nprob; ++i)
+    if (!hs[i]->fork_of || !hs[i]->ready) RR_CUDA(cudaStreamSynchronize(hs[i]->st));
   std::vector<cudaStream_t> saved(nprob);
   for (int32_t i = 0; i < nprob; ++i) {
     saved[i] = hs[i]->st;
@@ -1851,6 +2002,10 @@ rr_status rr_get_coarse(const rr_handle *h, double *Ac_host, int64_t *G_host) {
 rr_status rr_bayes(rr_handle *h, const double *y, const rr_bayes_params *p, int32_t n_samples,
                    int32_t burnin, double *w_mean, double *lam_trace, double *tau_trace,
                    int32_t *iters) {
+  if (h && h->fork_of) {
+    rr_set_error("rr_bayes: not supported on a handle from rr_fork_lambda");
+    return RR_UNSUPPORTED;
+  }
   NvtxRange nvtx_range("rr_bayes");
   if (!h || !y || !p) {
     rr_set_error("rr_bayes: handle, y and params must not be NULL");
@@ -1925,6 +2080,21 @@ rr_status rr_query(const rr_handle *h, int64_t *n_rows, int64_t *n_cols, int32_t
 
 void rr_free(rr_handle *h) {
   if (!h) return;
+  if (h->fork_of) {   // its own allocations, streams, events and pinned words only
+    if (h->st) cudaStreamSynchronize(h->st);
+    destroy_graph(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->limit_host) cudaFreeHost(h->limit_host);
+    if (h->ready) cudaEventDestroy(h->ready);
+    h->mem.free_all();
+    if (h->err_host) cudaFreeHost(h->err_host);
+    if (h->S_host) cudaFreeHost(h->S_host);
+    if (h->scal_host) cudaFreeHost(h->scal_host);
+    if (h->Sf_host) cudaFreeHost(h->Sf_host);
+    if (h->st) cudaStreamDestroy(h->st);
+    delete h;
+    return;
+  }
   cudaStreamSynchronize(h->st);
   destroy_graph(h);
   rr::batch_free(h->batch);

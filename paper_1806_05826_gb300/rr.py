@@ -87,6 +87,7 @@ _SIGS = {
                                 ctypes.POINTER(rr_options), ctypes.POINTER(_P)]),
     "rr_set_lambda": (ctypes.c_int, [_P, ctypes.c_double]),
     "rr_prepare_lambdas": (ctypes.c_int, [_P, _P, ctypes.c_int32]),
+    "rr_fork_lambda": (ctypes.c_int, [_P, ctypes.c_double, _P]),
     "rr_solve": (ctypes.c_int, [_P, _P, _P, ctypes.c_double, ctypes.POINTER(rr_info)]),
     "rr_solve_batch": (ctypes.c_int, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P,
                                       ctypes.c_double, _P]),
@@ -330,6 +331,14 @@ def rr_solve_batch(h: Handle, Y, lambdas, W, tol=1e-8) -> dict:
         raise RRError(st, rr_last_error())
     return {"status": _STATUS[st],
             "infos": [[infos[l * nrhs + j].as_dict() for j in range(nrhs)] for l in range(nlam)]}
+
+
+def rr_fork_lambda(h: Handle, lam) -> Handle:
+    """rr_fork_lambda: a handle for weight lam sharing h's X-dependent setup
+    (h must outlive it; rr_free it before h)."""
+    out = _P()
+    _check(load().rr_fork_lambda(h.ptr, float(lam), ctypes.byref(out)))
+    return Handle(out, h.F, h.N, (h,), h.k)
 
 
 def rr_solve_many(hs, ys, ws, tol=1e-8, stream=None) -> dict:

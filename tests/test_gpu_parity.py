@@ -596,6 +596,61 @@ def test_bounded_wait_expiry_returns_timeout(rr):
     rr.rr_free(h)
 
 
+def test_fork_lambda_gives_identical_bits(rr):
+    """rr_fork_lambda shares the base handle's X-dependent setup and builds its
+    own coarse level and smoother: its solve must equal, bit for bit, the base
+    re-targeted by rr_set_lambda (the same kernels on the same inputs), in both
+    precisions; rr_solve_many over the base and its forks (each fork's branch
+    waiting for its own factor) must equal the solves one at a time; the base
+    solves on unchanged afterwards; unsupported uses are refused."""
+    X = synth.zipf_binary(2000, 1000, 0.01, 1.1, 0)
+    y, _ = synth.ridge_targets(X, 0)
+    lams = (1e-2, 1e-3, 0.3)
+    yd = dev(y)
+    for prec in (rr.RR_PREC_FP64, rr.RR_PREC_MIXED):
+        ref = []
+        h = rr.rr_setup(X.row_ptr, X.col_idx, 2000, 1000, lams[0], 50, precision=prec)
+        for j, lam in enumerate(lams):
+            if j:
+                rr.rr_set_lambda(h, lam)
+            w = torch.empty(1000, dtype=torch.float64, device="cuda")
+            ref.append((rr.rr_solve(h, yd, w, tol=1e-8), w.cpu().numpy()))
+        rr.rr_free(h)
+        base = rr.rr_setup(X.row_ptr, X.col_idx, 2000, 1000, lams[0], 50, precision=prec)
+        forks = [rr.rr_fork_lambda(base, lam) for lam in lams[1:]]
+        # one at a time on the forks
+        for j, f in enumerate(forks, start=1):
+            w = torch.empty(1000, dtype=torch.float64, device="cuda")
+            info = rr.rr_solve(f, yd, w, tol=1e-8)
+            assert info["iters"] == ref[j][0]["iters"]
+            assert np.array_equal(w.cpu().numpy(), ref[j][1])
+        # concurrently, freshly forked (their factors still in flight)
+        for f in forks:
+            rr.rr_free(f)
+        forks = [rr.rr_fork_lambda(base, lam) for lam in lams[1:]]
+        W = [torch.empty(1000, dtype=torch.float64, device="cuda") for _ in lams]
+        out = rr.rr_solve_many([base] + forks, [yd] * 3, W, tol=1e-8)
+        assert out["status"] == "RR_OK"
+        for j in range(3):
+            assert out["infos"][j]["iters"] == ref[j][0]["iters"]
+            assert np.array_equal(W[j].cpu().numpy(), ref[j][1])
+        with pytest.raises(rr.RRError) as e:
+            rr.rr_fork_lambda(forks[0], 1.0)
+        assert e.value.status == rr.RR_UNSUPPORTED
+        with pytest.raises(rr.RRError) as e:
+            rr.rr_prepare_lambdas(forks[0], [1.0])
+        assert e.value.status == rr.RR_UNSUPPORTED
+        with pytest.raises(rr.RRError) as e:
+            rr.rr_fork_lambda(base, -1.0)
+        assert e.value.status == rr.RR_INVALID_ARG
+        for f in forks:
+            rr.rr_free(f)
+        w = torch.empty(1000, dtype=torch.float64, device="cuda")
+        rr.rr_solve(base, yd, w, tol=1e-8)
+        assert np.array_equal(w.cpu().numpy(), ref[0][1])
+        rr.rr_free(base)
+
+
 def test_prepared_lambdas_give_identical_bits(rr):
     """rr_prepare_lambdas builds the coarse levels of further weights on a
     second stream; installing one by rr_set_lambda gives the same bits as
