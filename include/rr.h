@@ -195,7 +195,14 @@ void rr_default_options(rr_options *o);
  * (Eq. (prolong)), the Galerkin coarse operator P^T A P = X_c^T X_c +
  * lambda I (Section 3.2), its Cholesky factor (Section 4), and the damped
  * Jacobi smoother. Empty clusters are dropped (info k_eff). Synchronises the
- * stream before returning. o may be NULL (defaults). On success *out owns
+ * stream before returning, except (binary X) for the coarse factor and
+ * inverse, which are left running on a stream of the handle's own: every later
+ * call that uses the coarse level waits for them (a solve's stream waits on
+ * their event; rr_set_lambda, rr_prepare_lambdas, rr_solve_batch, rr_harvest,
+ * rr_bayes and rr_get_coarse wait on the host; in rr_solve_many only this
+ * handle's problem waits), so that forks (rr_fork_lambda) build their own
+ * factors meanwhile. A non-positive pivot of that factor is reported by the
+ * first solve (RR_NOT_SPD). o may be NULL (defaults). On success *out owns
  * the handle; release it with rr_free.
  * Errors: RR_INVALID_ARG (see rr_matrix; lambda <= 0 or not finite; k < 1 or
  * k > F; repeated or out-of-range init_centers), RR_UNSUPPORTED (nnz >= 2^31,

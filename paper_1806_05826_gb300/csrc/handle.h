@@ -128,8 +128,10 @@ struct rr_handle {
   rr::PcgScalars *St = nullptr;
   void *fcg_cache = nullptr;   // the FCG loop graph without a network (kept until lambda changes)
   // rr_fork_lambda: the handle whose X-dependent setup this one shares (nullptr:
-  // none), and the event recorded after this handle's coarse factor
+  // none); the event recorded after this handle's coarse factor (a fork's, or
+  // the one rr_setup leaves running on fst, its own stream)
   rr_handle *fork_of = nullptr;
   cudaEvent_t ready = nullptr;
+  cudaStream_t fst = nullptr;
   DevArena mem;
 };

@@ -1286,6 +1286,10 @@ void batch_free(BatchState *B) {
 
 extern "C" rr_status rr_solve_batch(rr_handle *h, int32_t nrhs, const double *Y, int32_t nlam,
                                     const double *lambdas, double *W, double tol, rr_info *infos) {
+  if (h && h->ready && !h->fork_of && cudaEventSynchronize(h->ready) != cudaSuccess) {
+    rr_set_error("%s", cudaGetErrorString(cudaGetLastError()));
+    return RR_CUDA_ERROR;
+  }
   NvtxRange nvtx_range("rr_solve_batch");
   using namespace rr;
   if (!h || !Y || !W || !lambdas || nrhs < 1 || nlam < 1 || !(tol > 0.0 && tol < 1.0)) {
@@ -1464,6 +1468,10 @@ extern "C" rr_status rr_solve_batch(rr_handle *h, int32_t nrhs, const double *Y,
 extern "C" rr_status rr_harvest(rr_handle *h, int32_t nrhs, const double *Y, double lambda,
                                 const double *Wref, double tol, int32_t max_iter, float *Xp,
                                 float *Tp, int64_t max_pairs, int64_t *n_pairs) {
+  if (h && h->ready && !h->fork_of && cudaEventSynchronize(h->ready) != cudaSuccess) {
+    rr_set_error("%s", cudaGetErrorString(cudaGetLastError()));
+    return RR_CUDA_ERROR;
+  }
   NvtxRange nvtx_range("rr_harvest");
   using namespace rr;
   if (!h || !Y || !Wref || !Xp || !Tp || !n_pairs || nrhs < 1 || max_iter < 1 || max_pairs < 1 ||

@@ -153,6 +153,57 @@ rr_status build_lambda(rr_handle *h, double lambda) {
   return RR_OK;
 }
 
+// The smoother at lambda (d, omega read back, and omega/d of the split form);
+// the coarse level is left to start_coarse_factor.
+rr_status build_smoother(rr_handle *h, double lambda) {
+  cudaStream_t st = h->st;
+  RR_CUDA(cudaMemsetAsync(h->max_bits, 0, sizeof(unsigned long long), st));
+  RR_LAUNCH(k_jacobi_setup, rr::grid_for(h->F, kThreads), kThreads, 0, st, h->F, lambda,
+            h->col_ptr, h->gsum, h->d, h->max_bits);
+  RR_LAUNCH(k_omega, 1, 32, 0, st, h->max_bits, h->omega_dev);
+  double om = 0.0;
+  RR_CUDA(cudaMemcpyAsync(&om, h->omega_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  RR_CUDA(cudaStreamSynchronize(st));
+  h->omega = om;
+  h->lambda = lambda;
+  return RR_OK;
+}
+
+// The coarse operator, factor and inverse at lambda (the same operations as
+// build_lambda), left running on the handle's factor stream behind h->ready.
+// Every later call that uses the coarse level waits for it (wait_coarse); a
+// non-positive pivot is reported by the first of them that checks the error
+// word (a solve).
+rr_status start_coarse_factor(rr_handle *h, double lambda) {
+  RR_CUDA(cudaStreamCreateWithFlags(&h->fst, cudaStreamNonBlocking));
+  RR_CUDA(cudaEventCreateWithFlags(&h->ready, cudaEventDisableTiming));
+  cudaStream_t st = h->fst;
+  const int32_t k = h->k_eff;
+  RR_TRY(rr::coarse_operator(k, h->G, h->s, lambda, h->Ac, st));
+  if (h->mu) {
+    RR_TRY(rr::eig_dvec(k, h->mu, lambda, h->dvec, st));
+  } else {
+    RR_CUDA(cudaMemcpyAsync(h->Lw, h->Ac, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, st));
+    RR_TRY(rr::cholesky(k, h->Lw, h->err, st));
+    RR_TRY(rr::chol_inverse(k, h->Lw, h->Linv, h->Ainv, st));
+    if (h->Ainv32) RR_TRY(rr::coarse_to_f32(k, h->Ainv, h->Ainv32, st));
+  }
+  RR_CUDA(cudaEventRecord(h->ready, st));
+  return RR_OK;
+}
+
+// Orders st after the coarse factor rr_setup left running (no host wait).
+rr_status wait_coarse(const rr_handle *h, cudaStream_t st) {
+  if (h->ready && !h->fork_of) RR_CUDA(cudaStreamWaitEvent(st, h->ready, 0));
+  return RR_OK;
+}
+
+// The same, on the host: before a call rebuilds or swaps the coarse buffers.
+rr_status wait_coarse_host(const rr_handle *h) {
+  if (h->ready && !h->fork_of) RR_CUDA(cudaEventSynchronize(h->ready));
+  return RR_OK;
+}
+
 // The coarse inverse and the smoother at lambda into a prepared slot, on the
 // prepare stream (the Cholesky form; the same operations as build_lambda).
 rr_status prepare_one(rr_handle *h, rr_handle::Prepared &P, double lambda) {
@@ -717,7 +768,8 @@ rr_status setup_impl(rr_handle *h, const rr_matrix *X, double lambda, int32_t k)
   RR_TRY(coarse_eigen_setup(h));
   if (h->opt.precision == RR_PREC_MIXED && !h->mu)
     RR_TRY(m.alloc(&h->Ainv32, (int64_t)k_eff * ((k_eff + 3) & ~3)));
-  RR_TRY(build_lambda(h, lambda));
+  // the smoother now; the coarse factor is started when rr_setup returns
+  RR_TRY(build_smoother(h, lambda));
 
   RR_TRY(phase(6));
   // ---- the patterns (built alongside) and the solve workspace
@@ -1258,7 +1310,7 @@ rr_status build_many_graph(int32_t n, rr_handle *const *hs, ManyGraph &G, std::v
     cp.conditional.type = cudaGraphCondTypeWhile;
     cp.conditional.size = 1;
     cudaGraphNode_t wait = nullptr, node;
-    if (h->fork_of && h->ready) RR_CUDA(cudaGraphAddEventWaitNode(&wait, G.g, nullptr, 0, h->ready));
+    if (h->ready) RR_CUDA(cudaGraphAddEventWaitNode(&wait, G.g, nullptr, 0, h->ready));
     RR_CUDA(cudaGraphAddNode(&node, G.g, wait ? &wait : nullptr, nullptr, wait ? 1 : 0, &cp));
     cudaStream_t cs = h->cap_stream;
     RR_CUDA(cudaStreamBeginCaptureToGraph(cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
@@ -1582,6 +1634,7 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
     h->st = user;
     cudaStreamDestroy(hp);
   }
+  if (s == RR_OK && X->layout != RR_DENSE_F32_ROWMAJOR) s = start_coarse_factor(h, lambda);
   if (s != RR_OK) {
     rr_free(h);
     return s;
@@ -1592,6 +1645,7 @@ rr_status rr_setup(const rr_matrix *X, double lambda, int32_t k, const rr_option
 }
 
 rr_status rr_set_lambda(rr_handle *h, double lambda) {
+  if (h) RR_TRY(wait_coarse_host(h));
   NvtxRange nvtx_range("rr_set_lambda");
   if (!h) {
     rr_set_error("rr_set_lambda: NULL handle");
@@ -1712,6 +1766,7 @@ rr_status rr_fork_lambda(rr_handle *base, double lambda, rr_handle **out) {
   f->mem.ptrs.clear();
   f->fork_of = base;
   f->ready = nullptr;
+  f->fst = nullptr;
   f->st = nullptr;
   f->cap_stream = nullptr;
   f->loop_graph = nullptr;
@@ -1753,6 +1808,7 @@ rr_status rr_fork_lambda(rr_handle *base, double lambda, rr_handle **out) {
 }
 
 rr_status rr_prepare_lambdas(rr_handle *h, const double *lambdas, int32_t n) {
+  if (h) RR_TRY(wait_coarse_host(h));
   NvtxRange nvtx_range("rr_prepare_lambdas");
   if (!h || (n > 0 && !lambdas) || n < 0 || n > rr_handle::kPrepared) {
     rr_set_error("rr_prepare_lambdas: need a handle and 0 <= n <= %d lambdas",
@@ -1795,6 +1851,7 @@ rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info
   }
   const auto t0 = std::chrono::steady_clock::now();
   const int64_t l0 = rr_launch_counter;
+  RR_TRY(wait_coarse(h, h->st));
   rr_status s = h->opt.solver == RR_SOLVER_TLFCG ? solve_fcg_impl(h, nullptr, y, w, tol, info)
                                                  : solve_impl(h, y, w, tol, info);
   if (s == RR_OK || s == RR_NOT_CONVERGED) {
@@ -1818,6 +1875,7 @@ rr_status rr_solve(rr_handle *h, const double *y, double *w, double tol, rr_info
 
 rr_status rr_solve_fcg(rr_handle *h, const rr_mlp *net, const double *y, double *w, double tol,
                        rr_info *info) {
+  if (h) RR_TRY(wait_coarse(h, h->st));
   NvtxRange nvtx_range("rr_solve_fcg");
   if (!h || !y || !w) {
     rr_set_error("rr_solve_fcg: handle, y and w must not be NULL");
@@ -1925,6 +1983,7 @@ rr_status rr_precondition(rr_handle *h, const double *r, double *z) {
     return RR_INVALID_ARG;
   }
   int n = 0;
+  RR_TRY(wait_coarse(h, h->st));
   RR_TRY(apply_precond(h, r, z, nullptr, &n, false, h->st));
   return RR_OK;
 }
@@ -1981,6 +2040,7 @@ rr_status rr_get_coarse(const rr_handle *h, double *Ac_host, int64_t *G_host) {
     rr_set_error("rr_get_coarse: NULL handle");
     return RR_INVALID_ARG;
   }
+  RR_TRY(wait_coarse_host(h));
   if (h->dense && G_host) {
     rr_set_error("rr_get_coarse: the integer Gram exists for binary X only");
     return RR_UNSUPPORTED;
@@ -2006,6 +2066,7 @@ rr_status rr_bayes(rr_handle *h, const double *y, const rr_bayes_params *p, int3
     rr_set_error("rr_bayes: not supported on a handle from rr_fork_lambda");
     return RR_UNSUPPORTED;
   }
+  if (h) RR_TRY(wait_coarse_host(h));
   NvtxRange nvtx_range("rr_bayes");
   if (!h || !y || !p) {
     rr_set_error("rr_bayes: handle, y and params must not be NULL");
@@ -2096,6 +2157,11 @@ void rr_free(rr_handle *h) {
     return;
   }
   cudaStreamSynchronize(h->st);
+  if (h->fst) {
+    cudaStreamSynchronize(h->fst);
+    cudaStreamDestroy(h->fst);
+  }
+  if (h->ready) cudaEventDestroy(h->ready);
   destroy_graph(h);
   rr::batch_free(h->batch);
   h->batch = nullptr;
