@@ -1015,7 +1015,7 @@ rr_status batch_factors(rr_handle *h, BatchState *B, int32_t nlam, const double 
     } else {
       RR_TRY(coarse_operator(k, h->G, h->s, lambdas[l], B->Ac, st));
       RR_CUDA(cudaMemcpyAsync(B->Lw, B->Ac, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, st));
-      RR_TRY(cholesky(k, B->Lw, h->err, st));
+      RR_TRY(cholesky(k, B->Lw, B->Linv, h->err, st));
       RR_TRY(chol_inverse(k, B->Lw, B->Linv, B->Ainv, st));
     }
     RR_LAUNCH(k_binv_pad, grid_for((int64_t)kpad * kpad, kThreads), kThreads, 0, st, k, kpad,

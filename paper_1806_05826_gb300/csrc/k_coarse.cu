@@ -188,71 +188,85 @@ __global__ void k_coarse_operator(int32_t k, const double *__restrict__ G,
 
 constexpr int kNB = 32;   // Cholesky panel width
 
-// Factors the nb x nb diagonal block at j0 in shared memory (right-looking).
-__global__ void k_chol_diag(int32_t k, int32_t j0, double *__restrict__ L, int32_t *err) {
-  __shared__ double a[kNB][kNB + 1];
-  __shared__ int bad;
+// Factors the nb x nb diagonal block at j0 in one warp, lane i holding row i
+// in registers (right-looking: the pivot and each column entry reach the other
+// lanes by shuffles, so no step waits on a barrier), and, when Wd is given,
+// writes W = L11^{-1} (lower, 32 x 32 row-major, zero elsewhere) there for the
+// panel: lane c builds column c of W by forward substitution. Rows past nb are
+// an identity block.
+__global__ void __launch_bounds__(32) k_chol_diag(int32_t k, int32_t j0, double *__restrict__ L,
+                                                  double *__restrict__ Wd, int32_t *err) {
+  __shared__ double ls[kNB][kNB + 1];
+  const int i = threadIdx.x;
   const int nb = min(kNB, k - j0);
-  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
-    const int i = idx / nb, j = idx % nb;
-    a[i][j] = L[(int64_t)(j0 + i) * k + j0 + j];
-  }
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    if (threadIdx.x == 0) {
-      const double piv = a[j][j];
-      if (!(piv > 0.0)) {
-        bad = 1;
-        a[j][j] = 1.0;
-      } else {
-        a[j][j] = sqrt(piv);
-      }
-    }
-    __syncthreads();
-    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) a[i][j] /= a[j][j];
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
-      const int i = idx / nb, m = idx % nb;
-      if (i > j && m > j && m <= i) a[i][m] -= a[i][j] * a[m][j];
-    }
-    __syncthreads();
-  }
-  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
-    const int i = idx / nb, j = idx % nb;
-    L[(int64_t)(j0 + i) * k + j0 + j] = (j <= i) ? a[i][j] : 0.0;
-  }
-  if (threadIdx.x == 0 && bad) set_dev_error(err, DEV_NOT_SPD);
-}
-
-// Rows below the diagonal block: L21 = A21 L11^{-T}, one thread per row,
-// kPanelThreads rows per block (the rows spread over many SMs: each row's
-// solve is a chain of FP64 operations).
-constexpr int kPanelThreads = 32;
-__global__ void __launch_bounds__(kPanelThreads) k_chol_panel(int32_t k, int32_t j0,
-                                                              double *__restrict__ L) {
-  __shared__ double l11[kNB][kNB + 1];
-  const int nb = min(kNB, k - j0);
-  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
-    const int i = idx / nb, j = idx % nb;
-    l11[i][j] = L[(int64_t)(j0 + i) * k + j0 + j];
-  }
-  __syncthreads();
-  for (int64_t i = j0 + nb + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    double x[kNB];
-    double *row = L + i * k + j0;
+  double a[kNB];
 #pragma unroll
-    for (int j = 0; j < kNB; ++j) {
-      if (j < nb) {
-        double v = row[j];
-        for (int m = 0; m < j; ++m) v -= x[m] * l11[j][m];
-        x[j] = v / l11[j][j];
-      }
+  for (int j = 0; j < kNB; ++j)
+    a[j] = (i < nb && j <= i) ? L[(int64_t)(j0 + i) * k + j0 + j] : (i == j ? 1.0 : 0.0);
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < kNB; ++j) {
+    const double piv = __shfl_sync(0xffffffffu, a[j], j);
+    double dj;
+    if (!(piv > 0.0)) {
+      bad = true;
+      dj = 1.0;
+    } else {
+      dj = sqrt(piv);
     }
+    if (i == j) a[j] = dj;
+    else if (i > j) a[j] /= dj;
+#pragma unroll
+    for (int m = j + 1; m < kNB; ++m) {
+      const double lmj = __shfl_sync(0xffffffffu, a[j], m);
+      if (i >= m) a[m] -= a[j] * lmj;
+    }
+  }
+  if (i < nb) {
 #pragma unroll
     for (int j = 0; j < kNB; ++j)
-      if (j < nb) row[j] = x[j];
+      if (j < nb) L[(int64_t)(j0 + i) * k + j0 + j] = (j <= i) ? a[j] : 0.0;
+  }
+  if (bad && i == 0) set_dev_error(err, DEV_NOT_SPD);
+  if (!Wd) return;
+#pragma unroll
+  for (int j = 0; j < kNB; ++j) ls[i][j] = (j <= i) ? a[j] : 0.0;
+  __syncwarp();
+  const int c = i;
+  double w[kNB];
+#pragma unroll
+  for (int r = 0; r < kNB; ++r) {
+    double v = (r == c) ? 1.0 : 0.0;
+#pragma unroll
+    for (int m = 0; m < r; ++m) v -= ls[r][m] * w[m];
+    w[r] = (r < c) ? 0.0 : v / ls[r][r];
+  }
+#pragma unroll
+  for (int r = 0; r < kNB; ++r) Wd[r * kNB + c] = w[r];
+}
+
+// Rows below the diagonal block: L21 = A21 L11^{-T} = A21 W^T, a product with
+// no dependent chain: one thread per entry of kPanelRows rows, W and the
+// block's rows staged in shared memory (each block owns whole rows, read
+// before they are overwritten).
+constexpr int kPanelRows = 8;
+__global__ void __launch_bounds__(kPanelRows * kNB) k_chol_panel(int32_t k, int32_t j0,
+                                                                 double *__restrict__ L,
+                                                                 const double *__restrict__ Wd) {
+  __shared__ double ws[kNB][kNB + 1];
+  __shared__ double as[kPanelRows][kNB + 1];
+  const int nb = min(kNB, k - j0);
+  for (int idx = threadIdx.x; idx < kNB * kNB; idx += blockDim.x)
+    ws[idx / kNB][idx % kNB] = Wd[idx];
+  const int r = threadIdx.x / kNB, c = threadIdx.x % kNB;
+  const int64_t i = (int64_t)j0 + nb + (int64_t)blockIdx.x * kPanelRows + r;
+  const bool ok = i < k && c < nb;
+  if (ok) as[r][c] = L[i * k + j0 + c];
+  __syncthreads();
+  if (ok) {
+    double s = 0.0;
+    for (int m = 0; m <= c; ++m) s += as[r][m] * ws[c][m];
+    L[i * k + j0 + c] = s;
   }
 }
 
@@ -437,13 +451,13 @@ rr_status coarse_operator(int32_t k, const double *G, const double *s, double la
   return RR_OK;
 }
 
-rr_status cholesky(int32_t k, double *L, int32_t *err, cudaStream_t st) {
+rr_status cholesky(int32_t k, double *L, double *scratch, int32_t *err, cudaStream_t st) {
   for (int32_t j0 = 0; j0 < k; j0 += kNB) {
-    RR_LAUNCH(k_chol_diag, 1, kThreads, 0, st, k, j0, L, err);
     const int32_t rest = k - j0 - std::min(kNB, k - j0);
+    RR_LAUNCH(k_chol_diag, 1, 32, 0, st, k, j0, L, rest > 0 ? scratch : nullptr, err);
     if (rest > 0) {
-      RR_LAUNCH(k_chol_panel, (unsigned)((rest + kPanelThreads - 1) / kPanelThreads), kPanelThreads,
-                0, st, k, j0, L);
+      RR_LAUNCH(k_chol_panel, (unsigned)((rest + kPanelRows - 1) / kPanelRows), kPanelRows * kNB,
+                0, st, k, j0, L, scratch);
       const int64_t nt = (rest + 31) / 32;
       RR_LAUNCH(k_chol_update, tri_tiles(nt), kThreads, 0, st, k, j0, L);
     }

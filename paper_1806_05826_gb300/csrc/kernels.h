@@ -163,7 +163,8 @@ rr_status gram_exact_cuda_cores(int32_t k, int32_t k_pad, int64_t n_pad, const i
 rr_status coarse_operator(int32_t k, const double *G, const double *s, double lambda, double *Ac,
                           cudaStream_t st);
 // In-place lower Cholesky of Ac (k x k); records DEV_NOT_SPD on a pivot <= 0.
-rr_status cholesky(int32_t k, double *L, int32_t *err, cudaStream_t st);
+// scratch: k x k doubles it may overwrite (the inverses of the diagonal blocks).
+rr_status cholesky(int32_t k, double *L, double *scratch, int32_t *err, cudaStream_t st);
 // Ainv = L^{-T} L^{-1} (full symmetric). Linv: k x k workspace.
 rr_status chol_inverse(int32_t k, const double *L, double *Linv, double *Ainv, cudaStream_t st);
 

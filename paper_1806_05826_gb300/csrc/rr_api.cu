@@ -132,7 +132,7 @@ rr_status build_lambda(rr_handle *h, double lambda) {
     RR_TRY(rr::eig_dvec(k, h->mu, lambda, h->dvec, st));
   } else {
     RR_CUDA(cudaMemcpyAsync(h->Lw, h->Ac, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, st));
-    RR_TRY(rr::cholesky(k, h->Lw, h->err, st));
+    RR_TRY(rr::cholesky(k, h->Lw, h->Linv, h->err, st));
     RR_TRY(rr::chol_inverse(k, h->Lw, h->Linv, h->Ainv, st));
     if (h->Ainv32) RR_TRY(rr::coarse_to_f32(k, h->Ainv, h->Ainv32, st));
   }
@@ -184,7 +184,7 @@ rr_status start_coarse_factor(rr_handle *h, double lambda) {
     RR_TRY(rr::eig_dvec(k, h->mu, lambda, h->dvec, st));
   } else {
     RR_CUDA(cudaMemcpyAsync(h->Lw, h->Ac, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, st));
-    RR_TRY(rr::cholesky(k, h->Lw, h->err, st));
+    RR_TRY(rr::cholesky(k, h->Lw, h->Linv, h->err, st));
     RR_TRY(rr::chol_inverse(k, h->Lw, h->Linv, h->Ainv, st));
     if (h->Ainv32) RR_TRY(rr::coarse_to_f32(k, h->Ainv, h->Ainv32, st));
   }
@@ -222,7 +222,7 @@ rr_status prepare_one(rr_handle *h, rr_handle::Prepared &P, double lambda) {
   P.valid = false;
   RR_TRY(rr::coarse_operator(k, h->G, h->s, lambda, h->prep_Ac, st));
   RR_CUDA(cudaMemcpyAsync(h->prep_Lw, h->prep_Ac, sizeof(double) * kk, cudaMemcpyDeviceToDevice, st));
-  RR_TRY(rr::cholesky(k, h->prep_Lw, h->err, st));
+  RR_TRY(rr::cholesky(k, h->prep_Lw, h->prep_Linv, h->err, st));
   RR_TRY(rr::chol_inverse(k, h->prep_Lw, h->prep_Linv, P.Ainv, st));
   if (P.Ainv32) RR_TRY(rr::coarse_to_f32(k, P.Ainv, P.Ainv32, st));
   RR_CUDA(cudaMemsetAsync(P.max_bits, 0, sizeof(unsigned long long), st));
@@ -1736,7 +1736,7 @@ rr_status fork_impl(rr_handle *base, double lambda, rr_handle *f) {
     RR_TRY(rr::eig_dvec((int32_t)k, f->mu, lambda, f->dvec, st));
   } else {
     RR_CUDA(cudaMemcpyAsync(f->Lw, f->Ac, sizeof(double) * (size_t)k * k, cudaMemcpyDeviceToDevice, st));
-    RR_TRY(rr::cholesky((int32_t)k, f->Lw, f->err, st));
+    RR_TRY(rr::cholesky((int32_t)k, f->Lw, f->Linv, f->err, st));
     RR_TRY(rr::chol_inverse((int32_t)k, f->Lw, f->Linv, f->Ainv, st));
     if (f->Ainv32) RR_TRY(rr::coarse_to_f32((int32_t)k, f->Ainv, f->Ainv32, st));
   }
