@@ -188,61 +188,66 @@ __global__ void k_coarse_operator(int32_t k, const double *__restrict__ G,
 
 constexpr int kNB = 32;   // Cholesky panel width
 
-// Factors the nb x nb diagonal block at j0 in one warp, lane i holding row i
-// in registers (right-looking: the pivot and each column entry reach the other
-// lanes by shuffles, so no step waits on a barrier), and, when Wd is given,
-// writes W = L11^{-1} (lower, 32 x 32 row-major, zero elsewhere) there for the
-// panel: lane c builds column c of W by forward substitution. Rows past nb are
-// an identity block.
-__global__ void __launch_bounds__(32) k_chol_diag(int32_t k, int32_t j0, double *__restrict__ L,
-                                                  double *__restrict__ Wd, int32_t *err) {
-  __shared__ double ls[kNB][kNB + 1];
-  const int i = threadIdx.x;
+// Factors the nb x nb diagonal block at j0 in shared memory (right-looking,
+// the block's threads over the entries) and, when Wd is given, writes
+// W = L11^{-1} (lower, 32 x 32 row-major, zero elsewhere) there for the panel:
+// the same elimination applied to the identity (row j of W divided by L_jj,
+// then subtracted L_ij times from every row i > j).
+__global__ void k_chol_diag(int32_t k, int32_t j0, double *__restrict__ L, double *__restrict__ Wd,
+                            int32_t *err) {
+  __shared__ double a[kNB][kNB + 1];
+  __shared__ double w[kNB][kNB + 1];
+  __shared__ int bad;
   const int nb = min(kNB, k - j0);
-  double a[kNB];
-#pragma unroll
-  for (int j = 0; j < kNB; ++j)
-    a[j] = (i < nb && j <= i) ? L[(int64_t)(j0 + i) * k + j0 + j] : (i == j ? 1.0 : 0.0);
-  bool bad = false;
-#pragma unroll
-  for (int j = 0; j < kNB; ++j) {
-    const double piv = __shfl_sync(0xffffffffu, a[j], j);
-    double dj;
-    if (!(piv > 0.0)) {
-      bad = true;
-      dj = 1.0;
-    } else {
-      dj = sqrt(piv);
-    }
-    if (i == j) a[j] = dj;
-    else if (i > j) a[j] /= dj;
-#pragma unroll
-    for (int m = j + 1; m < kNB; ++m) {
-      const double lmj = __shfl_sync(0xffffffffu, a[j], m);
-      if (i >= m) a[m] -= a[j] * lmj;
-    }
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx / nb, j = idx % nb;
+    a[i][j] = L[(int64_t)(j0 + i) * k + j0 + j];
   }
-  if (i < nb) {
-#pragma unroll
-    for (int j = 0; j < kNB; ++j)
-      if (j < nb) L[(int64_t)(j0 + i) * k + j0 + j] = (j <= i) ? a[j] : 0.0;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (threadIdx.x == 0) {
+      const double piv = a[j][j];
+      if (!(piv > 0.0)) {
+        bad = 1;
+        a[j][j] = 1.0;
+      } else {
+        a[j][j] = sqrt(piv);
+      }
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) a[i][j] /= a[j][j];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+      const int i = idx / nb, m = idx % nb;
+      if (i > j && m > j && m <= i) a[i][m] -= a[i][j] * a[m][j];
+    }
+    __syncthreads();
   }
-  if (bad && i == 0) set_dev_error(err, DEV_NOT_SPD);
+  for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+    const int i = idx / nb, j = idx % nb;
+    L[(int64_t)(j0 + i) * k + j0 + j] = (j <= i) ? a[i][j] : 0.0;
+  }
+  if (threadIdx.x == 0 && bad) set_dev_error(err, DEV_NOT_SPD);
   if (!Wd) return;
-#pragma unroll
-  for (int j = 0; j < kNB; ++j) ls[i][j] = (j <= i) ? a[j] : 0.0;
-  __syncwarp();
-  const int c = i;
-  double w[kNB];
-#pragma unroll
-  for (int r = 0; r < kNB; ++r) {
-    double v = (r == c) ? 1.0 : 0.0;
-#pragma unroll
-    for (int m = 0; m < r; ++m) v -= ls[r][m] * w[m];
-    w[r] = (r < c) ? 0.0 : v / ls[r][r];
+  for (int idx = threadIdx.x; idx < kNB * kNB; idx += blockDim.x) {
+    const int i = idx / kNB, c = idx % kNB;
+    w[i][c] = (i == c) ? 1.0 : 0.0;
   }
-#pragma unroll
-  for (int r = 0; r < kNB; ++r) Wd[r * kNB + c] = w[r];
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    for (int c = threadIdx.x; c <= j; c += blockDim.x) w[j][c] /= a[j][j];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kNB * kNB; idx += blockDim.x) {
+      const int i = idx / kNB, c = idx % kNB;
+      if (i > j && i < nb && c <= j) w[i][c] -= a[i][j] * w[j][c];
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < kNB * kNB; idx += blockDim.x) {
+    const int i = idx / kNB, c = idx % kNB;
+    Wd[idx] = (i < nb && c < nb && c <= i) ? w[i][c] : 0.0;
+  }
 }
 
 // Rows below the diagonal block: L21 = A21 L11^{-T} = A21 W^T, a product with
@@ -454,7 +459,7 @@ rr_status coarse_operator(int32_t k, const double *G, const double *s, double la
 rr_status cholesky(int32_t k, double *L, double *scratch, int32_t *err, cudaStream_t st) {
   for (int32_t j0 = 0; j0 < k; j0 += kNB) {
     const int32_t rest = k - j0 - std::min(kNB, k - j0);
-    RR_LAUNCH(k_chol_diag, 1, 32, 0, st, k, j0, L, rest > 0 ? scratch : nullptr, err);
+    RR_LAUNCH(k_chol_diag, 1, kThreads, 0, st, k, j0, L, rest > 0 ? scratch : nullptr, err);
     if (rest > 0) {
       RR_LAUNCH(k_chol_panel, (unsigned)((rest + kPanelRows - 1) / kPanelRows), kPanelRows * kNB,
                 0, st, k, j0, L, scratch);
