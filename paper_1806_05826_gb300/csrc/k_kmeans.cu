@@ -697,9 +697,11 @@ __global__ void __launch_bounds__(kThreads) k_lloyd_pull(
     const int64_t *__restrict__ dptr, const int32_t *__restrict__ dcount,
     const typename DeltaEntry<P>::T *__restrict__ dlist, const int32_t *__restrict__ order,
     const int64_t *__restrict__ task_ptr, const int32_t *__restrict__ task_it, int64_t n_tasks,
-    int32_t *work_ctr, int32_t *__restrict__ D) {
+    int32_t *work_ctr, int32_t *__restrict__ D, const unsigned long long *__restrict__ work,
+    unsigned long long pull_work) {
   using E = DeltaEntry<P>;
   using T = typename E::T;
+  if (*work <= pull_work) return;   // the push form applies this step's lists
   extern __shared__ int32_t acc[];
   __shared__ int32_t cur;
   __shared__ int32_t touched;
@@ -793,8 +795,12 @@ __global__ void k_lloyd_push(int64_t N, int32_t k, const int64_t *__restrict__ r
                              const int32_t *__restrict__ dcount,
                              const typename DeltaEntry<P>::T *__restrict__ dlist,
                              int32_t *__restrict__ D, const int32_t *__restrict__ rows,
-                             const int32_t *__restrict__ nrows) {
+                             const int32_t *__restrict__ nrows,
+                             const unsigned long long *__restrict__ work,
+                             unsigned long long pull_work) {
   using E = DeltaEntry<P>;
+  const unsigned long long wk = *work;
+  if (wk == 0 || wk > pull_work) return;   // nothing to apply, or the pull form does it
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1072,23 +1078,21 @@ rr_status lloyd_delta_apply(int64_t N, int64_t F, const int64_t *row_ptr, const 
   RR_LAUNCH(k_row_delta<P>, std::min<int64_t>((N + warps_per_cta - 1) / warps_per_cta, kSMs * 16),
             32 * warps_per_cta, hsmem, st, N, k, row_ptr, col_idx, b.prev, b.labels, b.mptr,
             dlist, b.dcount, (unsigned long long *)b.work, rows, nrows);
-  unsigned long long work = 0;
-  RR_CUDA(cudaMemcpyAsync(&work, b.work, sizeof(work), cudaMemcpyDeviceToHost, st));
-  RR_CUDA(cudaStreamSynchronize(st));
-  if (work > pull_work) {
-    RR_CUDA(cudaMemsetAsync(b.work_ctr, 0, sizeof(int32_t), st));
-    const size_t smem = sizeof(int32_t) * (size_t)k;
-    RR_CUDA(cudaFuncSetAttribute(k_lloyd_pull<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)std::max<size_t>(smem, 1)));
-    int per_sm = 0;
-    RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lloyd_pull<P>, kThreads, smem));
-    RR_LAUNCH(k_lloyd_pull<P>, kSMs * std::max(1, per_sm), kThreads, smem, st, k, col_ptr,
-              row_idx, b.mptr, b.dcount, dlist, b.order, b.task_ptr, b.task_it, b.n_tasks,
-              b.work_ctr, b.D);
-  } else if (work > 0) {
-    RR_LAUNCH(k_lloyd_push<P>, grid_for(N, kWarps), kThreads, 0, st, N, k, row_ptr, col_idx,
-              b.mptr, b.dcount, dlist, b.D, rows, nrows);
-  }
+  // pull per feature when the lists' work exceeds pull_work, else push per
+  // row: both launched, each kernel reads the work on the device and one
+  // returns at once (no host round trip)
+  const unsigned long long *wk = (const unsigned long long *)b.work;
+  RR_CUDA(cudaMemsetAsync(b.work_ctr, 0, sizeof(int32_t), st));
+  const size_t smem = sizeof(int32_t) * (size_t)k;
+  RR_CUDA(cudaFuncSetAttribute(k_lloyd_pull<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)std::max<size_t>(smem, 1)));
+  int per_sm = 0;
+  RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lloyd_pull<P>, kThreads, smem));
+  RR_LAUNCH(k_lloyd_pull<P>, kSMs * std::max(1, per_sm), kThreads, smem, st, k, col_ptr,
+            row_idx, b.mptr, b.dcount, dlist, b.order, b.task_ptr, b.task_it, b.n_tasks,
+            b.work_ctr, b.D, wk, pull_work);
+  RR_LAUNCH(k_lloyd_push<P>, grid_for(N, kWarps), kThreads, 0, st, N, k, row_ptr, col_idx,
+            b.mptr, b.dcount, dlist, b.D, rows, nrows, wk, pull_work);
   return RR_OK;
 }
 
