@@ -94,9 +94,9 @@ __device__ __forceinline__ bool seed_pulls(int64_t nc, int64_t N, int64_t nnz, d
 }
 
 // Frequent features (at least kHotMin and N/128 rows; at most kHotBins of them)
-// get a bin of a per-block shared histogram in the overlap pass: every row of a
-// large centre holds most of them, and counting them in shared memory first
-// keeps those increments off a few global addresses.
+// get a bin of a per-block shared histogram in the push form of the overlap
+// pass: most rows of a centre hold many of them, and counting them in shared
+// memory first keeps those increments off a few global addresses.
 constexpr int kHotBins = 2048;
 constexpr int64_t kHotMin = 64;
 
