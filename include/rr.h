@@ -159,7 +159,7 @@ typedef struct {
   int64_t seed_pull_work;       /* a k-means++ round whose centre c's row entries (estimated as
                                    n_c nnz / N) exceed this counts the overlaps with c column by
                                    column against a bitmap of c's rows (pull), else row by row
-                                   with integer atomics (push); 0 = default (5e5), negative =
+                                   with integer atomics (push); 0 = default (7e5), negative =
                                    always push. Centres are identical either way */
   void *stream;                 /* cudaStream_t for all work; NULL = legacy default stream */
 } rr_options;

@@ -101,8 +101,8 @@ rr_status kmeanspp_seed(int64_t N, int64_t F, int64_t nnz, const int64_t *row_pt
                         int32_t k, uint64_t seed, int64_t pull_work, KmeansBuffers &b,
                         cudaStream_t st);
 // default pull threshold: a centre's overlaps are pulled when pushing them
-// would take more than about 5e5 atomic increments
-constexpr double kSeedPullWork = 5.0e5;
+// would take more than about 7e5 atomic increments
+constexpr double kSeedPullWork = 7.0e5;
 
 // labels <- -1 except labels[centers[S]] = S; prev <- -1; D <- 0.
 // tiles of features of the seeding pass (tile sums in part_i)
