@@ -70,6 +70,10 @@ def test_default_options_and_invalid_args_without_gpu(lib):
     # a dense X needs values and no CSR arrays
     X.layout = rr.RR_DENSE_F32_ROWMAJOR
     assert L.rr_setup(ctypes.byref(X), 1.0, 1, None, ctypes.byref(out)) == rr.RR_INVALID_ARG
+    # a fork needs a base handle and a place for the result; its lambda is checked
+    assert L.rr_fork_lambda(None, 1.0, ctypes.byref(out)) == rr.RR_INVALID_ARG
+    assert "rr_fork_lambda" in rr.rr_last_error()
+    assert L.rr_solve_many(0, None, None, None, 1e-8, None, None) == rr.RR_INVALID_ARG
 
 
 def header_prototypes():
