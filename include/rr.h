@@ -244,7 +244,8 @@ rr_status rr_prepare_lambdas(rr_handle *h, const double *lambdas, int32_t n);
  * the fork's stream, and rr_solve_many starts the fork's problem only once it
  * is done (the other problems start at once). base must outlive its forks, and
  * is not otherwise changed; a fork of a fork, or of a dense-X handle, is not
- * supported. rr_solve_batch, rr_bayes and rr_prepare_lambdas reject forks.
+ * supported. rr_solve_batch, rr_harvest, rr_bayes and rr_prepare_lambdas
+ * reject forks (RR_UNSUPPORTED).
  * rr_free(fork) frees only what the fork owns. Device memory: about 13 F + 3 N
  * doubles plus the coarse level (3 k_eff^2 doubles) and the operator's
  * intermediate vectors. Errors: RR_INVALID_ARG (NULL argument, lambda not

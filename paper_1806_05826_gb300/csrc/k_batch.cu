@@ -1468,6 +1468,10 @@ extern "C" rr_status rr_solve_batch(rr_handle *h, int32_t nrhs, const double *Y,
 extern "C" rr_status rr_harvest(rr_handle *h, int32_t nrhs, const double *Y, double lambda,
                                 const double *Wref, double tol, int32_t max_iter, float *Xp,
                                 float *Tp, int64_t max_pairs, int64_t *n_pairs) {
+  if (h && h->fork_of) {
+    rr_set_error("rr_harvest: not supported on a handle from rr_fork_lambda");
+    return RR_UNSUPPORTED;
+  }
   if (h && h->ready && !h->fork_of && cudaEventSynchronize(h->ready) != cudaSuccess) {
     rr_set_error("%s", cudaGetErrorString(cudaGetLastError()));
     return RR_CUDA_ERROR;
